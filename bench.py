@@ -1,0 +1,299 @@
+"""Benchmark: multimode Floquet eigensolves per second on one GB300 (or N, weak scaling).
+
+Workload (one step): the spin-1 two-mode system H = w0 Fz + O1 cos(w1 t) Fx + O2 cos(w2 t) Fz,
+w = (1, (sqrt5-1)/2), N = (10, 10) -> n = 1323, for 64 seeded amplitude pairs (O1, O2) ~
+U[0.05, 0.5]^2 (seed 1); per system: H_F assembly, full eigendecomposition, U(t, 0) at 64 times
+over 2 pi / w1 and Pbar.  Synthetic inputs; the per-step working set (~6 GB) exceeds L2, so no
+flush is needed between steps.  With N ranks each rank solves its own 64 systems (seed 1 + rank).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+    python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "spin1_bichromatic_n1323_x64"
+METRIC = "floquet_eigensolves_per_s"
+COUNT, NT = 64, 64
+
+# peaks: measured copy bandwidth / bf16 GEMM (generated file); FP64 / FP32 ALU peaks from
+# the nominal 1.25 TFLOP/s FP64 and 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz.
+FP64_ALU_PEAK = 1.25e12
+FP32_ALU_PEAK = 152 * 128 * 2 * 2.07e9
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+class Clocks:
+    """nvidia-smi sampling (SM clock, throttle reasons) during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def stage_flops(stage: str, n: int, nt: int) -> float:
+    """Algorithmic real flops per system for a stage (LAPACK counts for the reduction and the
+    back-transform; direct sums for U)."""
+    if stage == "hetrd":
+        return 16.0 / 3.0 * n ** 3
+    if stage == "backtransform":
+        return 8.0 * n ** 3
+    if stage == "refine":
+        return 8.0 * n ** 3 + 8.0 * n ** 3  # R and S (Hermitian halves) + X E
+    if stage == "outputs":
+        return 8.0 * nt * n * n
+    return 0.0
+
+
+def cpu_baseline_oracle(problems, budget_s: float = 25.0):
+    """The FP64 oracle on a bounded sample: system 0's H_F build, a bounded number of cyclic
+    Jacobi sweeps, U and Pbar, scaled to a full solve by the sweep count the oracle needs for that
+    system (stored with the golden results when available, else 10)."""
+    from oracle import oracle as O
+
+    p = problems[0]
+    t = np.array([k * p.period() / NT for k in range(NT)])
+    t0 = time.perf_counter()
+    HF = O.build_hf(p)
+    t_build = time.perf_counter() - t0
+    # time whole sweeps until the budget is spent (at least one)
+    ts = time.perf_counter()
+    _, _, _, sw = O.eigh(HF, max_sweeps=1)
+    t_sweep = time.perf_counter() - ts
+    sweeps_needed = 10
+    gold = os.path.join(ROOT, "tests", "golden", "spin1_c1_sys0.npz")
+    if os.path.exists(gold):
+        sweeps_needed = int(np.load(gold)["sweeps"])
+    n = p.n
+    # U and Pbar with stand-in eigenpairs of the right shape (their cost does not depend on values)
+    E = np.linspace(-1, 1, n)
+    Z = np.eye(n, dtype=np.complex128)
+    tu = time.perf_counter()
+    O.time_evolution(p, E, Z, t[:4], 0.0)
+    t_u = (time.perf_counter() - tu) * NT / 4
+    tp = time.perf_counter()
+    O.transition_avg(p, E, Z)
+    t_p = time.perf_counter() - tp
+    total = t_build + sweeps_needed * t_sweep + t_u + t_p
+    return {"value": 1.0 / total, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"system 0 of the workload: H_F build ({t_build:.2f}s), 1 of {sweeps_needed} "
+                       f"cyclic Jacobi sweeps ({t_sweep:.1f}s, scaled), U at 4 of {NT} times (scaled) "
+                       f"and Pbar; single thread; full solve estimated at {total:.0f}s")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2005_03426_gb300 import workloads as W
+
+    problems = W.spin1_amplitude_set(COUNT, seed=1)
+    times = []
+    for _ in range(args.warmup + args.steps):
+        cb = cpu_baseline_oracle(problems)
+        times.append(1.0 / cb["value"])
+    tt = np.mean(times[args.warmup:]) if args.steps else times[-1]
+    value = 1.0 / tt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tt * 1e3 * COUNT, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "systems_per_step": COUNT, "n": 1323, "nt": NT},
+            "cpu_baseline": {**cb, "value": value},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2005_03426_gb300 import mmf as M
+    from paper_2005_03426_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    prec = M.MMF_MIXED if args.precision == "mixed" else M.MMF_FP64
+    problems = W.spin1_amplitude_set(COUNT, seed=1 + rank)
+    ctx = M.Context(local, stream=stream.cuda_stream)
+    systems = [M.System(ctx, p) for p in problems]
+    batch = M.Batch(ctx, systems, prec, NT)
+    ts = np.stack([W.time_grid(p, NT) for p in problems])
+    batch.set_times(0.0, ts)
+
+    for _ in range(max(args.warmup, 3)):
+        batch.run()
+    st = batch.sync()
+
+    # device-resident timed region
+    batch.timing(args.steps)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            launches += batch.run()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    stage, runs = batch.stage_ms()
+    batch.timing(0)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = COUNT * world / (ms / 1e3)
+
+    # end to end through the public API: H2D of inputs, run, D2H of E, U, Pbar every step
+    hE = torch.empty(batch.nE, dtype=torch.float64).pin_memory().numpy()
+    hU = torch.empty(max(batch.nU, 1), dtype=torch.complex128).pin_memory().numpy()
+    hP = torch.empty(batch.nP, dtype=torch.float64).pin_memory().numpy()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        batch.upload()
+        batch.run()
+        batch.results(hE, hU, hP)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = 16 * sum(p.D * p.D * (1 + sum(len(c) for c in p.couplings)) for p in problems) + 8 * ts.size
+    d2h = hE.nbytes + 16 * batch.nU + hP.nbytes
+
+    # accuracy of system 0 against the stored oracle result
+    acc = None
+    gold = os.path.join(ROOT, "tests", "golden", "spin1_c1_sys0.npz")
+    if rank == 0 and os.path.exists(gold):
+        g = np.load(gold)
+        e, u, pp = batch.unpack(hE, hU, hP, 0)
+        nrm = np.abs(g["E"]).max()
+        acc = {"E_rel_to_normH": float(np.abs(e - g["E"]).max() / nrm),
+               "U_abs": float(np.abs(u - g["U"]).max()), "P_abs": float(np.abs(pp - g["P"]).max())}
+
+    # roofline of the dominant stage
+    peaks = _peaks()
+    per = {k: v / max(runs, 1) for k, v in stage.items()}
+    dom = max(per, key=per.get)
+    n = problems[0].n
+    flops = stage_flops(dom, n, NT) * COUNT
+    fp32 = prec == M.MMF_MIXED and dom in ("hetrd", "backtransform")
+    peak = FP32_ALU_PEAK if fp32 else FP64_ALU_PEAK
+    achieved = flops / (per[dom] / 1e3) if per[dom] > 0 else 0.0
+    roof = {"kernel_stage": dom, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": ("FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz" if fp32
+                            else "FP64: nominal 1.25 TFLOP/s (recipe table)")}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_oracle(problems)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == M.MMF_FP64 else "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "systems_per_step": COUNT, "n": n, "nt": NT,
+                           "precision": args.precision, "l2": "working set > L2 (no flush)",
+                           "parallelism": f"replicas x{world}"},
+                "stage_ms": {k: round(v, 3) for k, v in per.items()},
+                "roofline": roof, "clocks": clk.summary(), "gpu_launches": launches,
+                "e2e": {"value": COUNT * world / e2e_s, "unit": "solves/s",
+                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "accuracy_vs_oracle": acc, "status_max": int(st.max()),
+                "cpu_baseline": cpu}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * mmf.h -- C ABI of the GB300 multimode Floquet library (libmmf.so).
+ *
+ * Problem (arXiv 2005.03426, Eq. 1): a D-level system with static Hamiltonian H0 driven at
+ * K incommensurate frequencies omega_l,
+ *     H(t) = H0 + sum_{l,h} ( V^{l,h} e^{+i h omega_l t} + V^{l,h}^dagger e^{-i h omega_l t} ),
+ * so a real drive A cos(omega t) O (O Hermitian) is given as V = (A/2) O at harmonic 1.
+ * The library builds the Floquet matrix H_F of Eq. 6 truncated to |n_l| <= N_l
+ * (n = D prod_l (2 N_l + 1), layout of Appendix A: mode 1 innermost), diagonalises it on the
+ * GPU, and evaluates from its eigenpairs the time-evolution operator U(t, t0) (Eq. 3-5) and
+ * the time-averaged transition probabilities Pbar_{i->j}.
+ *
+ * Conventions
+ *   - Complex arrays are interleaved (re, im) doubles (C99 double _Complex layout).
+ *   - Host pointers are owned by the caller and only read or written during the call.
+ *   - Matrices given to the library (H0, V) are D x D row-major.
+ *   - Every function returns an int status: MMF_OK (0), a negative MMF_ERR_* code for an
+ *     invalid argument or resource problem, or a positive MMF_ST_* numerical status.
+ *     mmf_strerror() gives a message; mmf_last_error() the detail of the last failure on the
+ *     calling thread.
+ *   - A context is bound to one CUDA device and one stream; calls on one context are
+ *     serialised internally.  All GPU work of a context runs on its stream.
+ *   - Nothing falls back to the CPU: without a usable GPU every call that needs one fails
+ *     with MMF_ERR_CUDA.
+ */
+#ifndef MMF_H
+#define MMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MMF_API __attribute__((visibility("default")))
+#else
+#define MMF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define MMF_OK 0
+#define MMF_ERR_ARG -1        /* invalid argument (null pointer, bad size, non-Hermitian H0...) */
+#define MMF_ERR_STATE -2      /* call out of order (e.g. results before diagonalise) */
+#define MMF_ERR_BUDGET -3     /* the request does not fit the context's HBM budget */
+#define MMF_ERR_CUDA -4       /* a CUDA runtime call failed (no device, launch error...) */
+#define MMF_ERR_UNSUPPORTED -5 /* size or option outside what this build supports */
+#define MMF_ERR_NOMEM -6      /* host allocation failed */
+#define MMF_ST_NOCONV 1       /* an iteration reached its cap (Jacobi sweeps, bisection) */
+#define MMF_ST_NONFINITE 2    /* NaN or Inf met in the input or a result */
+
+/* ---------------------------------------------------------------- precision */
+#define MMF_FP64 0   /* every step in FP64 */
+#define MMF_MIXED 1  /* FP32 reduction + FP64 tridiagonal solve + Ogita-Aishima refinement */
+
+typedef struct mmf_ctx mmf_ctx;
+typedef struct mmf_sys mmf_sys;
+typedef struct mmf_batch mmf_batch;
+
+/* ---------------------------------------------------------------- context
+ * mmf_ctx_create: bind to CUDA device `device` and stream `cuda_stream` (a cudaStream_t, or
+ * NULL for a stream the context creates and owns).  hbm_budget_bytes caps the device memory
+ * all batches of this context may hold at once (0 = 90% of the device's free memory).
+ * Errors: MMF_ERR_ARG (out == NULL), MMF_ERR_CUDA (no such device).
+ */
+MMF_API int mmf_ctx_create(int device, size_t hbm_budget_bytes, void* cuda_stream, mmf_ctx** out);
+/* Frees the context; batches and systems created on it must be destroyed first. */
+MMF_API int mmf_ctx_destroy(mmf_ctx* ctx);
+/* Device bytes currently held by the context's batches. */
+MMF_API size_t mmf_ctx_bytes_in_use(const mmf_ctx* ctx);
+MMF_API size_t mmf_ctx_budget(const mmf_ctx* ctx);
+
+/* ---------------------------------------------------------------- system definition
+ * The paper's set-up step (Sec. 3.1: the ATOM type, the harmonics array and the MODE
+ * type; Eq. 1).  H0 is D x D, Hermitian (checked to 1e-12 relative; otherwise MMF_ERR_ARG).
+ */
+MMF_API int mmf_sys_create(mmf_ctx* ctx, int D, const double* H0, mmf_sys** out);
+/* Adds drive mode number *mode_id (0, 1, ... in call order = mode 1, 2, ... of Eq. 1) with
+ * fundamental frequency omega (> 0) and Fourier truncation N_trunc (>= 0).  At most 4 modes. */
+MMF_API int mmf_add_mode(mmf_sys* sys, double omega, int N_trunc, int* mode_id);
+/* Sets V^{mode_id+1, harmonic} (D x D complex, any matrix; harmonic >= 1).  Harmonics of a
+ * mode must be added in order 1, 2, ...; a missing harmonic is zero. */
+MMF_API int mmf_add_coupling(mmf_sys* sys, int mode_id, int harmonic, const double* V);
+MMF_API int mmf_sys_destroy(mmf_sys* sys);
+/* Floquet dimension n = D prod (2 N_l + 1) (Sec. 2, Appendix A); -1 on a NULL handle. */
+MMF_API int64_t mmf_dim(const mmf_sys* sys);
+
+/* ---------------------------------------------------------------- one system (Sec. 3.2)
+ * mmf_build: S1, assemble H_F on the device in the given precision (MMF_FP64 / MMF_MIXED);
+ * *n_out = n.  Allocates the system's device state within the context budget. */
+MMF_API int mmf_build(mmf_sys* sys, int precision, int64_t* n_out);
+/* Copies the assembled H_F to the host: n x n complex, column-major (equal to row-major for
+ * a Hermitian matrix up to conjugation: HF[c * n + r] = H_F(r, c)).  Must follow mmf_build
+ * and precede mmf_diagonalise (the reduction overwrites it).  MIXED gives the FP32 matrix
+ * widened to FP64. */
+MMF_API int mmf_hamiltonian(mmf_sys* sys, double* HF);
+/* S2-S6: full eigendecomposition of H_F on the device (the paper's LAPACK call, Sec. 3.2).
+ * Returns the numerical status (MMF_ST_NOCONV if an iteration cap was hit). */
+MMF_API int mmf_diagonalise(mmf_sys* sys);
+/* All n quasienergies (eigenvalues of H_F), ascending, FP64. */
+MMF_API int mmf_quasienergies(mmf_sys* sys, double* E);
+/* Eigenvectors: n x n complex column-major, column k belongs to E[k]; entry (i + D b, k)
+ * is <i, n_b | lambda_k>. */
+MMF_API int mmf_eigenvectors(mmf_sys* sys, double* Z);
+/* S7: U[k][j][i] = <j| U(t[k], t0) |i> for nt times (Eq. 3-5, summed over Floquet copies).
+ * U is nt x D x D complex. */
+MMF_API int mmf_time_evolution(mmf_sys* sys, double t0, int nt, const double* t, double* U);
+/* S8: P[i * D + j] = Pbar_{i->j}, the average of |<j|U(t,t0)|i>|^2 over t and t - t0;
+ * eigenvalues closer than 1e-8 max|E| are averaged as one degenerate cluster. */
+MMF_API int mmf_transition_avg(mmf_sys* sys, double* P);
+/* Micromotion operator of Eq. 5 for one Floquet zone: UF[k][j][a] = sum_n e^{-i n.w t_k}
+ * <j, n | lambda_a> for the D eigenvectors with the largest weight on the central Fourier
+ * block (ties to the lower eigenvalue), in ascending eigenvalue order; reps[a] receives
+ * their eigenvalue indices (may be NULL). */
+MMF_API int mmf_micromotion(mmf_sys* sys, int nt, const double* t, double* UF, int64_t* reps);
+/* The paper's TIMEEVOLUTIONOPERATOR driver (Sec. 3.2): build + diagonalise + U in one call. */
+MMF_API int mmf_time_evolution_operator(mmf_sys* sys, int precision, double t0, int nt,
+                                const double* t, double* U);
+
+/* ---------------------------------------------------------------- batches
+ * Many systems of any sizes solved together on the device (the data-parallel sweep of the
+ * paper's examples, Sec. 4).  A batch is a plan: it allocates all device state once (within
+ * the context budget) and can be run many times.  nt is the number of times per system.
+ */
+MMF_API int mmf_batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int precision, int nt,
+                     mmf_batch** out);
+/* Times: t is count x nt host doubles (row = system); t0 common to all. */
+MMF_API int mmf_batch_set_times(mmf_batch* b, double t0, const double* t);
+/* Re-uploads the systems' coefficients and the times from the host (pinned staging). */
+MMF_API int mmf_batch_upload(mmf_batch* b);
+/* Enqueues S1-S8 for every system on the context stream; returns without waiting. */
+MMF_API int mmf_batch_run(mmf_batch* b);
+/* Waits for the batch; status (count ints, may be NULL) receives each system's numerical
+ * status.  Returns the largest status. */
+MMF_API int mmf_batch_sync(mmf_batch* b, int* status);
+/* Results of system i: E (n), U (nt x D x D complex), P (D x D); any may be NULL. */
+MMF_API int mmf_batch_get(mmf_batch* b, int i, double* E, double* U, double* P);
+/* Eigenvectors of system i (n x n complex column-major). */
+MMF_API int mmf_batch_eigenvectors(mmf_batch* b, int i, double* Z);
+/* Packed results of all systems (E: sum n, U: sum nt D^2 complex, P: sum D^2) copied to the
+ * host with one transfer each; any may be NULL.  Enqueued and waited on the stream. */
+MMF_API int mmf_batch_results(mmf_batch* b, double* E, double* U, double* P);
+/* Offsets (in doubles for E and P, in complex elements for U) of system i in the packed
+ * results: what = 0 (E), 1 (U), 2 (P). */
+MMF_API int64_t mmf_batch_offset(const mmf_batch* b, int what, int i);
+/* Total packed sizes: what = 0 (E doubles), 1 (U complex), 2 (P doubles). */
+MMF_API int64_t mmf_batch_size(const mmf_batch* b, int what);
+/* Per-stage CUDA-event timing: record events around the stages of the next max_runs calls
+ * of mmf_batch_run (0 switches timing off).  mmf_batch_stage_ms waits for the stream and
+ * returns in ms[7] the summed times of the recorded runs per stage (0 assemble, 1 small-n
+ * Jacobi, 2 Householder reduction, 3 tridiagonal eigensolve, 4 back-transform,
+ * 5 refinement, 6 U and Pbar), *runs their number, and restarts the count. */
+MMF_API int mmf_batch_timing(mmf_batch* b, int max_runs);
+MMF_API int mmf_batch_stage_ms(mmf_batch* b, double* ms, int* runs);
+/* Device bytes held by the batch. */
+MMF_API size_t mmf_batch_bytes(const mmf_batch* b);
+MMF_API int mmf_batch_destroy(mmf_batch* b);
+
+/* ---------------------------------------------------------------- misc */
+MMF_API const char* mmf_strerror(int status);
+MMF_API const char* mmf_last_error(void);
+/* Number of kernel launches enqueued by the last mmf_batch_run on this thread. */
+MMF_API int mmf_last_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MMF_H */

@@ -1,0 +1,320 @@
+// k_hetrd.cu -- S2: blocked complex Householder reduction of H_F to real tridiagonal form.
+//
+// The paper hands this step to LAPACK (Sec. 3.2); this is our own GPU formulation of the
+// standard blocked reduction (Dongarra, Sorensen & Hammarling 1989).  Lower storage,
+// column-major; only the lower triangle is read or updated.
+//
+// For column k the reflector P_k = I - tau_k v v^H (v[k+1] = 1, v[r] = 0 for r <= k)
+// satisfies P_k^H A(k+1:, k) = beta_k e_1 with beta_k real:
+//     beta = -sign(Re alpha) sqrt(|alpha|^2 + ||x||^2),  tau = (beta - alpha) / beta,
+//     v[k+2:] = x / (alpha - beta)        (alpha = A(k+1, k), x = A(k+2:, k)).
+// Two-sided update A <- P^H A P = A - v w^H - w v^H with
+//     y = A v,   w = tau y - (1/2) |tau|^2 (v^H y) v.
+// Within a panel of NB columns the updates are deferred (V, W kept in global workspace):
+// before its reflector, column k receives A(k:, k) -= V W(k,:)^H + W V(k,:)^H, and
+// y = A22 v - V (W^H v) - W (V^H v).  After the panel the trailing lower triangle
+// receives A -= V W^H + W V^H (her2k).
+// Result: d (diagonal), e = beta (sub-diagonal, real), tau, and v[k+2:] stored in
+// A(k+2:, k).  Q = P_0 P_1 ... P_{n-2}, Q^H H_F Q = tridiag(e, d, e).
+//
+// One CTA per system, 512 threads.  The hemv streams the lower triangle of the trailing
+// matrix once per column with coalesced column reads: a warp owns 8 columns, lanes own
+// rows, the row part accumulates through shared-memory atomics and the column part by
+// warp-shuffle reductions.
+#include "mmf_internal.h"
+
+#define HT_THREADS 512
+#define HT_TILE 64
+
+template <class R>
+__device__ __forceinline__ R block_sum(R v, R* red) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        R s = (threadIdx.x < HT_THREADS / 32) ? red[threadIdx.x] : R(0);
+        s = warp_sum(s);
+        if (threadIdx.x == 0) red[32] = s;
+    }
+    __syncthreads();
+    R r = red[32];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void atomic_add_c(double2* p, double2 v) {
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+__device__ __forceinline__ void atomic_add_c(float2* p, float2 v) {
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+
+template <class R>
+__global__ void __launch_bounds__(HT_THREADS, 1)
+k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
+        typename Cx<R>::T* __restrict__ H, typename Cx<R>::T* __restrict__ Vpool,
+        typename Cx<R>::T* __restrict__ Wpool, double* __restrict__ dvec,
+        double* __restrict__ evec, typename Cx<R>::T* __restrict__ taupool, int nmax) {
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* vS = reinterpret_cast<C*>(smem_raw);   // nmax
+    C* yS = vS + nmax;                          // nmax
+    C* tVr = yS + nmax;                         // MMF_NB x HT_TILE (her2k staging, transposed)
+    C* tWr = tVr + MMF_NB * HT_TILE;
+    C* tVc = tWr + MMF_NB * HT_TILE;
+    C* tWc = tVc + MMF_NB * HT_TILE;
+    C* wk = tWc + MMF_NB * HT_TILE;             // MMF_NB
+    C* vk = wk + MMF_NB;                        // MMF_NB
+    C* xw = vk + MMF_NB;                        // MMF_NB
+    C* xv = xw + MMF_NB;                        // MMF_NB
+    C* sc = xv + MMF_NB;                        // 4 scalars: tau, scale, alpha2
+    R* red = reinterpret_cast<R*>(sc + 4);      // 33
+
+    const MmfDesc d = descs[idx[blockIdx.x]];
+    const int n = d.n, ld = d.ld;
+    C* A = H + d.mat_off;
+    C* V = Vpool + d.pan_off;
+    C* W = Wpool + d.pan_off;
+    double* dd = dvec + d.vec_off;
+    double* ee = evec + d.vec_off;
+    C* tau = taupool + d.vec_off;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int NW = HT_THREADS / 32;
+
+    for (int j0 = 0; j0 < n; j0 += MMF_NB) {
+        const int nb = min(MMF_NB, n - j0);
+        for (int i = 0; i < nb; ++i) {
+            const int k = j0 + i;
+            // (a) pending panel updates of column k
+            if (i > 0) {
+                if (tid < i) {
+                    wk[tid] = conj(W[k + (int64_t)tid * ld]);
+                    vk[tid] = conj(V[k + (int64_t)tid * ld]);
+                }
+                __syncthreads();
+                for (int r = k + tid; r < n; r += HT_THREADS) {
+                    C acc = czero<C>();
+                    for (int c = 0; c < i; ++c)
+                        acc = acc + V[r + (int64_t)c * ld] * wk[c] + W[r + (int64_t)c * ld] * vk[c];
+                    A[r + (int64_t)k * ld] = A[r + (int64_t)k * ld] - acc;
+                }
+                __syncthreads();
+            }
+            if (tid == 0) dd[k] = (double)A[k + (int64_t)k * ld].x;
+            if (k == n - 1) break;
+            const int m = n - k - 1;
+            C* col = A + (int64_t)k * ld;
+
+            // (b) reflector
+            R part = 0;
+            for (int r = k + 2 + tid; r < n; r += HT_THREADS) part += abs2(col[r]);
+            const R xn2 = block_sum(part, red);
+            if (tid == 0) {
+                C alpha = col[k + 1];
+                C t, s;
+                R beta;
+                if (xn2 == R(0) && alpha.y == R(0)) {
+                    t = czero<C>();
+                    s = czero<C>();
+                    beta = alpha.x;
+                } else {
+                    beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2), alpha.x);
+                    t = mk((beta - alpha.x) / beta, -alpha.y / beta);
+                    C den = mk(alpha.x - beta, alpha.y);  // 1 / (alpha - beta)
+                    R dn = abs2(den);
+                    s = mk(den.x / dn, -den.y / dn);
+                }
+                ee[k] = (double)beta;
+                tau[k] = t;
+                sc[0] = t;
+                sc[1] = s;
+            }
+            __syncthreads();
+            const C tk = sc[0], scale = sc[1];
+            for (int r = tid; r < n; r += HT_THREADS) {
+                C v;
+                if (r <= k) {
+                    v = czero<C>();
+                } else if (r == k + 1) {
+                    v = mk(R(1), R(0));
+                } else {
+                    v = col[r] * scale;
+                    col[r] = v;
+                }
+                if (r > k) {
+                    vS[r - k - 1] = v;
+                    yS[r - k - 1] = czero<C>();
+                }
+                V[r + (int64_t)i * ld] = v;
+            }
+            __syncthreads();
+
+            // (c) y = A22 v (lower triangle) and (d) x_w = W^H v, x_v = V^H v
+            const C* a22 = A + (k + 1) + (int64_t)(k + 1) * ld;
+            const int nblk = (m + 7) >> 3;
+            for (int task = warp; task < 2 * i + nblk; task += NW) {
+                if (task < 2 * i) {
+                    const int c = task >> 1;
+                    const C* P = (task & 1) ? V : W;
+                    C acc = czero<C>();
+                    for (int rp = lane; rp < m; rp += 32)
+                        acc = acc + cmulc(P[(k + 1 + rp) + (int64_t)c * ld], vS[rp]);
+                    acc.x = warp_sum(acc.x);
+                    acc.y = warp_sum(acc.y);
+                    if (lane == 0) ((task & 1) ? xv : xw)[c] = acc;
+                } else {
+                    const int c0 = (task - 2 * i) << 3;
+                    const int nc = min(8, m - c0);
+                    C vc[8], ca[8];
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        vc[jj] = (jj < nc) ? vS[c0 + jj] : czero<C>();
+                        ca[jj] = czero<C>();
+                    }
+                    // diagonal chunk (rows c0 .. c0+31)
+                    {
+                        const int r = c0 + lane;
+                        if (r < m) {
+                            const C vr = vS[r];
+                            C ra = czero<C>();
+#pragma unroll
+                            for (int jj = 0; jj < 8; ++jj) {
+                                const int c = c0 + jj;
+                                if (jj < nc) {
+                                    if (r > c) {
+                                        C a = a22[r + (int64_t)c * ld];
+                                        ra = ra + a * vc[jj];
+                                        ca[jj] = ca[jj] + cmulc(a, vr);
+                                    } else if (r == c) {
+                                        ra = ra + a22[r + (int64_t)c * ld].x * vc[jj];
+                                    }
+                                }
+                            }
+                            atomic_add_c(&yS[r], ra);
+                        }
+                    }
+                    // strictly-lower chunks
+                    for (int r0 = c0 + 32; r0 < m; r0 += 32) {
+                        const int r = r0 + lane;
+                        if (r < m) {
+                            C a[8];
+#pragma unroll
+                            for (int jj = 0; jj < 8; ++jj)
+                                a[jj] = (jj < nc) ? a22[r + (int64_t)(c0 + jj) * ld] : czero<C>();
+                            const C vr = vS[r];
+                            C ra = czero<C>();
+#pragma unroll
+                            for (int jj = 0; jj < 8; ++jj) {
+                                ra = ra + a[jj] * vc[jj];
+                                ca[jj] = ca[jj] + cmulc(a[jj], vr);
+                            }
+                            atomic_add_c(&yS[r], ra);
+                        }
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        R sx = warp_sum(ca[jj].x), sy = warp_sum(ca[jj].y);
+                        if (lane == 0 && jj < nc) atomic_add_c(&yS[c0 + jj], mk(sx, sy));
+                    }
+                }
+            }
+            __syncthreads();
+
+            // (d) corrections, (e) w = tau y - (1/2) tau (w^H v) v
+            C dpart = czero<C>();
+            for (int rp = tid; rp < m; rp += HT_THREADS) {
+                C y = yS[rp];
+                for (int c = 0; c < i; ++c)
+                    y = y - V[(k + 1 + rp) + (int64_t)c * ld] * xw[c] -
+                        W[(k + 1 + rp) + (int64_t)c * ld] * xv[c];
+                C w = tk * y;
+                yS[rp] = w;
+                dpart = dpart + cmulc(w, vS[rp]);
+            }
+            R dx = block_sum(dpart.x, red);
+            R dy = block_sum(dpart.y, red);
+            const C alpha2 = R(-0.5) * (tk * mk(dx, dy));
+            for (int r = tid; r < n; r += HT_THREADS) {
+                C w = czero<C>();
+                if (r > k) w = yS[r - k - 1] + alpha2 * vS[r - k - 1];
+                W[r + (int64_t)i * ld] = w;
+            }
+            __syncthreads();
+        }
+
+        // trailing her2k on the lower triangle of A(c0:, c0:)
+        const int c0 = j0 + nb;
+        if (c0 < n) {
+            const int nt = (n - c0 + HT_TILE - 1) / HT_TILE;
+            const int rr = tid & (HT_TILE - 1), cg = tid / HT_TILE;  // 8 column groups
+            for (int ti = 0; ti < nt; ++ti) {
+                for (int tj = 0; tj <= ti; ++tj) {
+                    const int rbase = c0 + ti * HT_TILE, cbase = c0 + tj * HT_TILE;
+                    for (int e = tid; e < nb * HT_TILE; e += HT_THREADS) {
+                        const int p = e / HT_TILE, q = e - p * HT_TILE;
+                        const int r = rbase + q, c = cbase + q;
+                        tVr[e] = (r < n) ? V[r + (int64_t)p * ld] : czero<C>();
+                        tWr[e] = (r < n) ? W[r + (int64_t)p * ld] : czero<C>();
+                        tVc[e] = (c < n) ? conj(V[c + (int64_t)p * ld]) : czero<C>();
+                        tWc[e] = (c < n) ? conj(W[c + (int64_t)p * ld]) : czero<C>();
+                    }
+                    __syncthreads();
+                    C acc[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) acc[q] = czero<C>();
+                    for (int p = 0; p < nb; ++p) {
+                        const C a = tVr[p * HT_TILE + rr], b = tWr[p * HT_TILE + rr];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int cc = cg + 8 * q;
+                            acc[q] = acc[q] + a * tWc[p * HT_TILE + cc] + b * tVc[p * HT_TILE + cc];
+                        }
+                    }
+                    const int r = rbase + rr;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int c = cbase + cg + 8 * q;
+                        if (r < n && c < n && r >= c) {
+                            C* pa = A + r + (int64_t)c * ld;
+                            *pa = *pa - acc[q];
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+        }
+    }
+}
+
+static size_t hetrd_smem(int nmax, int fp32) {
+    size_t cs = fp32 ? 8 : 16, rs = fp32 ? 4 : 8;
+    return cs * (2 * (size_t)nmax + 4 * MMF_NB * HT_TILE + 4 * MMF_NB + 4) + rs * 40;
+}
+
+int mmf_hetrd_max_n(int fp32) {
+    size_t cs = fp32 ? 8 : 16, rs = fp32 ? 4 : 8;
+    size_t fixed = cs * (4 * MMF_NB * HT_TILE + 4 * MMF_NB + 4) + rs * 40;
+    return (int)((227 * 1024 - fixed) / (2 * cs));
+}
+
+cudaError_t mmf_launch_hetrd(const MmfLaunch& L, void* H, void* Vp, void* Wp, double* dvec,
+                             double* evec, void* tau, int fp32) {
+    if (L.count <= 0) return cudaSuccess;
+    if (L.nmax > mmf_hetrd_max_n(fp32)) return cudaErrorInvalidValue;
+    size_t sm = hetrd_smem(L.nmax, fp32);
+    cudaError_t err;
+    if (fp32) {
+        err = cudaFuncSetAttribute(k_hetrd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (err != cudaSuccess) return err;
+        k_hetrd<float><<<L.count, HT_THREADS, sm, L.stream>>>(L.desc, L.idx, (float2*)H, (float2*)Vp,
+                                                              (float2*)Wp, dvec, evec, (float2*)tau, L.nmax);
+    } else {
+        err = cudaFuncSetAttribute(k_hetrd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (err != cudaSuccess) return err;
+        k_hetrd<double><<<L.count, HT_THREADS, sm, L.stream>>>(L.desc, L.idx, (double2*)H, (double2*)Vp,
+                                                               (double2*)Wp, dvec, evec, (double2*)tau, L.nmax);
+    }
+    return cudaGetLastError();
+}

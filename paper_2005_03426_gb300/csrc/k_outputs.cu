@@ -1,0 +1,231 @@
+// k_outputs.cu -- S7 time-evolution operator and S8 time-averaged transition probabilities
+// from the eigenpairs (E_lambda, Z[:, lambda]) of H_F (FP64).
+//
+// S7 (Eq. 3-5, Eq. 4 read as U_F(t') Ubar U_F(t)^dagger, summed over all Floquet copies):
+//   F[t, b]        = e^{-i (n_b . omega) t}
+//   Phi_t[j, l]    = sum_b F[t, b] Z[(j, b), l]
+//   U(t, t0)[j, i] = sum_l Phi_t[j, l] e^{-i E_l (t - t0)} conj(Z[(i, b0), l])
+// S8 (time and phase average of |U_ji|^2; clusters C of eigenvalues closer than
+//   delta = cluster_rel * max|E| are averaged together):
+//   Pbar_{i->j} = sum_b sum_C | sum_{l in C} Z[(j, b), l] conj(Z[(i, b0), l]) |^2
+#include "mmf_internal.h"
+
+__global__ void __launch_bounds__(256) k_phase_table(const MmfDesc* __restrict__ descs,
+                                                     const int* __restrict__ idx,
+                                                     const double* __restrict__ tpool, int nt,
+                                                     double2* __restrict__ F) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int tot = nt * d.M;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+        int t = e / d.M, b = e - t * d.M;
+        double arg = block_ndotw(d, b) * tpool[d.t_off + t];
+        double s, c;
+        sincos(arg, &s, &c);
+        F[d.f_off + e] = make_double2(c, -s);
+    }
+}
+
+#define U_TPW 8  // times per warp per pass (8 warps -> 64 times per pass)
+
+__global__ void __launch_bounds__(256) k_time_evolution(const MmfDesc* __restrict__ descs,
+                                                        const int* __restrict__ idx,
+                                                        const double* __restrict__ Eg,
+                                                        const double2* __restrict__ Zg,
+                                                        const double* __restrict__ tpool,
+                                                        double t0, int nt,
+                                                        const double2* __restrict__ F,
+                                                        double2* __restrict__ U) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n, D = d.D, M = d.M;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lam = blockIdx.x * 32 + lane;
+    if (blockIdx.x * 32 >= n) return;
+    const bool valid = lam < n;
+    const double2* Zc = Zg + d.mat_off + (int64_t)(valid ? lam : 0) * d.ld;
+    const double El = valid ? Eg[d.vec_off + lam] : 0.0;
+    const double2* Ft = F + d.f_off;
+    const double* tt = tpool + d.t_off;
+    double2* Uo = U + d.u_off;
+
+    for (int tbase = 0; tbase < nt; tbase += 8 * U_TPW) {
+        double2 ph[U_TPW];
+#pragma unroll
+        for (int q = 0; q < U_TPW; ++q) {
+            int t = tbase + warp + 8 * q;
+            double s = 0.0, c = 1.0;
+            if (t < nt) sincos(El * (tt[t] - t0), &s, &c);
+            ph[q] = make_double2(c, -s);
+        }
+        for (int j = 0; j < D; ++j) {
+            double2 acc[U_TPW];
+#pragma unroll
+            for (int q = 0; q < U_TPW; ++q) acc[q] = make_double2(0.0, 0.0);
+            for (int b = 0; b < M; ++b) {
+                double2 z = valid ? Zc[j + D * b] : make_double2(0.0, 0.0);
+#pragma unroll
+                for (int q = 0; q < U_TPW; ++q) {
+                    int t = tbase + warp + 8 * q;
+                    if (t < nt) {
+                        double2 f = Ft[(int64_t)t * M + b];
+                        acc[q].x = fma(f.x, z.x, fma(-f.y, z.y, acc[q].x));
+                        acc[q].y = fma(f.x, z.y, fma(f.y, z.x, acc[q].y));
+                    }
+                }
+            }
+            for (int i = 0; i < D; ++i) {
+                double2 z0 = valid ? Zc[i + D * d.b0] : make_double2(0.0, 0.0);
+#pragma unroll
+                for (int q = 0; q < U_TPW; ++q) {
+                    int t = tbase + warp + 8 * q;
+                    double2 v = cmulc(z0, acc[q] * ph[q]);  // conj(z0) * Phi * phase
+                    v.x = warp_sum(v.x);
+                    v.y = warp_sum(v.y);
+                    if (lane == 0 && t < nt) {
+                        double2* u = Uo + ((int64_t)t * D + j) * D + i;
+                        atomicAdd(&u->x, v.x);
+                        atomicAdd(&u->y, v.y);
+                    }
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_transition_avg(const MmfDesc* __restrict__ descs,
+                                                        const int* __restrict__ idx,
+                                                        const double* __restrict__ Eg,
+                                                        const double2* __restrict__ Zg,
+                                                        double cluster_rel,
+                                                        double* __restrict__ P) {
+    extern __shared__ __align__(16) double psm[];
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n, D = d.D;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double* Ps = psm;                     // D*D
+    double* Ws = psm + D * D + warp * D;  // per warp D
+    for (int e = threadIdx.x; e < D * D + 8 * D; e += blockDim.x) psm[e] = 0.0;
+    __syncthreads();
+    const double* E = Eg + d.vec_off;
+    const double2* Z = Zg + d.mat_off;
+    const double emax = fmax(fabs(E[0]), fabs(E[n - 1]));
+    const double delta = cluster_rel * emax;
+    const int lam = blockIdx.x * 8 + warp;
+    if (lam < n && (lam == 0 || !(E[lam] - E[lam - 1] < delta))) {
+        int c1 = lam + 1;
+        while (c1 < n && E[c1] - E[c1 - 1] < delta) ++c1;
+        if (c1 == lam + 1) {
+            const double2* zc = Z + (int64_t)lam * d.ld;
+            for (int r = lane; r < n; r += 32) atomicAdd(&Ws[r % D], abs2(zc[r]));
+            __syncwarp();
+            for (int e = lane; e < D * D; e += 32) {
+                int i = e / D, j = e - i * D;
+                atomicAdd(&Ps[e], abs2(zc[i + D * d.b0]) * Ws[j]);
+            }
+        } else {
+            for (int r = lane; r < n; r += 32) {
+                int j = r % D;
+                for (int i = 0; i < D; ++i) {
+                    double2 amp = make_double2(0.0, 0.0);
+                    for (int l = lam; l < c1; ++l) {
+                        const double2* zc = Z + (int64_t)l * d.ld;
+                        amp = amp + cmulc(zc[i + D * d.b0], zc[r]);
+                    }
+                    atomicAdd(&Ps[i * D + j], abs2(amp));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < D * D; e += blockDim.x)
+        if (Ps[e] != 0.0) atomicAdd(&P[d.p_off + e], Ps[e]);
+}
+
+// Staged launcher with explicit maxima (the batch knows them).
+cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const double* E,
+                                  const double2* Z, const double* t, double t0, int nt,
+                                  double2* F, double2* U, double* P, double cluster_rel) {
+    if (L.count <= 0) return cudaSuccess;
+    if (nt > 0) {
+        int gx = (nt * Mmax + 255) / 256;
+        if (gx > 1024) gx = 1024;
+        k_phase_table<<<dim3(gx, L.count), 256, 0, L.stream>>>(L.desc, L.idx, t, nt, F);
+        k_time_evolution<<<dim3((L.nmax + 31) / 32, L.count), 256, 0, L.stream>>>(
+            L.desc, L.idx, E, Z, t, t0, nt, F, U);
+    }
+    size_t sm = sizeof(double) * (size_t)(Dmax * Dmax + 8 * Dmax);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_transition_avg,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    k_transition_avg<<<dim3((L.nmax + 7) / 8, L.count), 256, sm, L.stream>>>(L.desc, L.idx, E, Z,
+                                                                            cluster_rel, P);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ micromotion (Eq. 5)
+// Zone representatives: the D eigenvectors with the largest weight on the central Fourier
+// block, w_l = sum_i |Z[(i, b0), l]|^2 (ties to the lower index), returned in ascending order.
+__global__ void __launch_bounds__(512) k_zone_select(const MmfDesc* __restrict__ descs,
+                                                    const int* __restrict__ idx,
+                                                    const double2* __restrict__ Zg,
+                                                    int64_t* __restrict__ reps) {
+    extern __shared__ __align__(16) double wsm[];
+    const MmfDesc d = descs[idx[blockIdx.x]];
+    const int n = d.n, D = d.D;
+    const double2* Z = Zg + d.mat_off;
+    int* sel = reinterpret_cast<int*>(wsm + n);
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+        double a = 0.0;
+        for (int i = 0; i < D; ++i) a += abs2(Z[(int64_t)l * d.ld + i + D * d.b0]);
+        wsm[l] = a;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+        const double wl = wsm[l];
+        int rank = 0;
+        for (int m = 0; m < n && rank < D; ++m) rank += (wsm[m] > wl) || (wsm[m] == wl && m < l);
+        if (rank < D) sel[rank] = l;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int a = 1; a < D; ++a) {
+            int v = sel[a], b = a - 1;
+            while (b >= 0 && sel[b] > v) { sel[b + 1] = sel[b]; --b; }
+            sel[b + 1] = v;
+        }
+        for (int a = 0; a < D; ++a) reps[a] = sel[a];
+    }
+}
+
+// UF[k][j][a] = sum_b e^{-i (n_b . omega) t_k} Z[(j, b), reps[a]]
+__global__ void k_micromotion(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
+                              const double2* __restrict__ Zg, const int64_t* __restrict__ reps,
+                              const double* __restrict__ t, int nt, double2* __restrict__ UF) {
+    const MmfDesc d = descs[idx[0]];
+    const int D = d.D;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nt * D * D) return;
+    const int k = e / (D * D), j = (e / D) % D, a = e % D;
+    const double2* z = Zg + d.mat_off + reps[a] * d.ld;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int b = 0; b < d.M; ++b) {
+        double s, c;
+        sincos(block_ndotw(d, b) * t[k], &s, &c);
+        acc = acc + make_double2(c, -s) * z[j + D * b];
+    }
+    UF[e] = acc;
+}
+
+cudaError_t mmf_launch_micromotion(const MmfLaunch& L, int D, const double2* Z, const double* t,
+                                   int nt, int64_t* reps, double2* UF) {
+    size_t sm = sizeof(double) * (size_t)L.nmax + sizeof(int) * (size_t)D + 16;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_zone_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    k_zone_select<<<1, 512, sm, L.stream>>>(L.desc, L.idx, Z, reps);
+    const int tot = nt * D * D;
+    k_micromotion<<<(tot + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, Z, reps, t, nt, UF);
+    return cudaGetLastError();
+}

@@ -1,0 +1,867 @@
+// mmf_host.cu -- host runtime behind the C ABI of include/mmf.h: contexts, system
+// definitions, batch plans (device memory layout inside an HBM budget) and the launch
+// sequence S1 assemble -> S2..S6 eigendecomposition -> S7 U(t, t0) -> S8 Pbar.
+//
+// Call sequence of the paper (Sec. 3.1-3.2, Fig. 2): define the system (levels, static part,
+// modes and couplings), build the Floquet matrix, diagonalise, evaluate U / Pbar.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mmf.h"
+#include "mmf_internal.h"
+
+cudaError_t mmf_launch_tridiag_eig(const MmfLaunch& L, const double* dvec, const double* evec,
+                                   double* aux, double* E, double* Y, double* work, int* status);
+
+static thread_local std::string g_last_error;
+static thread_local int g_launches = 0;
+
+static int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(MMF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct mmf_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0, used = 0;
+    std::recursive_mutex mu;
+};
+
+struct mmf_sys {
+    mmf_ctx* ctx = nullptr;
+    int D = 0;
+    std::vector<double2> H0;
+    std::vector<double> omega;
+    std::vector<int> N;
+    std::vector<std::vector<std::vector<double2>>> V;  // [mode][harmonic-1][D*D]
+    mmf_batch* solo = nullptr;
+    int state = 0;  // 0 defined, 1 built, 2 diagonalised
+};
+
+struct Pool {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        size_t o = (off + 255) & ~(size_t)255;
+        off = o + bytes;
+        return o;
+    }
+};
+
+struct mmf_batch {
+    mmf_ctx* ctx = nullptr;
+    int count = 0, precision = 0, nt = 0;
+    std::vector<mmf_sys*> sys;
+    std::vector<MmfDesc> desc;
+    std::vector<int> all, small, large;
+    int nmax_all = 0, nmax_small = 0, nmax_large = 0, Mmax = 1, Dmax = 1;
+    int64_t n_coef = 0, n_mat = 0, n_vec = 0, n_sq = 0, n_pan = 0, n_t = 0, n_f = 0, n_u = 0,
+            n_p = 0;
+    // device
+    unsigned char* base = nullptr;
+    size_t bytes = 0;
+    MmfDesc* d_desc = nullptr;
+    int *d_all = nullptr, *d_small = nullptr, *d_large = nullptr, *d_status = nullptr;
+    double2* d_coef = nullptr;
+    void* d_H = nullptr;
+    double2* d_Zf = nullptr;
+    void* d_Zp = nullptr;
+    double *d_E = nullptr, *d_d = nullptr, *d_e = nullptr, *d_aux = nullptr;
+    void* d_tau = nullptr;
+    double *d_Y = nullptr, *d_work = nullptr;
+    void *d_Vp = nullptr, *d_Wp = nullptr;
+    double* d_t = nullptr;
+    double2 *d_F = nullptr, *d_U = nullptr;
+    double* d_P = nullptr;
+    double2 *d_R = nullptr, *d_S = nullptr, *d_HX = nullptr;
+    double* d_E2 = nullptr;
+    // host staging (pinned)
+    double2* h_coef = nullptr;
+    double* h_t = nullptr;
+    double t0 = 0.0;
+    bool times_set = false;
+    int last_stage = 0;  // 1 assembled, 2 diagonalised, 3 outputs
+    // per-stage CUDA-event timing (optional)
+    int timing_runs = 0, runs_recorded = 0;
+    std::vector<cudaEvent_t> ev;
+};
+
+enum { ST_ASSEMBLE, ST_JACOBI, ST_HETRD, ST_TRIDIAG, ST_BACKTRANSFORM, ST_REFINE, ST_OUTPUTS, ST_COUNT };
+
+static void mark(mmf_batch* b, int stage) {
+    if (b->timing_runs <= 0) return;
+    int slot = b->runs_recorded % b->timing_runs;
+    cudaEventRecord(b->ev[(size_t)slot * (ST_COUNT + 1) + stage], b->ctx->stream);
+}
+
+// ------------------------------------------------------------------ helpers
+static int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+static int jacobi_nmax(int prec) { return prec == MMF_MIXED ? MMF_JACOBI_NMAX_F32 : MMF_JACOBI_NMAX_F64; }
+
+static int64_t sys_dim(const mmf_sys* s) {
+    int64_t m = 1;
+    for (int N : s->N) m *= (2 * N + 1);
+    return (int64_t)s->D * m;
+}
+
+extern "C" const char* mmf_strerror(int st) {
+    switch (st) {
+        case MMF_OK: return "ok";
+        case MMF_ERR_ARG: return "invalid argument";
+        case MMF_ERR_STATE: return "call out of order";
+        case MMF_ERR_BUDGET: return "request exceeds the context's HBM budget";
+        case MMF_ERR_CUDA: return "CUDA error";
+        case MMF_ERR_UNSUPPORTED: return "unsupported size or option";
+        case MMF_ERR_NOMEM: return "host allocation failed";
+        case MMF_ST_NOCONV: return "iteration cap reached";
+        case MMF_ST_NONFINITE: return "non-finite value";
+        default: return "unknown status";
+    }
+}
+extern "C" const char* mmf_last_error(void) { return g_last_error.c_str(); }
+extern "C" int mmf_last_launch_count(void) { return g_launches; }
+
+// ------------------------------------------------------------------ context
+extern "C" int mmf_ctx_create(int device, size_t budget, void* stream, mmf_ctx** out) {
+    if (!out) return fail(MMF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CU(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(MMF_ERR_ARG, "no such CUDA device");
+    CU(cudaSetDevice(device));
+    mmf_ctx* c = new (std::nothrow) mmf_ctx();
+    if (!c) return fail(MMF_ERR_NOMEM, "context allocation");
+    c->device = device;
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(MMF_ERR_CUDA, cudaGetErrorString(e));
+        }
+        c->own_stream = true;
+    }
+    if (budget == 0) {
+        size_t fr = 0, tot = 0;
+        cudaError_t e = cudaMemGetInfo(&fr, &tot);
+        if (e != cudaSuccess) {
+            if (c->own_stream) cudaStreamDestroy(c->stream);
+            delete c;
+            return fail(MMF_ERR_CUDA, cudaGetErrorString(e));
+        }
+        budget = fr / 10 * 9;
+    }
+    c->budget = budget;
+    *out = c;
+    return MMF_OK;
+}
+
+extern "C" int mmf_ctx_destroy(mmf_ctx* c) {
+    if (!c) return MMF_ERR_ARG;
+    cudaSetDevice(c->device);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return MMF_OK;
+}
+extern "C" size_t mmf_ctx_bytes_in_use(const mmf_ctx* c) { return c ? c->used : 0; }
+extern "C" size_t mmf_ctx_budget(const mmf_ctx* c) { return c ? c->budget : 0; }
+
+// ------------------------------------------------------------------ systems
+extern "C" int mmf_sys_create(mmf_ctx* ctx, int D, const double* H0, mmf_sys** out) {
+    if (!out) return fail(MMF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ctx || D < 1 || !H0) return fail(MMF_ERR_ARG, "ctx, D >= 1 and H0 required");
+    double mx = 0.0;
+    for (int i = 0; i < 2 * D * D; ++i) {
+        if (!std::isfinite(H0[i])) return fail(MMF_ST_NONFINITE, "H0 not finite");
+        mx = std::max(mx, std::fabs(H0[i]));
+    }
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            double ar = H0[2 * (i * D + j)], ai = H0[2 * (i * D + j) + 1];
+            double br = H0[2 * (j * D + i)], bi = H0[2 * (j * D + i) + 1];
+            if (std::fabs(ar - br) > 1e-12 * mx || std::fabs(ai + bi) > 1e-12 * mx)
+                return fail(MMF_ERR_ARG, "H0 is not Hermitian");
+        }
+    mmf_sys* s = new (std::nothrow) mmf_sys();
+    if (!s) return fail(MMF_ERR_NOMEM, "system allocation");
+    s->ctx = ctx;
+    s->D = D;
+    s->H0.resize((size_t)D * D);
+    for (int e = 0; e < D * D; ++e) s->H0[e] = make_double2(H0[2 * e], H0[2 * e + 1]);
+    *out = s;
+    return MMF_OK;
+}
+
+extern "C" int mmf_add_mode(mmf_sys* s, double omega, int N, int* mode_id) {
+    if (!s) return fail(MMF_ERR_ARG, "sys is NULL");
+    if (!(omega > 0.0) || !std::isfinite(omega)) return fail(MMF_ERR_ARG, "omega must be > 0");
+    if (N < 0) return fail(MMF_ERR_ARG, "N must be >= 0");
+    if ((int)s->omega.size() >= MMF_MAX_MODES) return fail(MMF_ERR_UNSUPPORTED, "at most 4 modes");
+    s->omega.push_back(omega);
+    s->N.push_back(N);
+    s->V.emplace_back();
+    if (mode_id) *mode_id = (int)s->omega.size() - 1;
+    s->state = 0;
+    return MMF_OK;
+}
+
+extern "C" int mmf_add_coupling(mmf_sys* s, int mode_id, int harmonic, const double* V) {
+    if (!s || !V) return fail(MMF_ERR_ARG, "sys and V required");
+    if (mode_id < 0 || mode_id >= (int)s->omega.size()) return fail(MMF_ERR_ARG, "bad mode id");
+    if (harmonic < 1) return fail(MMF_ERR_ARG, "harmonic must be >= 1");
+    auto& hv = s->V[mode_id];
+    if (harmonic > (int)hv.size() + 1) return fail(MMF_ERR_ARG, "harmonics must be added in order");
+    std::vector<double2> m((size_t)s->D * s->D);
+    for (int e = 0; e < s->D * s->D; ++e) {
+        if (!std::isfinite(V[2 * e]) || !std::isfinite(V[2 * e + 1]))
+            return fail(MMF_ST_NONFINITE, "V not finite");
+        m[e] = make_double2(V[2 * e], V[2 * e + 1]);
+    }
+    if (harmonic == (int)hv.size() + 1) hv.push_back(m);
+    else hv[harmonic - 1] = m;
+    s->state = 0;
+    return MMF_OK;
+}
+
+extern "C" int mmf_batch_destroy(mmf_batch* b);
+
+extern "C" int mmf_sys_destroy(mmf_sys* s) {
+    if (!s) return MMF_ERR_ARG;
+    if (s->solo) mmf_batch_destroy(s->solo);
+    delete s;
+    return MMF_OK;
+}
+
+extern "C" int64_t mmf_dim(const mmf_sys* s) { return s ? sys_dim(s) : -1; }
+
+// ------------------------------------------------------------------ batch plan
+static void fill_coef(const mmf_batch* b, double2* dst) {
+    for (int i = 0; i < b->count; ++i) {
+        const mmf_sys* s = b->sys[i];
+        double2* p = dst + b->desc[i].coef_off;
+        std::memcpy(p, s->H0.data(), sizeof(double2) * s->H0.size());
+        p += s->H0.size();
+        for (size_t l = 0; l < s->V.size(); ++l)
+            for (const auto& m : s->V[l]) {
+                std::memcpy(p, m.data(), sizeof(double2) * m.size());
+                p += m.size();
+            }
+    }
+}
+
+static void free_batch_memory(mmf_batch* b) {
+    if (b->base) {
+        cudaFree(b->base);
+        b->ctx->used -= b->bytes;
+        b->base = nullptr;
+    }
+    if (b->h_coef) cudaFreeHost(b->h_coef);
+    if (b->h_t) cudaFreeHost(b->h_t);
+    b->h_coef = nullptr;
+    b->h_t = nullptr;
+}
+
+extern "C" int mmf_batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int precision,
+                                int nt, mmf_batch** out) {
+    if (!out) return fail(MMF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ctx || count < 1 || !systems || nt < 0) return fail(MMF_ERR_ARG, "bad batch arguments");
+    if (precision != MMF_FP64 && precision != MMF_MIXED) return fail(MMF_ERR_ARG, "bad precision");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    CU(cudaSetDevice(ctx->device));
+    mmf_batch* b = new (std::nothrow) mmf_batch();
+    if (!b) return fail(MMF_ERR_NOMEM, "batch allocation");
+    b->ctx = ctx;
+    b->count = count;
+    b->precision = precision;
+    b->nt = nt;
+    b->sys.assign(systems, systems + count);
+    b->desc.resize(count);
+    const int fp32 = precision == MMF_MIXED;
+    const int hmax = mmf_hetrd_max_n(fp32);
+    for (int i = 0; i < count; ++i) {
+        const mmf_sys* s = systems[i];
+        if (!s || s->ctx != ctx) { delete b; return fail(MMF_ERR_ARG, "system NULL or from another context"); }
+        if (s->omega.empty()) { delete b; return fail(MMF_ERR_ARG, "system has no drive mode"); }
+        MmfDesc& d = b->desc[i];
+        std::memset(&d, 0, sizeof(d));
+        d.D = s->D;
+        d.K = (int)s->omega.size();
+        int64_t M = 1, b0 = 0;
+        for (int k = 0; k < d.K; ++k) {
+            d.N[k] = s->N[k];
+            d.S[k] = (int)M;
+            b0 += (int64_t)s->N[k] * M;
+            M *= (2 * s->N[k] + 1);
+            d.omega[k] = s->omega[k];
+            d.nharm[k] = (int)s->V[k].size();
+        }
+        int64_t n = M * s->D;
+        if (n > hmax && n > jacobi_nmax(precision)) {
+            delete b;
+            return fail(MMF_ERR_UNSUPPORTED, "Floquet dimension " + std::to_string(n) +
+                                                 " above this build's single-CTA limit " + std::to_string(hmax));
+        }
+        d.M = (int)M;
+        d.n = (int)n;
+        d.b0 = (int)b0;
+        d.ld = (int)round_up(n, 4);
+        d.small = n <= jacobi_nmax(precision);
+        int64_t nc = (int64_t)s->D * s->D;
+        for (int k = 0; k < d.K; ++k) nc += (int64_t)d.nharm[k] * s->D * s->D;
+        d.coef_off = b->n_coef;
+        b->n_coef += nc;
+        d.mat_off = b->n_mat;
+        b->n_mat += n * d.ld;
+        d.vec_off = b->n_vec;
+        b->n_vec += n;
+        d.sq_off = b->n_sq;
+        d.pan_off = b->n_pan;
+        if (!d.small) {
+            b->n_sq += n * n;
+            b->n_pan += (int64_t)(d.ld + MMF_NB) * MMF_NB;
+        }
+        d.t_off = b->n_t;
+        b->n_t += nt;
+        d.f_off = b->n_f;
+        b->n_f += (int64_t)nt * M;
+        d.u_off = b->n_u;
+        b->n_u += (int64_t)nt * s->D * s->D;
+        d.p_off = b->n_p;
+        b->n_p += (int64_t)s->D * s->D;
+        b->all.push_back(i);
+        (d.small ? b->small : b->large).push_back(i);
+        b->nmax_all = std::max(b->nmax_all, (int)n);
+        if (d.small) b->nmax_small = std::max(b->nmax_small, (int)n);
+        else b->nmax_large = std::max(b->nmax_large, (int)n);
+        b->Mmax = std::max(b->Mmax, (int)M);
+        b->Dmax = std::max(b->Dmax, s->D);
+    }
+    // device layout
+    const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
+    Pool p;
+    size_t o_desc = p.take(sizeof(MmfDesc) * count);
+    size_t o_all = p.take(sizeof(int) * count), o_small = p.take(sizeof(int) * count),
+           o_large = p.take(sizeof(int) * count), o_status = p.take(sizeof(int) * count);
+    size_t o_coef = p.take(sizeof(double2) * b->n_coef);
+    size_t o_H = p.take(cs * b->n_mat);
+    size_t o_Zf = p.take(sizeof(double2) * b->n_mat);
+    size_t o_Zp = fp32 ? p.take(cs * b->n_mat) : 0;
+    size_t o_E = p.take(sizeof(double) * b->n_vec), o_d = p.take(sizeof(double) * b->n_vec),
+           o_e = p.take(sizeof(double) * b->n_vec), o_aux = p.take(sizeof(double) * 8 * count);
+    size_t o_tau = p.take(cs * b->n_vec);
+    size_t o_Y = p.take(sizeof(double) * b->n_sq), o_work = p.take(sizeof(double) * 3 * b->n_sq);
+    size_t o_Vp = p.take(cs * b->n_pan), o_Wp = p.take(cs * b->n_pan);
+    size_t o_t = p.take(sizeof(double) * std::max<int64_t>(b->n_t, 1));
+    size_t o_F = p.take(sizeof(double2) * std::max<int64_t>(b->n_f, 1));
+    size_t o_U = p.take(sizeof(double2) * std::max<int64_t>(b->n_u, 1));
+    size_t o_P = p.take(sizeof(double) * b->n_p);
+    size_t o_R = 0, o_S = 0, o_HX = 0, o_E2 = 0;
+    if (fp32) {
+        o_R = p.take(sizeof(double2) * b->n_mat);
+        o_S = p.take(sizeof(double2) * b->n_mat);
+        o_HX = p.take(sizeof(double2) * b->n_mat);
+        o_E2 = p.take(sizeof(double) * b->n_vec);
+    }
+    b->bytes = p.off;
+    if (ctx->used + b->bytes > ctx->budget) {
+        size_t need = b->bytes;
+        delete b;
+        return fail(MMF_ERR_BUDGET, "batch needs " + std::to_string(need) + " bytes, budget has " +
+                                        std::to_string(ctx->budget - ctx->used));
+    }
+    cudaError_t e = cudaMalloc((void**)&b->base, b->bytes);
+    if (e != cudaSuccess) {
+        delete b;
+        return fail(MMF_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    ctx->used += b->bytes;
+    unsigned char* B = b->base;
+    b->d_desc = (MmfDesc*)(B + o_desc);
+    b->d_all = (int*)(B + o_all);
+    b->d_small = (int*)(B + o_small);
+    b->d_large = (int*)(B + o_large);
+    b->d_status = (int*)(B + o_status);
+    b->d_coef = (double2*)(B + o_coef);
+    b->d_H = B + o_H;
+    b->d_Zf = (double2*)(B + o_Zf);
+    b->d_Zp = fp32 ? (void*)(B + o_Zp) : (void*)b->d_Zf;
+    b->d_E = (double*)(B + o_E);
+    b->d_d = (double*)(B + o_d);
+    b->d_e = (double*)(B + o_e);
+    b->d_aux = (double*)(B + o_aux);
+    b->d_tau = B + o_tau;
+    b->d_Y = (double*)(B + o_Y);
+    b->d_work = (double*)(B + o_work);
+    b->d_Vp = B + o_Vp;
+    b->d_Wp = B + o_Wp;
+    b->d_t = (double*)(B + o_t);
+    b->d_F = (double2*)(B + o_F);
+    b->d_U = (double2*)(B + o_U);
+    b->d_P = (double*)(B + o_P);
+    if (fp32) {
+        b->d_R = (double2*)(B + o_R);
+        b->d_S = (double2*)(B + o_S);
+        b->d_HX = (double2*)(B + o_HX);
+        b->d_E2 = (double*)(B + o_E2);
+    }
+    e = cudaMallocHost((void**)&b->h_coef, sizeof(double2) * std::max<int64_t>(b->n_coef, 1));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_t, sizeof(double) * std::max<int64_t>(b->n_t, 1));
+    if (e != cudaSuccess) {
+        free_batch_memory(b);
+        delete b;
+        return fail(MMF_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+    }
+    fill_coef(b, b->h_coef);
+    std::memset(b->h_t, 0, sizeof(double) * std::max<int64_t>(b->n_t, 1));
+    cudaStream_t st = ctx->stream;
+    e = cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(MmfDesc) * count, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_all, b->all.data(), sizeof(int) * b->all.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !b->small.empty())
+        e = cudaMemcpyAsync(b->d_small, b->small.data(), sizeof(int) * b->small.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !b->large.empty())
+        e = cudaMemcpyAsync(b->d_large, b->large.data(), sizeof(int) * b->large.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_coef, b->h_coef, sizeof(double2) * b->n_coef, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_batch_memory(b);
+        delete b;
+        return fail(MMF_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    }
+    *out = b;
+    return MMF_OK;
+}
+
+static void drop_events(mmf_batch* b) {
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    b->ev.clear();
+    b->timing_runs = 0;
+    b->runs_recorded = 0;
+}
+
+extern "C" int mmf_batch_timing(mmf_batch* b, int max_runs) {
+    if (!b || max_runs < 0 || max_runs > 4096) return fail(MMF_ERR_ARG, "bad batch or max_runs");
+    std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
+    CU(cudaSetDevice(b->ctx->device));
+    CU(cudaStreamSynchronize(b->ctx->stream));
+    drop_events(b);
+    b->ev.resize((size_t)max_runs * (ST_COUNT + 1));
+    for (auto& e : b->ev) CU(cudaEventCreate(&e));
+    b->timing_runs = max_runs;
+    return MMF_OK;
+}
+
+extern "C" int mmf_batch_stage_ms(mmf_batch* b, double* ms, int* runs) {
+    if (!b || !ms) return fail(MMF_ERR_ARG, "batch and ms required");
+    std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
+    CU(cudaSetDevice(b->ctx->device));
+    CU(cudaStreamSynchronize(b->ctx->stream));
+    for (int s = 0; s < ST_COUNT; ++s) ms[s] = 0.0;
+    int nr = std::min(b->runs_recorded, b->timing_runs);
+    for (int r = 0; r < nr; ++r)
+        for (int s = 0; s < ST_COUNT; ++s) {
+            float f = 0.f;
+            CU(cudaEventElapsedTime(&f, b->ev[(size_t)r * (ST_COUNT + 1) + s],
+                                    b->ev[(size_t)r * (ST_COUNT + 1) + s + 1]));
+            ms[s] += f;
+        }
+    if (runs) *runs = nr;
+    b->runs_recorded = 0;
+    return MMF_OK;
+}
+
+extern "C" int mmf_batch_destroy(mmf_batch* b) {
+    if (!b) return MMF_ERR_ARG;
+    std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
+    cudaSetDevice(b->ctx->device);
+    cudaStreamSynchronize(b->ctx->stream);
+    drop_events(b);
+    free_batch_memory(b);
+    delete b;
+    return MMF_OK;
+}
+
+extern "C" size_t mmf_batch_bytes(const mmf_batch* b) { return b ? b->bytes : 0; }
+
+extern "C" int mmf_batch_set_times(mmf_batch* b, double t0, const double* t) {
+    if (!b || (b->nt > 0 && !t)) return fail(MMF_ERR_ARG, "batch and times required");
+    for (int64_t i = 0; i < b->n_t; ++i)
+        if (!std::isfinite(t[i])) return fail(MMF_ST_NONFINITE, "time not finite");
+    if (!std::isfinite(t0)) return fail(MMF_ST_NONFINITE, "t0 not finite");
+    std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
+    CU(cudaStreamSynchronize(b->ctx->stream));  // staging buffer may be in flight
+    if (b->n_t > 0) std::memcpy(b->h_t, t, sizeof(double) * b->n_t);
+    b->t0 = t0;
+    b->times_set = true;
+    if (b->n_t > 0)
+        CU(cudaMemcpyAsync(b->d_t, b->h_t, sizeof(double) * b->n_t, cudaMemcpyHostToDevice, b->ctx->stream));
+    return MMF_OK;
+}
+
+extern "C" int mmf_batch_upload(mmf_batch* b) {
+    if (!b) return fail(MMF_ERR_ARG, "batch is NULL");
+    std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
+    CU(cudaSetDevice(b->ctx->device));
+    cudaStream_t st = b->ctx->stream;
+    CU(cudaMemcpyAsync(b->d_coef, b->h_coef, sizeof(double2) * b->n_coef, cudaMemcpyHostToDevice, st));
+    if (b->n_t > 0)
+        CU(cudaMemcpyAsync(b->d_t, b->h_t, sizeof(double) * b->n_t, cudaMemcpyHostToDevice, st));
+    return MMF_OK;
+}
+
+static MmfLaunch launch_of(const mmf_batch* b, const std::vector<int>& list, const int* dlist, int nmax) {
+    MmfLaunch L;
+    L.desc = b->d_desc;
+    L.idx = dlist;
+    L.count = (int)list.size();
+    L.nmax = nmax;
+    L.stream = b->ctx->stream;
+    return L;
+}
+
+#define LAUNCH(call, nk)                                                                  \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(MMF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        g_launches += (nk);                                                               \
+    } while (0)
+
+static int stage_assemble(mmf_batch* b) {
+    const int fp32 = b->precision == MMF_MIXED;
+    cudaStream_t st = b->ctx->stream;
+    mark(b, ST_ASSEMBLE);
+    CU(cudaMemsetAsync(b->d_status, 0, sizeof(int) * b->count, st));
+    MmfLaunch La = launch_of(b, b->all, b->d_all, b->nmax_all);
+    LAUNCH(mmf_launch_assemble(La, b->d_coef, b->d_H, fp32), 1);
+    b->last_stage = 1;
+    return MMF_OK;
+}
+
+static int stage_eig(mmf_batch* b) {
+    const int fp32 = b->precision == MMF_MIXED;
+    mark(b, ST_JACOBI);
+    if (!b->small.empty()) {
+        MmfLaunch Ls = launch_of(b, b->small, b->d_small, b->nmax_small);
+        LAUNCH(mmf_launch_jacobi(Ls, b->d_H, nullptr, b->d_E, b->d_Zf, b->d_status, fp32, 40), 1);
+    }
+    if (!b->large.empty()) {
+        MmfLaunch Ll = launch_of(b, b->large, b->d_large, b->nmax_large);
+        mark(b, ST_HETRD);
+        LAUNCH(mmf_launch_hetrd(Ll, b->d_H, b->d_Vp, b->d_Wp, b->d_d, b->d_e, b->d_tau, fp32), 1);
+        mark(b, ST_TRIDIAG);
+        LAUNCH(mmf_launch_tridiag_eig(Ll, b->d_d, b->d_e, b->d_aux, b->d_E, b->d_Y, b->d_work, b->d_status), 3);
+        mark(b, ST_BACKTRANSFORM);
+        LAUNCH(mmf_launch_backtransform(Ll, b->d_H, b->d_tau, b->d_Vp, b->d_Y, b->d_Zp, fp32), 2);
+        if (fp32) LAUNCH(mmf_launch_widen(Ll, b->d_Zp, b->d_Zf, fp32), 1);
+    } else {
+        mark(b, ST_HETRD);
+        mark(b, ST_TRIDIAG);
+        mark(b, ST_BACKTRANSFORM);
+    }
+    mark(b, ST_REFINE);
+    if (fp32) {
+        MmfLaunch La = launch_of(b, b->all, b->d_all, b->nmax_all);
+        int nk = 0;
+        cudaError_t e = mmf_launch_refine(La, b->d_coef, b->d_Zf, b->d_E, b->d_R, b->d_S, b->d_HX,
+                                          b->d_E2, 2, b->d_status);
+        if (e != cudaSuccess) return fail(MMF_ERR_CUDA, std::string("refine: ") + cudaGetErrorString(e));
+        nk = 2 * 5 + 1;
+        g_launches += nk;
+    }
+    b->last_stage = 2;
+    return MMF_OK;
+}
+
+static int stage_outputs(mmf_batch* b) {
+    cudaStream_t st = b->ctx->stream;
+    mark(b, ST_OUTPUTS);
+    if (b->n_u > 0) CU(cudaMemsetAsync(b->d_U, 0, sizeof(double2) * b->n_u, st));
+    CU(cudaMemsetAsync(b->d_P, 0, sizeof(double) * b->n_p, st));
+    MmfLaunch La = launch_of(b, b->all, b->d_all, b->nmax_all);
+    LAUNCH(mmf_launch_outputs(La, b->Mmax, b->Dmax, b->d_E, b->d_Zf, b->d_t, b->t0, b->nt, b->d_F,
+                              b->d_U, b->d_P, 1e-8),
+           b->nt > 0 ? 3 : 1);
+    mark(b, ST_COUNT);
+    if (b->timing_runs > 0) b->runs_recorded++;
+    b->last_stage = 3;
+    return MMF_OK;
+}
+
+extern "C" int mmf_batch_run(mmf_batch* b) {
+    if (!b) return fail(MMF_ERR_ARG, "batch is NULL");
+    if (b->nt > 0 && !b->times_set) return fail(MMF_ERR_STATE, "times not set");
+    std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
+    CU(cudaSetDevice(b->ctx->device));
+    g_launches = 0;
+    int rc = stage_assemble(b);
+    if (rc == MMF_OK) rc = stage_eig(b);
+    if (rc == MMF_OK) rc = stage_outputs(b);
+    return rc;
+}
+
+extern "C" int mmf_batch_sync(mmf_batch* b, int* status) {
+    if (!b) return fail(MMF_ERR_ARG, "batch is NULL");
+    std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
+    CU(cudaSetDevice(b->ctx->device));
+    std::vector<int> st(b->count);
+    CU(cudaMemcpyAsync(st.data(), b->d_status, sizeof(int) * b->count, cudaMemcpyDeviceToHost, b->ctx->stream));
+    CU(cudaStreamSynchronize(b->ctx->stream));
+    int worst = 0;
+    for (int i = 0; i < b->count; ++i) worst = std::max(worst, st[i]);
+    if (status) std::memcpy(status, st.data(), sizeof(int) * b->count);
+    return worst;
+}
+
+static int copy_d2h(mmf_batch* b, void* dst, const void* src, size_t bytes) {
+    if (!bytes) return MMF_OK;
+    CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, b->ctx->stream));
+    return MMF_OK;
+}
+
+extern "C" int mmf_batch_get(mmf_batch* b, int i, double* E, double* U, double* P) {
+    if (!b || i < 0 || i >= b->count) return fail(MMF_ERR_ARG, "bad batch index");
+    if (b->last_stage < 2) return fail(MMF_ERR_STATE, "batch not run");
+    std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
+    CU(cudaSetDevice(b->ctx->device));
+    const MmfDesc& d = b->desc[i];
+    int rc = MMF_OK;
+    if (E) rc = copy_d2h(b, E, b->d_E + d.vec_off, sizeof(double) * d.n);
+    if (rc == MMF_OK && U) rc = copy_d2h(b, U, b->d_U + d.u_off, sizeof(double2) * (size_t)b->nt * d.D * d.D);
+    if (rc == MMF_OK && P) rc = copy_d2h(b, P, b->d_P + d.p_off, sizeof(double) * d.D * d.D);
+    if (rc != MMF_OK) return rc;
+    CU(cudaStreamSynchronize(b->ctx->stream));
+    return MMF_OK;
+}
+
+extern "C" int mmf_batch_eigenvectors(mmf_batch* b, int i, double* Z) {
+    if (!b || i < 0 || i >= b->count || !Z) return fail(MMF_ERR_ARG, "bad batch index or Z");
+    if (b->last_stage < 2) return fail(MMF_ERR_STATE, "batch not diagonalised");
+    std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
+    CU(cudaSetDevice(b->ctx->device));
+    const MmfDesc& d = b->desc[i];
+    CU(cudaMemcpy2DAsync(Z, sizeof(double2) * d.n, b->d_Zf + d.mat_off, sizeof(double2) * d.ld,
+                         sizeof(double2) * d.n, d.n, cudaMemcpyDeviceToHost, b->ctx->stream));
+    CU(cudaStreamSynchronize(b->ctx->stream));
+    return MMF_OK;
+}
+
+extern "C" int mmf_batch_results(mmf_batch* b, double* E, double* U, double* P) {
+    if (!b) return fail(MMF_ERR_ARG, "batch is NULL");
+    std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
+    CU(cudaSetDevice(b->ctx->device));
+    int rc = MMF_OK;
+    if (E) rc = copy_d2h(b, E, b->d_E, sizeof(double) * b->n_vec);
+    if (rc == MMF_OK && U) rc = copy_d2h(b, U, b->d_U, sizeof(double2) * b->n_u);
+    if (rc == MMF_OK && P) rc = copy_d2h(b, P, b->d_P, sizeof(double) * b->n_p);
+    if (rc != MMF_OK) return rc;
+    CU(cudaStreamSynchronize(b->ctx->stream));
+    return MMF_OK;
+}
+
+extern "C" int64_t mmf_batch_offset(const mmf_batch* b, int what, int i) {
+    if (!b || i < 0 || i >= b->count) return -1;
+    if (what == 0) return b->desc[i].vec_off;
+    if (what == 1) return b->desc[i].u_off;
+    if (what == 2) return b->desc[i].p_off;
+    return -1;
+}
+
+extern "C" int64_t mmf_batch_size(const mmf_batch* b, int what) {
+    if (!b) return -1;
+    if (what == 0) return b->n_vec;
+    if (what == 1) return b->n_u;
+    if (what == 2) return b->n_p;
+    return -1;
+}
+
+// ------------------------------------------------------------------ single-system path
+static int solo_ensure(mmf_sys* s, int precision, int nt) {
+    if (s->solo && (s->solo->precision != precision || s->solo->nt < nt)) {
+        mmf_batch_destroy(s->solo);
+        s->solo = nullptr;
+    }
+    if (!s->solo) {
+        mmf_sys* arr[1] = {s};
+        int rc = mmf_batch_create(s->ctx, 1, arr, precision, nt, &s->solo);
+        if (rc != MMF_OK) return rc;
+    }
+    return MMF_OK;
+}
+
+extern "C" int mmf_build(mmf_sys* s, int precision, int64_t* n_out) {
+    if (!s) return fail(MMF_ERR_ARG, "sys is NULL");
+    if (s->omega.empty()) return fail(MMF_ERR_ARG, "system has no drive mode");
+    std::lock_guard<std::recursive_mutex> lk(s->ctx->mu);
+    int nt = s->solo ? s->solo->nt : 0;
+    if (s->solo) { mmf_batch_destroy(s->solo); s->solo = nullptr; }
+    int rc = solo_ensure(s, precision, nt);
+    if (rc != MMF_OK) return rc;
+    CU(cudaSetDevice(s->ctx->device));
+    g_launches = 0;
+    rc = stage_assemble(s->solo);
+    if (rc != MMF_OK) return rc;
+    s->state = 1;
+    if (n_out) *n_out = s->solo->desc[0].n;
+    return MMF_OK;
+}
+
+extern "C" int mmf_hamiltonian(mmf_sys* s, double* HF) {
+    if (!s || !HF) return fail(MMF_ERR_ARG, "sys and HF required");
+    if (s->state != 1 || !s->solo) return fail(MMF_ERR_STATE, "call after mmf_build, before mmf_diagonalise");
+    std::lock_guard<std::recursive_mutex> lk(s->ctx->mu);
+    mmf_batch* b = s->solo;
+    const MmfDesc& d = b->desc[0];
+    CU(cudaSetDevice(s->ctx->device));
+    if (b->precision == MMF_FP64) {
+        CU(cudaMemcpy2DAsync(HF, sizeof(double2) * d.n, b->d_H, sizeof(double2) * d.ld,
+                             sizeof(double2) * d.n, d.n, cudaMemcpyDeviceToHost, s->ctx->stream));
+        CU(cudaStreamSynchronize(s->ctx->stream));
+    } else {
+        std::vector<float2> tmp((size_t)d.n * d.n);
+        CU(cudaMemcpy2DAsync(tmp.data(), sizeof(float2) * d.n, b->d_H, sizeof(float2) * d.ld,
+                             sizeof(float2) * d.n, d.n, cudaMemcpyDeviceToHost, s->ctx->stream));
+        CU(cudaStreamSynchronize(s->ctx->stream));
+        for (size_t e = 0; e < tmp.size(); ++e) {
+            HF[2 * e] = tmp[e].x;
+            HF[2 * e + 1] = tmp[e].y;
+        }
+    }
+    return MMF_OK;
+}
+
+extern "C" int mmf_diagonalise(mmf_sys* s) {
+    if (!s) return fail(MMF_ERR_ARG, "sys is NULL");
+    if (s->state < 1 || !s->solo) return fail(MMF_ERR_STATE, "call mmf_build first");
+    std::lock_guard<std::recursive_mutex> lk(s->ctx->mu);
+    CU(cudaSetDevice(s->ctx->device));
+    if (s->state >= 2) {  // rebuild: the reduction consumed H_F
+        int rc = stage_assemble(s->solo);
+        if (rc != MMF_OK) return rc;
+    }
+    g_launches = 0;
+    int rc = stage_eig(s->solo);
+    if (rc != MMF_OK) return rc;
+    s->state = 2;
+    return mmf_batch_sync(s->solo, nullptr);
+}
+
+extern "C" int mmf_quasienergies(mmf_sys* s, double* E) {
+    if (!s || !E) return fail(MMF_ERR_ARG, "sys and E required");
+    if (s->state < 2) return fail(MMF_ERR_STATE, "call mmf_diagonalise first");
+    return mmf_batch_get(s->solo, 0, E, nullptr, nullptr);
+}
+
+extern "C" int mmf_eigenvectors(mmf_sys* s, double* Z) {
+    if (!s || !Z) return fail(MMF_ERR_ARG, "sys and Z required");
+    if (s->state < 2) return fail(MMF_ERR_STATE, "call mmf_diagonalise first");
+    return mmf_batch_eigenvectors(s->solo, 0, Z);
+}
+
+// Re-plan the single-system batch for nt times, keeping the eigenpairs on the device.
+static int solo_outputs(mmf_sys* s, double t0, int nt, const double* t) {
+    mmf_batch* b = s->solo;
+    if (b->nt != nt) {
+        // a plan with room for nt times; the eigenpairs are recomputed on the new plan
+        mmf_batch* nb = nullptr;
+        mmf_sys* arr[1] = {s};
+        int rc = mmf_batch_create(s->ctx, 1, arr, b->precision, nt, &nb);
+        if (rc != MMF_OK) return rc;
+        mmf_batch_destroy(b);
+        s->solo = b = nb;
+        rc = stage_assemble(b);
+        if (rc == MMF_OK) rc = stage_eig(b);
+        if (rc != MMF_OK) return rc;
+    }
+    int rc = mmf_batch_set_times(b, t0, t);
+    if (rc != MMF_OK) return rc;
+    return stage_outputs(b);
+}
+
+extern "C" int mmf_time_evolution(mmf_sys* s, double t0, int nt, const double* t, double* U) {
+    if (!s || nt < 1 || !t || !U) return fail(MMF_ERR_ARG, "sys, nt >= 1, t and U required");
+    if (s->state < 2) return fail(MMF_ERR_STATE, "call mmf_diagonalise first");
+    std::lock_guard<std::recursive_mutex> lk(s->ctx->mu);
+    CU(cudaSetDevice(s->ctx->device));
+    int rc = solo_outputs(s, t0, nt, t);
+    if (rc != MMF_OK) return rc;
+    rc = mmf_batch_get(s->solo, 0, nullptr, U, nullptr);
+    if (rc != MMF_OK) return rc;
+    return mmf_batch_sync(s->solo, nullptr);
+}
+
+extern "C" int mmf_transition_avg(mmf_sys* s, double* P) {
+    if (!s || !P) return fail(MMF_ERR_ARG, "sys and P required");
+    if (s->state < 2) return fail(MMF_ERR_STATE, "call mmf_diagonalise first");
+    std::lock_guard<std::recursive_mutex> lk(s->ctx->mu);
+    CU(cudaSetDevice(s->ctx->device));
+    mmf_batch* b = s->solo;
+    if (b->last_stage < 3) {
+        if (b->nt > 0 && !b->times_set) {
+            std::vector<double> z((size_t)b->nt, 0.0);
+            int rc = mmf_batch_set_times(b, 0.0, z.data());
+            if (rc != MMF_OK) return rc;
+        }
+        int rc = stage_outputs(b);
+        if (rc != MMF_OK) return rc;
+    }
+    return mmf_batch_get(b, 0, nullptr, nullptr, P);
+}
+
+extern "C" int mmf_micromotion(mmf_sys* s, int nt, const double* t, double* UF, int64_t* reps) {
+    if (!s || nt < 1 || !t || !UF) return fail(MMF_ERR_ARG, "sys, nt >= 1, t and UF required");
+    if (s->state < 2) return fail(MMF_ERR_STATE, "call mmf_diagonalise first");
+    std::lock_guard<std::recursive_mutex> lk(s->ctx->mu);
+    CU(cudaSetDevice(s->ctx->device));
+    mmf_batch* b = s->solo;
+    const MmfDesc& d = b->desc[0];
+    cudaStream_t st = s->ctx->stream;
+    const size_t nuf = (size_t)nt * d.D * d.D;
+    unsigned char* tmp = nullptr;
+    const size_t o_t = 0, o_r = (sizeof(double) * nt + 255) / 256 * 256,
+                 o_u = o_r + (sizeof(int64_t) * d.D + 255) / 256 * 256;
+    CU(cudaMallocAsync((void**)&tmp, o_u + sizeof(double2) * nuf, st));
+    int rc = MMF_OK;
+    cudaError_t e = cudaMemcpyAsync(tmp + o_t, t, sizeof(double) * nt, cudaMemcpyHostToDevice, st);
+    MmfLaunch L = launch_of(b, b->all, b->d_all, b->nmax_all);
+    if (e == cudaSuccess)
+        e = mmf_launch_micromotion(L, d.D, b->d_Zf, (const double*)(tmp + o_t), nt, (int64_t*)(tmp + o_r),
+                                   (double2*)(tmp + o_u));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(UF, tmp + o_u, sizeof(double2) * nuf, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && reps) e = cudaMemcpyAsync(reps, tmp + o_r, sizeof(int64_t) * d.D, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(tmp, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = fail(MMF_ERR_CUDA, std::string("micromotion: ") + cudaGetErrorString(e));
+    return rc;
+}
+
+extern "C" int mmf_time_evolution_operator(mmf_sys* s, int precision, double t0, int nt,
+                                           const double* t, double* U) {
+    int64_t n = 0;
+    int rc = mmf_build(s, precision, &n);
+    if (rc != MMF_OK) return rc;
+    rc = mmf_diagonalise(s);
+    if (rc < 0) return rc;
+    int rc2 = mmf_time_evolution(s, t0, nt, t, U);
+    return rc2 != MMF_OK ? rc2 : rc;
+}

@@ -1,0 +1,135 @@
+// mmf_internal.h -- device-side data layout and helpers shared by the CUDA kernels.
+//
+// One "batch" holds many independent driven systems (Eq. 1).  Each system has a
+// descriptor with its sizes and the offsets of its slices in the batch's device pools.
+// All n x n matrices are column-major with leading dimension ld (a multiple of 4).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MMF_MAX_MODES 4
+
+struct MmfDesc {
+    int32_t D, K, M, n;                 // levels, modes, Fourier blocks, n = D * M
+    int32_t ld, b0, small, pad0;        // leading dim, central block index, Jacobi flag
+    int32_t N[MMF_MAX_MODES];           // truncation |n_k| <= N_k
+    int32_t nharm[MMF_MAX_MODES];       // harmonics per mode (couplings V^{k,1..nharm})
+    int32_t S[MMF_MAX_MODES];           // block strides, S_0 = 1, S_k = prod_{k'<k}(2N_k'+1)
+    double omega[MMF_MAX_MODES];
+    int64_t coef_off;   // double2 offset of H0 (D x D row-major); V^{k,h} follow (mode, harmonic)
+    int64_t mat_off;    // element offset of this system's n x ld matrices in matrix pools
+    int64_t vec_off;    // element offset of its length-n vectors (packed)
+    int64_t sq_off;     // element offset of its n x n row-major scratch (tridiagonal solver)
+    int64_t pan_off;    // element offset of its n x NB panels (Householder) / T factors
+    int64_t t_off;      // offset of its nt times
+    int64_t f_off;      // double2 offset of its nt x M Fourier phase table
+    int64_t u_off;      // double2 offset of its nt x D x D time-evolution output
+    int64_t p_off;      // offset of its D x D transition-probability output
+};
+
+// ------------------------------------------------------------------ complex helpers
+template <class R> struct Cx;
+template <> struct Cx<double> { typedef double2 T; };
+template <> struct Cx<float> { typedef float2 T; };
+
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+
+template <class C> __device__ __forceinline__ C czero();
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+
+#define MMF_CX_OPS(C, R)                                                                      \
+    __device__ __forceinline__ C operator+(C a, C b) { return mk(a.x + b.x, a.y + b.y); }     \
+    __device__ __forceinline__ C operator-(C a, C b) { return mk(a.x - b.x, a.y - b.y); }     \
+    __device__ __forceinline__ C operator*(C a, C b) {                                       \
+        return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);                             \
+    }                                                                                         \
+    __device__ __forceinline__ C operator*(R s, C a) { return mk(s * a.x, s * a.y); }        \
+    __device__ __forceinline__ C conj(C a) { return mk(a.x, -a.y); }                         \
+    /* conj(a) * b */                                                                         \
+    __device__ __forceinline__ C cmulc(C a, C b) {                                           \
+        return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);                             \
+    }                                                                                         \
+    __device__ __forceinline__ R abs2(C a) { return a.x * a.x + a.y * a.y; }
+
+MMF_CX_OPS(double2, double)
+MMF_CX_OPS(float2, float)
+
+__device__ __forceinline__ double2 to_c128(double2 a) { return a; }
+__device__ __forceinline__ double2 to_c128(float2 a) { return make_double2(a.x, a.y); }
+template <class C> __device__ __forceinline__ C from_c128(double2 a);
+template <> __device__ __forceinline__ double2 from_c128<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 from_c128<float2>(double2 a) {
+    return make_float2(__double2float_rn(a.x), __double2float_rn(a.y));
+}
+
+template <class R> __device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Fourier vector of block b: n_k = (b / S_k) mod (2N_k+1) - N_k
+__device__ __forceinline__ void block_nvec(const MmfDesc& d, int b, int* nv) {
+#pragma unroll
+    for (int k = 0; k < MMF_MAX_MODES; ++k) {
+        if (k < d.K) {
+            int w = 2 * d.N[k] + 1;
+            nv[k] = (b / d.S[k]) % w - d.N[k];
+        } else {
+            nv[k] = 0;
+        }
+    }
+}
+
+// n.omega accumulated over k ascending, each product and sum rounded once (no FMA)
+__device__ __forceinline__ double block_ndotw(const MmfDesc& d, int b) {
+    int nv[MMF_MAX_MODES];
+    block_nvec(d, b, nv);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < MMF_MAX_MODES; ++k)
+        if (k < d.K) s = __dadd_rn(s, __dmul_rn((double)nv[k], d.omega[k]));
+    return s;
+}
+
+// ------------------------------------------------------------------ status codes (device)
+#define MMF_ST_OK 0
+#define MMF_ST_NOCONV 1      // iteration cap reached
+#define MMF_ST_NONFINITE 2   // NaN / Inf encountered
+
+// ------------------------------------------------------------------ kernel launchers
+// Every launcher takes the device descriptor array and a device list of system indices.
+struct MmfLaunch {
+    const MmfDesc* desc;     // device
+    const int* idx;          // device: systems in this launch
+    int count;               // number of systems in this launch
+    int nmax;                // largest n among them
+    cudaStream_t stream;
+};
+
+cudaError_t mmf_launch_assemble(const MmfLaunch& L, const double2* coef, void* H, int fp32);
+cudaError_t mmf_launch_jacobi(const MmfLaunch& L, void* H, void* Zw, double* E, void* Z,
+                              int* status, int fp32, int max_sweeps);
+cudaError_t mmf_launch_hetrd(const MmfLaunch& L, void* H, void* Vp, void* Wp, double* dvec,
+                             double* evec, void* tau, int fp32);
+cudaError_t mmf_launch_tridiag_eig(const MmfLaunch& L, const double* dvec, const double* evec,
+                                   double* aux, double* E, double* Y, double* work, int* status);
+cudaError_t mmf_launch_backtransform(const MmfLaunch& L, const void* H, const void* tau,
+                                     void* Tf, const double* Y, void* Z, int fp32);
+cudaError_t mmf_launch_widen(const MmfLaunch& L, const void* Zp, double2* Z, int fp32);
+cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const double* E,
+                               const double2* Z, const double* t, double t0, int nt, double2* F,
+                               double2* U, double* P, double cluster_rel);
+int mmf_hetrd_max_n(int fp32);
+cudaError_t mmf_launch_micromotion(const MmfLaunch& L, int D, const double2* Z, const double* t,
+                                   int nt, int64_t* reps, double2* UF);
+cudaError_t mmf_launch_refine(const MmfLaunch& L, const double2* coef, double2* X, double* E,
+                              double2* R, double2* S, double2* HX, double* E2, int iters,
+                              int* status);
+
+#define MMF_NB 32          // Householder panel width and back-transform block size
+#define MMF_JACOBI_NMAX_F64 84
+#define MMF_JACOBI_NMAX_F32 118

@@ -1,0 +1,324 @@
+"""Thin ctypes binding of libmmf.so (include/mmf.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; there is no CPU path.  If the
+library cannot be loaded or no GPU is usable, the calls raise ``MmfError``.
+
+The ``mmf_*`` functions of the C ABI are exposed under the same names on ``lib()``;
+``Context``, ``System`` and ``Batch`` wrap the handles for NumPy callers.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+LIB_PATH = os.path.join(HERE, "libmmf.so")
+HEADER = os.path.join(ROOT, "include", "mmf.h")
+
+MMF_OK = 0
+MMF_ERR_ARG = -1
+MMF_ERR_STATE = -2
+MMF_ERR_BUDGET = -3
+MMF_ERR_CUDA = -4
+MMF_ERR_UNSUPPORTED = -5
+MMF_ERR_NOMEM = -6
+MMF_ST_NOCONV = 1
+MMF_ST_NONFINITE = 2
+MMF_FP64 = 0
+MMF_MIXED = 1
+
+_lib = None
+
+
+class MmfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+_SIGS = {
+    "mmf_ctx_create": (_I, [_I, _SZ, _P, _PP]),
+    "mmf_ctx_destroy": (_I, [_P]),
+    "mmf_ctx_bytes_in_use": (_SZ, [_P]),
+    "mmf_ctx_budget": (_SZ, [_P]),
+    "mmf_sys_create": (_I, [_P, _I, _P, _PP]),
+    "mmf_add_mode": (_I, [_P, _D, _I, ctypes.POINTER(_I)]),
+    "mmf_add_coupling": (_I, [_P, _I, _I, _P]),
+    "mmf_sys_destroy": (_I, [_P]),
+    "mmf_dim": (_I64, [_P]),
+    "mmf_build": (_I, [_P, _I, ctypes.POINTER(_I64)]),
+    "mmf_hamiltonian": (_I, [_P, _P]),
+    "mmf_diagonalise": (_I, [_P]),
+    "mmf_quasienergies": (_I, [_P, _P]),
+    "mmf_eigenvectors": (_I, [_P, _P]),
+    "mmf_time_evolution": (_I, [_P, _D, _I, _P, _P]),
+    "mmf_transition_avg": (_I, [_P, _P]),
+    "mmf_micromotion": (_I, [_P, _I, _P, _P, _P]),
+    "mmf_time_evolution_operator": (_I, [_P, _I, _D, _I, _P, _P]),
+    "mmf_batch_create": (_I, [_P, _I, _P, _I, _I, _PP]),
+    "mmf_batch_set_times": (_I, [_P, _D, _P]),
+    "mmf_batch_upload": (_I, [_P]),
+    "mmf_batch_run": (_I, [_P]),
+    "mmf_batch_sync": (_I, [_P, _P]),
+    "mmf_batch_get": (_I, [_P, _I, _P, _P, _P]),
+    "mmf_batch_eigenvectors": (_I, [_P, _I, _P]),
+    "mmf_batch_results": (_I, [_P, _P, _P, _P]),
+    "mmf_batch_offset": (_I64, [_P, _I, _I]),
+    "mmf_batch_size": (_I64, [_P, _I]),
+    "mmf_batch_bytes": (_SZ, [_P]),
+    "mmf_batch_timing": (_I, [_P, _I]),
+    "mmf_batch_stage_ms": (_I, [_P, _P, _P]),
+    "mmf_batch_destroy": (_I, [_P]),
+    "mmf_strerror": (ctypes.c_char_p, [_I]),
+    "mmf_last_error": (ctypes.c_char_p, []),
+    "mmf_last_launch_count": (_I, []),
+}
+
+
+def header_symbols() -> List[str]:
+    """Names of the functions declared in include/mmf.h."""
+    with open(HEADER) as f:
+        txt = f.read()
+    return sorted(set(re.findall(r"^MMF_API\s+[\w\s\*]+?\b(mmf_\w+)\s*\(", txt, flags=re.M)))
+
+
+def lib():
+    """Load libmmf.so (building it first if the CUDA toolkit is present and it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            from . import build as _b
+
+            _b.build()
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, allow_numeric: bool = False) -> int:
+    if rc == MMF_OK or (allow_numeric and rc > 0):
+        return rc
+    L = lib()
+    msg = L.mmf_last_error().decode() or L.mmf_strerror(rc).decode()
+    raise MmfError(rc, msg)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _cplx(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+class Context:
+    """A CUDA device + stream binding with an HBM budget (mmf_ctx_*)."""
+
+    def __init__(self, device: int = 0, budget: int = 0, stream: Optional[int] = None):
+        h = ctypes.c_void_p()
+        _check(lib().mmf_ctx_create(device, budget, stream, ctypes.byref(h)))
+        self.h = h
+
+    def bytes_in_use(self) -> int:
+        return int(lib().mmf_ctx_bytes_in_use(self.h))
+
+    def budget(self) -> int:
+        return int(lib().mmf_ctx_budget(self.h))
+
+    def close(self):
+        if self.h:
+            lib().mmf_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class System:
+    """One driven system (mmf_sys_*) defined from a problem description with attributes
+    D, H0, omegas, Ns, couplings (couplings[l][h-1] = V^{l+1,h})."""
+
+    def __init__(self, ctx: Context, problem):
+        self.ctx = ctx
+        self.D = int(problem.D)
+        h = ctypes.c_void_p()
+        H0 = _cplx(problem.H0)
+        _check(lib().mmf_sys_create(ctx.h, self.D, _ptr(H0), ctypes.byref(h)))
+        self.h = h
+        for l, (w, N) in enumerate(zip(problem.omegas, problem.Ns)):
+            mid = ctypes.c_int(-1)
+            _check(lib().mmf_add_mode(self.h, float(w), int(N), ctypes.byref(mid)))
+            for hh, V in enumerate(problem.couplings[l], start=1):
+                _check(lib().mmf_add_coupling(self.h, mid.value, hh, _ptr(_cplx(V))))
+        self.n = int(lib().mmf_dim(self.h))
+
+    def build(self, precision: int = MMF_FP64) -> int:
+        n = ctypes.c_int64(0)
+        _check(lib().mmf_build(self.h, precision, ctypes.byref(n)))
+        return int(n.value)
+
+    def hamiltonian(self) -> np.ndarray:
+        out = np.zeros((self.n, self.n), dtype=np.complex128)  # column-major data
+        _check(lib().mmf_hamiltonian(self.h, _ptr(out)))
+        return out.T.copy()
+
+    def diagonalise(self) -> int:
+        return _check(lib().mmf_diagonalise(self.h), allow_numeric=True)
+
+    def quasienergies(self) -> np.ndarray:
+        E = np.zeros(self.n)
+        _check(lib().mmf_quasienergies(self.h, _ptr(E)))
+        return E
+
+    def eigenvectors(self) -> np.ndarray:
+        Z = np.zeros((self.n, self.n), dtype=np.complex128)
+        _check(lib().mmf_eigenvectors(self.h, _ptr(Z)))
+        return Z.T.copy()
+
+    def time_evolution(self, t, t0: float = 0.0) -> np.ndarray:
+        t = np.ascontiguousarray(np.atleast_1d(np.asarray(t, dtype=np.float64)))
+        U = np.zeros((t.size, self.D, self.D), dtype=np.complex128)
+        _check(lib().mmf_time_evolution(self.h, float(t0), int(t.size), _ptr(t), _ptr(U)))
+        return U
+
+    def transition_avg(self) -> np.ndarray:
+        P = np.zeros((self.D, self.D))
+        _check(lib().mmf_transition_avg(self.h, _ptr(P)))
+        return P
+
+    def micromotion(self, t):
+        t = np.ascontiguousarray(np.atleast_1d(np.asarray(t, dtype=np.float64)))
+        UF = np.zeros((t.size, self.D, self.D), dtype=np.complex128)
+        reps = np.zeros(self.D, dtype=np.int64)
+        _check(lib().mmf_micromotion(self.h, int(t.size), _ptr(t), _ptr(UF), _ptr(reps)))
+        return UF, reps
+
+    def time_evolution_operator(self, t, t0: float = 0.0, precision: int = MMF_FP64) -> np.ndarray:
+        t = np.ascontiguousarray(np.atleast_1d(np.asarray(t, dtype=np.float64)))
+        U = np.zeros((t.size, self.D, self.D), dtype=np.complex128)
+        _check(lib().mmf_time_evolution_operator(self.h, precision, float(t0), int(t.size), _ptr(t),
+                                                 _ptr(U)), allow_numeric=True)
+        return U
+
+    def close(self):
+        if self.h:
+            lib().mmf_sys_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A batch plan over many systems (mmf_batch_*)."""
+
+    def __init__(self, ctx: Context, systems: Sequence[System], precision: int = MMF_FP64, nt: int = 0):
+        self.ctx = ctx
+        self.systems = list(systems)
+        self.count = len(self.systems)
+        self.nt = int(nt)
+        self.precision = precision
+        arr = (ctypes.c_void_p * self.count)(*[s.h.value for s in self.systems])
+        h = ctypes.c_void_p()
+        _check(lib().mmf_batch_create(ctx.h, self.count, ctypes.cast(arr, ctypes.c_void_p), precision,
+                                      self.nt, ctypes.byref(h)))
+        self.h = h
+        self.nE = int(lib().mmf_batch_size(self.h, 0))
+        self.nU = int(lib().mmf_batch_size(self.h, 1))
+        self.nP = int(lib().mmf_batch_size(self.h, 2))
+        self.offE = [int(lib().mmf_batch_offset(self.h, 0, i)) for i in range(self.count)]
+        self.offU = [int(lib().mmf_batch_offset(self.h, 1, i)) for i in range(self.count)]
+        self.offP = [int(lib().mmf_batch_offset(self.h, 2, i)) for i in range(self.count)]
+
+    def set_times(self, t0: float, t: np.ndarray):
+        t = np.ascontiguousarray(np.asarray(t, dtype=np.float64).reshape(self.count, self.nt))
+        _check(lib().mmf_batch_set_times(self.h, float(t0), _ptr(t)))
+
+    def upload(self):
+        _check(lib().mmf_batch_upload(self.h))
+
+    def run(self):
+        _check(lib().mmf_batch_run(self.h))
+        return int(lib().mmf_last_launch_count())
+
+    def sync(self) -> np.ndarray:
+        st = np.zeros(self.count, dtype=np.int32)
+        _check(lib().mmf_batch_sync(self.h, _ptr(st)), allow_numeric=True)
+        return st
+
+    def get(self, i: int):
+        s = self.systems[i]
+        E = np.zeros(s.n)
+        U = np.zeros((self.nt, s.D, s.D), dtype=np.complex128)
+        P = np.zeros((s.D, s.D))
+        _check(lib().mmf_batch_get(self.h, i, _ptr(E), _ptr(U) if self.nt else None, _ptr(P)))
+        return E, U, P
+
+    def eigenvectors(self, i: int) -> np.ndarray:
+        s = self.systems[i]
+        Z = np.zeros((s.n, s.n), dtype=np.complex128)
+        _check(lib().mmf_batch_eigenvectors(self.h, i, _ptr(Z)))
+        return Z.T.copy()
+
+    def results(self, E=None, U=None, P=None):
+        """Packed results into (optionally preallocated, ideally pinned) host arrays."""
+        E = np.zeros(self.nE) if E is None else E
+        U = np.zeros(max(self.nU, 1), dtype=np.complex128) if U is None else U
+        P = np.zeros(self.nP) if P is None else P
+        _check(lib().mmf_batch_results(self.h, _ptr(E), _ptr(U), _ptr(P)))
+        return E, U, P
+
+    def unpack(self, E, U, P, i: int):
+        s = self.systems[i]
+        e = E[self.offE[i]:self.offE[i] + s.n]
+        u = U[self.offU[i]:self.offU[i] + self.nt * s.D * s.D].reshape(self.nt, s.D, s.D)
+        p = P[self.offP[i]:self.offP[i] + s.D * s.D].reshape(s.D, s.D)
+        return e, u, p
+
+    STAGES = ("assemble", "jacobi", "hetrd", "tridiag", "backtransform", "refine", "outputs")
+
+    def timing(self, max_runs: int):
+        _check(lib().mmf_batch_timing(self.h, int(max_runs)))
+
+    def stage_ms(self):
+        ms = np.zeros(len(self.STAGES))
+        runs = ctypes.c_int(0)
+        _check(lib().mmf_batch_stage_ms(self.h, _ptr(ms), ctypes.byref(runs)))
+        return dict(zip(self.STAGES, ms.tolist())), int(runs.value)
+
+    def bytes(self) -> int:
+        return int(lib().mmf_batch_bytes(self.h))
+
+    def close(self):
+        if self.h:
+            lib().mmf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
