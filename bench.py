@@ -188,7 +188,10 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    stream = torch.cuda.current_stream()
+    # a dedicated stream shared by the library and the timing events (the legacy default
+    # stream has handle 0, which the library would read as "make your own")
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
 
     def barrier():
         if world > 1:

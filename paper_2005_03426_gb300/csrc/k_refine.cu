@@ -1,10 +1,543 @@
-// k_refine.cu -- S6: Ogita-Aishima refinement of the mixed-precision eigenpairs.
+// k_refine.cu -- S6: Ogita-Aishima refinement of approximate eigenpairs (mixed path).
+//
+// Ogita & Aishima, "Iterative refinement for symmetric eigenvalue decomposition",
+// Japan J. Indust. Appl. Math. 35 (2018), complexified.  For approximate eigenvectors X of
+// the Hermitian H_F (columns, near orthonormal):
+//     G = X^H X (r_ij = delta_ij - g_ij),  S = X^H H_F X,
+//     lam_i = s_ii / g_ii,
+//     Et_ij = (s_ij - lam_j g_ij) / (lam_j - lam_i)   for well separated pairs,
+//     Et_ij = r_ij / 2                                 on the diagonal and inside clusters,
+//     X <- X + X Et.
+// Products that decide the result (G, S) are formed FP64-accurately from FP32 pieces: every
+// FP64 value is split x = x1 + x2 (x1 = fl32(x), x2 = fl32(x - x1)); x1*y1 is taken exactly
+// (product + FMA error term), the cross terms in FP32, and the sums are accumulated in
+// double-FP32 (TwoSum, Knuth 1969).  X Et only needs FP32 (Et is small).  H_F X is applied in
+// FP64 from the coefficients, never from the FP32 matrix.
+// A pair is treated as clustered when |lam_i - lam_j| <= 20 |s_ij - lam_j g_ij| (the first-order
+// correction would exceed 0.05) or the gap is below 1e-13 |H_F|; consecutive clustered indices
+// form a cluster whose eigenvectors are separated by an FP64 Jacobi solve of the small
+// projected matrix X_C^H H_F X_C (clusters of up to RF_CMAX vectors).
 #include "mmf_internal.h"
 
+#define RF_TILE 32
+#define RF_KC 32
+#define RF_KG 16   // k-chunk of the FP64-accurate Gram kernel
+#define RF_CMAX 32
+#define RF_TAU 20.0
+
+// ------------------------------------------------------------------ HX = H_F X (FP64, sparse)
+__global__ void __launch_bounds__(256) k_apply_hf(const MmfDesc* __restrict__ descs,
+                                                  const int* __restrict__ idx,
+                                                  const double2* __restrict__ coef,
+                                                  const double2* __restrict__ Xg,
+                                                  double2* __restrict__ HXg, int col0, int ncols) {
+    const MmfDesc d = descs[idx[blockIdx.z]];
+    const int n = d.n, D = d.D;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cbeg = col0 + blockIdx.y * 16;
+    if (r >= n || cbeg >= n) return;
+    const int cend = min(min(cbeg + 16, n), col0 + ncols);
+    const int b = r / D, i = r - b * D;
+    int nv[MMF_MAX_MODES];
+    block_nvec(d, b, nv);
+    const double sh = block_ndotw(d, b);
+    const double2* H0 = coef + d.coef_off;
+    const double2* X = Xg + d.mat_off;
+    double2* HX = HXg + d.mat_off;
+    for (int c = cbeg; c < cend; ++c) {
+        const double2* x = X + (int64_t)c * d.ld;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int j = 0; j < D; ++j) acc = acc + H0[i * D + j] * x[j + D * b];
+        acc = acc - sh * x[r];
+        int64_t off = d.coef_off + (int64_t)D * D;
+        for (int l = 0; l < d.K; ++l) {
+            for (int h = 1; h <= d.nharm[l]; ++h) {
+                const double2* V = coef + off + (int64_t)(h - 1) * D * D;
+                if (nv[l] + h <= d.N[l]) {
+                    const int bu = b + h * d.S[l];
+                    for (int j = 0; j < D; ++j) acc = acc + V[i * D + j] * x[j + D * bu];
+                }
+                if (nv[l] - h >= -d.N[l]) {
+                    const int bd = b - h * d.S[l];
+                    for (int j = 0; j < D; ++j) acc = acc + cmulc(V[j * D + i], x[j + D * bd]);
+                }
+            }
+            off += (int64_t)d.nharm[l] * D * D;
+        }
+        HX[(int64_t)c * d.ld + r] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ double-FP32 helpers
+struct DF {
+    float hi, lo;
+};
+
+// acc += a * b with a = a1 + a2, b = b1 + b2 (FP32 pieces of FP64 values)
+__device__ __forceinline__ void df_mac(DF& acc, float a1, float a2, float b1, float b2) {
+    const float p = a1 * b1;
+    const float e = fmaf(a1, b1, -p);
+    const float c = fmaf(a1, b2, a2 * b1);
+    const float s = acc.hi + p;
+    const float bb = s - acc.hi;
+    const float err = (acc.hi - (s - bb)) + (p - bb);
+    acc.hi = s;
+    acc.lo += err + e + c;
+}
+__device__ __forceinline__ void df_renorm(DF& a) {
+    const float s = a.hi + a.lo;
+    a.lo = a.lo - (s - a.hi);
+    a.hi = s;
+}
+
+struct Split {  // FP32 pieces of one complex FP64 value
+    float r1, r2, i1, i2;
+};
+__device__ __forceinline__ Split split(double2 v) {
+    Split s;
+    s.r1 = __double2float_rn(v.x);
+    s.r2 = __double2float_rn(v.x - (double)s.r1);
+    s.i1 = __double2float_rn(v.y);
+    s.i2 = __double2float_rn(v.y - (double)s.i1);
+    return s;
+}
+
+// conj(a) * b accumulated into (re, im)
+__device__ __forceinline__ void df_cmacc(DF& re, DF& im, const Split& a, const Split& b) {
+    df_mac(re, a.r1, a.r2, b.r1, b.r2);
+    df_mac(re, a.i1, a.i2, b.i1, b.i2);
+    df_mac(im, a.r1, a.r2, b.i1, b.i2);
+    df_mac(im, -a.i1, -a.i2, b.r1, b.r2);
+}
+
+// ------------------------------------------------------------------ G = X^H X, S = X^H HX
+// Upper-triangle tiles (I <= J) of 32 x 32; both triangles are written.
+__global__ void __launch_bounds__(256) k_gram_df32(const MmfDesc* __restrict__ descs,
+                                                   const int* __restrict__ idx,
+                                                   const double2* __restrict__ Xg,
+                                                   const double2* __restrict__ HXg,
+                                                   double2* __restrict__ Gg,
+                                                   double2* __restrict__ Sg) {
+    __shared__ Split xi[RF_KG][RF_TILE + 1];
+    __shared__ Split xj[RF_KG][RF_TILE + 1];
+    __shared__ Split hj[RF_KG][RF_TILE + 1];
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n;
+    const int T = (n + RF_TILE - 1) / RF_TILE;
+    // tile index -> (I, J), I <= J
+    int t = blockIdx.x, I = 0;
+    if (t >= T * (T + 1) / 2) return;
+    while (t >= T - I) { t -= T - I; ++I; }
+    const int J = I + t;
+    const int i0 = I * RF_TILE, j0 = J * RF_TILE;
+    const double2* X = Xg + d.mat_off;
+    const double2* HX = HXg + d.mat_off;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // outputs (ty + 16a, tx + 16b)
+    DF gr[2][2], gi[2][2], sr[2][2], si[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            gr[a][b] = gi[a][b] = sr[a][b] = si[a][b] = DF{0.f, 0.f};
+        }
+    for (int k0 = 0; k0 < n; k0 += RF_KG) {
+        for (int e = threadIdx.x; e < RF_KG * RF_TILE; e += 256) {
+            const int c = e / RF_KG, kk = e - c * RF_KG;
+            const int k = k0 + kk;
+            const double2 z = make_double2(0.0, 0.0);
+            xi[kk][c] = split((k < n && i0 + c < n) ? X[(int64_t)(i0 + c) * d.ld + k] : z);
+            xj[kk][c] = split((k < n && j0 + c < n) ? X[(int64_t)(j0 + c) * d.ld + k] : z);
+            hj[kk][c] = split((k < n && j0 + c < n) ? HX[(int64_t)(j0 + c) * d.ld + k] : z);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < RF_KG; ++kk) {
+            const Split a0 = xi[kk][ty], a1 = xi[kk][ty + 16];
+            const Split b0 = xj[kk][tx], b1 = xj[kk][tx + 16];
+            const Split h0 = hj[kk][tx], h1 = hj[kk][tx + 16];
+            df_cmacc(gr[0][0], gi[0][0], a0, b0);
+            df_cmacc(gr[0][1], gi[0][1], a0, b1);
+            df_cmacc(gr[1][0], gi[1][0], a1, b0);
+            df_cmacc(gr[1][1], gi[1][1], a1, b1);
+            df_cmacc(sr[0][0], si[0][0], a0, h0);
+            df_cmacc(sr[0][1], si[0][1], a0, h1);
+            df_cmacc(sr[1][0], si[1][0], a1, h0);
+            df_cmacc(sr[1][1], si[1][1], a1, h1);
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                df_renorm(gr[a][b]); df_renorm(gi[a][b]); df_renorm(sr[a][b]); df_renorm(si[a][b]);
+            }
+        __syncthreads();
+    }
+    double2* G = Gg + d.mat_off;
+    double2* S = Sg + d.mat_off;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
+            if (i < n && j < n && (I < J || i <= j)) {
+                double2 g = make_double2((double)gr[a][b].hi + (double)gr[a][b].lo,
+                                         (double)gi[a][b].hi + (double)gi[a][b].lo);
+                double2 s = make_double2((double)sr[a][b].hi + (double)sr[a][b].lo,
+                                         (double)si[a][b].hi + (double)si[a][b].lo);
+                if (i == j) { g.y = 0.0; s.y = 0.0; }
+                G[(int64_t)j * d.ld + i] = g;
+                S[(int64_t)j * d.ld + i] = s;
+                G[(int64_t)i * d.ld + j] = conj(g);
+                S[(int64_t)i * d.ld + j] = conj(s);
+            }
+        }
+}
+
+// ------------------------------------------------------------------ lam, clusters
+// One CTA per system: lam_i = s_ii / g_ii; link_i = pair (i, i+1) clustered; cluster id = the
+// first index of its run.  aux per system: cid (n ints) stored in the E2 buffer's tail.
+__global__ void __launch_bounds__(256) k_oa_lambda(const MmfDesc* __restrict__ descs,
+                                                   const int* __restrict__ idx,
+                                                   const double2* __restrict__ Gg,
+                                                   const double2* __restrict__ Sg,
+                                                   double* __restrict__ lamg,
+                                                   int* __restrict__ cidg) {
+    const MmfDesc d = descs[idx[blockIdx.x]];
+    const int n = d.n;
+    const double2* G = Gg + d.mat_off;
+    const double2* S = Sg + d.mat_off;
+    double* lam = lamg + d.vec_off;
+    int* cid = cidg + d.vec_off;
+    __shared__ double hmax;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        lam[i] = S[(int64_t)i * d.ld + i].x / G[(int64_t)i * d.ld + i].x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < n; ++i) m = fmax(m, fabs(lam[i]));
+        hmax = m;
+    }
+    __syncthreads();
+    // link flags into cid (1 = linked to the next)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int link = 0;
+        if (i + 1 < n) {
+            const double gap = fabs(lam[i + 1] - lam[i]);
+            const double2 s = S[(int64_t)(i + 1) * d.ld + i], g = G[(int64_t)(i + 1) * d.ld + i];
+            const double2 num = s - lam[i + 1] * g;
+            link = (gap <= RF_TAU * sqrt(abs2(num))) || (gap <= 1e-13 * hmax);
+        }
+        cid[i] = link;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int start = 0, prev = 0;
+        for (int i = 0; i < n; ++i) {
+            const int link = cid[i];
+            if (i == 0 || !prev) start = i;
+            cid[i] = start;
+            prev = link;
+        }
+    }
+}
+
+// Et in place of G (diagonal and clustered pairs: r/2; others: OA formula)
+__global__ void __launch_bounds__(256) k_oa_etilde(const MmfDesc* __restrict__ descs,
+                                                   const int* __restrict__ idx,
+                                                   double2* __restrict__ Gg,
+                                                   const double2* __restrict__ Sg,
+                                                   const double* __restrict__ lamg,
+                                                   const int* __restrict__ cidg) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n;
+    const int64_t tot = (int64_t)n * n;
+    double2* G = Gg + d.mat_off;
+    const double2* S = Sg + d.mat_off;
+    const double* lam = lamg + d.vec_off;
+    const int* cid = cidg + d.vec_off;
+    double hmax = fmax(fabs(lam[0]), fabs(lam[n - 1]));
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / n), i = (int)(e - (int64_t)j * n);
+        const int64_t o = (int64_t)j * d.ld + i;
+        const double2 g = G[o];
+        double2 et;
+        if (i == j) {
+            et = make_double2(0.5 * (1.0 - g.x), 0.0);
+        } else {
+            const double2 num = S[o] - lam[j] * g;
+            const double gap = lam[j] - lam[i];
+            const bool clustered = cid[i] == cid[j] || fabs(gap) <= RF_TAU * sqrt(abs2(num)) ||
+                                   fabs(gap) <= 1e-13 * fmax(hmax, fabs(lam[i]));
+            et = clustered ? (-0.5) * g : (1.0 / gap) * num;
+        }
+        G[o] = et;
+    }
+}
+
+// ------------------------------------------------------------------ Xn = X + X Et (FP32 GEMM)
+__global__ void __launch_bounds__(256) k_xe_update(const MmfDesc* __restrict__ descs,
+                                                   const int* __restrict__ idx,
+                                                   const double2* __restrict__ Xg,
+                                                   const double2* __restrict__ Etg,
+                                                   double2* __restrict__ Xn) {
+    __shared__ float2 xs[RF_KC][64 + 1];
+    __shared__ float2 es[RF_KC][64 + 1];
+    const MmfDesc d = descs[idx[blockIdx.z]];
+    const int n = d.n;
+    const int r0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
+    if (r0 >= n || c0 >= n) return;
+    const double2* X = Xg + d.mat_off;
+    const double2* Et = Etg + d.mat_off;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // rows tx + 16a, cols ty + 16b
+    float2 acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < n; k0 += RF_KC) {
+        for (int e = threadIdx.x; e < RF_KC * 64; e += 256) {
+            // X tile: rows r0..r0+63, cols k0..k0+31 (coalesced over rows)
+            const int kk = e / 64, rr = e - kk * 64;
+            const int r = r0 + rr, k = k0 + kk;
+            double2 v = (r < n && k < n) ? X[(int64_t)k * d.ld + r] : make_double2(0.0, 0.0);
+            xs[kk][rr] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+            // Et tile: rows k0..k0+31, cols c0..c0+63 (coalesced over k)
+            const int cc = e / RF_KC, k2 = e - cc * RF_KC;
+            const int c = c0 + cc, kr = k0 + k2;
+            double2 w = (c < n && kr < n) ? Et[(int64_t)c * d.ld + kr] : make_double2(0.0, 0.0);
+            es[k2][cc] = make_float2(__double2float_rn(w.x), __double2float_rn(w.y));
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < RF_KC; ++kk) {
+            float2 xa[4], eb[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) xa[a] = xs[kk][tx + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) eb[b] = es[kk][ty + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    acc[a][b].x = fmaf(xa[a].x, eb[b].x, fmaf(-xa[a].y, eb[b].y, acc[a][b].x));
+                    acc[a][b].y = fmaf(xa[a].x, eb[b].y, fmaf(xa[a].y, eb[b].x, acc[a][b].y));
+                }
+        }
+        __syncthreads();
+    }
+    double2* O = Xn + d.mat_off;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int r = r0 + tx + 16 * a, c = c0 + ty + 16 * b;
+            if (r < n && c < n) {
+                const int64_t o = (int64_t)c * d.ld + r;
+                const double2 x = X[o];
+                O[o] = make_double2(x.x + (double)acc[a][b].x, x.y + (double)acc[a][b].y);
+            }
+        }
+}
+
+// ------------------------------------------------------------------ cluster separation
+// One CTA per system; clusters handled one after another.  For cluster C (m vectors):
+// B = X_C^H H_F X_C in FP64 (H_F X_C from the HX buffer, recomputed for the new X), cyclic
+// Jacobi on B, X_C <- X_C W, lam_C <- eigenvalues of B ascending.
+__device__ void small_jacobi(double2* B, double2* W, int m, double* w) {
+    // single-thread cyclic complex Jacobi on m x m (column-major, ld = RF_CMAX)
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) W[i + j * RF_CMAX] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        double off = 0.0, fro = 0.0;
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i < m; ++i) {
+                double a = abs2(B[i + j * RF_CMAX]);
+                fro += a;
+                if (i != j) off += a;
+            }
+        if (off <= 1e-32 * fro || off == 0.0) break;
+        for (int p = 0; p < m - 1; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                const double2 apq = B[p + q * RF_CMAX];
+                const double r = sqrt(abs2(apq));
+                if (r == 0.0) continue;
+                const double app = B[p + p * RF_CMAX].x, aqq = B[q + q * RF_CMAX].x;
+                const double2 em = make_double2(apq.x / r, -apq.y / r);  // e^{-i phi}
+                const double th = (aqq - app) / (2.0 * r);
+                const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                for (int k = 0; k < m; ++k) {  // columns
+                    const double2 bp = B[k + p * RF_CMAX], bq = B[k + q * RF_CMAX] * em;
+                    B[k + p * RF_CMAX] = c * bp - s * bq;
+                    B[k + q * RF_CMAX] = s * bp + c * bq;
+                    const double2 wp = W[k + p * RF_CMAX], wq = W[k + q * RF_CMAX] * em;
+                    W[k + p * RF_CMAX] = c * wp - s * wq;
+                    W[k + q * RF_CMAX] = s * wp + c * wq;
+                }
+                const double2 ep = conj(em);
+                for (int k = 0; k < m; ++k) {  // rows
+                    const double2 bp = B[p + k * RF_CMAX], bq = ep * B[q + k * RF_CMAX];
+                    B[p + k * RF_CMAX] = c * bp - s * bq;
+                    B[q + k * RF_CMAX] = s * bp + c * bq;
+                }
+                B[p + q * RF_CMAX] = B[q + p * RF_CMAX] = make_double2(0.0, 0.0);
+                B[p + p * RF_CMAX].y = B[q + q * RF_CMAX].y = 0.0;
+            }
+    }
+    for (int i = 0; i < m; ++i) w[i] = B[i + i * RF_CMAX].x;
+}
+
+__global__ void __launch_bounds__(256) k_cluster_sep(const MmfDesc* __restrict__ descs,
+                                                     const int* __restrict__ idx,
+                                                     const double2* __restrict__ coef,
+                                                     double2* __restrict__ Xg,
+                                                     double2* __restrict__ HXg,
+                                                     double* __restrict__ lamg,
+                                                     const int* __restrict__ cidg,
+                                                     int* __restrict__ status) {
+    __shared__ double2 B[RF_CMAX * RF_CMAX];
+    __shared__ double2 W[RF_CMAX * RF_CMAX];
+    __shared__ double w[RF_CMAX];
+    __shared__ int perm[RF_CMAX];
+    const int sid = idx[blockIdx.x];
+    const MmfDesc d = descs[sid];
+    const int n = d.n, D = d.D;
+    double2* X = Xg + d.mat_off;
+    double2* HX = HXg + d.mat_off;
+    double* lam = lamg + d.vec_off;
+    const int* cid = cidg + d.vec_off;
+    const double2* H0 = coef + d.coef_off;
+    int c0 = 0;
+    while (c0 < n) {
+        int c1 = c0 + 1;
+        while (c1 < n && cid[c1] == c0) ++c1;
+        const int m = c1 - c0;
+        if (m >= 2 && m <= RF_CMAX) {
+            // HX_C = H_F X_C (FP64)
+            for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
+                const int cc = e / n, r = e - cc * n;
+                const int c = c0 + cc;
+                const int b = r / D, i = r - b * D;
+                int nv[MMF_MAX_MODES];
+                block_nvec(d, b, nv);
+                const double2* x = X + (int64_t)c * d.ld;
+                double2 acc = make_double2(0.0, 0.0);
+                for (int j = 0; j < D; ++j) acc = acc + H0[i * D + j] * x[j + D * b];
+                acc = acc - block_ndotw(d, b) * x[r];
+                int64_t off = d.coef_off + (int64_t)D * D;
+                for (int l = 0; l < d.K; ++l) {
+                    for (int h = 1; h <= d.nharm[l]; ++h) {
+                        const double2* V = coef + off + (int64_t)(h - 1) * D * D;
+                        if (nv[l] + h <= d.N[l])
+                            for (int j = 0; j < D; ++j) acc = acc + V[i * D + j] * x[j + D * (b + h * d.S[l])];
+                        if (nv[l] - h >= -d.N[l])
+                            for (int j = 0; j < D; ++j) acc = acc + cmulc(V[j * D + i], x[j + D * (b - h * d.S[l])]);
+                    }
+                    off += (int64_t)d.nharm[l] * D * D;
+                }
+                HX[(int64_t)c * d.ld + r] = acc;
+            }
+            __syncthreads();
+            // B = X_C^H HX_C, one warp per entry
+            for (int e = threadIdx.x >> 5; e < m * m; e += blockDim.x >> 5) {
+                const int p = e % m, q = e / m;
+                const double2* xp = X + (int64_t)(c0 + p) * d.ld;
+                const double2* hq = HX + (int64_t)(c0 + q) * d.ld;
+                double2 acc = make_double2(0.0, 0.0);
+                for (int r = threadIdx.x & 31; r < n; r += 32) acc = acc + cmulc(xp[r], hq[r]);
+                acc.x = warp_sum(acc.x);
+                acc.y = warp_sum(acc.y);
+                if ((threadIdx.x & 31) == 0) B[p + q * RF_CMAX] = acc;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int p = 0; p < m; ++p)  // Hermitian part
+                    for (int q = p; q < m; ++q) {
+                        double2 a = B[p + q * RF_CMAX], b = B[q + p * RF_CMAX];
+                        double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+                        B[p + q * RF_CMAX] = h;
+                        B[q + p * RF_CMAX] = conj(h);
+                        if (p == q) B[p + p * RF_CMAX].y = 0.0;
+                    }
+                small_jacobi(B, W, m, w);
+                for (int a = 0; a < m; ++a) perm[a] = a;
+                for (int a = 1; a < m; ++a) {
+                    int v = perm[a], b = a - 1;
+                    while (b >= 0 && w[perm[b]] > w[v]) { perm[b + 1] = perm[b]; --b; }
+                    perm[b + 1] = v;
+                }
+            }
+            __syncthreads();
+            // X_C <- X_C W (columns in ascending eigenvalue order); rows independent
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {
+                double2 row[RF_CMAX];
+                for (int a = 0; a < m; ++a) row[a] = X[(int64_t)(c0 + a) * d.ld + r];
+                for (int a = 0; a < m; ++a) {
+                    double2 acc = make_double2(0.0, 0.0);
+                    const int pa = perm[a];
+                    for (int q = 0; q < m; ++q) acc = acc + row[q] * W[q + pa * RF_CMAX];
+                    X[(int64_t)(c0 + a) * d.ld + r] = acc;
+                }
+            }
+            for (int a = threadIdx.x; a < m; a += blockDim.x) lam[c0 + a] = w[perm[a]];
+            __syncthreads();
+        } else if (m > RF_CMAX) {
+            if (threadIdx.x == 0) status[sid] = MMF_ST_NOCONV;
+        }
+        c0 = c1;
+    }
+}
+
+// ------------------------------------------------------------------ final order
+// E ascending (ties by index) with the matching permutation of X's columns (into Xo).
+__global__ void __launch_bounds__(256) k_sort_pairs(const MmfDesc* __restrict__ descs,
+                                                    const int* __restrict__ idx,
+                                                    const double* __restrict__ lamg,
+                                                    const double2* __restrict__ Xg,
+                                                    double* __restrict__ Eg,
+                                                    double2* __restrict__ Xo) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n;
+    const int l = blockIdx.x;
+    if (l >= n) return;
+    const double* lam = lamg + d.vec_off;
+    __shared__ int rank_s;
+    if (threadIdx.x == 0) rank_s = 0;
+    __syncthreads();
+    const double v = lam[l];
+    int cnt = 0;
+    for (int m = threadIdx.x; m < n; m += blockDim.x) cnt += (lam[m] < v) || (lam[m] == v && m < l);
+    cnt = warp_sum(cnt);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&rank_s, cnt);
+    __syncthreads();
+    const int rk = rank_s;
+    if (threadIdx.x == 0) Eg[d.vec_off + rk] = v;
+    const double2* src = Xg + d.mat_off + (int64_t)l * d.ld;
+    double2* dst = Xo + d.mat_off + (int64_t)rk * d.ld;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) dst[r] = src[r];
+}
+
 cudaError_t mmf_launch_refine(const MmfLaunch& L, const double2* coef, double2* X, double* E,
-                              double2* R, double2* S, double2* HX, double* E2, int iters,
-                              int* status) {
-    (void)L; (void)coef; (void)X; (void)E; (void)R; (void)S; (void)HX; (void)E2; (void)iters;
-    (void)status;
-    return cudaErrorNotSupported;
+                              double2* G, double2* S, double2* HX, double* lam, int iters,
+                              int* status, int* cid, int64_t mat_elems) {
+    if (L.count <= 0) return cudaSuccess;
+    const int T = (L.nmax + RF_TILE - 1) / RF_TILE;
+    const int tiles = T * (T + 1) / 2;
+    for (int it = 0; it < iters; ++it) {
+        k_apply_hf<<<dim3((L.nmax + 255) / 256, (L.nmax + 15) / 16, L.count), 256, 0, L.stream>>>(
+            L.desc, L.idx, coef, X, HX, 0, L.nmax);
+        k_gram_df32<<<dim3(tiles, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, HX, G, S);
+        k_oa_lambda<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
+        k_oa_etilde<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
+        k_xe_update<<<dim3((L.nmax + 63) / 64, (L.nmax + 63) / 64, L.count), 256, 0, L.stream>>>(
+            L.desc, L.idx, X, G, S);
+        cudaError_t e = cudaMemcpyAsync(X, S, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
+        if (e != cudaSuccess) return e;
+        k_cluster_sep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, coef, X, HX, lam, cid, status);
+    }
+    k_sort_pairs<<<dim3(L.nmax, L.count), 256, 0, L.stream>>>(L.desc, L.idx, lam, X, E, S);
+    cudaError_t e = cudaMemcpyAsync(X, S, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
 }

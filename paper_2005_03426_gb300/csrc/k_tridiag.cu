@@ -1,9 +1,9 @@
 // k_tridiag.cu -- S4: eigenpairs of the real symmetric tridiagonal T = tridiag(e, d, e), FP64.
 //
 // Eigenvalues by Sturm-sequence bisection (Givens 1954; Barth, Martin & Wilkinson 1967):
-// count(x) = #{i : q_i < 0}, q_0 = d_0 - x, q_i = d_i - x - e_{i-1}^2 / q_{i-1}, with tiny
-// pivots replaced by -pivmin.  One thread per eigenvalue, each bracketing its own index
-// inside the Gershgorin interval until the bracket is below 2 eps max(|lo|, |hi|).
+// count(x) = number of sign changes of the leading principal minors of T - x I (a division-
+// free three-term recurrence).  One thread per eigenvalue, each bracketing its own index
+// inside the Gershgorin interval until the bracket is below max(2 eps max(|lo|,|hi|), eps |T|).
 //
 // Eigenvectors by inverse iteration (Wilkinson 1965): (T - lambda I) y = b solved by
 // Gaussian elimination with partial pivoting on the tridiagonal band, three iterations from
@@ -21,7 +21,7 @@ __device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : 
 // per system: gl, gu, pivmin, tnorm
 __global__ void k_tri_prep(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                            const double* __restrict__ dvec, const double* __restrict__ evec,
-                           double* __restrict__ aux) {
+                           double* __restrict__ aux, double* __restrict__ e2vec) {
     __shared__ double red[4][32];
     const int sid = idx[blockIdx.x];
     const MmfDesc d = descs[sid];
@@ -34,7 +34,10 @@ __global__ void k_tri_prep(const MmfDesc* __restrict__ descs, const int* __restr
         gl = fmin(gl, dd[i] - el - er);
         gu = fmax(gu, dd[i] + el + er);
         tn = fmax(tn, fabs(dd[i]) + el + er);
-        if (i < n - 1) e2max = fmax(e2max, ee[i] * ee[i]);
+        if (i < n - 1) {
+            e2max = fmax(e2max, ee[i] * ee[i]);
+            e2vec[d.vec_off + i] = ee[i] * ee[i];
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         gl = fmin(gl, __shfl_xor_sync(0xffffffffu, gl, o));
@@ -59,18 +62,31 @@ __global__ void k_tri_prep(const MmfDesc* __restrict__ descs, const int* __restr
     }
 }
 
+// Sturm count by the three-term recurrence of the leading principal minors,
+//   p_0 = 1, p_1 = d_0 - x, p_{i+1} = (d_i - x) p_i - e_{i-1}^2 p_{i-1},
+// counting sign changes (= eigenvalues below x); an exact zero takes the sign opposite to its
+// predecessor (a negative pivot, as in the ratio form).  Every 16 steps the pair (p_i, p_{i-1})
+// is rescaled by the power of two that brings the larger of the two below 1, which changes no
+// sign and keeps 16 further steps far from overflow.
 __device__ __forceinline__ int sturm_count(const double* __restrict__ dd,
-                                           const double* __restrict__ ee, int n, double x,
-                                           double pivmin) {
+                                           const double* __restrict__ e2, int n, double x) {
     int cnt = 0;
-    double q = dd[0] - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += (q < 0.0);
+    double pm = 1.0, p = dd[0] - x;
+    if (p == 0.0) p = -1e-300;
+    cnt += (p < 0.0);
     for (int i = 1; i < n; ++i) {
-        double e = ee[i - 1];
-        q = (dd[i] - x) - (e * e) / q;
-        if (fabs(q) < pivmin) q = -pivmin;
-        cnt += (q < 0.0);
+        double pn = fma(dd[i] - x, p, -e2[i - 1] * pm);
+        if (pn == 0.0) pn = (p < 0.0) ? 1e-300 : -1e-300;
+        cnt += ((pn < 0.0) != (p < 0.0));
+        pm = p;
+        p = pn;
+        if ((i & 15) == 0) {
+            int ex;
+            frexp(fmax(fabs(p), fabs(pm)), &ex);
+            const double sc = ldexp(1.0, -ex);
+            p *= sc;
+            pm *= sc;
+        }
     }
     return cnt;
 }
@@ -78,7 +94,7 @@ __device__ __forceinline__ int sturm_count(const double* __restrict__ dd,
 __global__ void __launch_bounds__(128) k_bisect(const MmfDesc* __restrict__ descs,
                                                 const int* __restrict__ idx,
                                                 const double* __restrict__ dvec,
-                                                const double* __restrict__ evec,
+                                                const double* __restrict__ e2vec,
                                                 const double* __restrict__ aux,
                                                 double* __restrict__ Eout,
                                                 int* __restrict__ status) {
@@ -88,7 +104,7 @@ __global__ void __launch_bounds__(128) k_bisect(const MmfDesc* __restrict__ desc
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const double* dd = dvec + d.vec_off;
-    const double* ee = evec + d.vec_off;
+    const double* e2 = e2vec + d.vec_off;
     double lo = aux[8 * sid], hi = aux[8 * sid + 1];
     const double pivmin = aux[8 * sid + 2];
     const double tn = aux[8 * sid + 3];
@@ -99,7 +115,7 @@ __global__ void __launch_bounds__(128) k_bisect(const MmfDesc* __restrict__ desc
         if (hi - lo <= tol) break;
         double mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
-        if (sturm_count(dd, ee, n, mid, pivmin) <= k) lo = mid;
+        if (sturm_count(dd, e2, n, mid) <= k) lo = mid;
         else hi = mid;
     }
     Eout[d.vec_off + k] = 0.5 * (lo + hi);
@@ -218,11 +234,12 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
 }
 
 cudaError_t mmf_launch_tridiag_eig(const MmfLaunch& L, const double* dvec, const double* evec,
-                                   double* aux, double* E, double* Y, double* work, int* status) {
+                                   double* aux, double* e2, double* E, double* Y, double* work,
+                                   int* status) {
     if (L.count <= 0) return cudaSuccess;
-    k_tri_prep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux);
+    k_tri_prep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux, e2);
     dim3 g((L.nmax + 127) / 128, L.count);
-    k_bisect<<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux, E, status);
+    k_bisect<<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, e2, aux, E, status);
     k_inviter<<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux, E, Y, work);
     return cudaGetLastError();
 }

@@ -18,8 +18,6 @@
 #include "../../include/mmf.h"
 #include "mmf_internal.h"
 
-cudaError_t mmf_launch_tridiag_eig(const MmfLaunch& L, const double* dvec, const double* evec,
-                                   double* aux, double* E, double* Y, double* work, int* status);
 
 static thread_local std::string g_last_error;
 static thread_local int g_launches = 0;
@@ -82,7 +80,7 @@ struct mmf_batch {
     void* d_H = nullptr;
     double2* d_Zf = nullptr;
     void* d_Zp = nullptr;
-    double *d_E = nullptr, *d_d = nullptr, *d_e = nullptr, *d_aux = nullptr;
+    double *d_E = nullptr, *d_d = nullptr, *d_e = nullptr, *d_e2 = nullptr, *d_aux = nullptr;
     void* d_tau = nullptr;
     double *d_Y = nullptr, *d_work = nullptr;
     void *d_Vp = nullptr, *d_Wp = nullptr;
@@ -91,6 +89,7 @@ struct mmf_batch {
     double* d_P = nullptr;
     double2 *d_R = nullptr, *d_S = nullptr, *d_HX = nullptr;
     double* d_E2 = nullptr;
+    int* d_cid = nullptr;
     // host staging (pinned)
     double2* h_coef = nullptr;
     double* h_t = nullptr;
@@ -367,7 +366,8 @@ extern "C" int mmf_batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems
     size_t o_Zf = p.take(sizeof(double2) * b->n_mat);
     size_t o_Zp = fp32 ? p.take(cs * b->n_mat) : 0;
     size_t o_E = p.take(sizeof(double) * b->n_vec), o_d = p.take(sizeof(double) * b->n_vec),
-           o_e = p.take(sizeof(double) * b->n_vec), o_aux = p.take(sizeof(double) * 8 * count);
+           o_e = p.take(sizeof(double) * b->n_vec), o_e2 = p.take(sizeof(double) * b->n_vec),
+           o_aux = p.take(sizeof(double) * 8 * count);
     size_t o_tau = p.take(cs * b->n_vec);
     size_t o_Y = p.take(sizeof(double) * b->n_sq), o_work = p.take(sizeof(double) * 3 * b->n_sq);
     size_t o_Vp = p.take(cs * b->n_pan), o_Wp = p.take(cs * b->n_pan);
@@ -375,12 +375,13 @@ extern "C" int mmf_batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems
     size_t o_F = p.take(sizeof(double2) * std::max<int64_t>(b->n_f, 1));
     size_t o_U = p.take(sizeof(double2) * std::max<int64_t>(b->n_u, 1));
     size_t o_P = p.take(sizeof(double) * b->n_p);
-    size_t o_R = 0, o_S = 0, o_HX = 0, o_E2 = 0;
+    size_t o_R = 0, o_S = 0, o_HX = 0, o_E2 = 0, o_cid = 0;
     if (fp32) {
         o_R = p.take(sizeof(double2) * b->n_mat);
         o_S = p.take(sizeof(double2) * b->n_mat);
         o_HX = p.take(sizeof(double2) * b->n_mat);
         o_E2 = p.take(sizeof(double) * b->n_vec);
+        o_cid = p.take(sizeof(int) * b->n_vec);
     }
     b->bytes = p.off;
     if (ctx->used + b->bytes > ctx->budget) {
@@ -408,6 +409,7 @@ extern "C" int mmf_batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems
     b->d_E = (double*)(B + o_E);
     b->d_d = (double*)(B + o_d);
     b->d_e = (double*)(B + o_e);
+    b->d_e2 = (double*)(B + o_e2);
     b->d_aux = (double*)(B + o_aux);
     b->d_tau = B + o_tau;
     b->d_Y = (double*)(B + o_Y);
@@ -423,6 +425,7 @@ extern "C" int mmf_batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems
         b->d_S = (double2*)(B + o_S);
         b->d_HX = (double2*)(B + o_HX);
         b->d_E2 = (double*)(B + o_E2);
+        b->d_cid = (int*)(B + o_cid);
     }
     e = cudaMallocHost((void**)&b->h_coef, sizeof(double2) * std::max<int64_t>(b->n_coef, 1));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_t, sizeof(double) * std::max<int64_t>(b->n_t, 1));
@@ -570,7 +573,8 @@ static int stage_eig(mmf_batch* b) {
         mark(b, ST_HETRD);
         LAUNCH(mmf_launch_hetrd(Ll, b->d_H, b->d_Vp, b->d_Wp, b->d_d, b->d_e, b->d_tau, fp32), 1);
         mark(b, ST_TRIDIAG);
-        LAUNCH(mmf_launch_tridiag_eig(Ll, b->d_d, b->d_e, b->d_aux, b->d_E, b->d_Y, b->d_work, b->d_status), 3);
+        LAUNCH(mmf_launch_tridiag_eig(Ll, b->d_d, b->d_e, b->d_aux, b->d_e2, b->d_E, b->d_Y, b->d_work,
+                                      b->d_status), 3);
         mark(b, ST_BACKTRANSFORM);
         LAUNCH(mmf_launch_backtransform(Ll, b->d_H, b->d_tau, b->d_Vp, b->d_Y, b->d_Zp, fp32), 2);
         if (fp32) LAUNCH(mmf_launch_widen(Ll, b->d_Zp, b->d_Zf, fp32), 1);
@@ -582,12 +586,10 @@ static int stage_eig(mmf_batch* b) {
     mark(b, ST_REFINE);
     if (fp32) {
         MmfLaunch La = launch_of(b, b->all, b->d_all, b->nmax_all);
-        int nk = 0;
         cudaError_t e = mmf_launch_refine(La, b->d_coef, b->d_Zf, b->d_E, b->d_R, b->d_S, b->d_HX,
-                                          b->d_E2, 2, b->d_status);
+                                          b->d_E2, MMF_REFINE_ITERS, b->d_status, b->d_cid, b->n_mat);
         if (e != cudaSuccess) return fail(MMF_ERR_CUDA, std::string("refine: ") + cudaGetErrorString(e));
-        nk = 2 * 5 + 1;
-        g_launches += nk;
+        g_launches += 6 * MMF_REFINE_ITERS + 1;
     }
     b->last_stage = 2;
     return MMF_OK;

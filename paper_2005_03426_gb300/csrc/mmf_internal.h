@@ -116,7 +116,8 @@ cudaError_t mmf_launch_jacobi(const MmfLaunch& L, void* H, void* Zw, double* E, 
 cudaError_t mmf_launch_hetrd(const MmfLaunch& L, void* H, void* Vp, void* Wp, double* dvec,
                              double* evec, void* tau, int fp32);
 cudaError_t mmf_launch_tridiag_eig(const MmfLaunch& L, const double* dvec, const double* evec,
-                                   double* aux, double* E, double* Y, double* work, int* status);
+                                   double* aux, double* e2, double* E, double* Y, double* work,
+                                   int* status);
 cudaError_t mmf_launch_backtransform(const MmfLaunch& L, const void* H, const void* tau,
                                      void* Tf, const double* Y, void* Z, int fp32);
 cudaError_t mmf_launch_widen(const MmfLaunch& L, const void* Zp, double2* Z, int fp32);
@@ -127,8 +128,9 @@ int mmf_hetrd_max_n(int fp32);
 cudaError_t mmf_launch_micromotion(const MmfLaunch& L, int D, const double2* Z, const double* t,
                                    int nt, int64_t* reps, double2* UF);
 cudaError_t mmf_launch_refine(const MmfLaunch& L, const double2* coef, double2* X, double* E,
-                              double2* R, double2* S, double2* HX, double* E2, int iters,
-                              int* status);
+                              double2* G, double2* S, double2* HX, double* lam, int iters,
+                              int* status, int* cid, int64_t mat_elems);
+#define MMF_REFINE_ITERS 2
 
 #define MMF_NB 32          // Householder panel width and back-transform block size
 #define MMF_JACOBI_NMAX_F64 84

@@ -256,3 +256,68 @@ def test_micromotion_matches_oracle(ctx):
         ph = UF[k, j, a] / UF_o[k, j, a]
         assert abs(abs(ph) - 1.0) < 1e-10
         np.testing.assert_allclose(UF[:, :, a], ph * UF_o[:, :, a], atol=1e-10)
+
+
+# ---------------------------------------------------------------------- mixed precision path
+# FP32 reduction + FP64 tridiagonal solve + Ogita-Aishima refinement; bound: quasienergies within
+# 1e-9 ||H_F||_2, U and Pbar within 1e-8 absolute of the FP64 oracle.
+MIX_E_REL = 1e-9
+MIX_UP_ABS = 1e-8
+
+
+@pytest.mark.parametrize("case", sorted(SOLVE_CASES))
+def test_mixed_path_matches_oracle(ctx, case):
+    p = SOLVE_CASES[case]()
+    t = W.time_grid(p, 16)
+    t0 = 0.3
+    s, E, U, P = _solve_gpu(ctx, p, t, t0, precision=M.MMF_MIXED)
+    _compare(p, E, U, P, t, t0, e_rel=MIX_E_REL, up_abs=MIX_UP_ABS)
+
+
+def test_mixed_zero_coupling_degenerate(ctx):
+    for N in (5, 30):
+        D = 2
+        p = W.Problem(D=D, H0=np.diag([0.3, 0.3]).astype(complex), omegas=[1.1], Ns=[N],
+                      couplings=[[np.zeros((D, D))]])
+        t = np.array([0.0, 0.7, 2.0])
+        s, E, U, P = _solve_gpu(ctx, p, t, 0.0, precision=M.MMF_MIXED)
+        ev = np.sort([0.3 - k * 1.1 for k in range(-N, N + 1) for _ in range(D)])
+        np.testing.assert_allclose(E, ev, atol=1e-9 * np.abs(ev).max())
+        for k, tk in enumerate(t):
+            np.testing.assert_allclose(U[k], np.exp(-0.3j * tk) * np.eye(D), atol=1e-8)
+        np.testing.assert_allclose(P, np.eye(D), atol=1e-8)
+
+
+def test_mixed_eigenpairs_residual(ctx):
+    p = SOLVE_CASES["spin1_n297"]()
+    s = M.System(ctx, p)
+    s.build(M.MMF_MIXED)
+    assert s.diagonalise() == 0
+    E, Z = s.quasienergies(), s.eigenvectors()
+    HF = O.build_hf(p)
+    nrm = np.abs(E).max()
+    assert np.all(np.diff(E) >= 0)
+    assert np.abs(HF @ Z - Z * E[None, :]).max() <= 1e-10 * nrm
+    assert np.abs(Z.conj().T @ Z - np.eye(p.n)).max() <= 1e-10
+
+
+def test_mixed_batch_alone_vs_mixed(ctx):
+    ps = [SOLVE_CASES[k]() for k in ("qubit_n82", "random_n245", "spin1_n27", "qubit_n242")]
+    nt = 8
+    ts = np.stack([W.time_grid(p, nt) for p in ps])
+    b = M.Batch(ctx, [M.System(ctx, p) for p in ps], M.MMF_MIXED, nt)
+    b.set_times(0.0, ts)
+    b.run()
+    assert (b.sync() == 0).all()
+    E, U, P = b.results()
+    for i, p in enumerate(ps):
+        e, u, pp = b.unpack(E, U, P, i)
+        solo = M.Batch(ctx, [M.System(ctx, p)], M.MMF_MIXED, nt)
+        solo.set_times(0.0, ts[i:i + 1])
+        solo.run()
+        solo.sync()
+        e1, u1, p1 = solo.get(0)
+        nrm = np.abs(e1).max()
+        assert np.abs(e - e1).max() <= 1e-9 * nrm
+        assert np.abs(u - u1).max() <= 1e-8 and np.abs(pp - p1).max() <= 1e-8
+        _compare(p, e, u, pp, ts[i], 0.0, e_rel=MIX_E_REL, up_abs=MIX_UP_ABS)
