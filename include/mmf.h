@@ -157,6 +157,25 @@ MMF_API int mmf_batch_stage_ms(mmf_batch* b, double* ms, int* runs);
 MMF_API size_t mmf_batch_bytes(const mmf_batch* b);
 MMF_API int mmf_batch_destroy(mmf_batch* b);
 
+/* ---------------------------------------------------------------- no device allocation
+ * No counterpart in the paper.  For callers that cannot allocate device memory (their HBM is
+ * owned by another allocator, or they cannot afford cudaMalloc's implicit device
+ * synchronisation): the eigenvalues and eigenvectors of one real symmetric tridiagonal matrix
+ * tridiag(e, d, e), computed by the library's tridiagonal eigensolver (bisection + inverse
+ * iteration, FP64) with all scratch taken from a fixed device array compiled into the library
+ * (about 1.6 MB on every GPU that loads it, held until the process exits) instead of allocated.
+ *   d  device, n doubles (diagonal);  e  device, n-1 doubles (off-diagonal; may be NULL if n == 1)
+ *   E  device, n doubles: eigenvalues ascending;  Y  device, n*n doubles, row-major:
+ *      Y[i*n + k] = component i of the eigenvector of E[k]
+ *   stream: a cudaStream_t (NULL = the legacy default stream); the call only enqueues work.
+ * n must be 1..MMF_NOALLOC_TRIDIAG_NMAX, otherwise MMF_ERR_UNSUPPORTED.  The first call on a
+ * device looks up the device address of the scratch array (with that device current); make that
+ * first call before any stream capture.  All calls share the scratch array: calls whose GPU work
+ * overlaps (other streams, other host threads) race on it and must be serialised by the caller. */
+#define MMF_NOALLOC_TRIDIAG_NMAX 256
+MMF_API int mmf_tridiag_eig_noalloc(const double* d, const double* e, int n, double* E, double* Y,
+                                    void* stream);
+
 /* ---------------------------------------------------------------- misc */
 MMF_API const char* mmf_strerror(int status);
 MMF_API const char* mmf_last_error(void);

@@ -27,6 +27,9 @@ static int fail(int code, const std::string& msg) {
     return code;
 }
 
+// error reporting for the library's other host translation units
+int mmf_set_error(int code, const std::string& msg) { return fail(code, msg); }
+
 #define CU(call)                                                                          \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \

@@ -82,6 +82,7 @@ _SIGS = {
     "mmf_batch_timing": (_I, [_P, _I]),
     "mmf_batch_stage_ms": (_I, [_P, _P, _P]),
     "mmf_batch_destroy": (_I, [_P]),
+    "mmf_tridiag_eig_noalloc": (_I, [_P, _P, _I, _P, _P, _P]),
     "mmf_strerror": (ctypes.c_char_p, [_I]),
     "mmf_last_error": (ctypes.c_char_p, []),
     "mmf_last_launch_count": (_I, []),
