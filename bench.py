@@ -90,18 +90,30 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def stage_flops(stage: str, n: int, nt: int) -> float:
-    """Algorithmic real flops per system for a stage (LAPACK counts for the reduction and the
-    back-transform; direct sums for U)."""
+# FP32 instruction issue peak (one FP32 op per lane per clock) and the double-FP32 scheme's cost:
+# an FP64-accurate complex multiply-add takes 4 real products x 13 FP32 instructions (exact
+# product + FMA error term + cross terms + TwoSum) for 8 FP64-equivalent flops.
+FP32_INSTR_PEAK = 152 * 128 * 2.07e9
+DF32_INSTR_PER_FLOP = 52.0 / 8.0
+
+
+def stage_model(stage: str, n: int, nt: int, mixed: bool):
+    """(algorithmic real flops per system, peak flop/s, peak description) of a stage's main kernel.
+    LAPACK counts for the reduction (16/3 n^3) and the back-transform (8 n^3); the Gram products
+    X^H X and X^H H X (Hermitian halves) are n^3 complex multiply-adds = 8 n^3 FP64-equivalent flops;
+    U is 8 nt n^2 (the Phi contraction)."""
     if stage == "hetrd":
-        return 16.0 / 3.0 * n ** 3
+        return 16.0 / 3.0 * n ** 3, (FP32_ALU_PEAK if mixed else FP64_ALU_PEAK), \
+            ("FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz" if mixed else "FP64: nominal 1.25 TFLOP/s")
     if stage == "backtransform":
-        return 8.0 * n ** 3
-    if stage == "refine":
-        return 8.0 * n ** 3 + 8.0 * n ** 3  # R and S (Hermitian halves) + X E
+        return 8.0 * n ** 3, (FP32_ALU_PEAK if mixed else FP64_ALU_PEAK), \
+            ("FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz" if mixed else "FP64: nominal 1.25 TFLOP/s")
+    if stage == "refine_gram":
+        return 8.0 * n ** 3, FP32_INSTR_PEAK / DF32_INSTR_PER_FLOP, \
+            "FP64-accurate double-FP32: FP32 issue peak 152 x 128 x 2.07 GHz / 6.5 instructions per flop"
     if stage == "outputs":
-        return 8.0 * nt * n * n
-    return 0.0
+        return 8.0 * nt * n * n, FP64_ALU_PEAK, "FP64: nominal 1.25 TFLOP/s"
+    return None
 
 
 def cpu_baseline_oracle(problems, budget_s: float = 25.0):
@@ -140,6 +152,43 @@ def cpu_baseline_oracle(problems, budget_s: float = 25.0):
                        f"and Pbar; single thread; full solve estimated at {total:.0f}s")}
 
 
+def run_serving(M, W, ctx, precision, rate_fracs, n_requests, slots=4, max_batch=16, seed=40):
+    """Poisson request streams through the continuous-batching server.  Saturation throughput is
+    measured first with a burst; each rate is a fraction of it.  Latency = submit -> results on host."""
+    problems = W.serving_stream(n_requests, seed=seed)
+    systems = [M.System(ctx, p) for p in problems]
+    times = [W.time_grid(p, NT) for p in problems]
+    srv = M.Server(ctx, slots=slots, max_batch=max_batch, precision=precision)
+    # saturation: everything at once
+    burst = min(len(problems), 96)
+    t0 = time.perf_counter()
+    tk = [srv.submit(systems[i], times[i]) for i in range(burst)]
+    for k in tk:
+        srv.wait(k)
+    sat = burst / (time.perf_counter() - t0)
+    out = {"saturation_solves_per_s": sat, "rates": []}
+    for r, frac in enumerate(rate_fracs):
+        srv.reset_stats()
+        rate = frac * sat
+        arr = W.poisson_arrivals(len(problems), rate, seed + 1 + r)
+        tickets = []
+        start = time.perf_counter()
+        for i, ta in enumerate(arr):
+            now = time.perf_counter() - start
+            if ta > now:
+                time.sleep(ta - now)
+            tickets.append(srv.submit(systems[i], times[i]))
+        for k in tickets:
+            srv.wait(k)
+        wall = time.perf_counter() - start
+        st = srv.stats()
+        out["rates"].append({"rate_frac": frac, "offered_per_s": rate, "requests": len(tickets),
+                             "solves_per_s": len(tickets) / wall, "p50_ms": st["p50_ms"],
+                             "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"]})
+    srv.close()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -169,9 +218,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--serve", action="store_true", help="only the serving rate sweep")
+    ap.add_argument("--serve-requests", type=int, default=240)
+    ap.add_argument("--count", type=int, default=COUNT,
+                    help="systems per step (64 = the benchmark workload; smaller for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -198,7 +251,19 @@ def main():
             dist.barrier()
 
     prec = M.MMF_MIXED if args.precision == "mixed" else M.MMF_FP64
-    problems = W.spin1_amplitude_set(COUNT, seed=1 + rank)
+    if args.serve:
+        ctx = M.Context(local, stream=stream.cuda_stream)
+        res = run_serving(M, W, ctx, prec, [0.1, 0.25, 0.5, 0.75, 0.9], args.serve_requests)
+        if rank == 0:
+            for rr in res["rates"]:
+                print(json.dumps({"metric": "serving_latency_p50_ms", "value": rr["p50_ms"], "unit": "ms",
+                                  "higher_is_better": False, "p99_ms": rr["p99_ms"], "n_gpus": world,
+                                  "precision": args.precision, "data": "synthetic",
+                                  "config": {"workload": "poisson_mix_qubit_spin1_uneven_nt64",
+                                             "saturation_solves_per_s": res["saturation_solves_per_s"], **rr}}))
+        return
+    count = args.count
+    problems = W.spin1_amplitude_set(count, seed=1 + rank)
     ctx = M.Context(local, stream=stream.cuda_stream)
     systems = [M.System(ctx, p) for p in problems]
     batch = M.Batch(ctx, systems, prec, NT)
@@ -229,7 +294,7 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = COUNT * world / (ms / 1e3)
+    value = count * world / (ms / 1e3)
 
     # end to end through the public API: H2D of inputs, run, D2H of E, U, Pbar every step
     hE = torch.empty(batch.nE, dtype=torch.float64).pin_memory().numpy()
@@ -260,19 +325,25 @@ def main():
         acc = {"E_rel_to_normH": float(np.abs(e - g["E"]).max() / nrm),
                "U_abs": float(np.abs(u - g["U"]).max()), "P_abs": float(np.abs(pp - g["P"]).max())}
 
-    # roofline of the dominant stage
-    peaks = _peaks()
+    # roofline of the dominant kernel (the stage holding it is timed on the library's stream)
     per = {k: v / max(runs, 1) for k, v in stage.items()}
-    dom = max(per, key=per.get)
     n = problems[0].n
-    flops = stage_flops(dom, n, NT) * COUNT
-    fp32 = prec == M.MMF_MIXED and dom in ("hetrd", "backtransform")
-    peak = FP32_ALU_PEAK if fp32 else FP64_ALU_PEAK
-    achieved = flops / (per[dom] / 1e3) if per[dom] > 0 else 0.0
-    roof = {"kernel_stage": dom, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+    mixed = prec == M.MMF_MIXED
+    modelled = {k: v for k, v in per.items() if stage_model(k, n, NT, mixed) is not None}
+    dom = max(modelled, key=modelled.get)
+    flops_sys, peak, peak_src = stage_model(dom, n, NT, mixed)
+    achieved = flops_sys * count / (per[dom] / 1e3) if per[dom] > 0 else 0.0
+    kernel = {"hetrd": "k_hetrd", "backtransform": "k_backtransform", "refine_gram": "k_gram_df32",
+              "outputs": "k_time_evolution"}[dom]
+    roof = {"kernel": kernel, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-            "peak_source": ("FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz" if fp32
-                            else "FP64: nominal 1.25 TFLOP/s (recipe table)")}
+            "peak_source": peak_src + " (derived from unit counts and clock)"}
+
+    serving = None
+    if rank == 0 and world == 1 and args.serve_requests > 0 and count == COUNT:
+        sv = run_serving(M, W, ctx, prec, [0.75], args.serve_requests)
+        serving = {"saturation_solves_per_s": sv["saturation_solves_per_s"], **sv["rates"][0],
+                   "mix": "1/3 qubit n=82, 1/3 spin-1 n=1323, 1/3 uneven n<=2000; nt=64"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -284,14 +355,15 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if prec == M.MMF_FP64 else "f32+f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "systems_per_step": COUNT, "n": n, "nt": NT,
+                "config": {"workload": WORKLOAD if count == COUNT else f"{WORKLOAD}[:{count}]",
+                           "systems_per_step": count, "n": n, "nt": NT,
                            "precision": args.precision, "l2": "working set > L2 (no flush)",
                            "parallelism": f"replicas x{world}"},
                 "stage_ms": {k: round(v, 3) for k, v in per.items()},
                 "roofline": roof, "clocks": clk.summary(), "gpu_launches": launches,
-                "e2e": {"value": COUNT * world / e2e_s, "unit": "solves/s",
+                "e2e": {"value": count * world / e2e_s, "unit": "solves/s",
                         "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-                "accuracy_vs_oracle": acc, "status_max": int(st.max()),
+                "accuracy_vs_oracle": acc, "status_max": int(st.max()), "serving": serving,
                 "cpu_baseline": cpu}
         print(json.dumps(line))
     if world > 1:

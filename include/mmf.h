@@ -57,6 +57,7 @@ extern "C" {
 typedef struct mmf_ctx mmf_ctx;
 typedef struct mmf_sys mmf_sys;
 typedef struct mmf_batch mmf_batch;
+typedef struct mmf_server mmf_server;
 
 /* ---------------------------------------------------------------- context
  * mmf_ctx_create: bind to CUDA device `device` and stream `cuda_stream` (a cudaStream_t, or
@@ -148,14 +149,43 @@ MMF_API int64_t mmf_batch_offset(const mmf_batch* b, int what, int i);
 MMF_API int64_t mmf_batch_size(const mmf_batch* b, int what);
 /* Per-stage CUDA-event timing: record events around the stages of the next max_runs calls
  * of mmf_batch_run (0 switches timing off).  mmf_batch_stage_ms waits for the stream and
- * returns in ms[7] the summed times of the recorded runs per stage (0 assemble, 1 small-n
- * Jacobi, 2 Householder reduction, 3 tridiagonal eigensolve, 4 back-transform,
- * 5 refinement, 6 U and Pbar), *runs their number, and restarts the count. */
+ * returns in ms[MMF_STAGES] the summed times of the recorded runs per stage (0 assemble,
+ * 1 small-n Jacobi, 2 Householder reduction, 3 tridiagonal eigensolve, 4 back-transform,
+ * 5 refinement: H_F X, 6 refinement: FP64-accurate Gram products X^H X and X^H H_F X,
+ * 7 refinement: the rest, 8 U and Pbar), *runs their number, and restarts the count. */
+#define MMF_STAGES 9
 MMF_API int mmf_batch_timing(mmf_batch* b, int max_runs);
 MMF_API int mmf_batch_stage_ms(mmf_batch* b, double* ms, int* runs);
 /* Device bytes held by the batch. */
 MMF_API size_t mmf_batch_bytes(const mmf_batch* b);
 MMF_API int mmf_batch_destroy(mmf_batch* b);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of independent solve requests (the paper's parameter sweeps served as
+ * they arrive).  A worker thread groups queued requests (same nt, at most max_batch per plan)
+ * into batch plans and runs each plan on one of `slots` CUDA streams; a plan is admitted only
+ * while the context's HBM budget has room for it, so requests wait in the queue until slots and
+ * memory free up.  Plans on different slots overlap on the device.  Each request's results are
+ * those of the same system solved alone (up to summation order).
+ *   mmf_serve_submit copies the system definition and the times; the caller may then change or
+ *   destroy its system.  *ticket identifies the request.
+ *   mmf_serve_wait blocks until the request is done (timeout_ms < 0: no limit; MMF_ERR_STATE on
+ *   timeout), copies E (n), U (nt x D x D complex) and P (D x D) (any may be NULL), sets *status
+ *   to the request's numerical status and releases the request.
+ *   mmf_serve_stats: latency from submit to results-on-host of the requests completed since the
+ *   last reset: median, 99th percentile and mean in ms, and their number.
+ *   mmf_serve_destroy: finishes the plans in flight, drops queued requests; call it after every
+ *   wait has returned. */
+MMF_API int mmf_serve_create(mmf_ctx* ctx, int slots, int max_batch, int precision, mmf_server** out);
+MMF_API int mmf_serve_submit(mmf_server* srv, const mmf_sys* sys, int nt, const double* t, double t0,
+                             uint64_t* ticket);
+MMF_API int mmf_serve_poll(mmf_server* srv, uint64_t ticket, int* done);
+MMF_API int mmf_serve_wait(mmf_server* srv, uint64_t ticket, int timeout_ms, double* E, double* U,
+                           double* P, int* status);
+MMF_API int mmf_serve_stats(mmf_server* srv, double* p50_ms, double* p99_ms, double* mean_ms,
+                            int64_t* completed);
+MMF_API int mmf_serve_reset_stats(mmf_server* srv);
+MMF_API int mmf_serve_destroy(mmf_server* srv);
 
 /* ---------------------------------------------------------------- no device allocation
  * No counterpart in the paper.  For callers that cannot allocate device memory (their HBM is

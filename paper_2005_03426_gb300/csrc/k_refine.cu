@@ -518,26 +518,227 @@ __global__ void __launch_bounds__(256) k_sort_pairs(const MmfDesc* __restrict__ 
     for (int r = threadIdx.x; r < n; r += blockDim.x) dst[r] = src[r];
 }
 
-cudaError_t mmf_launch_refine(const MmfLaunch& L, const double2* coef, double2* X, double* E,
-                              double2* G, double2* S, double2* HX, double* lam, int iters,
-                              int* status, int* cid, int64_t mat_elems) {
+// ================================================================== banded refinement step
+// After one full step, the remaining corrections between eigenpairs far apart in the sorted
+// order are second order in (eps |H| / gap) and negligible; the next step only forms G and S for
+// pairs |i - j| <= RF_W (band storage Bm[i * (2 RF_W + 1) + (j - i + RF_W)]) and applies
+// X <- X + X Et with the banded Et.
+#define RF_W 16
+#define RF_BW (2 * RF_W + 1)
+#define RF_BC 32            // columns per CTA
+#define RF_BR 16            // rows per staged chunk
+
+__global__ void __launch_bounds__(256) k_gram_band_df32(const MmfDesc* __restrict__ descs,
+                                                        const int* __restrict__ idx,
+                                                        const double2* __restrict__ Xg,
+                                                        const double2* __restrict__ HXg,
+                                                        double2* __restrict__ Gb,
+                                                        double2* __restrict__ Sb) {
+    __shared__ Split xs[RF_BR][RF_BC + 2 * RF_W + 1];
+    __shared__ Split hs[RF_BR][RF_BC + 2 * RF_W + 1];
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n;
+    const int i0 = blockIdx.x * RF_BC;
+    if (i0 >= n) return;
+    const int cbase = i0 - RF_W;             // first staged column
+    const int ncs = RF_BC + 2 * RF_W;         // staged columns
+    const double2* X = Xg + d.mat_off;
+    const double2* HX = HXg + d.mat_off;
+    // each thread owns up to 5 (i, j) pairs: pair p = tid + 256 q, i = i0 + p / BW, j = i + p % BW - W
+    DF gr[5], gi[5], sr[5], si[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) gr[q] = gi[q] = sr[q] = si[q] = DF{0.f, 0.f};
+    for (int k0 = 0; k0 < n; k0 += RF_BR) {
+        for (int e = threadIdx.x; e < RF_BR * ncs; e += 256) {
+            const int c = e / RF_BR, kk = e - c * RF_BR;
+            const int col = cbase + c, k = k0 + kk;
+            const bool ok = k < n && col >= 0 && col < n;
+            xs[kk][c] = split(ok ? X[(int64_t)col * d.ld + k] : make_double2(0.0, 0.0));
+            hs[kk][c] = split(ok ? HX[(int64_t)col * d.ld + k] : make_double2(0.0, 0.0));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const int p = threadIdx.x + 256 * q;
+            if (p < RF_BC * RF_BW) {
+                const int ii = p / RF_BW, off = p - ii * RF_BW;  // column i0+ii, partner i0+ii+off-W
+                const int ci = ii + RF_W, cj = ii + off;            // staged indices
+                for (int kk = 0; kk < RF_BR; ++kk) {
+                    df_cmacc(gr[q], gi[q], xs[kk][ci], xs[kk][cj]);
+                    df_cmacc(sr[q], si[q], xs[kk][ci], hs[kk][cj]);
+                }
+                df_renorm(gr[q]); df_renorm(gi[q]); df_renorm(sr[q]); df_renorm(si[q]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const int p = threadIdx.x + 256 * q;
+        if (p < RF_BC * RF_BW) {
+            const int ii = p / RF_BW, off = p - ii * RF_BW;
+            const int i = i0 + ii, j = i + off - RF_W;
+            if (i < n) {
+                double2 g = make_double2(0.0, 0.0), s = make_double2(0.0, 0.0);
+                if (j >= 0 && j < n) {
+                    g = make_double2((double)gr[q].hi + (double)gr[q].lo, (double)gi[q].hi + (double)gi[q].lo);
+                    s = make_double2((double)sr[q].hi + (double)sr[q].lo, (double)si[q].hi + (double)si[q].lo);
+                    if (i == j) { g.y = 0.0; s.y = 0.0; }
+                }
+                Gb[d.mat_off + (int64_t)i * RF_BW + off] = g;
+                Sb[d.mat_off + (int64_t)i * RF_BW + off] = s;
+            }
+        }
+    }
+}
+
+// band entry (i, j) with |i - j| <= W (0 outside the matrix)
+__device__ __forceinline__ double2 band_at(const double2* B, int i, int j) {
+    return B[(int64_t)i * RF_BW + (j - i + RF_W)];
+}
+
+__global__ void __launch_bounds__(256) k_oa_lambda_band(const MmfDesc* __restrict__ descs,
+                                                        const int* __restrict__ idx,
+                                                        const double2* __restrict__ Gbg,
+                                                        const double2* __restrict__ Sbg,
+                                                        double* __restrict__ lamg,
+                                                        int* __restrict__ cidg) {
+    const MmfDesc d = descs[idx[blockIdx.x]];
+    const int n = d.n;
+    const double2* G = Gbg + d.mat_off;
+    const double2* S = Sbg + d.mat_off;
+    double* lam = lamg + d.vec_off;
+    int* cid = cidg + d.vec_off;
+    __shared__ double hmax;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = band_at(S, i, i).x / band_at(G, i, i).x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < n; ++i) m = fmax(m, fabs(lam[i]));
+        hmax = m;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int link = 0;
+        if (i + 1 < n) {
+            const double gap = fabs(lam[i + 1] - lam[i]);
+            const double2 num = band_at(S, i, i + 1) - lam[i + 1] * band_at(G, i, i + 1);
+            link = (gap <= RF_TAU * sqrt(abs2(num))) || (gap <= 1e-13 * hmax);
+        }
+        cid[i] = link;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int start = 0, prev = 0;
+        for (int i = 0; i < n; ++i) {
+            const int link = cid[i];
+            if (i == 0 || !prev) start = i;
+            cid[i] = start;
+            prev = link;
+        }
+    }
+}
+
+// Xn(:, j) = X(:, j) + sum_{|i-j|<=W} X(:, i) Et(i, j)   (Et formed on the fly from the band)
+__global__ void __launch_bounds__(256) k_xe_band(const MmfDesc* __restrict__ descs,
+                                                 const int* __restrict__ idx,
+                                                 const double2* __restrict__ Xg,
+                                                 const double2* __restrict__ Gbg,
+                                                 const double2* __restrict__ Sbg,
+                                                 const double* __restrict__ lamg,
+                                                 const int* __restrict__ cidg,
+                                                 double2* __restrict__ Xn) {
+    __shared__ float2 et[RF_BW];
+    const MmfDesc d = descs[idx[blockIdx.z]];
+    const int n = d.n;
+    const int j = blockIdx.y;
+    if (j >= n) return;
+    const double2* G = Gbg + d.mat_off;
+    const double2* S = Sbg + d.mat_off;
+    const double* lam = lamg + d.vec_off;
+    const int* cid = cidg + d.vec_off;
+    if (threadIdx.x < RF_BW) {
+        const int i = j + threadIdx.x - RF_W;
+        float2 v = make_float2(0.f, 0.f);
+        if (i >= 0 && i < n) {
+            const double2 g = band_at(G, i, j);
+            double2 e;
+            if (i == j) {
+                e = make_double2(0.5 * (1.0 - g.x), 0.0);
+            } else {
+                const double2 num = band_at(S, i, j) - lam[j] * g;
+                const double gap = lam[j] - lam[i];
+                const double hmax = fmax(fabs(lam[0]), fabs(lam[n - 1]));
+                const bool clustered = cid[i] == cid[j] || fabs(gap) <= RF_TAU * sqrt(abs2(num)) ||
+                                       fabs(gap) <= 1e-13 * fmax(hmax, fabs(lam[i]));
+                e = clustered ? (-0.5) * g : (1.0 / gap) * num;
+            }
+            v = make_float2(__double2float_rn(e.x), __double2float_rn(e.y));
+        }
+        et[threadIdx.x] = v;
+    }
+    __syncthreads();
+    const double2* X = Xg + d.mat_off;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < RF_BW; ++q) {
+            const int i = j + q - RF_W;
+            if (i >= 0 && i < n) {
+                const double2 x = X[(int64_t)i * d.ld + r];
+                const float2 xf = make_float2(__double2float_rn(x.x), __double2float_rn(x.y));
+                acc.x = fmaf(xf.x, et[q].x, fmaf(-xf.y, et[q].y, acc.x));
+                acc.y = fmaf(xf.x, et[q].y, fmaf(xf.y, et[q].x, acc.y));
+            }
+        }
+        const double2 x = X[(int64_t)j * d.ld + r];
+        Xn[d.mat_off + (int64_t)j * d.ld + r] = make_double2(x.x + (double)acc.x, x.y + (double)acc.y);
+    }
+}
+
+// The refinement is launched in three parts so that the host can time the FP64-accurate Gram
+// product on its own: (1) HX = H_F X, (2) G = X^H X and S = X^H HX, (3) the rest of the full step,
+// the banded step, the cluster separations and the final ordering.
+cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const double2* coef, const double2* X, double2* HX) {
+    if (L.count <= 0) return cudaSuccess;
+    k_apply_hf<<<dim3((L.nmax + 255) / 256, (L.nmax + 15) / 16, L.count), 256, 0, L.stream>>>(
+        L.desc, L.idx, coef, X, HX, 0, L.nmax);
+    return cudaGetLastError();
+}
+
+cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const double2* X, const double2* HX, double2* G,
+                                   double2* S) {
     if (L.count <= 0) return cudaSuccess;
     const int T = (L.nmax + RF_TILE - 1) / RF_TILE;
-    const int tiles = T * (T + 1) / 2;
-    for (int it = 0; it < iters; ++it) {
-        k_apply_hf<<<dim3((L.nmax + 255) / 256, (L.nmax + 15) / 16, L.count), 256, 0, L.stream>>>(
-            L.desc, L.idx, coef, X, HX, 0, L.nmax);
-        k_gram_df32<<<dim3(tiles, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, HX, G, S);
-        k_oa_lambda<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
-        k_oa_etilde<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
-        k_xe_update<<<dim3((L.nmax + 63) / 64, (L.nmax + 63) / 64, L.count), 256, 0, L.stream>>>(
-            L.desc, L.idx, X, G, S);
-        cudaError_t e = cudaMemcpyAsync(X, S, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
-        if (e != cudaSuccess) return e;
-        k_cluster_sep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, coef, X, HX, lam, cid, status);
-    }
-    k_sort_pairs<<<dim3(L.nmax, L.count), 256, 0, L.stream>>>(L.desc, L.idx, lam, X, E, S);
+    k_gram_df32<<<dim3(T * (T + 1) / 2, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, HX, G, S);
+    return cudaGetLastError();
+}
+
+cudaError_t mmf_launch_refine_post(const MmfLaunch& L, const double2* coef, double2* X, double* E,
+                                   double2* G, double2* S, double2* HX, double* lam, int* status,
+                                   int* cid, int64_t mat_elems) {
+    if (L.count <= 0) return cudaSuccess;
+    // rest of the full step
+    k_oa_lambda<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
+    k_oa_etilde<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
+    k_xe_update<<<dim3((L.nmax + 63) / 64, (L.nmax + 63) / 64, L.count), 256, 0, L.stream>>>(
+        L.desc, L.idx, X, G, S);
     cudaError_t e = cudaMemcpyAsync(X, S, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
+    if (e != cudaSuccess) return e;
+    k_cluster_sep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, coef, X, HX, lam, cid, status);
+    // banded step
+    k_apply_hf<<<dim3((L.nmax + 255) / 256, (L.nmax + 15) / 16, L.count), 256, 0, L.stream>>>(
+        L.desc, L.idx, coef, X, HX, 0, L.nmax);
+    k_gram_band_df32<<<dim3((L.nmax + RF_BC - 1) / RF_BC, L.count), 256, 0, L.stream>>>(
+        L.desc, L.idx, X, HX, G, S);
+    k_oa_lambda_band<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
+    k_xe_band<<<dim3((L.nmax + 255) / 256, L.nmax, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, G, S,
+                                                                                lam, cid, HX);
+    e = cudaMemcpyAsync(X, HX, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
+    if (e != cudaSuccess) return e;
+    k_cluster_sep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, coef, X, HX, lam, cid, status);
+    k_sort_pairs<<<dim3(L.nmax, L.count), 256, 0, L.stream>>>(L.desc, L.idx, lam, X, E, S);
+    e = cudaMemcpyAsync(X, S, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

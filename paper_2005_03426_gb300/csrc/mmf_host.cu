@@ -67,6 +67,7 @@ struct Pool {
 
 struct mmf_batch {
     mmf_ctx* ctx = nullptr;
+    cudaStream_t stream = nullptr;  // the context's stream, or a serving slot's stream
     int count = 0, precision = 0, nt = 0;
     std::vector<mmf_sys*> sys;
     std::vector<MmfDesc> desc;
@@ -97,6 +98,7 @@ struct mmf_batch {
     double2* h_coef = nullptr;
     double* h_t = nullptr;
     double t0 = 0.0;
+    bool pinned = true;     // host staging buffers page-locked (false: pageable, for serving)
     bool times_set = false;
     int last_stage = 0;  // 1 assembled, 2 diagonalised, 3 outputs
     // per-stage CUDA-event timing (optional)
@@ -104,12 +106,13 @@ struct mmf_batch {
     std::vector<cudaEvent_t> ev;
 };
 
-enum { ST_ASSEMBLE, ST_JACOBI, ST_HETRD, ST_TRIDIAG, ST_BACKTRANSFORM, ST_REFINE, ST_OUTPUTS, ST_COUNT };
+enum { ST_ASSEMBLE, ST_JACOBI, ST_HETRD, ST_TRIDIAG, ST_BACKTRANSFORM, ST_REFINE, ST_GRAM, ST_REFINE2,
+       ST_OUTPUTS, ST_COUNT };
 
 static void mark(mmf_batch* b, int stage) {
     if (b->timing_runs <= 0) return;
     int slot = b->runs_recorded % b->timing_runs;
-    cudaEventRecord(b->ev[(size_t)slot * (ST_COUNT + 1) + stage], b->ctx->stream);
+    cudaEventRecord(b->ev[(size_t)slot * (ST_COUNT + 1) + stage], b->stream);
 }
 
 // ------------------------------------------------------------------ helpers
@@ -172,6 +175,12 @@ extern "C" int mmf_ctx_create(int device, size_t budget, void* stream, mmf_ctx**
         budget = fr / 10 * 9;
     }
     c->budget = budget;
+    // keep freed batch memory in the stream-ordered pool of this process for reuse
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
     *out = c;
     return MMF_OK;
 }
@@ -272,18 +281,31 @@ static void fill_coef(const mmf_batch* b, double2* dst) {
 
 static void free_batch_memory(mmf_batch* b) {
     if (b->base) {
-        cudaFree(b->base);
+        cudaFreeAsync(b->base, b->stream);
         b->ctx->used -= b->bytes;
         b->base = nullptr;
     }
-    if (b->h_coef) cudaFreeHost(b->h_coef);
-    if (b->h_t) cudaFreeHost(b->h_t);
+    if (b->pinned) {
+        if (b->h_coef) cudaFreeHost(b->h_coef);
+        if (b->h_t) cudaFreeHost(b->h_t);
+    } else {
+        free(b->h_coef);
+        free(b->h_t);
+    }
     b->h_coef = nullptr;
     b->h_t = nullptr;
 }
 
+static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int precision, int nt,
+                        cudaStream_t stream, bool pinned_staging, mmf_batch** out);
+
 extern "C" int mmf_batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int precision,
                                 int nt, mmf_batch** out) {
+    return batch_create(ctx, count, systems, precision, nt, ctx ? ctx->stream : nullptr, true, out);
+}
+
+static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int precision, int nt,
+                        cudaStream_t stream, bool pinned_staging, mmf_batch** out) {
     if (!out) return fail(MMF_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!ctx || count < 1 || !systems || nt < 0) return fail(MMF_ERR_ARG, "bad batch arguments");
@@ -293,6 +315,8 @@ extern "C" int mmf_batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems
     mmf_batch* b = new (std::nothrow) mmf_batch();
     if (!b) return fail(MMF_ERR_NOMEM, "batch allocation");
     b->ctx = ctx;
+    b->stream = stream;
+    b->pinned = pinned_staging;
     b->count = count;
     b->precision = precision;
     b->nt = nt;
@@ -326,7 +350,7 @@ extern "C" int mmf_batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems
         d.M = (int)M;
         d.n = (int)n;
         d.b0 = (int)b0;
-        d.ld = (int)round_up(n, 4);
+        d.ld = (int)round_up(std::max<int64_t>(n, MMF_MIN_LD), 4);
         d.small = n <= jacobi_nmax(precision);
         int64_t nc = (int64_t)s->D * s->D;
         for (int k = 0; k < d.K; ++k) nc += (int64_t)d.nharm[k] * s->D * s->D;
@@ -393,10 +417,10 @@ extern "C" int mmf_batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems
         return fail(MMF_ERR_BUDGET, "batch needs " + std::to_string(need) + " bytes, budget has " +
                                         std::to_string(ctx->budget - ctx->used));
     }
-    cudaError_t e = cudaMalloc((void**)&b->base, b->bytes);
+    cudaError_t e = cudaMallocAsync((void**)&b->base, b->bytes, b->stream);
     if (e != cudaSuccess) {
         delete b;
-        return fail(MMF_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return fail(MMF_ERR_CUDA, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
     }
     ctx->used += b->bytes;
     unsigned char* B = b->base;
@@ -430,8 +454,14 @@ extern "C" int mmf_batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems
         b->d_E2 = (double*)(B + o_E2);
         b->d_cid = (int*)(B + o_cid);
     }
-    e = cudaMallocHost((void**)&b->h_coef, sizeof(double2) * std::max<int64_t>(b->n_coef, 1));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_t, sizeof(double) * std::max<int64_t>(b->n_t, 1));
+    if (b->pinned) {
+        e = cudaMallocHost((void**)&b->h_coef, sizeof(double2) * std::max<int64_t>(b->n_coef, 1));
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_t, sizeof(double) * std::max<int64_t>(b->n_t, 1));
+    } else {
+        b->h_coef = (double2*)malloc(sizeof(double2) * std::max<int64_t>(b->n_coef, 1));
+        b->h_t = (double*)malloc(sizeof(double) * std::max<int64_t>(b->n_t, 1));
+        e = (b->h_coef && b->h_t) ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
     if (e != cudaSuccess) {
         free_batch_memory(b);
         delete b;
@@ -439,7 +469,7 @@ extern "C" int mmf_batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems
     }
     fill_coef(b, b->h_coef);
     std::memset(b->h_t, 0, sizeof(double) * std::max<int64_t>(b->n_t, 1));
-    cudaStream_t st = ctx->stream;
+    cudaStream_t st = b->stream;
     e = cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(MmfDesc) * count, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_all, b->all.data(), sizeof(int) * b->all.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !b->small.empty())
@@ -469,7 +499,7 @@ extern "C" int mmf_batch_timing(mmf_batch* b, int max_runs) {
     if (!b || max_runs < 0 || max_runs > 4096) return fail(MMF_ERR_ARG, "bad batch or max_runs");
     std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
     CU(cudaSetDevice(b->ctx->device));
-    CU(cudaStreamSynchronize(b->ctx->stream));
+    CU(cudaStreamSynchronize(b->stream));
     drop_events(b);
     b->ev.resize((size_t)max_runs * (ST_COUNT + 1));
     for (auto& e : b->ev) CU(cudaEventCreate(&e));
@@ -481,7 +511,7 @@ extern "C" int mmf_batch_stage_ms(mmf_batch* b, double* ms, int* runs) {
     if (!b || !ms) return fail(MMF_ERR_ARG, "batch and ms required");
     std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
     CU(cudaSetDevice(b->ctx->device));
-    CU(cudaStreamSynchronize(b->ctx->stream));
+    CU(cudaStreamSynchronize(b->stream));
     for (int s = 0; s < ST_COUNT; ++s) ms[s] = 0.0;
     int nr = std::min(b->runs_recorded, b->timing_runs);
     for (int r = 0; r < nr; ++r)
@@ -500,7 +530,7 @@ extern "C" int mmf_batch_destroy(mmf_batch* b) {
     if (!b) return MMF_ERR_ARG;
     std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
     cudaSetDevice(b->ctx->device);
-    cudaStreamSynchronize(b->ctx->stream);
+    cudaStreamSynchronize(b->stream);
     drop_events(b);
     free_batch_memory(b);
     delete b;
@@ -515,12 +545,12 @@ extern "C" int mmf_batch_set_times(mmf_batch* b, double t0, const double* t) {
         if (!std::isfinite(t[i])) return fail(MMF_ST_NONFINITE, "time not finite");
     if (!std::isfinite(t0)) return fail(MMF_ST_NONFINITE, "t0 not finite");
     std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
-    CU(cudaStreamSynchronize(b->ctx->stream));  // staging buffer may be in flight
+    CU(cudaStreamSynchronize(b->stream));  // staging buffer may be in flight
     if (b->n_t > 0) std::memcpy(b->h_t, t, sizeof(double) * b->n_t);
     b->t0 = t0;
     b->times_set = true;
     if (b->n_t > 0)
-        CU(cudaMemcpyAsync(b->d_t, b->h_t, sizeof(double) * b->n_t, cudaMemcpyHostToDevice, b->ctx->stream));
+        CU(cudaMemcpyAsync(b->d_t, b->h_t, sizeof(double) * b->n_t, cudaMemcpyHostToDevice, b->stream));
     return MMF_OK;
 }
 
@@ -528,7 +558,7 @@ extern "C" int mmf_batch_upload(mmf_batch* b) {
     if (!b) return fail(MMF_ERR_ARG, "batch is NULL");
     std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
     CU(cudaSetDevice(b->ctx->device));
-    cudaStream_t st = b->ctx->stream;
+    cudaStream_t st = b->stream;
     CU(cudaMemcpyAsync(b->d_coef, b->h_coef, sizeof(double2) * b->n_coef, cudaMemcpyHostToDevice, st));
     if (b->n_t > 0)
         CU(cudaMemcpyAsync(b->d_t, b->h_t, sizeof(double) * b->n_t, cudaMemcpyHostToDevice, st));
@@ -541,7 +571,7 @@ static MmfLaunch launch_of(const mmf_batch* b, const std::vector<int>& list, con
     L.idx = dlist;
     L.count = (int)list.size();
     L.nmax = nmax;
-    L.stream = b->ctx->stream;
+    L.stream = b->stream;
     return L;
 }
 
@@ -555,7 +585,7 @@ static MmfLaunch launch_of(const mmf_batch* b, const std::vector<int>& list, con
 
 static int stage_assemble(mmf_batch* b) {
     const int fp32 = b->precision == MMF_MIXED;
-    cudaStream_t st = b->ctx->stream;
+    cudaStream_t st = b->stream;
     mark(b, ST_ASSEMBLE);
     CU(cudaMemsetAsync(b->d_status, 0, sizeof(int) * b->count, st));
     MmfLaunch La = launch_of(b, b->all, b->d_all, b->nmax_all);
@@ -589,17 +619,23 @@ static int stage_eig(mmf_batch* b) {
     mark(b, ST_REFINE);
     if (fp32) {
         MmfLaunch La = launch_of(b, b->all, b->d_all, b->nmax_all);
-        cudaError_t e = mmf_launch_refine(La, b->d_coef, b->d_Zf, b->d_E, b->d_R, b->d_S, b->d_HX,
-                                          b->d_E2, MMF_REFINE_ITERS, b->d_status, b->d_cid, b->n_mat);
-        if (e != cudaSuccess) return fail(MMF_ERR_CUDA, std::string("refine: ") + cudaGetErrorString(e));
-        g_launches += 6 * MMF_REFINE_ITERS + 1;
+        LAUNCH(mmf_launch_refine_pre(La, b->d_coef, b->d_Zf, b->d_HX), 1);
+        mark(b, ST_GRAM);
+        LAUNCH(mmf_launch_refine_gram(La, b->d_Zf, b->d_HX, b->d_R, b->d_S), 1);
+        mark(b, ST_REFINE2);
+        LAUNCH(mmf_launch_refine_post(La, b->d_coef, b->d_Zf, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_E2,
+                                      b->d_status, b->d_cid, b->n_mat),
+               10);
+    } else {
+        mark(b, ST_GRAM);
+        mark(b, ST_REFINE2);
     }
     b->last_stage = 2;
     return MMF_OK;
 }
 
 static int stage_outputs(mmf_batch* b) {
-    cudaStream_t st = b->ctx->stream;
+    cudaStream_t st = b->stream;
     mark(b, ST_OUTPUTS);
     if (b->n_u > 0) CU(cudaMemsetAsync(b->d_U, 0, sizeof(double2) * b->n_u, st));
     CU(cudaMemsetAsync(b->d_P, 0, sizeof(double) * b->n_p, st));
@@ -630,8 +666,8 @@ extern "C" int mmf_batch_sync(mmf_batch* b, int* status) {
     std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
     CU(cudaSetDevice(b->ctx->device));
     std::vector<int> st(b->count);
-    CU(cudaMemcpyAsync(st.data(), b->d_status, sizeof(int) * b->count, cudaMemcpyDeviceToHost, b->ctx->stream));
-    CU(cudaStreamSynchronize(b->ctx->stream));
+    CU(cudaMemcpyAsync(st.data(), b->d_status, sizeof(int) * b->count, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
     int worst = 0;
     for (int i = 0; i < b->count; ++i) worst = std::max(worst, st[i]);
     if (status) std::memcpy(status, st.data(), sizeof(int) * b->count);
@@ -640,7 +676,7 @@ extern "C" int mmf_batch_sync(mmf_batch* b, int* status) {
 
 static int copy_d2h(mmf_batch* b, void* dst, const void* src, size_t bytes) {
     if (!bytes) return MMF_OK;
-    CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, b->ctx->stream));
+    CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, b->stream));
     return MMF_OK;
 }
 
@@ -655,7 +691,7 @@ extern "C" int mmf_batch_get(mmf_batch* b, int i, double* E, double* U, double* 
     if (rc == MMF_OK && U) rc = copy_d2h(b, U, b->d_U + d.u_off, sizeof(double2) * (size_t)b->nt * d.D * d.D);
     if (rc == MMF_OK && P) rc = copy_d2h(b, P, b->d_P + d.p_off, sizeof(double) * d.D * d.D);
     if (rc != MMF_OK) return rc;
-    CU(cudaStreamSynchronize(b->ctx->stream));
+    CU(cudaStreamSynchronize(b->stream));
     return MMF_OK;
 }
 
@@ -666,8 +702,8 @@ extern "C" int mmf_batch_eigenvectors(mmf_batch* b, int i, double* Z) {
     CU(cudaSetDevice(b->ctx->device));
     const MmfDesc& d = b->desc[i];
     CU(cudaMemcpy2DAsync(Z, sizeof(double2) * d.n, b->d_Zf + d.mat_off, sizeof(double2) * d.ld,
-                         sizeof(double2) * d.n, d.n, cudaMemcpyDeviceToHost, b->ctx->stream));
-    CU(cudaStreamSynchronize(b->ctx->stream));
+                         sizeof(double2) * d.n, d.n, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
     return MMF_OK;
 }
 
@@ -680,7 +716,7 @@ extern "C" int mmf_batch_results(mmf_batch* b, double* E, double* U, double* P) 
     if (rc == MMF_OK && U) rc = copy_d2h(b, U, b->d_U, sizeof(double2) * b->n_u);
     if (rc == MMF_OK && P) rc = copy_d2h(b, P, b->d_P, sizeof(double) * b->n_p);
     if (rc != MMF_OK) return rc;
-    CU(cudaStreamSynchronize(b->ctx->stream));
+    CU(cudaStreamSynchronize(b->stream));
     return MMF_OK;
 }
 
@@ -740,13 +776,13 @@ extern "C" int mmf_hamiltonian(mmf_sys* s, double* HF) {
     CU(cudaSetDevice(s->ctx->device));
     if (b->precision == MMF_FP64) {
         CU(cudaMemcpy2DAsync(HF, sizeof(double2) * d.n, b->d_H, sizeof(double2) * d.ld,
-                             sizeof(double2) * d.n, d.n, cudaMemcpyDeviceToHost, s->ctx->stream));
-        CU(cudaStreamSynchronize(s->ctx->stream));
+                             sizeof(double2) * d.n, d.n, cudaMemcpyDeviceToHost, s->solo->stream));
+        CU(cudaStreamSynchronize(s->solo->stream));
     } else {
         std::vector<float2> tmp((size_t)d.n * d.n);
         CU(cudaMemcpy2DAsync(tmp.data(), sizeof(float2) * d.n, b->d_H, sizeof(float2) * d.ld,
-                             sizeof(float2) * d.n, d.n, cudaMemcpyDeviceToHost, s->ctx->stream));
-        CU(cudaStreamSynchronize(s->ctx->stream));
+                             sizeof(float2) * d.n, d.n, cudaMemcpyDeviceToHost, s->solo->stream));
+        CU(cudaStreamSynchronize(s->solo->stream));
         for (size_t e = 0; e < tmp.size(); ++e) {
             HF[2 * e] = tmp[e].x;
             HF[2 * e + 1] = tmp[e].y;
@@ -840,7 +876,7 @@ extern "C" int mmf_micromotion(mmf_sys* s, int nt, const double* t, double* UF, 
     CU(cudaSetDevice(s->ctx->device));
     mmf_batch* b = s->solo;
     const MmfDesc& d = b->desc[0];
-    cudaStream_t st = s->ctx->stream;
+    cudaStream_t st = s->solo->stream;
     const size_t nuf = (size_t)nt * d.D * d.D;
     unsigned char* tmp = nullptr;
     const size_t o_t = 0, o_r = (sizeof(double) * nt + 255) / 256 * 256,
@@ -869,4 +905,349 @@ extern "C" int mmf_time_evolution_operator(mmf_sys* s, int precision, double t0,
     if (rc < 0) return rc;
     int rc2 = mmf_time_evolution(s, t0, nt, t, U);
     return rc2 != MMF_OK ? rc2 : rc;
+}
+
+// ================================================================== serving (continuous batching)
+// A worker thread turns queued requests into batch plans on free slots (each slot = one CUDA
+// stream with at most one plan in flight), admitting a plan only while the context's HBM budget
+// has room for it.  Plans on different slots overlap on the device; a finished plan's results are
+// copied out, its memory goes back to the pool, and the slot takes the next requests at once.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+
+namespace {
+typedef std::chrono::steady_clock Clock;
+
+struct ServeReq {
+    uint64_t id = 0;
+    mmf_sys* sys = nullptr;  // private copy of the caller's definition
+    int nt = 0;
+    std::vector<double> t;
+    double t0 = 0.0;
+    Clock::time_point t_submit, t_done;
+    int state = 0;  // 0 queued, 1 on the GPU, 2 done
+    int status = 0;
+    int64_t n = 0;
+    int D = 0;
+    std::vector<double> E, U, P;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    mmf_batch* b = nullptr;
+    std::vector<ServeReq*> reqs;
+    double* hE = nullptr;
+    double2* hU = nullptr;
+    double* hP = nullptr;
+    int* hst = nullptr;
+    size_t capE = 0, capU = 0, capP = 0, capS = 0;
+};
+
+template <class T>
+int grow_pinned(T** p, size_t* cap, size_t need) {
+    if (need <= *cap) return MMF_OK;
+    if (*p) cudaFreeHost(*p);
+    *p = nullptr;
+    size_t c = std::max(need, *cap * 2);
+    cudaError_t e = cudaMallocHost((void**)p, sizeof(T) * c);
+    if (e != cudaSuccess) return fail(MMF_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+    *cap = c;
+    return MMF_OK;
+}
+}  // namespace
+
+struct mmf_server {
+    mmf_ctx* ctx = nullptr;
+    int precision = 0, max_batch = 1;
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::thread worker;
+    bool stop = false;
+    std::deque<ServeReq*> pending;
+    std::unordered_map<uint64_t, ServeReq*> reqs;
+    uint64_t next_id = 1;
+    std::vector<double> lat_ms;
+    int64_t completed = 0, solves_started = 0;
+    int last_error = 0;
+};
+
+static mmf_sys* copy_sys(const mmf_sys* s) {
+    mmf_sys* c = new (std::nothrow) mmf_sys();
+    if (!c) return nullptr;
+    c->ctx = s->ctx;
+    c->D = s->D;
+    c->H0 = s->H0;
+    c->omega = s->omega;
+    c->N = s->N;
+    c->V = s->V;
+    return c;
+}
+
+// Finish a slot whose plan completed: hand results to the requests, release the plan.
+static void serve_finish(mmf_server* sv, Slot& sl) {
+    mmf_batch* b = sl.b;
+    auto now = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (size_t k = 0; k < sl.reqs.size(); ++k) {
+            ServeReq* r = sl.reqs[k];
+            const MmfDesc& d = b->desc[k];
+            r->E.assign(sl.hE + d.vec_off, sl.hE + d.vec_off + d.n);
+            const double* u = (const double*)(sl.hU + d.u_off);
+            r->U.assign(u, u + 2 * (size_t)b->nt * d.D * d.D);
+            r->P.assign(sl.hP + d.p_off, sl.hP + d.p_off + (size_t)d.D * d.D);
+            r->status = sl.hst[k];
+            r->t_done = now;
+            r->state = 2;
+            sv->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+            sv->completed++;
+        }
+    }
+    mmf_batch_destroy(b);
+    sl.b = nullptr;
+    sl.reqs.clear();
+    sv->cv.notify_all();
+}
+
+// Start a plan for up to max_batch queued requests (same nt) on a free slot.  Returns true if it
+// started one.
+static bool serve_admit(mmf_server* sv, Slot& sl) {
+    std::vector<ServeReq*> group;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->pending.empty()) return false;
+        const int nt = sv->pending.front()->nt;
+        for (auto it = sv->pending.begin(); it != sv->pending.end() && (int)group.size() < sv->max_batch; ++it)
+            if ((*it)->nt == nt) group.push_back(*it);
+    }
+    while (!group.empty()) {
+        std::vector<mmf_sys*> sys;
+        for (ServeReq* r : group) sys.push_back(r->sys);
+        mmf_batch* b = nullptr;
+        int rc = batch_create(sv->ctx, (int)sys.size(), sys.data(), sv->precision, group[0]->nt, sl.stream,
+                              false, &b);
+        if (rc == MMF_ERR_BUDGET) {  // admit fewer, or wait for memory to come back
+            group.pop_back();
+            continue;
+        }
+        if (rc != MMF_OK) {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            for (ServeReq* r : group) {
+                r->status = rc;
+                r->state = 2;
+                r->t_done = Clock::now();
+                sv->pending.erase(std::find(sv->pending.begin(), sv->pending.end(), r));
+            }
+            sv->last_error = rc;
+            sv->cv.notify_all();
+            return true;
+        }
+        std::vector<double> t;
+        for (ServeReq* r : group) t.insert(t.end(), r->t.begin(), r->t.end());
+        rc = mmf_batch_set_times(b, group[0]->t0, t.data());
+        if (rc == MMF_OK) rc = mmf_batch_run(b);
+        if (rc == MMF_OK) rc = grow_pinned(&sl.hE, &sl.capE, (size_t)std::max<int64_t>(b->n_vec, 1));
+        if (rc == MMF_OK) rc = grow_pinned(&sl.hU, &sl.capU, (size_t)std::max<int64_t>(b->n_u, 1));
+        if (rc == MMF_OK) rc = grow_pinned(&sl.hP, &sl.capP, (size_t)std::max<int64_t>(b->n_p, 1));
+        if (rc == MMF_OK) rc = grow_pinned(&sl.hst, &sl.capS, (size_t)b->count);
+        cudaError_t e = cudaSuccess;
+        if (rc == MMF_OK) e = cudaMemcpyAsync(sl.hE, b->d_E, sizeof(double) * b->n_vec, cudaMemcpyDeviceToHost, sl.stream);
+        if (rc == MMF_OK && e == cudaSuccess && b->n_u > 0)
+            e = cudaMemcpyAsync(sl.hU, b->d_U, sizeof(double2) * b->n_u, cudaMemcpyDeviceToHost, sl.stream);
+        if (rc == MMF_OK && e == cudaSuccess)
+            e = cudaMemcpyAsync(sl.hP, b->d_P, sizeof(double) * b->n_p, cudaMemcpyDeviceToHost, sl.stream);
+        if (rc == MMF_OK && e == cudaSuccess)
+            e = cudaMemcpyAsync(sl.hst, b->d_status, sizeof(int) * b->count, cudaMemcpyDeviceToHost, sl.stream);
+        if (rc == MMF_OK && e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
+        if (rc == MMF_OK && e != cudaSuccess) rc = fail(MMF_ERR_CUDA, cudaGetErrorString(e));
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (ServeReq* r : group) sv->pending.erase(std::find(sv->pending.begin(), sv->pending.end(), r));
+        if (rc != MMF_OK) {
+            for (ServeReq* r : group) {
+                r->status = rc;
+                r->state = 2;
+                r->t_done = Clock::now();
+            }
+            sv->last_error = rc;
+            mmf_batch_destroy(b);
+            sv->cv.notify_all();
+            return true;
+        }
+        for (ServeReq* r : group) r->state = 1;
+        sl.b = b;
+        sl.reqs = group;
+        sv->solves_started += (int64_t)group.size();
+        return true;
+    }
+    return false;  // not even one request fits the budget right now
+}
+
+static void serve_loop(mmf_server* sv) {
+    cudaSetDevice(sv->ctx->device);
+    while (true) {
+        bool progress = false;
+        for (Slot& sl : sv->slots)
+            if (sl.b && cudaEventQuery(sl.done) == cudaSuccess) {
+                serve_finish(sv, sl);
+                progress = true;
+            }
+        for (Slot& sl : sv->slots)
+            if (!sl.b && serve_admit(sv, sl)) progress = true;
+        std::unique_lock<std::mutex> lk(sv->mu);
+        if (sv->stop) {
+            bool busy = false;
+            for (Slot& sl : sv->slots) busy |= sl.b != nullptr;
+            if (!busy) break;
+        }
+        if (!progress) sv->cv.wait_for(lk, std::chrono::microseconds(100));
+    }
+}
+
+extern "C" int mmf_serve_create(mmf_ctx* ctx, int slots, int max_batch, int precision, mmf_server** out) {
+    if (!out) return fail(MMF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ctx || slots < 1 || slots > 64 || max_batch < 1) return fail(MMF_ERR_ARG, "bad server arguments");
+    if (precision != MMF_FP64 && precision != MMF_MIXED) return fail(MMF_ERR_ARG, "bad precision");
+    CU(cudaSetDevice(ctx->device));
+    mmf_server* sv = new (std::nothrow) mmf_server();
+    if (!sv) return fail(MMF_ERR_NOMEM, "server allocation");
+    sv->ctx = ctx;
+    sv->precision = precision;
+    sv->max_batch = max_batch;
+    sv->slots.resize(slots);
+    for (Slot& sl : sv->slots) {
+        cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (Slot& q : sv->slots) {
+                if (q.stream) cudaStreamDestroy(q.stream);
+                if (q.done) cudaEventDestroy(q.done);
+            }
+            delete sv;
+            return fail(MMF_ERR_CUDA, cudaGetErrorString(e));
+        }
+    }
+    sv->worker = std::thread(serve_loop, sv);
+    *out = sv;
+    return MMF_OK;
+}
+
+extern "C" int mmf_serve_submit(mmf_server* sv, const mmf_sys* sys, int nt, const double* t, double t0,
+                                uint64_t* ticket) {
+    if (!sv || !sys || nt < 0 || (nt > 0 && !t) || !ticket) return fail(MMF_ERR_ARG, "bad submit arguments");
+    if (sys->ctx != sv->ctx) return fail(MMF_ERR_ARG, "system from another context");
+    if (sys->omega.empty()) return fail(MMF_ERR_ARG, "system has no drive mode");
+    ServeReq* r = new (std::nothrow) ServeReq();
+    if (!r) return fail(MMF_ERR_NOMEM, "request allocation");
+    r->sys = copy_sys(sys);
+    if (!r->sys) { delete r; return fail(MMF_ERR_NOMEM, "request allocation"); }
+    r->nt = nt;
+    r->t.assign(t, t + nt);
+    r->t0 = t0;
+    r->n = sys_dim(sys);
+    r->D = sys->D;
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        r->id = sv->next_id++;
+        sv->pending.push_back(r);
+        sv->reqs[r->id] = r;
+        *ticket = r->id;
+    }
+    sv->cv.notify_all();
+    return MMF_OK;
+}
+
+extern "C" int mmf_serve_poll(mmf_server* sv, uint64_t ticket, int* done) {
+    if (!sv || !done) return fail(MMF_ERR_ARG, "bad poll arguments");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return fail(MMF_ERR_ARG, "unknown ticket");
+    *done = it->second->state == 2;
+    return MMF_OK;
+}
+
+extern "C" int mmf_serve_wait(mmf_server* sv, uint64_t ticket, int timeout_ms, double* E, double* U, double* P,
+                              int* status) {
+    if (!sv) return fail(MMF_ERR_ARG, "server is NULL");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return fail(MMF_ERR_ARG, "unknown ticket");
+    ServeReq* r = it->second;
+    auto ready = [&] { return r->state == 2; };
+    if (timeout_ms < 0) sv->cv.wait(lk, ready);
+    else if (!sv->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+        return fail(MMF_ERR_STATE, "request not finished within the timeout");
+    if (status) *status = r->status;
+    if (r->status < 0) {
+        sv->reqs.erase(it);
+        mmf_sys_destroy(r->sys);
+        delete r;
+        return fail(MMF_ERR_CUDA, "request failed");
+    }
+    if (E) std::memcpy(E, r->E.data(), sizeof(double) * r->E.size());
+    if (U) std::memcpy(U, r->U.data(), sizeof(double) * r->U.size());
+    if (P) std::memcpy(P, r->P.data(), sizeof(double) * r->P.size());
+    sv->reqs.erase(it);
+    mmf_sys_destroy(r->sys);
+    delete r;
+    return MMF_OK;
+}
+
+extern "C" int mmf_serve_stats(mmf_server* sv, double* p50_ms, double* p99_ms, double* mean_ms,
+                               int64_t* completed) {
+    if (!sv) return fail(MMF_ERR_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    std::vector<double> v = sv->lat_ms;
+    std::sort(v.begin(), v.end());
+    auto q = [&](double f) { return v.empty() ? 0.0 : v[std::min(v.size() - 1, (size_t)(f * (v.size() - 1) + 0.5))]; };
+    double m = 0.0;
+    for (double x : v) m += x;
+    if (p50_ms) *p50_ms = q(0.50);
+    if (p99_ms) *p99_ms = q(0.99);
+    if (mean_ms) *mean_ms = v.empty() ? 0.0 : m / v.size();
+    if (completed) *completed = sv->completed;
+    return MMF_OK;
+}
+
+extern "C" int mmf_serve_reset_stats(mmf_server* sv) {
+    if (!sv) return fail(MMF_ERR_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->lat_ms.clear();
+    sv->completed = 0;
+    return MMF_OK;
+}
+
+extern "C" int mmf_serve_destroy(mmf_server* sv) {
+    if (!sv) return MMF_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+        for (ServeReq* r : sv->pending) {  // never started
+            r->status = MMF_ERR_STATE;
+            r->state = 2;
+        }
+        sv->pending.clear();
+    }
+    sv->cv.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    for (auto& kv : sv->reqs) {
+        mmf_sys_destroy(kv.second->sys);
+        delete kv.second;
+    }
+    for (Slot& sl : sv->slots) {
+        cudaStreamDestroy(sl.stream);
+        cudaEventDestroy(sl.done);
+        if (sl.hE) cudaFreeHost(sl.hE);
+        if (sl.hU) cudaFreeHost(sl.hU);
+        if (sl.hP) cudaFreeHost(sl.hP);
+        if (sl.hst) cudaFreeHost(sl.hst);
+    }
+    delete sv;
+    return MMF_OK;
 }

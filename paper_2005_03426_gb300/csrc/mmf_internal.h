@@ -127,10 +127,13 @@ cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const dou
 int mmf_hetrd_max_n(int fp32);
 cudaError_t mmf_launch_micromotion(const MmfLaunch& L, int D, const double2* Z, const double* t,
                                    int nt, int64_t* reps, double2* UF);
-cudaError_t mmf_launch_refine(const MmfLaunch& L, const double2* coef, double2* X, double* E,
-                              double2* G, double2* S, double2* HX, double* lam, int iters,
-                              int* status, int* cid, int64_t mat_elems);
-#define MMF_REFINE_ITERS 2
+cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const double2* coef, const double2* X, double2* HX);
+cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const double2* X, const double2* HX, double2* G,
+                                   double2* S);
+cudaError_t mmf_launch_refine_post(const MmfLaunch& L, const double2* coef, double2* X, double* E,
+                                   double2* G, double2* S, double2* HX, double* lam, int* status,
+                                   int* cid, int64_t mat_elems);
+#define MMF_MIN_LD 36   // n x ld matrix slots also hold the n x 33 band of the refinement
 
 #define MMF_NB 32          // Householder panel width and back-transform block size
 #define MMF_JACOBI_NMAX_F64 84

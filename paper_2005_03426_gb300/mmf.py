@@ -83,6 +83,14 @@ _SIGS = {
     "mmf_batch_stage_ms": (_I, [_P, _P, _P]),
     "mmf_batch_destroy": (_I, [_P]),
     "mmf_tridiag_eig_noalloc": (_I, [_P, _P, _I, _P, _P, _P]),
+    "mmf_serve_create": (_I, [_P, _I, _I, _I, _PP]),
+    "mmf_serve_submit": (_I, [_P, _P, _I, _P, _D, ctypes.POINTER(ctypes.c_uint64)]),
+    "mmf_serve_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(_I)]),
+    "mmf_serve_wait": (_I, [_P, ctypes.c_uint64, _I, _P, _P, _P, ctypes.POINTER(_I)]),
+    "mmf_serve_stats": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
+                             ctypes.POINTER(_I64)]),
+    "mmf_serve_reset_stats": (_I, [_P]),
+    "mmf_serve_destroy": (_I, [_P]),
     "mmf_strerror": (ctypes.c_char_p, [_I]),
     "mmf_last_error": (ctypes.c_char_p, []),
     "mmf_last_launch_count": (_I, []),
@@ -299,7 +307,8 @@ class Batch:
         p = P[self.offP[i]:self.offP[i] + s.D * s.D].reshape(s.D, s.D)
         return e, u, p
 
-    STAGES = ("assemble", "jacobi", "hetrd", "tridiag", "backtransform", "refine", "outputs")
+    STAGES = ("assemble", "jacobi", "hetrd", "tridiag", "backtransform", "refine_hx", "refine_gram",
+              "refine_rest", "outputs")
 
     def timing(self, max_runs: int):
         _check(lib().mmf_batch_timing(self.h, int(max_runs)))
@@ -316,6 +325,60 @@ class Batch:
     def close(self):
         if self.h:
             lib().mmf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server (mmf_serve_*): submit systems, wait for their results."""
+
+    def __init__(self, ctx: Context, slots: int = 4, max_batch: int = 16, precision: int = MMF_MIXED):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        _check(lib().mmf_serve_create(ctx.h, slots, max_batch, precision, ctypes.byref(h)))
+        self.h = h
+        self._shape = {}
+
+    def submit(self, system: System, t, t0: float = 0.0) -> int:
+        t = np.ascontiguousarray(np.atleast_1d(np.asarray(t, dtype=np.float64)))
+        tk = ctypes.c_uint64(0)
+        _check(lib().mmf_serve_submit(self.h, system.h, int(t.size), _ptr(t), float(t0), ctypes.byref(tk)))
+        self._shape[tk.value] = (system.n, system.D, int(t.size))
+        return int(tk.value)
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int(0)
+        _check(lib().mmf_serve_poll(self.h, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        n, D, nt = self._shape.pop(ticket)
+        E = np.zeros(n)
+        U = np.zeros((nt, D, D), dtype=np.complex128)
+        P = np.zeros((D, D))
+        st = ctypes.c_int(0)
+        _check(lib().mmf_serve_wait(self.h, ticket, timeout_ms, _ptr(E), _ptr(U) if nt else None, _ptr(P),
+                                    ctypes.byref(st)))
+        return E, U, P, int(st.value)
+
+    def stats(self):
+        p50, p99, mean = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        cnt = ctypes.c_int64()
+        _check(lib().mmf_serve_stats(self.h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(mean),
+                                     ctypes.byref(cnt)))
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "mean_ms": mean.value, "completed": cnt.value}
+
+    def reset_stats(self):
+        _check(lib().mmf_serve_reset_stats(self.h))
+
+    def close(self):
+        if self.h:
+            lib().mmf_serve_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -255,3 +255,41 @@ def random_small(seed: int, D: int, Ns: List[int], nharm: List[int] | None = Non
             cl.append(G)
         couplings.append(cl)
     return Problem(D=D, H0=H0, omegas=omegas, Ns=list(Ns), couplings=couplings)
+
+
+def serving_stream(count: int, seed: int = 40) -> List[Problem]:
+    """Request mix for the serving benchmark: each request is, with equal probability, a driven
+    qubit (omega ~ U[0.2, 2], N = 20, n = 82), a spin-1 two-mode system (amplitudes ~ U[0.05, 0.5],
+    N = (10, 10), n = 1323) or an uneven-batch draw (n <= 2000)."""
+    rng = SplitMix64(seed)
+    out = []
+    while len(out) < count:
+        kind = rng.integer(0, 2)
+        if kind == 0:
+            out.append(two_level(rng.uniform_in(0.2, 2.0), N=20))
+        elif kind == 1:
+            a1 = rng.uniform_in(0.05, 0.5)
+            a2 = rng.uniform_in(0.05, 0.5)
+            out.append(spin1_bichromatic(a1, a2))
+        else:
+            while True:
+                D = rng.integer(2, 8)
+                K = rng.integer(1, 2)
+                Ns = [rng.integer(4, 30) for _ in range(K)]
+                n = D
+                for N in Ns:
+                    n *= 2 * N + 1
+                if n <= 2000:
+                    break
+            out.append(random_multimode(rng, D, Ns))
+    return out
+
+
+def poisson_arrivals(count: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of the given rate (exponential gaps)."""
+    rng = SplitMix64(seed)
+    t, out = 0.0, []
+    for _ in range(count):
+        t += -math.log(1.0 - rng.uniform()) / rate
+        out.append(t)
+    return np.array(out)
