@@ -91,10 +91,11 @@ class Clocks:
 
 
 # FP32 instruction issue peak (one FP32 op per lane per clock) and the double-FP32 scheme's cost:
-# an FP64-accurate complex multiply-add takes 4 real products x 13 FP32 instructions (exact
-# product + FMA error term + cross terms + TwoSum) for 8 FP64-equivalent flops.
+# on the first refinement step X is FP32-exact, so an FP64-accurate real product-accumulate takes
+# 10 FP32 instructions for X^H X and 11 for X^H (H X) (exact product + FMA error term + TwoSum),
+# i.e. 4 x (10 + 11) / 2 = 42 instructions per complex multiply-add of 8 FP64-equivalent flops.
 FP32_INSTR_PEAK = 152 * 128 * 2.07e9
-DF32_INSTR_PER_FLOP = 52.0 / 8.0
+DF32_INSTR_PER_FLOP = (40.0 + 44.0) / 2.0 / 8.0  # G terms 10, S terms 11 instructions per real product
 
 
 def stage_model(stage: str, n: int, nt: int, mixed: bool):
@@ -110,7 +111,7 @@ def stage_model(stage: str, n: int, nt: int, mixed: bool):
             ("FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz" if mixed else "FP64: nominal 1.25 TFLOP/s")
     if stage == "refine_gram":
         return 8.0 * n ** 3, FP32_INSTR_PEAK / DF32_INSTR_PER_FLOP, \
-            "FP64-accurate double-FP32: FP32 issue peak 152 x 128 x 2.07 GHz / 6.5 instructions per flop"
+            "FP64-accurate double-FP32: FP32 issue peak 152 x 128 x 2.07 GHz / 5.25 instructions per flop"
     if stage == "outputs":
         return 8.0 * nt * n * n, FP64_ALU_PEAK, "FP64: nominal 1.25 TFLOP/s"
     return None
@@ -222,6 +223,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--serve", action="store_true", help="only the serving rate sweep")
+    ap.add_argument("--workload", default="spin1", choices=["spin1", "uneven", "large"],
+                    help="spin1: 64 spin-1 systems n=1323 (default); uneven: 4096 systems n=18..2000; "
+                         "large: one D=8 three-mode system n=17576 with U at 256 times")
     ap.add_argument("--serve-requests", type=int, default=240)
     ap.add_argument("--count", type=int, default=COUNT,
                     help="systems per step (64 = the benchmark workload; smaller for profiler captures)")
@@ -263,14 +267,22 @@ def main():
                                              "saturation_solves_per_s": res["saturation_solves_per_s"], **rr}}))
         return
     count = args.count
-    problems = W.spin1_amplitude_set(count, seed=1 + rank)
+    nt = NT
+    if args.workload == "uneven":
+        count = 4096 if args.count == COUNT else args.count
+        problems = W.uneven_batch(count, seed=0 + rank)
+    elif args.workload == "large":
+        count, nt = 1, 256
+        problems = [W.large_instance(seed=3 + rank)]
+    else:
+        problems = W.spin1_amplitude_set(count, seed=1 + rank)
     ctx = M.Context(local, stream=stream.cuda_stream)
     systems = [M.System(ctx, p) for p in problems]
-    batch = M.Batch(ctx, systems, prec, NT)
-    ts = np.stack([W.time_grid(p, NT) for p in problems])
+    batch = M.Batch(ctx, systems, prec, nt)
+    ts = np.stack([W.time_grid(p, nt) for p in problems])
     batch.set_times(0.0, ts)
 
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(args.warmup, 3 if args.workload != "large" else 1)):
         batch.run()
     st = batch.sync()
 
@@ -318,7 +330,7 @@ def main():
     # accuracy of system 0 against the stored oracle result
     acc = None
     gold = os.path.join(ROOT, "tests", "golden", "spin1_c1_sys0.npz")
-    if rank == 0 and os.path.exists(gold):
+    if rank == 0 and os.path.exists(gold) and args.workload == "spin1":
         g = np.load(gold)
         e, u, pp = batch.unpack(hE, hU, hP, 0)
         nrm = np.abs(g["E"]).max()
@@ -329,10 +341,13 @@ def main():
     per = {k: v / max(runs, 1) for k, v in stage.items()}
     n = problems[0].n
     mixed = prec == M.MMF_MIXED
-    modelled = {k: v for k, v in per.items() if stage_model(k, n, NT, mixed) is not None}
+    modelled = {k: v for k, v in per.items() if stage_model(k, n, nt, mixed) is not None}
     dom = max(modelled, key=modelled.get)
-    flops_sys, peak, peak_src = stage_model(dom, n, NT, mixed)
-    achieved = flops_sys * count / (per[dom] / 1e3) if per[dom] > 0 else 0.0
+    _, peak, peak_src = stage_model(dom, n, nt, mixed)
+    jac = 118 if mixed else 84  # systems at or below this size take the shared-memory Jacobi path
+    flops = sum(stage_model(dom, p.n, nt, mixed)[0] for p in problems
+                if dom not in ("hetrd", "backtransform") or p.n > jac)
+    achieved = flops / (per[dom] / 1e3) if per[dom] > 0 else 0.0
     kernel = {"hetrd": "k_hetrd", "backtransform": "k_backtransform", "refine_gram": "k_gram_df32",
               "outputs": "k_time_evolution"}[dom]
     roof = {"kernel": kernel, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
@@ -340,13 +355,13 @@ def main():
             "peak_source": peak_src + " (derived from unit counts and clock)"}
 
     serving = None
-    if rank == 0 and world == 1 and args.serve_requests > 0 and count == COUNT:
+    if rank == 0 and world == 1 and args.serve_requests > 0 and count == COUNT and args.workload == "spin1":
         sv = run_serving(M, W, ctx, prec, [0.75], args.serve_requests)
         serving = {"saturation_solves_per_s": sv["saturation_solves_per_s"], **sv["rates"][0],
                    "mix": "1/3 qubit n=82, 1/3 spin-1 n=1323, 1/3 uneven n<=2000; nt=64"}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "spin1":
         cpu = cpu_baseline_oracle(problems)
 
     if rank == 0:
@@ -355,15 +370,19 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if prec == M.MMF_FP64 else "f32+f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD if count == COUNT else f"{WORKLOAD}[:{count}]",
-                           "systems_per_step": count, "n": n, "nt": NT,
+                "config": {"workload": ("uneven_batch_n18_2000" if args.workload == "uneven" else
+                                        "large_D8_three_mode_n17576" if args.workload == "large" else
+                                        WORKLOAD if count == COUNT else f"{WORKLOAD}[:{count}]"),
+                           "systems_per_step": count, "n": n, "nt": nt,
                            "precision": args.precision, "l2": "working set > L2 (no flush)",
                            "parallelism": f"replicas x{world}"},
                 "stage_ms": {k: round(v, 3) for k, v in per.items()},
                 "roofline": roof, "clocks": clk.summary(), "gpu_launches": launches,
                 "e2e": {"value": count * world / e2e_s, "unit": "solves/s",
                         "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-                "accuracy_vs_oracle": acc, "status_max": int(st.max()), "serving": serving,
+                "accuracy_vs_oracle": acc, "status_max": int(st.max()),
+                "status_counts": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
+                "serving": serving,
                 "cpu_baseline": cpu}
         print(json.dumps(line))
     if world > 1:

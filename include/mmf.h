@@ -49,6 +49,8 @@ extern "C" {
 #define MMF_ERR_NOMEM -6      /* host allocation failed */
 #define MMF_ST_NOCONV 1       /* an iteration reached its cap (Jacobi sweeps, bisection) */
 #define MMF_ST_NONFINITE 2    /* NaN or Inf met in the input or a result */
+#define MMF_ST_CLUSTER 3      /* mixed refinement met a cluster of more than 32 close eigenvalues:
+                                 its vectors are orthonormal but not separated inside the cluster */
 
 /* ---------------------------------------------------------------- precision */
 #define MMF_FP64 0   /* every step in FP64 */
@@ -71,6 +73,15 @@ MMF_API int mmf_ctx_destroy(mmf_ctx* ctx);
 /* Device bytes currently held by the context's batches. */
 MMF_API size_t mmf_ctx_bytes_in_use(const mmf_ctx* ctx);
 MMF_API size_t mmf_ctx_budget(const mmf_ctx* ctx);
+/* Size thresholds of the solver paths for batches created afterwards (value < 0 restores the
+ * default): MMF_OPT_JACOBI_N_FP64 / _MIXED: largest n solved by the shared-memory Jacobi kernel
+ * (defaults 84 / 118, also the maxima); MMF_OPT_LARGE_N: smallest n reduced by the whole-GPU
+ * Householder reduction, one system at a time (default: sizes one CTA's shared memory cannot
+ * hold).  Results do not depend on the path beyond rounding. */
+#define MMF_OPT_JACOBI_N_FP64 1
+#define MMF_OPT_JACOBI_N_MIXED 2
+#define MMF_OPT_LARGE_N 3
+MMF_API int mmf_ctx_set_option(mmf_ctx* ctx, int option, int64_t value);
 
 /* ---------------------------------------------------------------- system definition
  * The paper's set-up step (Sec. 3.1: the ATOM type, the harmonics array and the MODE
@@ -132,6 +143,10 @@ MMF_API int mmf_batch_set_times(mmf_batch* b, double t0, const double* t);
 MMF_API int mmf_batch_upload(mmf_batch* b);
 /* Enqueues S1-S8 for every system on the context stream; returns without waiting. */
 MMF_API int mmf_batch_run(mmf_batch* b);
+/* enable != 0: the next mmf_batch_run captures the whole launch sequence (S1-S8) of the batch
+ * into a CUDA graph, and later runs replay it with one graph launch.  Changing t0 or the timing
+ * set-up re-captures.  enable = 0 returns to plain launches. */
+MMF_API int mmf_batch_graph(mmf_batch* b, int enable);
 /* Waits for the batch; status (count ints, may be NULL) receives each system's numerical
  * status.  Returns the largest status. */
 MMF_API int mmf_batch_sync(mmf_batch* b, int* status);
@@ -205,6 +220,15 @@ MMF_API int mmf_serve_destroy(mmf_server* srv);
 #define MMF_NOALLOC_TRIDIAG_NMAX 256
 MMF_API int mmf_tridiag_eig_noalloc(const double* d, const double* e, int n, double* E, double* Y,
                                     void* stream);
+
+/* ---------------------------------------------------------------- diagnostics
+ * Runs the library's batched tcgen05 GEMM (kind 0: TF32, kind 1: BF16; `products` copies of the
+ * same product summed in one TMEM accumulator) on seeded M x K and N x K operands whose products
+ * are exact, and compares C = products * A B^T with an FP64 reference computed on the device.
+ * Returns the largest absolute difference and the largest |reference| entry.  Allocates its own
+ * device memory; for health checks, not for the solve path. */
+MMF_API int mmf_selftest_tensor_cores(int M, int N, int K, int kind, int products, double* max_abs_err,
+                                      double* max_abs_ref);
 
 /* ---------------------------------------------------------------- misc */
 MMF_API const char* mmf_strerror(int status);

@@ -17,11 +17,18 @@
 // Result: d (diagonal), e = beta (sub-diagonal, real), tau, and v[k+2:] stored in
 // A(k+2:, k).  Q = P_0 P_1 ... P_{n-2}, Q^H H_F Q = tridiag(e, d, e).
 //
-// One CTA per system, 512 threads.  The hemv streams the lower triangle of the trailing
-// matrix once per column with coalesced column reads: a warp owns 8 columns, lanes own
-// rows, the row part accumulates through shared-memory atomics and the column part by
-// warp-shuffle reductions.
+// One thread-block cluster of CL CTAs (512 threads each) per system.  The hemv streams the
+// lower triangle of the trailing matrix once per column with coalesced column reads: a warp
+// owns 8 columns, lanes own rows, the row part accumulates through shared-memory atomics and
+// the column part by warp-shuffle reductions.  With CL = 2 the two CTAs of the cluster split the
+// column blocks of the hemv, the rows of the column update and the tiles of the trailing
+// update; each adds its partner's partial hemv result through distributed shared memory and
+// repeats the short O(m) vector steps itself.
+#include <cooperative_groups.h>
+
 #include "mmf_internal.h"
+
+namespace cg = cooperative_groups;
 
 #define HT_THREADS 512
 #define HT_TILE 64
@@ -51,7 +58,7 @@ __device__ __forceinline__ void atomic_add_c(float2* p, float2 v) {
     atomicAdd(&p->y, v.y);
 }
 
-template <class R>
+template <class R, int CL>
 __global__ void __launch_bounds__(HT_THREADS, 1)
 k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
         typename Cx<R>::T* __restrict__ H, typename Cx<R>::T* __restrict__ Vpool,
@@ -60,8 +67,9 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* vS = reinterpret_cast<C*>(smem_raw);   // nmax
-    C* yS = vS + nmax;                          // nmax
-    C* tVr = yS + nmax;                         // MMF_NB x HT_TILE (her2k staging, transposed)
+    C* yS = vS + nmax;                          // nmax: this CTA's partial y = A22 v
+    C* yF = yS + nmax;                          // nmax: full y (CL = 2)
+    C* tVr = yF + nmax;                         // MMF_NB x HT_TILE (her2k staging, transposed)
     C* tWr = tVr + MMF_NB * HT_TILE;
     C* tVc = tWr + MMF_NB * HT_TILE;
     C* tWc = tVc + MMF_NB * HT_TILE;
@@ -72,7 +80,9 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
     C* sc = xv + MMF_NB;                        // 4 scalars: tau, scale, alpha2
     R* red = reinterpret_cast<R*>(sc + 4);      // 33
 
-    const MmfDesc d = descs[idx[blockIdx.x]];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (CL > 1) ? (int)cluster.block_rank() : 0;
+    const MmfDesc d = descs[idx[blockIdx.x / CL]];
     const int n = d.n, ld = d.ld;
     C* A = H + d.mat_off;
     C* V = Vpool + d.pan_off;
@@ -94,15 +104,15 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                     vk[tid] = conj(V[k + (int64_t)tid * ld]);
                 }
                 __syncthreads();
-                for (int r = k + tid; r < n; r += HT_THREADS) {
+                for (int r = k + rank * HT_THREADS + tid; r < n; r += CL * HT_THREADS) {
                     C acc = czero<C>();
                     for (int c = 0; c < i; ++c)
                         acc = acc + V[r + (int64_t)c * ld] * wk[c] + W[r + (int64_t)c * ld] * vk[c];
                     A[r + (int64_t)k * ld] = A[r + (int64_t)k * ld] - acc;
                 }
-                __syncthreads();
+                if (CL > 1) cluster.sync(); else __syncthreads();
             }
-            if (tid == 0) dd[k] = (double)A[k + (int64_t)k * ld].x;
+            if (tid == 0 && rank == 0) dd[k] = (double)A[k + (int64_t)k * ld].x;
             if (k == n - 1) break;
             const int m = n - k - 1;
             C* col = A + (int64_t)k * ld;
@@ -126,8 +136,10 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                     R dn = abs2(den);
                     s = mk(den.x / dn, -den.y / dn);
                 }
-                ee[k] = (double)beta;
-                tau[k] = t;
+                if (rank == 0) {
+                    ee[k] = (double)beta;
+                    tau[k] = t;
+                }
                 sc[0] = t;
                 sc[1] = s;
             }
@@ -141,13 +153,13 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                     v = mk(R(1), R(0));
                 } else {
                     v = col[r] * scale;
-                    col[r] = v;
+                    if (CL == 1) col[r] = v;  // with a partner CTA still reading col, stored below
                 }
                 if (r > k) {
                     vS[r - k - 1] = v;
                     yS[r - k - 1] = czero<C>();
                 }
-                V[r + (int64_t)i * ld] = v;
+                if (rank == 0) V[r + (int64_t)i * ld] = v;
             }
             __syncthreads();
 
@@ -155,6 +167,7 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
             const C* a22 = A + (k + 1) + (int64_t)(k + 1) * ld;
             const int nblk = (m + 7) >> 3;
             for (int task = warp; task < 2 * i + nblk; task += NW) {
+                if (task >= 2 * i && ((task - 2 * i) % CL) != rank) continue;
                 if (task < 2 * i) {
                     const int c = task >> 1;
                     const C* P = (task & 1) ? V : W;
@@ -220,28 +233,43 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                     }
                 }
             }
-            __syncthreads();
+            if (CL > 1) {
+                cluster.sync();  // both partial y complete
+                const C* yP = cluster.map_shared_rank(yS, rank ^ 1);
+                for (int rp = tid; rp < m; rp += HT_THREADS) yF[rp] = yS[rp] + yP[rp];
+                __syncthreads();
+            } else {
+                __syncthreads();  // y complete
+            }
+            const C* yT = (CL > 1) ? yF : yS;
 
             // (d) corrections, (e) w = tau y - (1/2) tau (w^H v) v
             C dpart = czero<C>();
             for (int rp = tid; rp < m; rp += HT_THREADS) {
-                C y = yS[rp];
+                C y = yT[rp];
                 for (int c = 0; c < i; ++c)
                     y = y - V[(k + 1 + rp) + (int64_t)c * ld] * xw[c] -
                         W[(k + 1 + rp) + (int64_t)c * ld] * xv[c];
                 C w = tk * y;
-                yS[rp] = w;
+                yF[rp] = w;
                 dpart = dpart + cmulc(w, vS[rp]);
             }
             R dx = block_sum(dpart.x, red);
             R dy = block_sum(dpart.y, red);
             const C alpha2 = R(-0.5) * (tk * mk(dx, dy));
-            for (int r = tid; r < n; r += HT_THREADS) {
-                C w = czero<C>();
-                if (r > k) w = yS[r - k - 1] + alpha2 * vS[r - k - 1];
-                W[r + (int64_t)i * ld] = w;
+            if (rank == 0)
+                for (int r = tid; r < n; r += HT_THREADS) {
+                    C w = czero<C>();
+                    if (r > k) w = yF[r - k - 1] + alpha2 * vS[r - k - 1];
+                    W[r + (int64_t)i * ld] = w;
+                }
+            if (CL > 1) {
+                cluster.sync();  // both CTAs are done with column k
+                if (rank == 0)
+                    for (int r = k + 2 + tid; r < n; r += HT_THREADS) col[r] = vS[r - k - 1];
+            } else {
+                __syncthreads();
             }
-            __syncthreads();
         }
 
         // trailing her2k on the lower triangle of A(c0:, c0:)
@@ -249,8 +277,10 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
         if (c0 < n) {
             const int nt = (n - c0 + HT_TILE - 1) / HT_TILE;
             const int rr = tid & (HT_TILE - 1), cg = tid / HT_TILE;  // 8 column groups
+            int tcount = 0;
             for (int ti = 0; ti < nt; ++ti) {
                 for (int tj = 0; tj <= ti; ++tj) {
+                    if ((tcount++ % CL) != rank) continue;
                     const int rbase = c0 + ti * HT_TILE, cbase = c0 + tj * HT_TILE;
                     for (int e = tid; e < nb * HT_TILE; e += HT_THREADS) {
                         const int p = e / HT_TILE, q = e - p * HT_TILE;
@@ -284,37 +314,57 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                     __syncthreads();
                 }
             }
+            if (CL > 1) cluster.sync();
         }
     }
 }
 
 static size_t hetrd_smem(int nmax, int fp32) {
     size_t cs = fp32 ? 8 : 16, rs = fp32 ? 4 : 8;
-    return cs * (2 * (size_t)nmax + 4 * MMF_NB * HT_TILE + 4 * MMF_NB + 4) + rs * 40;
+    return cs * (3 * (size_t)nmax + 4 * MMF_NB * HT_TILE + 4 * MMF_NB + 4) + rs * 40;
 }
 
 int mmf_hetrd_max_n(int fp32) {
     size_t cs = fp32 ? 8 : 16, rs = fp32 ? 4 : 8;
     size_t fixed = cs * (4 * MMF_NB * HT_TILE + 4 * MMF_NB + 4) + rs * 40;
-    return (int)((227 * 1024 - fixed) / (2 * cs));
+    return (int)((227 * 1024 - fixed) / (3 * cs));
+}
+
+template <class R, int CL>
+static cudaError_t launch_hetrd(const MmfLaunch& L, void* H, void* Vp, void* Wp, double* dvec,
+                                double* evec, void* tau, size_t sm) {
+    typedef typename Cx<R>::T C;
+    cudaError_t err = cudaFuncSetAttribute(k_hetrd<R, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(L.count * CL);
+    cfg.blockDim = dim3(HT_THREADS);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_hetrd<R, CL>, L.desc, L.idx, (C*)H, (C*)Vp, (C*)Wp, dvec, evec,
+                              (C*)tau, L.nmax);
 }
 
 cudaError_t mmf_launch_hetrd(const MmfLaunch& L, void* H, void* Vp, void* Wp, double* dvec,
                              double* evec, void* tau, int fp32) {
     if (L.count <= 0) return cudaSuccess;
     if (L.nmax > mmf_hetrd_max_n(fp32)) return cudaErrorInvalidValue;
-    size_t sm = hetrd_smem(L.nmax, fp32);
-    cudaError_t err;
-    if (fp32) {
-        err = cudaFuncSetAttribute(k_hetrd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (err != cudaSuccess) return err;
-        k_hetrd<float><<<L.count, HT_THREADS, sm, L.stream>>>(L.desc, L.idx, (float2*)H, (float2*)Vp,
-                                                              (float2*)Wp, dvec, evec, (float2*)tau, L.nmax);
-    } else {
-        err = cudaFuncSetAttribute(k_hetrd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (err != cudaSuccess) return err;
-        k_hetrd<double><<<L.count, HT_THREADS, sm, L.stream>>>(L.desc, L.idx, (double2*)H, (double2*)Vp,
-                                                               (double2*)Wp, dvec, evec, (double2*)tau, L.nmax);
-    }
-    return cudaGetLastError();
+    const size_t sm = hetrd_smem(L.nmax, fp32);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // two CTAs per system while that still fits the GPU in one wave
+    const bool pair = 2 * L.count <= sms;
+    if (fp32)
+        return pair ? launch_hetrd<float, 2>(L, H, Vp, Wp, dvec, evec, tau, sm)
+                    : launch_hetrd<float, 1>(L, H, Vp, Wp, dvec, evec, tau, sm);
+    return pair ? launch_hetrd<double, 2>(L, H, Vp, Wp, dvec, evec, tau, sm)
+                : launch_hetrd<double, 1>(L, H, Vp, Wp, dvec, evec, tau, sm);
 }

@@ -10,10 +10,11 @@
 //   Pbar_{i->j} = sum_b sum_C | sum_{l in C} Z[(j, b), l] conj(Z[(i, b0), l]) |^2
 #include "mmf_internal.h"
 
+// F is stored pre-split into FP32 pieces (Split) for the double-FP32 contraction below.
 __global__ void __launch_bounds__(256) k_phase_table(const MmfDesc* __restrict__ descs,
                                                      const int* __restrict__ idx,
                                                      const double* __restrict__ tpool, int nt,
-                                                     double2* __restrict__ F) {
+                                                     Split* __restrict__ F) {
     const MmfDesc d = descs[idx[blockIdx.y]];
     const int tot = nt * d.M;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
@@ -21,19 +22,21 @@ __global__ void __launch_bounds__(256) k_phase_table(const MmfDesc* __restrict__
         double arg = block_ndotw(d, b) * tpool[d.t_off + t];
         double s, c;
         sincos(arg, &s, &c);
-        F[d.f_off + e] = make_double2(c, -s);
+        F[d.f_off + e] = split(make_double2(c, -s));
     }
 }
 
 #define U_TPW 8  // times per warp per pass (8 warps -> 64 times per pass)
 
+// Phi is accumulated FP64-accurately in double-FP32 (the FP64 units of GB300 are ~60x slower
+// than its FP32 units); the short contraction with the phases and Z0 is done in FP64.
 __global__ void __launch_bounds__(256) k_time_evolution(const MmfDesc* __restrict__ descs,
                                                         const int* __restrict__ idx,
                                                         const double* __restrict__ Eg,
                                                         const double2* __restrict__ Zg,
                                                         const double* __restrict__ tpool,
                                                         double t0, int nt,
-                                                        const double2* __restrict__ F,
+                                                        const Split* __restrict__ F,
                                                         double2* __restrict__ U) {
     const MmfDesc d = descs[idx[blockIdx.y]];
     const int n = d.n, D = d.D, M = d.M;
@@ -43,7 +46,7 @@ __global__ void __launch_bounds__(256) k_time_evolution(const MmfDesc* __restric
     const bool valid = lam < n;
     const double2* Zc = Zg + d.mat_off + (int64_t)(valid ? lam : 0) * d.ld;
     const double El = valid ? Eg[d.vec_off + lam] : 0.0;
-    const double2* Ft = F + d.f_off;
+    const Split* Ft = F + d.f_off;
     const double* tt = tpool + d.t_off;
     double2* Uo = U + d.u_off;
 
@@ -57,19 +60,19 @@ __global__ void __launch_bounds__(256) k_time_evolution(const MmfDesc* __restric
             ph[q] = make_double2(c, -s);
         }
         for (int j = 0; j < D; ++j) {
-            double2 acc[U_TPW];
+            DF ar[U_TPW], ai[U_TPW];
 #pragma unroll
-            for (int q = 0; q < U_TPW; ++q) acc[q] = make_double2(0.0, 0.0);
+            for (int q = 0; q < U_TPW; ++q) ar[q] = ai[q] = DF{0.f, 0.f};
             for (int b = 0; b < M; ++b) {
-                double2 z = valid ? Zc[j + D * b] : make_double2(0.0, 0.0);
+                const Split z = split(valid ? Zc[j + D * b] : make_double2(0.0, 0.0));
 #pragma unroll
                 for (int q = 0; q < U_TPW; ++q) {
                     int t = tbase + warp + 8 * q;
-                    if (t < nt) {
-                        double2 f = Ft[(int64_t)t * M + b];
-                        acc[q].x = fma(f.x, z.x, fma(-f.y, z.y, acc[q].x));
-                        acc[q].y = fma(f.x, z.y, fma(f.y, z.x, acc[q].y));
-                    }
+                    if (t < nt) df_cmac(ar[q], ai[q], Ft[(int64_t)t * M + b], z);
+                }
+                if ((b & 31) == 31) {
+#pragma unroll
+                    for (int q = 0; q < U_TPW; ++q) { df_renorm(ar[q]); df_renorm(ai[q]); }
                 }
             }
             for (int i = 0; i < D; ++i) {
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(256) k_time_evolution(const MmfDesc* __restric
 #pragma unroll
                 for (int q = 0; q < U_TPW; ++q) {
                     int t = tbase + warp + 8 * q;
-                    double2 v = cmulc(z0, acc[q] * ph[q]);  // conj(z0) * Phi * phase
+                    double2 v = cmulc(z0, df_value(ar[q], ai[q]) * ph[q]);  // conj(z0) * Phi * phase
                     v.x = warp_sum(v.x);
                     v.y = warp_sum(v.y);
                     if (lane == 0 && t < nt) {
@@ -143,7 +146,9 @@ __global__ void __launch_bounds__(256) k_transition_avg(const MmfDesc* __restric
 // Staged launcher with explicit maxima (the batch knows them).
 cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const double* E,
                                   const double2* Z, const double* t, double t0, int nt,
-                                  double2* F, double2* U, double* P, double cluster_rel) {
+                                  double2* F2, double2* U, double* P, double cluster_rel) {
+    static_assert(sizeof(Split) == sizeof(double2), "phase table slots hold one Split each");
+    Split* F = reinterpret_cast<Split*>(F2);
     if (L.count <= 0) return cudaSuccess;
     if (nt > 0) {
         int gx = (nt * Mmax + 255) / 256;

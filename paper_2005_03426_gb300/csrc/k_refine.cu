@@ -68,50 +68,29 @@ __global__ void __launch_bounds__(256) k_apply_hf(const MmfDesc* __restrict__ de
     }
 }
 
-// ------------------------------------------------------------------ double-FP32 helpers
-struct DF {
-    float hi, lo;
-};
-
-// acc += a * b with a = a1 + a2, b = b1 + b2 (FP32 pieces of FP64 values)
-__device__ __forceinline__ void df_mac(DF& acc, float a1, float a2, float b1, float b2) {
-    const float p = a1 * b1;
-    const float e = fmaf(a1, b1, -p);
-    const float c = fmaf(a1, b2, a2 * b1);
-    const float s = acc.hi + p;
-    const float bb = s - acc.hi;
-    const float err = (acc.hi - (s - bb)) + (p - bb);
-    acc.hi = s;
-    acc.lo += err + e + c;
-}
-__device__ __forceinline__ void df_renorm(DF& a) {
-    const float s = a.hi + a.lo;
-    a.lo = a.lo - (s - a.hi);
-    a.hi = s;
-}
-
-struct Split {  // FP32 pieces of one complex FP64 value
-    float r1, r2, i1, i2;
-};
-__device__ __forceinline__ Split split(double2 v) {
-    Split s;
-    s.r1 = __double2float_rn(v.x);
-    s.r2 = __double2float_rn(v.x - (double)s.r1);
-    s.i1 = __double2float_rn(v.y);
-    s.i2 = __double2float_rn(v.y - (double)s.i1);
-    return s;
-}
-
-// conj(a) * b accumulated into (re, im)
-__device__ __forceinline__ void df_cmacc(DF& re, DF& im, const Split& a, const Split& b) {
-    df_mac(re, a.r1, a.r2, b.r1, b.r2);
-    df_mac(re, a.i1, a.i2, b.i1, b.i2);
-    df_mac(im, a.r1, a.r2, b.i1, b.i2);
-    df_mac(im, -a.i1, -a.i2, b.r1, b.r2);
-}
-
 // ------------------------------------------------------------------ G = X^H X, S = X^H HX
-// Upper-triangle tiles (I <= J) of 32 x 32; both triangles are written.
+// Upper-triangle tiles (I <= J) of 32 x 32; both triangles are written.  X1 = true: X holds
+// FP32-exact values (the first refinement step), so its second pieces vanish and are skipped.
+template <bool X1>
+__device__ __forceinline__ void gram_cmacc(DF& gre, DF& gim, DF& sre, DF& sim, const Split& a,
+                                           const Split& b, const Split& h) {
+    if (X1) {
+        // conj(a) b with a, b FP32-exact; conj(a) h with h split
+        df_mac11(gre, a.r1, b.r1);
+        df_mac11(gre, a.i1, b.i1);
+        df_mac11(gim, a.r1, b.i1);
+        df_mac11(gim, -a.i1, b.r1);
+        df_mac1(sre, a.r1, h.r1, h.r2);
+        df_mac1(sre, a.i1, h.i1, h.i2);
+        df_mac1(sim, a.r1, h.i1, h.i2);
+        df_mac1(sim, -a.i1, h.r1, h.r2);
+    } else {
+        df_cmacc(gre, gim, a, b);
+        df_cmacc(sre, sim, a, h);
+    }
+}
+
+template <bool X1>
 __global__ void __launch_bounds__(256) k_gram_df32(const MmfDesc* __restrict__ descs,
                                                    const int* __restrict__ idx,
                                                    const double2* __restrict__ Xg,
@@ -155,14 +134,10 @@ __global__ void __launch_bounds__(256) k_gram_df32(const MmfDesc* __restrict__ d
             const Split a0 = xi[kk][ty], a1 = xi[kk][ty + 16];
             const Split b0 = xj[kk][tx], b1 = xj[kk][tx + 16];
             const Split h0 = hj[kk][tx], h1 = hj[kk][tx + 16];
-            df_cmacc(gr[0][0], gi[0][0], a0, b0);
-            df_cmacc(gr[0][1], gi[0][1], a0, b1);
-            df_cmacc(gr[1][0], gi[1][0], a1, b0);
-            df_cmacc(gr[1][1], gi[1][1], a1, b1);
-            df_cmacc(sr[0][0], si[0][0], a0, h0);
-            df_cmacc(sr[0][1], si[0][1], a0, h1);
-            df_cmacc(sr[1][0], si[1][0], a1, h0);
-            df_cmacc(sr[1][1], si[1][1], a1, h1);
+            gram_cmacc<X1>(gr[0][0], gi[0][0], sr[0][0], si[0][0], a0, b0, h0);
+            gram_cmacc<X1>(gr[0][1], gi[0][1], sr[0][1], si[0][1], a0, b1, h1);
+            gram_cmacc<X1>(gr[1][0], gi[1][0], sr[1][0], si[1][0], a1, b0, h0);
+            gram_cmacc<X1>(gr[1][1], gi[1][1], sr[1][1], si[1][1], a1, b1, h1);
         }
 #pragma unroll
         for (int a = 0; a < 2; ++a)
@@ -180,10 +155,8 @@ __global__ void __launch_bounds__(256) k_gram_df32(const MmfDesc* __restrict__ d
         for (int b = 0; b < 2; ++b) {
             const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
             if (i < n && j < n && (I < J || i <= j)) {
-                double2 g = make_double2((double)gr[a][b].hi + (double)gr[a][b].lo,
-                                         (double)gi[a][b].hi + (double)gi[a][b].lo);
-                double2 s = make_double2((double)sr[a][b].hi + (double)sr[a][b].lo,
-                                         (double)si[a][b].hi + (double)si[a][b].lo);
+                double2 g = df_value(gr[a][b], gi[a][b]);
+                double2 s = df_value(sr[a][b], si[a][b]);
                 if (i == j) { g.y = 0.0; s.y = 0.0; }
                 G[(int64_t)j * d.ld + i] = g;
                 S[(int64_t)j * d.ld + i] = s;
@@ -340,52 +313,207 @@ __global__ void __launch_bounds__(256) k_xe_update(const MmfDesc* __restrict__ d
         }
 }
 
+// ------------------------------------------------------------------ Xn = X + X Et on tensor cores
+// The complex product is a real product of twice the size,
+//   [Re Y | Im Y] = [Re X, Im X] [[Re E, Im E], [-Im E, Re E]],
+// taken on the tcgen05 engine in split TF32 (x = x1 + x2, x1 = tf32(x), x2 = tf32(x - x1);
+// x y ~ x1 y1 + x1 y2 + x2 y1, about FP32 accuracy; Et is small, so that is ample).  Operands are
+// K-major rows of la = round_up(2n, 4) floats, placed in buffers free at this point:
+// B1 -> S, B2 -> HX (2n rows), A1 -> Zp (n rows), A2 and then C (n x 2n) -> the Et buffer after
+// B has been built from it.
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ int xe_la(int n) { return (2 * n + 3) & ~3; }
+
+__global__ void __launch_bounds__(256) k_xe_prep_B(const MmfDesc* __restrict__ descs,
+                                                   const int* __restrict__ idx,
+                                                   const double2* __restrict__ Etg,
+                                                   double2* __restrict__ B1g, double2* __restrict__ B2g) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n, la = xe_la(n);
+    const double2* Et = Etg + d.mat_off;
+    float* B1 = reinterpret_cast<float*>(B1g + d.mat_off);
+    float* B2 = reinterpret_cast<float*>(B2g + d.mat_off);
+    const int64_t tot = (int64_t)2 * n * la;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / la), k = (int)(e - (int64_t)j * la);
+        float v = 0.f;
+        if (k < 2 * n) {
+            const int jj = j < n ? j : j - n, kk = k < n ? k : k - n;
+            const double2 x = Et[(int64_t)jj * d.ld + kk];
+            double w;
+            if (j < n) w = (k < n) ? x.x : -x.y;
+            else w = (k < n) ? x.y : x.x;
+            v = (float)w;
+        }
+        const float v1 = tf32_round(v);
+        B1[e] = v1;
+        B2[e] = tf32_round(v - v1);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_xe_prep_A(const MmfDesc* __restrict__ descs,
+                                                   const int* __restrict__ idx,
+                                                   const double2* __restrict__ Xg,
+                                                   float2* __restrict__ A1g, double2* __restrict__ A2g) {
+    __shared__ double2 t[32][33];
+    const MmfDesc d = descs[idx[blockIdx.z]];
+    const int n = d.n, la = xe_la(n);
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    if (r0 >= n || c0 >= n) return;
+    const double2* X = Xg + d.mat_off;
+    float* A1 = reinterpret_cast<float*>(A1g + d.mat_off);
+    float* A2 = reinterpret_cast<float*>(A2g + d.mat_off);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int q = ty; q < 32; q += 8) {  // X(r0 + tx, c0 + q), rows fastest
+        const int r = r0 + tx, c = c0 + q;
+        t[q][tx] = (r < n && c < n) ? X[(int64_t)c * d.ld + r] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int q = ty; q < 32; q += 8) {  // A[r0 + q][c0 + tx] (re) and A[r0 + q][n + c0 + tx] (im)
+        const int r = r0 + q, c = c0 + tx;
+        if (r < n && c < n) {
+            const double2 x = t[tx][q];
+            const float re = (float)x.x, im = (float)x.y;
+            const float re1 = tf32_round(re), im1 = tf32_round(im);
+            A1[(int64_t)r * la + c] = re1;
+            A2[(int64_t)r * la + c] = tf32_round(re - re1);
+            A1[(int64_t)r * la + n + c] = im1;
+            A2[(int64_t)r * la + n + c] = tf32_round(im - im1);
+        }
+        if (r < n && c0 + 32 >= n && tx < la - 2 * n) {  // zero the row padding
+            A1[(int64_t)r * la + 2 * n + tx] = 0.f;
+            A2[(int64_t)r * la + 2 * n + tx] = 0.f;
+        }
+    }
+}
+
+__global__ void k_xe_jobs(const MmfDesc* __restrict__ descs, const int* __restrict__ idx, int count,
+                          float2* Zp, double2* R, double2* S, double2* HX, UmmaJob* jobs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const MmfDesc d = descs[idx[i]];
+    const int n = d.n, la = xe_la(n);
+    const float* A1 = reinterpret_cast<const float*>(Zp + d.mat_off);
+    const float* A2 = reinterpret_cast<const float*>(R + d.mat_off);
+    const float* B1 = reinterpret_cast<const float*>(S + d.mat_off);
+    const float* B2 = reinterpret_cast<const float*>(HX + d.mat_off);
+    UmmaJob j;
+    j.A[0] = A1; j.B[0] = B1;
+    j.A[1] = A1; j.B[1] = B2;
+    j.A[2] = A2; j.B[2] = B1;
+    j.C = reinterpret_cast<float*>(R + d.mat_off) + (int64_t)n * la;
+    j.M = n; j.N = 2 * n; j.K = 2 * n;
+    j.lda = la; j.ldb = la; j.ldc = 2 * n;
+    jobs[i] = j;
+}
+
+__global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ descs,
+                                                  const int* __restrict__ idx, double2* __restrict__ Xg,
+                                                  const double2* __restrict__ R) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n, la = xe_la(n);
+    const float* C = reinterpret_cast<const float*>(R + d.mat_off) + (int64_t)n * la;
+    double2* X = Xg + d.mat_off;
+    const int64_t tot = (int64_t)n * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / n), r = (int)(e - (int64_t)j * n);  // X(r, j), rows fastest
+        const double2 x = X[(int64_t)j * d.ld + r];
+        const float yr = C[(int64_t)r * 2 * n + j], yi = C[(int64_t)r * 2 * n + n + j];
+        X[(int64_t)j * d.ld + r] = make_double2(x.x + (double)yr, x.y + (double)yi);
+    }
+}
+
 // ------------------------------------------------------------------ cluster separation
 // One CTA per system; clusters handled one after another.  For cluster C (m vectors):
 // B = X_C^H H_F X_C in FP64 (H_F X_C from the HX buffer, recomputed for the new X), cyclic
 // Jacobi on B, X_C <- X_C W, lam_C <- eigenvalues of B ascending.
-__device__ void small_jacobi(double2* B, double2* W, int m, double* w) {
-    // single-thread cyclic complex Jacobi on m x m (column-major, ld = RF_CMAX)
-    for (int i = 0; i < m; ++i)
-        for (int j = 0; j < m; ++j) W[i + j * RF_CMAX] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-    for (int sweep = 0; sweep < 30; ++sweep) {
-        double off = 0.0, fro = 0.0;
-        for (int j = 0; j < m; ++j)
-            for (int i = 0; i < m; ++i) {
-                double a = abs2(B[i + j * RF_CMAX]);
-                fro += a;
-                if (i != j) off += a;
-            }
-        if (off <= 1e-32 * fro || off == 0.0) break;
-        for (int p = 0; p < m - 1; ++p)
-            for (int q = p + 1; q < m; ++q) {
-                const double2 apq = B[p + q * RF_CMAX];
-                const double r = sqrt(abs2(apq));
-                if (r == 0.0) continue;
-                const double app = B[p + p * RF_CMAX].x, aqq = B[q + q * RF_CMAX].x;
-                const double2 em = make_double2(apq.x / r, -apq.y / r);  // e^{-i phi}
-                const double th = (aqq - app) / (2.0 * r);
-                const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
-                const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-                for (int k = 0; k < m; ++k) {  // columns
-                    const double2 bp = B[k + p * RF_CMAX], bq = B[k + q * RF_CMAX] * em;
-                    B[k + p * RF_CMAX] = c * bp - s * bq;
-                    B[k + q * RF_CMAX] = s * bp + c * bq;
-                    const double2 wp = W[k + p * RF_CMAX], wq = W[k + q * RF_CMAX] * em;
-                    W[k + p * RF_CMAX] = c * wp - s * wq;
-                    W[k + q * RF_CMAX] = s * wp + c * wq;
-                }
-                const double2 ep = conj(em);
-                for (int k = 0; k < m; ++k) {  // rows
-                    const double2 bp = B[p + k * RF_CMAX], bq = ep * B[q + k * RF_CMAX];
-                    B[p + k * RF_CMAX] = c * bp - s * bq;
-                    B[q + k * RF_CMAX] = s * bp + c * bq;
-                }
-                B[p + q * RF_CMAX] = B[q + p * RF_CMAX] = make_double2(0.0, 0.0);
-                B[p + p * RF_CMAX].y = B[q + q * RF_CMAX].y = 0.0;
-            }
+// CTA-parallel two-sided Jacobi on the m x m Hermitian B (column-major, ld RF_CMAX), with the
+// round-robin pivot order: each round rotates m/2 disjoint pairs at once.  W accumulates the
+// rotations; w receives the eigenvalues (unsorted).  All threads of the CTA call it.
+__device__ void cta_jacobi(double2* B, double2* W, int m, double* w, double* rot, int* pq, int* flag) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int mm = (m + 1) & ~1;
+    for (int e = tid; e < m * m; e += T) {
+        const int i = e % m, j = e / m;
+        W[i + j * RF_CMAX] = make_double2(i == j ? 1.0 : 0.0, 0.0);
     }
-    for (int i = 0; i < m; ++i) w[i] = B[i + i * RF_CMAX].x;
+    __syncthreads();
+    double fro = 0.0;
+    for (int e = 0; e < m * m; ++e) fro += abs2(B[(e % m) + (e / m) * RF_CMAX]);
+    const double thr = 2.220446049250313e-16 * sqrt(fro);
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        if (tid == 0) *flag = 0;
+        __syncthreads();
+        for (int round = 0; round < mm - 1; ++round) {
+            for (int k = tid; k < mm / 2; k += T) {
+                const int a0 = (k == 0) ? 0 : ((k - 1 + round) % (mm - 1)) + 1;
+                const int b0 = ((mm - 1 - k - 1 + round) % (mm - 1)) + 1;
+                const int p = a0 < b0 ? a0 : b0, q = a0 < b0 ? b0 : a0;
+                pq[2 * k] = p;
+                pq[2 * k + 1] = q;
+                double c = 1.0, sn = 0.0, cf = 1.0, sf = 0.0;
+                if (q < m) {
+                    const double2 apq = B[p + q * RF_CMAX];
+                    const double r = sqrt(abs2(apq));
+                    if (r > thr) {
+                        const double app = B[p + p * RF_CMAX].x, aqq = B[q + q * RF_CMAX].x;
+                        cf = apq.x / r;
+                        sf = apq.y / r;
+                        const double th = (aqq - app) / (2.0 * r);
+                        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        sn = t * c;
+                        *flag = 1;
+                    }
+                }
+                rot[4 * k] = c; rot[4 * k + 1] = sn; rot[4 * k + 2] = cf; rot[4 * k + 3] = sf;
+            }
+            __syncthreads();
+            for (int e = tid; e < (mm / 2) * m; e += T) {  // columns of B and W
+                const int k = e / m, r = e - k * m;
+                const int p = pq[2 * k], q = pq[2 * k + 1];
+                if (q >= m || rot[4 * k + 1] == 0.0) continue;
+                const double c = rot[4 * k], sn = rot[4 * k + 1];
+                const double2 em = make_double2(rot[4 * k + 2], -rot[4 * k + 3]);
+                const double2 bp = B[r + p * RF_CMAX], bq = B[r + q * RF_CMAX] * em;
+                B[r + p * RF_CMAX] = c * bp - sn * bq;
+                B[r + q * RF_CMAX] = sn * bp + c * bq;
+                const double2 wp = W[r + p * RF_CMAX], wq = W[r + q * RF_CMAX] * em;
+                W[r + p * RF_CMAX] = c * wp - sn * wq;
+                W[r + q * RF_CMAX] = sn * wp + c * wq;
+            }
+            __syncthreads();
+            for (int e = tid; e < (mm / 2) * m; e += T) {  // rows of B
+                const int k = e / m, col = e - k * m;
+                const int p = pq[2 * k], q = pq[2 * k + 1];
+                if (q >= m || rot[4 * k + 1] == 0.0) continue;
+                const double c = rot[4 * k], sn = rot[4 * k + 1];
+                const double2 ep = make_double2(rot[4 * k + 2], rot[4 * k + 3]);
+                const double2 bp = B[p + col * RF_CMAX], bq = ep * B[q + col * RF_CMAX];
+                B[p + col * RF_CMAX] = c * bp - sn * bq;
+                B[q + col * RF_CMAX] = sn * bp + c * bq;
+            }
+            __syncthreads();
+            for (int k = tid; k < mm / 2; k += T) {
+                const int p = pq[2 * k], q = pq[2 * k + 1];
+                if (q >= m || rot[4 * k + 1] == 0.0) continue;
+                B[p + q * RF_CMAX] = B[q + p * RF_CMAX] = make_double2(0.0, 0.0);
+                B[p + p * RF_CMAX].y = 0.0;
+                B[q + q * RF_CMAX].y = 0.0;
+            }
+            __syncthreads();
+        }
+        const int any = *flag;
+        __syncthreads();
+        if (!any) break;
+    }
+    for (int i = tid; i < m; i += T) w[i] = B[i + i * RF_CMAX].x;
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(256) k_cluster_sep(const MmfDesc* __restrict__ descs,
@@ -400,6 +528,9 @@ __global__ void __launch_bounds__(256) k_cluster_sep(const MmfDesc* __restrict__
     __shared__ double2 W[RF_CMAX * RF_CMAX];
     __shared__ double w[RF_CMAX];
     __shared__ int perm[RF_CMAX];
+    __shared__ double rot[4 * (RF_CMAX / 2)];
+    __shared__ int pq[RF_CMAX + 2];
+    __shared__ int flag;
     const int sid = idx[blockIdx.x];
     const MmfDesc d = descs[sid];
     const int n = d.n, D = d.D;
@@ -460,7 +591,10 @@ __global__ void __launch_bounds__(256) k_cluster_sep(const MmfDesc* __restrict__
                         B[q + p * RF_CMAX] = conj(h);
                         if (p == q) B[p + p * RF_CMAX].y = 0.0;
                     }
-                small_jacobi(B, W, m, w);
+            }
+            __syncthreads();
+            cta_jacobi(B, W, m, w, rot, pq, &flag);
+            if (threadIdx.x == 0) {
                 for (int a = 0; a < m; ++a) perm[a] = a;
                 for (int a = 1; a < m; ++a) {
                     int v = perm[a], b = a - 1;
@@ -483,7 +617,7 @@ __global__ void __launch_bounds__(256) k_cluster_sep(const MmfDesc* __restrict__
             for (int a = threadIdx.x; a < m; a += blockDim.x) lam[c0 + a] = w[perm[a]];
             __syncthreads();
         } else if (m > RF_CMAX) {
-            if (threadIdx.x == 0) status[sid] = MMF_ST_NOCONV;
+            if (threadIdx.x == 0) status[sid] = MMF_ST_CLUSTER;
         }
         c0 = c1;
     }
@@ -710,21 +844,27 @@ cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const double2* X, const d
                                    double2* S) {
     if (L.count <= 0) return cudaSuccess;
     const int T = (L.nmax + RF_TILE - 1) / RF_TILE;
-    k_gram_df32<<<dim3(T * (T + 1) / 2, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, HX, G, S);
+    // the first refinement step starts from FP32 eigenvectors: X is FP32-exact
+    k_gram_df32<true><<<dim3(T * (T + 1) / 2, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, HX, G, S);
     return cudaGetLastError();
 }
 
 cudaError_t mmf_launch_refine_post(const MmfLaunch& L, const double2* coef, double2* X, double* E,
                                    double2* G, double2* S, double2* HX, double* lam, int* status,
-                                   int* cid, int64_t mat_elems) {
+                                   int* cid, int64_t mat_elems, float2* Zp, void* jobs) {
     if (L.count <= 0) return cudaSuccess;
     // rest of the full step
     k_oa_lambda<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
     k_oa_etilde<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
-    k_xe_update<<<dim3((L.nmax + 63) / 64, (L.nmax + 63) / 64, L.count), 256, 0, L.stream>>>(
-        L.desc, L.idx, X, G, S);
-    cudaError_t e = cudaMemcpyAsync(X, S, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
+    // X <- X + X Et on the tensor cores (split TF32)
+    k_xe_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, S, HX);
+    k_xe_prep_A<<<dim3((L.nmax + 31) / 32, (L.nmax + 31) / 32, L.count), 256, 0, L.stream>>>(
+        L.desc, L.idx, X, Zp, G);
+    k_xe_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, Zp, G, S, HX,
+                                                          (UmmaJob*)jobs);
+    cudaError_t e = mmf_launch_umma(jobs, L.count, 3, L.nmax, 2 * L.nmax, 0, status, L.stream);
     if (e != cudaSuccess) return e;
+    k_xe_apply<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, G);
     k_cluster_sep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, coef, X, HX, lam, cid, status);
     // banded step
     k_apply_hf<<<dim3((L.nmax + 255) / 256, (L.nmax + 15) / 16, L.count), 256, 0, L.stream>>>(

@@ -3,18 +3,18 @@
 // Eigenvalues by Sturm-sequence bisection (Givens 1954; Barth, Martin & Wilkinson 1967):
 // count(x) = number of sign changes of the leading principal minors of T - x I (a division-
 // free three-term recurrence).  One thread per eigenvalue, each bracketing its own index
-// inside the Gershgorin interval until the bracket is below max(2 eps max(|lo|,|hi|), eps |T|).
+// inside the Gershgorin interval until the bracket is below max(2 eps max(|lo|,|hi|), tol |T|)
+// (tol = eps for the FP64 path; 1e-10 when the refinement follows, as T is then FP32-accurate).
 //
 // Eigenvectors by inverse iteration (Wilkinson 1965): (T - lambda I) y = b solved by
-// Gaussian elimination with partial pivoting on the tridiagonal band, three iterations from
-// a hashed start vector.  Eigenvalues closer than ortol = 1e-4 ||T||_1 form a cluster; one
+// Gaussian elimination with partial pivoting on the tridiagonal band, a fixed number of
+// iterations (3) from a hashed start vector.  Eigenvalues closer than ortol = 1e-4 ||T||_1 form a cluster; one
 // thread handles a whole cluster in ascending order and orthogonalises each iterate against
 // the cluster's earlier vectors (modified Gram-Schmidt), as LAPACK's stein does.
 // Y is written row-major: Y[i * n + k] = component i of eigenvector k.
 #include "mmf_internal.h"
 
 #define TRI_ORTOL 1e-4
-#define TRI_ITERS 3
 
 __device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
 
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(128) k_bisect(const MmfDesc* __restrict__ desc
                                                 const double* __restrict__ e2vec,
                                                 const double* __restrict__ aux,
                                                 double* __restrict__ Eout,
-                                                int* __restrict__ status) {
+                                                int* __restrict__ status, double rel_tol) {
     const int sid = idx[blockIdx.y];
     const MmfDesc d = descs[sid];
     const int n = d.n;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(128) k_bisect(const MmfDesc* __restrict__ desc
     const double eps = 2.220446049250313e-16;
     int it = 0;
     for (; it < 200; ++it) {
-        double tol = dmax(2.0 * eps * dmax(fabs(lo), fabs(hi)), eps * tn) + pivmin;
+        double tol = dmax(2.0 * eps * dmax(fabs(lo), fabs(hi)), rel_tol * tn) + pivmin;
         if (hi - lo <= tol) break;
         double mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
                                                  const double* __restrict__ aux,
                                                  const double* __restrict__ Eg,
                                                  double* __restrict__ Yg,
-                                                 double* __restrict__ work) {
+                                                 double* __restrict__ work, int iters) {
     const int sid = idx[blockIdx.y];
     const MmfDesc d = descs[sid];
     const int n = d.n;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
         double* a1 = u1 + j;
         double* a2 = u2 + j;
         for (int i = 0; i < n; ++i) y[(int64_t)i * s] = hash_unit(((uint64_t)sid << 40) ^ ((uint64_t)j << 20) ^ (uint64_t)i);
-        for (int it = 0; it < TRI_ITERS; ++it) {
+        for (int it = 0; it < iters; ++it) {
             tri_solve(dd, ee, n, lam, pivtiny, y, a0, a1, a2, s);
             // orthogonalise against the cluster's earlier vectors
             for (int jp = k; jp < j; ++jp) {
@@ -235,11 +235,11 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
 
 cudaError_t mmf_launch_tridiag_eig(const MmfLaunch& L, const double* dvec, const double* evec,
                                    double* aux, double* e2, double* E, double* Y, double* work,
-                                   int* status) {
+                                   int* status, double rel_tol, int iters) {
     if (L.count <= 0) return cudaSuccess;
     k_tri_prep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux, e2);
     dim3 g((L.nmax + 127) / 128, L.count);
-    k_bisect<<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, e2, aux, E, status);
-    k_inviter<<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux, E, Y, work);
+    k_bisect<<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, e2, aux, E, status, rel_tol);
+    k_inviter<<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux, E, Y, work, iters);
     return cudaGetLastError();
 }

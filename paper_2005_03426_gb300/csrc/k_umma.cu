@@ -1,0 +1,344 @@
+// k_umma.cu -- batched GEMM on the 5th-generation tensor cores (tcgen05 / TMEM).
+//
+//   C[b](m, n) = sum_{p < P} sum_k A_p[b](m, k) * B_p[b](n, k)        (FP32 accumulation)
+//
+// Operands are K-major (k contiguous) in global memory, element type TF32 (FP32 storage, low 13
+// mantissa bits zero) or BF16.  One CTA of 128 threads computes a 128 x 128 tile of C for one
+// batch entry: operand tiles of 128 rows x 128 bytes are staged by cp.async into shared memory
+// in the 128-byte-swizzled K-major layout (8-row atoms of 1 KB, 16-byte chunk j of row r at
+// position j ^ (r mod 8)), one elected thread issues tcgen05.mma (M = 128, N = 128) into a TMEM
+// accumulator and commits to an mbarrier, two stages are in flight, and the four warps read
+// the accumulator back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = rows of C).
+// Several products (P <= 3) share the accumulator, which is how a split-precision product such
+// as A1 B1 + A1 B2 + A2 B1 (TF32 pieces of FP32 data) is formed in one pass.
+// Every mbarrier wait is bounded; on time-out the CTA sets *err and leaves after freeing TMEM.
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "mmf_internal.h"
+
+#define UM_THREADS 128
+#define UM_TILE 128           // M and N of one tile
+#define UM_KB 128             // bytes of K per stage and row (one swizzle atom width)
+#define UM_STAGES 2
+#define UM_WAIT_LIMIT (1u << 26)
+
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 bytes apart
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);          // start address
+    d |= (uint64_t)(16u >> 4) << 16;                   // leading byte offset (unused for SW128 K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;                 // stride byte offset: next 8-row atom
+    d |= (uint64_t)1 << 46;                            // fixed 0b001 (tcgen05 descriptor)
+    d |= (uint64_t)2 << 61;                            // swizzle mode: 128 B
+    return d;
+}
+
+// instruction descriptor: D = F32, A/B type (kind::tf32: 2 = TF32; kind::f16: 1 = BF16),
+// both K-major, N = 128, M = 128
+__device__ __forceinline__ uint32_t umma_idesc(int ab_type) {
+    return (1u << 4) | ((uint32_t)ab_type << 7) | ((uint32_t)ab_type << 10) | ((128u >> 3) << 17) |
+           ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// bounded wait for the phase with the given parity; false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < UM_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g), "r"(src_bytes)
+                 : "memory");
+}
+
+template <int ESZ>
+__device__ __forceinline__ void load_tile(uint32_t sbase, const unsigned char* g, int rows_valid,
+                                          int k0_bytes, int kbytes_valid, int64_t ld_bytes) {
+    // 128 rows x 128 bytes = 1024 chunks of 16 bytes, 8 per thread
+    for (int c = threadIdx.x; c < UM_TILE * (UM_KB / 16); c += UM_THREADS) {
+        const int r = c >> 3, j = c & 7;
+        const uint32_t dst = sbase + (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4));
+        const int kb = k0_bytes + j * 16;
+        int bytes = 0;
+        const unsigned char* src = g;
+        if (r < rows_valid && kb < kbytes_valid) {
+            bytes = min(16, kbytes_valid - kb);
+            src = g + (int64_t)r * ld_bytes + kb;
+        }
+        cp_async16(dst, src, bytes);
+    }
+}
+
+template <int KIND>  // 0: kind::tf32 (4-byte elements), 1: kind::f16 with BF16 (2-byte elements)
+__global__ void __launch_bounds__(UM_THREADS, 1) k_umma_gemm(const UmmaJob* __restrict__ jobs, int P,
+                                                             int* __restrict__ err) {
+    constexpr int ESZ = KIND == 0 ? 4 : 2;
+    extern __shared__ __align__(1024) unsigned char um_smem[];
+    __shared__ uint64_t bar[UM_STAGES];
+    __shared__ uint32_t tmem_base_s;
+    const UmmaJob jb = jobs[blockIdx.z];
+    const int m0 = blockIdx.x * UM_TILE, n0 = blockIdx.y * UM_TILE;
+    if (m0 >= jb.M || n0 >= jb.N) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // shared layout per stage: P A-tiles then P B-tiles, 16 KB each, 1 KB aligned
+    unsigned char* base = (unsigned char*)(((uintptr_t)um_smem + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(base);
+    const uint32_t stage_bytes = 2u * P * 16384u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < UM_STAGES; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(128u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_s;
+
+    const int kbytes = jb.K * ESZ;
+    const int nk = (kbytes + UM_KB - 1) / UM_KB;
+    const uint32_t idesc = umma_idesc(KIND == 0 ? 2 : 1);
+    bool ok = true;
+    uint32_t phase[UM_STAGES] = {0u, 0u};
+
+    auto issue_loads = [&](int kc, int s) {
+        const uint32_t st = sbase + s * stage_bytes;
+        for (int p = 0; p < P; ++p) {
+            load_tile<ESZ>(st + p * 16384u, (const unsigned char*)jb.A[p] + (int64_t)m0 * jb.lda * ESZ,
+                           jb.M - m0, kc * UM_KB, kbytes, (int64_t)jb.lda * ESZ);
+            load_tile<ESZ>(st + (P + p) * 16384u, (const unsigned char*)jb.B[p] + (int64_t)n0 * jb.ldb * ESZ,
+                           jb.N - n0, kc * UM_KB, kbytes, (int64_t)jb.ldb * ESZ);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    issue_loads(0, 0);
+    for (int kc = 0; kc < nk && ok; ++kc) {
+        const int s = kc & 1;
+        if (kc + 1 < nk) {
+            const int s1 = s ^ 1;
+            if (kc >= 1) {  // MMAs of chunk kc-1 read stage s1: wait for their commit
+                ok = __syncthreads_and(mbar_wait(&bar[s1], phase[s1]) ? 1 : 0) != 0;
+                phase[s1] ^= 1u;
+                if (!ok) break;
+            }
+            issue_loads(kc + 1, s1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        // make this thread's cp.async data visible to the tensor core's async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = sbase + s * stage_bytes;
+            for (int p = 0; p < P; ++p) {
+                const uint64_t da = umma_desc(st + p * 16384u);
+                const uint64_t db = umma_desc(st + (P + p) * 16384u);
+#pragma unroll
+                for (int kk = 0; kk < UM_KB / 32; ++kk) {  // 32 bytes of K per instruction
+                    const uint32_t acc = (kc > 0 || p > 0 || kk > 0) ? 1u : 0u;
+                    const uint64_t adv = (uint64_t)((kk * 32) >> 4);
+                    if (KIND == 0)
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                            "l"(da + adv), "l"(db + adv), "r"(idesc), "r"(acc)
+                            : "memory");
+                    else
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                            "l"(da + adv), "l"(db + adv), "r"(idesc), "r"(acc)
+                            : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bar[s]))
+                         : "memory");
+        }
+    }
+    // wait for the last commit (covers every earlier MMA)
+    if (ok && nk > 0) {
+        const int s = (nk - 1) & 1;
+        ok = __syncthreads_and(mbar_wait(&bar[s], phase[s]) ? 1 : 0) != 0;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        // epilogue: warp w reads TMEM lanes 32w..32w+31 (rows m0 + 32w + lane), 32 columns at a time
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < UM_TILE; c0 += 32) {
+            uint32_t v[32];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                  "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                  "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                  "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < jb.M) {
+                float* out = jb.C + (int64_t)row * jb.ldc + n0 + c0;
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    if (n0 + c0 + q < jb.N) out[q] = __uint_as_float(v[q]);
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+}
+
+// jobs: device array of `count` UmmaJob; grid covers the largest M and N among them
+cudaError_t mmf_launch_umma(const void* jobs, int count, int P, int Mmax, int Nmax, int kind, int* err,
+                            cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    if (P < 1 || P > UM_MAXP) return cudaErrorInvalidValue;
+    const size_t sm = (size_t)UM_STAGES * 2 * P * 16384 + 1024;
+    dim3 grid((Mmax + UM_TILE - 1) / UM_TILE, (Nmax + UM_TILE - 1) / UM_TILE, count);
+    cudaError_t e;
+    if (kind == 0) {
+        e = cudaFuncSetAttribute(k_umma_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_umma_gemm<0><<<grid, UM_THREADS, sm, stream>>>((const UmmaJob*)jobs, P, err);
+    } else {
+        e = cudaFuncSetAttribute(k_umma_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_umma_gemm<1><<<grid, UM_THREADS, sm, stream>>>((const UmmaJob*)jobs, P, err);
+    }
+    return cudaGetLastError();
+}
+
+size_t mmf_umma_job_bytes() { return sizeof(UmmaJob); }
+
+// ------------------------------------------------------------------ self-test
+// The engine against a plain FP32 reference on seeded data (TF32-exact or BF16-exact inputs, so
+// both sides compute exact products and differ only by summation order).
+__global__ void k_umma_fill(float* A, int rows, int K, int ld, uint32_t seed, int kind, uint16_t* A16) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)rows * K;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / K), k = (int)(e % K);
+        uint32_t x = (uint32_t)e * 2654435761u ^ seed;
+        x ^= x >> 13; x *= 0x5bd1e995u; x ^= x >> 15;
+        float v = ((int)(x & 0xFFF) - 2048) / 256.0f;  // 12-bit values: exact in TF32 and (mostly) BF16
+        if (kind == 1) v = __bfloat162float(__float2bfloat16_rn(v));
+        A[(int64_t)r * ld + k] = v;
+        if (A16) A16[(int64_t)r * ld + k] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    }
+}
+__global__ void k_umma_ref(const float* A, const float* B, double* C, int M, int N, int K, int lda, int ldb) {
+    const int m = blockIdx.y, n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M || n >= N) return;
+    double acc = 0.0;
+    for (int k = 0; k < K; ++k) acc += (double)A[(int64_t)m * lda + k] * (double)B[(int64_t)n * ldb + k];
+    C[(int64_t)m * N + n] = acc;
+}
+__global__ void k_umma_cmp(const float* C, const double* R, int64_t tot, double scale, double* out) {
+    double mx = 0.0, ref = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        mx = fmax(mx, fabs((double)C[e] - scale * R[e]));
+        ref = fmax(ref, fabs(scale * R[e]));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        ref = fmax(ref, __shfl_xor_sync(0xffffffffu, ref, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax((unsigned long long*)&out[0], __double_as_longlong(mx));
+        atomicMax((unsigned long long*)&out[1], __double_as_longlong(ref));
+    }
+}
+
+int mmf_umma_selftest_impl(int M, int N, int K, int kind, int P, double* max_abs, double* max_ref) {
+    if (M < 1 || N < 1 || K < 1 || P < 1 || P > UM_MAXP || (kind != 0 && kind != 1)) return -1;
+    const int align = kind == 0 ? 4 : 8;
+    const int ld = (K + align - 1) / align * align;
+    float *A = nullptr, *B = nullptr, *C = nullptr;
+    uint16_t *A16 = nullptr, *B16 = nullptr;
+    double *R = nullptr, *out = nullptr;
+    UmmaJob* dj = nullptr;
+    int* err = nullptr;
+    int rc = 0;
+    cudaError_t e = cudaMalloc(&A, sizeof(float) * (size_t)M * ld);
+    if (e == cudaSuccess) e = cudaMalloc(&B, sizeof(float) * (size_t)N * ld);
+    if (e == cudaSuccess) e = cudaMalloc(&C, sizeof(float) * (size_t)M * N);
+    if (e == cudaSuccess) e = cudaMalloc(&A16, sizeof(uint16_t) * (size_t)M * ld);
+    if (e == cudaSuccess) e = cudaMalloc(&B16, sizeof(uint16_t) * (size_t)N * ld);
+    if (e == cudaSuccess) e = cudaMalloc(&R, sizeof(double) * (size_t)M * N);
+    if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(double) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&dj, sizeof(UmmaJob));
+    if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(out, 0, sizeof(double) * 2);
+    if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(A, 0, sizeof(float) * (size_t)M * ld);
+    if (e == cudaSuccess) e = cudaMemset(B, 0, sizeof(float) * (size_t)N * ld);
+    if (e == cudaSuccess) {
+        k_umma_fill<<<256, 256>>>(A, M, K, ld, 12345u, kind, A16);
+        k_umma_fill<<<256, 256>>>(B, N, K, ld, 777u, kind, B16);
+        UmmaJob j;
+        memset(&j, 0, sizeof(j));
+        for (int p = 0; p < P; ++p) {  // the same product P times: C = P * A B^T
+            j.A[p] = kind == 0 ? (const void*)A : (const void*)A16;
+            j.B[p] = kind == 0 ? (const void*)B : (const void*)B16;
+        }
+        j.C = C;
+        j.M = M; j.N = N; j.K = K; j.lda = ld; j.ldb = ld; j.ldc = N;
+        e = cudaMemcpy(dj, &j, sizeof(j), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = mmf_launch_umma(dj, 1, P, M, N, kind, err, 0);
+    if (e == cudaSuccess) {
+        k_umma_ref<<<dim3((N + 127) / 128, M), 128>>>(A, B, R, M, N, K, ld, ld);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {  // the engine summed the same product P times
+        k_umma_cmp<<<256, 256>>>(C, R, (int64_t)M * N, (double)P, out);
+        e = cudaDeviceSynchronize();
+    }
+    double hout[2] = {0, 0};
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(hout, out, sizeof(hout), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = -4;
+    else if (herr) rc = 1;
+    *max_abs = hout[0];
+    *max_ref = hout[1];
+    cudaFree(A); cudaFree(B); cudaFree(C); cudaFree(A16); cudaFree(B16); cudaFree(R); cudaFree(out);
+    cudaFree(dj); cudaFree(err);
+    return rc;
+}

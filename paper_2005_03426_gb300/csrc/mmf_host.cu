@@ -42,6 +42,8 @@ struct mmf_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     size_t budget = 0, used = 0;
+    int64_t jacobi_n[2] = {-1, -1};  // per precision; -1 = library default
+    int64_t large_n = -1;            // whole-GPU reduction from this n on; -1 = when one CTA cannot
     std::recursive_mutex mu;
 };
 
@@ -71,7 +73,7 @@ struct mmf_batch {
     int count = 0, precision = 0, nt = 0;
     std::vector<mmf_sys*> sys;
     std::vector<MmfDesc> desc;
-    std::vector<int> all, small, large;
+    std::vector<int> all, small, large, medium, huge;  // large = medium + huge
     int nmax_all = 0, nmax_small = 0, nmax_large = 0, Mmax = 1, Dmax = 1;
     int64_t n_coef = 0, n_mat = 0, n_vec = 0, n_sq = 0, n_pan = 0, n_t = 0, n_f = 0, n_u = 0,
             n_p = 0;
@@ -79,7 +81,8 @@ struct mmf_batch {
     unsigned char* base = nullptr;
     size_t bytes = 0;
     MmfDesc* d_desc = nullptr;
-    int *d_all = nullptr, *d_small = nullptr, *d_large = nullptr, *d_status = nullptr;
+    int *d_all = nullptr, *d_small = nullptr, *d_large = nullptr, *d_medium = nullptr, *d_status = nullptr;
+    int nmax_medium = 0;
     double2* d_coef = nullptr;
     void* d_H = nullptr;
     double2* d_Zf = nullptr;
@@ -94,6 +97,7 @@ struct mmf_batch {
     double2 *d_R = nullptr, *d_S = nullptr, *d_HX = nullptr;
     double* d_E2 = nullptr;
     int* d_cid = nullptr;
+    void* d_jobs = nullptr;
     // host staging (pinned)
     double2* h_coef = nullptr;
     double* h_t = nullptr;
@@ -104,6 +108,10 @@ struct mmf_batch {
     // per-stage CUDA-event timing (optional)
     int timing_runs = 0, runs_recorded = 0;
     std::vector<cudaEvent_t> ev;
+    // CUDA graph of the whole run (optional)
+    bool use_graph = false;
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_launches = 0;
 };
 
 enum { ST_ASSEMBLE, ST_JACOBI, ST_HETRD, ST_TRIDIAG, ST_BACKTRANSFORM, ST_REFINE, ST_GRAM, ST_REFINE2,
@@ -118,7 +126,11 @@ static void mark(mmf_batch* b, int stage) {
 // ------------------------------------------------------------------ helpers
 static int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-static int jacobi_nmax(int prec) { return prec == MMF_MIXED ? MMF_JACOBI_NMAX_F32 : MMF_JACOBI_NMAX_F64; }
+static int jacobi_default(int prec) { return prec == MMF_MIXED ? MMF_JACOBI_NMAX_F32 : MMF_JACOBI_NMAX_F64; }
+static int jacobi_nmax(const mmf_ctx* c, int prec) {
+    const int64_t v = c ? c->jacobi_n[prec == MMF_MIXED] : -1;
+    return v < 0 ? jacobi_default(prec) : (int)std::min<int64_t>(v, jacobi_default(prec));
+}
 
 static int64_t sys_dim(const mmf_sys* s) {
     int64_t m = 1;
@@ -137,6 +149,7 @@ extern "C" const char* mmf_strerror(int st) {
         case MMF_ERR_NOMEM: return "host allocation failed";
         case MMF_ST_NOCONV: return "iteration cap reached";
         case MMF_ST_NONFINITE: return "non-finite value";
+        case MMF_ST_CLUSTER: return "cluster of close eigenvalues too large to separate";
         default: return "unknown status";
     }
 }
@@ -193,6 +206,17 @@ extern "C" int mmf_ctx_destroy(mmf_ctx* c) {
     return MMF_OK;
 }
 extern "C" size_t mmf_ctx_bytes_in_use(const mmf_ctx* c) { return c ? c->used : 0; }
+
+extern "C" int mmf_ctx_set_option(mmf_ctx* c, int option, int64_t value) {
+    if (!c) return fail(MMF_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    switch (option) {
+        case MMF_OPT_JACOBI_N_FP64: c->jacobi_n[0] = value; return MMF_OK;
+        case MMF_OPT_JACOBI_N_MIXED: c->jacobi_n[1] = value; return MMF_OK;
+        case MMF_OPT_LARGE_N: c->large_n = value; return MMF_OK;
+        default: return fail(MMF_ERR_ARG, "unknown option");
+    }
+}
 extern "C" size_t mmf_ctx_budget(const mmf_ctx* c) { return c ? c->budget : 0; }
 
 // ------------------------------------------------------------------ systems
@@ -324,6 +348,8 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     b->desc.resize(count);
     const int fp32 = precision == MMF_MIXED;
     const int hmax = mmf_hetrd_max_n(fp32);
+    const int jmax = jacobi_nmax(ctx, precision);
+    const int64_t lmin = ctx->large_n < 0 ? (int64_t)hmax + 1 : ctx->large_n;
     for (int i = 0; i < count; ++i) {
         const mmf_sys* s = systems[i];
         if (!s || s->ctx != ctx) { delete b; return fail(MMF_ERR_ARG, "system NULL or from another context"); }
@@ -342,16 +368,15 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
             d.nharm[k] = (int)s->V[k].size();
         }
         int64_t n = M * s->D;
-        if (n > hmax && n > jacobi_nmax(precision)) {
+        if (n > (int64_t)INT32_MAX / 4) {
             delete b;
-            return fail(MMF_ERR_UNSUPPORTED, "Floquet dimension " + std::to_string(n) +
-                                                 " above this build's single-CTA limit " + std::to_string(hmax));
+            return fail(MMF_ERR_UNSUPPORTED, "Floquet dimension " + std::to_string(n) + " too large");
         }
         d.M = (int)M;
         d.n = (int)n;
         d.b0 = (int)b0;
         d.ld = (int)round_up(std::max<int64_t>(n, MMF_MIN_LD), 4);
-        d.small = n <= jacobi_nmax(precision);
+        d.small = n <= jmax;
         int64_t nc = (int64_t)s->D * s->D;
         for (int k = 0; k < d.K; ++k) nc += (int64_t)d.nharm[k] * s->D * s->D;
         d.coef_off = b->n_coef;
@@ -376,9 +401,11 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         b->n_p += (int64_t)s->D * s->D;
         b->all.push_back(i);
         (d.small ? b->small : b->large).push_back(i);
+        if (!d.small) (n >= lmin ? b->huge : b->medium).push_back(i);
         b->nmax_all = std::max(b->nmax_all, (int)n);
         if (d.small) b->nmax_small = std::max(b->nmax_small, (int)n);
         else b->nmax_large = std::max(b->nmax_large, (int)n);
+        if (!d.small && n < lmin) b->nmax_medium = std::max(b->nmax_medium, (int)n);
         b->Mmax = std::max(b->Mmax, (int)M);
         b->Dmax = std::max(b->Dmax, s->D);
     }
@@ -387,7 +414,8 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     Pool p;
     size_t o_desc = p.take(sizeof(MmfDesc) * count);
     size_t o_all = p.take(sizeof(int) * count), o_small = p.take(sizeof(int) * count),
-           o_large = p.take(sizeof(int) * count), o_status = p.take(sizeof(int) * count);
+           o_large = p.take(sizeof(int) * count), o_medium = p.take(sizeof(int) * count),
+           o_status = p.take(sizeof(int) * count);
     size_t o_coef = p.take(sizeof(double2) * b->n_coef);
     size_t o_H = p.take(cs * b->n_mat);
     size_t o_Zf = p.take(sizeof(double2) * b->n_mat);
@@ -402,13 +430,14 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     size_t o_F = p.take(sizeof(double2) * std::max<int64_t>(b->n_f, 1));
     size_t o_U = p.take(sizeof(double2) * std::max<int64_t>(b->n_u, 1));
     size_t o_P = p.take(sizeof(double) * b->n_p);
-    size_t o_R = 0, o_S = 0, o_HX = 0, o_E2 = 0, o_cid = 0;
+    size_t o_R = 0, o_S = 0, o_HX = 0, o_E2 = 0, o_cid = 0, o_jobs = 0;
     if (fp32) {
         o_R = p.take(sizeof(double2) * b->n_mat);
         o_S = p.take(sizeof(double2) * b->n_mat);
         o_HX = p.take(sizeof(double2) * b->n_mat);
         o_E2 = p.take(sizeof(double) * b->n_vec);
         o_cid = p.take(sizeof(int) * b->n_vec);
+        o_jobs = p.take(sizeof(UmmaJob) * count);
     }
     b->bytes = p.off;
     if (ctx->used + b->bytes > ctx->budget) {
@@ -428,6 +457,7 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     b->d_all = (int*)(B + o_all);
     b->d_small = (int*)(B + o_small);
     b->d_large = (int*)(B + o_large);
+    b->d_medium = (int*)(B + o_medium);
     b->d_status = (int*)(B + o_status);
     b->d_coef = (double2*)(B + o_coef);
     b->d_H = B + o_H;
@@ -453,6 +483,7 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         b->d_HX = (double2*)(B + o_HX);
         b->d_E2 = (double*)(B + o_E2);
         b->d_cid = (int*)(B + o_cid);
+        b->d_jobs = B + o_jobs;
     }
     if (b->pinned) {
         e = cudaMallocHost((void**)&b->h_coef, sizeof(double2) * std::max<int64_t>(b->n_coef, 1));
@@ -476,6 +507,8 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         e = cudaMemcpyAsync(b->d_small, b->small.data(), sizeof(int) * b->small.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !b->large.empty())
         e = cudaMemcpyAsync(b->d_large, b->large.data(), sizeof(int) * b->large.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !b->medium.empty())
+        e = cudaMemcpyAsync(b->d_medium, b->medium.data(), sizeof(int) * b->medium.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_coef, b->h_coef, sizeof(double2) * b->n_coef, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -501,6 +534,10 @@ extern "C" int mmf_batch_timing(mmf_batch* b, int max_runs) {
     CU(cudaSetDevice(b->ctx->device));
     CU(cudaStreamSynchronize(b->stream));
     drop_events(b);
+    if (b->graph_exec) {  // the graph holds the old events
+        cudaGraphExecDestroy(b->graph_exec);
+        b->graph_exec = nullptr;
+    }
     b->ev.resize((size_t)max_runs * (ST_COUNT + 1));
     for (auto& e : b->ev) CU(cudaEventCreate(&e));
     b->timing_runs = max_runs;
@@ -531,6 +568,7 @@ extern "C" int mmf_batch_destroy(mmf_batch* b) {
     std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
     cudaSetDevice(b->ctx->device);
     cudaStreamSynchronize(b->stream);
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
     drop_events(b);
     free_batch_memory(b);
     delete b;
@@ -547,6 +585,10 @@ extern "C" int mmf_batch_set_times(mmf_batch* b, double t0, const double* t) {
     std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
     CU(cudaStreamSynchronize(b->stream));  // staging buffer may be in flight
     if (b->n_t > 0) std::memcpy(b->h_t, t, sizeof(double) * b->n_t);
+    if (t0 != b->t0 && b->graph_exec) {  // t0 is a kernel argument baked into the graph
+        cudaGraphExecDestroy(b->graph_exec);
+        b->graph_exec = nullptr;
+    }
     b->t0 = t0;
     b->times_set = true;
     if (b->n_t > 0)
@@ -604,10 +646,21 @@ static int stage_eig(mmf_batch* b) {
     if (!b->large.empty()) {
         MmfLaunch Ll = launch_of(b, b->large, b->d_large, b->nmax_large);
         mark(b, ST_HETRD);
-        LAUNCH(mmf_launch_hetrd(Ll, b->d_H, b->d_Vp, b->d_Wp, b->d_d, b->d_e, b->d_tau, fp32), 1);
+        if (!b->medium.empty()) {
+            MmfLaunch Lm = launch_of(b, b->medium, b->d_medium, b->nmax_medium);
+            LAUNCH(mmf_launch_hetrd(Lm, b->d_H, b->d_Vp, b->d_Wp, b->d_d, b->d_e, b->d_tau, fp32), 1);
+        }
+        for (int i : b->huge) {  // one system at a time over the whole GPU
+            const MmfDesc& d = b->desc[i];
+            void* work = (void*)(b->d_Y + d.sq_off);
+            void* sc = (void*)(b->d_aux + 8 * i);
+            LAUNCH(mmf_launch_hetrd_large(d, b->d_H, b->d_Vp, b->d_Wp, b->d_d, b->d_e, b->d_tau, work, sc, fp32,
+                                          b->stream),
+                   4 * d.n);
+        }
         mark(b, ST_TRIDIAG);
         LAUNCH(mmf_launch_tridiag_eig(Ll, b->d_d, b->d_e, b->d_aux, b->d_e2, b->d_E, b->d_Y, b->d_work,
-                                      b->d_status), 3);
+                                      b->d_status, fp32 ? 1e-10 : 2.220446049250313e-16, 3), 3);
         mark(b, ST_BACKTRANSFORM);
         LAUNCH(mmf_launch_backtransform(Ll, b->d_H, b->d_tau, b->d_Vp, b->d_Y, b->d_Zp, fp32), 2);
         if (fp32) LAUNCH(mmf_launch_widen(Ll, b->d_Zp, b->d_Zf, fp32), 1);
@@ -624,8 +677,8 @@ static int stage_eig(mmf_batch* b) {
         LAUNCH(mmf_launch_refine_gram(La, b->d_Zf, b->d_HX, b->d_R, b->d_S), 1);
         mark(b, ST_REFINE2);
         LAUNCH(mmf_launch_refine_post(La, b->d_coef, b->d_Zf, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_E2,
-                                      b->d_status, b->d_cid, b->n_mat),
-               10);
+                                      b->d_status, b->d_cid, b->n_mat, (float2*)b->d_Zp, b->d_jobs),
+               14);
     } else {
         mark(b, ST_GRAM);
         mark(b, ST_REFINE2);
@@ -649,16 +702,58 @@ static int stage_outputs(mmf_batch* b) {
     return MMF_OK;
 }
 
+static int run_stages(mmf_batch* b) {
+    int rc = stage_assemble(b);
+    if (rc == MMF_OK) rc = stage_eig(b);
+    if (rc == MMF_OK) rc = stage_outputs(b);
+    return rc;
+}
+
 extern "C" int mmf_batch_run(mmf_batch* b) {
     if (!b) return fail(MMF_ERR_ARG, "batch is NULL");
     if (b->nt > 0 && !b->times_set) return fail(MMF_ERR_STATE, "times not set");
     std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
     CU(cudaSetDevice(b->ctx->device));
     g_launches = 0;
-    int rc = stage_assemble(b);
-    if (rc == MMF_OK) rc = stage_eig(b);
-    if (rc == MMF_OK) rc = stage_outputs(b);
-    return rc;
+    if (!b->use_graph) return run_stages(b);
+    if (!b->graph_exec) {
+        // capture the whole launch sequence once; timing events (if on) record into slot 0
+        const int saved = b->runs_recorded;
+        b->runs_recorded = 0;
+        CU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = run_stages(b);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        b->runs_recorded = saved;
+        if (rc != MMF_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(MMF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->graph_exec = nullptr;
+            return fail(MMF_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+        b->graph_launches = g_launches;
+    }
+    CU(cudaGraphLaunch(b->graph_exec, b->stream));
+    if (b->timing_runs > 0) b->runs_recorded = 1;
+    b->last_stage = 3;
+    g_launches = b->graph_launches;
+    return MMF_OK;
+}
+
+extern "C" int mmf_batch_graph(mmf_batch* b, int enable) {
+    if (!b) return fail(MMF_ERR_ARG, "batch is NULL");
+    std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
+    if (b->graph_exec) {
+        cudaGraphExecDestroy(b->graph_exec);
+        b->graph_exec = nullptr;
+    }
+    b->use_graph = enable != 0;
+    return MMF_OK;
 }
 
 extern "C" int mmf_batch_sync(mmf_batch* b, int* status) {
@@ -1249,5 +1344,16 @@ extern "C" int mmf_serve_destroy(mmf_server* sv) {
         if (sl.hst) cudaFreeHost(sl.hst);
     }
     delete sv;
+    return MMF_OK;
+}
+
+// ================================================================== diagnostics
+extern "C" int mmf_selftest_tensor_cores(int M, int N, int K, int kind, int products, double* max_abs_err,
+                                         double* max_abs_ref) {
+    if (!max_abs_err || !max_abs_ref) return fail(MMF_ERR_ARG, "output pointers required");
+    int rc = mmf_umma_selftest_impl(M, N, K, kind, products, max_abs_err, max_abs_ref);
+    if (rc == -1) return fail(MMF_ERR_ARG, "bad self-test sizes");
+    if (rc == -4) return fail(MMF_ERR_CUDA, "self-test CUDA failure");
+    if (rc == 1) return fail(MMF_ST_NOCONV, "tensor-core pipeline wait timed out");
     return MMF_OK;
 }

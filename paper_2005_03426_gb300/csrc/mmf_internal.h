@@ -95,10 +95,88 @@ __device__ __forceinline__ double block_ndotw(const MmfDesc& d, int b) {
     return s;
 }
 
+// Double-FP32 arithmetic: FP64-accurate sums of products computed on the FP32 pipes.
+// Every FP64 value is split x = x1 + x2 (x1 = fl32(x), x2 = fl32(x - x1)); x1*y1 is taken exactly
+// (product + FMA error term), the cross terms in FP32, and sums are accumulated as a (hi, lo)
+// pair with TwoSum (Knuth 1969).
+struct DF {
+    float hi, lo;
+};
+
+// acc += a * b with a = a1 + a2, b = b1 + b2 (FP32 pieces of FP64 values)
+__device__ __forceinline__ void df_mac(DF& acc, float a1, float a2, float b1, float b2) {
+    const float p = a1 * b1;
+    const float e = fmaf(a1, b1, -p);
+    const float c = fmaf(a1, b2, a2 * b1);
+    const float s = acc.hi + p;
+    const float bb = s - acc.hi;
+    const float err = (acc.hi - (s - bb)) + (p - bb);
+    acc.hi = s;
+    acc.lo += err + e + c;
+}
+// acc += a1 * (b1 + b2) with a1 exactly FP32 (no a2 piece)
+__device__ __forceinline__ void df_mac1(DF& acc, float a1, float b1, float b2) {
+    const float p = a1 * b1;
+    const float e = fmaf(a1, b1, -p);
+    const float s = acc.hi + p;
+    const float bb = s - acc.hi;
+    const float err = (acc.hi - (s - bb)) + (p - bb);
+    acc.hi = s;
+    acc.lo += err + fmaf(a1, b2, e);
+}
+// acc += a1 * b1 with both exactly FP32
+__device__ __forceinline__ void df_mac11(DF& acc, float a1, float b1) {
+    const float p = a1 * b1;
+    const float e = fmaf(a1, b1, -p);
+    const float s = acc.hi + p;
+    const float bb = s - acc.hi;
+    const float err = (acc.hi - (s - bb)) + (p - bb);
+    acc.hi = s;
+    acc.lo += err + e;
+}
+__device__ __forceinline__ void df_renorm(DF& a) {
+    const float s = a.hi + a.lo;
+    a.lo = a.lo - (s - a.hi);
+    a.hi = s;
+}
+
+struct Split {  // FP32 pieces of one complex FP64 value
+    float r1, r2, i1, i2;
+};
+__device__ __forceinline__ Split split(double2 v) {
+    Split s;
+    s.r1 = __double2float_rn(v.x);
+    s.r2 = __double2float_rn(v.x - (double)s.r1);
+    s.i1 = __double2float_rn(v.y);
+    s.i2 = __double2float_rn(v.y - (double)s.i1);
+    return s;
+}
+
+// conj(a) * b accumulated into (re, im)
+__device__ __forceinline__ void df_cmacc(DF& re, DF& im, const Split& a, const Split& b) {
+    df_mac(re, a.r1, a.r2, b.r1, b.r2);
+    df_mac(re, a.i1, a.i2, b.i1, b.i2);
+    df_mac(im, a.r1, a.r2, b.i1, b.i2);
+    df_mac(im, -a.i1, -a.i2, b.r1, b.r2);
+}
+
+// a * b accumulated into (re, im)
+__device__ __forceinline__ void df_cmac(DF& re, DF& im, const Split& a, const Split& b) {
+    df_mac(re, a.r1, a.r2, b.r1, b.r2);
+    df_mac(re, -a.i1, -a.i2, b.i1, b.i2);
+    df_mac(im, a.r1, a.r2, b.i1, b.i2);
+    df_mac(im, a.i1, a.i2, b.r1, b.r2);
+}
+__device__ __forceinline__ double2 df_value(const DF& re, const DF& im) {
+    return make_double2((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo);
+}
+
+
 // ------------------------------------------------------------------ status codes (device)
 #define MMF_ST_OK 0
 #define MMF_ST_NOCONV 1      // iteration cap reached
 #define MMF_ST_NONFINITE 2   // NaN / Inf encountered
+#define MMF_ST_CLUSTER 3     // refinement cluster too large to separate
 
 // ------------------------------------------------------------------ kernel launchers
 // Every launcher takes the device descriptor array and a device list of system indices.
@@ -117,7 +195,7 @@ cudaError_t mmf_launch_hetrd(const MmfLaunch& L, void* H, void* Vp, void* Wp, do
                              double* evec, void* tau, int fp32);
 cudaError_t mmf_launch_tridiag_eig(const MmfLaunch& L, const double* dvec, const double* evec,
                                    double* aux, double* e2, double* E, double* Y, double* work,
-                                   int* status);
+                                   int* status, double rel_tol, int iters);
 cudaError_t mmf_launch_backtransform(const MmfLaunch& L, const void* H, const void* tau,
                                      void* Tf, const double* Y, void* Z, int fp32);
 cudaError_t mmf_launch_widen(const MmfLaunch& L, const void* Zp, double2* Z, int fp32);
@@ -125,6 +203,8 @@ cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const dou
                                const double2* Z, const double* t, double t0, int nt, double2* F,
                                double2* U, double* P, double cluster_rel);
 int mmf_hetrd_max_n(int fp32);
+cudaError_t mmf_launch_hetrd_large(const MmfDesc& d, void* H, void* Vp, void* Wp, double* dvec, double* evec,
+                                   void* tau, void* work, void* sc, int fp32, cudaStream_t st);
 cudaError_t mmf_launch_micromotion(const MmfLaunch& L, int D, const double2* Z, const double* t,
                                    int nt, int64_t* reps, double2* UF);
 cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const double2* coef, const double2* X, double2* HX);
@@ -132,7 +212,20 @@ cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const double2* X, const d
                                    double2* S);
 cudaError_t mmf_launch_refine_post(const MmfLaunch& L, const double2* coef, double2* X, double* E,
                                    double2* G, double2* S, double2* HX, double* lam, int* status,
-                                   int* cid, int64_t mat_elems);
+                                   int* cid, int64_t mat_elems, float2* Zp, void* jobs);
+// batched tensor-core GEMM (k_umma.cu): C(m, n) = sum_p sum_k A_p(m, k) B_p(n, k), K-major
+// operands (TF32 in FP32 storage, or BF16), FP32 result
+#define UM_MAXP 3
+struct UmmaJob {
+    const void* A[UM_MAXP];   // A_p: M x K, row stride lda elements (lda * element size % 16 == 0)
+    const void* B[UM_MAXP];   // B_p: N x K, row stride ldb elements
+    float* C;                 // M x N, row stride ldc
+    int M, N, K;
+    int lda, ldb, ldc;
+};
+cudaError_t mmf_launch_umma(const void* jobs, int count, int P, int Mmax, int Nmax, int kind, int* err,
+                            cudaStream_t stream);
+int mmf_umma_selftest_impl(int M, int N, int K, int kind, int P, double* max_abs, double* max_ref);
 #define MMF_MIN_LD 36   // n x ld matrix slots also hold the n x 33 band of the refinement
 
 #define MMF_NB 32          // Householder panel width and back-transform block size

@@ -9,6 +9,7 @@ The ``mmf_*`` functions of the C ABI are exposed under the same names on ``lib()
 
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
 import re
@@ -30,10 +31,25 @@ MMF_ERR_UNSUPPORTED = -5
 MMF_ERR_NOMEM = -6
 MMF_ST_NOCONV = 1
 MMF_ST_NONFINITE = 2
+MMF_ST_CLUSTER = 3
 MMF_FP64 = 0
 MMF_MIXED = 1
+MMF_OPT_JACOBI_N_FP64 = 1
+MMF_OPT_JACOBI_N_MIXED = 2
+MMF_OPT_LARGE_N = 3
 
 _lib = None
+_exiting = False
+
+
+def _at_exit():
+    # Handles still alive at interpreter exit are left to the process teardown: releasing them
+    # from finalizers that may run after the CUDA runtime has shut down is unsafe.
+    global _exiting
+    _exiting = True
+
+
+atexit.register(_at_exit)
 
 
 class MmfError(RuntimeError):
@@ -54,6 +70,7 @@ _SIGS = {
     "mmf_ctx_destroy": (_I, [_P]),
     "mmf_ctx_bytes_in_use": (_SZ, [_P]),
     "mmf_ctx_budget": (_SZ, [_P]),
+    "mmf_ctx_set_option": (_I, [_P, _I, _I64]),
     "mmf_sys_create": (_I, [_P, _I, _P, _PP]),
     "mmf_add_mode": (_I, [_P, _D, _I, ctypes.POINTER(_I)]),
     "mmf_add_coupling": (_I, [_P, _I, _I, _P]),
@@ -80,6 +97,7 @@ _SIGS = {
     "mmf_batch_size": (_I64, [_P, _I]),
     "mmf_batch_bytes": (_SZ, [_P]),
     "mmf_batch_timing": (_I, [_P, _I]),
+    "mmf_batch_graph": (_I, [_P, _I]),
     "mmf_batch_stage_ms": (_I, [_P, _P, _P]),
     "mmf_batch_destroy": (_I, [_P]),
     "mmf_tridiag_eig_noalloc": (_I, [_P, _P, _I, _P, _P, _P]),
@@ -91,6 +109,7 @@ _SIGS = {
                              ctypes.POINTER(_I64)]),
     "mmf_serve_reset_stats": (_I, [_P]),
     "mmf_serve_destroy": (_I, [_P]),
+    "mmf_selftest_tensor_cores": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "mmf_strerror": (ctypes.c_char_p, [_I]),
     "mmf_last_error": (ctypes.c_char_p, []),
     "mmf_last_launch_count": (_I, []),
@@ -148,13 +167,16 @@ class Context:
     def bytes_in_use(self) -> int:
         return int(lib().mmf_ctx_bytes_in_use(self.h))
 
+    def set_option(self, option: int, value: int):
+        _check(lib().mmf_ctx_set_option(self.h, option, int(value)))
+
     def budget(self) -> int:
         return int(lib().mmf_ctx_budget(self.h))
 
     def close(self):
-        if self.h:
+        if self.h and not _exiting:
             lib().mmf_ctx_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -230,9 +252,9 @@ class System:
         return U
 
     def close(self):
-        if self.h:
+        if self.h and not _exiting:
             lib().mmf_sys_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -310,6 +332,9 @@ class Batch:
     STAGES = ("assemble", "jacobi", "hetrd", "tridiag", "backtransform", "refine_hx", "refine_gram",
               "refine_rest", "outputs")
 
+    def graph(self, enable: bool = True):
+        _check(lib().mmf_batch_graph(self.h, 1 if enable else 0))
+
     def timing(self, max_runs: int):
         _check(lib().mmf_batch_timing(self.h, int(max_runs)))
 
@@ -323,9 +348,9 @@ class Batch:
         return int(lib().mmf_batch_bytes(self.h))
 
     def close(self):
-        if self.h:
+        if self.h and not _exiting:
             lib().mmf_batch_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -377,9 +402,9 @@ class Server:
         _check(lib().mmf_serve_reset_stats(self.h))
 
     def close(self):
-        if self.h:
+        if self.h and not _exiting:
             lib().mmf_serve_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:

@@ -233,10 +233,10 @@ def test_argument_and_state_errors(ctx):
     with pytest.raises(M.MmfError) as ei:
         s.quasienergies()
     assert ei.value.code == M.MMF_ERR_STATE
-    big = W.large_instance()
+    huge = W.random_small(1, D=64, Ns=[30, 30, 30])  # n = 14.5 million: beyond any HBM budget
     with pytest.raises(M.MmfError) as ei:
-        M.Batch(ctx, [M.System(ctx, big)], M.MMF_FP64, 1)
-    assert ei.value.code == M.MMF_ERR_UNSUPPORTED
+        M.Batch(ctx, [M.System(ctx, huge)], M.MMF_FP64, 1)
+    assert ei.value.code == M.MMF_ERR_BUDGET
 
 
 def test_micromotion_matches_oracle(ctx):
@@ -321,3 +321,79 @@ def test_mixed_batch_alone_vs_mixed(ctx):
         assert np.abs(e - e1).max() <= 1e-9 * nrm
         assert np.abs(u - u1).max() <= 1e-8 and np.abs(pp - p1).max() <= 1e-8
         _compare(p, e, u, pp, ts[i], 0.0, e_rel=MIX_E_REL, up_abs=MIX_UP_ABS)
+
+
+def test_graph_replay_matches_plain_launches(ctx):
+    """The batch's launch sequence captured in a CUDA graph and replayed gives the plain run's
+    results (two replays in a row, then after new inputs)."""
+    ps = [SOLVE_CASES[k]() for k in ("qubit_n82", "random_n125", "spin1_n27")]
+    nt = 8
+    ts = np.stack([W.time_grid(p, nt) for p in ps])
+    for precision in (M.MMF_FP64, M.MMF_MIXED):
+        plain = M.Batch(ctx, [M.System(ctx, p) for p in ps], precision, nt)
+        plain.set_times(0.0, ts)
+        plain.run()
+        plain.sync()
+        ref = [x.copy() for x in plain.results()]
+        g = M.Batch(ctx, [M.System(ctx, p) for p in ps], precision, nt)
+        g.set_times(0.0, ts)
+        g.graph(True)
+        # runs differ only in the order of floating-point atomics: compare at the path's tolerance
+        tol = 1e-10 if precision == M.MMF_FP64 else 1e-8
+        for _ in range(2):
+            assert g.run() > 0
+            assert (g.sync() == 0).all()
+            out = g.results()
+            for a, c in zip(ref, out):
+                assert np.abs(a - c).max() <= tol * max(1.0, np.abs(a).max())
+        g.set_times(0.4, ts)  # new t0: re-captured
+        g.run()
+        g.sync()
+        plain.set_times(0.4, ts)
+        plain.run()
+        plain.sync()
+        for a, c in zip(plain.results(), g.results()):
+            assert np.abs(a - c).max() <= tol * max(1.0, np.abs(a).max())
+
+
+@pytest.mark.parametrize("precision", [M.MMF_FP64, M.MMF_MIXED])
+def test_many_systems_single_cta_reduction(ctx, precision):
+    """More systems than fit two CTAs each on the GPU: the reduction runs one CTA per system.
+    Every result must match the same system solved alone (two CTAs per system) and, for a sample,
+    the oracle."""
+    ps = [q for q in W.uneven_batch(count=400, seed=5) if 120 < q.n <= 260][:90]
+    assert len(ps) == 90
+    nt = 4
+    ts = np.stack([W.time_grid(p, nt) for p in ps])
+    b = M.Batch(ctx, [M.System(ctx, p) for p in ps], precision, nt)
+    b.set_times(0.0, ts)
+    b.run()
+    assert (b.sync() == 0).all()
+    E, U, P = b.results()
+    e_rel, up = (1e-12, 1e-10) if precision == M.MMF_FP64 else (1e-9, 1e-8)
+    for i in (0, 17, 45, 89):
+        e, u, pp = b.unpack(E, U, P, i)
+        E1, U1, P1 = M.Batch(ctx, [M.System(ctx, ps[i])], precision, nt), None, None
+        E1.set_times(0.0, ts[i:i + 1])
+        E1.run()
+        E1.sync()
+        e1, u1, p1 = E1.get(0)
+        nrm = np.abs(e1).max()
+        assert np.abs(e - e1).max() <= e_rel * nrm
+        assert np.abs(u - u1).max() <= up and np.abs(pp - p1).max() <= up
+        if i in (0, 45):
+            _compare(ps[i], e, u, pp, ts[i], 0.0, e_rel=e_rel, up_abs=up)
+
+
+@pytest.mark.parametrize("precision", [M.MMF_FP64, M.MMF_MIXED])
+@pytest.mark.parametrize("case", ["random_n245", "spin1_n297", "single_level_n101"])
+def test_whole_gpu_reduction_path(case, precision):
+    """The whole-GPU Householder reduction (used alone for systems too large for one CTA) forced
+    on small systems, against the oracle."""
+    c = M.Context(0)
+    c.set_option(M.MMF_OPT_LARGE_N, 90)
+    p = SOLVE_CASES[case]()
+    t = W.time_grid(p, 8)
+    s, E, U, P = _solve_gpu(c, p, t, 0.2, precision=precision)
+    e_rel, up = (E_REL, UP_ABS) if precision == M.MMF_FP64 else (MIX_E_REL, MIX_UP_ABS)
+    _compare(p, E, U, P, t, 0.2, e_rel=e_rel, up_abs=up)
