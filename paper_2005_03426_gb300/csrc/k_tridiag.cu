@@ -1,28 +1,33 @@
-// k_tridiag.cu -- S4: eigenpairs of the real symmetric tridiagonal T = tridiag(e, d, e), FP64.
+// k_tridiag.cu -- S4: eigenpairs of the real symmetric tridiagonal T = tridiag(e, d, e), in FP64
+// (the FP64 path) or in FP32 (the mixed path, whose T comes from an FP32 reduction and whose
+// eigenpairs are refined afterwards, so FP32 accuracy here loses nothing).
 //
 // Eigenvalues by Sturm-sequence bisection (Givens 1954; Barth, Martin & Wilkinson 1967):
 // count(x) = number of sign changes of the leading principal minors of T - x I (a division-
 // free three-term recurrence).  One thread per eigenvalue, each bracketing its own index
 // inside the Gershgorin interval until the bracket is below max(2 eps max(|lo|,|hi|), tol |T|)
-// (tol = eps for the FP64 path; 1e-10 when the refinement follows, as T is then FP32-accurate).
+// (tol = eps of the working precision).  The FP32 solver first scales T by the power of two that
+// brings ||T|| to at most 1 (exact), so that the recurrence grows by at most a factor 3 a step.
 //
 // Eigenvectors by inverse iteration (Wilkinson 1965): (T - lambda I) y = b solved by
 // Gaussian elimination with partial pivoting on the tridiagonal band, a fixed number of
-// iterations (3) from a hashed start vector.  Eigenvalues closer than ortol = 1e-4 ||T||_1 form a cluster; one
+// iterations (3) from a hashed start vector.  Eigenvalues closer than ortol = 1e-4 ||T||_1 form a
+// cluster (LAPACK's stein takes 1e-3, which at n ~ 2e4 would chain the whole spectrum); one
 // thread handles a whole cluster in ascending order and orthogonalises each iterate against
 // the cluster's earlier vectors (modified Gram-Schmidt), as LAPACK's stein does.
 // Y is written row-major: Y[i * n + k] = component i of eigenvector k.
 #include "mmf_internal.h"
 
-#define TRI_ORTOL 1e-4
 
 __device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
 
 // per system: gl, gu, pivmin, tnorm
 __global__ void k_tri_prep(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                            const double* __restrict__ dvec, const double* __restrict__ evec,
-                           double* __restrict__ aux, double* __restrict__ e2vec) {
+                           double* __restrict__ aux, double* __restrict__ e2vec,
+                           float* __restrict__ fwork) {
     __shared__ double red[4][32];
+    __shared__ double scale_sh;
     const int sid = idx[blockIdx.x];
     const MmfDesc d = descs[sid];
     const int n = d.n;
@@ -59,31 +64,78 @@ __global__ void k_tri_prep(const MmfDesc* __restrict__ descs, const int* __restr
         aux[8 * sid + 1] = gu + pad;
         aux[8 * sid + 2] = 2.2250738585072014e-308 * fmax(1.0, e2max);  // pivmin
         aux[8 * sid + 3] = tn;
+        // FP32 solver: T scaled by s = 2^-k with ||T|| s <= 1
+        int ex = 0;
+        if (tn > 0.0) frexp(tn, &ex);
+        const double sc = ldexp(1.0, -ex);
+        aux[8 * sid + 4] = sc;
+        scale_sh = sc;
     }
+    if (fwork == nullptr) return;
+    __syncthreads();
+    // scaled FP32 copies after the 4 n^2 floats of the inverse-iteration arrays:
+    // (d_i s, e_{i-1}^2 s^2) pairs, then e_i s
+    const double sc = scale_sh;
+    float2* de2 = (float2*)(fwork + 2 * d.sq_off * 3 + 4 * (int64_t)n * n);
+    float* ef = (float*)(de2 + n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double el = (i > 0) ? ee[i - 1] * sc : 0.0;
+        de2[i] = make_float2((float)(dd[i] * sc), (float)(el * el));
+        ef[i] = (i < n - 1) ? (float)(ee[i] * sc) : 0.0f;
+    }
+}
+
+template <class R> struct TriP;
+template <> struct TriP<double> {
+    static __device__ __forceinline__ double eps() { return 2.220446049250313e-16; }
+    static __device__ __forceinline__ double tiny() { return 1e-300; }
+    static constexpr double ortol = 1e-4;
+    static constexpr int rescale_mask = 15;
+};
+template <> struct TriP<float> {
+    static __device__ __forceinline__ float eps() { return 5.9604645e-8f; }
+    static __device__ __forceinline__ float tiny() { return 1e-37f; }
+    static constexpr float ortol = 1e-4f;
+    static constexpr int rescale_mask = 7;
+};
+
+// Power of two 2^-e with e the exponent of v (v > 0 finite), so that v 2^-e lies in [0.5, 1).
+__device__ __forceinline__ double pow2_below(double v) {
+    int ex;
+    frexp(v, &ex);
+    return ldexp(1.0, -ex);
+}
+__device__ __forceinline__ float pow2_below(float v) {
+    // exponent field of a normal float; subnormal or zero v takes the scale 2^126
+    const int be = (__float_as_int(v) >> 23) & 0xff;
+    const int e = be == 0 ? -125 : be - 126;
+    const int se = 127 - e;
+    return __int_as_float((se < 1 ? 1 : (se > 254 ? 254 : se)) << 23);
 }
 
 // Sturm count by the three-term recurrence of the leading principal minors,
 //   p_0 = 1, p_1 = d_0 - x, p_{i+1} = (d_i - x) p_i - e_{i-1}^2 p_{i-1},
 // counting sign changes (= eigenvalues below x); an exact zero takes the sign opposite to its
-// predecessor (a negative pivot, as in the ratio form).  Every 16 steps the pair (p_i, p_{i-1})
-// is rescaled by the power of two that brings the larger of the two below 1, which changes no
-// sign and keeps 16 further steps far from overflow.
-__device__ __forceinline__ int sturm_count(const double* __restrict__ dd,
-                                           const double* __restrict__ e2, int n, double x) {
+// predecessor (a negative pivot, as in the ratio form).  Every 16 (FP64) or 8 (FP32) steps the
+// pair (p_i, p_{i-1}) is rescaled by the power of two that brings the larger of the two below
+// 1, which changes no sign; with ||T|| <= 1 (FP32) a step grows the pair by at most 3, and in
+// FP64 the exponent range leaves room for 16 steps at any ||T|| the workloads produce.
+// de2[i] = (d_i, e_{i-1}^2) with e_{-1} = 0.
+template <class R, class R2>
+__device__ __forceinline__ int sturm_count(const R2* __restrict__ de2, int n, R x) {
     int cnt = 0;
-    double pm = 1.0, p = dd[0] - x;
-    if (p == 0.0) p = -1e-300;
-    cnt += (p < 0.0);
+    R pm = R(1), p = de2[0].x - x;
+    if (p == R(0)) p = -TriP<R>::tiny();
+    cnt += (p < R(0));
     for (int i = 1; i < n; ++i) {
-        double pn = fma(dd[i] - x, p, -e2[i - 1] * pm);
-        if (pn == 0.0) pn = (p < 0.0) ? 1e-300 : -1e-300;
-        cnt += ((pn < 0.0) != (p < 0.0));
+        const R2 v = de2[i];
+        R pn = fma(v.x - x, p, -v.y * pm);
+        if (pn == R(0)) pn = (p < R(0)) ? TriP<R>::tiny() : -TriP<R>::tiny();
+        cnt += ((pn < R(0)) != (p < R(0)));
         pm = p;
         p = pn;
-        if ((i & 15) == 0) {
-            int ex;
-            frexp(fmax(fabs(p), fabs(pm)), &ex);
-            const double sc = ldexp(1.0, -ex);
+        if ((i & TriP<R>::rescale_mask) == 0) {
+            const R sc = pow2_below(fmax(fabs(p), fabs(pm)));
             p *= sc;
             pm *= sc;
         }
@@ -91,84 +143,166 @@ __device__ __forceinline__ int sturm_count(const double* __restrict__ dd,
     return cnt;
 }
 
+// FP64 solver input: d and e^2 read from their own arrays.
+struct De2View {
+    const double* d;
+    const double* e2;
+    __device__ __forceinline__ double2 operator[](int i) const {
+        return make_double2(d[i], i > 0 ? e2[i - 1] : 0.0);
+    }
+};
+__device__ __forceinline__ int sturm_count(const De2View& v, int n, double x) {
+    int cnt = 0;
+    double pm = 1.0, p = v.d[0] - x;
+    if (p == 0.0) p = -1e-300;
+    cnt += (p < 0.0);
+    for (int i = 1; i < n; ++i) {
+        double pn = fma(v.d[i] - x, p, -v.e2[i - 1] * pm);
+        if (pn == 0.0) pn = (p < 0.0) ? 1e-300 : -1e-300;
+        cnt += ((pn < 0.0) != (p < 0.0));
+        pm = p;
+        p = pn;
+        if ((i & 15) == 0) {
+            const double sc = pow2_below(fmax(fabs(p), fabs(pm)));
+            p *= sc;
+            pm *= sc;
+        }
+    }
+    return cnt;
+}
+
+// Per-system views of the solver's inputs in its working precision.
+template <class R> struct TriIn;
+template <> struct TriIn<double> {
+    const double* d;
+    const double* e;
+    De2View de2;
+    double scale;
+    __device__ TriIn(const MmfDesc& ds, const double* dvec, const double* evec, const double* e2vec,
+                     const double*, const float*) {
+        d = dvec + ds.vec_off;
+        e = evec + ds.vec_off;
+        de2.d = d;
+        de2.e2 = e2vec + ds.vec_off;
+        scale = 1.0;
+    }
+    __device__ __forceinline__ double dv(int i) const { return d[i]; }
+    __device__ __forceinline__ double ev(int i) const { return e[i]; }
+};
+template <> struct TriIn<float> {
+    const float2* de2;
+    const float* e;
+    double scale;
+    __device__ TriIn(const MmfDesc& ds, const double*, const double*, const double*, const double* aux_sys,
+                     const float* fwork) {
+        const int n = ds.n;
+        de2 = (const float2*)(fwork + 2 * ds.sq_off * 3 + 4 * (int64_t)n * n);
+        e = (const float*)(de2 + n);
+        scale = aux_sys[4];
+    }
+    __device__ __forceinline__ float dv(int i) const { return de2[i].x; }
+    __device__ __forceinline__ float ev(int i) const { return e[i]; }
+};
+
+template <class R>
 __global__ void __launch_bounds__(128) k_bisect(const MmfDesc* __restrict__ descs,
                                                 const int* __restrict__ idx,
                                                 const double* __restrict__ dvec,
                                                 const double* __restrict__ e2vec,
                                                 const double* __restrict__ aux,
+                                                const float* __restrict__ fwork,
                                                 double* __restrict__ Eout,
-                                                int* __restrict__ status, double rel_tol) {
+                                                int* __restrict__ status) {
     const int sid = idx[blockIdx.y];
     const MmfDesc d = descs[sid];
     const int n = d.n;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const double* dd = dvec + d.vec_off;
-    const double* e2 = e2vec + d.vec_off;
-    double lo = aux[8 * sid], hi = aux[8 * sid + 1];
-    const double pivmin = aux[8 * sid + 2];
-    const double tn = aux[8 * sid + 3];
-    const double eps = 2.220446049250313e-16;
+    const TriIn<R> in(d, dvec, dvec, e2vec, aux + 8 * sid, fwork);
+    const double sc = in.scale;
+    // bracket and tolerances in the working precision (scaled for FP32; rounded outwards)
+    R lo, hi, pivmin, tn;
+    if (sizeof(R) == 4) {
+        lo = __double2float_rd(aux[8 * sid] * sc);
+        hi = __double2float_ru(aux[8 * sid + 1] * sc);
+        pivmin = R(1.1754944e-38);  // e^2 s^2 <= 1 after scaling
+        tn = R(aux[8 * sid + 3] * sc);
+    } else {
+        lo = R(aux[8 * sid]);
+        hi = R(aux[8 * sid + 1]);
+        pivmin = R(aux[8 * sid + 2]);
+        tn = R(aux[8 * sid + 3]);
+    }
+    const R eps = TriP<R>::eps();
     int it = 0;
     for (; it < 200; ++it) {
-        double tol = dmax(2.0 * eps * dmax(fabs(lo), fabs(hi)), rel_tol * tn) + pivmin;
+        R tol = fmax(R(2) * eps * fmax(fabs(lo), fabs(hi)), eps * tn) + pivmin;
         if (hi - lo <= tol) break;
-        double mid = 0.5 * (lo + hi);
+        R mid = R(0.5) * (lo + hi);
         if (mid <= lo || mid >= hi) break;
-        if (sturm_count(dd, e2, n, mid) <= k) lo = mid;
+        if (sturm_count(in.de2, n, mid) <= k) lo = mid;
         else hi = mid;
     }
-    Eout[d.vec_off + k] = 0.5 * (lo + hi);
+    Eout[d.vec_off + k] = (0.5 * ((double)lo + (double)hi)) / sc;
     if (it >= 200) status[sid] = MMF_ST_NOCONV;
 }
 
-__device__ __forceinline__ double hash_unit(uint64_t x) {
+// Quotient for the elimination: correctly rounded in FP64; in FP32 the fast reciprocal-based
+// quotient (2 ulp), whose denominators here stay far below 2^126 because ||T|| s <= 1.
+__device__ __forceinline__ double tdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float tdiv(float a, float b) { return __fdividef(a, b); }
+
+template <class R>
+__device__ __forceinline__ R hash_unit(uint64_t x) {
     x += 0x9E3779B97F4A7C15ull;
     x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
     x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
     x ^= x >> 31;
-    return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    return (R)((double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0);
 }
 
 // Solve (T - lam I) y = y in place; u0/u1/u2 are the (strided) U factor arrays.
-__device__ void tri_solve(const double* __restrict__ dd, const double* __restrict__ ee, int n,
-                          double lam, double pivtiny, double* y, double* u0, double* u1,
-                          double* u2, int64_t s) {
-    double p = dd[0] - lam, q = (n > 1) ? ee[0] : 0.0, r = 0.0, rb = y[0];
+template <class R, class In>
+__device__ void tri_solve(const In& in, int n, R lam, R pivtiny, R* y, R* u0, R* u1, R* u2, int64_t s) {
+    R p = in.dv(0) - lam, q = (n > 1) ? in.ev(0) : R(0), r = R(0), rb = y[0];
     for (int i = 0; i < n - 1; ++i) {
-        const double a = ee[i];
-        const double bb = dd[i + 1] - lam;
-        const double cc = (i + 1 < n - 1) ? ee[i + 1] : 0.0;
-        const double b1 = y[(int64_t)(i + 1) * s];
+        const R a = in.ev(i);
+        const R bb = in.dv(i + 1) - lam;
+        const R cc = (i + 1 < n - 1) ? in.ev(i + 1) : R(0);
+        const R b1 = y[(int64_t)(i + 1) * s];
         if (fabs(a) <= fabs(p)) {
-            if (p == 0.0) p = pivtiny;
-            const double l = a / p;
+            if (p == R(0)) p = pivtiny;
+            const R l = tdiv(a, p);
             u0[(int64_t)i * s] = p; u1[(int64_t)i * s] = q; u2[(int64_t)i * s] = r;
             y[(int64_t)i * s] = rb;
-            p = bb - l * q; q = cc - l * r; r = 0.0; rb = b1 - l * rb;
+            p = bb - l * q; q = cc - l * r; r = R(0); rb = b1 - l * rb;
         } else {
-            const double l = p / a;
+            const R l = tdiv(p, a);
             u0[(int64_t)i * s] = a; u1[(int64_t)i * s] = bb; u2[(int64_t)i * s] = cc;
             y[(int64_t)i * s] = b1;
-            const double np = q - l * bb, nq = r - l * cc, nrb = rb - l * b1;
-            p = np; q = nq; r = 0.0; rb = nrb;
+            const R np = q - l * bb, nq = r - l * cc, nrb = rb - l * b1;
+            p = np; q = nq; r = R(0); rb = nrb;
         }
     }
-    if (fabs(p) < pivtiny) p = (p < 0.0) ? -pivtiny : pivtiny;
+    if (fabs(p) < pivtiny) p = (p < R(0)) ? -pivtiny : pivtiny;
     u0[(int64_t)(n - 1) * s] = p;
     // back substitution
-    double y2 = 0.0, y1 = rb / p;
+    R y2 = R(0), y1 = tdiv(rb, p);
     y[(int64_t)(n - 1) * s] = y1;
     for (int i = n - 2; i >= 0; --i) {
-        double up = u0[(int64_t)i * s];
-        if (fabs(up) < pivtiny) up = (up < 0.0) ? -pivtiny : pivtiny;
-        const double yi = (y[(int64_t)i * s] - u1[(int64_t)i * s] * y1 - u2[(int64_t)i * s] * y2) / up;
+        R up = u0[(int64_t)i * s];
+        if (fabs(up) < pivtiny) up = (up < R(0)) ? -pivtiny : pivtiny;
+        const R yi = tdiv(y[(int64_t)i * s] - u1[(int64_t)i * s] * y1 - u2[(int64_t)i * s] * y2, up);
         y[(int64_t)i * s] = yi;
         y2 = y1;
         y1 = yi;
     }
 }
 
+// Inverse iteration.  FP64: the iterate lives in Y itself and the factors in work (3 n^2
+// doubles).  FP32: factors and iterate are n^2-float arrays at the start of work, and the
+// normalised iterate is written to Y (FP64) at the end.
+template <class R>
 __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ descs,
                                                  const int* __restrict__ idx,
                                                  const double* __restrict__ dvec,
@@ -182,64 +316,77 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
     const int n = d.n;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const double* dd = dvec + d.vec_off;
-    const double* ee = evec + d.vec_off;
+    const TriIn<R> in(d, dvec, evec, evec, aux + 8 * sid, (const float*)work);
     const double* E = Eg + d.vec_off;
-    const double tn = aux[8 * sid + 3];
-    const double ortol = TRI_ORTOL * tn;
-    if (k > 0 && E[k] - E[k - 1] <= ortol) return;  // not the first of its cluster
+    const double sc = in.scale;
+    const double tnd = aux[8 * sid + 3] * sc;
+    const double ortol = (double)TriP<R>::ortol * tnd;
+    if (k > 0 && (E[k] - E[k - 1]) * sc <= ortol) return;  // not the first of its cluster
     int kend = k + 1;
-    while (kend < n && E[kend] - E[kend - 1] <= ortol) ++kend;
-    const double eps = 2.220446049250313e-16;
-    const double pivtiny = eps * fmax(tn, 1e-300);
+    while (kend < n && (E[kend] - E[kend - 1]) * sc <= ortol) ++kend;
+    const R eps = TriP<R>::eps();
+    const R tn = R(tnd);
+    const R pivtiny = eps * fmax(tn, R(1e-30));
     const int64_t s = n;  // row stride of the row-major arrays
-    double* Y = Yg + d.sq_off;
-    double* u0 = work + 3 * d.sq_off;
-    double* u1 = u0 + (int64_t)n * n;
-    double* u2 = u1 + (int64_t)n * n;
-    double lamprev = 0.0;
+    const int64_t nn = (int64_t)n * n;
+    R* base = sizeof(R) == 8 ? (R*)(work + 3 * d.sq_off) : (R*)((float*)work + 2 * d.sq_off * 3);
+    R* u0 = base;
+    R* u1 = u0 + nn;
+    R* u2 = u1 + nn;
+    R* Yw = sizeof(R) == 8 ? (R*)(Yg + d.sq_off) : u2 + nn;
+    R lamprev = R(0);
     for (int j = k; j < kend; ++j) {
-        double lam = E[j];
+        R lam = R(E[j] * sc);
         if (j > k) {
-            const double pert = 10.0 * eps * fmax(fabs(lam), tn * 1e-3);
+            const R pert = R(10) * eps * fmax(fabs(lam), tn * R(1e-3));
             if (lam - lamprev < pert) lam = lamprev + pert;
         }
         lamprev = lam;
-        double* y = Y + j;
-        double* a0 = u0 + j;
-        double* a1 = u1 + j;
-        double* a2 = u2 + j;
-        for (int i = 0; i < n; ++i) y[(int64_t)i * s] = hash_unit(((uint64_t)sid << 40) ^ ((uint64_t)j << 20) ^ (uint64_t)i);
+        R* y = Yw + j;
+        R* a0 = u0 + j;
+        R* a1 = u1 + j;
+        R* a2 = u2 + j;
+        for (int i = 0; i < n; ++i)
+            y[(int64_t)i * s] = hash_unit<R>(((uint64_t)sid << 40) ^ ((uint64_t)j << 20) ^ (uint64_t)i);
         for (int it = 0; it < iters; ++it) {
-            tri_solve(dd, ee, n, lam, pivtiny, y, a0, a1, a2, s);
+            tri_solve<R>(in, n, lam, pivtiny, y, a0, a1, a2, s);
             // orthogonalise against the cluster's earlier vectors
             for (int jp = k; jp < j; ++jp) {
-                const double* z = Y + jp;
-                double dot = 0.0;
+                const R* z = Yw + jp;
+                R dot = R(0);
                 for (int i = 0; i < n; ++i) dot += y[(int64_t)i * s] * z[(int64_t)i * s];
                 for (int i = 0; i < n; ++i) y[(int64_t)i * s] -= dot * z[(int64_t)i * s];
             }
-            double mx = 0.0;
+            R mx = R(0);
             for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(y[(int64_t)i * s]));
-            const double inv1 = (mx > 0.0) ? 1.0 / mx : 1.0;
-            double nrm = 0.0;
+            const R inv1 = (mx > R(0)) ? R(1) / mx : R(1);
+            R nrm = R(0);
             for (int i = 0; i < n; ++i) {
-                double v = y[(int64_t)i * s] * inv1;
+                R v = y[(int64_t)i * s] * inv1;
                 nrm += v * v;
             }
-            const double inv = inv1 / sqrt(nrm);
+            const R inv = inv1 / sqrt(nrm);
             for (int i = 0; i < n; ++i) y[(int64_t)i * s] *= inv;
+        }
+        if (sizeof(R) == 4) {
+            double* yo = Yg + d.sq_off + j;
+            for (int i = 0; i < n; ++i) yo[(int64_t)i * s] = (double)y[(int64_t)i * s];
         }
     }
 }
 
 cudaError_t mmf_launch_tridiag_eig(const MmfLaunch& L, const double* dvec, const double* evec,
                                    double* aux, double* e2, double* E, double* Y, double* work,
-                                   int* status, double rel_tol, int iters) {
+                                   int* status, int fp32, int iters) {
     if (L.count <= 0) return cudaSuccess;
-    k_tri_prep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux, e2);
+    k_tri_prep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux, e2, fp32 ? (float*)work : nullptr);
     dim3 g((L.nmax + 127) / 128, L.count);
-    k_bisect<<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, e2, aux, E, status, rel_tol);
-    k_inviter<<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux, E, Y, work, iters);
+    if (fp32) {
+        k_bisect<float><<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, e2, aux, (const float*)work, E, status);
+        k_inviter<float><<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux, E, Y, work, iters);
+    } else {
+        k_bisect<double><<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, e2, aux, nullptr, E, status);
+        k_inviter<double><<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux, E, Y, work, iters);
+    }
     return cudaGetLastError();
 }

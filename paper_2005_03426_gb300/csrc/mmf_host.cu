@@ -660,7 +660,7 @@ static int stage_eig(mmf_batch* b) {
         }
         mark(b, ST_TRIDIAG);
         LAUNCH(mmf_launch_tridiag_eig(Ll, b->d_d, b->d_e, b->d_aux, b->d_e2, b->d_E, b->d_Y, b->d_work,
-                                      b->d_status, fp32 ? 1e-10 : 2.220446049250313e-16, 3), 3);
+                                      b->d_status, fp32, 3), 3);
         mark(b, ST_BACKTRANSFORM);
         LAUNCH(mmf_launch_backtransform(Ll, b->d_H, b->d_tau, b->d_Vp, b->d_Y, b->d_Zp, fp32), 2);
         if (fp32) LAUNCH(mmf_launch_widen(Ll, b->d_Zp, b->d_Zf, fp32), 1);

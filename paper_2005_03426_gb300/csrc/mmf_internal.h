@@ -195,7 +195,7 @@ cudaError_t mmf_launch_hetrd(const MmfLaunch& L, void* H, void* Vp, void* Wp, do
                              double* evec, void* tau, int fp32);
 cudaError_t mmf_launch_tridiag_eig(const MmfLaunch& L, const double* dvec, const double* evec,
                                    double* aux, double* e2, double* E, double* Y, double* work,
-                                   int* status, double rel_tol, int iters);
+                                   int* status, int fp32, int iters);
 cudaError_t mmf_launch_backtransform(const MmfLaunch& L, const void* H, const void* tau,
                                      void* Tf, const double* Y, void* Z, int fp32);
 cudaError_t mmf_launch_widen(const MmfLaunch& L, const void* Zp, double2* Z, int fp32);

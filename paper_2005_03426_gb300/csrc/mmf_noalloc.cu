@@ -92,7 +92,7 @@ extern "C" int mmf_tridiag_eig_noalloc(const double* d, const double* e, int n, 
     L.stream = st;
     err = mmf_launch_tridiag_eig(L, d, e, (double*)(s + NA_OFF_AUX), (double*)(s + NA_OFF_E2), E, Y,
                                  (double*)(s + NA_OFF_WORK), (int*)(s + NA_OFF_INT + sizeof(int)),
-                                 2.220446049250313e-16, 3);
+                                 0, 3);
     if (err != cudaSuccess)
         return mmf_set_error(MMF_ERR_CUDA, std::string("mmf_tridiag_eig_noalloc: ") + cudaGetErrorString(err));
     return MMF_OK;

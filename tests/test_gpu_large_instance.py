@@ -1,0 +1,77 @@
+"""The single large instance at full size: D = 8, three modes, N = (6, 6, 6), n = 17576, solved
+by the whole-GPU reduction in the launch configuration the benchmark times (one system per
+batch, 256 times over one period of the first mode).
+
+The oracle cannot diagonalise n = 17576 in test time, so the eigenpairs are checked through
+properties that hold at any size, against the oracle's own H_F and formulas:
+- residuals |H_F z - E z| of sampled eigenpairs, with H_F built by the oracle (Eq. 6);
+- orthonormality of the sampled eigenvectors;
+- U(t, t0) at sampled times recomputed from the GPU eigenpairs by the Eq. 3-5 sum in numpy (the
+  oracle's loop form takes minutes per time at this size), and Pbar by the oracle's formula;
+- U(t0, t0) = I, unitarity of U(t), sum_j Pbar_ij = 1, and the Floquet copy E + omega_1."""
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2005_03426_gb300 import mmf as M
+from paper_2005_03426_gb300 import workloads as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+TOL = {M.MMF_FP64: (1e-12, 1e-10), M.MMF_MIXED: (1e-9, 1e-8)}
+
+
+@pytest.mark.parametrize("precision", [M.MMF_MIXED])
+def test_large_instance_properties(precision):
+    p = W.large_instance(seed=3)
+    assert p.n == 17576
+    nt = 256
+    t = W.time_grid(p, nt)
+    ctx = M.Context(0)
+    b = M.Batch(ctx, [M.System(ctx, p)], precision, nt)
+    b.set_times(0.0, t[None, :])
+    b.run()
+    st = b.sync()
+    assert st[0] == 0
+    E, U, P = b.get(0)
+    Z = b.eigenvectors(0)            # Z[:, k] = eigenvector k
+    del b
+    e_rel, up = TOL[precision]
+    nrm = np.abs(E).max()
+    assert np.all(np.diff(E) >= 0)
+
+    rng = np.random.default_rng(5)
+    cols = np.sort(rng.choice(p.n, 48, replace=False))
+    cols = np.unique(np.concatenate([cols, [0, p.n // 2, p.n - 1]]))
+    HF = O.build_hf(p)
+    Zs = Z[:, cols]
+    R = HF @ Zs - Zs * E[cols][None, :]
+    del HF
+    assert np.abs(R).max() <= e_rel * nrm * 10.0
+    G = Zs.conj().T @ Zs
+    assert np.abs(G - np.eye(len(cols))).max() <= up
+
+    # outputs against the Eq. 3-5 sums evaluated on the same eigenpairs
+    D, M_ = p.D, p.M
+    grids = np.meshgrid(*[np.arange(-N, N + 1) for N in p.Ns[::-1]], indexing="ij")
+    nvec = np.array(grids).reshape(len(p.Ns), -1)[::-1].T   # block b -> (n_1, ..., n_K), mode 1 fastest
+    nw = nvec @ np.asarray(p.omegas)
+    b0 = int(np.argmin(np.abs(nvec).sum(axis=1)))
+    Z3 = Z.reshape(M_, D, p.n)
+    Z0 = Z3[b0]
+    for k in (37, 200):
+        Phi = np.tensordot(np.exp(-1j * nw * t[k]), Z3, axes=(0, 0))       # D x n
+        Uk = (Phi * np.exp(-1j * E * t[k])[None, :]) @ Z0.conj().T
+        assert np.abs(U[k] - Uk).max() <= up
+    Po = O.transition_avg(p, E, Z, 1e-8)
+    assert np.abs(P - Po).max() <= up
+
+    D = p.D
+    np.testing.assert_allclose(U[0], np.eye(D), atol=up)
+    for k in range(0, nt, 17):
+        assert np.abs(U[k].conj().T @ U[k] - np.eye(D)).max() <= 10 * up
+    np.testing.assert_allclose(P.sum(axis=1), 1.0, atol=up)
+    assert P.min() >= -up
+    mid = E[np.argmin(np.abs(E - np.median(E)))]
+    assert np.min(np.abs(E - (mid + p.omegas[0]))) <= 1e-6
