@@ -75,12 +75,16 @@ MMF_API size_t mmf_ctx_bytes_in_use(const mmf_ctx* ctx);
 MMF_API size_t mmf_ctx_budget(const mmf_ctx* ctx);
 /* Size thresholds of the solver paths for batches created afterwards (value < 0 restores the
  * default): MMF_OPT_JACOBI_N_FP64 / _MIXED: largest n solved by the shared-memory Jacobi kernel
- * (defaults 84 / 118, also the maxima); MMF_OPT_LARGE_N: smallest n reduced by the whole-GPU
+ * (defaults 84 / 118, also the maxima; values below 4 act as 4); MMF_OPT_LARGE_N: smallest n reduced by the whole-GPU
  * Householder reduction, one system at a time (default: sizes one CTA's shared memory cannot
- * hold).  Results do not depend on the path beyond rounding. */
+ * hold); MMF_OPT_REFINE_FULL_N: in the mixed path, smallest n whose second refinement step is a
+ * full one instead of the banded one (default 3000; dense spectra of large H_F leave first-step
+ * errors between eigenpairs far apart in the sorted order that the banded step cannot reach).
+ * Results do not depend on the path beyond rounding. */
 #define MMF_OPT_JACOBI_N_FP64 1
 #define MMF_OPT_JACOBI_N_MIXED 2
 #define MMF_OPT_LARGE_N 3
+#define MMF_OPT_REFINE_FULL_N 4
 MMF_API int mmf_ctx_set_option(mmf_ctx* ctx, int option, int64_t value);
 
 /* ---------------------------------------------------------------- system definition

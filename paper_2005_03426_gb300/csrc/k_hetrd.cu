@@ -105,10 +105,14 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                 }
                 __syncthreads();
                 for (int r = k + rank * HT_THREADS + tid; r < n; r += CL * HT_THREADS) {
-                    C acc = czero<C>();
-                    for (int c = 0; c < i; ++c)
-                        acc = acc + V[r + (int64_t)c * ld] * wk[c] + W[r + (int64_t)c * ld] * vk[c];
-                    A[r + (int64_t)k * ld] = A[r + (int64_t)k * ld] - acc;
+                    // unrolled so that the panel's loads (L2 latency each) are in flight together
+                    C acc = czero<C>(), acc2 = czero<C>();
+#pragma unroll 8
+                    for (int c = 0; c < i; ++c) {
+                        acc = acc + V[r + (int64_t)c * ld] * wk[c];
+                        acc2 = acc2 + W[r + (int64_t)c * ld] * vk[c];
+                    }
+                    A[r + (int64_t)k * ld] = A[r + (int64_t)k * ld] - (acc + acc2);
                 }
                 if (CL > 1) cluster.sync(); else __syncthreads();
             }
@@ -246,10 +250,13 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
             // (d) corrections, (e) w = tau y - (1/2) tau (w^H v) v
             C dpart = czero<C>();
             for (int rp = tid; rp < m; rp += HT_THREADS) {
-                C y = yT[rp];
-                for (int c = 0; c < i; ++c)
-                    y = y - V[(k + 1 + rp) + (int64_t)c * ld] * xw[c] -
-                        W[(k + 1 + rp) + (int64_t)c * ld] * xv[c];
+                C y = yT[rp], y2 = czero<C>();
+#pragma unroll 8
+                for (int c = 0; c < i; ++c) {
+                    y = y - V[(k + 1 + rp) + (int64_t)c * ld] * xw[c];
+                    y2 = y2 + W[(k + 1 + rp) + (int64_t)c * ld] * xv[c];
+                }
+                y = y - y2;
                 C w = tk * y;
                 yF[rp] = w;
                 dpart = dpart + cmulc(w, vS[rp]);

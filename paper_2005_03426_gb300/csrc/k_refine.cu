@@ -8,11 +8,22 @@
 //     Et_ij = (s_ij - lam_j g_ij) / (lam_j - lam_i)   for well separated pairs,
 //     Et_ij = r_ij / 2                                 on the diagonal and inside clusters,
 //     X <- X + X Et.
-// Products that decide the result (G, S) are formed FP64-accurately from FP32 pieces: every
-// FP64 value is split x = x1 + x2 (x1 = fl32(x), x2 = fl32(x - x1)); x1*y1 is taken exactly
-// (product + FMA error term), the cross terms in FP32, and the sums are accumulated in
-// double-FP32 (TwoSum, Knuth 1969).  X Et only needs FP32 (Et is small).  H_F X is applied in
-// FP64 from the coefficients, never from the FP32 matrix.
+// G decides the orthogonality of the result and is formed FP64-accurately from FP32 pieces:
+// every FP64 value is split x = x1 + x2 (x1 = fl32(x), x2 = fl32(x - x1)); x1*y1 is taken
+// exactly (product + FMA error term), the cross terms in FP32, and the sums are accumulated in
+// double-FP32 (TwoSum, Knuth 1969).  H_F X is applied in FP64 from the coefficients, never from
+// the FP32 matrix.
+// First step, residual form of S: with lam0 the eigenvalues that came with X and the residual
+// W = H_F X - X diag(lam0) (FP64, small: |W| ~ eps32 |H_F|),
+//     S = G diag(lam0) + C,   C = X^H W,
+// so lam_i = lam0_i + c_ii / g_ii and s_ij - lam_j g_ij = c_ij - (lam_j - lam0_j) g_ij.  C only
+// needs FP32 relative accuracy (its absolute error is then ~eps32^2 |H_F|) and is taken on the
+// tensor cores in split TF32.  X Et only needs FP32 (Et is small) and is taken there as well.
+// A second full step (large n, where one step leaves second-order errors ~(eps32 |H_F| / gap)^2
+// between eigenpairs far apart in the sorted order) starts from FP64 X = X1 + Dx with
+// X1 = fl32(X): G = X1^H X1 + C' + C'^H + O(|Dx|^2) with C' = X1^H Dx, the first term by the
+// same double-FP32 kernel (X1 is FP32-exact), C' on the tensor cores (|Dx| ~ 2^-24 |X|).
+// Otherwise the second step is banded (below).
 // A pair is treated as clustered when |lam_i - lam_j| <= 20 |s_ij - lam_j g_ij| (the first-order
 // correction would exceed 0.05) or the gap is below 1e-13 |H_F|; consecutive clustered indices
 // form a cluster whose eigenvectors are separated by an FP64 Jacobi solve of the small
@@ -24,6 +35,21 @@
 #define RF_KG 16   // k-chunk of the FP64-accurate Gram kernel
 #define RF_CMAX 32
 #define RF_TAU 20.0
+// Band |i - j| <= RF_W of the sorted eigenpairs: the first step applies Et there in double-FP32
+// (entries up to ~0.05), and the second step refines only inside it.
+#define RF_W 16
+#define RF_BW (2 * RF_W + 1)
+static_assert(RF_BW == MMF_REFINE_BW, "band buffer width");
+
+// TF32 operands for the tcgen05 engine: round to nearest (ties away) to 10 explicit bits
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// row length (floats) of the real K-major operands built from n complex entries: [Re | Im | pad]
+__device__ __forceinline__ int xe_la(int n) { return (2 * n + 3) & ~3; }
 
 // ------------------------------------------------------------------ HX = H_F X (FP64, sparse)
 __global__ void __launch_bounds__(256) k_apply_hf(const MmfDesc* __restrict__ descs,
@@ -68,38 +94,28 @@ __global__ void __launch_bounds__(256) k_apply_hf(const MmfDesc* __restrict__ de
     }
 }
 
-// ------------------------------------------------------------------ G = X^H X, S = X^H HX
-// Upper-triangle tiles (I <= J) of 32 x 32; both triangles are written.  X1 = true: X holds
-// FP32-exact values (the first refinement step), so its second pieces vanish and are skipped.
-template <bool X1>
-__device__ __forceinline__ void gram_cmacc(DF& gre, DF& gim, DF& sre, DF& sim, const Split& a,
-                                           const Split& b, const Split& h) {
-    if (X1) {
-        // conj(a) b with a, b FP32-exact; conj(a) h with h split
-        df_mac11(gre, a.r1, b.r1);
-        df_mac11(gre, a.i1, b.i1);
-        df_mac11(gim, a.r1, b.i1);
-        df_mac11(gim, -a.i1, b.r1);
-        df_mac1(sre, a.r1, h.r1, h.r2);
-        df_mac1(sre, a.i1, h.i1, h.i2);
-        df_mac1(sim, a.r1, h.i1, h.i2);
-        df_mac1(sim, -a.i1, h.r1, h.r2);
-    } else {
-        df_cmacc(gre, gim, a, b);
-        df_cmacc(sre, sim, a, h);
+// ------------------------------------------------------------------ G = X1^H X1 (double-FP32)
+// X1 = fl32(X) in its own FP32 buffer (written once by k_to_fp32), so the kernel converts
+// nothing: each conj(a) b of FP32 values is accumulated exactly (product + FMA error term) into
+// a double-FP32 sum.  Upper-triangle tiles (I <= J) of 32 x 32; both triangles are written.
+__global__ void __launch_bounds__(256) k_to_fp32(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
+                                                 const double2* __restrict__ Xg, float2* __restrict__ X1g) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int64_t tot = (int64_t)d.n * d.ld;
+    const double2* X = Xg + d.mat_off;
+    float2* X1 = X1g + d.mat_off;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const double2 x = X[e];
+        X1[e] = make_float2((float)x.x, (float)x.y);
     }
 }
 
-template <bool X1>
-__global__ void __launch_bounds__(256) k_gram_df32(const MmfDesc* __restrict__ descs,
-                                                   const int* __restrict__ idx,
-                                                   const double2* __restrict__ Xg,
-                                                   const double2* __restrict__ HXg,
-                                                   double2* __restrict__ Gg,
-                                                   double2* __restrict__ Sg) {
-    __shared__ Split xi[RF_KG][RF_TILE + 1];
-    __shared__ Split xj[RF_KG][RF_TILE + 1];
-    __shared__ Split hj[RF_KG][RF_TILE + 1];
+__global__ void __launch_bounds__(256) k_gram_x1(const MmfDesc* __restrict__ descs,
+                                                 const int* __restrict__ idx,
+                                                 const float2* __restrict__ X1g,
+                                                 double2* __restrict__ Gg) {
+    __shared__ float2 xi[RF_KG][RF_TILE + 1];
+    __shared__ float2 xj[RF_KG][RF_TILE + 1];
     const MmfDesc d = descs[idx[blockIdx.y]];
     const int n = d.n;
     const int T = (n + RF_TILE - 1) / RF_TILE;
@@ -109,46 +125,46 @@ __global__ void __launch_bounds__(256) k_gram_df32(const MmfDesc* __restrict__ d
     while (t >= T - I) { t -= T - I; ++I; }
     const int J = I + t;
     const int i0 = I * RF_TILE, j0 = J * RF_TILE;
-    const double2* X = Xg + d.mat_off;
-    const double2* HX = HXg + d.mat_off;
+    const float2* X = X1g + d.mat_off;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // outputs (ty + 16a, tx + 16b)
-    DF gr[2][2], gi[2][2], sr[2][2], si[2][2];
+    DF gr[2][2], gi[2][2];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            gr[a][b] = gi[a][b] = sr[a][b] = si[a][b] = DF{0.f, 0.f};
-        }
+        for (int b = 0; b < 2; ++b) gr[a][b] = gi[a][b] = DF{0.f, 0.f};
     for (int k0 = 0; k0 < n; k0 += RF_KG) {
         for (int e = threadIdx.x; e < RF_KG * RF_TILE; e += 256) {
             const int c = e / RF_KG, kk = e - c * RF_KG;
             const int k = k0 + kk;
-            const double2 z = make_double2(0.0, 0.0);
-            xi[kk][c] = split((k < n && i0 + c < n) ? X[(int64_t)(i0 + c) * d.ld + k] : z);
-            xj[kk][c] = split((k < n && j0 + c < n) ? X[(int64_t)(j0 + c) * d.ld + k] : z);
-            hj[kk][c] = split((k < n && j0 + c < n) ? HX[(int64_t)(j0 + c) * d.ld + k] : z);
+            const float2 z = make_float2(0.f, 0.f);
+            xi[kk][c] = (k < n && i0 + c < n) ? X[(int64_t)(i0 + c) * d.ld + k] : z;
+            xj[kk][c] = (k < n && j0 + c < n) ? X[(int64_t)(j0 + c) * d.ld + k] : z;
         }
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < RF_KG; ++kk) {
-            const Split a0 = xi[kk][ty], a1 = xi[kk][ty + 16];
-            const Split b0 = xj[kk][tx], b1 = xj[kk][tx + 16];
-            const Split h0 = hj[kk][tx], h1 = hj[kk][tx + 16];
-            gram_cmacc<X1>(gr[0][0], gi[0][0], sr[0][0], si[0][0], a0, b0, h0);
-            gram_cmacc<X1>(gr[0][1], gi[0][1], sr[0][1], si[0][1], a0, b1, h1);
-            gram_cmacc<X1>(gr[1][0], gi[1][0], sr[1][0], si[1][0], a1, b0, h0);
-            gram_cmacc<X1>(gr[1][1], gi[1][1], sr[1][1], si[1][1], a1, b1, h1);
+            const float2 a[2] = {xi[kk][ty], xi[kk][ty + 16]};
+            const float2 b[2] = {xj[kk][tx], xj[kk][tx + 16]};
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {  // conj(a) b
+                    df_mac11(gr[p][q], a[p].x, b[q].x);
+                    df_mac11(gr[p][q], a[p].y, b[q].y);
+                    df_mac11(gi[p][q], a[p].x, b[q].y);
+                    df_mac11(gi[p][q], -a[p].y, b[q].x);
+                }
         }
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
-                df_renorm(gr[a][b]); df_renorm(gi[a][b]); df_renorm(sr[a][b]); df_renorm(si[a][b]);
+                df_renorm(gr[a][b]);
+                df_renorm(gi[a][b]);
             }
         __syncthreads();
     }
     double2* G = Gg + d.mat_off;
-    double2* S = Sg + d.mat_off;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -156,34 +172,176 @@ __global__ void __launch_bounds__(256) k_gram_df32(const MmfDesc* __restrict__ d
             const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
             if (i < n && j < n && (I < J || i <= j)) {
                 double2 g = df_value(gr[a][b], gi[a][b]);
-                double2 s = df_value(sr[a][b], si[a][b]);
-                if (i == j) { g.y = 0.0; s.y = 0.0; }
+                if (i == j) g.y = 0.0;
                 G[(int64_t)j * d.ld + i] = g;
-                S[(int64_t)j * d.ld + i] = s;
                 G[(int64_t)i * d.ld + j] = conj(g);
-                S[(int64_t)i * d.ld + j] = conj(s);
             }
         }
 }
 
+// ------------------------------------------------------------------ C = X^H W on tensor cores
+// Re C = Xr^T Wr + Xi^T Wi and Im C = Xr^T Wi - Xi^T Wr as one real product over K = 2n:
+//   A row i = [Re x_i | Im x_i],  B row j = [Re w_j | Im w_j] (j < n), [Im w_j | -Re w_j] (n + j),
+//   C row i = [Re c_i. | Im c_i.]   (x_i, w_j columns of X and W),
+// in split TF32 (three products).  Placement, in buffers free at this point: B1 -> S, B2 -> G,
+// A1 -> Zp, A2 -> HX (after B, the only reader of HX, has been built), C -> T.  For X in FP64
+// (second step) A holds the split of fl32(X).
+__global__ void __launch_bounds__(256) k_w_prep_B(const MmfDesc* __restrict__ descs,
+                                                  const int* __restrict__ idx,
+                                                  const double2* __restrict__ Xg,
+                                                  const double2* __restrict__ HXg,
+                                                  const double* __restrict__ lam0g,
+                                                  double2* __restrict__ B1g, double2* __restrict__ B2g) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n, la = xe_la(n);
+    const double2* X = Xg + d.mat_off;
+    const double2* HX = HXg + d.mat_off;
+    const double* lam0 = lam0g + d.vec_off;
+    float* B1 = reinterpret_cast<float*>(B1g + d.mat_off);
+    float* B2 = reinterpret_cast<float*>(B2g + d.mat_off);
+    const int64_t tot = (int64_t)2 * n * la;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / la), k = (int)(e - (int64_t)j * la);
+        float v = 0.f;
+        if (k < 2 * n) {
+            const int jj = j < n ? j : j - n, kk = k < n ? k : k - n;
+            const int64_t o = (int64_t)jj * d.ld + kk;
+            const double2 w = HX[o] - lam0[jj] * X[o];
+            double r;
+            if (j < n) r = (k < n) ? w.x : w.y;
+            else r = (k < n) ? w.y : -w.x;
+            v = (float)r;
+        }
+        const float v1 = tf32_round(v);
+        B1[e] = v1;
+        B2[e] = tf32_round(v - v1);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_w_prep_A(const MmfDesc* __restrict__ descs,
+                                                  const int* __restrict__ idx,
+                                                  const double2* __restrict__ Xg,
+                                                  float2* __restrict__ A1g, double2* __restrict__ A2g) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n, la = xe_la(n);
+    const double2* X = Xg + d.mat_off;
+    float* A1 = reinterpret_cast<float*>(A1g + d.mat_off);
+    float* A2 = reinterpret_cast<float*>(A2g + d.mat_off);
+    const int64_t tot = (int64_t)n * la;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / la), k = (int)(e - (int64_t)i * la);
+        float v = 0.f;
+        if (k < 2 * n) {
+            const double2 x = X[(int64_t)i * d.ld + (k < n ? k : k - n)];
+            v = (float)(k < n ? x.x : x.y);
+        }
+        const float v1 = tf32_round(v);
+        A1[e] = v1;
+        A2[e] = tf32_round(v - v1);
+    }
+}
+
+// B rows for C' = X1^H Dx: [Re dx_j | Im dx_j] (j < n), [Im dx_j | -Re dx_j] (n + j), with
+// Dx = X - fl32(X) (exact in FP64), split in TF32 pieces
+__global__ void __launch_bounds__(256) k_d_prep_B(const MmfDesc* __restrict__ descs,
+                                                  const int* __restrict__ idx,
+                                                  const double2* __restrict__ Xg,
+                                                  double2* __restrict__ B1g, double2* __restrict__ B2g) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n, la = xe_la(n);
+    const double2* X = Xg + d.mat_off;
+    float* B1 = reinterpret_cast<float*>(B1g + d.mat_off);
+    float* B2 = reinterpret_cast<float*>(B2g + d.mat_off);
+    const int64_t tot = (int64_t)2 * n * la;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / la), k = (int)(e - (int64_t)j * la);
+        float v = 0.f;
+        if (k < 2 * n) {
+            const int jj = j < n ? j : j - n, kk = k < n ? k : k - n;
+            const double2 x = X[(int64_t)jj * d.ld + kk];
+            const double2 dx = make_double2(x.x - (double)(float)x.x, x.y - (double)(float)x.y);
+            double r;
+            if (j < n) r = (k < n) ? dx.x : dx.y;
+            else r = (k < n) ? dx.y : -dx.x;
+            v = (float)r;
+        }
+        const float v1 = tf32_round(v);
+        B1[e] = v1;
+        B2[e] = tf32_round(v - v1);
+    }
+}
+
+// one job per system: A = [A1, A1, A2] (Zp, HX), B = [B1, B2, B1] (S, G), C at float offset coff
+// of the system's T slot
+__global__ void k_w_jobs(const MmfDesc* __restrict__ descs, const int* __restrict__ idx, int count,
+                         float2* Zp, double2* G, double2* S, double2* HX, double2* T, int second_c,
+                         UmmaJob* jobs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const MmfDesc d = descs[idx[i]];
+    const int n = d.n, la = xe_la(n);
+    const float* A1 = reinterpret_cast<const float*>(Zp + d.mat_off);
+    const float* A2 = reinterpret_cast<const float*>(HX + d.mat_off);
+    const float* B1 = reinterpret_cast<const float*>(S + d.mat_off);
+    const float* B2 = reinterpret_cast<const float*>(G + d.mat_off);
+    UmmaJob j;
+    j.A[0] = A1; j.B[0] = B1;
+    j.A[1] = A1; j.B[1] = B2;
+    j.A[2] = A2; j.B[2] = B1;
+    j.C = reinterpret_cast<float*>(T + d.mat_off) + (second_c ? (int64_t)2 * n * n : 0);
+    j.M = n; j.N = 2 * n; j.K = 2 * n;
+    j.lda = la; j.ldb = la; j.ldc = 2 * n;
+    jobs[i] = j;
+}
+
+// G <- G + C' + C'^H (both triangles; C' row i = [Re c'_i. | Im c'_i.])
+__global__ void __launch_bounds__(256) k_gram_fix(const MmfDesc* __restrict__ descs,
+                                                  const int* __restrict__ idx, double2* __restrict__ Gg,
+                                                  const double2* __restrict__ Tg) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n;
+    double2* G = Gg + d.mat_off;
+    const float* Cp = reinterpret_cast<const float*>(Tg + d.mat_off) + (int64_t)2 * n * n;
+    const int64_t tot = (int64_t)n * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / n), i = (int)(e - (int64_t)j * n);
+        const double re = (double)Cp[(int64_t)i * 2 * n + j] + (double)Cp[(int64_t)j * 2 * n + i];
+        const double im = (double)Cp[(int64_t)i * 2 * n + n + j] - (double)Cp[(int64_t)j * 2 * n + n + i];
+        double2& g = G[(int64_t)j * d.ld + i];
+        g = make_double2(g.x + re, i == j ? 0.0 : g.y + im);
+    }
+}
+
 // ------------------------------------------------------------------ lam, clusters
-// One CTA per system: lam_i = s_ii / g_ii; link_i = pair (i, i+1) clustered; cluster id = the
-// first index of its run.  aux per system: cid (n ints) stored in the E2 buffer's tail.
+// C = X^H W from the tensor cores, at the start of the system's slot of the T buffer: row i holds
+// Re c_i. (n floats) then Im c_i. (n floats).  C' (second full step) follows it.
+__device__ __forceinline__ double2 c_entry(const float* C, int n, int i, int j) {
+    return make_double2((double)C[(int64_t)i * 2 * n + j], (double)C[(int64_t)i * 2 * n + n + j]);
+}
+// s_ij - lam_j g_ij in the residual form, with dl_j = lam_j - lam0_j = c_jj / g_jj
+__device__ __forceinline__ double2 oa_num(const float* C, int n, int i, int j, double2 g, double dl_j) {
+    return c_entry(C, n, i, j) - dl_j * g;
+}
+
+// One CTA per system: lam_i = lam0_i + c_ii / g_ii; link_i = pair (i, i+1) clustered; cluster
+// id = the first index of its run.  aux per system: cid (n ints) stored in the E2 buffer's tail.
 __global__ void __launch_bounds__(256) k_oa_lambda(const MmfDesc* __restrict__ descs,
                                                    const int* __restrict__ idx,
                                                    const double2* __restrict__ Gg,
-                                                   const double2* __restrict__ Sg,
+                                                   const double2* __restrict__ Cg,
+                                                   const double* __restrict__ lam0g,
                                                    double* __restrict__ lamg,
                                                    int* __restrict__ cidg) {
     const MmfDesc d = descs[idx[blockIdx.x]];
     const int n = d.n;
     const double2* G = Gg + d.mat_off;
-    const double2* S = Sg + d.mat_off;
+    const float* C = reinterpret_cast<const float*>(Cg + d.mat_off);
+    const double* lam0 = lam0g + d.vec_off;
     double* lam = lamg + d.vec_off;
     int* cid = cidg + d.vec_off;
     __shared__ double hmax;
     for (int i = threadIdx.x; i < n; i += blockDim.x)
-        lam[i] = S[(int64_t)i * d.ld + i].x / G[(int64_t)i * d.ld + i].x;
+        lam[i] = lam0[i] + (double)C[(int64_t)i * 2 * n + i] / G[(int64_t)i * d.ld + i].x;
     __syncthreads();
     if (threadIdx.x == 0) {
         double m = 0.0;
@@ -196,8 +354,7 @@ __global__ void __launch_bounds__(256) k_oa_lambda(const MmfDesc* __restrict__ d
         int link = 0;
         if (i + 1 < n) {
             const double gap = fabs(lam[i + 1] - lam[i]);
-            const double2 s = S[(int64_t)(i + 1) * d.ld + i], g = G[(int64_t)(i + 1) * d.ld + i];
-            const double2 num = s - lam[i + 1] * g;
+            const double2 num = oa_num(C, n, i, i + 1, G[(int64_t)(i + 1) * d.ld + i], lam[i + 1] - lam0[i + 1]);
             link = (gap <= RF_TAU * sqrt(abs2(num))) || (gap <= 1e-13 * hmax);
         }
         cid[i] = link;
@@ -218,14 +375,16 @@ __global__ void __launch_bounds__(256) k_oa_lambda(const MmfDesc* __restrict__ d
 __global__ void __launch_bounds__(256) k_oa_etilde(const MmfDesc* __restrict__ descs,
                                                    const int* __restrict__ idx,
                                                    double2* __restrict__ Gg,
-                                                   const double2* __restrict__ Sg,
+                                                   const double2* __restrict__ Cg,
+                                                   const double* __restrict__ lam0g,
                                                    const double* __restrict__ lamg,
                                                    const int* __restrict__ cidg) {
     const MmfDesc d = descs[idx[blockIdx.y]];
     const int n = d.n;
     const int64_t tot = (int64_t)n * n;
     double2* G = Gg + d.mat_off;
-    const double2* S = Sg + d.mat_off;
+    const float* C = reinterpret_cast<const float*>(Cg + d.mat_off);
+    const double* lam0 = lam0g + d.vec_off;
     const double* lam = lamg + d.vec_off;
     const int* cid = cidg + d.vec_off;
     double hmax = fmax(fabs(lam[0]), fabs(lam[n - 1]));
@@ -238,7 +397,7 @@ __global__ void __launch_bounds__(256) k_oa_etilde(const MmfDesc* __restrict__ d
         if (i == j) {
             et = make_double2(0.5 * (1.0 - g.x), 0.0);
         } else {
-            const double2 num = S[o] - lam[j] * g;
+            const double2 num = oa_num(C, n, i, j, g, lam[j] - lam0[j]);
             const double gap = lam[j] - lam[i];
             const bool clustered = cid[i] == cid[j] || fabs(gap) <= RF_TAU * sqrt(abs2(num)) ||
                                    fabs(gap) <= 1e-13 * fmax(hmax, fabs(lam[i]));
@@ -248,87 +407,17 @@ __global__ void __launch_bounds__(256) k_oa_etilde(const MmfDesc* __restrict__ d
     }
 }
 
-// ------------------------------------------------------------------ Xn = X + X Et (FP32 GEMM)
-__global__ void __launch_bounds__(256) k_xe_update(const MmfDesc* __restrict__ descs,
-                                                   const int* __restrict__ idx,
-                                                   const double2* __restrict__ Xg,
-                                                   const double2* __restrict__ Etg,
-                                                   double2* __restrict__ Xn) {
-    __shared__ float2 xs[RF_KC][64 + 1];
-    __shared__ float2 es[RF_KC][64 + 1];
-    const MmfDesc d = descs[idx[blockIdx.z]];
-    const int n = d.n;
-    const int r0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
-    if (r0 >= n || c0 >= n) return;
-    const double2* X = Xg + d.mat_off;
-    const double2* Et = Etg + d.mat_off;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // rows tx + 16a, cols ty + 16b
-    float2 acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
-    for (int k0 = 0; k0 < n; k0 += RF_KC) {
-        for (int e = threadIdx.x; e < RF_KC * 64; e += 256) {
-            // X tile: rows r0..r0+63, cols k0..k0+31 (coalesced over rows)
-            const int kk = e / 64, rr = e - kk * 64;
-            const int r = r0 + rr, k = k0 + kk;
-            double2 v = (r < n && k < n) ? X[(int64_t)k * d.ld + r] : make_double2(0.0, 0.0);
-            xs[kk][rr] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
-            // Et tile: rows k0..k0+31, cols c0..c0+63 (coalesced over k)
-            const int cc = e / RF_KC, k2 = e - cc * RF_KC;
-            const int c = c0 + cc, kr = k0 + k2;
-            double2 w = (c < n && kr < n) ? Et[(int64_t)c * d.ld + kr] : make_double2(0.0, 0.0);
-            es[k2][cc] = make_float2(__double2float_rn(w.x), __double2float_rn(w.y));
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < RF_KC; ++kk) {
-            float2 xa[4], eb[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) xa[a] = xs[kk][tx + 16 * a];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) eb[b] = es[kk][ty + 16 * b];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    acc[a][b].x = fmaf(xa[a].x, eb[b].x, fmaf(-xa[a].y, eb[b].y, acc[a][b].x));
-                    acc[a][b].y = fmaf(xa[a].x, eb[b].y, fmaf(xa[a].y, eb[b].x, acc[a][b].y));
-                }
-        }
-        __syncthreads();
-    }
-    double2* O = Xn + d.mat_off;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int r = r0 + tx + 16 * a, c = c0 + ty + 16 * b;
-            if (r < n && c < n) {
-                const int64_t o = (int64_t)c * d.ld + r;
-                const double2 x = X[o];
-                O[o] = make_double2(x.x + (double)acc[a][b].x, x.y + (double)acc[a][b].y);
-            }
-        }
-}
-
 // ------------------------------------------------------------------ Xn = X + X Et on tensor cores
 // The complex product is a real product of twice the size,
 //   [Re Y | Im Y] = [Re X, Im X] [[Re E, Im E], [-Im E, Re E]],
 // taken on the tcgen05 engine in split TF32 (x = x1 + x2, x1 = tf32(x), x2 = tf32(x - x1);
-// x y ~ x1 y1 + x1 y2 + x2 y1, about FP32 accuracy; Et is small, so that is ample).  Operands are
+// x y ~ x1 y1 + x1 y2 + x2 y1, about FP32 accuracy) for the entries of Et outside the band
+// |i - j| <= RF_W, which are small (|Et_ij| ~ eps32 |H_F| / gap_ij), so that the FP32 error
+// stays far below the target.  The band, where Et reaches ~0.05 for close pairs, is applied in
+// double-FP32 on the SIMT units (k_et_band, k_xe_apply).  Operands are
 // K-major rows of la = round_up(2n, 4) floats, placed in buffers free at this point:
 // B1 -> S, B2 -> HX (2n rows), A1 -> Zp (n rows), A2 and then C (n x 2n) -> the Et buffer after
 // B has been built from it.
-__device__ __forceinline__ float tf32_round(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-__device__ __forceinline__ int xe_la(int n) { return (2 * n + 3) & ~3; }
-
 __global__ void __launch_bounds__(256) k_xe_prep_B(const MmfDesc* __restrict__ descs,
                                                    const int* __restrict__ idx,
                                                    const double2* __restrict__ Etg,
@@ -344,11 +433,13 @@ __global__ void __launch_bounds__(256) k_xe_prep_B(const MmfDesc* __restrict__ d
         float v = 0.f;
         if (k < 2 * n) {
             const int jj = j < n ? j : j - n, kk = k < n ? k : k - n;
-            const double2 x = Et[(int64_t)jj * d.ld + kk];
-            double w;
-            if (j < n) w = (k < n) ? x.x : -x.y;
-            else w = (k < n) ? x.y : x.x;
-            v = (float)w;
+            if (abs(jj - kk) > RF_W) {  // the band is applied in double-FP32 by k_xe_apply
+                const double2 x = Et[(int64_t)jj * d.ld + kk];
+                double w;
+                if (j < n) w = (k < n) ? x.x : -x.y;
+                else w = (k < n) ? x.y : x.x;
+                v = (float)w;
+            }
         }
         const float v1 = tf32_round(v);
         B1[e] = v1;
@@ -412,19 +503,60 @@ __global__ void k_xe_jobs(const MmfDesc* __restrict__ descs, const int* __restri
     jobs[i] = j;
 }
 
-__global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ descs,
-                                                  const int* __restrict__ idx, double2* __restrict__ Xg,
-                                                  const double2* __restrict__ R) {
+// the band of Et, Eb[i * RF_BW + (j - i + RF_W)] = Et(i, j) (0 outside the matrix), saved before
+// the Et buffer is reused for the tensor-core operands
+__global__ void __launch_bounds__(256) k_et_band(const MmfDesc* __restrict__ descs,
+                                                 const int* __restrict__ idx,
+                                                 const double2* __restrict__ Etg,
+                                                 double2* __restrict__ Ebg) {
     const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n;
+    const double2* Et = Etg + d.mat_off;
+    double2* Eb = Ebg + (int64_t)d.vec_off * RF_BW;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * RF_BW; e += gridDim.x * blockDim.x) {
+        const int i = e / RF_BW, j = i + (e - i * RF_BW) - RF_W;
+        Eb[e] = (j >= 0 && j < n) ? Et[(int64_t)j * d.ld + i] : make_double2(0.0, 0.0);
+    }
+}
+
+// Xn(:, j) = X(:, j) + C(:, j) + sum_{|i-j|<=W} X(:, i) Et(i, j): C from the tensor cores (Et
+// outside the band), the band in double-FP32 (X is FP32-exact in the first step, Et split in two
+// FP32 pieces).  Xn goes to a separate buffer (the band reads neighbouring columns of X).
+__global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ descs,
+                                                  const int* __restrict__ idx, const double2* __restrict__ Xg,
+                                                  const double2* __restrict__ R, const double2* __restrict__ Ebg,
+                                                  double2* __restrict__ Xn) {
+    __shared__ Split et[RF_BW];
+    const MmfDesc d = descs[idx[blockIdx.z]];
     const int n = d.n, la = xe_la(n);
+    const int j = blockIdx.y;
+    if (j >= n) return;
+    const double2* Eb = Ebg + (int64_t)d.vec_off * RF_BW;
+    if (threadIdx.x < RF_BW) {
+        const int i = j + threadIdx.x - RF_W;
+        et[threadIdx.x] = split((i >= 0 && i < n) ? Eb[(int64_t)i * RF_BW + (j - i + RF_W)] : make_double2(0.0, 0.0));
+    }
+    __syncthreads();
     const float* C = reinterpret_cast<const float*>(R + d.mat_off) + (int64_t)n * la;
-    double2* X = Xg + d.mat_off;
-    const int64_t tot = (int64_t)n * n;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e / n), r = (int)(e - (int64_t)j * n);  // X(r, j), rows fastest
+    const double2* X = Xg + d.mat_off;
+    const int qlo = max(0, RF_W - j), qhi = min(RF_BW, n - j + RF_W);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        DF ar = DF{0.f, 0.f}, ai = DF{0.f, 0.f};
+        for (int q = qlo; q < qhi; ++q) {
+            const int i = j + q - RF_W;
+            const double2 x = X[(int64_t)i * d.ld + r];
+            const float xr = (float)x.x, xi = (float)x.y;
+            const Split e = et[q];
+            df_mac1(ar, xr, e.r1, e.r2);
+            df_mac1(ar, -xi, e.i1, e.i2);
+            df_mac1(ai, xr, e.i1, e.i2);
+            df_mac1(ai, xi, e.r1, e.r2);
+        }
         const double2 x = X[(int64_t)j * d.ld + r];
-        const float yr = C[(int64_t)r * 2 * n + j], yi = C[(int64_t)r * 2 * n + n + j];
-        X[(int64_t)j * d.ld + r] = make_double2(x.x + (double)yr, x.y + (double)yi);
+        const double2 band = df_value(ar, ai);
+        const float cr = C[(int64_t)r * 2 * n + j], ci = C[(int64_t)r * 2 * n + n + j];
+        Xn[d.mat_off + (int64_t)j * d.ld + r] =
+            make_double2(x.x + ((double)cr + band.x), x.y + ((double)ci + band.y));
     }
 }
 
@@ -657,8 +789,6 @@ __global__ void __launch_bounds__(256) k_sort_pairs(const MmfDesc* __restrict__ 
 // order are second order in (eps |H| / gap) and negligible; the next step only forms G and S for
 // pairs |i - j| <= RF_W (band storage Bm[i * (2 RF_W + 1) + (j - i + RF_W)]) and applies
 // X <- X + X Et with the banded Et.
-#define RF_W 16
-#define RF_BW (2 * RF_W + 1)
 #define RF_BC 32            // columns per CTA
 #define RF_BR 16            // rows per staged chunk
 
@@ -830,33 +960,50 @@ __global__ void __launch_bounds__(256) k_xe_band(const MmfDesc* __restrict__ des
     }
 }
 
-// The refinement is launched in three parts so that the host can time the FP64-accurate Gram
-// product on its own: (1) HX = H_F X, (2) G = X^H X and S = X^H HX, (3) the rest of the full step,
-// the banded step, the cluster separations and the final ordering.
-cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const double2* coef, const double2* X, double2* HX) {
+// The refinement is launched in parts so that the host can time the FP64-accurate Gram product
+// on its own and choose the second step per system:
+//   pre:    HX = H_F X, C = X^H W (and C' = X1^H Dx for a second full step) on the tensor cores
+//   gram:   G = X1^H X1 in double-FP32 (+ C' + C'^H)
+//   update: lam, Et, X <- X + X Et, cluster separation
+//   band:   the banded second step;   finish: final ordering.
+cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const double2* coef, const double2* X, const double* lam0,
+                                  double2* HX, double2* G, double2* S, float2* Zp, double2* T, void* jobs,
+                                  int* status, int second) {
     if (L.count <= 0) return cudaSuccess;
     k_apply_hf<<<dim3((L.nmax + 255) / 256, (L.nmax + 15) / 16, L.count), 256, 0, L.stream>>>(
         L.desc, L.idx, coef, X, HX, 0, L.nmax);
+    k_w_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, HX, lam0, S, G);
+    k_w_prep_A<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, Zp, HX);
+    k_w_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, Zp, G, S, HX, T, 0,
+                                                         (UmmaJob*)jobs);
+    cudaError_t e = mmf_launch_umma(jobs, L.count, 3, L.nmax, 2 * L.nmax, 0, status, L.stream);
+    if (e != cudaSuccess || !second) return e;
+    k_d_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, S, G);
+    k_w_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, Zp, G, S, HX, T, 1,
+                                                         (UmmaJob*)jobs);
+    return mmf_launch_umma(jobs, L.count, 3, L.nmax, 2 * L.nmax, 0, status, L.stream);
+}
+
+cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const double2* X, float2* X1, double2* G, const double2* T,
+                                   int second) {
+    if (L.count <= 0) return cudaSuccess;
+    const int nt = (L.nmax + RF_TILE - 1) / RF_TILE;
+    // G of fl32(X): X itself in the first step (FP32 eigenvectors), X1 in a second full step
+    k_to_fp32<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, X1);
+    k_gram_x1<<<dim3(nt * (nt + 1) / 2, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X1, G);
+    if (second) k_gram_fix<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, T);
     return cudaGetLastError();
 }
 
-cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const double2* X, const double2* HX, double2* G,
-                                   double2* S) {
+cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, double2* X, const double* lam0,
+                                     double2* G, double2* S, double2* HX, const double2* T, double* lam,
+                                     int* status, int* cid, int64_t mat_elems, float2* Zp, void* jobs,
+                                     double2* Eb) {
     if (L.count <= 0) return cudaSuccess;
-    const int T = (L.nmax + RF_TILE - 1) / RF_TILE;
-    // the first refinement step starts from FP32 eigenvectors: X is FP32-exact
-    k_gram_df32<true><<<dim3(T * (T + 1) / 2, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, HX, G, S);
-    return cudaGetLastError();
-}
-
-cudaError_t mmf_launch_refine_post(const MmfLaunch& L, const double2* coef, double2* X, double* E,
-                                   double2* G, double2* S, double2* HX, double* lam, int* status,
-                                   int* cid, int64_t mat_elems, float2* Zp, void* jobs) {
-    if (L.count <= 0) return cudaSuccess;
-    // rest of the full step
-    k_oa_lambda<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
-    k_oa_etilde<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
-    // X <- X + X Et on the tensor cores (split TF32)
+    k_oa_lambda<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, T, lam0, lam, cid);
+    k_oa_etilde<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, T, lam0, lam, cid);
+    // X <- X + X Et: band in double-FP32, the rest on the tensor cores (split TF32)
+    k_et_band<<<dim3(64, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, Eb);
     k_xe_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, S, HX);
     k_xe_prep_A<<<dim3((L.nmax + 31) / 32, (L.nmax + 31) / 32, L.count), 256, 0, L.stream>>>(
         L.desc, L.idx, X, Zp, G);
@@ -864,9 +1011,16 @@ cudaError_t mmf_launch_refine_post(const MmfLaunch& L, const double2* coef, doub
                                                           (UmmaJob*)jobs);
     cudaError_t e = mmf_launch_umma(jobs, L.count, 3, L.nmax, 2 * L.nmax, 0, status, L.stream);
     if (e != cudaSuccess) return e;
-    k_xe_apply<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, G);
+    k_xe_apply<<<dim3((L.nmax + 255) / 256, L.nmax, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, G, Eb, HX);
+    e = cudaMemcpyAsync(X, HX, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
+    if (e != cudaSuccess) return e;
     k_cluster_sep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, coef, X, HX, lam, cid, status);
-    // banded step
+    return cudaGetLastError();
+}
+
+cudaError_t mmf_launch_refine_band(const MmfLaunch& L, const double2* coef, double2* X, double2* G, double2* S,
+                                   double2* HX, double* lam, int* status, int* cid, int64_t mat_elems) {
+    if (L.count <= 0) return cudaSuccess;
     k_apply_hf<<<dim3((L.nmax + 255) / 256, (L.nmax + 15) / 16, L.count), 256, 0, L.stream>>>(
         L.desc, L.idx, coef, X, HX, 0, L.nmax);
     k_gram_band_df32<<<dim3((L.nmax + RF_BC - 1) / RF_BC, L.count), 256, 0, L.stream>>>(
@@ -874,11 +1028,17 @@ cudaError_t mmf_launch_refine_post(const MmfLaunch& L, const double2* coef, doub
     k_oa_lambda_band<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
     k_xe_band<<<dim3((L.nmax + 255) / 256, L.nmax, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, G, S,
                                                                                 lam, cid, HX);
-    e = cudaMemcpyAsync(X, HX, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
+    cudaError_t e = cudaMemcpyAsync(X, HX, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
     if (e != cudaSuccess) return e;
     k_cluster_sep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, coef, X, HX, lam, cid, status);
+    return cudaGetLastError();
+}
+
+cudaError_t mmf_launch_refine_finish(const MmfLaunch& L, double2* X, double* E, const double* lam, double2* S,
+                                     int64_t mat_elems) {
+    if (L.count <= 0) return cudaSuccess;
     k_sort_pairs<<<dim3(L.nmax, L.count), 256, 0, L.stream>>>(L.desc, L.idx, lam, X, E, S);
-    e = cudaMemcpyAsync(X, S, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
+    cudaError_t e = cudaMemcpyAsync(X, S, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -21,6 +21,18 @@
 
 __device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
 
+// FP32 solver work layout inside a system's slot of 3 n^2 doubles (24 n^2 bytes): from the first
+// 16-byte boundary, the packed factors (n^2 float4), the iterate (n^2 floats), then (at an even
+// float offset) the scaled (d_i, e_{i-1}^2) pairs and the scaled e_i (3 n floats).  Needs n >= 4.
+__device__ __forceinline__ float* tri_f32_base(const float* fwork, const MmfDesc& d) {
+    const uintptr_t p = (uintptr_t)(fwork + 6 * d.sq_off);
+    return (float*)((p + 15) & ~(uintptr_t)15);
+}
+__device__ __forceinline__ float2* tri_f32_de2(const float* fwork, const MmfDesc& d) {
+    const int64_t nn = (int64_t)d.n * d.n;
+    return (float2*)(tri_f32_base(fwork, d) + 5 * nn + (nn & 1));
+}
+
 // per system: gl, gu, pivmin, tnorm
 __global__ void k_tri_prep(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                            const double* __restrict__ dvec, const double* __restrict__ evec,
@@ -73,10 +85,10 @@ __global__ void k_tri_prep(const MmfDesc* __restrict__ descs, const int* __restr
     }
     if (fwork == nullptr) return;
     __syncthreads();
-    // scaled FP32 copies after the 4 n^2 floats of the inverse-iteration arrays:
+    // scaled FP32 copies after the 5 n^2 floats of the inverse-iteration arrays:
     // (d_i s, e_{i-1}^2 s^2) pairs, then e_i s
     const double sc = scale_sh;
-    float2* de2 = (float2*)(fwork + 2 * d.sq_off * 3 + 4 * (int64_t)n * n);
+    float2* de2 = tri_f32_de2(fwork, d);
     float* ef = (float*)(de2 + n);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const double el = (i > 0) ? ee[i - 1] * sc : 0.0;
@@ -196,7 +208,7 @@ template <> struct TriIn<float> {
     __device__ TriIn(const MmfDesc& ds, const double*, const double*, const double*, const double* aux_sys,
                      const float* fwork) {
         const int n = ds.n;
-        de2 = (const float2*)(fwork + 2 * ds.sq_off * 3 + 4 * (int64_t)n * n);
+        de2 = tri_f32_de2(fwork, ds);
         e = (const float*)(de2 + n);
         scale = aux_sys[4];
     }
@@ -299,9 +311,46 @@ __device__ void tri_solve(const In& in, int n, R lam, R pivtiny, R* y, R* u0, R*
     }
 }
 
+// FP32 variant: the three U-factor entries of row i and the eliminated right-hand side are kept
+// together, F[i * s] = (u0, u1, u2, rhs), so that each step of either sweep moves one 16-byte
+// word per thread (the sweeps are latency-bound chains).
+template <class In>
+__device__ void tri_solve_packed(const In& in, int n, float lam, float pivtiny, float* y, float4* F, int64_t s) {
+    float p = in.dv(0) - lam, q = (n > 1) ? in.ev(0) : 0.f, r = 0.f, rb = y[0];
+    for (int i = 0; i < n - 1; ++i) {
+        const float a = in.ev(i);
+        const float bb = in.dv(i + 1) - lam;
+        const float cc = (i + 1 < n - 1) ? in.ev(i + 1) : 0.f;
+        const float b1 = y[(int64_t)(i + 1) * s];
+        if (fabsf(a) <= fabsf(p)) {
+            if (p == 0.f) p = pivtiny;
+            const float l = tdiv(a, p);
+            F[(int64_t)i * s] = make_float4(p, q, r, rb);
+            p = bb - l * q; q = cc - l * r; r = 0.f; rb = b1 - l * rb;
+        } else {
+            const float l = tdiv(p, a);
+            F[(int64_t)i * s] = make_float4(a, bb, cc, b1);
+            const float np = q - l * bb, nq = r - l * cc, nrb = rb - l * b1;
+            p = np; q = nq; r = 0.f; rb = nrb;
+        }
+    }
+    if (fabsf(p) < pivtiny) p = (p < 0.f) ? -pivtiny : pivtiny;
+    float y2 = 0.f, y1 = tdiv(rb, p);
+    y[(int64_t)(n - 1) * s] = y1;
+    for (int i = n - 2; i >= 0; --i) {
+        const float4 f = F[(int64_t)i * s];
+        float up = f.x;
+        if (fabsf(up) < pivtiny) up = (up < 0.f) ? -pivtiny : pivtiny;
+        const float yi = tdiv(f.w - f.y * y1 - f.z * y2, up);
+        y[(int64_t)i * s] = yi;
+        y2 = y1;
+        y1 = yi;
+    }
+}
+
 // Inverse iteration.  FP64: the iterate lives in Y itself and the factors in work (3 n^2
-// doubles).  FP32: factors and iterate are n^2-float arrays at the start of work, and the
-// normalised iterate is written to Y (FP64) at the end.
+// doubles).  FP32: the packed factors (n^2 float4) and the iterate (n^2 floats) are at the start
+// of work, and the normalised iterate is written to Y (FP64) at the end.
 template <class R>
 __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ descs,
                                                  const int* __restrict__ idx,
@@ -329,11 +378,12 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
     const R pivtiny = eps * fmax(tn, R(1e-30));
     const int64_t s = n;  // row stride of the row-major arrays
     const int64_t nn = (int64_t)n * n;
-    R* base = sizeof(R) == 8 ? (R*)(work + 3 * d.sq_off) : (R*)((float*)work + 2 * d.sq_off * 3);
+    R* base = sizeof(R) == 8 ? (R*)(work + 3 * d.sq_off) : (R*)tri_f32_base((const float*)work, d);
     R* u0 = base;
     R* u1 = u0 + nn;
     R* u2 = u1 + nn;
-    R* Yw = sizeof(R) == 8 ? (R*)(Yg + d.sq_off) : u2 + nn;
+    float4* F = (float4*)base;  // FP32: packed factors (4 n^2 floats), then the iterate
+    R* Yw = sizeof(R) == 8 ? (R*)(Yg + d.sq_off) : base + 4 * nn;
     R lamprev = R(0);
     for (int j = k; j < kend; ++j) {
         R lam = R(E[j] * sc);
@@ -349,7 +399,10 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
         for (int i = 0; i < n; ++i)
             y[(int64_t)i * s] = hash_unit<R>(((uint64_t)sid << 40) ^ ((uint64_t)j << 20) ^ (uint64_t)i);
         for (int it = 0; it < iters; ++it) {
-            tri_solve<R>(in, n, lam, pivtiny, y, a0, a1, a2, s);
+            if constexpr (sizeof(R) == 4)
+                tri_solve_packed(in, n, lam, pivtiny, (float*)y, F + j, s);
+            else
+                tri_solve<R>(in, n, lam, pivtiny, y, a0, a1, a2, s);
             // orthogonalise against the cluster's earlier vectors
             for (int jp = k; jp < j; ++jp) {
                 const R* z = Yw + jp;

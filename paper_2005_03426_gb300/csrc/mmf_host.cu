@@ -44,6 +44,7 @@ struct mmf_ctx {
     size_t budget = 0, used = 0;
     int64_t jacobi_n[2] = {-1, -1};  // per precision; -1 = library default
     int64_t large_n = -1;            // whole-GPU reduction from this n on; -1 = when one CTA cannot
+    int64_t refine_full_n = -1;      // mixed path: second refinement step in full from this n on
     std::recursive_mutex mu;
 };
 
@@ -74,6 +75,8 @@ struct mmf_batch {
     std::vector<mmf_sys*> sys;
     std::vector<MmfDesc> desc;
     std::vector<int> all, small, large, medium, huge;  // large = medium + huge
+    std::vector<int> rband, rfull;                     // mixed: banded / full second refinement step
+    int nmax_rband = 0, nmax_rfull = 0;
     int nmax_all = 0, nmax_small = 0, nmax_large = 0, Mmax = 1, Dmax = 1;
     int64_t n_coef = 0, n_mat = 0, n_vec = 0, n_sq = 0, n_pan = 0, n_t = 0, n_f = 0, n_u = 0,
             n_p = 0;
@@ -82,6 +85,7 @@ struct mmf_batch {
     size_t bytes = 0;
     MmfDesc* d_desc = nullptr;
     int *d_all = nullptr, *d_small = nullptr, *d_large = nullptr, *d_medium = nullptr, *d_status = nullptr;
+    int *d_rband = nullptr, *d_rfull = nullptr;
     int nmax_medium = 0;
     double2* d_coef = nullptr;
     void* d_H = nullptr;
@@ -94,7 +98,8 @@ struct mmf_batch {
     double* d_t = nullptr;
     double2 *d_F = nullptr, *d_U = nullptr;
     double* d_P = nullptr;
-    double2 *d_R = nullptr, *d_S = nullptr, *d_HX = nullptr;
+    double2 *d_R = nullptr, *d_S = nullptr, *d_HX = nullptr, *d_Eb = nullptr, *d_T = nullptr;
+    float2* d_X1 = nullptr;
     double* d_E2 = nullptr;
     int* d_cid = nullptr;
     void* d_jobs = nullptr;
@@ -129,7 +134,13 @@ static int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 static int jacobi_default(int prec) { return prec == MMF_MIXED ? MMF_JACOBI_NMAX_F32 : MMF_JACOBI_NMAX_F64; }
 static int jacobi_nmax(const mmf_ctx* c, int prec) {
     const int64_t v = c ? c->jacobi_n[prec == MMF_MIXED] : -1;
-    return v < 0 ? jacobi_default(prec) : (int)std::min<int64_t>(v, jacobi_default(prec));
+    // systems with n <= 4 always take the Jacobi kernel (the tridiagonal solver's FP32 work layout
+    // assumes n >= 4)
+    return v < 0 ? jacobi_default(prec) : (int)std::max<int64_t>(4, std::min<int64_t>(v, jacobi_default(prec)));
+}
+
+static int64_t refine_full_n(const mmf_ctx* c) {
+    return (c && c->refine_full_n >= 0) ? c->refine_full_n : (int64_t)MMF_REFINE_FULL2_N;
 }
 
 static int64_t sys_dim(const mmf_sys* s) {
@@ -214,6 +225,7 @@ extern "C" int mmf_ctx_set_option(mmf_ctx* c, int option, int64_t value) {
         case MMF_OPT_JACOBI_N_FP64: c->jacobi_n[0] = value; return MMF_OK;
         case MMF_OPT_JACOBI_N_MIXED: c->jacobi_n[1] = value; return MMF_OK;
         case MMF_OPT_LARGE_N: c->large_n = value; return MMF_OK;
+        case MMF_OPT_REFINE_FULL_N: c->refine_full_n = value; return MMF_OK;
         default: return fail(MMF_ERR_ARG, "unknown option");
     }
 }
@@ -408,6 +420,13 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         if (!d.small && n < lmin) b->nmax_medium = std::max(b->nmax_medium, (int)n);
         b->Mmax = std::max(b->Mmax, (int)M);
         b->Dmax = std::max(b->Dmax, s->D);
+        if (n >= refine_full_n(ctx)) {
+            b->rfull.push_back(i);
+            b->nmax_rfull = std::max(b->nmax_rfull, (int)n);
+        } else {
+            b->rband.push_back(i);
+            b->nmax_rband = std::max(b->nmax_rband, (int)n);
+        }
     }
     // device layout
     const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
@@ -415,7 +434,8 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     size_t o_desc = p.take(sizeof(MmfDesc) * count);
     size_t o_all = p.take(sizeof(int) * count), o_small = p.take(sizeof(int) * count),
            o_large = p.take(sizeof(int) * count), o_medium = p.take(sizeof(int) * count),
-           o_status = p.take(sizeof(int) * count);
+           o_status = p.take(sizeof(int) * count), o_rband = p.take(sizeof(int) * count),
+           o_rfull = p.take(sizeof(int) * count);
     size_t o_coef = p.take(sizeof(double2) * b->n_coef);
     size_t o_H = p.take(cs * b->n_mat);
     size_t o_Zf = p.take(sizeof(double2) * b->n_mat);
@@ -430,8 +450,11 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     size_t o_F = p.take(sizeof(double2) * std::max<int64_t>(b->n_f, 1));
     size_t o_U = p.take(sizeof(double2) * std::max<int64_t>(b->n_u, 1));
     size_t o_P = p.take(sizeof(double) * b->n_p);
-    size_t o_R = 0, o_S = 0, o_HX = 0, o_E2 = 0, o_cid = 0, o_jobs = 0;
+    size_t o_R = 0, o_S = 0, o_HX = 0, o_E2 = 0, o_cid = 0, o_jobs = 0, o_Eb = 0, o_T = 0, o_X1 = 0;
     if (fp32) {
+        o_Eb = p.take(sizeof(double2) * b->n_vec * MMF_REFINE_BW);
+        o_T = p.take(sizeof(double2) * b->n_mat);
+        o_X1 = p.take(sizeof(float2) * b->n_mat);
         o_R = p.take(sizeof(double2) * b->n_mat);
         o_S = p.take(sizeof(double2) * b->n_mat);
         o_HX = p.take(sizeof(double2) * b->n_mat);
@@ -459,6 +482,8 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     b->d_large = (int*)(B + o_large);
     b->d_medium = (int*)(B + o_medium);
     b->d_status = (int*)(B + o_status);
+    b->d_rband = (int*)(B + o_rband);
+    b->d_rfull = (int*)(B + o_rfull);
     b->d_coef = (double2*)(B + o_coef);
     b->d_H = B + o_H;
     b->d_Zf = (double2*)(B + o_Zf);
@@ -484,6 +509,9 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         b->d_E2 = (double*)(B + o_E2);
         b->d_cid = (int*)(B + o_cid);
         b->d_jobs = B + o_jobs;
+        b->d_Eb = (double2*)(B + o_Eb);
+        b->d_T = (double2*)(B + o_T);
+        b->d_X1 = (float2*)(B + o_X1);
     }
     if (b->pinned) {
         e = cudaMallocHost((void**)&b->h_coef, sizeof(double2) * std::max<int64_t>(b->n_coef, 1));
@@ -509,6 +537,10 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         e = cudaMemcpyAsync(b->d_large, b->large.data(), sizeof(int) * b->large.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !b->medium.empty())
         e = cudaMemcpyAsync(b->d_medium, b->medium.data(), sizeof(int) * b->medium.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !b->rband.empty())
+        e = cudaMemcpyAsync(b->d_rband, b->rband.data(), sizeof(int) * b->rband.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !b->rfull.empty())
+        e = cudaMemcpyAsync(b->d_rfull, b->rfull.data(), sizeof(int) * b->rfull.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_coef, b->h_coef, sizeof(double2) * b->n_coef, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -672,13 +704,35 @@ static int stage_eig(mmf_batch* b) {
     mark(b, ST_REFINE);
     if (fp32) {
         MmfLaunch La = launch_of(b, b->all, b->d_all, b->nmax_all);
-        LAUNCH(mmf_launch_refine_pre(La, b->d_coef, b->d_Zf, b->d_HX), 1);
+        float2* Zp = (float2*)b->d_Zp;
+        LAUNCH(mmf_launch_refine_pre(La, b->d_coef, b->d_Zf, b->d_E, b->d_HX, b->d_R, b->d_S, Zp, b->d_T,
+                                     b->d_jobs, b->d_status, 0),
+               5);
         mark(b, ST_GRAM);
-        LAUNCH(mmf_launch_refine_gram(La, b->d_Zf, b->d_HX, b->d_R, b->d_S), 1);
+        LAUNCH(mmf_launch_refine_gram(La, b->d_Zf, b->d_X1, b->d_R, b->d_T, 0), 2);
         mark(b, ST_REFINE2);
-        LAUNCH(mmf_launch_refine_post(La, b->d_coef, b->d_Zf, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_E2,
-                                      b->d_status, b->d_cid, b->n_mat, (float2*)b->d_Zp, b->d_jobs),
-               14);
+        LAUNCH(mmf_launch_refine_update(La, b->d_coef, b->d_Zf, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_T, b->d_E2,
+                                        b->d_status, b->d_cid, b->n_mat, Zp, b->d_jobs, b->d_Eb),
+               9);
+        if (!b->rband.empty()) {
+            MmfLaunch Lb = launch_of(b, b->rband, b->d_rband, b->nmax_rband);
+            LAUNCH(mmf_launch_refine_band(Lb, b->d_coef, b->d_Zf, b->d_R, b->d_S, b->d_HX, b->d_E2, b->d_status,
+                                          b->d_cid, b->n_mat),
+                   5);
+        }
+        if (!b->rfull.empty()) {
+            // second full step from lam0 = the first step's eigenvalues (E is rewritten at the end)
+            MmfLaunch Lf = launch_of(b, b->rfull, b->d_rfull, b->nmax_rfull);
+            CU(cudaMemcpyAsync(b->d_E, b->d_E2, sizeof(double) * b->n_vec, cudaMemcpyDeviceToDevice, b->stream));
+            LAUNCH(mmf_launch_refine_pre(Lf, b->d_coef, b->d_Zf, b->d_E, b->d_HX, b->d_R, b->d_S, Zp, b->d_T,
+                                         b->d_jobs, b->d_status, 1),
+                   8);
+            LAUNCH(mmf_launch_refine_gram(Lf, b->d_Zf, b->d_X1, b->d_R, b->d_T, 1), 3);
+            LAUNCH(mmf_launch_refine_update(Lf, b->d_coef, b->d_Zf, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_T,
+                                            b->d_E2, b->d_status, b->d_cid, b->n_mat, Zp, b->d_jobs, b->d_Eb),
+                   9);
+        }
+        LAUNCH(mmf_launch_refine_finish(La, b->d_Zf, b->d_E, b->d_E2, b->d_S, b->n_mat), 1);
     } else {
         mark(b, ST_GRAM);
         mark(b, ST_REFINE2);

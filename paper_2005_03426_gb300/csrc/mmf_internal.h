@@ -207,12 +207,21 @@ cudaError_t mmf_launch_hetrd_large(const MmfDesc& d, void* H, void* Vp, void* Wp
                                    void* tau, void* work, void* sc, int fp32, cudaStream_t st);
 cudaError_t mmf_launch_micromotion(const MmfLaunch& L, int D, const double2* Z, const double* t,
                                    int nt, int64_t* reps, double2* UF);
-cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const double2* coef, const double2* X, double2* HX);
-cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const double2* X, const double2* HX, double2* G,
-                                   double2* S);
-cudaError_t mmf_launch_refine_post(const MmfLaunch& L, const double2* coef, double2* X, double* E,
-                                   double2* G, double2* S, double2* HX, double* lam, int* status,
-                                   int* cid, int64_t mat_elems, float2* Zp, void* jobs);
+cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const double2* coef, const double2* X, const double* lam0,
+                                  double2* HX, double2* G, double2* S, float2* Zp, double2* T, void* jobs,
+                                  int* status, int second);
+cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const double2* X, float2* X1, double2* G, const double2* T,
+                                   int second);
+cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, double2* X, const double* lam0,
+                                     double2* G, double2* S, double2* HX, const double2* T, double* lam,
+                                     int* status, int* cid, int64_t mat_elems, float2* Zp, void* jobs,
+                                     double2* Eb);
+cudaError_t mmf_launch_refine_band(const MmfLaunch& L, const double2* coef, double2* X, double2* G, double2* S,
+                                   double2* HX, double* lam, int* status, int* cid, int64_t mat_elems);
+cudaError_t mmf_launch_refine_finish(const MmfLaunch& L, double2* X, double* E, const double* lam, double2* S,
+                                     int64_t mat_elems);
+#define MMF_REFINE_BW 33   // entries per row of the refinement's band buffer (2 W + 1)
+#define MMF_REFINE_FULL2_N 3000   // from this n on the second refinement step is a full one
 // batched tensor-core GEMM (k_umma.cu): C(m, n) = sum_p sum_k A_p(m, k) B_p(n, k), K-major
 // operands (TF32 in FP32 storage, or BF16), FP32 result
 #define UM_MAXP 3

@@ -37,6 +37,7 @@ MMF_MIXED = 1
 MMF_OPT_JACOBI_N_FP64 = 1
 MMF_OPT_JACOBI_N_MIXED = 2
 MMF_OPT_LARGE_N = 3
+MMF_OPT_REFINE_FULL_N = 4
 
 _lib = None
 _exiting = False

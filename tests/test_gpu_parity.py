@@ -397,3 +397,33 @@ def test_whole_gpu_reduction_path(case, precision):
     s, E, U, P = _solve_gpu(c, p, t, 0.2, precision=precision)
     e_rel, up = (E_REL, UP_ABS) if precision == M.MMF_FP64 else (MIX_E_REL, MIX_UP_ABS)
     _compare(p, E, U, P, t, 0.2, e_rel=e_rel, up_abs=up)
+
+
+@pytest.mark.parametrize("case", ["random_n60", "qubit_n242", "random_n245", "spin1_n297"])
+def test_mixed_second_full_refinement_step(case):
+    """The mixed path's second full refinement step (used alone for large n, where G of the FP64
+    iterate is G(fl32 X) + C' + C'^H) forced on small systems, against the oracle; and a batch of
+    both kinds of second step against each system solved alone."""
+    c = M.Context(0)
+    c.set_option(M.MMF_OPT_REFINE_FULL_N, 0)
+    p = SOLVE_CASES[case]()
+    t = W.time_grid(p, 8)
+    s, E, U, P = _solve_gpu(c, p, t, 0.2, precision=M.MMF_MIXED)
+    _compare(p, E, U, P, t, 0.2, e_rel=MIX_E_REL, up_abs=MIX_UP_ABS)
+
+
+def test_mixed_batch_both_second_steps():
+    c = M.Context(0)
+    c.set_option(M.MMF_OPT_REFINE_FULL_N, 200)   # n >= 200: full second step, below: banded
+    ps = [SOLVE_CASES[k]() for k in ("qubit_n82", "random_n245", "random_n125", "spin1_n297")]
+    nt = 8
+    b = M.Batch(c, [M.System(c, p) for p in ps], M.MMF_MIXED, nt)
+    b.set_times(0.0, np.stack([W.time_grid(p, nt) for p in ps]))
+    b.run()
+    assert (b.sync() == 0).all()
+    for i, p in enumerate(ps):
+        E, U, P = b.get(i)
+        ref = O.solve(p, t=W.time_grid(p, nt), t0=0.0)
+        assert np.abs(E - ref["E"]).max() <= MIX_E_REL * np.abs(ref["E"]).max()
+        assert np.abs(U - ref["U"]).max() <= MIX_UP_ABS
+        assert np.abs(P - ref["P"]).max() <= MIX_UP_ABS
