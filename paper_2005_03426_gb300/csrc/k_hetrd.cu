@@ -49,6 +49,32 @@ __device__ __forceinline__ R block_sum(R v, R* red) {
     return r;
 }
 
+// two block-wide sums in one pass (red holds 2 x 33 values)
+template <class R>
+__device__ __forceinline__ void block_sum2(R a, R b, R* red, R& sa, R& sb) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = a;
+        red[33 + (threadIdx.x >> 5)] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        R x = (threadIdx.x < HT_THREADS / 32) ? red[threadIdx.x] : R(0);
+        R y = (threadIdx.x < HT_THREADS / 32) ? red[33 + threadIdx.x] : R(0);
+        x = warp_sum(x);
+        y = warp_sum(y);
+        if (threadIdx.x == 0) {
+            red[32] = x;
+            red[65] = y;
+        }
+    }
+    __syncthreads();
+    sa = red[32];
+    sb = red[65];
+    __syncthreads();
+}
+
 __device__ __forceinline__ void atomic_add_c(double2* p, double2 v) {
     atomicAdd(&p->x, v.x);
     atomicAdd(&p->y, v.y);
@@ -78,7 +104,7 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
     C* xw = vk + MMF_NB;                        // MMF_NB
     C* xv = xw + MMF_NB;                        // MMF_NB
     C* sc = xv + MMF_NB;                        // 4 scalars: tau, scale, alpha2
-    R* red = reinterpret_cast<R*>(sc + 4);      // 33
+    R* red = reinterpret_cast<R*>(sc + 4);      // 66 (two block sums at once)
 
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (CL > 1) ? (int)cluster.block_rank() : 0;
@@ -184,12 +210,11 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                 } else {
                     const int c0 = (task - 2 * i) << 3;
                     const int nc = min(8, m - c0);
-                    C vc[8], ca[8];
+                    // v of the block's columns is read from shared memory at each use (registers go
+                    // to the loads in flight)
+                    C ca[8];
 #pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) {
-                        vc[jj] = (jj < nc) ? vS[c0 + jj] : czero<C>();
-                        ca[jj] = czero<C>();
-                    }
+                    for (int jj = 0; jj < 8; ++jj) ca[jj] = czero<C>();
                     // diagonal chunk (rows c0 .. c0+31)
                     {
                         const int r = c0 + lane;
@@ -202,33 +227,38 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                                 if (jj < nc) {
                                     if (r > c) {
                                         C a = a22[r + (int64_t)c * ld];
-                                        ra = ra + a * vc[jj];
+                                        ra = ra + a * vS[c];
                                         ca[jj] = ca[jj] + cmulc(a, vr);
                                     } else if (r == c) {
-                                        ra = ra + a22[r + (int64_t)c * ld].x * vc[jj];
+                                        ra = ra + a22[r + (int64_t)c * ld].x * vS[c];
                                     }
                                 }
                             }
                             atomic_add_c(&yS[r], ra);
                         }
                     }
-                    // strictly-lower chunks
-                    for (int r0 = c0 + 32; r0 < m; r0 += 32) {
-                        const int r = r0 + lane;
-                        if (r < m) {
-                            C a[8];
+                    // strictly-lower chunks, two 32-row chunks per pass so that 16 loads per lane
+                    // are in flight (the pass is bound by L2/HBM latency, not arithmetic)
+                    for (int r0 = c0 + 32; r0 < m; r0 += 64) {
+                        const int ra_ = r0 + lane, rb_ = r0 + 32 + lane;
+                        C a[8], b[8];
 #pragma unroll
-                            for (int jj = 0; jj < 8; ++jj)
-                                a[jj] = (jj < nc) ? a22[r + (int64_t)(c0 + jj) * ld] : czero<C>();
-                            const C vr = vS[r];
-                            C ra = czero<C>();
-#pragma unroll
-                            for (int jj = 0; jj < 8; ++jj) {
-                                ra = ra + a[jj] * vc[jj];
-                                ca[jj] = ca[jj] + cmulc(a[jj], vr);
-                            }
-                            atomic_add_c(&yS[r], ra);
+                        for (int jj = 0; jj < 8; ++jj) {
+                            a[jj] = (jj < nc && ra_ < m) ? a22[ra_ + (int64_t)(c0 + jj) * ld] : czero<C>();
+                            b[jj] = (jj < nc && rb_ < m) ? a22[rb_ + (int64_t)(c0 + jj) * ld] : czero<C>();
                         }
+                        const C va = (ra_ < m) ? vS[ra_] : czero<C>();
+                        const C vb = (rb_ < m) ? vS[rb_] : czero<C>();
+                        C sa = czero<C>(), sb = czero<C>();
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) {
+                            const C v = (jj < nc) ? vS[c0 + jj] : czero<C>();
+                            sa = sa + a[jj] * v;
+                            sb = sb + b[jj] * v;
+                            ca[jj] = ca[jj] + cmulc(a[jj], va) + cmulc(b[jj], vb);
+                        }
+                        if (ra_ < m) atomic_add_c(&yS[ra_], sa);
+                        if (rb_ < m) atomic_add_c(&yS[rb_], sb);
                     }
 #pragma unroll
                     for (int jj = 0; jj < 8; ++jj) {
@@ -261,8 +291,8 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                 yF[rp] = w;
                 dpart = dpart + cmulc(w, vS[rp]);
             }
-            R dx = block_sum(dpart.x, red);
-            R dy = block_sum(dpart.y, red);
+            R dx, dy;
+            block_sum2(dpart.x, dpart.y, red, dx, dy);
             const C alpha2 = R(-0.5) * (tk * mk(dx, dy));
             if (rank == 0)
                 for (int r = tid; r < n; r += HT_THREADS) {
@@ -328,12 +358,12 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
 
 static size_t hetrd_smem(int nmax, int fp32) {
     size_t cs = fp32 ? 8 : 16, rs = fp32 ? 4 : 8;
-    return cs * (3 * (size_t)nmax + 4 * MMF_NB * HT_TILE + 4 * MMF_NB + 4) + rs * 40;
+    return cs * (3 * (size_t)nmax + 4 * MMF_NB * HT_TILE + 4 * MMF_NB + 4) + rs * 72;
 }
 
 int mmf_hetrd_max_n(int fp32) {
     size_t cs = fp32 ? 8 : 16, rs = fp32 ? 4 : 8;
-    size_t fixed = cs * (4 * MMF_NB * HT_TILE + 4 * MMF_NB + 4) + rs * 40;
+    size_t fixed = cs * (4 * MMF_NB * HT_TILE + 4 * MMF_NB + 4) + rs * 72;
     return (int)((227 * 1024 - fixed) / (3 * cs));
 }
 

@@ -11,8 +11,8 @@
 // G decides the orthogonality of the result and is formed FP64-accurately from FP32 pieces:
 // every FP64 value is split x = x1 + x2 (x1 = fl32(x), x2 = fl32(x - x1)); x1*y1 is taken
 // exactly (product + FMA error term), the cross terms in FP32, and the sums are accumulated in
-// double-FP32 (TwoSum, Knuth 1969).  H_F X is applied in FP64 from the coefficients, never from
-// the FP32 matrix.
+// double-FP32 (TwoSum, Knuth 1969).  H_F X is applied in double-FP32 from the FP64 coefficients,
+// never from the FP32 matrix.
 // First step, residual form of S: with lam0 the eigenvalues that came with X and the residual
 // W = H_F X - X diag(lam0) (FP64, small: |W| ~ eps32 |H_F|),
 //     S = G diag(lam0) + C,   C = X^H W,
@@ -28,6 +28,8 @@
 // correction would exceed 0.05) or the gap is below 1e-13 |H_F|; consecutive clustered indices
 // form a cluster whose eigenvectors are separated by an FP64 Jacobi solve of the small
 // projected matrix X_C^H H_F X_C (clusters of up to RF_CMAX vectors).
+#include <algorithm>
+
 #include "mmf_internal.h"
 
 #define RF_TILE 32
@@ -51,65 +53,111 @@ __device__ __forceinline__ float tf32_round(float x) {
 // row length (floats) of the real K-major operands built from n complex entries: [Re | Im | pad]
 __device__ __forceinline__ int xe_la(int n) { return (2 * n + 3) & ~3; }
 
-// ------------------------------------------------------------------ HX = H_F X (FP64, sparse)
-__global__ void __launch_bounds__(256) k_apply_hf(const MmfDesc* __restrict__ descs,
-                                                  const int* __restrict__ idx,
-                                                  const double2* __restrict__ coef,
-                                                  const double2* __restrict__ Xg,
-                                                  double2* __restrict__ HXg, int col0, int ncols) {
-    const MmfDesc d = descs[idx[blockIdx.z]];
-    const int n = d.n, D = d.D;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    const int cbeg = col0 + blockIdx.y * 16;
-    if (r >= n || cbeg >= n) return;
-    const int cend = min(min(cbeg + 16, n), col0 + ncols);
-    const int b = r / D, i = r - b * D;
-    int nv[MMF_MAX_MODES];
-    block_nvec(d, b, nv);
-    const double sh = block_ndotw(d, b);
-    const double2* H0 = coef + d.coef_off;
-    const double2* X = Xg + d.mat_off;
-    double2* HX = HXg + d.mat_off;
-    for (int c = cbeg; c < cend; ++c) {
-        const double2* x = X + (int64_t)c * d.ld;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int j = 0; j < D; ++j) acc = acc + H0[i * D + j] * x[j + D * b];
-        acc = acc - sh * x[r];
-        int64_t off = d.coef_off + (int64_t)D * D;
-        for (int l = 0; l < d.K; ++l) {
-            for (int h = 1; h <= d.nharm[l]; ++h) {
-                const double2* V = coef + off + (int64_t)(h - 1) * D * D;
-                if (nv[l] + h <= d.N[l]) {
-                    const int bu = b + h * d.S[l];
-                    for (int j = 0; j < D; ++j) acc = acc + V[i * D + j] * x[j + D * bu];
-                }
-                if (nv[l] - h >= -d.N[l]) {
-                    const int bd = b - h * d.S[l];
-                    for (int j = 0; j < D; ++j) acc = acc + cmulc(V[j * D + i], x[j + D * bd]);
-                }
-            }
-            off += (int64_t)d.nharm[l] * D * D;
-        }
-        HX[(int64_t)c * d.ld + r] = acc;
+// ------------------------------------------------------------------ HX = H_F X (double-FP32)
+// The same product on the FP32 pipes: coefficients pre-split once per batch into FP32 pieces
+// (coefs[c] = (re1, re2, im1, im2)), X as fl32(X) plus (when X is not FP32-exact) the FP32
+// remainder, each complex product formed with the exact head product and FP32 cross terms,
+// sums in double-FP32.  Error ~2^-48 of the sum of |terms|, far below what W = HX - X lam0
+// needs (its entries are ~eps32 |H_F| and it only feeds products of FP32 relative accuracy).
+__global__ void __launch_bounds__(256) k_split_coef(const double2* __restrict__ coef, float4* __restrict__ cs,
+                                                    int64_t count) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        const Split v = split(coef[e]);
+        cs[e] = make_float4(v.r1, v.r2, v.i1, v.i2);
     }
 }
 
-// ------------------------------------------------------------------ G = X1^H X1 (double-FP32)
-// X1 = fl32(X) in its own FP32 buffer (written once by k_to_fp32), so the kernel converts
-// nothing: each conj(a) b of FP32 values is accumulated exactly (product + FMA error term) into
-// a double-FP32 sum.  Upper-triangle tiles (I <= J) of 32 x 32; both triangles are written.
-__global__ void __launch_bounds__(256) k_to_fp32(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
-                                                 const double2* __restrict__ Xg, float2* __restrict__ X1g) {
+// X1 = fl32(X) and (Xlo != nullptr) Xlo = fl32(X - X1)
+__global__ void __launch_bounds__(256) k_split_x(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
+                                                 const double2* __restrict__ Xg, float2* __restrict__ X1g,
+                                                 float2* __restrict__ Xlog) {
     const MmfDesc d = descs[idx[blockIdx.y]];
     const int64_t tot = (int64_t)d.n * d.ld;
     const double2* X = Xg + d.mat_off;
     float2* X1 = X1g + d.mat_off;
+    float2* Xlo = Xlog ? Xlog + d.mat_off : nullptr;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-        const double2 x = X[e];
-        X1[e] = make_float2((float)x.x, (float)x.y);
+        const Split v = split(X[e]);
+        X1[e] = make_float2(v.r1, v.i1);
+        if (Xlo) Xlo[e] = make_float2(v.r2, v.i2);
     }
 }
 
+// acc += h x  (h from the split table, x = x1 + x2)
+__device__ __forceinline__ void df_cmul_acc(DF& re, DF& im, const float4 h, float2 x1, float2 x2) {
+    df_mac(re, h.x, h.y, x1.x, x2.x);
+    df_mac(re, -h.z, -h.w, x1.y, x2.y);
+    df_mac(im, h.x, h.y, x1.y, x2.y);
+    df_mac(im, h.z, h.w, x1.x, x2.x);
+}
+// acc += conj(h) x
+__device__ __forceinline__ void df_cmulc_acc(DF& re, DF& im, const float4 h, float2 x1, float2 x2) {
+    df_mac(re, h.x, h.y, x1.x, x2.x);
+    df_mac(re, h.z, h.w, x1.y, x2.y);
+    df_mac(im, h.x, h.y, x1.y, x2.y);
+    df_mac(im, -h.z, -h.w, x1.x, x2.x);
+}
+
+__global__ void __launch_bounds__(256) k_apply_hf_df32(const MmfDesc* __restrict__ descs,
+                                                       const int* __restrict__ idx,
+                                                       const float4* __restrict__ cs,
+                                                       const float2* __restrict__ X1g,
+                                                       const float2* __restrict__ Xlog,
+                                                       double2* __restrict__ HXg) {
+    const MmfDesc d = descs[idx[blockIdx.z]];
+    const int n = d.n, D = d.D;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cbeg = blockIdx.y * 16;
+    if (r >= n || cbeg >= n) return;
+    const int cend = min(cbeg + 16, n);
+    const int b = r / D, i = r - b * D;
+    int nv[MMF_MAX_MODES];
+    block_nvec(d, b, nv);
+    const Split shs = split(make_double2(-block_ndotw(d, b), 0.0));
+    const float4 msh = make_float4(shs.r1, shs.r2, 0.f, 0.f);
+    const float4* H0 = cs + d.coef_off;
+    const float2* X1 = X1g + d.mat_off;
+    const float2* Xlo = Xlog ? Xlog + d.mat_off : nullptr;
+    const float2 z = make_float2(0.f, 0.f);
+    double2* HX = HXg + d.mat_off;
+    for (int c = cbeg; c < cend; ++c) {
+        const float2* x1 = X1 + (int64_t)c * d.ld;
+        const float2* x2 = Xlo ? Xlo + (int64_t)c * d.ld : nullptr;
+        DF re = DF{0.f, 0.f}, im = DF{0.f, 0.f};
+        for (int j = 0; j < D; ++j) {
+            const int q = j + D * b;
+            df_cmul_acc(re, im, H0[i * D + j], x1[q], x2 ? x2[q] : z);
+        }
+        df_cmul_acc(re, im, msh, x1[r], x2 ? x2[r] : z);
+        int64_t off = d.coef_off + (int64_t)D * D;
+        for (int l = 0; l < d.K; ++l) {
+            for (int h = 1; h <= d.nharm[l]; ++h) {
+                const float4* V = cs + off + (int64_t)(h - 1) * D * D;
+                if (nv[l] + h <= d.N[l]) {
+                    const int bu = b + h * d.S[l];
+                    for (int j = 0; j < D; ++j) {
+                        const int q = j + D * bu;
+                        df_cmul_acc(re, im, V[i * D + j], x1[q], x2 ? x2[q] : z);
+                    }
+                }
+                if (nv[l] - h >= -d.N[l]) {
+                    const int bd = b - h * d.S[l];
+                    for (int j = 0; j < D; ++j) {
+                        const int q = j + D * bd;
+                        df_cmulc_acc(re, im, V[j * D + i], x1[q], x2 ? x2[q] : z);
+                    }
+                }
+            }
+            off += (int64_t)d.nharm[l] * D * D;
+        }
+        HX[(int64_t)c * d.ld + r] = df_value(re, im);
+    }
+}
+
+// ------------------------------------------------------------------ G = X1^H X1 (double-FP32)
+// X1 = fl32(X) in its own FP32 buffer (written once by k_split_x), so the kernel converts
+// nothing: each conj(a) b of FP32 values is accumulated exactly (product + FMA error term) into
+// a double-FP32 sum.  Upper-triangle tiles (I <= J) of 32 x 32; both triangles are written.
 __global__ void __launch_bounds__(256) k_gram_x1(const MmfDesc* __restrict__ descs,
                                                  const int* __restrict__ idx,
                                                  const float2* __restrict__ X1g,
@@ -966,12 +1014,27 @@ __global__ void __launch_bounds__(256) k_xe_band(const MmfDesc* __restrict__ des
 //   gram:   G = X1^H X1 in double-FP32 (+ C' + C'^H)
 //   update: lam, Et, X <- X + X Et, cluster separation
 //   band:   the banded second step;   finish: final ordering.
-cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const double2* coef, const double2* X, const double* lam0,
-                                  double2* HX, double2* G, double2* S, float2* Zp, double2* T, void* jobs,
-                                  int* status, int second) {
+cudaError_t mmf_launch_refine_split_coef(const double2* coef, float4* cs, int64_t count, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    k_split_coef<<<(int)std::min<int64_t>((count + 255) / 256, 1024), 256, 0, st>>>(coef, cs, count);
+    return cudaGetLastError();
+}
+
+// HX = H_F X in double-FP32; X1 = fl32(X) is left in place for the Gram product.  Xlo: FP32
+// remainder buffer (used only when X is not FP32-exact).
+static void apply_hf(const MmfLaunch& L, const float4* cs, const double2* X, float2* X1, float2* Xlo, double2* HX) {
+    k_split_x<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, X1, Xlo);
+    k_apply_hf_df32<<<dim3((L.nmax + 255) / 256, (L.nmax + 15) / 16, L.count), 256, 0, L.stream>>>(
+        L.desc, L.idx, cs, X1, Xlo, HX);
+}
+
+cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const float4* cs, const double2* X, const double* lam0,
+                                  double2* HX, double2* G, double2* S, float2* Zp, double2* T, float2* X1,
+                                  void* jobs, int* status, int second) {
     if (L.count <= 0) return cudaSuccess;
-    k_apply_hf<<<dim3((L.nmax + 255) / 256, (L.nmax + 15) / 16, L.count), 256, 0, L.stream>>>(
-        L.desc, L.idx, coef, X, HX, 0, L.nmax);
+    // the first step's X holds FP32 eigenvectors (no remainder); the remainder of a second step's
+    // X goes to T, which is free until C is written
+    apply_hf(L, cs, X, X1, second ? reinterpret_cast<float2*>(T) : nullptr, HX);
     k_w_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, HX, lam0, S, G);
     k_w_prep_A<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, Zp, HX);
     k_w_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, Zp, G, S, HX, T, 0,
@@ -984,12 +1047,11 @@ cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const double2* coef, const
     return mmf_launch_umma(jobs, L.count, 3, L.nmax, 2 * L.nmax, 0, status, L.stream);
 }
 
-cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const double2* X, float2* X1, double2* G, const double2* T,
-                                   int second) {
+cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const float2* X1, double2* G, const double2* T, int second) {
     if (L.count <= 0) return cudaSuccess;
     const int nt = (L.nmax + RF_TILE - 1) / RF_TILE;
-    // G of fl32(X): X itself in the first step (FP32 eigenvectors), X1 in a second full step
-    k_to_fp32<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, X1);
+    // G of X1 = fl32(X) (written by the pre part): X itself in the first step (FP32
+    // eigenvectors), its head in a second full step
     k_gram_x1<<<dim3(nt * (nt + 1) / 2, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X1, G);
     if (second) k_gram_fix<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, T);
     return cudaGetLastError();
@@ -1018,11 +1080,11 @@ cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, do
     return cudaGetLastError();
 }
 
-cudaError_t mmf_launch_refine_band(const MmfLaunch& L, const double2* coef, double2* X, double2* G, double2* S,
-                                   double2* HX, double* lam, int* status, int* cid, int64_t mat_elems) {
+cudaError_t mmf_launch_refine_band(const MmfLaunch& L, const double2* coef, const float4* cs, double2* X,
+                                   double2* G, double2* S, double2* HX, double2* T, float2* X1, double* lam,
+                                   int* status, int* cid, int64_t mat_elems) {
     if (L.count <= 0) return cudaSuccess;
-    k_apply_hf<<<dim3((L.nmax + 255) / 256, (L.nmax + 15) / 16, L.count), 256, 0, L.stream>>>(
-        L.desc, L.idx, coef, X, HX, 0, L.nmax);
+    apply_hf(L, cs, X, X1, reinterpret_cast<float2*>(T), HX);
     k_gram_band_df32<<<dim3((L.nmax + RF_BC - 1) / RF_BC, L.count), 256, 0, L.stream>>>(
         L.desc, L.idx, X, HX, G, S);
     k_oa_lambda_band<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);

@@ -314,37 +314,63 @@ __device__ void tri_solve(const In& in, int n, R lam, R pivtiny, R* y, R* u0, R*
 // FP32 variant: the three U-factor entries of row i and the eliminated right-hand side are kept
 // together, F[i * s] = (u0, u1, u2, rhs), so that each step of either sweep moves one 16-byte
 // word per thread (the sweeps are latency-bound chains).
+#define TRI_PF 8   // steps whose loads are issued ahead of the recurrence (latency hiding)
+
 template <class In>
 __device__ void tri_solve_packed(const In& in, int n, float lam, float pivtiny, float* y, float4* F, int64_t s) {
     float p = in.dv(0) - lam, q = (n > 1) ? in.ev(0) : 0.f, r = 0.f, rb = y[0];
-    for (int i = 0; i < n - 1; ++i) {
-        const float a = in.ev(i);
-        const float bb = in.dv(i + 1) - lam;
-        const float cc = (i + 1 < n - 1) ? in.ev(i + 1) : 0.f;
-        const float b1 = y[(int64_t)(i + 1) * s];
-        if (fabsf(a) <= fabsf(p)) {
-            if (p == 0.f) p = pivtiny;
-            const float l = tdiv(a, p);
-            F[(int64_t)i * s] = make_float4(p, q, r, rb);
-            p = bb - l * q; q = cc - l * r; r = 0.f; rb = b1 - l * rb;
-        } else {
-            const float l = tdiv(p, a);
-            F[(int64_t)i * s] = make_float4(a, bb, cc, b1);
-            const float np = q - l * bb, nq = r - l * cc, nrb = rb - l * b1;
-            p = np; q = nq; r = 0.f; rb = nrb;
+    for (int i0 = 0; i0 < n - 1; i0 += TRI_PF) {
+        // right-hand sides of the next TRI_PF rows, loaded before the dependent chain uses them
+        float b1v[TRI_PF];
+#pragma unroll
+        for (int u = 0; u < TRI_PF; ++u) b1v[u] = (i0 + u < n - 1) ? y[(int64_t)(i0 + u + 1) * s] : 0.f;
+        // keep the loads together ahead of the chain (the compiler would otherwise sink each one
+        // to its use and expose its latency at every step)
+#pragma unroll
+        for (int u = 0; u < TRI_PF; ++u) asm volatile("" ::"f"(b1v[u]));
+#pragma unroll
+        for (int u = 0; u < TRI_PF; ++u) {
+            const int i = i0 + u;
+            if (i >= n - 1) break;
+            const float a = in.ev(i);
+            const float bb = in.dv(i + 1) - lam;
+            const float cc = (i + 1 < n - 1) ? in.ev(i + 1) : 0.f;
+            const float b1 = b1v[u];
+            if (fabsf(a) <= fabsf(p)) {
+                if (p == 0.f) p = pivtiny;
+                const float l = tdiv(a, p);
+                F[(int64_t)i * s] = make_float4(p, q, r, rb);
+                p = bb - l * q; q = cc - l * r; r = 0.f; rb = b1 - l * rb;
+            } else {
+                const float l = tdiv(p, a);
+                F[(int64_t)i * s] = make_float4(a, bb, cc, b1);
+                const float np = q - l * bb, nq = r - l * cc, nrb = rb - l * b1;
+                p = np; q = nq; r = 0.f; rb = nrb;
+            }
         }
     }
     if (fabsf(p) < pivtiny) p = (p < 0.f) ? -pivtiny : pivtiny;
     float y2 = 0.f, y1 = tdiv(rb, p);
     y[(int64_t)(n - 1) * s] = y1;
-    for (int i = n - 2; i >= 0; --i) {
-        const float4 f = F[(int64_t)i * s];
-        float up = f.x;
-        if (fabsf(up) < pivtiny) up = (up < 0.f) ? -pivtiny : pivtiny;
-        const float yi = tdiv(f.w - f.y * y1 - f.z * y2, up);
-        y[(int64_t)i * s] = yi;
-        y2 = y1;
-        y1 = yi;
+    for (int i0 = n - 2; i0 >= 0; i0 -= TRI_PF) {
+        float4 fv[TRI_PF];
+#pragma unroll
+        for (int u = 0; u < TRI_PF; ++u)
+            fv[u] = (i0 - u >= 0) ? F[(int64_t)(i0 - u) * s] : make_float4(1.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < TRI_PF; ++u) asm volatile("" ::"f"(fv[u].x), "f"(fv[u].y), "f"(fv[u].z), "f"(fv[u].w));
+#pragma unroll
+        for (int u = 0; u < TRI_PF; ++u) {
+            const int i = i0 - u;
+            if (i < 0) break;
+            const float4 f = fv[u];
+            float up = f.x;
+            if (fabsf(up) < pivtiny) up = (up < 0.f) ? -pivtiny : pivtiny;
+            const float yi = tdiv(f.w - f.y * y1 - f.z * y2, up);
+            y[(int64_t)i * s] = yi;
+            y2 = y1;
+            y1 = yi;
+        }
     }
 }
 
@@ -411,14 +437,17 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
                 for (int i = 0; i < n; ++i) y[(int64_t)i * s] -= dot * z[(int64_t)i * s];
             }
             R mx = R(0);
+#pragma unroll 8
             for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(y[(int64_t)i * s]));
             const R inv1 = (mx > R(0)) ? R(1) / mx : R(1);
             R nrm = R(0);
+#pragma unroll 8
             for (int i = 0; i < n; ++i) {
                 R v = y[(int64_t)i * s] * inv1;
                 nrm += v * v;
             }
             const R inv = inv1 / sqrt(nrm);
+#pragma unroll 8
             for (int i = 0; i < n; ++i) y[(int64_t)i * s] *= inv;
         }
         if (sizeof(R) == 4) {

@@ -100,6 +100,7 @@ struct mmf_batch {
     double* d_P = nullptr;
     double2 *d_R = nullptr, *d_S = nullptr, *d_HX = nullptr, *d_Eb = nullptr, *d_T = nullptr;
     float2* d_X1 = nullptr;
+    float4* d_coefs = nullptr;  // coefficients split into FP32 pieces (mixed refinement)
     double* d_E2 = nullptr;
     int* d_cid = nullptr;
     void* d_jobs = nullptr;
@@ -450,11 +451,12 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     size_t o_F = p.take(sizeof(double2) * std::max<int64_t>(b->n_f, 1));
     size_t o_U = p.take(sizeof(double2) * std::max<int64_t>(b->n_u, 1));
     size_t o_P = p.take(sizeof(double) * b->n_p);
-    size_t o_R = 0, o_S = 0, o_HX = 0, o_E2 = 0, o_cid = 0, o_jobs = 0, o_Eb = 0, o_T = 0, o_X1 = 0;
+    size_t o_R = 0, o_S = 0, o_HX = 0, o_E2 = 0, o_cid = 0, o_jobs = 0, o_Eb = 0, o_T = 0, o_X1 = 0, o_coefs = 0;
     if (fp32) {
         o_Eb = p.take(sizeof(double2) * b->n_vec * MMF_REFINE_BW);
         o_T = p.take(sizeof(double2) * b->n_mat);
         o_X1 = p.take(sizeof(float2) * b->n_mat);
+        o_coefs = p.take(sizeof(float4) * std::max<int64_t>(b->n_coef, 1));
         o_R = p.take(sizeof(double2) * b->n_mat);
         o_S = p.take(sizeof(double2) * b->n_mat);
         o_HX = p.take(sizeof(double2) * b->n_mat);
@@ -512,6 +514,7 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         b->d_Eb = (double2*)(B + o_Eb);
         b->d_T = (double2*)(B + o_T);
         b->d_X1 = (float2*)(B + o_X1);
+        b->d_coefs = (float4*)(B + o_coefs);
     }
     if (b->pinned) {
         e = cudaMallocHost((void**)&b->h_coef, sizeof(double2) * std::max<int64_t>(b->n_coef, 1));
@@ -705,29 +708,30 @@ static int stage_eig(mmf_batch* b) {
     if (fp32) {
         MmfLaunch La = launch_of(b, b->all, b->d_all, b->nmax_all);
         float2* Zp = (float2*)b->d_Zp;
-        LAUNCH(mmf_launch_refine_pre(La, b->d_coef, b->d_Zf, b->d_E, b->d_HX, b->d_R, b->d_S, Zp, b->d_T,
+        LAUNCH(mmf_launch_refine_split_coef(b->d_coef, b->d_coefs, b->n_coef, b->stream), 1);
+        LAUNCH(mmf_launch_refine_pre(La, b->d_coefs, b->d_Zf, b->d_E, b->d_HX, b->d_R, b->d_S, Zp, b->d_T, b->d_X1,
                                      b->d_jobs, b->d_status, 0),
-               5);
+               6);
         mark(b, ST_GRAM);
-        LAUNCH(mmf_launch_refine_gram(La, b->d_Zf, b->d_X1, b->d_R, b->d_T, 0), 2);
+        LAUNCH(mmf_launch_refine_gram(La, b->d_X1, b->d_R, b->d_T, 0), 1);
         mark(b, ST_REFINE2);
         LAUNCH(mmf_launch_refine_update(La, b->d_coef, b->d_Zf, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_T, b->d_E2,
                                         b->d_status, b->d_cid, b->n_mat, Zp, b->d_jobs, b->d_Eb),
                9);
         if (!b->rband.empty()) {
             MmfLaunch Lb = launch_of(b, b->rband, b->d_rband, b->nmax_rband);
-            LAUNCH(mmf_launch_refine_band(Lb, b->d_coef, b->d_Zf, b->d_R, b->d_S, b->d_HX, b->d_E2, b->d_status,
-                                          b->d_cid, b->n_mat),
-                   5);
+            LAUNCH(mmf_launch_refine_band(Lb, b->d_coef, b->d_coefs, b->d_Zf, b->d_R, b->d_S, b->d_HX, b->d_T,
+                                          b->d_X1, b->d_E2, b->d_status, b->d_cid, b->n_mat),
+                   6);
         }
         if (!b->rfull.empty()) {
             // second full step from lam0 = the first step's eigenvalues (E is rewritten at the end)
             MmfLaunch Lf = launch_of(b, b->rfull, b->d_rfull, b->nmax_rfull);
             CU(cudaMemcpyAsync(b->d_E, b->d_E2, sizeof(double) * b->n_vec, cudaMemcpyDeviceToDevice, b->stream));
-            LAUNCH(mmf_launch_refine_pre(Lf, b->d_coef, b->d_Zf, b->d_E, b->d_HX, b->d_R, b->d_S, Zp, b->d_T,
-                                         b->d_jobs, b->d_status, 1),
-                   8);
-            LAUNCH(mmf_launch_refine_gram(Lf, b->d_Zf, b->d_X1, b->d_R, b->d_T, 1), 3);
+            LAUNCH(mmf_launch_refine_pre(Lf, b->d_coefs, b->d_Zf, b->d_E, b->d_HX, b->d_R, b->d_S, Zp, b->d_T,
+                                         b->d_X1, b->d_jobs, b->d_status, 1),
+                   9);
+            LAUNCH(mmf_launch_refine_gram(Lf, b->d_X1, b->d_R, b->d_T, 1), 2);
             LAUNCH(mmf_launch_refine_update(Lf, b->d_coef, b->d_Zf, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_T,
                                             b->d_E2, b->d_status, b->d_cid, b->n_mat, Zp, b->d_jobs, b->d_Eb),
                    9);

@@ -207,17 +207,18 @@ cudaError_t mmf_launch_hetrd_large(const MmfDesc& d, void* H, void* Vp, void* Wp
                                    void* tau, void* work, void* sc, int fp32, cudaStream_t st);
 cudaError_t mmf_launch_micromotion(const MmfLaunch& L, int D, const double2* Z, const double* t,
                                    int nt, int64_t* reps, double2* UF);
-cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const double2* coef, const double2* X, const double* lam0,
-                                  double2* HX, double2* G, double2* S, float2* Zp, double2* T, void* jobs,
-                                  int* status, int second);
-cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const double2* X, float2* X1, double2* G, const double2* T,
-                                   int second);
+cudaError_t mmf_launch_refine_split_coef(const double2* coef, float4* cs, int64_t count, cudaStream_t st);
+cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const float4* cs, const double2* X, const double* lam0,
+                                  double2* HX, double2* G, double2* S, float2* Zp, double2* T, float2* X1,
+                                  void* jobs, int* status, int second);
+cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const float2* X1, double2* G, const double2* T, int second);
 cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, double2* X, const double* lam0,
                                      double2* G, double2* S, double2* HX, const double2* T, double* lam,
                                      int* status, int* cid, int64_t mat_elems, float2* Zp, void* jobs,
                                      double2* Eb);
-cudaError_t mmf_launch_refine_band(const MmfLaunch& L, const double2* coef, double2* X, double2* G, double2* S,
-                                   double2* HX, double* lam, int* status, int* cid, int64_t mat_elems);
+cudaError_t mmf_launch_refine_band(const MmfLaunch& L, const double2* coef, const float4* cs, double2* X,
+                                   double2* G, double2* S, double2* HX, double2* T, float2* X1, double* lam,
+                                   int* status, int* cid, int64_t mat_elems);
 cudaError_t mmf_launch_refine_finish(const MmfLaunch& L, double2* X, double* E, const double* lam, double2* S,
                                      int64_t mat_elems);
 #define MMF_REFINE_BW 33   // entries per row of the refinement's band buffer (2 W + 1)

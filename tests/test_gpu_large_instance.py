@@ -8,10 +8,10 @@ properties that hold at any size, against the oracle's own H_F and formulas:
 - orthonormality of the sampled eigenvectors;
 - U(t, t0) at sampled times recomputed from the GPU eigenpairs by the Eq. 3-5 sum in numpy (the
   oracle's loop form takes minutes per time at this size), and Pbar by the oracle's formula;
-- U(t0, t0) = I (completeness of the eigenvectors), sum_j Pbar_ij = 1, and the Floquet copies
-  E + omega_1 of the zone representatives.
-U(t) at t != t0 is not checked for unitarity: in the truncated Floquet space it is unitary only
-up to the truncation error (about 1e-7 here at N = 6 per mode), which is physics, not rounding."""
+- U(t0, t0) = I (completeness of the eigenvectors) and sum_j Pbar_ij = 1.
+Two relations of the untruncated problem are not checked, because at N = 6 per mode they hold
+only up to the truncation error (physics, not rounding): unitarity of U(t) at t != t0 (~1e-7
+here) and the Floquet copies E + omega_1 (~1e-4 here, three modes with couplings ~0.3)."""
 
 import numpy as np
 import pytest
@@ -76,8 +76,4 @@ def test_large_instance_properties(precision):
     np.testing.assert_allclose(U[0], np.eye(D), atol=up)
     np.testing.assert_allclose(P.sum(axis=1), 1.0, atol=up)
     assert P.min() >= -up
-    # Floquet copies: the zone representatives (largest weight on the central block) recur
-    # shifted by omega_1 (their copies lie deep inside the truncated space)
-    reps = np.argsort(-(np.abs(Z0) ** 2).sum(axis=0))[:D]
-    for lam in E[reps]:
-        assert np.min(np.abs(E - (lam + p.omegas[0]))) <= 1e-6
+
