@@ -32,6 +32,7 @@ namespace cg = cooperative_groups;
 
 #define HT_THREADS 512
 #define HT_TILE 64
+#define HT_SEG 128   // rows per hemv task (a multiple of 64)
 
 template <class R>
 __device__ __forceinline__ R block_sum(R v, R* red) {
@@ -195,9 +196,14 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
 
             // (c) y = A22 v (lower triangle) and (d) x_w = W^H v, x_v = V^H v
             const C* a22 = A + (k + 1) + (int64_t)(k + 1) * ld;
+            // Tasks: the 2i dot products (every CTA needs them all), then this CTA's share of the
+            // hemv: column blocks of 8 (blocks rank, rank + CL, ...) cut into row segments of
+            // HT_SEG rows, so that tasks cost about the same and every warp gets some.
             const int nblk = (m + 7) >> 3;
-            for (int task = warp; task < 2 * i + nblk; task += NW) {
-                if (task >= 2 * i && ((task - 2 * i) % CL) != rank) continue;
+            const int nloc = (nblk - rank + CL - 1) / CL;
+            const int nseg = (m + HT_SEG - 1) / HT_SEG;
+            const int ntask = 2 * i + nloc * nseg;
+            for (int task = warp; task < ntask; task += NW) {
                 if (task < 2 * i) {
                     const int c = task >> 1;
                     const C* P = (task & 1) ? V : W;
@@ -207,64 +213,71 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                     acc.x = warp_sum(acc.x);
                     acc.y = warp_sum(acc.y);
                     if (lane == 0) ((task & 1) ? xv : xw)[c] = acc;
-                } else {
-                    const int c0 = (task - 2 * i) << 3;
-                    const int nc = min(8, m - c0);
-                    // v of the block's columns is read from shared memory at each use (registers go
-                    // to the loads in flight)
-                    C ca[8];
+                    continue;
+                }
+                const int t = task - 2 * i;
+                const int q = t % nloc, sg = t / nloc;
+                const int c0 = (rank + CL * q) << 3;
+                const int rbeg = c0 + sg * HT_SEG;
+                if (rbeg >= m) continue;  // the segment lies below the matrix
+                const int rend = min(rbeg + HT_SEG, m);
+                const int nc = min(8, m - c0);
+                // v of the block's columns is read from shared memory at each use (registers go
+                // to the loads in flight)
+                C ca[8];
 #pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) ca[jj] = czero<C>();
-                    // diagonal chunk (rows c0 .. c0+31)
-                    {
-                        const int r = c0 + lane;
-                        if (r < m) {
-                            const C vr = vS[r];
-                            C ra = czero<C>();
+                for (int jj = 0; jj < 8; ++jj) ca[jj] = czero<C>();
+                int r0 = rbeg;
+                if (sg == 0) {  // diagonal chunk (rows c0 .. c0+31)
+                    const int r = c0 + lane;
+                    if (r < m) {
+                        const C vr = vS[r];
+                        C ra = czero<C>();
 #pragma unroll
-                            for (int jj = 0; jj < 8; ++jj) {
-                                const int c = c0 + jj;
-                                if (jj < nc) {
-                                    if (r > c) {
-                                        C a = a22[r + (int64_t)c * ld];
-                                        ra = ra + a * vS[c];
-                                        ca[jj] = ca[jj] + cmulc(a, vr);
-                                    } else if (r == c) {
-                                        ra = ra + a22[r + (int64_t)c * ld].x * vS[c];
-                                    }
+                        for (int jj = 0; jj < 8; ++jj) {
+                            const int c = c0 + jj;
+                            if (jj < nc) {
+                                if (r > c) {
+                                    C a = a22[r + (int64_t)c * ld];
+                                    ra = ra + a * vS[c];
+                                    ca[jj] = ca[jj] + cmulc(a, vr);
+                                } else if (r == c) {
+                                    ra = ra + a22[r + (int64_t)c * ld].x * vS[c];
                                 }
                             }
-                            atomic_add_c(&yS[r], ra);
                         }
+                        atomic_add_c(&yS[r], ra);
                     }
-                    // strictly-lower chunks, two 32-row chunks per pass so that 16 loads per lane
-                    // are in flight (the pass is bound by L2/HBM latency, not arithmetic)
-                    for (int r0 = c0 + 32; r0 < m; r0 += 64) {
-                        const int ra_ = r0 + lane, rb_ = r0 + 32 + lane;
-                        C a[8], b[8];
-#pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) {
-                            a[jj] = (jj < nc && ra_ < m) ? a22[ra_ + (int64_t)(c0 + jj) * ld] : czero<C>();
-                            b[jj] = (jj < nc && rb_ < m) ? a22[rb_ + (int64_t)(c0 + jj) * ld] : czero<C>();
-                        }
-                        const C va = (ra_ < m) ? vS[ra_] : czero<C>();
-                        const C vb = (rb_ < m) ? vS[rb_] : czero<C>();
-                        C sa = czero<C>(), sb = czero<C>();
-#pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) {
-                            const C v = (jj < nc) ? vS[c0 + jj] : czero<C>();
-                            sa = sa + a[jj] * v;
-                            sb = sb + b[jj] * v;
-                            ca[jj] = ca[jj] + cmulc(a[jj], va) + cmulc(b[jj], vb);
-                        }
-                        if (ra_ < m) atomic_add_c(&yS[ra_], sa);
-                        if (rb_ < m) atomic_add_c(&yS[rb_], sb);
-                    }
+                    r0 = c0 + 32;
+                }
+                // strictly-lower chunks, two 32-row chunks per pass so that 16 loads per lane are in
+                // flight (the pass is bound by L2/HBM latency, not arithmetic)
+                for (; r0 < rend; r0 += 64) {
+                    const int ra_ = r0 + lane, rb_ = r0 + 32 + lane;
+                    const bool oka = ra_ < rend, okb = rb_ < rend;
+                    C a[8], b[8];
 #pragma unroll
                     for (int jj = 0; jj < 8; ++jj) {
-                        R sx = warp_sum(ca[jj].x), sy = warp_sum(ca[jj].y);
-                        if (lane == 0 && jj < nc) atomic_add_c(&yS[c0 + jj], mk(sx, sy));
+                        a[jj] = (jj < nc && oka) ? a22[ra_ + (int64_t)(c0 + jj) * ld] : czero<C>();
+                        b[jj] = (jj < nc && okb) ? a22[rb_ + (int64_t)(c0 + jj) * ld] : czero<C>();
                     }
+                    const C va = oka ? vS[ra_] : czero<C>();
+                    const C vb = okb ? vS[rb_] : czero<C>();
+                    C sa = czero<C>(), sb = czero<C>();
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const C v = (jj < nc) ? vS[c0 + jj] : czero<C>();
+                        sa = sa + a[jj] * v;
+                        sb = sb + b[jj] * v;
+                        ca[jj] = ca[jj] + cmulc(a[jj], va) + cmulc(b[jj], vb);
+                    }
+                    if (oka) atomic_add_c(&yS[ra_], sa);
+                    if (okb) atomic_add_c(&yS[rb_], sb);
+                }
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    R sx = warp_sum(ca[jj].x), sy = warp_sum(ca[jj].y);
+                    if (lane == 0 && jj < nc) atomic_add_c(&yS[c0 + jj], mk(sx, sy));
                 }
             }
             if (CL > 1) {

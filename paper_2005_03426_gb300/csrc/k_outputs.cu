@@ -28,12 +28,29 @@ __global__ void __launch_bounds__(256) k_phase_table(const MmfDesc* __restrict__
 
 #define U_TPW 8  // times per warp per pass (8 warps -> 64 times per pass)
 
+// Z split once into FP32 pieces, Z = Z1 + Zlo (Z1 = fl32(Z), Zlo = fl32(Z - Z1)), so that the
+// contraction below converts nothing on the FP64 pipe.
+__global__ void __launch_bounds__(256) k_split_z(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
+                                                 const double2* __restrict__ Zg, float2* __restrict__ Z1g,
+                                                 float2* __restrict__ Zlog) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int64_t tot = (int64_t)d.n * d.ld;
+    const double2* Z = Zg + d.mat_off;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const Split v = split(Z[e]);
+        Z1g[d.mat_off + e] = make_float2(v.r1, v.i1);
+        Zlog[d.mat_off + e] = make_float2(v.r2, v.i2);
+    }
+}
+
 // Phi is accumulated FP64-accurately in double-FP32 (the FP64 units of GB300 are ~60x slower
 // than its FP32 units); the short contraction with the phases and Z0 is done in FP64.
 __global__ void __launch_bounds__(256) k_time_evolution(const MmfDesc* __restrict__ descs,
                                                         const int* __restrict__ idx,
                                                         const double* __restrict__ Eg,
                                                         const double2* __restrict__ Zg,
+                                                        const float2* __restrict__ Z1g,
+                                                        const float2* __restrict__ Zlog,
                                                         const double* __restrict__ tpool,
                                                         double t0, int nt,
                                                         const Split* __restrict__ F,
@@ -45,6 +62,8 @@ __global__ void __launch_bounds__(256) k_time_evolution(const MmfDesc* __restric
     if (blockIdx.x * 32 >= n) return;
     const bool valid = lam < n;
     const double2* Zc = Zg + d.mat_off + (int64_t)(valid ? lam : 0) * d.ld;
+    const float2* Z1c = Z1g + d.mat_off + (int64_t)(valid ? lam : 0) * d.ld;
+    const float2* Zlc = Zlog + d.mat_off + (int64_t)(valid ? lam : 0) * d.ld;
     const double El = valid ? Eg[d.vec_off + lam] : 0.0;
     const Split* Ft = F + d.f_off;
     const double* tt = tpool + d.t_off;
@@ -64,7 +83,11 @@ __global__ void __launch_bounds__(256) k_time_evolution(const MmfDesc* __restric
 #pragma unroll
             for (int q = 0; q < U_TPW; ++q) ar[q] = ai[q] = DF{0.f, 0.f};
             for (int b = 0; b < M; ++b) {
-                const Split z = split(valid ? Zc[j + D * b] : make_double2(0.0, 0.0));
+                Split z = Split{0.f, 0.f, 0.f, 0.f};
+                if (valid) {
+                    const float2 z1 = Z1c[j + D * b], zl = Zlc[j + D * b];
+                    z = Split{z1.x, zl.x, z1.y, zl.y};
+                }
 #pragma unroll
                 for (int q = 0; q < U_TPW; ++q) {
                     int t = tbase + warp + 8 * q;
@@ -145,7 +168,7 @@ __global__ void __launch_bounds__(256) k_transition_avg(const MmfDesc* __restric
 
 // Staged launcher with explicit maxima (the batch knows them).
 cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const double* E,
-                                  const double2* Z, const double* t, double t0, int nt,
+                                  const double2* Z, float2* Z1, float2* Zlo, const double* t, double t0, int nt,
                                   double2* F2, double2* U, double* P, double cluster_rel) {
     static_assert(sizeof(Split) == sizeof(double2), "phase table slots hold one Split each");
     Split* F = reinterpret_cast<Split*>(F2);
@@ -154,8 +177,9 @@ cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const dou
         int gx = (nt * Mmax + 255) / 256;
         if (gx > 1024) gx = 1024;
         k_phase_table<<<dim3(gx, L.count), 256, 0, L.stream>>>(L.desc, L.idx, t, nt, F);
+        k_split_z<<<dim3(128, L.count), 256, 0, L.stream>>>(L.desc, L.idx, Z, Z1, Zlo);
         k_time_evolution<<<dim3((L.nmax + 31) / 32, L.count), 256, 0, L.stream>>>(
-            L.desc, L.idx, E, Z, t, t0, nt, F, U);
+            L.desc, L.idx, E, Z, Z1, Zlo, t, t0, nt, F, U);
     }
     size_t sm = sizeof(double) * (size_t)(Dmax * Dmax + 8 * Dmax);
     if (sm > 48 * 1024) {

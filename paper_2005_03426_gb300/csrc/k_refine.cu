@@ -268,11 +268,11 @@ __global__ void __launch_bounds__(256) k_w_prep_B(const MmfDesc* __restrict__ de
 
 __global__ void __launch_bounds__(256) k_w_prep_A(const MmfDesc* __restrict__ descs,
                                                   const int* __restrict__ idx,
-                                                  const double2* __restrict__ Xg,
+                                                  const float2* __restrict__ X1g,
                                                   float2* __restrict__ A1g, double2* __restrict__ A2g) {
     const MmfDesc d = descs[idx[blockIdx.y]];
     const int n = d.n, la = xe_la(n);
-    const double2* X = Xg + d.mat_off;
+    const float2* X = X1g + d.mat_off;
     float* A1 = reinterpret_cast<float*>(A1g + d.mat_off);
     float* A2 = reinterpret_cast<float*>(A2g + d.mat_off);
     const int64_t tot = (int64_t)n * la;
@@ -280,8 +280,8 @@ __global__ void __launch_bounds__(256) k_w_prep_A(const MmfDesc* __restrict__ de
         const int i = (int)(e / la), k = (int)(e - (int64_t)i * la);
         float v = 0.f;
         if (k < 2 * n) {
-            const double2 x = X[(int64_t)i * d.ld + (k < n ? k : k - n)];
-            v = (float)(k < n ? x.x : x.y);
+            const float2 x = X[(int64_t)i * d.ld + (k < n ? k : k - n)];
+            v = k < n ? x.x : x.y;
         }
         const float v1 = tf32_round(v);
         A1[e] = v1;
@@ -497,27 +497,27 @@ __global__ void __launch_bounds__(256) k_xe_prep_B(const MmfDesc* __restrict__ d
 
 __global__ void __launch_bounds__(256) k_xe_prep_A(const MmfDesc* __restrict__ descs,
                                                    const int* __restrict__ idx,
-                                                   const double2* __restrict__ Xg,
+                                                   const float2* __restrict__ X1g,
                                                    float2* __restrict__ A1g, double2* __restrict__ A2g) {
-    __shared__ double2 t[32][33];
+    __shared__ float2 t[32][33];
     const MmfDesc d = descs[idx[blockIdx.z]];
     const int n = d.n, la = xe_la(n);
     const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
     if (r0 >= n || c0 >= n) return;
-    const double2* X = Xg + d.mat_off;
+    const float2* X = X1g + d.mat_off;
     float* A1 = reinterpret_cast<float*>(A1g + d.mat_off);
     float* A2 = reinterpret_cast<float*>(A2g + d.mat_off);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
     for (int q = ty; q < 32; q += 8) {  // X(r0 + tx, c0 + q), rows fastest
         const int r = r0 + tx, c = c0 + q;
-        t[q][tx] = (r < n && c < n) ? X[(int64_t)c * d.ld + r] : make_double2(0.0, 0.0);
+        t[q][tx] = (r < n && c < n) ? X[(int64_t)c * d.ld + r] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     for (int q = ty; q < 32; q += 8) {  // A[r0 + q][c0 + tx] (re) and A[r0 + q][n + c0 + tx] (im)
         const int r = r0 + q, c = c0 + tx;
         if (r < n && c < n) {
-            const double2 x = t[tx][q];
-            const float re = (float)x.x, im = (float)x.y;
+            const float2 x = t[tx][q];
+            const float re = x.x, im = x.y;
             const float re1 = tf32_round(re), im1 = tf32_round(im);
             A1[(int64_t)r * la + c] = re1;
             A2[(int64_t)r * la + c] = tf32_round(re - re1);
@@ -568,12 +568,13 @@ __global__ void __launch_bounds__(256) k_et_band(const MmfDesc* __restrict__ des
 }
 
 // Xn(:, j) = X(:, j) + C(:, j) + sum_{|i-j|<=W} X(:, i) Et(i, j): C from the tensor cores (Et
-// outside the band), the band in double-FP32 (X is FP32-exact in the first step, Et split in two
-// FP32 pieces).  Xn goes to a separate buffer (the band reads neighbouring columns of X).
+// outside the band), the band in double-FP32 from X1 = fl32(X) (exact in the first step; in a
+// second full step the remainder times Et is below 2^-24 |Et| and dropped) and Et split in two
+// FP32 pieces.  Xn goes to a separate buffer (the band reads neighbouring columns of X).
 __global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ descs,
                                                   const int* __restrict__ idx, const double2* __restrict__ Xg,
-                                                  const double2* __restrict__ R, const double2* __restrict__ Ebg,
-                                                  double2* __restrict__ Xn) {
+                                                  const float2* __restrict__ X1g, const double2* __restrict__ R,
+                                                  const double2* __restrict__ Ebg, double2* __restrict__ Xn) {
     __shared__ Split et[RF_BW];
     const MmfDesc d = descs[idx[blockIdx.z]];
     const int n = d.n, la = xe_la(n);
@@ -587,13 +588,14 @@ __global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ de
     __syncthreads();
     const float* C = reinterpret_cast<const float*>(R + d.mat_off) + (int64_t)n * la;
     const double2* X = Xg + d.mat_off;
+    const float2* X1 = X1g + d.mat_off;
     const int qlo = max(0, RF_W - j), qhi = min(RF_BW, n - j + RF_W);
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         DF ar = DF{0.f, 0.f}, ai = DF{0.f, 0.f};
         for (int q = qlo; q < qhi; ++q) {
             const int i = j + q - RF_W;
-            const double2 x = X[(int64_t)i * d.ld + r];
-            const float xr = (float)x.x, xi = (float)x.y;
+            const float2 x = X1[(int64_t)i * d.ld + r];
+            const float xr = x.x, xi = x.y;
             const Split e = et[q];
             df_mac1(ar, xr, e.r1, e.r2);
             df_mac1(ar, -xi, e.i1, e.i2);
@@ -955,6 +957,7 @@ __global__ void __launch_bounds__(256) k_oa_lambda_band(const MmfDesc* __restric
 __global__ void __launch_bounds__(256) k_xe_band(const MmfDesc* __restrict__ descs,
                                                  const int* __restrict__ idx,
                                                  const double2* __restrict__ Xg,
+                                                 const float2* __restrict__ X1g,
                                                  const double2* __restrict__ Gbg,
                                                  const double2* __restrict__ Sbg,
                                                  const double* __restrict__ lamg,
@@ -991,14 +994,14 @@ __global__ void __launch_bounds__(256) k_xe_band(const MmfDesc* __restrict__ des
     }
     __syncthreads();
     const double2* X = Xg + d.mat_off;
+    const float2* X1 = X1g + d.mat_off;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < RF_BW; ++q) {
             const int i = j + q - RF_W;
             if (i >= 0 && i < n) {
-                const double2 x = X[(int64_t)i * d.ld + r];
-                const float2 xf = make_float2(__double2float_rn(x.x), __double2float_rn(x.y));
+                const float2 xf = X1[(int64_t)i * d.ld + r];
                 acc.x = fmaf(xf.x, et[q].x, fmaf(-xf.y, et[q].y, acc.x));
                 acc.y = fmaf(xf.x, et[q].y, fmaf(xf.y, et[q].x, acc.y));
             }
@@ -1036,7 +1039,7 @@ cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const float4* cs, const do
     // X goes to T, which is free until C is written
     apply_hf(L, cs, X, X1, second ? reinterpret_cast<float2*>(T) : nullptr, HX);
     k_w_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, HX, lam0, S, G);
-    k_w_prep_A<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, Zp, HX);
+    k_w_prep_A<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X1, Zp, HX);
     k_w_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, Zp, G, S, HX, T, 0,
                                                          (UmmaJob*)jobs);
     cudaError_t e = mmf_launch_umma(jobs, L.count, 3, L.nmax, 2 * L.nmax, 0, status, L.stream);
@@ -1057,9 +1060,9 @@ cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const float2* X1, double2
     return cudaGetLastError();
 }
 
-cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, double2* X, const double* lam0,
-                                     double2* G, double2* S, double2* HX, const double2* T, double* lam,
-                                     int* status, int* cid, int64_t mat_elems, float2* Zp, void* jobs,
+cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, double2* X, const float2* X1,
+                                     const double* lam0, double2* G, double2* S, double2* HX, const double2* T,
+                                     double* lam, int* status, int* cid, int64_t mat_elems, float2* Zp, void* jobs,
                                      double2* Eb) {
     if (L.count <= 0) return cudaSuccess;
     k_oa_lambda<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, T, lam0, lam, cid);
@@ -1068,12 +1071,12 @@ cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, do
     k_et_band<<<dim3(64, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, Eb);
     k_xe_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, S, HX);
     k_xe_prep_A<<<dim3((L.nmax + 31) / 32, (L.nmax + 31) / 32, L.count), 256, 0, L.stream>>>(
-        L.desc, L.idx, X, Zp, G);
+        L.desc, L.idx, X1, Zp, G);
     k_xe_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, Zp, G, S, HX,
                                                           (UmmaJob*)jobs);
     cudaError_t e = mmf_launch_umma(jobs, L.count, 3, L.nmax, 2 * L.nmax, 0, status, L.stream);
     if (e != cudaSuccess) return e;
-    k_xe_apply<<<dim3((L.nmax + 255) / 256, L.nmax, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, G, Eb, HX);
+    k_xe_apply<<<dim3((L.nmax + 255) / 256, L.nmax, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, X1, G, Eb, HX);
     e = cudaMemcpyAsync(X, HX, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
     if (e != cudaSuccess) return e;
     k_cluster_sep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, coef, X, HX, lam, cid, status);
@@ -1088,7 +1091,7 @@ cudaError_t mmf_launch_refine_band(const MmfLaunch& L, const double2* coef, cons
     k_gram_band_df32<<<dim3((L.nmax + RF_BC - 1) / RF_BC, L.count), 256, 0, L.stream>>>(
         L.desc, L.idx, X, HX, G, S);
     k_oa_lambda_band<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
-    k_xe_band<<<dim3((L.nmax + 255) / 256, L.nmax, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, G, S,
+    k_xe_band<<<dim3((L.nmax + 255) / 256, L.nmax, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, X1, G, S,
                                                                                 lam, cid, HX);
     cudaError_t e = cudaMemcpyAsync(X, HX, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
     if (e != cudaSuccess) return e;

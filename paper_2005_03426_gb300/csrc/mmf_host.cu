@@ -101,6 +101,7 @@ struct mmf_batch {
     double2 *d_R = nullptr, *d_S = nullptr, *d_HX = nullptr, *d_Eb = nullptr, *d_T = nullptr;
     float2* d_X1 = nullptr;
     float4* d_coefs = nullptr;  // coefficients split into FP32 pieces (mixed refinement)
+    float2* d_Zs = nullptr;     // FP64 path: Z split into FP32 pieces for the time evolution
     double* d_E2 = nullptr;
     int* d_cid = nullptr;
     void* d_jobs = nullptr;
@@ -452,6 +453,7 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     size_t o_U = p.take(sizeof(double2) * std::max<int64_t>(b->n_u, 1));
     size_t o_P = p.take(sizeof(double) * b->n_p);
     size_t o_R = 0, o_S = 0, o_HX = 0, o_E2 = 0, o_cid = 0, o_jobs = 0, o_Eb = 0, o_T = 0, o_X1 = 0, o_coefs = 0;
+    const size_t o_Zs = (!fp32 && nt > 0) ? p.take(sizeof(float2) * 2 * b->n_mat) : 0;
     if (fp32) {
         o_Eb = p.take(sizeof(double2) * b->n_vec * MMF_REFINE_BW);
         o_T = p.take(sizeof(double2) * b->n_mat);
@@ -504,6 +506,7 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     b->d_F = (double2*)(B + o_F);
     b->d_U = (double2*)(B + o_U);
     b->d_P = (double*)(B + o_P);
+    if (!fp32 && nt > 0) b->d_Zs = (float2*)(B + o_Zs);
     if (fp32) {
         b->d_R = (double2*)(B + o_R);
         b->d_S = (double2*)(B + o_S);
@@ -715,7 +718,7 @@ static int stage_eig(mmf_batch* b) {
         mark(b, ST_GRAM);
         LAUNCH(mmf_launch_refine_gram(La, b->d_X1, b->d_R, b->d_T, 0), 1);
         mark(b, ST_REFINE2);
-        LAUNCH(mmf_launch_refine_update(La, b->d_coef, b->d_Zf, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_T, b->d_E2,
+        LAUNCH(mmf_launch_refine_update(La, b->d_coef, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_T, b->d_E2,
                                         b->d_status, b->d_cid, b->n_mat, Zp, b->d_jobs, b->d_Eb),
                9);
         if (!b->rband.empty()) {
@@ -732,7 +735,7 @@ static int stage_eig(mmf_batch* b) {
                                          b->d_X1, b->d_jobs, b->d_status, 1),
                    9);
             LAUNCH(mmf_launch_refine_gram(Lf, b->d_X1, b->d_R, b->d_T, 1), 2);
-            LAUNCH(mmf_launch_refine_update(Lf, b->d_coef, b->d_Zf, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_T,
+            LAUNCH(mmf_launch_refine_update(Lf, b->d_coef, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_T,
                                             b->d_E2, b->d_status, b->d_cid, b->n_mat, Zp, b->d_jobs, b->d_Eb),
                    9);
         }
@@ -751,9 +754,12 @@ static int stage_outputs(mmf_batch* b) {
     if (b->n_u > 0) CU(cudaMemsetAsync(b->d_U, 0, sizeof(double2) * b->n_u, st));
     CU(cudaMemsetAsync(b->d_P, 0, sizeof(double) * b->n_p, st));
     MmfLaunch La = launch_of(b, b->all, b->d_all, b->nmax_all);
-    LAUNCH(mmf_launch_outputs(La, b->Mmax, b->Dmax, b->d_E, b->d_Zf, b->d_t, b->t0, b->nt, b->d_F,
+    // FP32 pieces of Z: the mixed path reuses the refinement's X1 and T buffers (free by now)
+    float2* Z1 = b->precision == MMF_MIXED ? b->d_X1 : b->d_Zs;
+    float2* Zlo = b->precision == MMF_MIXED ? reinterpret_cast<float2*>(b->d_T) : b->d_Zs + b->n_mat;
+    LAUNCH(mmf_launch_outputs(La, b->Mmax, b->Dmax, b->d_E, b->d_Zf, Z1, Zlo, b->d_t, b->t0, b->nt, b->d_F,
                               b->d_U, b->d_P, 1e-8),
-           b->nt > 0 ? 3 : 1);
+           b->nt > 0 ? 4 : 1);
     mark(b, ST_COUNT);
     if (b->timing_runs > 0) b->runs_recorded++;
     b->last_stage = 3;

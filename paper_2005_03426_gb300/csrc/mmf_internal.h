@@ -200,8 +200,8 @@ cudaError_t mmf_launch_backtransform(const MmfLaunch& L, const void* H, const vo
                                      void* Tf, const double* Y, void* Z, int fp32);
 cudaError_t mmf_launch_widen(const MmfLaunch& L, const void* Zp, double2* Z, int fp32);
 cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const double* E,
-                               const double2* Z, const double* t, double t0, int nt, double2* F,
-                               double2* U, double* P, double cluster_rel);
+                               const double2* Z, float2* Z1, float2* Zlo, const double* t, double t0, int nt,
+                               double2* F, double2* U, double* P, double cluster_rel);
 int mmf_hetrd_max_n(int fp32);
 cudaError_t mmf_launch_hetrd_large(const MmfDesc& d, void* H, void* Vp, void* Wp, double* dvec, double* evec,
                                    void* tau, void* work, void* sc, int fp32, cudaStream_t st);
@@ -212,9 +212,9 @@ cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const float4* cs, const do
                                   double2* HX, double2* G, double2* S, float2* Zp, double2* T, float2* X1,
                                   void* jobs, int* status, int second);
 cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const float2* X1, double2* G, const double2* T, int second);
-cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, double2* X, const double* lam0,
-                                     double2* G, double2* S, double2* HX, const double2* T, double* lam,
-                                     int* status, int* cid, int64_t mat_elems, float2* Zp, void* jobs,
+cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, double2* X, const float2* X1,
+                                     const double* lam0, double2* G, double2* S, double2* HX, const double2* T,
+                                     double* lam, int* status, int* cid, int64_t mat_elems, float2* Zp, void* jobs,
                                      double2* Eb);
 cudaError_t mmf_launch_refine_band(const MmfLaunch& L, const double2* coef, const float4* cs, double2* X,
                                    double2* G, double2* S, double2* HX, double2* T, float2* X1, double* lam,
