@@ -50,6 +50,32 @@ __device__ __forceinline__ R block_sum(R v, R* red) {
     return r;
 }
 
+
+// FP32 hemv pipeline: per warp two stages of HT_CH rows x 8 columns, filled by cp.async
+#define HT_CH 64
+#define HT_STAGE_ELEMS (8 * HT_CH)
+
+template <class R>
+__host__ __device__ constexpr size_t ht_fixed_bytes() {
+    return sizeof(typename Cx<R>::T) * (4 * MMF_NB + 4) + sizeof(R) * 72;
+}
+template <class R>
+__host__ __device__ inline size_t ht_big_offset(int nmax) {
+    const size_t o = sizeof(typename Cx<R>::T) * 3 * (size_t)nmax + ht_fixed_bytes<R>();
+    return (o + 15) & ~(size_t)15;
+}
+template <class R>
+__host__ __device__ constexpr size_t ht_big_bytes() {
+    return sizeof(R) == 4 ? (size_t)(HT_THREADS / 32) * 2 * HT_STAGE_ELEMS * sizeof(typename Cx<R>::T)
+                          : (size_t)4 * MMF_NB * HT_TILE * sizeof(typename Cx<R>::T);
+}
+
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc, int src_bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+static_assert(4 * MMF_NB * HT_TILE <= (HT_THREADS / 32) * 2 * HT_STAGE_ELEMS, "her2k tiles fit the hemv stages");
+
 // two block-wide sums in one pass (red holds 2 x 33 values)
 template <class R>
 __device__ __forceinline__ void block_sum2(R a, R b, R* red, R& sa, R& sb) {
@@ -85,6 +111,108 @@ __device__ __forceinline__ void atomic_add_c(float2* p, float2 v) {
     atomicAdd(&p->y, v.y);
 }
 
+
+// FP32 hemv share of one warp, pipelined through shared memory: the warp's chunks (HT_CH rows x
+// 8 columns of its row-segment tasks) are copied by cp.async two stages ahead of the arithmetic,
+// so the trailing matrix streams while the previous chunk is multiplied.  Task h of the CTA:
+// column block (rank + CL (h % nloc)) of 8 columns, rows from segment h / nloc (HT_SEG rows).
+__device__ __forceinline__ bool ht_chunk(int h, int u, int nloc, int rank, int CL, int m, int& c0, int& r0,
+                                         int& rend) {
+    const int qb = h % nloc, sg = h / nloc;
+    c0 = (rank + CL * qb) << 3;
+    const int rbeg = c0 + sg * HT_SEG;
+    rend = min(rbeg + HT_SEG, m);
+    r0 = rbeg + u * HT_CH;
+    return r0 < rend;
+}
+
+__device__ void hemv_f32_staged(const float2* __restrict__ a22, int ld, int m, const float2* __restrict__ vS,
+                                float2* yS, float2* stg, int rank, int CL, int nloc, int nseg, int warp,
+                                int lane) {
+    const int NW = HT_THREADS / 32;
+    const int nh = nloc * nseg;
+    int h = warp, u = 0, c0, r0, rend;
+    auto advance = [&](int& hh, int& uu) {
+        int a, b, c;
+        for (;;) {
+            if (uu == 0) {
+                uu = 1;
+            } else {
+                uu = 0;
+                hh += NW;
+            }
+            if (hh >= nh || ht_chunk(hh, uu, nloc, rank, CL, m, a, b, c)) return;
+        }
+    };
+    auto issue = [&](int hh, int uu, float2* buf) {
+        int cc0, rr0, re;
+        ht_chunk(hh, uu, nloc, rank, CL, m, cc0, rr0, re);
+#pragma unroll
+        for (int q = 0; q < HT_STAGE_ELEMS / 32; ++q) {
+            const int e = lane + 32 * q, jj = e / HT_CH, rr = e - jj * HT_CH;
+            const int row = rr0 + rr, col = cc0 + jj;
+            const bool ok = row < re && col < m && row >= col;
+            cp_async8(buf + e, ok ? (const void*)(a22 + row + (int64_t)col * ld) : (const void*)a22, ok ? 8 : 0);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (h < nh && !ht_chunk(h, 0, nloc, rank, CL, m, c0, r0, rend)) advance(h, u);
+    float2 ca[8];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) ca[jj] = czero<float2>();
+    int buf = 0;
+    if (h < nh) issue(h, u, stg);
+    while (h < nh) {
+        int hn = h, un = u;
+        advance(hn, un);
+        if (hn < nh) {
+            issue(hn, un, stg + (buf ^ 1) * HT_STAGE_ELEMS);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncwarp();
+        ht_chunk(h, u, nloc, rank, CL, m, c0, r0, rend);
+        const int nc = min(8, m - c0);
+        const float2* sb = stg + buf * HT_STAGE_ELEMS;
+#pragma unroll
+        for (int half = 0; half < HT_CH / 32; ++half) {
+            const int r = r0 + lane + 32 * half;
+            if (r < rend) {
+                const float2 vr = vS[r];
+                float2 ra = czero<float2>();
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int c = c0 + jj;
+                    if (jj < nc && r >= c) {
+                        const float2 a = sb[jj * HT_CH + lane + 32 * half];
+                        const float2 vc = vS[c];
+                        if (r > c) {
+                            ra = ra + a * vc;
+                            ca[jj] = ca[jj] + cmulc(a, vr);
+                        } else {
+                            ra = ra + a.x * vc;
+                        }
+                    }
+                }
+                atomic_add_c(&yS[r], ra);
+            }
+        }
+        if (hn != h) {  // the task is complete: add its column part
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const float sx = warp_sum(ca[jj].x), sy = warp_sum(ca[jj].y);
+                if (lane == 0 && jj < nc) atomic_add_c(&yS[c0 + jj], mk(sx, sy));
+                ca[jj] = czero<float2>();
+            }
+        }
+        __syncwarp();  // every lane is done with this stage before it is refilled
+        h = hn;
+        u = un;
+        buf ^= 1;
+    }
+}
+
 template <class R, int CL>
 __global__ void __launch_bounds__(HT_THREADS, 1)
 k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
@@ -96,16 +224,18 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
     C* vS = reinterpret_cast<C*>(smem_raw);   // nmax
     C* yS = vS + nmax;                          // nmax: this CTA's partial y = A22 v
     C* yF = yS + nmax;                          // nmax: full y (CL = 2)
-    C* tVr = yF + nmax;                         // MMF_NB x HT_TILE (her2k staging, transposed)
-    C* tWr = tVr + MMF_NB * HT_TILE;
-    C* tVc = tWr + MMF_NB * HT_TILE;
-    C* tWc = tVc + MMF_NB * HT_TILE;
-    C* wk = tWc + MMF_NB * HT_TILE;             // MMF_NB
+    C* wk = yF + nmax;                          // MMF_NB
     C* vk = wk + MMF_NB;                        // MMF_NB
     C* xw = vk + MMF_NB;                        // MMF_NB
     C* xv = xw + MMF_NB;                        // MMF_NB
     C* sc = xv + MMF_NB;                        // 4 scalars: tau, scale, alpha2
     R* red = reinterpret_cast<R*>(sc + 4);      // 66 (two block sums at once)
+    // one region shared by the her2k staging tiles and (FP32) the hemv's cp.async stages
+    C* big = reinterpret_cast<C*>(smem_raw + ht_big_offset<R>(nmax));
+    C* tVr = big;                               // MMF_NB x HT_TILE (her2k staging, transposed)
+    C* tWr = tVr + MMF_NB * HT_TILE;
+    C* tVc = tWr + MMF_NB * HT_TILE;
+    C* tWc = tVc + MMF_NB * HT_TILE;
 
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (CL > 1) ? (int)cluster.block_rank() : 0;
@@ -203,13 +333,39 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
             const int nloc = (nblk - rank + CL - 1) / CL;
             const int nseg = (m + HT_SEG - 1) / HT_SEG;
             const int ntask = 2 * i + nloc * nseg;
+            if constexpr (sizeof(R) == 4) {
+                for (int task = warp; task < 2 * i; task += NW) {
+                    const int c = task >> 1;
+                    const C* P = (task & 1) ? V : W;
+                    // unrolled: the loads of the V / W column are independent (L2 latency each)
+                    C acc = czero<C>(), acc2 = czero<C>();
+#pragma unroll 4
+                    for (int rp = lane; rp < m; rp += 64) {
+                        acc = acc + cmulc(P[(k + 1 + rp) + (int64_t)c * ld], vS[rp]);
+                        if (rp + 32 < m) acc2 = acc2 + cmulc(P[(k + 1 + rp + 32) + (int64_t)c * ld], vS[rp + 32]);
+                    }
+                    acc = acc + acc2;
+                    acc.x = warp_sum(acc.x);
+                    acc.y = warp_sum(acc.y);
+                    if (lane == 0) ((task & 1) ? xv : xw)[c] = acc;
+                }
+                hemv_f32_staged(reinterpret_cast<const float2*>(a22), ld, m, reinterpret_cast<const float2*>(vS),
+                                reinterpret_cast<float2*>(yS),
+                                reinterpret_cast<float2*>(big) + (size_t)warp * 2 * HT_STAGE_ELEMS, rank, CL,
+                                nloc, nseg, warp, lane);
+            } else
             for (int task = warp; task < ntask; task += NW) {
                 if (task < 2 * i) {
                     const int c = task >> 1;
                     const C* P = (task & 1) ? V : W;
-                    C acc = czero<C>();
-                    for (int rp = lane; rp < m; rp += 32)
+                    // unrolled: the loads of the V / W column are independent (L2 latency each)
+                    C acc = czero<C>(), acc2 = czero<C>();
+#pragma unroll 4
+                    for (int rp = lane; rp < m; rp += 64) {
                         acc = acc + cmulc(P[(k + 1 + rp) + (int64_t)c * ld], vS[rp]);
+                        if (rp + 32 < m) acc2 = acc2 + cmulc(P[(k + 1 + rp + 32) + (int64_t)c * ld], vS[rp + 32]);
+                    }
+                    acc = acc + acc2;
                     acc.x = warp_sum(acc.x);
                     acc.y = warp_sum(acc.y);
                     if (lane == 0) ((task & 1) ? xv : xw)[c] = acc;
@@ -250,29 +406,25 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                     }
                     r0 = c0 + 32;
                 }
-                // strictly-lower chunks, two 32-row chunks per pass so that 16 loads per lane are in
-                // flight (the pass is bound by L2/HBM latency, not arithmetic)
-                for (; r0 < rend; r0 += 64) {
-                    const int ra_ = r0 + lane, rb_ = r0 + 32 + lane;
-                    const bool oka = ra_ < rend, okb = rb_ < rend;
-                    C a[8], b[8];
+                // strictly-lower chunks of 32 rows (this loop serves the FP64 path, which is bound by
+                // the FP64 units; the FP32 path streams through hemv_f32_staged)
+                for (; r0 < rend; r0 += 32) {
+                    const int rr = r0 + lane;
+                    if (rr < rend) {
+                        C a[8];
 #pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) {
-                        a[jj] = (jj < nc && oka) ? a22[ra_ + (int64_t)(c0 + jj) * ld] : czero<C>();
-                        b[jj] = (jj < nc && okb) ? a22[rb_ + (int64_t)(c0 + jj) * ld] : czero<C>();
-                    }
-                    const C va = oka ? vS[ra_] : czero<C>();
-                    const C vb = okb ? vS[rb_] : czero<C>();
-                    C sa = czero<C>(), sb = czero<C>();
+                        for (int jj = 0; jj < 8; ++jj)
+                            a[jj] = (jj < nc) ? a22[rr + (int64_t)(c0 + jj) * ld] : czero<C>();
+                        const C vr = vS[rr];
+                        C sa = czero<C>();
 #pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) {
-                        const C v = (jj < nc) ? vS[c0 + jj] : czero<C>();
-                        sa = sa + a[jj] * v;
-                        sb = sb + b[jj] * v;
-                        ca[jj] = ca[jj] + cmulc(a[jj], va) + cmulc(b[jj], vb);
+                        for (int jj = 0; jj < 8; ++jj) {
+                            const C v = (jj < nc) ? vS[c0 + jj] : czero<C>();
+                            sa = sa + a[jj] * v;
+                            ca[jj] = ca[jj] + cmulc(a[jj], vr);
+                        }
+                        atomic_add_c(&yS[rr], sa);
                     }
-                    if (oka) atomic_add_c(&yS[ra_], sa);
-                    if (okb) atomic_add_c(&yS[rb_], sb);
                 }
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
@@ -370,14 +522,15 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
 }
 
 static size_t hetrd_smem(int nmax, int fp32) {
-    size_t cs = fp32 ? 8 : 16, rs = fp32 ? 4 : 8;
-    return cs * (3 * (size_t)nmax + 4 * MMF_NB * HT_TILE + 4 * MMF_NB + 4) + rs * 72;
+    return fp32 ? ht_big_offset<float>(nmax) + ht_big_bytes<float>()
+                : ht_big_offset<double>(nmax) + ht_big_bytes<double>();
 }
 
 int mmf_hetrd_max_n(int fp32) {
-    size_t cs = fp32 ? 8 : 16, rs = fp32 ? 4 : 8;
-    size_t fixed = cs * (4 * MMF_NB * HT_TILE + 4 * MMF_NB + 4) + rs * 72;
-    return (int)((227 * 1024 - fixed) / (3 * cs));
+    const size_t cs = fp32 ? 8 : 16;
+    const size_t fixed = fp32 ? ht_fixed_bytes<float>() + ht_big_bytes<float>()
+                              : ht_fixed_bytes<double>() + ht_big_bytes<double>();
+    return (int)((227 * 1024 - fixed - 16) / (3 * cs));
 }
 
 template <class R, int CL>

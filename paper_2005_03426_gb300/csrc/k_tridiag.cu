@@ -12,9 +12,12 @@
 // Eigenvectors by inverse iteration (Wilkinson 1965): (T - lambda I) y = b solved by
 // Gaussian elimination with partial pivoting on the tridiagonal band, a fixed number of
 // iterations (3) from a hashed start vector.  Eigenvalues closer than ortol = 1e-4 ||T||_1 form a
-// cluster (LAPACK's stein takes 1e-3, which at n ~ 2e4 would chain the whole spectrum); one
-// thread handles a whole cluster in ascending order and orthogonalises each iterate against
-// the cluster's earlier vectors (modified Gram-Schmidt), as LAPACK's stein does.
+// cluster (LAPACK's stein takes 1e-3, which at n ~ 2e4 would chain the whole spectrum).  FP64:
+// one thread handles a whole cluster in ascending order and orthogonalises each iterate against
+// the cluster's earlier vectors (modified Gram-Schmidt), as LAPACK's stein does.  FP32 (followed
+// by the refinement): every vector is iterated on its own thread, and each cluster is then
+// orthonormalised by one warp (two Gram-Schmidt passes), which keeps the serial work per thread
+// at O(n) even where clusters are long.
 // Y is written row-major: Y[i * n + k] = component i of eigenvector k.
 #include "mmf_internal.h"
 
@@ -396,11 +399,27 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
     const double sc = in.scale;
     const double tnd = aux[8 * sid + 3] * sc;
     const double ortol = (double)TriP<R>::ortol * tnd;
-    if (k > 0 && (E[k] - E[k - 1]) * sc <= ortol) return;  // not the first of its cluster
-    int kend = k + 1;
-    while (kend < n && (E[kend] - E[kend - 1]) * sc <= ortol) ++kend;
     const R eps = TriP<R>::eps();
     const R tn = R(tnd);
+    int kbeg = k, kend = k + 1;
+    R lam_first = R(E[k] * sc);
+    if constexpr (sizeof(R) == 4) {
+        // FP32 (mixed path): every vector on its own; clusters are orthonormalised afterwards by
+        // k_cluster_mgs_f32.  Numerically equal eigenvalues (gaps below pert) get staggered shifts
+        // so that their iterates differ: shift = lam of the first of the run + (position) pert.
+        int k1 = k;
+        while (k1 > 0) {
+            const R a = R(E[k1 - 1] * sc), b = R(E[k1] * sc);
+            if (b - a >= R(10) * eps * fmax(fabs(b), tn * R(1e-3))) break;
+            --k1;
+        }
+        const R l1 = R(E[k1] * sc);
+        lam_first = l1 + R(k - k1) * (R(10) * eps * fmax(fabs(l1), tn * R(1e-3)));
+        if (lam_first < R(E[k] * sc)) lam_first = R(E[k] * sc);
+    } else {
+        if (k > 0 && (E[k] - E[k - 1]) * sc <= ortol) return;  // not the first of its cluster
+        while (kend < n && (E[kend] - E[kend - 1]) * sc <= ortol) ++kend;
+    }
     const R pivtiny = eps * fmax(tn, R(1e-30));
     const int64_t s = n;  // row stride of the row-major arrays
     const int64_t nn = (int64_t)n * n;
@@ -411,8 +430,8 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
     float4* F = (float4*)base;  // FP32: packed factors (4 n^2 floats), then the iterate
     R* Yw = sizeof(R) == 8 ? (R*)(Yg + d.sq_off) : base + 4 * nn;
     R lamprev = R(0);
-    for (int j = k; j < kend; ++j) {
-        R lam = R(E[j] * sc);
+    for (int j = kbeg; j < kend; ++j) {
+        R lam = (j == k) ? lam_first : R(E[j] * sc);
         if (j > k) {
             const R pert = R(10) * eps * fmax(fabs(lam), tn * R(1e-3));
             if (lam - lamprev < pert) lam = lamprev + pert;
@@ -429,8 +448,8 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
                 tri_solve_packed(in, n, lam, pivtiny, (float*)y, F + j, s);
             else
                 tri_solve<R>(in, n, lam, pivtiny, y, a0, a1, a2, s);
-            // orthogonalise against the cluster's earlier vectors
-            for (int jp = k; jp < j; ++jp) {
+            // FP64: orthogonalise against the cluster's earlier vectors
+            for (int jp = k; jp < j && sizeof(R) == 8; ++jp) {
                 const R* z = Yw + jp;
                 R dot = R(0);
                 for (int i = 0; i < n; ++i) dot += y[(int64_t)i * s] * z[(int64_t)i * s];
@@ -450,11 +469,61 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
 #pragma unroll 8
             for (int i = 0; i < n; ++i) y[(int64_t)i * s] *= inv;
         }
-        if (sizeof(R) == 4) {
-            double* yo = Yg + d.sq_off + j;
-            for (int i = 0; i < n; ++i) yo[(int64_t)i * s] = (double)y[(int64_t)i * s];
-        }
     }
+}
+
+// FP32 clusters: eigenvalues closer than ortol ||T|| are orthonormalised by one warp each, two
+// passes of modified Gram-Schmidt over the cluster in ascending order (the refinement that
+// follows resolves the eigenvectors inside the cluster).
+__global__ void __launch_bounds__(256) k_cluster_mgs_f32(const MmfDesc* __restrict__ descs,
+                                                         const int* __restrict__ idx,
+                                                         const double* __restrict__ aux,
+                                                         const double* __restrict__ Eg,
+                                                         double* __restrict__ work) {
+    const int sid = idx[blockIdx.y];
+    const MmfDesc d = descs[sid];
+    const int n = d.n;
+    const int lane = threadIdx.x & 31;
+    const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (k >= n) return;
+    const double* E = Eg + d.vec_off;
+    const double ortol = (double)TriP<float>::ortol * aux[8 * sid + 3];
+    if (k > 0 && E[k] - E[k - 1] <= ortol) return;  // not the first of its cluster
+    int kend = k + 1;
+    while (kend < n && E[kend] - E[kend - 1] <= ortol) ++kend;
+    if (kend - k < 2) return;
+    const int64_t s = n, nn = (int64_t)n * n;
+    float* Yw = tri_f32_base((const float*)work, d) + 4 * nn;
+    for (int j = k + 1; j < kend; ++j) {
+        float* y = Yw + j;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int jp = k; jp < j; ++jp) {
+                const float* z = Yw + jp;
+                float dot = 0.f;
+                for (int i = lane; i < n; i += 32) dot += y[(int64_t)i * s] * z[(int64_t)i * s];
+                dot = warp_sum(dot);
+                for (int i = lane; i < n; i += 32) y[(int64_t)i * s] -= dot * z[(int64_t)i * s];
+                __syncwarp();
+            }
+        }
+        float nrm = 0.f;
+        for (int i = lane; i < n; i += 32) nrm += y[(int64_t)i * s] * y[(int64_t)i * s];
+        nrm = warp_sum(nrm);
+        const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
+        for (int i = lane; i < n; i += 32) y[(int64_t)i * s] *= inv;
+        __syncwarp();
+    }
+}
+
+// Y (FP64, row-major) from the FP32 iterates
+__global__ void __launch_bounds__(256) k_widen_y_f32(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
+                                                     const double* __restrict__ work, double* __restrict__ Yg) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int64_t nn = (int64_t)d.n * d.n;
+    const float* Yw = tri_f32_base((const float*)work, d) + 4 * nn;
+    double* Y = Yg + d.sq_off;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x)
+        Y[e] = (double)Yw[e];
 }
 
 cudaError_t mmf_launch_tridiag_eig(const MmfLaunch& L, const double* dvec, const double* evec,
@@ -466,6 +535,8 @@ cudaError_t mmf_launch_tridiag_eig(const MmfLaunch& L, const double* dvec, const
     if (fp32) {
         k_bisect<float><<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, e2, aux, (const float*)work, E, status);
         k_inviter<float><<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux, E, Y, work, iters);
+        k_cluster_mgs_f32<<<dim3((L.nmax + 7) / 8, L.count), 256, 0, L.stream>>>(L.desc, L.idx, aux, E, work);
+        k_widen_y_f32<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, work, Y);
     } else {
         k_bisect<double><<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, e2, aux, nullptr, E, status);
         k_inviter<double><<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux, E, Y, work, iters);
