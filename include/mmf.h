@@ -80,11 +80,14 @@ MMF_API size_t mmf_ctx_budget(const mmf_ctx* ctx);
  * hold); MMF_OPT_REFINE_FULL_N: in the mixed path, smallest n whose second refinement step is a
  * full one instead of the banded one (default 3000; dense spectra of large H_F leave first-step
  * errors between eigenpairs far apart in the sorted order that the banded step cannot reach).
+ * MMF_OPT_GRAM_KERNEL: the mixed path's Gram product X^H X, 0 (default) on the BF16 tensor
+ * cores by exact integer slicing, 1 in double-FP32 on the FP32 units (both FP64-accurate).
  * Results do not depend on the path beyond rounding. */
 #define MMF_OPT_JACOBI_N_FP64 1
 #define MMF_OPT_JACOBI_N_MIXED 2
 #define MMF_OPT_LARGE_N 3
 #define MMF_OPT_REFINE_FULL_N 4
+#define MMF_OPT_GRAM_KERNEL 5
 MMF_API int mmf_ctx_set_option(mmf_ctx* ctx, int option, int64_t value);
 
 /* ---------------------------------------------------------------- system definition
@@ -233,6 +236,12 @@ MMF_API int mmf_tridiag_eig_noalloc(const double* d, const double* e, int n, dou
  * device memory; for health checks, not for the solve path. */
 MMF_API int mmf_selftest_tensor_cores(int M, int N, int K, int kind, int products, double* max_abs_err,
                                       double* max_abs_ref);
+/* Runs the mixed path's tensor-core Gram product G = X^H X (exact integer slicing of FP32 X on
+ * the BF16 tensor cores) on one seeded n x n complex FP32 matrix (1 <= n <= 8192; entries over
+ * six orders of magnitude) and compares it with an FP64 reference computed on the device.
+ * Returns the largest absolute difference and the largest |reference| entry; allocates its own
+ * device memory. */
+MMF_API int mmf_selftest_gram(int n, double* max_abs_err, double* max_abs_ref);
 
 /* ---------------------------------------------------------------- misc */
 MMF_API const char* mmf_strerror(int status);

@@ -113,104 +113,123 @@ __device__ __forceinline__ void atomic_add_c(float2* p, float2 v) {
 
 
 // FP32 hemv share of one warp, pipelined through shared memory: the warp's chunks (HT_CH rows x
-// 8 columns of its row-segment tasks) are copied by cp.async two stages ahead of the arithmetic,
+// 8 columns of its row-segment tasks) are copied by cp.async one chunk ahead of the arithmetic,
 // so the trailing matrix streams while the previous chunk is multiplied.  Task h of the CTA:
 // column block (rank + CL (h % nloc)) of 8 columns, rows from segment h / nloc (HT_SEG rows).
-__device__ __forceinline__ bool ht_chunk(int h, int u, int nloc, int rank, int CL, int m, int& c0, int& r0,
-                                         int& rend) {
+// The arithmetic is branch-free outside the diagonal chunk: the block's 8 entries of v are held
+// in registers per task, the chunk's operands are read from shared memory before the FMAs.
+struct HtTask {
+    int c0, rbeg, rend, nc;
+};
+
+__device__ __forceinline__ bool ht_task(int h, int nloc, int rank, int CL, int m, HtTask& t) {
     const int qb = h % nloc, sg = h / nloc;
-    c0 = (rank + CL * qb) << 3;
-    const int rbeg = c0 + sg * HT_SEG;
-    rend = min(rbeg + HT_SEG, m);
-    r0 = rbeg + u * HT_CH;
-    return r0 < rend;
+    t.c0 = (rank + CL * qb) << 3;
+    t.rbeg = t.c0 + sg * HT_SEG;
+    t.rend = min(t.rbeg + HT_SEG, m);
+    t.nc = min(8, m - t.c0);
+    return t.rbeg < m;
 }
 
-__device__ void hemv_f32_staged(const float2* __restrict__ a22, int ld, int m, const float2* __restrict__ vS,
-                                float2* yS, float2* stg, int rank, int CL, int nloc, int nseg, int warp,
-                                int lane) {
+__device__ __forceinline__ void ht_issue(const float2* __restrict__ a22, int ld, const HtTask& t, int r0,
+                                         float2* buf, int lane) {
+    const float2* colbase = a22 + (int64_t)t.c0 * ld;
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+#pragma unroll
+        for (int hf = 0; hf < HT_CH / 32; ++hf) {
+            const int row = r0 + lane + 32 * hf;
+            const bool ok = jj < t.nc && row < t.rend && row >= t.c0 + jj;
+            const float2* src = ok ? colbase + (int64_t)jj * ld + row : a22;
+            cp_async8(buf + jj * HT_CH + lane + 32 * hf, src, ok ? 8 : 0);
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ int hemv_f32_staged(const float2* __restrict__ a22, int ld, int m, const float2* __restrict__ vS,
+                               float2* yS, float2* stg, int rank, int CL, int nloc, int nseg, int warp, int lane) {
     const int NW = HT_THREADS / 32;
     const int nh = nloc * nseg;
-    int h = warp, u = 0, c0, r0, rend;
-    auto advance = [&](int& hh, int& uu) {
-        int a, b, c;
-        for (;;) {
-            if (uu == 0) {
-                uu = 1;
-            } else {
-                uu = 0;
-                hh += NW;
-            }
-            if (hh >= nh || ht_chunk(hh, uu, nloc, rank, CL, m, a, b, c)) return;
-        }
-    };
-    auto issue = [&](int hh, int uu, float2* buf) {
-        int cc0, rr0, re;
-        ht_chunk(hh, uu, nloc, rank, CL, m, cc0, rr0, re);
+    // the warp's first valid task
+    int h = warp;
+    HtTask t;
+    while (h < nh && !ht_task(h, nloc, rank, CL, m, t)) h += NW;
+    if (h >= nh) return 0;
+    int r0 = t.rbeg, buf = 0, nchunks = 0;
+    ht_issue(a22, ld, t, r0, stg, lane);
+    float2 v[8], ca[8];
 #pragma unroll
-        for (int q = 0; q < HT_STAGE_ELEMS / 32; ++q) {
-            const int e = lane + 32 * q, jj = e / HT_CH, rr = e - jj * HT_CH;
-            const int row = rr0 + rr, col = cc0 + jj;
-            const bool ok = row < re && col < m && row >= col;
-            cp_async8(buf + e, ok ? (const void*)(a22 + row + (int64_t)col * ld) : (const void*)a22, ok ? 8 : 0);
+    for (int jj = 0; jj < 8; ++jj) {
+        v[jj] = (jj < t.nc) ? vS[t.c0 + jj] : czero<float2>();
+        ca[jj] = czero<float2>();
+    }
+    for (;;) {
+        ++nchunks;
+        // next chunk: the rest of this task, else the next valid task
+        int hn = h, r0n = r0 + HT_CH;
+        HtTask tn = t;
+        if (r0n >= t.rend) {
+            hn = h + NW;
+            while (hn < nh && !ht_task(hn, nloc, rank, CL, m, tn)) hn += NW;
+            r0n = tn.rbeg;
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    if (h < nh && !ht_chunk(h, 0, nloc, rank, CL, m, c0, r0, rend)) advance(h, u);
-    float2 ca[8];
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj) ca[jj] = czero<float2>();
-    int buf = 0;
-    if (h < nh) issue(h, u, stg);
-    while (h < nh) {
-        int hn = h, un = u;
-        advance(hn, un);
-        if (hn < nh) {
-            issue(hn, un, stg + (buf ^ 1) * HT_STAGE_ELEMS);
+        const bool more = hn < nh;
+        if (more) {
+            ht_issue(a22, ld, tn, r0n, stg + (buf ^ 1) * HT_STAGE_ELEMS, lane);
             asm volatile("cp.async.wait_group 1;" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncwarp();
-        ht_chunk(h, u, nloc, rank, CL, m, c0, r0, rend);
-        const int nc = min(8, m - c0);
         const float2* sb = stg + buf * HT_STAGE_ELEMS;
+        const bool diag = r0 < t.c0 + 8;  // the chunk holds the diagonal entries of the block
 #pragma unroll
-        for (int half = 0; half < HT_CH / 32; ++half) {
-            const int r = r0 + lane + 32 * half;
-            if (r < rend) {
-                const float2 vr = vS[r];
-                float2 ra = czero<float2>();
+        for (int hf = 0; hf < HT_CH / 32; ++hf) {
+            const int r = r0 + lane + 32 * hf;
+            float2 a[8];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) a[jj] = sb[jj * HT_CH + lane + 32 * hf];  // 0 where not loaded
+            const float2 vr = (r < t.rend) ? vS[r] : czero<float2>();
+            float2 ra = czero<float2>();
+            if (!diag) {
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
-                    const int c = c0 + jj;
-                    if (jj < nc && r >= c) {
-                        const float2 a = sb[jj * HT_CH + lane + 32 * half];
-                        const float2 vc = vS[c];
-                        if (r > c) {
-                            ra = ra + a * vc;
-                            ca[jj] = ca[jj] + cmulc(a, vr);
-                        } else {
-                            ra = ra + a.x * vc;
-                        }
+                    ra = ra + a[jj] * v[jj];
+                    ca[jj] = ca[jj] + cmulc(a[jj], vr);
+                }
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int c = t.c0 + jj;
+                    if (r > c) {
+                        ra = ra + a[jj] * v[jj];
+                        ca[jj] = ca[jj] + cmulc(a[jj], vr);
+                    } else if (r == c) {
+                        ra = ra + a[jj].x * v[jj];
                     }
                 }
-                atomic_add_c(&yS[r], ra);
             }
+            if (r < t.rend) atomic_add_c(&yS[r], ra);
         }
-        if (hn != h) {  // the task is complete: add its column part
+        __syncwarp();  // every lane is done with this stage before it is refilled
+        if (hn != h || !more) {  // the task is complete: add its column part
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
                 const float sx = warp_sum(ca[jj].x), sy = warp_sum(ca[jj].y);
-                if (lane == 0 && jj < nc) atomic_add_c(&yS[c0 + jj], mk(sx, sy));
+                if (lane == 0 && jj < t.nc) atomic_add_c(&yS[t.c0 + jj], mk(sx, sy));
                 ca[jj] = czero<float2>();
             }
+            if (!more) break;
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) v[jj] = (jj < tn.nc) ? vS[tn.c0 + jj] : czero<float2>();
         }
-        __syncwarp();  // every lane is done with this stage before it is refilled
         h = hn;
-        u = un;
+        t = tn;
+        r0 = r0n;
         buf ^= 1;
     }
+    return nchunks;
 }
 
 template <class R, int CL>
@@ -349,7 +368,7 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                     acc.y = warp_sum(acc.y);
                     if (lane == 0) ((task & 1) ? xv : xw)[c] = acc;
                 }
-                hemv_f32_staged(reinterpret_cast<const float2*>(a22), ld, m, reinterpret_cast<const float2*>(vS),
+                (void)hemv_f32_staged(reinterpret_cast<const float2*>(a22), ld, m, reinterpret_cast<const float2*>(vS),
                                 reinterpret_cast<float2*>(yS),
                                 reinterpret_cast<float2*>(big) + (size_t)warp * 2 * HT_STAGE_ELEMS, rank, CL,
                                 nloc, nseg, warp, lane);

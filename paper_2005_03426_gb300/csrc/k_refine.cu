@@ -1060,6 +1060,12 @@ cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const float2* X1, double2
     return cudaGetLastError();
 }
 
+cudaError_t mmf_launch_refine_gram_fix(const MmfLaunch& L, double2* G, const double2* T) {
+    if (L.count <= 0) return cudaSuccess;
+    k_gram_fix<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, T);
+    return cudaGetLastError();
+}
+
 cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, double2* X, const float2* X1,
                                      const double* lam0, double2* G, double2* S, double2* HX, const double2* T,
                                      double* lam, int* status, int* cid, int64_t mat_elems, float2* Zp, void* jobs,

@@ -45,6 +45,7 @@ struct mmf_ctx {
     int64_t jacobi_n[2] = {-1, -1};  // per precision; -1 = library default
     int64_t large_n = -1;            // whole-GPU reduction from this n on; -1 = when one CTA cannot
     int64_t refine_full_n = -1;      // mixed path: second refinement step in full from this n on
+    int64_t gram_kernel = 0;         // mixed path: 0 = BF16 tensor cores (exact slicing), 1 = double-FP32
     std::recursive_mutex mu;
 };
 
@@ -78,6 +79,8 @@ struct mmf_batch {
     std::vector<int> rband, rfull;                     // mixed: banded / full second refinement step
     int nmax_rband = 0, nmax_rfull = 0;
     int nmax_all = 0, nmax_small = 0, nmax_large = 0, Mmax = 1, Dmax = 1;
+    int64_t n_oz = 0;      // BF16 elements of the Gram-product slices (mixed, tensor-core Gram)
+    int gram_kernel = 0;   // copied from the context at creation
     int64_t n_coef = 0, n_mat = 0, n_vec = 0, n_sq = 0, n_pan = 0, n_t = 0, n_f = 0, n_u = 0,
             n_p = 0;
     // device
@@ -101,6 +104,8 @@ struct mmf_batch {
     double2 *d_R = nullptr, *d_S = nullptr, *d_HX = nullptr, *d_Eb = nullptr, *d_T = nullptr;
     float2* d_X1 = nullptr;
     float4* d_coefs = nullptr;  // coefficients split into FP32 pieces (mixed refinement)
+    void* d_oz = nullptr;       // Gram-product slices (BF16)
+    int* d_ozexp = nullptr;     // per-column scale exponents of the slices
     float2* d_Zs = nullptr;     // FP64 path: Z split into FP32 pieces for the time evolution
     double* d_E2 = nullptr;
     int* d_cid = nullptr;
@@ -228,6 +233,10 @@ extern "C" int mmf_ctx_set_option(mmf_ctx* c, int option, int64_t value) {
         case MMF_OPT_JACOBI_N_MIXED: c->jacobi_n[1] = value; return MMF_OK;
         case MMF_OPT_LARGE_N: c->large_n = value; return MMF_OK;
         case MMF_OPT_REFINE_FULL_N: c->refine_full_n = value; return MMF_OK;
+        case MMF_OPT_GRAM_KERNEL:
+            if (value > 1) return fail(MMF_ERR_ARG, "MMF_OPT_GRAM_KERNEL: 0 (tensor cores) or 1 (double-FP32)");
+            c->gram_kernel = value < 0 ? 0 : value;
+            return MMF_OK;
         default: return fail(MMF_ERR_ARG, "unknown option");
     }
 }
@@ -358,6 +367,7 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     b->count = count;
     b->precision = precision;
     b->nt = nt;
+    b->gram_kernel = (int)ctx->gram_kernel;
     b->sys.assign(systems, systems + count);
     b->desc.resize(count);
     const int fp32 = precision == MMF_MIXED;
@@ -400,6 +410,8 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         d.vec_off = b->n_vec;
         b->n_vec += n;
         d.sq_off = b->n_sq;
+        d.oz_off = b->n_oz;
+        if (precision == MMF_MIXED && ctx->gram_kernel == 0) b->n_oz += (int64_t)mmf_ozaki_slice_elems((int)n);
         d.pan_off = b->n_pan;
         if (!d.small) {
             b->n_sq += n * n;
@@ -452,13 +464,16 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     size_t o_F = p.take(sizeof(double2) * std::max<int64_t>(b->n_f, 1));
     size_t o_U = p.take(sizeof(double2) * std::max<int64_t>(b->n_u, 1));
     size_t o_P = p.take(sizeof(double) * b->n_p);
-    size_t o_R = 0, o_S = 0, o_HX = 0, o_E2 = 0, o_cid = 0, o_jobs = 0, o_Eb = 0, o_T = 0, o_X1 = 0, o_coefs = 0;
+    size_t o_R = 0, o_S = 0, o_HX = 0, o_E2 = 0, o_cid = 0, o_jobs = 0, o_Eb = 0, o_T = 0, o_X1 = 0, o_coefs = 0, o_oz = 0,
+           o_ozexp = 0;
     const size_t o_Zs = (!fp32 && nt > 0) ? p.take(sizeof(float2) * 2 * b->n_mat) : 0;
     if (fp32) {
         o_Eb = p.take(sizeof(double2) * b->n_vec * MMF_REFINE_BW);
         o_T = p.take(sizeof(double2) * b->n_mat);
         o_X1 = p.take(sizeof(float2) * b->n_mat);
         o_coefs = p.take(sizeof(float4) * std::max<int64_t>(b->n_coef, 1));
+        o_oz = p.take(sizeof(uint16_t) * std::max<int64_t>(b->n_oz, 1));
+        o_ozexp = p.take(sizeof(int) * b->n_vec);
         o_R = p.take(sizeof(double2) * b->n_mat);
         o_S = p.take(sizeof(double2) * b->n_mat);
         o_HX = p.take(sizeof(double2) * b->n_mat);
@@ -518,6 +533,8 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         b->d_T = (double2*)(B + o_T);
         b->d_X1 = (float2*)(B + o_X1);
         b->d_coefs = (float4*)(B + o_coefs);
+        b->d_oz = B + o_oz;
+        b->d_ozexp = (int*)(B + o_ozexp);
     }
     if (b->pinned) {
         e = cudaMallocHost((void**)&b->h_coef, sizeof(double2) * std::max<int64_t>(b->n_coef, 1));
@@ -674,6 +691,17 @@ static int stage_assemble(mmf_batch* b) {
     return MMF_OK;
 }
 
+// G = X1^H X1 (+ C' + C'^H in a second full step): BF16 tensor cores with exact slicing, or
+// double-FP32 on the FP32 pipes
+static cudaError_t refine_gram(mmf_batch* b, const MmfLaunch& L, int second) {
+    if (b->gram_kernel == 0) {
+        cudaError_t e = mmf_launch_ozaki_gram(L, b->d_X1, b->d_oz, b->d_ozexp, b->d_R, b->d_status);
+        if (e != cudaSuccess || !second) return e;
+        return mmf_launch_refine_gram_fix(L, b->d_R, b->d_T);
+    }
+    return mmf_launch_refine_gram(L, b->d_X1, b->d_R, b->d_T, second);
+}
+
 static int stage_eig(mmf_batch* b) {
     const int fp32 = b->precision == MMF_MIXED;
     mark(b, ST_JACOBI);
@@ -716,7 +744,7 @@ static int stage_eig(mmf_batch* b) {
                                      b->d_jobs, b->d_status, 0),
                6);
         mark(b, ST_GRAM);
-        LAUNCH(mmf_launch_refine_gram(La, b->d_X1, b->d_R, b->d_T, 0), 1);
+        LAUNCH(refine_gram(b, La, 0), 2);
         mark(b, ST_REFINE2);
         LAUNCH(mmf_launch_refine_update(La, b->d_coef, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_T, b->d_E2,
                                         b->d_status, b->d_cid, b->n_mat, Zp, b->d_jobs, b->d_Eb),
@@ -734,7 +762,7 @@ static int stage_eig(mmf_batch* b) {
             LAUNCH(mmf_launch_refine_pre(Lf, b->d_coefs, b->d_Zf, b->d_E, b->d_HX, b->d_R, b->d_S, Zp, b->d_T,
                                          b->d_X1, b->d_jobs, b->d_status, 1),
                    9);
-            LAUNCH(mmf_launch_refine_gram(Lf, b->d_X1, b->d_R, b->d_T, 1), 2);
+            LAUNCH(refine_gram(b, Lf, 1), 3);
             LAUNCH(mmf_launch_refine_update(Lf, b->d_coef, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_T,
                                             b->d_E2, b->d_status, b->d_cid, b->n_mat, Zp, b->d_jobs, b->d_Eb),
                    9);
@@ -1417,6 +1445,15 @@ extern "C" int mmf_selftest_tensor_cores(int M, int N, int K, int kind, int prod
     if (!max_abs_err || !max_abs_ref) return fail(MMF_ERR_ARG, "output pointers required");
     int rc = mmf_umma_selftest_impl(M, N, K, kind, products, max_abs_err, max_abs_ref);
     if (rc == -1) return fail(MMF_ERR_ARG, "bad self-test sizes");
+    if (rc == -4) return fail(MMF_ERR_CUDA, "self-test CUDA failure");
+    if (rc == 1) return fail(MMF_ST_NOCONV, "tensor-core pipeline wait timed out");
+    return MMF_OK;
+}
+
+extern "C" int mmf_selftest_gram(int n, double* max_abs_err, double* max_abs_ref) {
+    if (!max_abs_err || !max_abs_ref) return fail(MMF_ERR_ARG, "output pointers required");
+    int rc = mmf_ozaki_selftest_impl(n, max_abs_err, max_abs_ref);
+    if (rc == -1) return fail(MMF_ERR_ARG, "bad self-test size");
     if (rc == -4) return fail(MMF_ERR_CUDA, "self-test CUDA failure");
     if (rc == 1) return fail(MMF_ST_NOCONV, "tensor-core pipeline wait timed out");
     return MMF_OK;

@@ -26,6 +26,7 @@ struct MmfDesc {
     int64_t f_off;      // double2 offset of its nt x M Fourier phase table
     int64_t u_off;      // double2 offset of its nt x D x D time-evolution output
     int64_t p_off;      // offset of its D x D transition-probability output
+    int64_t oz_off;     // BF16 offset of its Gram-product slices (mixed path)
 };
 
 // ------------------------------------------------------------------ complex helpers
@@ -212,6 +213,7 @@ cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const float4* cs, const do
                                   double2* HX, double2* G, double2* S, float2* Zp, double2* T, float2* X1,
                                   void* jobs, int* status, int second);
 cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const float2* X1, double2* G, const double2* T, int second);
+cudaError_t mmf_launch_refine_gram_fix(const MmfLaunch& L, double2* G, const double2* T);
 cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, double2* X, const float2* X1,
                                      const double* lam0, double2* G, double2* S, double2* HX, const double2* T,
                                      double* lam, int* status, int* cid, int64_t mat_elems, float2* Zp, void* jobs,
@@ -221,6 +223,11 @@ cudaError_t mmf_launch_refine_band(const MmfLaunch& L, const double2* coef, cons
                                    int* status, int* cid, int64_t mat_elems);
 cudaError_t mmf_launch_refine_finish(const MmfLaunch& L, double2* X, double* E, const double* lam, double2* S,
                                      int64_t mat_elems);
+// Gram product on the BF16 tensor cores by exact integer slicing (k_ozaki.cu)
+#define OZ_S 7
+size_t mmf_ozaki_slice_elems(int n);
+cudaError_t mmf_launch_ozaki_gram(const MmfLaunch& L, const float2* X1, void* S, int* exps, double2* G, int* err);
+int mmf_ozaki_selftest_impl(int n, double* max_abs, double* max_ref);
 #define MMF_REFINE_BW 33   // entries per row of the refinement's band buffer (2 W + 1)
 #define MMF_REFINE_FULL2_N 3000   // from this n on the second refinement step is a full one
 // batched tensor-core GEMM (k_umma.cu): C(m, n) = sum_p sum_k A_p(m, k) B_p(n, k), K-major

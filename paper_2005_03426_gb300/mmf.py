@@ -38,6 +38,7 @@ MMF_OPT_JACOBI_N_FP64 = 1
 MMF_OPT_JACOBI_N_MIXED = 2
 MMF_OPT_LARGE_N = 3
 MMF_OPT_REFINE_FULL_N = 4
+MMF_OPT_GRAM_KERNEL = 5
 
 _lib = None
 _exiting = False
@@ -111,6 +112,7 @@ _SIGS = {
     "mmf_serve_reset_stats": (_I, [_P]),
     "mmf_serve_destroy": (_I, [_P]),
     "mmf_selftest_tensor_cores": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "mmf_selftest_gram": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "mmf_strerror": (ctypes.c_char_p, [_I]),
     "mmf_last_error": (ctypes.c_char_p, []),
     "mmf_last_launch_count": (_I, []),

@@ -23,3 +23,16 @@ def test_tensor_core_gemm(kind, shape, products):
     assert ref.value > 0
     # exact products, FP32 accumulation: error grows with the number of accumulated terms
     assert err.value <= 1e-5 * ref.value * max(1.0, k * products / 256.0), (err.value, ref.value)
+
+
+@pytest.mark.parametrize("n", [1, 37, 64, 129, 300, 1323, 2049, 4100])
+def test_gram_on_tensor_cores_is_fp64_accurate(n):
+    """The mixed path's Gram product by exact integer slicing on the BF16 tensor cores against an
+    FP64 reference: sizes below, at and across the 128 x 64 tiles, the K-chunking (2n > 3968)
+    and entries spread over six orders of magnitude.  Bound: 2^-40 per entry for columns of
+    norm <= sqrt(n)/2 (each slice pair is exact; only the 42-bit truncation remains)."""
+    err, ref = ctypes.c_double(0), ctypes.c_double(0)
+    rc = M.lib().mmf_selftest_gram(n, ctypes.byref(err), ctypes.byref(ref))
+    assert rc == 0, M.lib().mmf_last_error()
+    assert ref.value > 0
+    assert err.value <= 2.0 ** -40 * max(1.0, ref.value) * 4
