@@ -171,6 +171,116 @@ __global__ void __launch_bounds__(BT_THREADS) k_backtransform(
     }
 }
 
+// FP32 variant arranged for the FP32 pipes rather than shared-memory bandwidth: lane = column
+// of the slab, so the reflector entries are shared-memory broadcasts and each thread keeps
+// several outputs in registers.  Z tiles of BF_RT rows pass through shared memory so that global
+// accesses stay coalesced.
+//   X = V^H Z:  thread (group g, warp w < 8, lane c): X(4w .. 4w+3, c) over the tile rows of
+//               parity g; the two groups' partial sums are added at the end.
+//   X <- T X:   thread (w, c): X(w, c), X(w + 16, c).
+//   Z -= V X:   thread (w, c): rows 8w .. 8w+7 of column c.
+#define BF_RT 128
+
+__global__ void __launch_bounds__(BT_THREADS) k_backtransform_f32(
+    const MmfDesc* __restrict__ descs, const int* __restrict__ idx, const float2* __restrict__ H,
+    const float2* __restrict__ Tf, const double* __restrict__ Yg, float2* __restrict__ Zg) {
+    extern __shared__ __align__(16) unsigned char bf_smem[];
+    float2(*Vt)[MMF_NB + 1] = reinterpret_cast<float2(*)[MMF_NB + 1]>(bf_smem);      // BF_RT rows
+    float2(*Zt)[BT_CW + 1] = reinterpret_cast<float2(*)[BT_CW + 1]>(Vt + BF_RT);     // BF_RT rows
+    float2(*X)[BT_CW] = reinterpret_cast<float2(*)[BT_CW]>(Zt + BF_RT);              // MMF_NB rows
+    float2(*Xp)[BT_CW] = X + MMF_NB;                                                 // MMF_NB rows
+    float2(*Ts)[MMF_NB + 1] = reinterpret_cast<float2(*)[MMF_NB + 1]>(Xp + MMF_NB);  // MMF_NB rows
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n, ld = d.ld;
+    const int c0 = blockIdx.x * BT_CW;
+    if (c0 >= n) return;
+    const int ncol = min(BT_CW, n - c0);
+    const float2* A = H + d.mat_off;
+    float2* Z = Zg + d.mat_off;
+    const double* Y = Yg + d.sq_off;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // Z(:, slab) = Y(:, slab)
+    for (int e = tid; e < n * BT_CW; e += BT_THREADS) {
+        const int r = e / BT_CW, c = e - r * BT_CW;
+        if (c < ncol) Z[r + (int64_t)(c0 + c) * ld] = make_float2((float)Y[(int64_t)r * n + c0 + c], 0.f);
+    }
+    __syncthreads();
+    const int nref = n - 1;
+    const int nblk = (nref + MMF_NB - 1) / MMF_NB;
+    const int g = warp >> 3, w8 = warp & 7;
+    auto load_tiles = [&](int k0, int nbk, int r0) {
+        for (int e = tid; e < BF_RT * MMF_NB; e += BT_THREADS) {
+            const int c = e / BF_RT, rr = e - c * BF_RT, r = r0 + rr;
+            Vt[rr][c] = (r < n && c < nbk) ? refl<float>(A, ld, k0 + c, r) : make_float2(0.f, 0.f);
+        }
+        for (int e = tid; e < BF_RT * BT_CW; e += BT_THREADS) {
+            const int c = e / BF_RT, rr = e - c * BF_RT, r = r0 + rr;
+            Zt[rr][c] = (r < n && c < ncol) ? Z[r + (int64_t)(c0 + c) * ld] : make_float2(0.f, 0.f);
+        }
+    };
+    for (int bi = nblk - 1; bi >= 0; --bi) {
+        const int k0 = bi * MMF_NB;
+        const int nbk = min(MMF_NB, nref - k0);
+        const float2* Tb = Tf + d.pan_off + (int64_t)bi * MMF_NB * MMF_NB;
+        for (int e = tid; e < MMF_NB * MMF_NB; e += BT_THREADS) Ts[e / MMF_NB][e % MMF_NB] = Tb[e];
+        // X = V^H Z over rows k0+1 .. n-1
+        float2 x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = make_float2(0.f, 0.f);
+        for (int r0 = k0 + 1; r0 < n; r0 += BF_RT) {
+            load_tiles(k0, nbk, r0);
+            __syncthreads();
+#pragma unroll 4
+            for (int rr = g; rr < BF_RT; rr += 2) {
+                const float2 z = Zt[rr][lane];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) x[q] = x[q] + cmulc(Vt[rr][4 * w8 + q], z);
+            }
+            __syncthreads();
+        }
+        if (g == 1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Xp[4 * w8 + q][lane] = x[q];
+        }
+        __syncthreads();
+        if (g == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) X[4 * w8 + q][lane] = x[q] + Xp[4 * w8 + q][lane];
+        }
+        __syncthreads();
+        // X <- T X (T upper triangular)
+        float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
+        for (int q = warp; q < MMF_NB; ++q) y0 = y0 + Ts[warp][q] * X[q][lane];
+        for (int q = warp + 16; q < MMF_NB; ++q) y1 = y1 + Ts[warp + 16][q] * X[q][lane];
+        __syncthreads();
+        X[warp][lane] = y0;
+        X[warp + 16][lane] = y1;
+        __syncthreads();
+        // Z <- Z - V X
+        for (int r0 = k0 + 1; r0 < n; r0 += BF_RT) {
+            load_tiles(k0, nbk, r0);
+            __syncthreads();
+            float2 acc[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+#pragma unroll 4
+            for (int p = 0; p < MMF_NB; ++p) {
+                const float2 xv = X[p][lane];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[q] = acc[q] + Vt[8 * warp + q][p] * xv;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) Zt[8 * warp + q][lane] = Zt[8 * warp + q][lane] - acc[q];
+            __syncthreads();
+            for (int e = tid; e < BF_RT * BT_CW; e += BT_THREADS) {
+                const int c = e / BF_RT, rr = e - c * BF_RT, r = r0 + rr;
+                if (r < n && c < ncol) Z[r + (int64_t)(c0 + c) * ld] = Zt[rr][c];
+            }
+            __syncthreads();
+        }
+    }
+}
+
 template <class R>
 __global__ void k_widen(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                         const typename Cx<R>::T* __restrict__ Zp, double2* __restrict__ Z) {
@@ -192,12 +302,14 @@ cudaError_t mmf_launch_backtransform(const MmfLaunch& L, const void* H, const vo
                                     MMF_NB * (BT_CW + 1) + MMF_NB * (MMF_NB + 1));
     cudaError_t err;
     if (fp32) {
-        err = cudaFuncSetAttribute(k_backtransform<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        const size_t smf = sizeof(float2) * (size_t)(BF_RT * (MMF_NB + 1) + BF_RT * (BT_CW + 1) +
+                                                     2 * MMF_NB * BT_CW + MMF_NB * (MMF_NB + 1));
+        err = cudaFuncSetAttribute(k_backtransform_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
         if (err != cudaSuccess) return err;
         k_larft<float><<<gt, BT_THREADS, 0, L.stream>>>(L.desc, L.idx, (const float2*)H,
                                                         (const float2*)tau, (float2*)Tf);
-        k_backtransform<float><<<gb, BT_THREADS, sm, L.stream>>>(L.desc, L.idx, (const float2*)H,
-                                                                 (const float2*)Tf, Y, (float2*)Z);
+        k_backtransform_f32<<<gb, BT_THREADS, smf, L.stream>>>(L.desc, L.idx, (const float2*)H,
+                                                              (const float2*)Tf, Y, (float2*)Z);
     } else {
         err = cudaFuncSetAttribute(k_backtransform<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (err != cudaSuccess) return err;

@@ -20,11 +20,20 @@
 // end G_ij = 2^(e_i + e_j - 6 (OZ_L + 2) + 6) acc_ij, one rounding to FP64.
 // Error: the dropped pairs and slice remainders are below ~2^-40 |x_i| |x_j| per entry.
 //
-// One CTA of 128 threads per 128 x 64 tile of the lower triangle (Re and Im accumulated side by
-// side in TMEM: columns 0..63 and 64..127), two cp.async stages of A (128 rows) and B, B' (64 rows)
-// in the 128-byte-swizzled K-major layout, one thread issuing tcgen05.mma, int64 accumulators in
-// shared memory [column][row].  Every mbarrier wait is bounded; a time-out sets *err, frees
-// TMEM and leaves.
+// Data layout: the slicing kernel writes every slice pre-tiled in the shared-memory layout the
+// tensor cores read (64-row x 64-K tiles of 8 KB, 128-byte swizzle, K-major), so one stage of
+// operands is three bulk copies.  One CTA per 128 x 64 tile of the lower triangle of G, six warps:
+//   warp 4 (one lane): producer, fills a ring of OZ_STAGES stages (A 16 KB, B 8 KB, B' 8 KB) with
+//                      cp.async.bulk, completion counted on full[stage];
+//   warp 5 (one lane): MMA issuer, tcgen05.mma into one of two TMEM accumulators (Re | Im,
+//                      128 columns each), releasing stages through tcgen05.commit on empty[stage]
+//                      and finished chunks on accfull[buffer];
+//   warps 0-3:         drain each finished chunk (TMEM lanes = tile rows) into int64 accumulators
+//                      kept in TMEM (low words in columns 256..383, high words in 384..511) and
+//                      release the buffer on accempty[buffer], so the next chunk's products run
+//                      meanwhile; at the end they scale the sums and write G.
+// Every wait is bounded and also ends on a shared abort flag; a time-out sets *err and the CTA
+// frees its TMEM and leaves.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -41,15 +50,24 @@
 #define OZ_KSTEP 64            // BF16 elements of K per stage (one 128-byte row segment)
 #define OZ_KCH (62 * OZ_KSTEP) // K per exact FP32 accumulation: 3968 * 2^12 < 2^24
 #define OZ_STAGE_BYTES (16384 + 8192 + 8192)
+#define OZ_STAGES 6
+#define OZ_TILE_ELEMS 4096      // one 64 x 64 BF16 tile (8 KB)
+#define OZ_WARPS 6
 
 static_assert(OZ_S == OZ_L + 1, "slices cover the kept pairs");
 
 __host__ __device__ __forceinline__ int oz_la(int n) { return (2 * n + OZ_KSTEP - 1) / OZ_KSTEP * OZ_KSTEP; }
+__host__ __device__ __forceinline__ int oz_nt(int n) { return oz_la(n) / OZ_KSTEP; }             // K tiles
+__host__ __device__ __forceinline__ int oz_nq(int n) { return ((n + 63) / 64 + 1) / 2 * 2; }     // 64-row panels
+// element offset of tile (slice s, K tile t, row panel q); A tiles (128 rows) are panels 2I, 2I+1
+__host__ __device__ __forceinline__ int64_t oz_tile_off(int n, int s, int t, int q) {
+    return (((int64_t)s * oz_nt(n) + t) * oz_nq(n) + q) * OZ_TILE_ELEMS;
+}
 
 // ------------------------------------------------------------------ slicing
-// One warp per column: scale exponent, then the OZ_S slices of a_i (Sa) and a'_i (Sb).
-// Slice s of system d: Sa + oz_off + s * n * la (rows i, la BF16 each); Sb likewise after the
-// OZ_S Sa slices.
+// One warp per row i of the slice matrices (column i of X1; rows past n are zero): the scale
+// exponent, then for each 16-byte chunk of 8 K entries the OZ_S slices of a_i and a'_i, written
+// at their swizzled place in the tile.
 __global__ void __launch_bounds__(256) k_oz_slice(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                                                   const float2* __restrict__ X1g, __nv_bfloat16* __restrict__ S,
                                                   int* __restrict__ expg) {
@@ -57,56 +75,62 @@ __global__ void __launch_bounds__(256) k_oz_slice(const MmfDesc* __restrict__ de
     const int n = d.n, la = oz_la(n);
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n) return;
-    const float2* x = X1g + d.mat_off + (int64_t)i * d.ld;
+    if (i >= oz_nq(n) * 64) return;
+    const bool live = i < n;
+    const float2* x = X1g + d.mat_off + (int64_t)(live ? i : 0) * d.ld;
     float m = 0.f;
-    for (int k = lane; k < n; k += 32) m = fmaxf(m, fmaxf(fabsf(x[k].x), fabsf(x[k].y)));
+    if (live)
+        for (int k = lane; k < n; k += 32) m = fmaxf(m, fmaxf(fabsf(x[k].x), fabsf(x[k].y)));
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     int e = 0;
     if (m > 0.f) frexpf(m, &e);  // m = f 2^e, f in [0.5, 1): |x| 2^-e < 1
-    if (lane == 0) expg[d.vec_off + i] = e;
-    const int64_t plane = (int64_t)n * la;
-    __nv_bfloat16* Sa = S + d.oz_off + (int64_t)i * la;
-    __nv_bfloat16* Sb = Sa + OZ_S * plane;
-    for (int k = lane; k < la; k += 32) {
-        float tr = 0.f, ti = 0.f;  // the two entries of a_i that k and k + n address
-        if (k < n) {
-            tr = ldexpf(x[k].x, -e);  // a_i[k] = Re x_ki; a'_i[k + n] = -Re x_ki
-            ti = ldexpf(x[k].y, -e);  // a_i[k + n] = Im x_ki; a'_i[k] = Im x_ki
-        }
+    if (live && lane == 0) expg[d.vec_off + i] = e;
+    __nv_bfloat16* Sys = S + d.oz_off;
+    const int q = i >> 6, r = i & 63;
+    for (int jc = lane; jc < la / 8; jc += 32) {
+        const int k0 = jc * 8;
+        float ta[8], tb[8];  // scaled entries of a_i and a'_i
 #pragma unroll
-        for (int s = 0; s < OZ_S; ++s) {
-            tr *= 64.f;
-            ti *= 64.f;
-            const float vr = rintf(tr), vi = rintf(ti);
-            tr -= vr;
-            ti -= vi;
-            if (k < n) {
-                Sa[s * plane + k] = __float2bfloat16_rn(vr);
-                Sa[s * plane + n + k] = __float2bfloat16_rn(vi);
-                Sb[s * plane + k] = __float2bfloat16_rn(vi);
-                Sb[s * plane + n + k] = __float2bfloat16_rn(-vr);
-            } else if (k >= 2 * n) {  // row padding
-                Sa[s * plane + k] = __float2bfloat16_rn(0.f);
-                Sb[s * plane + k] = __float2bfloat16_rn(0.f);
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + u;
+            float va = 0.f, vb = 0.f;
+            if (live && k < 2 * n) {
+                if (k < n) {
+                    va = x[k].x;   // Re x_ki
+                    vb = x[k].y;   // Im x_ki
+                } else {
+                    va = x[k - n].y;   // Im x_ki
+                    vb = -x[k - n].x;  // -Re x_ki
+                }
             }
+            ta[u] = ldexpf(va, -e);
+            tb[u] = ldexpf(vb, -e);
+        }
+        const int t = k0 >> 6, j = (k0 & 63) >> 3;
+        const int64_t inner = (int64_t)(r >> 3) * 512 + (r & 7) * 64 + ((j ^ (r & 7)) << 3);  // BF16 units
+#pragma unroll
+        for (int sl = 0; sl < OZ_S; ++sl) {
+            uint32_t pa[4], pb[4];
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                float a0 = ta[u] * 64.f, a1 = ta[u + 1] * 64.f, b0 = tb[u] * 64.f, b1 = tb[u + 1] * 64.f;
+                const float ra0 = rintf(a0), ra1 = rintf(a1), rb0 = rintf(b0), rb1 = rintf(b1);
+                ta[u] = a0 - ra0;
+                ta[u + 1] = a1 - ra1;
+                tb[u] = b0 - rb0;
+                tb[u + 1] = b1 - rb1;
+                const __nv_bfloat162 ha = __floats2bfloat162_rn(ra0, ra1), hb = __floats2bfloat162_rn(rb0, rb1);
+                pa[u >> 1] = *reinterpret_cast<const uint32_t*>(&ha);
+                pb[u >> 1] = *reinterpret_cast<const uint32_t*>(&hb);
+            }
+            *reinterpret_cast<uint4*>(Sys + oz_tile_off(n, sl, t, q) + inner) = make_uint4(pa[0], pa[1], pa[2], pa[3]);
+            *reinterpret_cast<uint4*>(Sys + oz_tile_off(n, OZ_S + sl, t, q) + inner) =
+                make_uint4(pb[0], pb[1], pb[2], pb[3]);
         }
     }
 }
 
 // ------------------------------------------------------------------ products
-__device__ __forceinline__ void oz_load(uint32_t sbase, const __nv_bfloat16* g, int rows, int rows_valid,
-                                        int64_t k0, int la) {
-    // rows x 128 bytes, 16-byte chunks into the swizzled K-major layout
-    for (int c = threadIdx.x; c < rows * 8; c += OZ_THREADS) {
-        const int r = c >> 3, j = c & 7;
-        const uint32_t dst = sbase + (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4));
-        const bool ok = r < rows_valid;
-        const void* src = ok ? (const void*)(g + (int64_t)r * la + k0 + j * 8) : (const void*)g;
-        cp_async16(dst, src, ok ? 16 : 0);
-    }
-}
-
 // tile t of the lower triangle of an n x n matrix in OZ_TM x OZ_TN tiles: (I, J) with J <= 2 I + 1
 __device__ __forceinline__ bool oz_tile(int t, int n, int& I, int& J) {
     const int nI = (n + OZ_TM - 1) / OZ_TM, nJ = (n + OZ_TN - 1) / OZ_TN;
@@ -121,14 +145,65 @@ __device__ __forceinline__ bool oz_tile(int t, int n, int& I, int& J) {
     return false;
 }
 
-__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gram(const MmfDesc* __restrict__ descs,
-                                                           const int* __restrict__ idx,
-                                                           const __nv_bfloat16* __restrict__ S,
-                                                           const int* __restrict__ expg, double2* __restrict__ Gg,
-                                                           int* __restrict__ err) {
+#define OZ_TMEM_COLS 512u
+#define OZ_COL_LO 256   // int64 accumulators in TMEM: low words (Re 256..319, Im 320..383)
+#define OZ_COL_HI 384   //                               high words (Re 384..447, Im 448..511)
+
+__device__ __forceinline__ void tm_ld32(uint32_t ta, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+          "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+          "=r"(v[30]), "=r"(v[31])
+        : "r"(ta));
+}
+__device__ __forceinline__ void tm_st32(uint32_t ta, const uint32_t* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(ta),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),
+        "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),
+        "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+
+// bounded wait that also gives up when another role has aborted; sets the abort flag on time-out
+__device__ __forceinline__ bool oz_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < UM_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 255u) == 255u && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+__device__ __forceinline__ void oz_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(OZ_WARPS * 32, 1) k_oz_gram(const MmfDesc* __restrict__ descs,
+                                                              const int* __restrict__ idx,
+                                                              const __nv_bfloat16* __restrict__ S,
+                                                              const int* __restrict__ expg, double2* __restrict__ Gg,
+                                                              int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char oz_smem[];
-    __shared__ uint64_t bar[2];
+    __shared__ uint64_t full[OZ_STAGES], empty[OZ_STAGES], accfull[2], accempty[2];
     __shared__ uint32_t tmem_s;
+    __shared__ int abort_s;
     const MmfDesc d = descs[idx[blockIdx.y]];
     const int n = d.n, la = oz_la(n);
     int I, J;
@@ -137,16 +212,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gram(const MmfDesc* __rest
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* base = (unsigned char*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(base);
-    long long* acc = reinterpret_cast<long long*>(base + 2 * OZ_STAGE_BYTES);  // [2][OZ_TN][OZ_TM]
-    for (int e = threadIdx.x; e < 2 * OZ_TN * OZ_TM; e += OZ_THREADS) acc[e] = 0;
+    volatile int* abort_flag = &abort_s;
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        abort_s = 0;
+        for (int q = 0; q < OZ_STAGES; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&accfull[q], 1);
+            mbar_init(&accempty[q], 128);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
-                     "r"(128u)
+                     "r"(OZ_TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -154,158 +235,185 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gram(const MmfDesc* __rest
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_s;
-    const uint32_t idesc = umma_idesc_mn(1, OZ_TM, OZ_TN);
-    const int64_t plane = (int64_t)n * la;
+    const int nkc = (la + OZ_KCH - 1) / OZ_KCH;      // K chunks per pair
+    const int npairs = (OZ_L + 1) * (OZ_L + 2) / 2;  // pairs a + b <= OZ_L
+    const int nchunks = npairs * nkc;
     const __nv_bfloat16* Sys = S + d.oz_off;
-    uint32_t phase[2] = {0u, 0u};  // parity of the next phase to wait for, per stage barrier
-    bool ok = true;
+    const int nt = oz_nt(n);
 
-    for (int a = 0; a <= OZ_L && ok; ++a) {
-        for (int b = 0; a + b <= OZ_L && ok; ++b) {
-            const __nv_bfloat16* Ag = Sys + a * plane + (int64_t)i0 * la;
-            const __nv_bfloat16* Bg = Sys + b * plane + (int64_t)j0 * la;
-            const __nv_bfloat16* Bpg = Sys + (OZ_S + b) * plane + (int64_t)j0 * la;
-            const int sh = 6 * (OZ_L - a - b) - 6;
-            for (int kc0 = 0; kc0 < la && ok; kc0 += OZ_KCH) {
-                const int nk = (min(la, kc0 + OZ_KCH) - kc0) / OZ_KSTEP;
-                // stage 0 of the chunk (every earlier MMA has completed: both stages are free)
-                {
-                    const uint32_t st = sbase;
-                    oz_load(st, Ag, OZ_TM, n - i0, kc0, la);
-                    oz_load(st + 16384, Bg, OZ_TN, n - j0, kc0, la);
-                    oz_load(st + 24576, Bpg, OZ_TN, n - j0, kc0, la);
-                    asm volatile("cp.async.commit_group;" ::: "memory");
-                }
-                for (int kk = 0; kk < nk && ok; ++kk) {
-                    const int s = kk & 1;
-                    if (kk + 1 < nk) {
-                        const int s1 = s ^ 1;
-                        if (kk >= 1) {  // the MMAs of step kk-1 read stage s1: wait for their commit
-                            ok = __syncthreads_and(mbar_wait(&bar[s1], phase[s1]) ? 1 : 0) != 0;
-                            phase[s1] ^= 1u;
-                            if (!ok) break;
-                        }
-                        const uint32_t st = sbase + s1 * OZ_STAGE_BYTES;
-                        const int64_t k1 = kc0 + (int64_t)(kk + 1) * OZ_KSTEP;
-                        oz_load(st, Ag, OZ_TM, n - i0, k1, la);
-                        oz_load(st + 16384, Bg, OZ_TN, n - j0, k1, la);
-                        oz_load(st + 24576, Bpg, OZ_TN, n - j0, k1, la);
-                        asm volatile("cp.async.commit_group;" ::: "memory");
-                        asm volatile("cp.async.wait_group 1;" ::: "memory");
-                    } else {
-                        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (warp == 4) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int a = 0; a <= OZ_L; ++a)
+                for (int b = 0; a + b <= OZ_L; ++b)
+                    for (int t = 0; t < nt; ++t, ++it) {
+                        const int st = (int)(it % OZ_STAGES);
+                        const uint32_t use = it / OZ_STAGES;
+                        if (use > 0 && !oz_wait(&empty[st], (use - 1) & 1u, abort_flag)) goto producer_done;
+                        const uint32_t fb = smem_u32(&full[st]);
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                                     "r"((uint32_t)OZ_STAGE_BYTES)
+                                     : "memory");
+                        const uint32_t dst = sbase + (uint32_t)st * OZ_STAGE_BYTES;
+                        const __nv_bfloat16* srcA = Sys + oz_tile_off(n, a, t, 2 * I);
+                        const __nv_bfloat16* srcB = Sys + oz_tile_off(n, b, t, J);
+                        const __nv_bfloat16* srcBp = Sys + oz_tile_off(n, OZ_S + b, t, J);
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                dst),
+                            "l"(srcA), "r"(16384u), "r"(fb)
+                            : "memory");
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                dst + 16384u),
+                            "l"(srcB), "r"(8192u), "r"(fb)
+                            : "memory");
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                dst + 24576u),
+                            "l"(srcBp), "r"(8192u), "r"(fb)
+                            : "memory");
                     }
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    __syncthreads();
-                    if (threadIdx.x == 0) {
+        producer_done:;
+        }
+    } else if (warp == 5) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc_mn(1, OZ_TM, OZ_TN);
+            uint32_t it = 0;
+            int c = 0;
+            bool ok = true;
+            for (int p = 0; p < npairs && ok; ++p)
+                for (int kc = 0; kc < nkc && ok; ++kc, ++c) {
+                    const int buf = c & 1;
+                    const uint32_t v = (uint32_t)c >> 1;
+                    if (v > 0 && !oz_wait(&accempty[buf], (v - 1) & 1u, abort_flag)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t dre = tmem + (uint32_t)buf * 128u, dim = dre + OZ_TN;
+                    const int t0 = kc * (OZ_KCH / OZ_KSTEP), t1 = min(nt, t0 + OZ_KCH / OZ_KSTEP);
+                    for (int t = t0; t < t1; ++t, ++it) {
+                        const int st = (int)(it % OZ_STAGES);
+                        if (!oz_wait(&full[st], (it / OZ_STAGES) & 1u, abort_flag)) { ok = false; break; }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint32_t st = sbase + s * OZ_STAGE_BYTES;
-                        const uint64_t da = umma_desc(st), db = umma_desc(st + 16384), dbp = umma_desc(st + 24576);
+                        const uint32_t sa = sbase + (uint32_t)st * OZ_STAGE_BYTES;
+                        const uint64_t da = umma_desc(sa), db = umma_desc(sa + 16384u), dbp = umma_desc(sa + 24576u);
 #pragma unroll
                         for (int q = 0; q < OZ_KSTEP / 16; ++q) {  // 32 bytes of K per instruction
-                            const uint32_t accf = (kk > 0 || q > 0) ? 1u : 0u;
+                            const uint32_t accf = (t > t0 || q > 0) ? 1u : 0u;
                             const uint64_t adv = (uint64_t)((q * 32) >> 4);
                             asm volatile(
                                 "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dre),
                                 "l"(da + adv), "l"(db + adv), "r"(idesc), "r"(accf)
                                 : "memory");
                             asm volatile(
                                 "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + OZ_TN),
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dim),
                                 "l"(da + adv), "l"(dbp + adv), "r"(idesc), "r"(accf)
                                 : "memory");
                         }
-                        asm volatile(
-                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                smem_u32(&bar[s]))
-                            : "memory");
+                        oz_commit(&empty[st]);  // the stage is free once these MMAs have read it
                     }
+                    if (!ok) break;
+                    oz_commit(&accfull[buf]);  // the chunk's sums are complete
                 }
-                if (!ok) break;
-                // wait for the chunk's last commit, then drain TMEM into the int64 accumulators
-                {
-                    const int s = (nk - 1) & 1;
-                    ok = __syncthreads_and(mbar_wait(&bar[s], phase[s]) ? 1 : 0) != 0;
-                    phase[s] ^= 1u;
-                    // the other stage's commit (if any) precedes this one and is complete too
-                    if (ok && nk >= 2) {
-                        const int s1 = s ^ 1;
-                        ok = __syncthreads_and(mbar_wait(&bar[s1], phase[s1]) ? 1 : 0) != 0;
-                        phase[s1] ^= 1u;
-                    }
-                }
-                if (!ok) break;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int row = warp * 32 + lane;
-#pragma unroll 1
-                for (int c0 = 0; c0 < 2 * OZ_TN; c0 += 32) {
-                    uint32_t v[32];
-                    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-                        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-                          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-                          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-                          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-                          "=r"(v[31])
-                        : "r"(ta));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        }
+    } else {
+        // ---------------------------------------------------------------- drain (warps 0-3)
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        {
+            uint32_t z[32];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        const long long iv = __float2ll_rn(__uint_as_float(v[q]));  // an exact integer
-                        const long long term = sh >= 0 ? (iv << sh) : (iv >> (-sh));
-                        acc[(int64_t)(c0 + q) * OZ_TM + row] += term;
+            for (int q = 0; q < 32; ++q) z[q] = 0u;
+#pragma unroll 1
+            for (int col = OZ_COL_LO; col < OZ_COL_HI + 2 * OZ_TN; col += 32) tm_st32(trow + (uint32_t)col, z);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        int c = 0;
+        bool ok = true;
+        for (int a = 0; a <= OZ_L && ok; ++a)
+            for (int b = 0; a + b <= OZ_L && ok; ++b) {
+                const int sh = 6 * (OZ_L - a - b) - 6;
+                for (int kc = 0; kc < nkc; ++kc, ++c) {
+                    const int buf = c & 1;
+                    if (!oz_wait(&accfull[buf], ((uint32_t)c >> 1) & 1u, abort_flag)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+                    for (int g = 0; g < 2 * OZ_TN; g += 32) {
+                        uint32_t v[32], lo[32], hi[32];
+                        tm_ld32(trow + (uint32_t)(buf * 128 + g), v);
+                        tm_ld32(trow + (uint32_t)(OZ_COL_LO + g), lo);
+                        tm_ld32(trow + (uint32_t)(OZ_COL_HI + g), hi);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            const long long iv = __float2ll_rn(__uint_as_float(v[q]));  // an exact integer
+                            const long long term = sh >= 0 ? (iv << sh) : (iv >> (-sh));
+                            const long long acc64 = (long long)(((unsigned long long)hi[q] << 32) | lo[q]) + term;
+                            lo[q] = (uint32_t)(unsigned long long)acc64;
+                            hi[q] = (uint32_t)((unsigned long long)acc64 >> 32);
+                        }
+                        tm_st32(trow + (uint32_t)(OZ_COL_LO + g), lo);
+                        tm_st32(trow + (uint32_t)(OZ_COL_HI + g), hi);
+                    }
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&accempty[buf]))
+                                 : "memory");
+                }
+            }
+        (void)nchunks;
+        if (ok) {
+            const int i = i0 + warp * 32 + lane;
+            const int ei = i < n ? expg[d.vec_off + i] : 0;
+            double2* G = Gg + d.mat_off;
+#pragma unroll 1
+            for (int g = 0; g < OZ_TN; g += 32) {
+                uint32_t rlo[32], rhi[32], ilo[32], ihi[32];
+                tm_ld32(trow + (uint32_t)(OZ_COL_LO + g), rlo);
+                tm_ld32(trow + (uint32_t)(OZ_COL_HI + g), rhi);
+                tm_ld32(trow + (uint32_t)(OZ_COL_LO + OZ_TN + g), ilo);
+                tm_ld32(trow + (uint32_t)(OZ_COL_HI + OZ_TN + g), ihi);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int j = j0 + g + q;
+                    if (i < n && j <= i) {  // j <= i < n
+                        const int sc = ei + expg[d.vec_off + j] - 6 * (OZ_L + 2) + 6;
+                        const long long ar = (long long)(((unsigned long long)rhi[q] << 32) | rlo[q]);
+                        const long long ai = (long long)(((unsigned long long)ihi[q] << 32) | ilo[q]);
+                        const double gr = ldexp((double)ar, sc);
+                        const double gi = (i == j) ? 0.0 : ldexp((double)ai, sc);
+                        G[(int64_t)j * d.ld + i] = make_double2(gr, gi);
+                        if (i != j) G[(int64_t)i * d.ld + j] = make_double2(gr, -gi);
                     }
                 }
-                // TMEM is overwritten by the next chunk's first MMA only after every thread's loads
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncthreads();
             }
         }
-    }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (ok) {
-        __syncthreads();
-        const int row = warp * 32 + lane;
-        const int i = i0 + row;
-        if (i < n) {
-            const int ei = expg[d.vec_off + i];
-            double2* G = Gg + d.mat_off;
-            for (int c = 0; c < OZ_TN; ++c) {
-                const int j = j0 + c;
-                if (j >= n || j > i) continue;
-                const int sc = ei + expg[d.vec_off + j] - 6 * (OZ_L + 2) + 6;
-                const double gr = ldexp((double)acc[(int64_t)c * OZ_TM + row], sc);
-                const double gi = (i == j) ? 0.0 : ldexp((double)acc[(int64_t)(OZ_TN + c) * OZ_TM + row], sc);
-                G[(int64_t)j * d.ld + i] = make_double2(gr, gi);
-                if (i != j) G[(int64_t)i * d.ld + j] = make_double2(gr, -gi);
-            }
-        }
-    } else if (threadIdx.x == 0) {
-        atomicExch(err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    if (threadIdx.x == 0 && abort_s) atomicExch(err, 1);
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS)
+                     : "memory");
 }
 
-size_t mmf_ozaki_slice_elems(int n) { return (size_t)2 * OZ_S * n * oz_la(n); }
+size_t mmf_ozaki_slice_elems(int n) { return (size_t)2 * OZ_S * oz_nt(n) * oz_nq(n) * OZ_TILE_ELEMS; }
 
 cudaError_t mmf_launch_ozaki_gram(const MmfLaunch& L, const float2* X1, void* S, int* exps, double2* G, int* err) {
     if (L.count <= 0) return cudaSuccess;
-    k_oz_slice<<<dim3((L.nmax + 7) / 8, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X1, (__nv_bfloat16*)S, exps);
+    const int rows = oz_nq(L.nmax) * 64;
+    k_oz_slice<<<dim3((rows + 7) / 8, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X1, (__nv_bfloat16*)S, exps);
     const int nI = (L.nmax + OZ_TM - 1) / OZ_TM, nJ = (L.nmax + OZ_TN - 1) / OZ_TN;
     int tiles = 0;
     for (int I = 0; I < nI; ++I) tiles += std::min(2 * I + 2, nJ);
-    const size_t sm = 2 * (size_t)OZ_STAGE_BYTES + sizeof(long long) * 2 * OZ_TN * OZ_TM + 1024;
+    const size_t sm = (size_t)OZ_STAGES * OZ_STAGE_BYTES + 1024;
     cudaError_t e = cudaFuncSetAttribute(k_oz_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_oz_gram<<<dim3(tiles, L.count), OZ_THREADS, sm, L.stream>>>(L.desc, L.idx, (const __nv_bfloat16*)S, exps, G,
-                                                                   err);
+    k_oz_gram<<<dim3(tiles, L.count), OZ_WARPS * 32, sm, L.stream>>>(L.desc, L.idx, (const __nv_bfloat16*)S, exps, G,
+                                                                      err);
     return cudaGetLastError();
 }
 
