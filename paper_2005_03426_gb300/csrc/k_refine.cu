@@ -231,27 +231,36 @@ __global__ void __launch_bounds__(256) k_gram_x1(const MmfDesc* __restrict__ des
 // Re C = Xr^T Wr + Xi^T Wi and Im C = Xr^T Wi - Xi^T Wr as one real product over K = 2n:
 //   A row i = [Re x_i | Im x_i],  B row j = [Re w_j | Im w_j] (j < n), [Im w_j | -Re w_j] (n + j),
 //   C row i = [Re c_i. | Im c_i.]   (x_i, w_j columns of X and W),
-// in split TF32 (three products).  Placement, in buffers free at this point: B1 -> S, B2 -> G,
-// A1 -> Zp, A2 -> HX (after B, the only reader of HX, has been built), C -> T.  For X in FP64
-// (second step) A holds the split of fl32(X).
+// in split TF32 (three products) by k_tf3_gemm.  The operands are written pre-tiled (hi and lo
+// pieces, zero padding) into the system's operand area (ops: A, then B); C goes to T.  For X in
+// FP64 (second step) A holds the split of fl32(X).
+__device__ __forceinline__ float* tf3_area(void* pool, const MmfDesc& d) {
+    return reinterpret_cast<float*>(reinterpret_cast<uint16_t*>(pool) + d.oz_off);
+}
+__device__ __forceinline__ void tf3_put(float* P, int rows, int K, int r, int k, float v) {
+    const float v1 = tf32_round(v);
+    P[tf3_pos(rows, K, 0, r, k)] = v1;
+    P[tf3_pos(rows, K, 1, r, k)] = tf32_round(v - v1);
+}
+
+// B (2n x 2n) from W = HX - X diag(lam0) (FP64, rounded once to FP32)
 __global__ void __launch_bounds__(256) k_w_prep_B(const MmfDesc* __restrict__ descs,
                                                   const int* __restrict__ idx,
                                                   const double2* __restrict__ Xg,
                                                   const double2* __restrict__ HXg,
-                                                  const double* __restrict__ lam0g,
-                                                  double2* __restrict__ B1g, double2* __restrict__ B2g) {
+                                                  const double* __restrict__ lam0g, void* __restrict__ pool) {
     const MmfDesc d = descs[idx[blockIdx.y]];
-    const int n = d.n, la = xe_la(n);
+    const int n = d.n, K = 2 * n;
+    const int rp = tf3_nq(2 * n) * 128, kp = tf3_nt(K) * 32;
     const double2* X = Xg + d.mat_off;
     const double2* HX = HXg + d.mat_off;
     const double* lam0 = lam0g + d.vec_off;
-    float* B1 = reinterpret_cast<float*>(B1g + d.mat_off);
-    float* B2 = reinterpret_cast<float*>(B2g + d.mat_off);
-    const int64_t tot = (int64_t)2 * n * la;
+    float* B = tf3_area(pool, d) + 2 * tf3_piece(n, K);
+    const int64_t tot = (int64_t)rp * kp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e / la), k = (int)(e - (int64_t)j * la);
+        const int j = (int)(e / kp), k = (int)(e - (int64_t)j * kp);
         float v = 0.f;
-        if (k < 2 * n) {
+        if (j < 2 * n && k < K) {
             const int jj = j < n ? j : j - n, kk = k < n ? k : k - n;
             const int64_t o = (int64_t)jj * d.ld + kk;
             const double2 w = HX[o] - lam0[jj] * X[o];
@@ -260,51 +269,46 @@ __global__ void __launch_bounds__(256) k_w_prep_B(const MmfDesc* __restrict__ de
             else r = (k < n) ? w.y : -w.x;
             v = (float)r;
         }
-        const float v1 = tf32_round(v);
-        B1[e] = v1;
-        B2[e] = tf32_round(v - v1);
+        tf3_put(B, 2 * n, K, j, k, v);
     }
 }
 
+// A (n x 2n): row i = [Re x_i | Im x_i] of X1 = fl32(X)
 __global__ void __launch_bounds__(256) k_w_prep_A(const MmfDesc* __restrict__ descs,
                                                   const int* __restrict__ idx,
-                                                  const float2* __restrict__ X1g,
-                                                  float2* __restrict__ A1g, double2* __restrict__ A2g) {
+                                                  const float2* __restrict__ X1g, void* __restrict__ pool) {
     const MmfDesc d = descs[idx[blockIdx.y]];
-    const int n = d.n, la = xe_la(n);
+    const int n = d.n, K = 2 * n;
+    const int rp = tf3_nq(n) * 128, kp = tf3_nt(K) * 32;
     const float2* X = X1g + d.mat_off;
-    float* A1 = reinterpret_cast<float*>(A1g + d.mat_off);
-    float* A2 = reinterpret_cast<float*>(A2g + d.mat_off);
-    const int64_t tot = (int64_t)n * la;
+    float* A = tf3_area(pool, d);
+    const int64_t tot = (int64_t)rp * kp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / la), k = (int)(e - (int64_t)i * la);
+        const int i = (int)(e / kp), k = (int)(e - (int64_t)i * kp);
         float v = 0.f;
-        if (k < 2 * n) {
+        if (i < n && k < K) {
             const float2 x = X[(int64_t)i * d.ld + (k < n ? k : k - n)];
             v = k < n ? x.x : x.y;
         }
-        const float v1 = tf32_round(v);
-        A1[e] = v1;
-        A2[e] = tf32_round(v - v1);
+        tf3_put(A, n, K, i, k, v);
     }
 }
 
 // B rows for C' = X1^H Dx: [Re dx_j | Im dx_j] (j < n), [Im dx_j | -Re dx_j] (n + j), with
-// Dx = X - fl32(X) (exact in FP64), split in TF32 pieces
+// Dx = X - fl32(X) (exact in FP64)
 __global__ void __launch_bounds__(256) k_d_prep_B(const MmfDesc* __restrict__ descs,
                                                   const int* __restrict__ idx,
-                                                  const double2* __restrict__ Xg,
-                                                  double2* __restrict__ B1g, double2* __restrict__ B2g) {
+                                                  const double2* __restrict__ Xg, void* __restrict__ pool) {
     const MmfDesc d = descs[idx[blockIdx.y]];
-    const int n = d.n, la = xe_la(n);
+    const int n = d.n, K = 2 * n;
+    const int rp = tf3_nq(2 * n) * 128, kp = tf3_nt(K) * 32;
     const double2* X = Xg + d.mat_off;
-    float* B1 = reinterpret_cast<float*>(B1g + d.mat_off);
-    float* B2 = reinterpret_cast<float*>(B2g + d.mat_off);
-    const int64_t tot = (int64_t)2 * n * la;
+    float* B = tf3_area(pool, d) + 2 * tf3_piece(n, K);
+    const int64_t tot = (int64_t)rp * kp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e / la), k = (int)(e - (int64_t)j * la);
+        const int j = (int)(e / kp), k = (int)(e - (int64_t)j * kp);
         float v = 0.f;
-        if (k < 2 * n) {
+        if (j < 2 * n && k < K) {
             const int jj = j < n ? j : j - n, kk = k < n ? k : k - n;
             const double2 x = X[(int64_t)jj * d.ld + kk];
             const double2 dx = make_double2(x.x - (double)(float)x.x, x.y - (double)(float)x.y);
@@ -313,32 +317,23 @@ __global__ void __launch_bounds__(256) k_d_prep_B(const MmfDesc* __restrict__ de
             else r = (k < n) ? dx.y : -dx.x;
             v = (float)r;
         }
-        const float v1 = tf32_round(v);
-        B1[e] = v1;
-        B2[e] = tf32_round(v - v1);
+        tf3_put(B, 2 * n, K, j, k, v);
     }
 }
 
-// one job per system: A = [A1, A1, A2] (Zp, HX), B = [B1, B2, B1] (S, G), C at float offset coff
-// of the system's T slot
-__global__ void k_w_jobs(const MmfDesc* __restrict__ descs, const int* __restrict__ idx, int count,
-                         float2* Zp, double2* G, double2* S, double2* HX, double2* T, int second_c,
-                         UmmaJob* jobs) {
+// one job per system: A and B from the operand area, C at float offset (second ? 2 n^2 : 0) of
+// the system's T slot
+__global__ void k_w_jobs(const MmfDesc* __restrict__ descs, const int* __restrict__ idx, int count, void* pool,
+                         double2* T, int second_c, Tf3Job* jobs) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const MmfDesc d = descs[idx[i]];
-    const int n = d.n, la = xe_la(n);
-    const float* A1 = reinterpret_cast<const float*>(Zp + d.mat_off);
-    const float* A2 = reinterpret_cast<const float*>(HX + d.mat_off);
-    const float* B1 = reinterpret_cast<const float*>(S + d.mat_off);
-    const float* B2 = reinterpret_cast<const float*>(G + d.mat_off);
-    UmmaJob j;
-    j.A[0] = A1; j.B[0] = B1;
-    j.A[1] = A1; j.B[1] = B2;
-    j.A[2] = A2; j.B[2] = B1;
+    const int n = d.n;
+    Tf3Job j;
+    j.A = tf3_area(pool, d);
+    j.B = j.A + 2 * tf3_piece(n, 2 * n);
     j.C = reinterpret_cast<float*>(T + d.mat_off) + (second_c ? (int64_t)2 * n * n : 0);
-    j.M = n; j.N = 2 * n; j.K = 2 * n;
-    j.lda = la; j.ldb = la; j.ldc = 2 * n;
+    j.M = n; j.N = 2 * n; j.K = 2 * n; j.ldc = 2 * n;
     jobs[i] = j;
 }
 
@@ -462,24 +457,22 @@ __global__ void __launch_bounds__(256) k_oa_etilde(const MmfDesc* __restrict__ d
 // x y ~ x1 y1 + x1 y2 + x2 y1, about FP32 accuracy) for the entries of Et outside the band
 // |i - j| <= RF_W, which are small (|Et_ij| ~ eps32 |H_F| / gap_ij), so that the FP32 error
 // stays far below the target.  The band, where Et reaches ~0.05 for close pairs, is applied in
-// double-FP32 on the SIMT units (k_et_band, k_xe_apply).  Operands are
-// K-major rows of la = round_up(2n, 4) floats, placed in buffers free at this point:
-// B1 -> S, B2 -> HX (2n rows), A1 -> Zp (n rows), A2 and then C (n x 2n) -> the Et buffer after
-// B has been built from it.
+// double-FP32 on the SIMT units (k_et_band, k_xe_apply).  The operands are written pre-tiled
+// into the system's operand area (as for C = X^H W); C (n x 2n) goes to the Et buffer after B
+// has been built from it.
 __global__ void __launch_bounds__(256) k_xe_prep_B(const MmfDesc* __restrict__ descs,
                                                    const int* __restrict__ idx,
-                                                   const double2* __restrict__ Etg,
-                                                   double2* __restrict__ B1g, double2* __restrict__ B2g) {
+                                                   const double2* __restrict__ Etg, void* __restrict__ pool) {
     const MmfDesc d = descs[idx[blockIdx.y]];
-    const int n = d.n, la = xe_la(n);
+    const int n = d.n, K = 2 * n;
+    const int rp = tf3_nq(2 * n) * 128, kp = tf3_nt(K) * 32;
     const double2* Et = Etg + d.mat_off;
-    float* B1 = reinterpret_cast<float*>(B1g + d.mat_off);
-    float* B2 = reinterpret_cast<float*>(B2g + d.mat_off);
-    const int64_t tot = (int64_t)2 * n * la;
+    float* B = tf3_area(pool, d) + 2 * tf3_piece(n, K);
+    const int64_t tot = (int64_t)rp * kp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e / la), k = (int)(e - (int64_t)j * la);
+        const int j = (int)(e / kp), k = (int)(e - (int64_t)j * kp);
         float v = 0.f;
-        if (k < 2 * n) {
+        if (j < 2 * n && k < K) {
             const int jj = j < n ? j : j - n, kk = k < n ? k : k - n;
             if (abs(jj - kk) > RF_W) {  // the band is applied in double-FP32 by k_xe_apply
                 const double2 x = Et[(int64_t)jj * d.ld + kk];
@@ -489,65 +482,52 @@ __global__ void __launch_bounds__(256) k_xe_prep_B(const MmfDesc* __restrict__ d
                 v = (float)w;
             }
         }
-        const float v1 = tf32_round(v);
-        B1[e] = v1;
-        B2[e] = tf32_round(v - v1);
+        tf3_put(B, 2 * n, K, j, k, v);
     }
 }
 
+// A (n x 2n): row r = [Re X(r, :) | Im X(r, :)] of X1, transposed through shared memory in 32 x 32
+// blocks; the grid covers the padded rows, and the blocks of the last column block also zero
+// the K padding.
 __global__ void __launch_bounds__(256) k_xe_prep_A(const MmfDesc* __restrict__ descs,
                                                    const int* __restrict__ idx,
-                                                   const float2* __restrict__ X1g,
-                                                   float2* __restrict__ A1g, double2* __restrict__ A2g) {
+                                                   const float2* __restrict__ X1g, void* __restrict__ pool) {
     __shared__ float2 t[32][33];
     const MmfDesc d = descs[idx[blockIdx.z]];
-    const int n = d.n, la = xe_la(n);
+    const int n = d.n, K = 2 * n;
+    const int rp = tf3_nq(n) * 128, kp = tf3_nt(K) * 32;
     const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
-    if (r0 >= n || c0 >= n) return;
+    if (r0 >= rp || c0 >= n) return;
     const float2* X = X1g + d.mat_off;
-    float* A1 = reinterpret_cast<float*>(A1g + d.mat_off);
-    float* A2 = reinterpret_cast<float*>(A2g + d.mat_off);
+    float* A = tf3_area(pool, d);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
     for (int q = ty; q < 32; q += 8) {  // X(r0 + tx, c0 + q), rows fastest
         const int r = r0 + tx, c = c0 + q;
         t[q][tx] = (r < n && c < n) ? X[(int64_t)c * d.ld + r] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    for (int q = ty; q < 32; q += 8) {  // A[r0 + q][c0 + tx] (re) and A[r0 + q][n + c0 + tx] (im)
+    for (int q = ty; q < 32; q += 8) {  // A(r0 + q, c0 + tx) = Re, A(r0 + q, n + c0 + tx) = Im
         const int r = r0 + q, c = c0 + tx;
-        if (r < n && c < n) {
+        if (c < n) {
             const float2 x = t[tx][q];
-            const float re = x.x, im = x.y;
-            const float re1 = tf32_round(re), im1 = tf32_round(im);
-            A1[(int64_t)r * la + c] = re1;
-            A2[(int64_t)r * la + c] = tf32_round(re - re1);
-            A1[(int64_t)r * la + n + c] = im1;
-            A2[(int64_t)r * la + n + c] = tf32_round(im - im1);
+            tf3_put(A, n, K, r, c, x.x);
+            tf3_put(A, n, K, r, n + c, x.y);
         }
-        if (r < n && c0 + 32 >= n && tx < la - 2 * n) {  // zero the row padding
-            A1[(int64_t)r * la + 2 * n + tx] = 0.f;
-            A2[(int64_t)r * la + 2 * n + tx] = 0.f;
-        }
+        if (c0 + 32 >= n && 2 * n + tx < kp) tf3_put(A, n, K, r, 2 * n + tx, 0.f);  // K padding
     }
 }
 
-__global__ void k_xe_jobs(const MmfDesc* __restrict__ descs, const int* __restrict__ idx, int count,
-                          float2* Zp, double2* R, double2* S, double2* HX, UmmaJob* jobs) {
+__global__ void k_xe_jobs(const MmfDesc* __restrict__ descs, const int* __restrict__ idx, int count, void* pool,
+                          double2* R, Tf3Job* jobs) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const MmfDesc d = descs[idx[i]];
     const int n = d.n, la = xe_la(n);
-    const float* A1 = reinterpret_cast<const float*>(Zp + d.mat_off);
-    const float* A2 = reinterpret_cast<const float*>(R + d.mat_off);
-    const float* B1 = reinterpret_cast<const float*>(S + d.mat_off);
-    const float* B2 = reinterpret_cast<const float*>(HX + d.mat_off);
-    UmmaJob j;
-    j.A[0] = A1; j.B[0] = B1;
-    j.A[1] = A1; j.B[1] = B2;
-    j.A[2] = A2; j.B[2] = B1;
+    Tf3Job j;
+    j.A = tf3_area(pool, d);
+    j.B = j.A + 2 * tf3_piece(n, 2 * n);
     j.C = reinterpret_cast<float*>(R + d.mat_off) + (int64_t)n * la;
-    j.M = n; j.N = 2 * n; j.K = 2 * n;
-    j.lda = la; j.ldb = la; j.ldc = 2 * n;
+    j.M = n; j.N = 2 * n; j.K = 2 * n; j.ldc = 2 * n;
     jobs[i] = j;
 }
 
@@ -1032,22 +1012,20 @@ static void apply_hf(const MmfLaunch& L, const float4* cs, const double2* X, flo
 }
 
 cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const float4* cs, const double2* X, const double* lam0,
-                                  double2* HX, double2* G, double2* S, float2* Zp, double2* T, float2* X1,
-                                  void* jobs, int* status, int second) {
+                                  double2* HX, double2* T, float2* X1, void* ops, void* jobs, int* status,
+                                  int second) {
     if (L.count <= 0) return cudaSuccess;
     // the first step's X holds FP32 eigenvectors (no remainder); the remainder of a second step's
     // X goes to T, which is free until C is written
     apply_hf(L, cs, X, X1, second ? reinterpret_cast<float2*>(T) : nullptr, HX);
-    k_w_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, HX, lam0, S, G);
-    k_w_prep_A<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X1, Zp, HX);
-    k_w_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, Zp, G, S, HX, T, 0,
-                                                         (UmmaJob*)jobs);
-    cudaError_t e = mmf_launch_umma(jobs, L.count, 3, L.nmax, 2 * L.nmax, 0, status, L.stream);
+    k_w_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, HX, lam0, ops);
+    k_w_prep_A<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X1, ops);
+    k_w_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, ops, T, 0, (Tf3Job*)jobs);
+    cudaError_t e = mmf_launch_tf3(jobs, L.count, L.nmax, 2 * L.nmax, status, L.stream);
     if (e != cudaSuccess || !second) return e;
-    k_d_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, S, G);
-    k_w_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, Zp, G, S, HX, T, 1,
-                                                         (UmmaJob*)jobs);
-    return mmf_launch_umma(jobs, L.count, 3, L.nmax, 2 * L.nmax, 0, status, L.stream);
+    k_d_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, ops);
+    k_w_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, ops, T, 1, (Tf3Job*)jobs);
+    return mmf_launch_tf3(jobs, L.count, L.nmax, 2 * L.nmax, status, L.stream);
 }
 
 cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const float2* X1, double2* G, const double2* T, int second) {
@@ -1067,20 +1045,19 @@ cudaError_t mmf_launch_refine_gram_fix(const MmfLaunch& L, double2* G, const dou
 }
 
 cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, double2* X, const float2* X1,
-                                     const double* lam0, double2* G, double2* S, double2* HX, const double2* T,
-                                     double* lam, int* status, int* cid, int64_t mat_elems, float2* Zp, void* jobs,
+                                     const double* lam0, double2* G, double2* HX, const double2* T, double* lam,
+                                     int* status, int* cid, int64_t mat_elems, void* ops, void* jobs,
                                      double2* Eb) {
     if (L.count <= 0) return cudaSuccess;
     k_oa_lambda<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, T, lam0, lam, cid);
     k_oa_etilde<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, T, lam0, lam, cid);
     // X <- X + X Et: band in double-FP32, the rest on the tensor cores (split TF32)
     k_et_band<<<dim3(64, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, Eb);
-    k_xe_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, S, HX);
-    k_xe_prep_A<<<dim3((L.nmax + 31) / 32, (L.nmax + 31) / 32, L.count), 256, 0, L.stream>>>(
-        L.desc, L.idx, X1, Zp, G);
-    k_xe_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, Zp, G, S, HX,
-                                                          (UmmaJob*)jobs);
-    cudaError_t e = mmf_launch_umma(jobs, L.count, 3, L.nmax, 2 * L.nmax, 0, status, L.stream);
+    k_xe_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, ops);
+    k_xe_prep_A<<<dim3(tf3_nq(L.nmax) * 4, (L.nmax + 31) / 32, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X1,
+                                                                                             ops);
+    k_xe_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, ops, G, (Tf3Job*)jobs);
+    cudaError_t e = mmf_launch_tf3(jobs, L.count, L.nmax, 2 * L.nmax, status, L.stream);
     if (e != cudaSuccess) return e;
     k_xe_apply<<<dim3((L.nmax + 255) / 256, L.nmax, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, X1, G, Eb, HX);
     e = cudaMemcpyAsync(X, HX, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);

@@ -177,6 +177,169 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma_gemm(const UmmaJob* __re
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
 }
 
+// ------------------------------------------------------------------ split-TF32, warp-specialized
+// C = A1 B1^T + A1 B2^T + A2 B1^T for pre-tiled operands (layout in mmf_internal.h).  One CTA per
+// 128 x 128 tile of C, six warps: warp 4 (one lane) streams the four 16-KB operand tiles of each
+// K step into a ring of TF_STAGES stages with cp.async.bulk (completion counted on full[stage]);
+// warp 5 (one lane) issues the 12 tcgen05.mma of the step and frees the stage with
+// tcgen05.commit on empty[stage]; warps 0-3 wait for the final commit and write C from TMEM.
+// Every wait is bounded and ends on a shared abort flag.
+#define TF_STAGES 3
+#define TF_TILE_BYTES 16384u
+#define TF_STAGE_BYTES (4u * TF_TILE_BYTES)
+
+__device__ __forceinline__ bool tf_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < UM_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 255u) == 255u && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+__global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ jobs, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char tf_smem[];
+    __shared__ uint64_t full[TF_STAGES], empty[TF_STAGES], accfull;
+    __shared__ uint32_t tmem_s;
+    __shared__ int abort_s;
+    const Tf3Job jb = jobs[blockIdx.z];
+    const int I = blockIdx.x, J = blockIdx.y;
+    if (I * 128 >= jb.M || J * 128 >= jb.N) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* base = (unsigned char*)(((uintptr_t)tf_smem + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(base);
+    volatile int* abort_flag = &abort_s;
+    if (threadIdx.x == 0) {
+        abort_s = 0;
+        for (int q = 0; q < TF_STAGES; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 1);
+        }
+        mbar_init(&accfull, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
+                     "r"(128u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_s;
+    const int nt = tf3_nt(jb.K), nqa = tf3_nq(jb.M), nqb = tf3_nq(jb.N);
+    const int64_t pa = tf3_piece(jb.M, jb.K), pb = tf3_piece(jb.N, jb.K);
+
+    if (warp == 4) {
+        if (lane == 0) {
+            for (int t = 0; t < nt; ++t) {
+                const int st = t % TF_STAGES;
+                const uint32_t use = (uint32_t)(t / TF_STAGES);
+                if (use > 0 && !tf_wait(&empty[st], (use - 1) & 1u, abort_flag)) break;
+                const uint32_t fb = smem_u32(&full[st]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(TF_STAGE_BYTES)
+                             : "memory");
+                const uint32_t dst = sbase + (uint32_t)st * TF_STAGE_BYTES;
+                const float* src[4] = {jb.A + ((int64_t)t * nqa + I) * 4096, jb.A + pa + ((int64_t)t * nqa + I) * 4096,
+                                       jb.B + ((int64_t)t * nqb + J) * 4096, jb.B + pb + ((int64_t)t * nqb + J) * 4096};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            dst + (uint32_t)q * TF_TILE_BYTES),
+                        "l"(src[q]), "r"(TF_TILE_BYTES), "r"(fb)
+                        : "memory");
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc(2);  // TF32, M = N = 128
+            bool ok = true;
+            for (int t = 0; t < nt; ++t) {
+                const int st = t % TF_STAGES;
+                if (!tf_wait(&full[st], (uint32_t)(t / TF_STAGES) & 1u, abort_flag)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = sbase + (uint32_t)st * TF_STAGE_BYTES;
+                const uint64_t a1 = umma_desc(sa), a2 = umma_desc(sa + TF_TILE_BYTES);
+                const uint64_t b1 = umma_desc(sa + 2 * TF_TILE_BYTES), b2 = umma_desc(sa + 3 * TF_TILE_BYTES);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {  // 32 bytes (8 TF32) of K per instruction
+                    const uint64_t adv = (uint64_t)((q * 32) >> 4);
+                    const uint32_t acc0 = (t > 0 || q > 0) ? 1u : 0u;
+                    const uint64_t pa_[3] = {a1, a1, a2}, pb_[3] = {b1, b2, b1};
+#pragma unroll
+                    for (int pp = 0; pp < 3; ++pp) {
+                        const uint32_t accf = (pp > 0) ? 1u : acc0;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                            "l"(pa_[pp] + adv), "l"(pb_[pp] + adv), "r"(idesc), "r"(accf)
+                            : "memory");
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&empty[st]))
+                             : "memory");
+            }
+            if (ok)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&accfull))
+                             : "memory");
+        }
+    } else {
+        // epilogue: warp w holds rows 32w .. 32w+31 of the tile (its TMEM lanes)
+        if (tf_wait(&accfull, 0u, abort_flag)) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = I * 128 + warp * 32 + lane;
+            for (int c0 = 0; c0 < 128; c0 += 32) {
+                uint32_t v[32];
+                const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                      "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < jb.M) {
+                    float* out = jb.C + (int64_t)row * jb.ldc + J * 128 + c0;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        if (J * 128 + c0 + q < jb.N) out[q] = __uint_as_float(v[q]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && abort_s) atomicExch(err, 1);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+}
+
+cudaError_t mmf_launch_tf3(const void* jobs, int count, int Mmax, int Nmax, int* err, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    const size_t sm = (size_t)TF_STAGES * TF_STAGE_BYTES + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_tf3_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((Mmax + 127) / 128, (Nmax + 127) / 128, count);
+    k_tf3_gemm<<<grid, 192, sm, stream>>>((const Tf3Job*)jobs, err);
+    return cudaGetLastError();
+}
+
 // jobs: device array of `count` UmmaJob; grid covers the largest M and N among them
 cudaError_t mmf_launch_umma(const void* jobs, int count, int P, int Mmax, int Nmax, int kind, int* err,
                             cudaStream_t stream) {

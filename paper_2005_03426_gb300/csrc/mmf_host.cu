@@ -411,7 +411,10 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         b->n_vec += n;
         d.sq_off = b->n_sq;
         d.oz_off = b->n_oz;
-        if (precision == MMF_MIXED && ctx->gram_kernel == 0) b->n_oz += (int64_t)mmf_ozaki_slice_elems((int)n);
+        if (precision == MMF_MIXED) {  // Gram slices (BF16) and split-TF32 operands share the area
+            const int64_t oz = ctx->gram_kernel == 0 ? (int64_t)mmf_ozaki_slice_elems((int)n) : 0;
+            b->n_oz += std::max<int64_t>(oz, 2 * mmf_tf3_floats((int)n));
+        }
         d.pan_off = b->n_pan;
         if (!d.small) {
             b->n_sq += n * n;
@@ -479,7 +482,7 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         o_HX = p.take(sizeof(double2) * b->n_mat);
         o_E2 = p.take(sizeof(double) * b->n_vec);
         o_cid = p.take(sizeof(int) * b->n_vec);
-        o_jobs = p.take(sizeof(UmmaJob) * count);
+        o_jobs = p.take(std::max(sizeof(UmmaJob), sizeof(Tf3Job)) * count);
     }
     b->bytes = p.off;
     if (ctx->used + b->bytes > ctx->budget) {
@@ -738,16 +741,15 @@ static int stage_eig(mmf_batch* b) {
     mark(b, ST_REFINE);
     if (fp32) {
         MmfLaunch La = launch_of(b, b->all, b->d_all, b->nmax_all);
-        float2* Zp = (float2*)b->d_Zp;
         LAUNCH(mmf_launch_refine_split_coef(b->d_coef, b->d_coefs, b->n_coef, b->stream), 1);
-        LAUNCH(mmf_launch_refine_pre(La, b->d_coefs, b->d_Zf, b->d_E, b->d_HX, b->d_R, b->d_S, Zp, b->d_T, b->d_X1,
-                                     b->d_jobs, b->d_status, 0),
+        LAUNCH(mmf_launch_refine_pre(La, b->d_coefs, b->d_Zf, b->d_E, b->d_HX, b->d_T, b->d_X1, b->d_oz, b->d_jobs,
+                                     b->d_status, 0),
                6);
         mark(b, ST_GRAM);
         LAUNCH(refine_gram(b, La, 0), 2);
         mark(b, ST_REFINE2);
-        LAUNCH(mmf_launch_refine_update(La, b->d_coef, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_T, b->d_E2,
-                                        b->d_status, b->d_cid, b->n_mat, Zp, b->d_jobs, b->d_Eb),
+        LAUNCH(mmf_launch_refine_update(La, b->d_coef, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_HX, b->d_T, b->d_E2,
+                                        b->d_status, b->d_cid, b->n_mat, b->d_oz, b->d_jobs, b->d_Eb),
                9);
         if (!b->rband.empty()) {
             MmfLaunch Lb = launch_of(b, b->rband, b->d_rband, b->nmax_rband);
@@ -759,12 +761,12 @@ static int stage_eig(mmf_batch* b) {
             // second full step from lam0 = the first step's eigenvalues (E is rewritten at the end)
             MmfLaunch Lf = launch_of(b, b->rfull, b->d_rfull, b->nmax_rfull);
             CU(cudaMemcpyAsync(b->d_E, b->d_E2, sizeof(double) * b->n_vec, cudaMemcpyDeviceToDevice, b->stream));
-            LAUNCH(mmf_launch_refine_pre(Lf, b->d_coefs, b->d_Zf, b->d_E, b->d_HX, b->d_R, b->d_S, Zp, b->d_T,
-                                         b->d_X1, b->d_jobs, b->d_status, 1),
+            LAUNCH(mmf_launch_refine_pre(Lf, b->d_coefs, b->d_Zf, b->d_E, b->d_HX, b->d_T, b->d_X1, b->d_oz,
+                                         b->d_jobs, b->d_status, 1),
                    9);
             LAUNCH(refine_gram(b, Lf, 1), 3);
-            LAUNCH(mmf_launch_refine_update(Lf, b->d_coef, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_S, b->d_HX, b->d_T,
-                                            b->d_E2, b->d_status, b->d_cid, b->n_mat, Zp, b->d_jobs, b->d_Eb),
+            LAUNCH(mmf_launch_refine_update(Lf, b->d_coef, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_HX, b->d_T,
+                                            b->d_E2, b->d_status, b->d_cid, b->n_mat, b->d_oz, b->d_jobs, b->d_Eb),
                    9);
         }
         LAUNCH(mmf_launch_refine_finish(La, b->d_Zf, b->d_E, b->d_E2, b->d_S, b->n_mat), 1);

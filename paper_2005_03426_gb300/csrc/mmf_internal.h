@@ -210,13 +210,13 @@ cudaError_t mmf_launch_micromotion(const MmfLaunch& L, int D, const double2* Z, 
                                    int nt, int64_t* reps, double2* UF);
 cudaError_t mmf_launch_refine_split_coef(const double2* coef, float4* cs, int64_t count, cudaStream_t st);
 cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const float4* cs, const double2* X, const double* lam0,
-                                  double2* HX, double2* G, double2* S, float2* Zp, double2* T, float2* X1,
-                                  void* jobs, int* status, int second);
+                                  double2* HX, double2* T, float2* X1, void* ops, void* jobs, int* status,
+                                  int second);
 cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const float2* X1, double2* G, const double2* T, int second);
 cudaError_t mmf_launch_refine_gram_fix(const MmfLaunch& L, double2* G, const double2* T);
 cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, double2* X, const float2* X1,
-                                     const double* lam0, double2* G, double2* S, double2* HX, const double2* T,
-                                     double* lam, int* status, int* cid, int64_t mat_elems, float2* Zp, void* jobs,
+                                     const double* lam0, double2* G, double2* HX, const double2* T, double* lam,
+                                     int* status, int* cid, int64_t mat_elems, void* ops, void* jobs,
                                      double2* Eb);
 cudaError_t mmf_launch_refine_band(const MmfLaunch& L, const double2* coef, const float4* cs, double2* X,
                                    double2* G, double2* S, double2* HX, double2* T, float2* X1, double* lam,
@@ -242,6 +242,34 @@ struct UmmaJob {
 };
 cudaError_t mmf_launch_umma(const void* jobs, int count, int P, int Mmax, int Nmax, int kind, int* err,
                             cudaStream_t stream);
+
+// Split-TF32 products on the tensor cores with pre-tiled operands (k_umma.cu, k_tf3_gemm):
+//   C(m, n) = A1 B1^T + A1 B2^T + A2 B1^T   (A = A1 + A2, B = B1 + B2 in TF32 pieces)
+// Each operand (rows x K) is stored as two pieces (A1 then A2), each in 128-row x 32-K tiles of
+// 16 KB in the tensor cores' shared-memory layout (128-byte swizzle, K-major); tile (t, q) of a
+// piece sits at ((t * nq + q) * 4096) floats, nq = ceil(rows / 128).  Padding rows and K columns
+// hold zeros.
+__host__ __device__ __forceinline__ int tf3_nq(int rows) { return (rows + 127) / 128; }
+__host__ __device__ __forceinline__ int tf3_nt(int K) { return (K + 31) / 32; }
+__host__ __device__ __forceinline__ int64_t tf3_piece(int rows, int K) {
+    return (int64_t)tf3_nt(K) * tf3_nq(rows) * 4096;
+}
+__host__ __device__ __forceinline__ int64_t tf3_pos(int rows, int K, int piece, int r, int k) {
+    const int t = k >> 5, kk = k & 31, q = r >> 7, rr = r & 127;
+    return (((int64_t)piece * tf3_nt(K) + t) * tf3_nq(rows) + q) * 4096 + (rr >> 3) * 256 + (rr & 7) * 32 +
+           (((kk >> 2) ^ (rr & 7)) << 2) + (kk & 3);
+}
+struct Tf3Job {
+    const float* A;   // piece 1 of A (piece 2 follows after tf3_piece(M, K) floats)
+    const float* B;   // piece 1 of B
+    float* C;         // M x N, row stride ldc
+    int M, N, K, ldc;
+};
+cudaError_t mmf_launch_tf3(const void* jobs, int count, int Mmax, int Nmax, int* err, cudaStream_t stream);
+// floats of the refinement's split-TF32 operands for one system (A: n x 2n, B: 2n x 2n)
+__host__ __device__ __forceinline__ int64_t mmf_tf3_floats(int n) {
+    return 2 * tf3_piece(n, 2 * n) + 2 * tf3_piece(2 * n, 2 * n);
+}
 int mmf_umma_selftest_impl(int M, int N, int K, int kind, int P, double* max_abs, double* max_ref);
 #define MMF_MIN_LD 36   // n x ld matrix slots also hold the n x 33 band of the refinement
 
