@@ -551,42 +551,62 @@ __global__ void __launch_bounds__(256) k_et_band(const MmfDesc* __restrict__ des
 // outside the band), the band in double-FP32 from X1 = fl32(X) (exact in the first step; in a
 // second full step the remainder times Et is below 2^-24 |Et| and dropped) and Et split in two
 // FP32 pieces.  Xn goes to a separate buffer (the band reads neighbouring columns of X).
+// One CTA per XT_R x XT_C tile of Xn: the XT_C + 2W neighbouring columns of X1, the band of Et
+// and the tile of C are staged in shared memory; thread (row, group of XT_CPT columns).
+#define XT_R 32
+#define XT_C 32
+#define XT_CPT (XT_C * XT_R / 256)   // output columns per thread
 __global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ descs,
                                                   const int* __restrict__ idx, const double2* __restrict__ Xg,
                                                   const float2* __restrict__ X1g, const double2* __restrict__ R,
                                                   const double2* __restrict__ Ebg, double2* __restrict__ Xn) {
-    __shared__ Split et[RF_BW];
+    __shared__ float2 xs[XT_C + 2 * RF_W][XT_R];
+    __shared__ Split es[RF_BW][XT_C];
+    __shared__ float cs[2][XT_R][XT_C + 1];
     const MmfDesc d = descs[idx[blockIdx.z]];
     const int n = d.n, la = xe_la(n);
-    const int j = blockIdx.y;
-    if (j >= n) return;
+    const int r0 = blockIdx.x * XT_R, j0 = blockIdx.y * XT_C;
+    if (r0 >= n || j0 >= n) return;
     const double2* Eb = Ebg + (int64_t)d.vec_off * RF_BW;
-    if (threadIdx.x < RF_BW) {
-        const int i = j + threadIdx.x - RF_W;
-        et[threadIdx.x] = split((i >= 0 && i < n) ? Eb[(int64_t)i * RF_BW + (j - i + RF_W)] : make_double2(0.0, 0.0));
+    const float* C = reinterpret_cast<const float*>(R + d.mat_off) + (int64_t)n * la;
+    const float2* X1 = X1g + d.mat_off;
+    for (int e = threadIdx.x; e < (XT_C + 2 * RF_W) * XT_R; e += 256) {
+        const int cc = e / XT_R, rr = e - cc * XT_R, col = j0 - RF_W + cc, row = r0 + rr;
+        xs[cc][rr] = (col >= 0 && col < n && row < n) ? X1[(int64_t)col * d.ld + row] : make_float2(0.f, 0.f);
+    }
+    for (int e = threadIdx.x; e < RF_BW * XT_C; e += 256) {
+        const int q = e / XT_C, c = e - q * XT_C, j = j0 + c, i = j + q - RF_W;
+        es[q][c] = split((j < n && i >= 0 && i < n) ? Eb[(int64_t)i * RF_BW + (j - i + RF_W)] : make_double2(0.0, 0.0));
+    }
+    for (int e = threadIdx.x; e < XT_R * XT_C; e += 256) {
+        const int rr = e / XT_C, c = e - rr * XT_C, row = r0 + rr, j = j0 + c;
+        const bool ok = row < n && j < n;
+        cs[0][rr][c] = ok ? C[(int64_t)row * 2 * n + j] : 0.f;
+        cs[1][rr][c] = ok ? C[(int64_t)row * 2 * n + n + j] : 0.f;
     }
     __syncthreads();
-    const float* C = reinterpret_cast<const float*>(R + d.mat_off) + (int64_t)n * la;
+    const int rr = threadIdx.x & (XT_R - 1), cg = threadIdx.x / XT_R;
+    const int r = r0 + rr;
+    if (r >= n) return;
     const double2* X = Xg + d.mat_off;
-    const float2* X1 = X1g + d.mat_off;
-    const int qlo = max(0, RF_W - j), qhi = min(RF_BW, n - j + RF_W);
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+#pragma unroll 1
+    for (int c = cg * XT_CPT; c < cg * XT_CPT + XT_CPT; ++c) {
+        const int j = j0 + c;
+        if (j >= n) break;
         DF ar = DF{0.f, 0.f}, ai = DF{0.f, 0.f};
-        for (int q = qlo; q < qhi; ++q) {
-            const int i = j + q - RF_W;
-            const float2 x = X1[(int64_t)i * d.ld + r];
-            const float xr = x.x, xi = x.y;
-            const Split e = et[q];
-            df_mac1(ar, xr, e.r1, e.r2);
-            df_mac1(ar, -xi, e.i1, e.i2);
-            df_mac1(ai, xr, e.i1, e.i2);
-            df_mac1(ai, xi, e.r1, e.r2);
+#pragma unroll 11
+        for (int q = 0; q < RF_BW; ++q) {  // zero outside the matrix (staged as zeros)
+            const float2 x = xs[c + q][rr];
+            const Split e = es[q][c];
+            df_mac1(ar, x.x, e.r1, e.r2);
+            df_mac1(ar, -x.y, e.i1, e.i2);
+            df_mac1(ai, x.x, e.i1, e.i2);
+            df_mac1(ai, x.y, e.r1, e.r2);
         }
-        const double2 x = X[(int64_t)j * d.ld + r];
         const double2 band = df_value(ar, ai);
-        const float cr = C[(int64_t)r * 2 * n + j], ci = C[(int64_t)r * 2 * n + n + j];
+        const double2 x = X[(int64_t)j * d.ld + r];
         Xn[d.mat_off + (int64_t)j * d.ld + r] =
-            make_double2(x.x + ((double)cr + band.x), x.y + ((double)ci + band.y));
+            make_double2(x.x + ((double)cs[0][rr][c] + band.x), x.y + ((double)cs[1][rr][c] + band.y));
     }
 }
 
@@ -934,6 +954,8 @@ __global__ void __launch_bounds__(256) k_oa_lambda_band(const MmfDesc* __restric
 }
 
 // Xn(:, j) = X(:, j) + sum_{|i-j|<=W} X(:, i) Et(i, j)   (Et formed on the fly from the band)
+// Banded step: Xn(:, j) = X(:, j) + sum_{|i-j|<=W} X1(:, i) Et(i, j) in FP32 (Et here is the
+// second step's small correction), Et formed from the band of G and S; tiled like k_xe_apply.
 __global__ void __launch_bounds__(256) k_xe_band(const MmfDesc* __restrict__ descs,
                                                  const int* __restrict__ idx,
                                                  const double2* __restrict__ Xg,
@@ -943,48 +965,56 @@ __global__ void __launch_bounds__(256) k_xe_band(const MmfDesc* __restrict__ des
                                                  const double* __restrict__ lamg,
                                                  const int* __restrict__ cidg,
                                                  double2* __restrict__ Xn) {
-    __shared__ float2 et[RF_BW];
+    __shared__ float2 xs[XT_C + 2 * RF_W][XT_R];
+    __shared__ float2 es[RF_BW][XT_C];
     const MmfDesc d = descs[idx[blockIdx.z]];
     const int n = d.n;
-    const int j = blockIdx.y;
-    if (j >= n) return;
+    const int r0 = blockIdx.x * XT_R, j0 = blockIdx.y * XT_C;
+    if (r0 >= n || j0 >= n) return;
     const double2* G = Gbg + d.mat_off;
     const double2* S = Sbg + d.mat_off;
     const double* lam = lamg + d.vec_off;
     const int* cid = cidg + d.vec_off;
-    if (threadIdx.x < RF_BW) {
-        const int i = j + threadIdx.x - RF_W;
+    const float2* X1 = X1g + d.mat_off;
+    for (int e = threadIdx.x; e < (XT_C + 2 * RF_W) * XT_R; e += 256) {
+        const int cc = e / XT_R, rr = e - cc * XT_R, col = j0 - RF_W + cc, row = r0 + rr;
+        xs[cc][rr] = (col >= 0 && col < n && row < n) ? X1[(int64_t)col * d.ld + row] : make_float2(0.f, 0.f);
+    }
+    const double hmax = fmax(fabs(lam[0]), fabs(lam[n - 1]));
+    for (int e = threadIdx.x; e < RF_BW * XT_C; e += 256) {
+        const int q = e / XT_C, c = e - q * XT_C, j = j0 + c, i = j + q - RF_W;
         float2 v = make_float2(0.f, 0.f);
-        if (i >= 0 && i < n) {
+        if (j < n && i >= 0 && i < n) {
             const double2 g = band_at(G, i, j);
-            double2 e;
+            double2 et;
             if (i == j) {
-                e = make_double2(0.5 * (1.0 - g.x), 0.0);
+                et = make_double2(0.5 * (1.0 - g.x), 0.0);
             } else {
                 const double2 num = band_at(S, i, j) - lam[j] * g;
                 const double gap = lam[j] - lam[i];
-                const double hmax = fmax(fabs(lam[0]), fabs(lam[n - 1]));
                 const bool clustered = cid[i] == cid[j] || fabs(gap) <= RF_TAU * sqrt(abs2(num)) ||
                                        fabs(gap) <= 1e-13 * fmax(hmax, fabs(lam[i]));
-                e = clustered ? (-0.5) * g : (1.0 / gap) * num;
+                et = clustered ? (-0.5) * g : (1.0 / gap) * num;
             }
-            v = make_float2(__double2float_rn(e.x), __double2float_rn(e.y));
+            v = make_float2(__double2float_rn(et.x), __double2float_rn(et.y));
         }
-        et[threadIdx.x] = v;
+        es[q][c] = v;
     }
     __syncthreads();
+    const int rr = threadIdx.x & (XT_R - 1), cg = threadIdx.x / XT_R;
+    const int r = r0 + rr;
+    if (r >= n) return;
     const double2* X = Xg + d.mat_off;
-    const float2* X1 = X1g + d.mat_off;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+#pragma unroll 1
+    for (int c = cg * XT_CPT; c < cg * XT_CPT + XT_CPT; ++c) {
+        const int j = j0 + c;
+        if (j >= n) break;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < RF_BW; ++q) {
-            const int i = j + q - RF_W;
-            if (i >= 0 && i < n) {
-                const float2 xf = X1[(int64_t)i * d.ld + r];
-                acc.x = fmaf(xf.x, et[q].x, fmaf(-xf.y, et[q].y, acc.x));
-                acc.y = fmaf(xf.x, et[q].y, fmaf(xf.y, et[q].x, acc.y));
-            }
+            const float2 xf = xs[c + q][rr], e = es[q][c];
+            acc.x = fmaf(xf.x, e.x, fmaf(-xf.y, e.y, acc.x));
+            acc.y = fmaf(xf.x, e.y, fmaf(xf.y, e.x, acc.y));
         }
         const double2 x = X[(int64_t)j * d.ld + r];
         Xn[d.mat_off + (int64_t)j * d.ld + r] = make_double2(x.x + (double)acc.x, x.y + (double)acc.y);
@@ -1059,7 +1089,8 @@ cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, do
     k_xe_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, ops, G, (Tf3Job*)jobs);
     cudaError_t e = mmf_launch_tf3(jobs, L.count, L.nmax, 2 * L.nmax, status, L.stream);
     if (e != cudaSuccess) return e;
-    k_xe_apply<<<dim3((L.nmax + 255) / 256, L.nmax, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, X1, G, Eb, HX);
+    k_xe_apply<<<dim3((L.nmax + XT_R - 1) / XT_R, (L.nmax + XT_C - 1) / XT_C, L.count), 256, 0, L.stream>>>(
+        L.desc, L.idx, X, X1, G, Eb, HX);
     e = cudaMemcpyAsync(X, HX, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
     if (e != cudaSuccess) return e;
     k_cluster_sep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, coef, X, HX, lam, cid, status);
@@ -1074,8 +1105,8 @@ cudaError_t mmf_launch_refine_band(const MmfLaunch& L, const double2* coef, cons
     k_gram_band_df32<<<dim3((L.nmax + RF_BC - 1) / RF_BC, L.count), 256, 0, L.stream>>>(
         L.desc, L.idx, X, HX, G, S);
     k_oa_lambda_band<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
-    k_xe_band<<<dim3((L.nmax + 255) / 256, L.nmax, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, X1, G, S,
-                                                                                lam, cid, HX);
+    k_xe_band<<<dim3((L.nmax + XT_R - 1) / XT_R, (L.nmax + XT_C - 1) / XT_C, L.count), 256, 0, L.stream>>>(
+        L.desc, L.idx, X, X1, G, S, lam, cid, HX);
     cudaError_t e = cudaMemcpyAsync(X, HX, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
     if (e != cudaSuccess) return e;
     k_cluster_sep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, coef, X, HX, lam, cid, status);
