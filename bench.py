@@ -90,30 +90,35 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-# FP32 instruction issue peak (one FP32 op per lane per clock) and the double-FP32 scheme's cost:
-# on the first refinement step X is FP32-exact, so an FP64-accurate real product-accumulate takes
-# 10 FP32 instructions for X^H X and 11 for X^H (H X) (exact product + FMA error term + TwoSum),
-# i.e. 4 x (10 + 11) / 2 = 42 instructions per complex multiply-add of 8 FP64-equivalent flops.
-FP32_INSTR_PEAK = 152 * 128 * 2.07e9
-DF32_INSTR_PER_FLOP = (40.0 + 44.0) / 2.0 / 8.0  # G terms 10, S terms 11 instructions per real product
-
-
 def stage_model(stage: str, n: int, nt: int, mixed: bool):
-    """(algorithmic real flops per system, peak flop/s, peak description) of a stage's main kernel.
-    LAPACK counts for the reduction (16/3 n^3) and the back-transform (8 n^3); the Gram products
-    X^H X and X^H H X (Hermitian halves) are n^3 complex multiply-adds = 8 n^3 FP64-equivalent flops;
-    U is 8 nt n^2 (the Phi contraction)."""
+    """The bounds of a stage's main kernel for one system: a list of (bound, algorithmic work,
+    peak per second, unit, peak description, kernel).  The roofline reports the bound whose
+    work / peak is largest (the one that limits the kernel).
+    - hetrd: (16/3) n^3 real flops (LAPACK count); the hemv of every column streams the trailing
+      lower triangle, sum_m m^2/2 = n^3/6 complex entries (8 bytes FP32, 16 bytes FP64).
+    - backtransform: 8 n^3 real flops (LAPACK count).
+    - refine_gram: the tensor-core Gram product by integer slicing, 28 slice pairs x (Re, Im) x
+      n x n/2 x 2n multiply-adds (lower-triangle tiles) on the BF16 tensor cores, against the
+      sustained cuBLAS bf16 rate (the kernel runs inside a long step).
+    - outputs: 8 nt n^2 flops (the Phi contraction)."""
+    pk = _peaks()
+    hbm = pk["hbm_gbs"] * 1e9
+    bf16 = pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * 1e12
+    src = "of fallback" if pk.get("fallback") else "of measured"
+    alu = (FP32_ALU_PEAK, "FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived from unit counts and clock)") \
+        if mixed else (FP64_ALU_PEAK, "FP64: nominal 1.25 TFLOP/s")
     if stage == "hetrd":
-        return 16.0 / 3.0 * n ** 3, (FP32_ALU_PEAK if mixed else FP64_ALU_PEAK), \
-            ("FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz" if mixed else "FP64: nominal 1.25 TFLOP/s")
+        esz = 8.0 if mixed else 16.0
+        return [("alu", 16.0 / 3.0 * n ** 3, alu[0], "TFLOP/s", alu[1], "k_hetrd"),
+                ("hbm", esz * n ** 3 / 6.0, hbm, "GB/s", f"copy bandwidth {pk['hbm_gbs']} GB/s {src}", "k_hetrd")]
     if stage == "backtransform":
-        return 8.0 * n ** 3, (FP32_ALU_PEAK if mixed else FP64_ALU_PEAK), \
-            ("FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz" if mixed else "FP64: nominal 1.25 TFLOP/s")
-    if stage == "refine_gram":
-        return 8.0 * n ** 3, FP32_INSTR_PEAK / DF32_INSTR_PER_FLOP, \
-            "FP64-accurate double-FP32: FP32 issue peak 152 x 128 x 2.07 GHz / 5.25 instructions per flop"
+        return [("alu", 8.0 * n ** 3, alu[0], "TFLOP/s", alu[1],
+                 "k_backtransform_f32" if mixed else "k_backtransform")]
+    if stage == "refine_gram" and mixed:
+        return [("tensor", 112.0 * n ** 3, bf16, "TFLOP/s",
+                 f"cuBLAS bf16 sustained {bf16 / 1e12:.1f} TFLOP/s {src}", "k_oz_gram")]
     if stage == "outputs":
-        return 8.0 * nt * n * n, FP64_ALU_PEAK, "FP64: nominal 1.25 TFLOP/s"
+        return [("alu", 8.0 * nt * n * n, alu[0], "TFLOP/s", alu[1], "k_time_evolution")]
     return None
 
 
@@ -343,16 +348,18 @@ def main():
     mixed = prec == M.MMF_MIXED
     modelled = {k: v for k, v in per.items() if stage_model(k, n, nt, mixed) is not None}
     dom = max(modelled, key=modelled.get)
-    _, peak, peak_src = stage_model(dom, n, nt, mixed)
     jac = 118 if mixed else 84  # systems at or below this size take the shared-memory Jacobi path
-    flops = sum(stage_model(dom, p.n, nt, mixed)[0] for p in problems
-                if dom not in ("hetrd", "backtransform") or p.n > jac)
-    achieved = flops / (per[dom] / 1e3) if per[dom] > 0 else 0.0
-    kernel = {"hetrd": "k_hetrd", "backtransform": "k_backtransform", "refine_gram": "k_gram_df32",
-              "outputs": "k_time_evolution"}[dom]
-    roof = {"kernel": kernel, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-            "peak_source": peak_src + " (derived from unit counts and clock)"}
+    bounds = []
+    for j, (bnd, _, peak, unit, src, kern) in enumerate(stage_model(dom, n, nt, mixed)):
+        work = sum(stage_model(dom, p.n, nt, mixed)[j][1] for p in problems
+                   if dom not in ("hetrd", "backtransform") or p.n > jac)
+        bounds.append((work / peak, bnd, work, peak, unit, src, kern))
+    _, bnd, work, peak, unit, src, kern = max(bounds)
+    achieved = work / (per[dom] / 1e3) if per[dom] > 0 else 0.0
+    scale = 1e9 if unit == "GB/s" else 1e12
+    roof = {"kernel": kern, "bound": bnd, "achieved": achieved / scale, "peak": peak / scale,
+            "unit": unit, "frac": achieved / peak, "traffic": None, "peak_source": src,
+            "work_per_launch": work}
 
     serving = None
     if rank == 0 and world == 1 and args.serve_requests > 0 and count == COUNT and args.workload == "spin1":
