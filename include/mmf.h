@@ -82,12 +82,16 @@ MMF_API size_t mmf_ctx_budget(const mmf_ctx* ctx);
  * errors between eigenpairs far apart in the sorted order that the banded step cannot reach).
  * MMF_OPT_GRAM_KERNEL: the mixed path's Gram product X^H X, 0 (default) on the BF16 tensor
  * cores by exact integer slicing, 1 in double-FP32 on the FP32 units (both FP64-accurate).
+ * MMF_OPT_BT_TC_N: in the mixed path, smallest n whose back-transform (Z = Q Y, Sec. 3.2's
+ * eigenvectors from the tridiagonal ones) runs on the tensor cores in split TF32 (default 256);
+ * smaller systems use the FP32 SIMT kernel.
  * Results do not depend on the path beyond rounding. */
 #define MMF_OPT_JACOBI_N_FP64 1
 #define MMF_OPT_JACOBI_N_MIXED 2
 #define MMF_OPT_LARGE_N 3
 #define MMF_OPT_REFINE_FULL_N 4
 #define MMF_OPT_GRAM_KERNEL 5
+#define MMF_OPT_BT_TC_N 6
 MMF_API int mmf_ctx_set_option(mmf_ctx* ctx, int option, int64_t value);
 
 /* ---------------------------------------------------------------- system definition

@@ -43,13 +43,6 @@
 #define RF_BW (2 * RF_W + 1)
 static_assert(RF_BW == MMF_REFINE_BW, "band buffer width");
 
-// TF32 operands for the tcgen05 engine: round to nearest (ties away) to 10 explicit bits
-__device__ __forceinline__ float tf32_round(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
 // row length (floats) of the real K-major operands built from n complex entries: [Re | Im | pad]
 __device__ __forceinline__ int xe_la(int n) { return (2 * n + 3) & ~3; }
 
@@ -334,6 +327,7 @@ __global__ void k_w_jobs(const MmfDesc* __restrict__ descs, const int* __restric
     j.B = j.A + 2 * tf3_piece(n, 2 * n);
     j.C = reinterpret_cast<float*>(T + d.mat_off) + (second_c ? (int64_t)2 * n * n : 0);
     j.M = n; j.N = 2 * n; j.K = 2 * n; j.ldc = 2 * n;
+    j.mode = TF3_STORE;
     jobs[i] = j;
 }
 
@@ -528,6 +522,7 @@ __global__ void k_xe_jobs(const MmfDesc* __restrict__ descs, const int* __restri
     j.B = j.A + 2 * tf3_piece(n, 2 * n);
     j.C = reinterpret_cast<float*>(R + d.mat_off) + (int64_t)n * la;
     j.M = n; j.N = 2 * n; j.K = 2 * n; j.ldc = 2 * n;
+    j.mode = TF3_STORE;
     jobs[i] = j;
 }
 

@@ -314,11 +314,52 @@ __global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ 
                       "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                     : "r"(ta));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (row < jb.M) {
-                    float* out = jb.C + (int64_t)row * jb.ldc + J * 128 + c0;
+                const int col = J * 128 + c0;
+                if (jb.mode == TF3_OPERAND) {
+                    // the row's 32 values are one 128-byte row of K-tile col / 32 (16-byte chunks
+                    // swizzled); rows past M are written as zeros
+                    const int64_t pc = tf3_piece(jb.M, jb.N);
+                    const int sw = row & 7;
+                    // start of the row: tf3_pos of column col (a multiple of 32) holds chunk 0 at
+                    // its swizzled place sw
+                    float* o1 = jb.C + tf3_pos(jb.M, jb.N, 0, row, col) - (sw << 2);
 #pragma unroll
-                    for (int q = 0; q < 32; ++q)
-                        if (J * 128 + c0 + q < jb.N) out[q] = __uint_as_float(v[q]);
+                    for (int q = 0; q < 8; ++q) {
+                        float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+                        if (row < jb.M) {
+                            const float x0 = __uint_as_float(v[4 * q]), x1 = __uint_as_float(v[4 * q + 1]);
+                            const float x2 = __uint_as_float(v[4 * q + 2]), x3 = __uint_as_float(v[4 * q + 3]);
+                            h = make_float4(tf32_round(x0), tf32_round(x1), tf32_round(x2), tf32_round(x3));
+                            l = make_float4(tf32_round(x0 - h.x), tf32_round(x1 - h.y), tf32_round(x2 - h.z),
+                                            tf32_round(x3 - h.w));
+                        }
+                        *reinterpret_cast<float4*>(o1 + ((q ^ sw) << 2)) = h;
+                        *reinterpret_cast<float4*>(o1 + pc + ((q ^ sw) << 2)) = l;
+                    }
+                } else if (row < jb.M) {
+                    float* out = jb.C + (int64_t)row * jb.ldc + col;
+                    if (jb.mode == TF3_SUBTRACT) {
+                        // C is 16-byte aligned per row and N is even
+#pragma unroll
+                        for (int q = 0; q < 32; q += 4) {
+                            if (col + q + 3 < jb.N) {
+                                float4 c = *reinterpret_cast<float4*>(out + q);
+                                c.x -= __uint_as_float(v[q]);
+                                c.y -= __uint_as_float(v[q + 1]);
+                                c.z -= __uint_as_float(v[q + 2]);
+                                c.w -= __uint_as_float(v[q + 3]);
+                                *reinterpret_cast<float4*>(out + q) = c;
+                            } else {
+#pragma unroll
+                                for (int u = 0; u < 4; ++u)
+                                    if (col + q + u < jb.N) out[q + u] -= __uint_as_float(v[q + u]);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q)
+                            if (col + q < jb.N) out[q] = __uint_as_float(v[q]);
+                    }
                 }
             }
         }

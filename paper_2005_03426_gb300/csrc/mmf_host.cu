@@ -46,6 +46,7 @@ struct mmf_ctx {
     int64_t large_n = -1;            // whole-GPU reduction from this n on; -1 = when one CTA cannot
     int64_t refine_full_n = -1;      // mixed path: second refinement step in full from this n on
     int64_t gram_kernel = 0;         // mixed path: 0 = BF16 tensor cores (exact slicing), 1 = double-FP32
+    int64_t bt_tc_n = -1;            // mixed path: back-transform on the tensor cores from this n on
     std::recursive_mutex mu;
 };
 
@@ -77,6 +78,11 @@ struct mmf_batch {
     std::vector<MmfDesc> desc;
     std::vector<int> all, small, large, medium, huge;  // large = medium + huge
     std::vector<int> rband, rfull;                     // mixed: banded / full second refinement step
+    std::vector<int> btc, bts;                         // large: back-transform on tensor cores / SIMT
+    std::vector<int> btc_n;                            // n of each system in btc
+    int nmax_btc = 0, nmax_bts = 0;
+    int *d_btc = nullptr, *d_bts = nullptr;
+    void* d_btjobs = nullptr;                          // 4 x count Tf3Job
     int nmax_rband = 0, nmax_rfull = 0;
     int nmax_all = 0, nmax_small = 0, nmax_large = 0, Mmax = 1, Dmax = 1;
     int64_t n_oz = 0;      // BF16 elements of the Gram-product slices (mixed, tensor-core Gram)
@@ -146,6 +152,9 @@ static int jacobi_nmax(const mmf_ctx* c, int prec) {
     return v < 0 ? jacobi_default(prec) : (int)std::max<int64_t>(4, std::min<int64_t>(v, jacobi_default(prec)));
 }
 
+static int64_t bt_tc_n(const mmf_ctx* c) {
+    return (c && c->bt_tc_n >= 0) ? c->bt_tc_n : (int64_t)MMF_BT_TC_NMIN;
+}
 static int64_t refine_full_n(const mmf_ctx* c) {
     return (c && c->refine_full_n >= 0) ? c->refine_full_n : (int64_t)MMF_REFINE_FULL2_N;
 }
@@ -233,6 +242,7 @@ extern "C" int mmf_ctx_set_option(mmf_ctx* c, int option, int64_t value) {
         case MMF_OPT_JACOBI_N_MIXED: c->jacobi_n[1] = value; return MMF_OK;
         case MMF_OPT_LARGE_N: c->large_n = value; return MMF_OK;
         case MMF_OPT_REFINE_FULL_N: c->refine_full_n = value; return MMF_OK;
+        case MMF_OPT_BT_TC_N: c->bt_tc_n = value; return MMF_OK;
         case MMF_OPT_GRAM_KERNEL:
             if (value > 1) return fail(MMF_ERR_ARG, "MMF_OPT_GRAM_KERNEL: 0 (tensor cores) or 1 (double-FP32)");
             c->gram_kernel = value < 0 ? 0 : value;
@@ -411,9 +421,21 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         b->n_vec += n;
         d.sq_off = b->n_sq;
         d.oz_off = b->n_oz;
+        // mixed: back-transform on the tensor cores for large enough systems (SIMT otherwise)
+        const bool tc = precision == MMF_MIXED && !d.small && n >= std::max<int64_t>(bt_tc_n(ctx), 3);
         if (precision == MMF_MIXED) {  // Gram slices (BF16) and split-TF32 operands share the area
             const int64_t oz = ctx->gram_kernel == 0 ? (int64_t)mmf_ozaki_slice_elems((int)n) : 0;
-            b->n_oz += std::max<int64_t>(oz, 2 * mmf_tf3_floats((int)n));
+            b->n_oz += std::max<int64_t>(std::max<int64_t>(oz, 2 * mmf_tf3_floats((int)n)),
+                                         tc ? 2 * mmf_bt_floats((int)n) : 0);
+        }
+        if (!d.small) {
+            (tc ? b->btc : b->bts).push_back(i);
+            if (tc) {
+                b->btc_n.push_back((int)n);
+                b->nmax_btc = std::max(b->nmax_btc, (int)n);
+            } else {
+                b->nmax_bts = std::max(b->nmax_bts, (int)n);
+            }
         }
         d.pan_off = b->n_pan;
         if (!d.small) {
@@ -452,7 +474,8 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     size_t o_all = p.take(sizeof(int) * count), o_small = p.take(sizeof(int) * count),
            o_large = p.take(sizeof(int) * count), o_medium = p.take(sizeof(int) * count),
            o_status = p.take(sizeof(int) * count), o_rband = p.take(sizeof(int) * count),
-           o_rfull = p.take(sizeof(int) * count);
+           o_rfull = p.take(sizeof(int) * count), o_btc = p.take(sizeof(int) * count),
+           o_bts = p.take(sizeof(int) * count);
     size_t o_coef = p.take(sizeof(double2) * b->n_coef);
     size_t o_H = p.take(cs * b->n_mat);
     size_t o_Zf = p.take(sizeof(double2) * b->n_mat);
@@ -484,12 +507,16 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         o_cid = p.take(sizeof(int) * b->n_vec);
         o_jobs = p.take(std::max(sizeof(UmmaJob), sizeof(Tf3Job)) * count);
     }
+    const size_t o_btjobs = b->btc.empty() ? 0 : p.take(sizeof(Tf3Job) * 4 * b->btc.size());
     b->bytes = p.off;
     if (ctx->used + b->bytes > ctx->budget) {
         size_t need = b->bytes;
+        const int64_t b_nmat = b->n_mat, b_noz = b->n_oz, b_nmax = b->nmax_all;
         delete b;
         return fail(MMF_ERR_BUDGET, "batch needs " + std::to_string(need) + " bytes, budget has " +
-                                        std::to_string(ctx->budget - ctx->used));
+                                        std::to_string(ctx->budget - ctx->used) + " (elements: matrices " +
+                                        std::to_string(b_nmat) + ", operand area " + std::to_string(b_noz) +
+                                        ", largest n " + std::to_string(b_nmax) + ")");
     }
     cudaError_t e = cudaMallocAsync((void**)&b->base, b->bytes, b->stream);
     if (e != cudaSuccess) {
@@ -506,6 +533,9 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     b->d_status = (int*)(B + o_status);
     b->d_rband = (int*)(B + o_rband);
     b->d_rfull = (int*)(B + o_rfull);
+    b->d_btc = (int*)(B + o_btc);
+    b->d_bts = (int*)(B + o_bts);
+    if (!b->btc.empty()) b->d_btjobs = B + o_btjobs;
     b->d_coef = (double2*)(B + o_coef);
     b->d_H = B + o_H;
     b->d_Zf = (double2*)(B + o_Zf);
@@ -567,6 +597,10 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         e = cudaMemcpyAsync(b->d_rband, b->rband.data(), sizeof(int) * b->rband.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !b->rfull.empty())
         e = cudaMemcpyAsync(b->d_rfull, b->rfull.data(), sizeof(int) * b->rfull.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !b->btc.empty())
+        e = cudaMemcpyAsync(b->d_btc, b->btc.data(), sizeof(int) * b->btc.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !b->bts.empty())
+        e = cudaMemcpyAsync(b->d_bts, b->bts.data(), sizeof(int) * b->bts.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_coef, b->h_coef, sizeof(double2) * b->n_coef, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -731,7 +765,18 @@ static int stage_eig(mmf_batch* b) {
         LAUNCH(mmf_launch_tridiag_eig(Ll, b->d_d, b->d_e, b->d_aux, b->d_e2, b->d_E, b->d_Y, b->d_work,
                                       b->d_status, fp32, 3), 3);
         mark(b, ST_BACKTRANSFORM);
-        LAUNCH(mmf_launch_backtransform(Ll, b->d_H, b->d_tau, b->d_Vp, b->d_Y, b->d_Zp, fp32), 2);
+        if (!b->bts.empty()) {
+            MmfLaunch Ls = launch_of(b, b->bts, b->d_bts, b->nmax_bts);
+            LAUNCH(mmf_launch_backtransform(Ls, b->d_H, b->d_tau, b->d_Vp, b->d_Y, b->d_Zp, fp32), 2);
+        }
+        if (!b->btc.empty()) {
+            MmfLaunch Lc = launch_of(b, b->btc, b->d_btc, b->nmax_btc);
+            int nl = 0;
+            LAUNCH(mmf_launch_backtransform_tc(Lc, b->btc_n.data(), b->d_H, b->d_tau, b->d_Y, b->d_Zp, b->d_oz,
+                                               b->d_btjobs, b->d_status, &nl),
+                   0);
+            g_launches += nl;
+        }
         if (fp32) LAUNCH(mmf_launch_widen(Ll, b->d_Zp, b->d_Zf, fp32), 1);
     } else {
         mark(b, ST_HETRD);
@@ -857,9 +902,12 @@ extern "C" int mmf_batch_sync(mmf_batch* b, int* status) {
     std::vector<int> st(b->count);
     CU(cudaMemcpyAsync(st.data(), b->d_status, sizeof(int) * b->count, cudaMemcpyDeviceToHost, b->stream));
     CU(cudaStreamSynchronize(b->stream));
-    int worst = 0;
-    for (int i = 0; i < b->count; ++i) worst = std::max(worst, st[i]);
+    int worst = 0, at = 0;
+    for (int i = 0; i < b->count; ++i)
+        if (st[i] > worst) worst = st[i], at = i;
     if (status) std::memcpy(status, st.data(), sizeof(int) * b->count);
+    // a numeric status replaces the message of any earlier call
+    if (worst > 0) return fail(worst, "system " + std::to_string(at) + ": " + mmf_strerror(worst));
     return worst;
 }
 

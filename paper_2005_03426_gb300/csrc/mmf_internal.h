@@ -259,18 +259,49 @@ __host__ __device__ __forceinline__ int64_t tf3_pos(int rows, int K, int piece, 
     return (((int64_t)piece * tf3_nt(K) + t) * tf3_nq(rows) + q) * 4096 + (rr >> 3) * 256 + (rr & 7) * 32 +
            (((kk >> 2) ^ (rr & 7)) << 2) + (kk & 3);
 }
+// Output modes: 0 stores C (M x N, row stride ldc); 1 subtracts the product from C; 2 writes the
+// product's TF32 pieces as an operand of a further product (rows = M, K = N, a multiple of 32,
+// piece 1 at C, piece 2 after tf3_piece(M, N) floats; padding rows written as zeros).
+#define TF3_STORE 0
+#define TF3_SUBTRACT 1
+#define TF3_OPERAND 2
 struct Tf3Job {
     const float* A;   // piece 1 of A (piece 2 follows after tf3_piece(M, K) floats)
     const float* B;   // piece 1 of B
     float* C;         // M x N, row stride ldc
     int M, N, K, ldc;
+    int mode;
 };
+#ifdef __CUDACC__
+// TF32 operands for the tcgen05 engine: round to nearest (ties away) to 10 explicit bits
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+#endif
 cudaError_t mmf_launch_tf3(const void* jobs, int count, int Mmax, int Nmax, int* err, cudaStream_t stream);
 // floats of the refinement's split-TF32 operands for one system (A: n x 2n, B: 2n x 2n)
 __host__ __device__ __forceinline__ int64_t mmf_tf3_floats(int n) {
     return 2 * tf3_piece(n, 2 * n) + 2 * tf3_piece(2 * n, 2 * n);
 }
 int mmf_umma_selftest_impl(int M, int N, int K, int kind, int P, double* max_abs, double* max_ref);
+
+// Back-transform of the mixed path on the tensor cores (k_bt_tc.cu): reflectors in super-blocks
+// of MMF_BT_SB, each applied as split-TF32 products.  Systems with n >= MMF_BT_TC_NMIN take it.
+#define MMF_BT_SB 128
+#define MMF_BT_TC_NMIN 256
+__host__ __device__ __forceinline__ int mmf_bt_rp(int n) { return (n + 31) & ~31; }
+__host__ __device__ __forceinline__ int mmf_bt_nsb(int n) { return (n - 1 + MMF_BT_SB - 1) / MMF_BT_SB; }
+// floats of one system's back-transform operands (they live in the refinement's operand area)
+cudaError_t mmf_launch_backtransform_tc(const MmfLaunch& L, const int* hn, const void* H, const void* tau,
+                                        const double* Y, void* Z, void* pool, void* jobs, int* err,
+                                        int* launches);
+__host__ __device__ __forceinline__ int64_t mmf_bt_floats(int n) {
+    const int K1 = 2 * mmf_bt_rp(n);
+    return 2 * tf3_piece(n, K1) + 2 * tf3_piece(256, K1) + 2 * tf3_piece(2 * n, 256) + 4 * tf3_piece(n, 256) +
+           2 * tf3_piece(256, 256) + 256 * 256;
+}
 #define MMF_MIN_LD 36   // n x ld matrix slots also hold the n x 33 band of the refinement
 
 #define MMF_NB 32          // Householder panel width and back-transform block size

@@ -39,6 +39,7 @@ MMF_OPT_JACOBI_N_MIXED = 2
 MMF_OPT_LARGE_N = 3
 MMF_OPT_REFINE_FULL_N = 4
 MMF_OPT_GRAM_KERNEL = 5
+MMF_OPT_BT_TC_N = 6
 
 _lib = None
 _exiting = False

@@ -427,3 +427,67 @@ def test_mixed_batch_both_second_steps():
         assert np.abs(E - ref["E"]).max() <= MIX_E_REL * np.abs(ref["E"]).max()
         assert np.abs(U - ref["U"]).max() <= MIX_UP_ABS
         assert np.abs(P - ref["P"]).max() <= MIX_UP_ABS
+
+
+# ---------------------------------------------------------------------- back-transform paths
+# The mixed path's back-transform (Z = Q Y) runs on the tensor cores (super-blocks of 128
+# reflectors, split-TF32 products) from n = MMF_OPT_BT_TC_N on, on the FP32 SIMT kernel below.
+SIMT_ONLY = 1 << 40
+
+
+@pytest.mark.parametrize("case", ["random_n125", "qubit_n242", "random_n245", "spin1_n297", "c2_like_n"])
+@pytest.mark.parametrize("bt_tc_n", [0, SIMT_ONLY])
+def test_mixed_backtransform_paths_match_oracle(case, bt_tc_n):
+    """Both back-transform paths forced on systems with one to three super-blocks (ragged last
+    ones), against the oracle."""
+    c = M.Context(0)
+    c.set_option(M.MMF_OPT_BT_TC_N, bt_tc_n)
+    p = SOLVE_CASES[case]()
+    t = W.time_grid(p, 8)
+    s, E, U, P = _solve_gpu(c, p, t, 0.2, precision=M.MMF_MIXED)
+    _compare(p, E, U, P, t, 0.2, e_rel=MIX_E_REL, up_abs=MIX_UP_ABS)
+
+
+def test_mixed_backtransform_many_super_blocks():
+    """n = 693 (six super-blocks, the last one ragged) on the tensor-core path, against the
+    oracle, with eigenpair residuals and orthonormality of all eigenvectors within the mixed
+    path's bound (residual <= 1e-9 ||H_F||, the quasienergy tolerance)."""
+    c = M.Context(0)
+    p = W.spin1_bichromatic(0.35, 0.2, N1=10, N2=5)
+    assert p.n == 693
+    t = W.time_grid(p, 8)
+    s, E, U, P = _solve_gpu(c, p, t, 0.1, precision=M.MMF_MIXED)
+    _compare(p, E, U, P, t, 0.1, e_rel=MIX_E_REL, up_abs=MIX_UP_ABS)
+    Z = s.eigenvectors()
+    HF = O.build_hf(p)
+    nrm = np.abs(E).max()
+    res = np.abs(HF @ Z - Z * E[None, :]).max() / nrm
+    orth = np.abs(Z.conj().T @ Z - np.eye(p.n)).max()
+    print(f"n = 693: residual {res:.3e} |H_F|, orthogonality {orth:.3e}")
+    assert res <= MIX_E_REL
+    assert orth <= MIX_E_REL
+
+
+def test_mixed_batch_both_backtransform_paths():
+    """A batch whose systems take different back-transform paths (and different numbers of
+    super-blocks) against each system solved alone on the other path."""
+    c = M.Context(0)
+    c.set_option(M.MMF_OPT_BT_TC_N, 240)   # n >= 240: tensor cores, below: SIMT
+    ps = [SOLVE_CASES[k]() for k in ("qubit_n82", "random_n125", "spin1_n297", "qubit_n242", "random_n245")]
+    nt = 8
+    ts = np.stack([W.time_grid(p, nt) for p in ps])
+    b = M.Batch(c, [M.System(c, p) for p in ps], M.MMF_MIXED, nt)
+    b.set_times(0.0, ts)
+    b.run()
+    assert (b.sync() == 0).all()
+    c2 = M.Context(0)
+    c2.set_option(M.MMF_OPT_BT_TC_N, 100)  # every Householder system on the tensor cores
+    for i, p in enumerate(ps):
+        e, u, pp = b.get(i)
+        solo = M.Batch(c2, [M.System(c2, p)], M.MMF_MIXED, nt)
+        solo.set_times(0.0, ts[i:i + 1])
+        solo.run()
+        assert solo.sync()[0] == 0
+        e1, u1, p1 = solo.get(0)
+        assert np.abs(e - e1).max() <= 1e-9 * np.abs(e1).max()
+        assert np.abs(u - u1).max() <= 1e-8 and np.abs(pp - p1).max() <= 1e-8
