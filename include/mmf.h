@@ -246,6 +246,15 @@ MMF_API int mmf_selftest_tensor_cores(int M, int N, int K, int kind, int product
  * Returns the largest absolute difference and the largest |reference| entry; allocates its own
  * device memory. */
 MMF_API int mmf_selftest_gram(int n, double* max_abs_err, double* max_abs_ref);
+/* Runs the split-TF32 tensor-core product used by the mixed path's refinement and back-transform
+ * (each FP32 operand cut into two TF32 pieces, three products in one FP32 accumulator) on seeded
+ * M x K and N x K FP32 operands with full 24-bit mantissas, in output mode 0 (store C = A B^T),
+ * 1 (subtract A B^T from C) or 2 (write C's TF32 pieces as an operand; N a multiple of 32), and
+ * compares with an FP64 reference computed on the device.  Returns the largest error relative to
+ * sum_k |a_k b_k| of its entry, and the same for a sequential FP32 dot product (fmaf) for
+ * comparison.  M x K, N x K and M x N at most 2^26 each; allocates its own device memory. */
+MMF_API int mmf_selftest_split_tf32(int M, int N, int K, int mode, double* max_rel_err,
+                                    double* max_rel_err_fp32);
 
 /* ---------------------------------------------------------------- misc */
 MMF_API const char* mmf_strerror(int status);

@@ -182,11 +182,15 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma_gemm(const UmmaJob* __re
 // 128 x 128 tile of C, six warps: warp 4 (one lane) streams the four 16-KB operand tiles of each
 // K step into a ring of TF_STAGES stages with cp.async.bulk (completion counted on full[stage]);
 // warp 5 (one lane) issues the 12 tcgen05.mma of the step and frees the stage with
-// tcgen05.commit on empty[stage]; warps 0-3 wait for the final commit and write C from TMEM.
-// Every wait is bounded and ends on a shared abort flag.
+// tcgen05.commit on empty[stage]; warps 0-3 own the tile's rows (their TMEM lanes).
+// The tensor cores' FP32 accumulation loses accuracy over long K, so the sum is cut into chunks
+// of TF_KC K steps: each chunk is accumulated in one of two TMEM buffers (commit on accfull[b])
+// and added, rounded to nearest, into the epilogue warps' registers, which then free the buffer
+// (accempty[b]) while the next chunk runs.  Every wait is bounded and ends on a shared abort flag.
 #define TF_STAGES 3
 #define TF_TILE_BYTES 16384u
 #define TF_STAGE_BYTES (4u * TF_TILE_BYTES)
+#define TF_KC 4
 
 __device__ __forceinline__ bool tf_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
     const uint32_t a = smem_u32(bar);
@@ -206,9 +210,21 @@ __device__ __forceinline__ bool tf_wait(uint64_t* bar, uint32_t parity, volatile
     return false;
 }
 
+__device__ __forceinline__ void tf_ld32(uint32_t ta, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+          "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+          "=r"(v[30]), "=r"(v[31])
+        : "r"(ta));
+}
+
 __global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ jobs, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char tf_smem[];
-    __shared__ uint64_t full[TF_STAGES], empty[TF_STAGES], accfull;
+    __shared__ uint64_t full[TF_STAGES], empty[TF_STAGES], accfull[2], accempty[2];
     __shared__ uint32_t tmem_s;
     __shared__ int abort_s;
     const Tf3Job jb = jobs[blockIdx.z];
@@ -224,12 +240,15 @@ __global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ 
             mbar_init(&full[q], 1);
             mbar_init(&empty[q], 1);
         }
-        mbar_init(&accfull, 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&accfull[q], 1);
+            mbar_init(&accempty[q], 4);  // one arrival per epilogue warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
-                     "r"(128u)
+                     "r"(256u)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -238,6 +257,7 @@ __global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ 
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_s;
     const int nt = tf3_nt(jb.K), nqa = tf3_nq(jb.M), nqb = tf3_nq(jb.N);
+    const int nch = (nt + TF_KC - 1) / TF_KC;
     const int64_t pa = tf3_piece(jb.M, jb.K), pb = tf3_piece(jb.N, jb.K);
 
     if (warp == 4) {
@@ -264,25 +284,27 @@ __global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ 
     } else if (warp == 5) {
         if (lane == 0) {
             const uint32_t idesc = umma_idesc(2);  // TF32, M = N = 128
-            bool ok = true;
             for (int t = 0; t < nt; ++t) {
                 const int st = t % TF_STAGES;
-                if (!tf_wait(&full[st], (uint32_t)(t / TF_STAGES) & 1u, abort_flag)) { ok = false; break; }
+                const int ch = t / TF_KC, kin = t - ch * TF_KC, bsel = ch & 1;
+                if (kin == 0 && ch >= 2 && !tf_wait(&accempty[bsel], (uint32_t)((ch >> 1) - 1) & 1u, abort_flag)) break;
+                if (!tf_wait(&full[st], (uint32_t)(t / TF_STAGES) & 1u, abort_flag)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t sa = sbase + (uint32_t)st * TF_STAGE_BYTES;
                 const uint64_t a1 = umma_desc(sa), a2 = umma_desc(sa + TF_TILE_BYTES);
                 const uint64_t b1 = umma_desc(sa + 2 * TF_TILE_BYTES), b2 = umma_desc(sa + 3 * TF_TILE_BYTES);
+                const uint32_t dacc = tmem + (uint32_t)(bsel * 128);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {  // 32 bytes (8 TF32) of K per instruction
                     const uint64_t adv = (uint64_t)((q * 32) >> 4);
-                    const uint32_t acc0 = (t > 0 || q > 0) ? 1u : 0u;
+                    const uint32_t acc0 = (kin > 0 || q > 0) ? 1u : 0u;
                     const uint64_t pa_[3] = {a1, a1, a2}, pb_[3] = {b1, b2, b1};
 #pragma unroll
                     for (int pp = 0; pp < 3; ++pp) {
                         const uint32_t accf = (pp > 0) ? 1u : acc0;
                         asm volatile(
                             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
                             "l"(pa_[pp] + adv), "l"(pb_[pp] + adv), "r"(idesc), "r"(accf)
                             : "memory");
                     }
@@ -290,31 +312,43 @@ __global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ 
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  smem_u32(&empty[st]))
                              : "memory");
+                if (kin == TF_KC - 1 || t == nt - 1)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&accfull[bsel]))
+                                 : "memory");
             }
-            if (ok)
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_u32(&accfull))
-                             : "memory");
         }
     } else {
-        // epilogue: warp w holds rows 32w .. 32w+31 of the tile (its TMEM lanes)
-        if (tf_wait(&accfull, 0u, abort_flag)) {
+        // epilogue: warp w holds rows 32w .. 32w+31 of the tile (its TMEM lanes); the chunks are
+        // summed in registers
+        float acc[128];
+#pragma unroll
+        for (int q = 0; q < 128; ++q) acc[q] = 0.f;
+        bool ok = true;
+        for (int ch = 0; ch < nch && ok; ++ch) {
+            const int bsel = ch & 1;
+            if (!tf_wait(&accfull[bsel], (uint32_t)(ch >> 1) & 1u, abort_flag)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int row = I * 128 + warp * 32 + lane;
+#pragma unroll
             for (int c0 = 0; c0 < 128; c0 += 32) {
                 uint32_t v[32];
-                const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
-                      "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
-                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(ta));
+                tf_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bsel * 128 + c0), v);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 32; ++q) acc[c0 + q] += __uint_as_float(v[q]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&accempty[bsel])) : "memory");
+            }
+        }
+        if (ok) {
+            const int row = I * 128 + warp * 32 + lane;
+#pragma unroll
+            for (int c0 = 0; c0 < 128; c0 += 32) {
                 const int col = J * 128 + c0;
+                if (col >= jb.N) break;
                 if (jb.mode == TF3_OPERAND) {
                     // the row's 32 values are one 128-byte row of K-tile col / 32 (16-byte chunks
                     // swizzled); rows past M are written as zeros
@@ -327,8 +361,8 @@ __global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ 
                     for (int q = 0; q < 8; ++q) {
                         float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
                         if (row < jb.M) {
-                            const float x0 = __uint_as_float(v[4 * q]), x1 = __uint_as_float(v[4 * q + 1]);
-                            const float x2 = __uint_as_float(v[4 * q + 2]), x3 = __uint_as_float(v[4 * q + 3]);
+                            const float x0 = acc[c0 + 4 * q], x1 = acc[c0 + 4 * q + 1];
+                            const float x2 = acc[c0 + 4 * q + 2], x3 = acc[c0 + 4 * q + 3];
                             h = make_float4(tf32_round(x0), tf32_round(x1), tf32_round(x2), tf32_round(x3));
                             l = make_float4(tf32_round(x0 - h.x), tf32_round(x1 - h.y), tf32_round(x2 - h.z),
                                             tf32_round(x3 - h.w));
@@ -344,21 +378,21 @@ __global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ 
                         for (int q = 0; q < 32; q += 4) {
                             if (col + q + 3 < jb.N) {
                                 float4 c = *reinterpret_cast<float4*>(out + q);
-                                c.x -= __uint_as_float(v[q]);
-                                c.y -= __uint_as_float(v[q + 1]);
-                                c.z -= __uint_as_float(v[q + 2]);
-                                c.w -= __uint_as_float(v[q + 3]);
+                                c.x -= acc[c0 + q];
+                                c.y -= acc[c0 + q + 1];
+                                c.z -= acc[c0 + q + 2];
+                                c.w -= acc[c0 + q + 3];
                                 *reinterpret_cast<float4*>(out + q) = c;
                             } else {
 #pragma unroll
                                 for (int u = 0; u < 4; ++u)
-                                    if (col + q + u < jb.N) out[q + u] -= __uint_as_float(v[q + u]);
+                                    if (col + q + u < jb.N) out[q + u] -= acc[c0 + q + u];
                             }
                         }
                     } else {
 #pragma unroll
                         for (int q = 0; q < 32; ++q)
-                            if (col + q < jb.N) out[q] = __uint_as_float(v[q]);
+                            if (col + q < jb.N) out[q] = acc[c0 + q];
                     }
                 }
             }
@@ -368,7 +402,7 @@ __global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ 
     __syncthreads();
     if (threadIdx.x == 0 && abort_s) atomicExch(err, 1);
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
 }
 
 cudaError_t mmf_launch_tf3(const void* jobs, int count, int Mmax, int Nmax, int* err, cudaStream_t stream) {
@@ -496,5 +530,130 @@ int mmf_umma_selftest_impl(int M, int N, int K, int kind, int P, double* max_abs
     *max_ref = hout[1];
     cudaFree(A); cudaFree(B); cudaFree(C); cudaFree(A16); cudaFree(B16); cudaFree(R); cudaFree(out);
     cudaFree(dj); cudaFree(err);
+    return rc;
+}
+
+// ------------------------------------------------------------------ split-TF32 engine self-test
+// k_tf3_gemm on seeded FP32 operands that are not TF32-exact (24-bit mantissas), in each output
+// mode, against an FP64 reference; the error of a sequential FP32 dot product (fmaf, round to
+// nearest) is reported beside it.  Errors are relative to sum_k |a_k b_k| of each entry.
+__global__ void k_tf3_fill(float* A, int64_t count, uint32_t seed) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)e * 2654435761u ^ seed;
+        x ^= x >> 13; x *= 0x5bd1e995u; x ^= x >> 15; x *= 0x27d4eb2fu; x ^= x >> 16;
+        A[e] = (float)((int)(x >> 8) - (1 << 23)) / (float)(1 << 23);  // 24-bit values in [-1, 1)
+    }
+}
+__global__ void k_tf3_tile(const float* __restrict__ A, int rows, int K, float* __restrict__ P) {
+    const int64_t tot = (int64_t)tf3_nq(rows) * 128 * tf3_nt(K) * 32;
+    const int Kp = tf3_nt(K) * 32;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / Kp), k = (int)(e - (int64_t)r * Kp);
+        const float v = (r < rows && k < K) ? A[(int64_t)r * K + k] : 0.f;
+        const float h = tf32_round(v);
+        P[tf3_pos(rows, K, 0, r, k)] = h;
+        P[tf3_pos(rows, K, 1, r, k)] = tf32_round(v - h);
+    }
+}
+__global__ void k_tf3_ref(const float* __restrict__ A, const float* __restrict__ B, int M, int N, int K,
+                          double* __restrict__ R, double* __restrict__ S, float* __restrict__ R32) {
+    const int m = blockIdx.y, n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M || n >= N) return;
+    double acc = 0.0, sc = 0.0;
+    float a32 = 0.f;
+    for (int k = 0; k < K; ++k) {
+        const float a = A[(int64_t)m * K + k], b = B[(int64_t)n * K + k];
+        acc += (double)a * (double)b;
+        sc += fabs((double)a * (double)b);
+        a32 = fmaf(a, b, a32);
+    }
+    R[(int64_t)m * N + n] = acc;
+    S[(int64_t)m * N + n] = sc;
+    R32[(int64_t)m * N + n] = a32;
+}
+__global__ void k_tf3_cmp(const float* __restrict__ C, const float* __restrict__ C0, const double* __restrict__ R,
+                          const double* __restrict__ S, const float* __restrict__ R32, int M, int N, int mode,
+                          double* out) {
+    double mx = 0.0, mx32 = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)M * N;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(e / N), n = (int)(e - (int64_t)m * N);
+        double c, x = R[e];
+        if (mode == TF3_OPERAND) {
+            c = (double)C[tf3_pos(M, N, 0, m, n)] + (double)C[tf3_pos(M, N, 1, m, n)];
+        } else {
+            c = C[e];
+            if (mode == TF3_SUBTRACT) x = (double)C0[e] - x;
+        }
+        const double sc = fmax(S[e], 1e-300);
+        mx = fmax(mx, fabs(c - x) / sc);
+        mx32 = fmax(mx32, fabs((double)R32[e] - R[e]) / sc);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mx32 = fmax(mx32, __shfl_xor_sync(0xffffffffu, mx32, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax((unsigned long long*)&out[0], __double_as_longlong(mx));
+        atomicMax((unsigned long long*)&out[1], __double_as_longlong(mx32));
+    }
+}
+
+int mmf_tf3_selftest_impl(int M, int N, int K, int mode, double* max_rel, double* max_rel_fp32) {
+    if (M < 1 || M > 65535 || N < 1 || K < 1 || mode < 0 || mode > 2 || (mode == TF3_OPERAND && N % 32 != 0))
+        return -1;
+    if ((int64_t)M * K > (1 << 26) || (int64_t)N * K > (1 << 26) || (int64_t)M * N > (1 << 26)) return -1;
+    float *A = nullptr, *B = nullptr, *PA = nullptr, *PB = nullptr, *C = nullptr, *C0 = nullptr, *R32 = nullptr;
+    double *R = nullptr, *S = nullptr, *out = nullptr;
+    Tf3Job* dj = nullptr;
+    int* err = nullptr;
+    const int64_t pa = tf3_piece(M, K), pb = tf3_piece(N, K);
+    const int64_t nc = mode == TF3_OPERAND ? 2 * tf3_piece(M, N) : (int64_t)M * N;
+    cudaError_t e = cudaMalloc(&A, sizeof(float) * (size_t)M * K);
+    if (e == cudaSuccess) e = cudaMalloc(&B, sizeof(float) * (size_t)N * K);
+    if (e == cudaSuccess) e = cudaMalloc(&PA, sizeof(float) * 2 * (size_t)pa);
+    if (e == cudaSuccess) e = cudaMalloc(&PB, sizeof(float) * 2 * (size_t)pb);
+    if (e == cudaSuccess) e = cudaMalloc(&C, sizeof(float) * (size_t)nc);
+    if (e == cudaSuccess) e = cudaMalloc(&C0, sizeof(float) * (size_t)M * N);
+    if (e == cudaSuccess) e = cudaMalloc(&R32, sizeof(float) * (size_t)M * N);
+    if (e == cudaSuccess) e = cudaMalloc(&R, sizeof(double) * (size_t)M * N);
+    if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(double) * (size_t)M * N);
+    if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(double) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&dj, sizeof(Tf3Job));
+    if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(out, 0, sizeof(double) * 2);
+    if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        k_tf3_fill<<<256, 256>>>(A, (int64_t)M * K, 12345u);
+        k_tf3_fill<<<256, 256>>>(B, (int64_t)N * K, 777u);
+        k_tf3_fill<<<256, 256>>>(C0, (int64_t)M * N, 4242u);
+        k_tf3_tile<<<512, 256>>>(A, M, K, PA);
+        k_tf3_tile<<<512, 256>>>(B, N, K, PB);
+        if (mode == TF3_OPERAND) e = cudaMemset(C, 0xff, sizeof(float) * (size_t)nc);  // padding must be rewritten
+        else e = cudaMemcpy(C, C0, sizeof(float) * (size_t)M * N, cudaMemcpyDeviceToDevice);
+    }
+    if (e == cudaSuccess) {
+        Tf3Job j;
+        j.A = PA; j.B = PB; j.C = C;
+        j.M = M; j.N = N; j.K = K; j.ldc = N; j.mode = mode;
+        e = cudaMemcpy(dj, &j, sizeof(j), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = mmf_launch_tf3(dj, 1, M, N, err, 0);
+    if (e == cudaSuccess) {
+        k_tf3_ref<<<dim3((N + 127) / 128, M), 128>>>(A, B, M, N, K, R, S, R32);
+        k_tf3_cmp<<<256, 256>>>(C, C0, R, S, R32, M, N, mode, out);
+        e = cudaDeviceSynchronize();
+    }
+    double hout[2] = {0, 0};
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(hout, out, sizeof(hout), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+    int rc = 0;
+    if (e != cudaSuccess) rc = -4;
+    else if (herr) rc = 1;
+    *max_rel = hout[0];
+    *max_rel_fp32 = hout[1];
+    cudaFree(A); cudaFree(B); cudaFree(PA); cudaFree(PB); cudaFree(C); cudaFree(C0); cudaFree(R32);
+    cudaFree(R); cudaFree(S); cudaFree(out); cudaFree(dj); cudaFree(err);
     return rc;
 }

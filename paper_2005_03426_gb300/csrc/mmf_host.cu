@@ -1500,6 +1500,16 @@ extern "C" int mmf_selftest_tensor_cores(int M, int N, int K, int kind, int prod
     return MMF_OK;
 }
 
+extern "C" int mmf_selftest_split_tf32(int M, int N, int K, int mode, double* max_rel_err,
+                                       double* max_rel_err_fp32) {
+    if (!max_rel_err || !max_rel_err_fp32) return fail(MMF_ERR_ARG, "output pointers required");
+    int rc = mmf_tf3_selftest_impl(M, N, K, mode, max_rel_err, max_rel_err_fp32);
+    if (rc == -1) return fail(MMF_ERR_ARG, "bad self-test sizes or mode");
+    if (rc == -4) return fail(MMF_ERR_CUDA, "self-test CUDA failure");
+    if (rc == 1) return fail(MMF_ST_NOCONV, "tensor-core pipeline wait timed out");
+    return MMF_OK;
+}
+
 extern "C" int mmf_selftest_gram(int n, double* max_abs_err, double* max_abs_ref) {
     if (!max_abs_err || !max_abs_ref) return fail(MMF_ERR_ARG, "output pointers required");
     int rc = mmf_ozaki_selftest_impl(n, max_abs_err, max_abs_ref);

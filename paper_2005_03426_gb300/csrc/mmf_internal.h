@@ -286,6 +286,7 @@ __host__ __device__ __forceinline__ int64_t mmf_tf3_floats(int n) {
     return 2 * tf3_piece(n, 2 * n) + 2 * tf3_piece(2 * n, 2 * n);
 }
 int mmf_umma_selftest_impl(int M, int N, int K, int kind, int P, double* max_abs, double* max_ref);
+int mmf_tf3_selftest_impl(int M, int N, int K, int mode, double* max_rel, double* max_rel_fp32);
 
 // Back-transform of the mixed path on the tensor cores (k_bt_tc.cu): reflectors in super-blocks
 // of MMF_BT_SB, each applied as split-TF32 products.  Systems with n >= MMF_BT_TC_NMIN take it.

@@ -114,6 +114,7 @@ _SIGS = {
     "mmf_serve_destroy": (_I, [_P]),
     "mmf_selftest_tensor_cores": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "mmf_selftest_gram": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "mmf_selftest_split_tf32": (_I, [_I, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "mmf_strerror": (ctypes.c_char_p, [_I]),
     "mmf_last_error": (ctypes.c_char_p, []),
     "mmf_last_launch_count": (_I, []),

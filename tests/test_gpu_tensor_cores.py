@@ -36,3 +36,21 @@ def test_gram_on_tensor_cores_is_fp64_accurate(n):
     assert rc == 0, M.lib().mmf_last_error()
     assert ref.value > 0
     assert err.value <= 2.0 ** -40 * max(1.0, ref.value) * 4
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(128, 128, 32), (300, 256, 640), (1323, 256, 2688), (200, 96, 2646),
+                                   (1, 32, 5)])
+def test_split_tf32_products(mode, shape):
+    """The split-TF32 product (two TF32 pieces per FP32 operand, three products in one FP32
+    accumulator) on operands with full FP32 mantissas, in the three output modes (store, subtract
+    in place, TF32 pieces as the next product's operand), against FP64: within a few FP32 roundings
+    per accumulated term of sum_k |a_k b_k|, as a sequential FP32 dot product is."""
+    m, n, k = shape
+    if mode == 2 and n % 32:
+        pytest.skip("operand mode needs N a multiple of 32")
+    err, err32 = ctypes.c_double(), ctypes.c_double()
+    rc = M.lib().mmf_selftest_split_tf32(m, n, k, mode, ctypes.byref(err), ctypes.byref(err32))
+    assert rc == 0, M.lib().mmf_last_error()
+    print(f"split TF32 {shape} mode {mode}: {err.value:.3e} (sequential FP32 {err32.value:.3e})")
+    assert err.value <= 2.0 ** -24 * (8 + k / 16.0)
