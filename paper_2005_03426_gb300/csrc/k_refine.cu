@@ -23,7 +23,8 @@
 // between eigenpairs far apart in the sorted order) starts from FP64 X = X1 + Dx with
 // X1 = fl32(X): G = X1^H X1 + C' + C'^H + O(|Dx|^2) with C' = X1^H Dx, the first term by the
 // same double-FP32 kernel (X1 is FP32-exact), C' on the tensor cores (|Dx| ~ 2^-24 |X|).
-// Otherwise the second step is banded (below).
+// Below that size the second step is hybrid (below): C for all pairs as in the first step, G
+// (FP64-accurate) only on the band |i - j| <= RF_W, where the near pairs need it.
 // A pair is treated as clustered when |lam_i - lam_j| <= 20 |s_ij - lam_j g_ij| (the first-order
 // correction would exceed 0.05) or the gap is below 1e-13 |H_F|; consecutive clustered indices
 // form a cluster whose eigenvectors are separated by an FP64 Jacobi solve of the small
@@ -37,8 +38,8 @@
 #define RF_KG 16   // k-chunk of the FP64-accurate Gram kernel
 #define RF_CMAX 32
 #define RF_TAU 20.0
-// Band |i - j| <= RF_W of the sorted eigenpairs: the first step applies Et there in double-FP32
-// (entries up to ~0.05), and the second step refines only inside it.
+// Band |i - j| <= RF_W of the sorted eigenpairs: every step applies Et there in double-FP32
+// (entries up to ~0.05), and the hybrid second step forms G only inside it.
 #define RF_W 16
 #define RF_BW (2 * RF_W + 1)
 static_assert(RF_BW == MMF_REFINE_BW, "band buffer width");
@@ -829,22 +830,23 @@ __global__ void __launch_bounds__(256) k_sort_pairs(const MmfDesc* __restrict__ 
     for (int r = threadIdx.x; r < n; r += blockDim.x) dst[r] = src[r];
 }
 
-// ================================================================== banded refinement step
-// After one full step, the remaining corrections between eigenpairs far apart in the sorted
-// order are second order in (eps |H| / gap) and negligible; the next step only forms G and S for
-// pairs |i - j| <= RF_W (band storage Bm[i * (2 RF_W + 1) + (j - i + RF_W)]) and applies
-// X <- X + X Et with the banded Et.
+// ================================================================== hybrid second step
+// After one full step X is accurate to second order in the FP32 iterate's error.  The second step
+// (below the size of a full one) takes C = X^H W for all pairs on the tensor cores, as the first
+// step does, but G = X^H X only on the band |i - j| <= RF_W: off the band G - I is of the size of
+// the first step's second-order error, and (lam0_j - lam_j) G_ij, the only place it enters the
+// update of a non-clustered pair, is negligible; a cluster wider than the band meets G_ij ~ 0
+// outside it, the same up to that error.  Only near pairs need G to FP64 accuracy.
 #define RF_BC 32            // columns per CTA
 #define RF_BR 16            // rows per staged chunk
 
+// G = X^H X on the band |i - j| <= RF_W in double-FP32, written into the full n x n G (column-major,
+// ld), whose other entries the caller has zeroed.
 __global__ void __launch_bounds__(256) k_gram_band_df32(const MmfDesc* __restrict__ descs,
                                                         const int* __restrict__ idx,
                                                         const double2* __restrict__ Xg,
-                                                        const double2* __restrict__ HXg,
-                                                        double2* __restrict__ Gb,
-                                                        double2* __restrict__ Sb) {
+                                                        double2* __restrict__ Gg) {
     __shared__ Split xs[RF_BR][RF_BC + 2 * RF_W + 1];
-    __shared__ Split hs[RF_BR][RF_BC + 2 * RF_W + 1];
     const MmfDesc d = descs[idx[blockIdx.y]];
     const int n = d.n;
     const int i0 = blockIdx.x * RF_BC;
@@ -852,18 +854,16 @@ __global__ void __launch_bounds__(256) k_gram_band_df32(const MmfDesc* __restric
     const int cbase = i0 - RF_W;             // first staged column
     const int ncs = RF_BC + 2 * RF_W;         // staged columns
     const double2* X = Xg + d.mat_off;
-    const double2* HX = HXg + d.mat_off;
     // each thread owns up to 5 (i, j) pairs: pair p = tid + 256 q, i = i0 + p / BW, j = i + p % BW - W
-    DF gr[5], gi[5], sr[5], si[5];
+    DF gr[5], gi[5];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) gr[q] = gi[q] = sr[q] = si[q] = DF{0.f, 0.f};
+    for (int q = 0; q < 5; ++q) gr[q] = gi[q] = DF{0.f, 0.f};
     for (int k0 = 0; k0 < n; k0 += RF_BR) {
         for (int e = threadIdx.x; e < RF_BR * ncs; e += 256) {
             const int c = e / RF_BR, kk = e - c * RF_BR;
             const int col = cbase + c, k = k0 + kk;
             const bool ok = k < n && col >= 0 && col < n;
             xs[kk][c] = split(ok ? X[(int64_t)col * d.ld + k] : make_double2(0.0, 0.0));
-            hs[kk][c] = split(ok ? HX[(int64_t)col * d.ld + k] : make_double2(0.0, 0.0));
         }
         __syncthreads();
 #pragma unroll
@@ -871,157 +871,36 @@ __global__ void __launch_bounds__(256) k_gram_band_df32(const MmfDesc* __restric
             const int p = threadIdx.x + 256 * q;
             if (p < RF_BC * RF_BW) {
                 const int ii = p / RF_BW, off = p - ii * RF_BW;  // column i0+ii, partner i0+ii+off-W
-                const int ci = ii + RF_W, cj = ii + off;            // staged indices
-                for (int kk = 0; kk < RF_BR; ++kk) {
-                    df_cmacc(gr[q], gi[q], xs[kk][ci], xs[kk][cj]);
-                    df_cmacc(sr[q], si[q], xs[kk][ci], hs[kk][cj]);
-                }
-                df_renorm(gr[q]); df_renorm(gi[q]); df_renorm(sr[q]); df_renorm(si[q]);
+                const int cix = ii + RF_W, cj = ii + off;           // staged indices
+                for (int kk = 0; kk < RF_BR; ++kk) df_cmacc(gr[q], gi[q], xs[kk][cix], xs[kk][cj]);
+                df_renorm(gr[q]); df_renorm(gi[q]);
             }
         }
         __syncthreads();
     }
+    double2* G = Gg + d.mat_off;
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const int p = threadIdx.x + 256 * q;
         if (p < RF_BC * RF_BW) {
             const int ii = p / RF_BW, off = p - ii * RF_BW;
             const int i = i0 + ii, j = i + off - RF_W;
-            if (i < n) {
-                double2 g = make_double2(0.0, 0.0), s = make_double2(0.0, 0.0);
-                if (j >= 0 && j < n) {
-                    g = make_double2((double)gr[q].hi + (double)gr[q].lo, (double)gi[q].hi + (double)gi[q].lo);
-                    s = make_double2((double)sr[q].hi + (double)sr[q].lo, (double)si[q].hi + (double)si[q].lo);
-                    if (i == j) { g.y = 0.0; s.y = 0.0; }
-                }
-                Gb[d.mat_off + (int64_t)i * RF_BW + off] = g;
-                Sb[d.mat_off + (int64_t)i * RF_BW + off] = s;
+            if (i < n && j >= 0 && j < n) {
+                double2 g = make_double2((double)gr[q].hi + (double)gr[q].lo, (double)gi[q].hi + (double)gi[q].lo);
+                if (i == j) g.y = 0.0;
+                G[(int64_t)j * d.ld + i] = g;
             }
         }
     }
 }
 
-// band entry (i, j) with |i - j| <= W (0 outside the matrix)
-__device__ __forceinline__ double2 band_at(const double2* B, int i, int j) {
-    return B[(int64_t)i * RF_BW + (j - i + RF_W)];
-}
-
-__global__ void __launch_bounds__(256) k_oa_lambda_band(const MmfDesc* __restrict__ descs,
-                                                        const int* __restrict__ idx,
-                                                        const double2* __restrict__ Gbg,
-                                                        const double2* __restrict__ Sbg,
-                                                        double* __restrict__ lamg,
-                                                        int* __restrict__ cidg) {
-    const MmfDesc d = descs[idx[blockIdx.x]];
-    const int n = d.n;
-    const double2* G = Gbg + d.mat_off;
-    const double2* S = Sbg + d.mat_off;
-    double* lam = lamg + d.vec_off;
-    int* cid = cidg + d.vec_off;
-    __shared__ double hmax;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = band_at(S, i, i).x / band_at(G, i, i).x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int i = 0; i < n; ++i) m = fmax(m, fabs(lam[i]));
-        hmax = m;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        int link = 0;
-        if (i + 1 < n) {
-            const double gap = fabs(lam[i + 1] - lam[i]);
-            const double2 num = band_at(S, i, i + 1) - lam[i + 1] * band_at(G, i, i + 1);
-            link = (gap <= RF_TAU * sqrt(abs2(num))) || (gap <= 1e-13 * hmax);
-        }
-        cid[i] = link;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int start = 0, prev = 0;
-        for (int i = 0; i < n; ++i) {
-            const int link = cid[i];
-            if (i == 0 || !prev) start = i;
-            cid[i] = start;
-            prev = link;
-        }
-    }
-}
-
-// Xn(:, j) = X(:, j) + sum_{|i-j|<=W} X(:, i) Et(i, j)   (Et formed on the fly from the band)
-// Banded step: Xn(:, j) = X(:, j) + sum_{|i-j|<=W} X1(:, i) Et(i, j) in FP32 (Et here is the
-// second step's small correction), Et formed from the band of G and S; tiled like k_xe_apply.
-__global__ void __launch_bounds__(256) k_xe_band(const MmfDesc* __restrict__ descs,
-                                                 const int* __restrict__ idx,
-                                                 const double2* __restrict__ Xg,
-                                                 const float2* __restrict__ X1g,
-                                                 const double2* __restrict__ Gbg,
-                                                 const double2* __restrict__ Sbg,
-                                                 const double* __restrict__ lamg,
-                                                 const int* __restrict__ cidg,
-                                                 double2* __restrict__ Xn) {
-    __shared__ float2 xs[XT_C + 2 * RF_W][XT_R];
-    __shared__ float2 es[RF_BW][XT_C];
-    const MmfDesc d = descs[idx[blockIdx.z]];
-    const int n = d.n;
-    const int r0 = blockIdx.x * XT_R, j0 = blockIdx.y * XT_C;
-    if (r0 >= n || j0 >= n) return;
-    const double2* G = Gbg + d.mat_off;
-    const double2* S = Sbg + d.mat_off;
-    const double* lam = lamg + d.vec_off;
-    const int* cid = cidg + d.vec_off;
-    const float2* X1 = X1g + d.mat_off;
-    for (int e = threadIdx.x; e < (XT_C + 2 * RF_W) * XT_R; e += 256) {
-        const int cc = e / XT_R, rr = e - cc * XT_R, col = j0 - RF_W + cc, row = r0 + rr;
-        xs[cc][rr] = (col >= 0 && col < n && row < n) ? X1[(int64_t)col * d.ld + row] : make_float2(0.f, 0.f);
-    }
-    const double hmax = fmax(fabs(lam[0]), fabs(lam[n - 1]));
-    for (int e = threadIdx.x; e < RF_BW * XT_C; e += 256) {
-        const int q = e / XT_C, c = e - q * XT_C, j = j0 + c, i = j + q - RF_W;
-        float2 v = make_float2(0.f, 0.f);
-        if (j < n && i >= 0 && i < n) {
-            const double2 g = band_at(G, i, j);
-            double2 et;
-            if (i == j) {
-                et = make_double2(0.5 * (1.0 - g.x), 0.0);
-            } else {
-                const double2 num = band_at(S, i, j) - lam[j] * g;
-                const double gap = lam[j] - lam[i];
-                const bool clustered = cid[i] == cid[j] || fabs(gap) <= RF_TAU * sqrt(abs2(num)) ||
-                                       fabs(gap) <= 1e-13 * fmax(hmax, fabs(lam[i]));
-                et = clustered ? (-0.5) * g : (1.0 / gap) * num;
-            }
-            v = make_float2(__double2float_rn(et.x), __double2float_rn(et.y));
-        }
-        es[q][c] = v;
-    }
-    __syncthreads();
-    const int rr = threadIdx.x & (XT_R - 1), cg = threadIdx.x / XT_R;
-    const int r = r0 + rr;
-    if (r >= n) return;
-    const double2* X = Xg + d.mat_off;
-#pragma unroll 1
-    for (int c = cg * XT_CPT; c < cg * XT_CPT + XT_CPT; ++c) {
-        const int j = j0 + c;
-        if (j >= n) break;
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int q = 0; q < RF_BW; ++q) {
-            const float2 xf = xs[c + q][rr], e = es[q][c];
-            acc.x = fmaf(xf.x, e.x, fmaf(-xf.y, e.y, acc.x));
-            acc.y = fmaf(xf.x, e.y, fmaf(xf.y, e.x, acc.y));
-        }
-        const double2 x = X[(int64_t)j * d.ld + r];
-        Xn[d.mat_off + (int64_t)j * d.ld + r] = make_double2(x.x + (double)acc.x, x.y + (double)acc.y);
-    }
-}
 
 // The refinement is launched in parts so that the host can time the FP64-accurate Gram product
 // on its own and choose the second step per system:
 //   pre:    HX = H_F X, C = X^H W (and C' = X1^H Dx for a second full step) on the tensor cores
 //   gram:   G = X1^H X1 in double-FP32 (+ C' + C'^H)
 //   update: lam, Et, X <- X + X Et, cluster separation
-//   band:   the banded second step;   finish: final ordering.
+//   band_g: G on the band for the hybrid second step;   finish: final ordering.
 cudaError_t mmf_launch_refine_split_coef(const double2* coef, float4* cs, int64_t count, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     k_split_coef<<<(int)std::min<int64_t>((count + 255) / 256, 1024), 256, 0, st>>>(coef, cs, count);
@@ -1047,7 +926,7 @@ cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const float4* cs, const do
     k_w_prep_A<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X1, ops);
     k_w_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, ops, T, 0, (Tf3Job*)jobs);
     cudaError_t e = mmf_launch_tf3(jobs, L.count, L.nmax, 2 * L.nmax, status, L.stream);
-    if (e != cudaSuccess || !second) return e;
+    if (e != cudaSuccess || second != 1) return e;
     k_d_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, ops);
     k_w_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, ops, T, 1, (Tf3Job*)jobs);
     return mmf_launch_tf3(jobs, L.count, L.nmax, 2 * L.nmax, status, L.stream);
@@ -1092,19 +971,11 @@ cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, do
     return cudaGetLastError();
 }
 
-cudaError_t mmf_launch_refine_band(const MmfLaunch& L, const double2* coef, const float4* cs, double2* X,
-                                   double2* G, double2* S, double2* HX, double2* T, float2* X1, double* lam,
-                                   int* status, int* cid, int64_t mat_elems) {
+cudaError_t mmf_launch_refine_band_g(const MmfLaunch& L, const double2* X, double2* G, int64_t mat_elems) {
     if (L.count <= 0) return cudaSuccess;
-    apply_hf(L, cs, X, X1, reinterpret_cast<float2*>(T), HX);
-    k_gram_band_df32<<<dim3((L.nmax + RF_BC - 1) / RF_BC, L.count), 256, 0, L.stream>>>(
-        L.desc, L.idx, X, HX, G, S);
-    k_oa_lambda_band<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, S, lam, cid);
-    k_xe_band<<<dim3((L.nmax + XT_R - 1) / XT_R, (L.nmax + XT_C - 1) / XT_C, L.count), 256, 0, L.stream>>>(
-        L.desc, L.idx, X, X1, G, S, lam, cid, HX);
-    cudaError_t e = cudaMemcpyAsync(X, HX, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
+    cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double2) * mat_elems, L.stream);
     if (e != cudaSuccess) return e;
-    k_cluster_sep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, coef, X, HX, lam, cid, status);
+    k_gram_band_df32<<<dim3((L.nmax + RF_BC - 1) / RF_BC, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, G);
     return cudaGetLastError();
 }
 

@@ -77,7 +77,7 @@ struct mmf_batch {
     std::vector<mmf_sys*> sys;
     std::vector<MmfDesc> desc;
     std::vector<int> all, small, large, medium, huge;  // large = medium + huge
-    std::vector<int> rband, rfull;                     // mixed: banded / full second refinement step
+    std::vector<int> rband, rfull;                     // mixed: hybrid / full second refinement step
     std::vector<int> btc, bts;                         // large: back-transform on tensor cores / SIMT
     std::vector<int> btc_n;                            // n of each system in btc
     int nmax_btc = 0, nmax_bts = 0;
@@ -796,16 +796,22 @@ static int stage_eig(mmf_batch* b) {
         LAUNCH(mmf_launch_refine_update(La, b->d_coef, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_HX, b->d_T, b->d_E2,
                                         b->d_status, b->d_cid, b->n_mat, b->d_oz, b->d_jobs, b->d_Eb),
                9);
+        // second step from lam0 = the first step's eigenvalues (E is rewritten at the end)
+        CU(cudaMemcpyAsync(b->d_E, b->d_E2, sizeof(double) * b->n_vec, cudaMemcpyDeviceToDevice, b->stream));
         if (!b->rband.empty()) {
+            // hybrid: C = X1^H W for all pairs on the tensor cores, G only on the band
             MmfLaunch Lb = launch_of(b, b->rband, b->d_rband, b->nmax_rband);
-            LAUNCH(mmf_launch_refine_band(Lb, b->d_coef, b->d_coefs, b->d_Zf, b->d_R, b->d_S, b->d_HX, b->d_T,
-                                          b->d_X1, b->d_E2, b->d_status, b->d_cid, b->n_mat),
+            LAUNCH(mmf_launch_refine_pre(Lb, b->d_coefs, b->d_Zf, b->d_E, b->d_HX, b->d_T, b->d_X1, b->d_oz,
+                                         b->d_jobs, b->d_status, 2),
                    6);
+            LAUNCH(mmf_launch_refine_band_g(Lb, b->d_Zf, b->d_R, b->n_mat), 1);
+            LAUNCH(mmf_launch_refine_update(Lb, b->d_coef, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_HX, b->d_T,
+                                            b->d_E2, b->d_status, b->d_cid, b->n_mat, b->d_oz, b->d_jobs, b->d_Eb),
+                   9);
         }
         if (!b->rfull.empty()) {
-            // second full step from lam0 = the first step's eigenvalues (E is rewritten at the end)
+            // full second step: G of the FP64 iterate as G(X1) + C' + C'^H
             MmfLaunch Lf = launch_of(b, b->rfull, b->d_rfull, b->nmax_rfull);
-            CU(cudaMemcpyAsync(b->d_E, b->d_E2, sizeof(double) * b->n_vec, cudaMemcpyDeviceToDevice, b->stream));
             LAUNCH(mmf_launch_refine_pre(Lf, b->d_coefs, b->d_Zf, b->d_E, b->d_HX, b->d_T, b->d_X1, b->d_oz,
                                          b->d_jobs, b->d_status, 1),
                    9);

@@ -218,9 +218,8 @@ cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, do
                                      const double* lam0, double2* G, double2* HX, const double2* T, double* lam,
                                      int* status, int* cid, int64_t mat_elems, void* ops, void* jobs,
                                      double2* Eb);
-cudaError_t mmf_launch_refine_band(const MmfLaunch& L, const double2* coef, const float4* cs, double2* X,
-                                   double2* G, double2* S, double2* HX, double2* T, float2* X1, double* lam,
-                                   int* status, int* cid, int64_t mat_elems);
+// hybrid second step: G = X^H X on the band |i - j| <= 16 (double-FP32) into the zeroed full G
+cudaError_t mmf_launch_refine_band_g(const MmfLaunch& L, const double2* X, double2* G, int64_t mat_elems);
 cudaError_t mmf_launch_refine_finish(const MmfLaunch& L, double2* X, double* E, const double* lam, double2* S,
                                      int64_t mat_elems);
 // Gram product on the BF16 tensor cores by exact integer slicing (k_ozaki.cu)
