@@ -167,9 +167,11 @@ __global__ void __launch_bounds__(256) k_transition_avg(const MmfDesc* __restric
 }
 
 // Staged launcher with explicit maxima (the batch knows them).
+// skip_u: the phase table and the FP32 pieces of Z are prepared, but U is left to the
+// tensor-core path (mmf_launch_phi)
 cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const double* E,
                                   const double2* Z, float2* Z1, float2* Zlo, const double* t, double t0, int nt,
-                                  double2* F2, double2* U, double* P, double cluster_rel) {
+                                  double2* F2, double2* U, double* P, double cluster_rel, int skip_u) {
     static_assert(sizeof(Split) == sizeof(double2), "phase table slots hold one Split each");
     Split* F = reinterpret_cast<Split*>(F2);
     if (L.count <= 0) return cudaSuccess;
@@ -178,8 +180,9 @@ cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const dou
         if (gx > 1024) gx = 1024;
         k_phase_table<<<dim3(gx, L.count), 256, 0, L.stream>>>(L.desc, L.idx, t, nt, F);
         k_split_z<<<dim3(128, L.count), 256, 0, L.stream>>>(L.desc, L.idx, Z, Z1, Zlo);
-        k_time_evolution<<<dim3((L.nmax + 31) / 32, L.count), 256, 0, L.stream>>>(
-            L.desc, L.idx, E, Z, Z1, Zlo, t, t0, nt, F, U);
+        if (!skip_u)
+            k_time_evolution<<<dim3((L.nmax + 31) / 32, L.count), 256, 0, L.stream>>>(
+                L.desc, L.idx, E, Z, Z1, Zlo, t, t0, nt, F, U);
     }
     size_t sm = sizeof(double) * (size_t)(Dmax * Dmax + 8 * Dmax);
     if (sm > 48 * 1024) {

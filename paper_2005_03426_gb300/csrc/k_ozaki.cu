@@ -417,6 +417,453 @@ cudaError_t mmf_launch_ozaki_gram(const MmfLaunch& L, const float2* X1, void* S,
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ time evolution (Eq. 3-5)
+// Phi_j(t, l) = sum_b F(t, b) Z[(j, b), l] for every level j, eigenvector l and time t, by the
+// same exact slicing: A rows r = j n + l hold a_r = [Re Z((j, b), l) | Im Z((j, b), l)] over b
+// (K = 2M), B rows t hold [Re F(t, b) | -Im F(t, b)] and B' rows [Im F(t, b) | Re F(t, b)], so
+// that a_r . b_t = Re Phi and a_r . b'_t = Im Phi.  Z (FP64) is sliced from its FP32 pieces
+// Z1 + Zlo in double-FP32 (each step 64 t - rint(64 t) exact, the pair renormalised by TwoSum),
+// F from its pre-split phase table.  Phi goes to FP64 (error below ~2^-40 of each row's largest
+// |Z| times sum_b |F|); U(t, t0)[j, i] = sum_l Phi_j(t, l) e^{-i E_l (t - t0)} conj(Z[(i, b0), l])
+// follows in FP64.  The operands and Phi live in the system's operand area.
+struct PhiLayout {
+    int ra, nqa, nqb, ntk;           // A rows (D n), 64-row panels of A (even) and B, K tiles
+    int64_t sa, sb, ea, eb, phi, total;  // offsets in BF16 units from the area's start
+};
+__host__ __device__ inline PhiLayout phi_layout(int n, int D, int M, int nt) {
+    PhiLayout o;
+    o.ra = D * n;
+    o.nqa = ((o.ra + 63) / 64 + 1) / 2 * 2;
+    o.nqb = (nt + 63) / 64;
+    o.ntk = (2 * M + OZ_KSTEP - 1) / OZ_KSTEP;
+    o.sa = 0;
+    o.sb = o.sa + (int64_t)OZ_S * o.ntk * o.nqa * OZ_TILE_ELEMS;
+    o.ea = o.sb + (int64_t)2 * OZ_S * o.ntk * o.nqb * OZ_TILE_ELEMS;  // int exponents of A rows
+    o.eb = o.ea + (int64_t)2 * o.nqa * 64;                             // int exponents of B rows
+    o.phi = (o.eb + (int64_t)2 * o.nqb * 64 + 7) / 8 * 8;              // double2, 16-byte aligned
+    o.total = o.phi + (int64_t)8 * o.ra * nt;
+    return o;
+}
+
+// place of the 16-byte chunk j (K entries 8j .. 8j+7 of a 64-K tile) of row r in a 64-row panel
+__device__ __forceinline__ int64_t oz_inner(int r, int j) {
+    return (int64_t)(r >> 3) * 512 + (r & 7) * 64 + ((j ^ (r & 7)) << 3);
+}
+
+// OZ_S slices of eight scaled entries given as double-FP32 pairs (t1 + t2, |t1 + t2| < 1)
+__device__ __forceinline__ void oz_slices8(float* t1, float* t2, uint4* out) {
+#pragma unroll
+    for (int sl = 0; sl < OZ_S; ++sl) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            float v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float x = t1[u + h] * 64.f;   // exact
+                const float r = rintf(x);
+                const float a = x - r;               // exact
+                const float b = t2[u + h] * 64.f;    // exact
+                const float s = a + b;               // TwoSum: (s, err) = a + b exactly
+                const float bb = s - a;
+                t1[u + h] = s;
+                t2[u + h] = (a - (s - bb)) + (b - bb);
+                v[h] = r;
+            }
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(v[0], v[1]);
+            pk[u >> 1] = *reinterpret_cast<const uint32_t*>(&hv);
+        }
+        out[sl] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+}
+
+// A slices: one warp per row r = j n + l (rows past D n are zero)
+__global__ void __launch_bounds__(256) k_phi_slice_a(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
+                                                     const float2* __restrict__ Z1g, const float2* __restrict__ Zlog,
+                                                     uint16_t* __restrict__ pool, int nt) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const PhiLayout o = phi_layout(d.n, d.D, d.M, nt);
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= o.nqa * 64) return;
+    uint16_t* W = pool + d.oz_off;
+    const bool live = r < o.ra;
+    const int j = live ? r / d.n : 0, l = live ? r - j * d.n : 0;
+    const float2* z1 = Z1g + d.mat_off + (int64_t)l * d.ld + j;
+    const float2* zl = Zlog + d.mat_off + (int64_t)l * d.ld + j;
+    const int M = d.M, D = d.D;
+    float m = 0.f;
+    if (live)
+        for (int b = lane; b < M; b += 32) {
+            const float2 z = z1[b * D];
+            m = fmaxf(m, fmaxf(fabsf(z.x), fabsf(z.y)));
+        }
+    for (int q = 16; q > 0; q >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, q));
+    int e = 0;
+    if (m > 0.f) frexpf(m, &e);  // |z| 2^-e < 1 (also for z1 + zlo, see the comment above)
+    if (live && lane == 0) reinterpret_cast<int*>(W + o.ea)[r] = e;
+    const float sc = ldexpf(1.f, -e);
+    __nv_bfloat16* SA = reinterpret_cast<__nv_bfloat16*>(W + o.sa);
+    const int q = r >> 6, rr = r & 63;
+    for (int jc = lane; jc < o.ntk * 8; jc += 32) {
+        const int k0 = jc * 8;
+        float t1[8], t2[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + u;
+            float a = 0.f, b = 0.f;
+            if (live && k < 2 * M) {
+                const int bb = k < M ? k : k - M;
+                const float2 h = z1[bb * D], lo = zl[bb * D];
+                a = k < M ? h.x : h.y;
+                b = k < M ? lo.x : lo.y;
+            }
+            t1[u] = a * sc;
+            t2[u] = b * sc;
+        }
+        uint4 sl[OZ_S];
+        oz_slices8(t1, t2, sl);
+        const int t = k0 >> 6, jj = (k0 & 63) >> 3;
+#pragma unroll
+        for (int s = 0; s < OZ_S; ++s)
+            *reinterpret_cast<uint4*>(SA + (((int64_t)s * o.ntk + t) * o.nqa + q) * OZ_TILE_ELEMS + oz_inner(rr, jj)) =
+                sl[s];
+    }
+}
+
+// B and B' slices from the phase table (F[t][b] in FP32 pieces): one warp per time row
+__global__ void __launch_bounds__(256) k_phi_slice_b(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
+                                                     const Split* __restrict__ Fg, uint16_t* __restrict__ pool,
+                                                     int nt) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const PhiLayout o = phi_layout(d.n, d.D, d.M, nt);
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= o.nqb * 64) return;
+    uint16_t* W = pool + d.oz_off;
+    const bool live = t < nt;
+    const Split* F = Fg + d.f_off + (int64_t)(live ? t : 0) * d.M;
+    const int M = d.M;
+    float m = 0.f;
+    if (live)
+        for (int b = lane; b < M; b += 32) m = fmaxf(m, fmaxf(fabsf(F[b].r1), fabsf(F[b].i1)));
+    for (int q = 16; q > 0; q >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, q));
+    int e = 0;
+    if (m > 0.f) frexpf(m, &e);
+    if (live && lane == 0) reinterpret_cast<int*>(W + o.eb)[t] = e;
+    const float sc = ldexpf(1.f, -e);
+    __nv_bfloat16* SB = reinterpret_cast<__nv_bfloat16*>(W + o.sb);
+    const int q = t >> 6, rr = t & 63;
+    for (int jc = lane; jc < o.ntk * 8; jc += 32) {
+        const int k0 = jc * 8;
+        float a1[8], a2[8], c1[8], c2[8];  // B (Re F | -Im F) and B' (Im F | Re F)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + u;
+            float x1 = 0.f, x2 = 0.f, y1 = 0.f, y2 = 0.f;
+            if (live && k < 2 * M) {
+                const Split f = F[k < M ? k : k - M];
+                if (k < M) { x1 = f.r1; x2 = f.r2; y1 = f.i1; y2 = f.i2; }
+                else       { x1 = -f.i1; x2 = -f.i2; y1 = f.r1; y2 = f.r2; }
+            }
+            a1[u] = x1 * sc; a2[u] = x2 * sc;
+            c1[u] = y1 * sc; c2[u] = y2 * sc;
+        }
+        uint4 sl[OZ_S];
+        const int tk = k0 >> 6, jj = (k0 & 63) >> 3;
+        oz_slices8(a1, a2, sl);
+#pragma unroll
+        for (int s = 0; s < OZ_S; ++s)
+            *reinterpret_cast<uint4*>(SB + (((int64_t)s * o.ntk + tk) * o.nqb + q) * OZ_TILE_ELEMS + oz_inner(rr, jj)) =
+                sl[s];
+        oz_slices8(c1, c2, sl);
+#pragma unroll
+        for (int s = 0; s < OZ_S; ++s)
+            *reinterpret_cast<uint4*>(SB + (((int64_t)(OZ_S + s) * o.ntk + tk) * o.nqb + q) * OZ_TILE_ELEMS +
+                                      oz_inner(rr, jj)) = sl[s];
+    }
+}
+
+// Phi on the tensor cores: one CTA per 128 (rows r) x 64 (times) tile, roles as in k_oz_gram
+__global__ void __launch_bounds__(OZ_WARPS * 32, 1) k_oz_phi(const MmfDesc* __restrict__ descs,
+                                                             const int* __restrict__ idx, uint16_t* __restrict__ pool,
+                                                             int nt, int nqb_max, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char oz_smem[];
+    __shared__ uint64_t full[OZ_STAGES], empty[OZ_STAGES], accfull[2], accempty[2];
+    __shared__ uint32_t tmem_s;
+    __shared__ int abort_s;
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const PhiLayout o = phi_layout(d.n, d.D, d.M, nt);
+    const int I = blockIdx.x / nqb_max, J = blockIdx.x - I * nqb_max;
+    if (2 * I >= o.nqa || J >= o.nqb) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* base = (unsigned char*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(base);
+    volatile int* abort_flag = &abort_s;
+    if (threadIdx.x == 0) {
+        abort_s = 0;
+        for (int q = 0; q < OZ_STAGES; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&accfull[q], 1);
+            mbar_init(&accempty[q], 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
+                     "r"(OZ_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_s;
+    const int la = o.ntk * OZ_KSTEP;
+    const int nkc = (la + OZ_KCH - 1) / OZ_KCH;      // K chunks per pair
+    const int npairs = (OZ_L + 1) * (OZ_L + 2) / 2;  // pairs a + b <= OZ_L
+    const uint16_t* W = pool + d.oz_off;
+    const __nv_bfloat16* SA = reinterpret_cast<const __nv_bfloat16*>(W + o.sa);
+    const __nv_bfloat16* SB = reinterpret_cast<const __nv_bfloat16*>(W + o.sb);
+    const int ntk = o.ntk;
+
+    if (warp == 4) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int a = 0; a <= OZ_L; ++a)
+                for (int b = 0; a + b <= OZ_L; ++b)
+                    for (int t = 0; t < ntk; ++t, ++it) {
+                        const int st = (int)(it % OZ_STAGES);
+                        const uint32_t use = it / OZ_STAGES;
+                        if (use > 0 && !oz_wait(&empty[st], (use - 1) & 1u, abort_flag)) goto phi_producer_done;
+                        const uint32_t fb = smem_u32(&full[st]);
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                                     "r"((uint32_t)OZ_STAGE_BYTES)
+                                     : "memory");
+                        const uint32_t dst = sbase + (uint32_t)st * OZ_STAGE_BYTES;
+                        const __nv_bfloat16* srcA = SA + (((int64_t)a * ntk + t) * o.nqa + 2 * I) * OZ_TILE_ELEMS;
+                        const __nv_bfloat16* srcB = SB + (((int64_t)b * ntk + t) * o.nqb + J) * OZ_TILE_ELEMS;
+                        const __nv_bfloat16* srcBp =
+                            SB + (((int64_t)(OZ_S + b) * ntk + t) * o.nqb + J) * OZ_TILE_ELEMS;
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                dst),
+                            "l"(srcA), "r"(16384u), "r"(fb)
+                            : "memory");
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                dst + 16384u),
+                            "l"(srcB), "r"(8192u), "r"(fb)
+                            : "memory");
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                dst + 24576u),
+                            "l"(srcBp), "r"(8192u), "r"(fb)
+                            : "memory");
+                    }
+        phi_producer_done:;
+        }
+    } else if (warp == 5) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc_mn(1, OZ_TM, OZ_TN);
+            uint32_t it = 0;
+            int c = 0;
+            bool ok = true;
+            for (int p = 0; p < npairs && ok; ++p)
+                for (int kc = 0; kc < nkc && ok; ++kc, ++c) {
+                    const int buf = c & 1;
+                    const uint32_t v = (uint32_t)c >> 1;
+                    if (v > 0 && !oz_wait(&accempty[buf], (v - 1) & 1u, abort_flag)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t dre = tmem + (uint32_t)buf * 128u, dim = dre + OZ_TN;
+                    const int t0 = kc * (OZ_KCH / OZ_KSTEP), t1 = min(ntk, t0 + OZ_KCH / OZ_KSTEP);
+                    for (int t = t0; t < t1; ++t, ++it) {
+                        const int st = (int)(it % OZ_STAGES);
+                        if (!oz_wait(&full[st], (it / OZ_STAGES) & 1u, abort_flag)) { ok = false; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t sa = sbase + (uint32_t)st * OZ_STAGE_BYTES;
+                        const uint64_t da = umma_desc(sa), db = umma_desc(sa + 16384u), dbp = umma_desc(sa + 24576u);
+#pragma unroll
+                        for (int q = 0; q < OZ_KSTEP / 16; ++q) {  // 32 bytes of K per instruction
+                            const uint32_t accf = (t > t0 || q > 0) ? 1u : 0u;
+                            const uint64_t adv = (uint64_t)((q * 32) >> 4);
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dre),
+                                "l"(da + adv), "l"(db + adv), "r"(idesc), "r"(accf)
+                                : "memory");
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dim),
+                                "l"(da + adv), "l"(dbp + adv), "r"(idesc), "r"(accf)
+                                : "memory");
+                        }
+                        oz_commit(&empty[st]);
+                    }
+                    if (!ok) break;
+                    oz_commit(&accfull[buf]);
+                }
+        }
+    } else {
+        // ---------------------------------------------------------------- drain (warps 0-3)
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        {
+            uint32_t z[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) z[q] = 0u;
+#pragma unroll 1
+            for (int col = OZ_COL_LO; col < OZ_COL_HI + 2 * OZ_TN; col += 32) tm_st32(trow + (uint32_t)col, z);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        int c = 0;
+        bool ok = true;
+        for (int a = 0; a <= OZ_L && ok; ++a)
+            for (int b = 0; a + b <= OZ_L && ok; ++b) {
+                const int sh = 6 * (OZ_L - a - b) - 6;
+                for (int kc = 0; kc < nkc; ++kc, ++c) {
+                    const int buf = c & 1;
+                    if (!oz_wait(&accfull[buf], ((uint32_t)c >> 1) & 1u, abort_flag)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+                    for (int g = 0; g < 2 * OZ_TN; g += 32) {
+                        uint32_t v[32], lo[32], hi[32];
+                        tm_ld32(trow + (uint32_t)(buf * 128 + g), v);
+                        tm_ld32(trow + (uint32_t)(OZ_COL_LO + g), lo);
+                        tm_ld32(trow + (uint32_t)(OZ_COL_HI + g), hi);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            const long long iv = __float2ll_rn(__uint_as_float(v[q]));  // an exact integer
+                            const long long term = sh >= 0 ? (iv << sh) : (iv >> (-sh));
+                            const long long acc64 = (long long)(((unsigned long long)hi[q] << 32) | lo[q]) + term;
+                            lo[q] = (uint32_t)(unsigned long long)acc64;
+                            hi[q] = (uint32_t)((unsigned long long)acc64 >> 32);
+                        }
+                        tm_st32(trow + (uint32_t)(OZ_COL_LO + g), lo);
+                        tm_st32(trow + (uint32_t)(OZ_COL_HI + g), hi);
+                    }
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&accempty[buf]))
+                                 : "memory");
+                }
+            }
+        if (ok) {
+            const int r = I * OZ_TM + warp * 32 + lane;
+            const int* ea = reinterpret_cast<const int*>(W + o.ea);
+            const int* eb = reinterpret_cast<const int*>(W + o.eb);
+            double2* Phi = reinterpret_cast<double2*>(pool + d.oz_off + o.phi);
+            const int er = r < o.ra ? ea[r] : 0;
+#pragma unroll 1
+            for (int g = 0; g < OZ_TN; g += 32) {
+                uint32_t rlo[32], rhi[32], ilo[32], ihi[32];
+                tm_ld32(trow + (uint32_t)(OZ_COL_LO + g), rlo);
+                tm_ld32(trow + (uint32_t)(OZ_COL_HI + g), rhi);
+                tm_ld32(trow + (uint32_t)(OZ_COL_LO + OZ_TN + g), ilo);
+                tm_ld32(trow + (uint32_t)(OZ_COL_HI + OZ_TN + g), ihi);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (r < o.ra) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int t = J * OZ_TN + g + q;
+                        if (t < nt) {
+                            const int sc = er + eb[t] - 6 * (OZ_L + 2) + 6;
+                            const long long ar = (long long)(((unsigned long long)rhi[q] << 32) | rlo[q]);
+                            const long long ai = (long long)(((unsigned long long)ihi[q] << 32) | ilo[q]);
+                            Phi[(int64_t)r * nt + t] = make_double2(ldexp((double)ar, sc), ldexp((double)ai, sc));
+                        }
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && abort_s) atomicExch(err, 1);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS)
+                     : "memory");
+}
+
+// U(t, t0)[j, i] += sum over the CTA's 32 eigenvectors l of Phi_j(t, l) e^{-i E_l (t - t0)} conj(Z0(i, l)),
+// FP64; CTA (eigenvector chunk, 64-time chunk); thread (t, j) keeps the D sums over i
+#define PU_L 32
+#define PU_T 64
+#define PU_DMAX 16  // levels per system on this path (more take the double-FP32 kernel)
+__global__ void __launch_bounds__(256) k_phi_u(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
+                                               const uint16_t* __restrict__ pool, const double* __restrict__ Eg,
+                                               const double2* __restrict__ Zg, const double* __restrict__ tpool,
+                                               double t0, int nt, double2* __restrict__ U) {
+    __shared__ double2 ph[PU_L][PU_T];
+    __shared__ double2 z0[PU_L][PU_DMAX];
+    const MmfDesc d = descs[idx[blockIdx.z]];
+    const int n = d.n, D = d.D;
+    const int l0 = blockIdx.x * PU_L, tb = blockIdx.y * PU_T;
+    if (l0 >= n || tb >= nt) return;
+    const int nl = min(PU_L, n - l0), ntt = min(PU_T, nt - tb);
+    const PhiLayout o = phi_layout(n, D, d.M, nt);
+    const double2* Phi = reinterpret_cast<const double2*>(pool + d.oz_off + o.phi);
+    for (int e = threadIdx.x; e < PU_L * PU_T; e += blockDim.x) {
+        const int a = e / PU_T, tt = e - a * PU_T;
+        double s = 0.0, c = 1.0;
+        if (a < nl && tt < ntt) sincos(Eg[d.vec_off + l0 + a] * (tpool[d.t_off + tb + tt] - t0), &s, &c);
+        ph[a][tt] = make_double2(c, -s);
+    }
+    for (int e = threadIdx.x; e < PU_L * D; e += blockDim.x) {
+        const int a = e / D, i = e - a * D;
+        z0[a][i] = a < nl ? Zg[d.mat_off + (int64_t)(l0 + a) * d.ld + i + D * d.b0] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < ntt * D; task += blockDim.x) {
+        const int tt = task % ntt, j = task / ntt;
+        double2 acc[PU_DMAX];
+#pragma unroll
+        for (int i = 0; i < PU_DMAX; ++i) acc[i] = make_double2(0.0, 0.0);
+        for (int a = 0; a < nl; ++a) {
+            const double2 f = Phi[((int64_t)j * n + l0 + a) * nt + tb + tt] * ph[a][tt];
+#pragma unroll
+            for (int i = 0; i < PU_DMAX; ++i)
+                if (i < D) acc[i] = acc[i] + cmulc(z0[a][i], f);
+        }
+        double2* u = U + d.u_off + ((int64_t)(tb + tt) * D + j) * D;
+#pragma unroll
+        for (int i = 0; i < PU_DMAX; ++i)
+            if (i < D) {
+                atomicAdd(&u[i].x, acc[i].x);
+                atomicAdd(&u[i].y, acc[i].y);
+            }
+    }
+}
+
+int64_t mmf_phi_elems(int n, int D, int M, int nt) { return phi_layout(n, D, M, nt).total; }
+
+int mmf_phi_max_levels() { return PU_DMAX; }
+
+cudaError_t mmf_launch_phi(const MmfLaunch& L, int Dmax, int nt, const float2* Z1, const float2* Zlo,
+                           const void* F, const double* E, const double2* Z, const double* t, double t0, void* pool,
+                           double2* U, int* err) {
+    if (L.count <= 0 || nt <= 0) return cudaSuccess;
+    if (Dmax > PU_DMAX) return cudaErrorInvalidValue;
+    uint16_t* P = (uint16_t*)pool;
+    const int rowsA = ((Dmax * L.nmax + 63) / 64 + 1) / 2 * 2 * 64;
+    const int nqb = (nt + 63) / 64;
+    k_phi_slice_a<<<dim3((rowsA + 7) / 8, L.count), 256, 0, L.stream>>>(L.desc, L.idx, Z1, Zlo, P, nt);
+    k_phi_slice_b<<<dim3(nqb * 8, L.count), 256, 0, L.stream>>>(L.desc, L.idx, (const Split*)F, P, nt);
+    const size_t sm = (size_t)OZ_STAGES * OZ_STAGE_BYTES + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_oz_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int nI = rowsA / 128;
+    k_oz_phi<<<dim3(nI * nqb, L.count), OZ_WARPS * 32, sm, L.stream>>>(L.desc, L.idx, P, nt, nqb, err);
+    k_phi_u<<<dim3((L.nmax + PU_L - 1) / PU_L, (nt + PU_T - 1) / PU_T, L.count), 256, 0, L.stream>>>(
+        L.desc, L.idx, P, E, Z, t, t0, nt, U);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ self-test
 // G of one seeded n x n FP32 matrix (columns of unit norm, entries spread over several orders
 // of magnitude) against an FP64 reference; returns the largest |G - G_ref|.

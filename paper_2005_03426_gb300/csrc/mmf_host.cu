@@ -423,10 +423,13 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         d.oz_off = b->n_oz;
         // mixed: back-transform on the tensor cores for large enough systems (SIMT otherwise)
         const bool tc = precision == MMF_MIXED && !d.small && n >= std::max<int64_t>(bt_tc_n(ctx), 3);
-        if (precision == MMF_MIXED) {  // Gram slices (BF16) and split-TF32 operands share the area
+        if (precision == MMF_MIXED) {
+            // one area per system, used in turn by the back-transform's operands, the Gram slices
+            // (BF16) and split-TF32 operands of the refinement, and the time evolution's slices and Phi
             const int64_t oz = ctx->gram_kernel == 0 ? (int64_t)mmf_ozaki_slice_elems((int)n) : 0;
+            const int64_t ph = (nt > 0 && s->D <= mmf_phi_max_levels()) ? mmf_phi_elems((int)n, s->D, (int)M, nt) : 0;
             b->n_oz += std::max<int64_t>(std::max<int64_t>(oz, 2 * mmf_tf3_floats((int)n)),
-                                         tc ? 2 * mmf_bt_floats((int)n) : 0);
+                                         std::max<int64_t>(tc ? 2 * mmf_bt_floats((int)n) : 0, ph));
         }
         if (!d.small) {
             (tc ? b->btc : b->bts).push_back(i);
@@ -838,9 +841,15 @@ static int stage_outputs(mmf_batch* b) {
     // FP32 pieces of Z: the mixed path reuses the refinement's X1 and T buffers (free by now)
     float2* Z1 = b->precision == MMF_MIXED ? b->d_X1 : b->d_Zs;
     float2* Zlo = b->precision == MMF_MIXED ? reinterpret_cast<float2*>(b->d_T) : b->d_Zs + b->n_mat;
+    // mixed path: U on the tensor cores (exact slicing) unless a system has too many levels
+    const bool phi = b->precision == MMF_MIXED && b->nt > 0 && b->Dmax <= mmf_phi_max_levels();
     LAUNCH(mmf_launch_outputs(La, b->Mmax, b->Dmax, b->d_E, b->d_Zf, Z1, Zlo, b->d_t, b->t0, b->nt, b->d_F,
-                              b->d_U, b->d_P, 1e-8),
-           b->nt > 0 ? 4 : 1);
+                              b->d_U, b->d_P, 1e-8, phi ? 1 : 0),
+           b->nt > 0 ? (phi ? 3 : 4) : 1);
+    if (phi)
+        LAUNCH(mmf_launch_phi(La, b->Dmax, b->nt, Z1, Zlo, b->d_F, b->d_E, b->d_Zf, b->d_t, b->t0, b->d_oz, b->d_U,
+                              b->d_status),
+               4);
     mark(b, ST_COUNT);
     if (b->timing_runs > 0) b->runs_recorded++;
     b->last_stage = 3;

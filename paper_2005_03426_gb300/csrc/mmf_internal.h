@@ -202,7 +202,7 @@ cudaError_t mmf_launch_backtransform(const MmfLaunch& L, const void* H, const vo
 cudaError_t mmf_launch_widen(const MmfLaunch& L, const void* Zp, double2* Z, int fp32);
 cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const double* E,
                                const double2* Z, float2* Z1, float2* Zlo, const double* t, double t0, int nt,
-                               double2* F, double2* U, double* P, double cluster_rel);
+                               double2* F, double2* U, double* P, double cluster_rel, int skip_u);
 int mmf_hetrd_max_n(int fp32);
 cudaError_t mmf_launch_hetrd_large(const MmfDesc& d, void* H, void* Vp, void* Wp, double* dvec, double* evec,
                                    void* tau, void* work, void* sc, int fp32, cudaStream_t st);
@@ -226,6 +226,13 @@ cudaError_t mmf_launch_refine_finish(const MmfLaunch& L, double2* X, double* E, 
 #define OZ_S 7
 size_t mmf_ozaki_slice_elems(int n);
 cudaError_t mmf_launch_ozaki_gram(const MmfLaunch& L, const float2* X1, void* S, int* exps, double2* G, int* err);
+// time evolution on the tensor cores (mixed path): Phi by exact slicing, then U in FP64; operands
+// and Phi in the system's operand area (mmf_phi_elems BF16 units); Dmax <= mmf_phi_max_levels()
+int64_t mmf_phi_elems(int n, int D, int M, int nt);
+int mmf_phi_max_levels();
+cudaError_t mmf_launch_phi(const MmfLaunch& L, int Dmax, int nt, const float2* Z1, const float2* Zlo,
+                           const void* F, const double* E, const double2* Z, const double* t, double t0, void* pool,
+                           double2* U, int* err);
 int mmf_ozaki_selftest_impl(int n, double* max_abs, double* max_ref);
 #define MMF_REFINE_BW 33   // entries per row of the refinement's band buffer (2 W + 1)
 #define MMF_REFINE_FULL2_N 3000   // from this n on the second refinement step is a full one
