@@ -250,20 +250,32 @@ __global__ void __launch_bounds__(256) k_w_prep_B(const MmfDesc* __restrict__ de
     const double2* HX = HXg + d.mat_off;
     const double* lam0 = lam0g + d.vec_off;
     float* B = tf3_area(pool, d) + 2 * tf3_piece(n, K);
-    const int64_t tot = (int64_t)rp * kp;
+    // each complex entry w = W(kk, jj) once (FP64), written as its four real entries
+    const int64_t tot = (int64_t)n * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e / kp), k = (int)(e - (int64_t)j * kp);
-        float v = 0.f;
-        if (j < 2 * n && k < K) {
-            const int jj = j < n ? j : j - n, kk = k < n ? k : k - n;
-            const int64_t o = (int64_t)jj * d.ld + kk;
-            const double2 w = HX[o] - lam0[jj] * X[o];
-            double r;
-            if (j < n) r = (k < n) ? w.x : w.y;
-            else r = (k < n) ? w.y : -w.x;
-            v = (float)r;
+        const int jj = (int)(e / n), kk = (int)(e - (int64_t)jj * n);
+        const int64_t o = (int64_t)jj * d.ld + kk;
+        const double2 w = HX[o] - lam0[jj] * X[o];
+        const float wr = (float)w.x, wi = (float)w.y;
+        tf3_put(B, 2 * n, K, jj, kk, wr);
+        tf3_put(B, 2 * n, K, jj, n + kk, wi);
+        tf3_put(B, 2 * n, K, n + jj, kk, wi);
+        tf3_put(B, 2 * n, K, n + jj, n + kk, -wr);
+    }
+    // zeros: K padding of every row, and the padding rows
+    const int kpad = kp - K;
+    const int64_t tz = (int64_t)rp * kpad + (int64_t)(rp - 2 * n) * K;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tz; e += (int64_t)gridDim.x * blockDim.x) {
+        int j, k;
+        if (e < (int64_t)rp * kpad) {
+            j = (int)(e / kpad);
+            k = K + (int)(e - (int64_t)j * kpad);
+        } else {
+            const int64_t f = e - (int64_t)rp * kpad;
+            j = 2 * n + (int)(f / K);
+            k = (int)(f - (int64_t)(j - 2 * n) * K);
         }
-        tf3_put(B, 2 * n, K, j, k, v);
+        tf3_put(B, 2 * n, K, j, k, 0.f);
     }
 }
 
@@ -426,6 +438,7 @@ __global__ void __launch_bounds__(256) k_oa_etilde(const MmfDesc* __restrict__ d
     const double* lam = lamg + d.vec_off;
     const int* cid = cidg + d.vec_off;
     double hmax = fmax(fabs(lam[0]), fabs(lam[n - 1]));
+    const float tiny = (float)(1e-13 * hmax);  // |lam_i| <= hmax (ascending order)
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int j = (int)(e / n), i = (int)(e - (int64_t)j * n);
@@ -434,12 +447,24 @@ __global__ void __launch_bounds__(256) k_oa_etilde(const MmfDesc* __restrict__ d
         double2 et;
         if (i == j) {
             et = make_double2(0.5 * (1.0 - g.x), 0.0);
-        } else {
+        } else if (abs(i - j) <= RF_W) {
+            // the band is applied in double-FP32: FP64 here
             const double2 num = oa_num(C, n, i, j, g, lam[j] - lam0[j]);
             const double gap = lam[j] - lam[i];
-            const bool clustered = cid[i] == cid[j] || fabs(gap) <= RF_TAU * sqrt(abs2(num)) ||
+            const bool clustered = cid[i] == cid[j] || gap * gap <= RF_TAU * RF_TAU * abs2(num) ||
                                    fabs(gap) <= 1e-13 * fmax(hmax, fabs(lam[i]));
             et = clustered ? (-0.5) * g : (1.0 / gap) * num;
+        } else {
+            // off the band Et goes through the split-TF32 product (FP32 accuracy): FP32 here,
+            // with the gap taken in FP64 before rounding
+            const float gx = (float)g.x, gy = (float)g.y;
+            const float dl = (float)(lam[j] - lam0[j]);
+            const float nr = C[(int64_t)i * 2 * n + j] - dl * gx, ni = C[(int64_t)i * 2 * n + n + j] - dl * gy;
+            const float gap = (float)(lam[j] - lam[i]);
+            const bool clustered = cid[i] == cid[j] || gap * gap <= (float)(RF_TAU * RF_TAU) * (nr * nr + ni * ni) ||
+                                   fabsf(gap) <= tiny;
+            const float r = 1.f / gap;
+            et = clustered ? make_double2(-0.5 * g.x, -0.5 * g.y) : make_double2(nr * r, ni * r);
         }
         G[o] = et;
     }
@@ -463,21 +488,35 @@ __global__ void __launch_bounds__(256) k_xe_prep_B(const MmfDesc* __restrict__ d
     const int rp = tf3_nq(2 * n) * 128, kp = tf3_nt(K) * 32;
     const double2* Et = Etg + d.mat_off;
     float* B = tf3_area(pool, d) + 2 * tf3_piece(n, K);
-    const int64_t tot = (int64_t)rp * kp;
+    // each complex entry Et(kk, jj) once, written as its four real entries (0 on the band)
+    const int64_t tot = (int64_t)n * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e / kp), k = (int)(e - (int64_t)j * kp);
-        float v = 0.f;
-        if (j < 2 * n && k < K) {
-            const int jj = j < n ? j : j - n, kk = k < n ? k : k - n;
-            if (abs(jj - kk) > RF_W) {  // the band is applied in double-FP32 by k_xe_apply
-                const double2 x = Et[(int64_t)jj * d.ld + kk];
-                double w;
-                if (j < n) w = (k < n) ? x.x : -x.y;
-                else w = (k < n) ? x.y : x.x;
-                v = (float)w;
-            }
+        const int jj = (int)(e / n), kk = (int)(e - (int64_t)jj * n);
+        float xr = 0.f, xi = 0.f;
+        if (abs(jj - kk) > RF_W) {  // the band is applied in double-FP32 by k_xe_apply
+            const double2 x = Et[(int64_t)jj * d.ld + kk];
+            xr = (float)x.x;
+            xi = (float)x.y;
         }
-        tf3_put(B, 2 * n, K, j, k, v);
+        tf3_put(B, 2 * n, K, jj, kk, xr);
+        tf3_put(B, 2 * n, K, jj, n + kk, -xi);
+        tf3_put(B, 2 * n, K, n + jj, kk, xi);
+        tf3_put(B, 2 * n, K, n + jj, n + kk, xr);
+    }
+    // zeros: K padding of every row, and the padding rows
+    const int kpad = kp - K;
+    const int64_t tz = (int64_t)rp * kpad + (int64_t)(rp - 2 * n) * K;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tz; e += (int64_t)gridDim.x * blockDim.x) {
+        int j, k;
+        if (e < (int64_t)rp * kpad) {
+            j = (int)(e / kpad);
+            k = K + (int)(e - (int64_t)j * kpad);
+        } else {
+            const int64_t f = e - (int64_t)rp * kpad;
+            j = 2 * n + (int)(f / K);
+            k = (int)(f - (int64_t)(j - 2 * n) * K);
+        }
+        tf3_put(B, 2 * n, K, j, k, 0.f);
     }
 }
 

@@ -482,7 +482,6 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     size_t o_coef = p.take(sizeof(double2) * b->n_coef);
     size_t o_H = p.take(cs * b->n_mat);
     size_t o_Zf = p.take(sizeof(double2) * b->n_mat);
-    size_t o_Zp = fp32 ? p.take(cs * b->n_mat) : 0;
     size_t o_E = p.take(sizeof(double) * b->n_vec), o_d = p.take(sizeof(double) * b->n_vec),
            o_e = p.take(sizeof(double) * b->n_vec), o_e2 = p.take(sizeof(double) * b->n_vec),
            o_aux = p.take(sizeof(double) * 8 * count);
@@ -542,7 +541,8 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     b->d_coef = (double2*)(B + o_coef);
     b->d_H = B + o_H;
     b->d_Zf = (double2*)(B + o_Zf);
-    b->d_Zp = fp32 ? (void*)(B + o_Zp) : (void*)b->d_Zf;
+    // the FP32 back-transform output lives in HX, which the refinement only uses after widening
+    b->d_Zp = fp32 ? (void*)(B + o_HX) : (void*)b->d_Zf;
     b->d_E = (double*)(B + o_E);
     b->d_d = (double*)(B + o_d);
     b->d_e = (double*)(B + o_e);
