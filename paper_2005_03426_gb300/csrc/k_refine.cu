@@ -590,6 +590,7 @@ __global__ void __launch_bounds__(256) k_et_band(const MmfDesc* __restrict__ des
 // and the tile of C are staged in shared memory; thread (row, group of XT_CPT columns).
 #define XT_R 32
 #define XT_C 32
+#define XT_SMALL 1e-7f  // band entries below this go through FP32 (see k_xe_apply)
 #define XT_CPT (XT_C * XT_R / 256)   // output columns per thread
 __global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ descs,
                                                   const int* __restrict__ idx, const double2* __restrict__ Xg,
@@ -598,8 +599,11 @@ __global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ de
     __shared__ float2 xs[XT_C + 2 * RF_W][XT_R];
     __shared__ Split es[RF_BW][XT_C];
     __shared__ float cs[2][XT_R][XT_C + 1];
+    __shared__ int big;
     const MmfDesc d = descs[idx[blockIdx.z]];
     const int n = d.n, la = xe_la(n);
+    if (threadIdx.x == 0) big = 0;
+    __syncthreads();
     const int r0 = blockIdx.x * XT_R, j0 = blockIdx.y * XT_C;
     if (r0 >= n || j0 >= n) return;
     const double2* Eb = Ebg + (int64_t)d.vec_off * RF_BW;
@@ -609,10 +613,14 @@ __global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ de
         const int cc = e / XT_R, rr = e - cc * XT_R, col = j0 - RF_W + cc, row = r0 + rr;
         xs[cc][rr] = (col >= 0 && col < n && row < n) ? X1[(int64_t)col * d.ld + row] : make_float2(0.f, 0.f);
     }
+    bool bigl = false;
     for (int e = threadIdx.x; e < RF_BW * XT_C; e += 256) {
         const int q = e / XT_C, c = e - q * XT_C, j = j0 + c, i = j + q - RF_W;
-        es[q][c] = split((j < n && i >= 0 && i < n) ? Eb[(int64_t)i * RF_BW + (j - i + RF_W)] : make_double2(0.0, 0.0));
+        const Split v = split((j < n && i >= 0 && i < n) ? Eb[(int64_t)i * RF_BW + (j - i + RF_W)] : make_double2(0.0, 0.0));
+        es[q][c] = v;
+        bigl |= fmaxf(fabsf(v.r1), fabsf(v.i1)) > XT_SMALL;
     }
+    if (__any_sync(0xffffffffu, bigl) && (threadIdx.x & 31) == 0) big = 1;
     for (int e = threadIdx.x; e < XT_R * XT_C; e += 256) {
         const int rr = e / XT_C, c = e - rr * XT_C, row = r0 + rr, j = j0 + c;
         const bool ok = row < n && j < n;
@@ -624,6 +632,27 @@ __global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ de
     const int r = r0 + rr;
     if (r >= n) return;
     const double2* X = Xg + d.mat_off;
+    if (!big) {
+        // every band entry of the tile is below XT_SMALL (a second step's corrections): plain
+        // FP32, whose error (about 33 x 2^-24 x XT_SMALL for |X| <= 1) stays near 2e-13 at most
+#pragma unroll 1
+        for (int c = cg * XT_CPT; c < cg * XT_CPT + XT_CPT; ++c) {
+            const int j = j0 + c;
+            if (j >= n) break;
+            float ar = 0.f, ai = 0.f;
+#pragma unroll 11
+            for (int q = 0; q < RF_BW; ++q) {
+                const float2 x = xs[c + q][rr];
+                const Split e = es[q][c];
+                ar = fmaf(x.x, e.r1, fmaf(-x.y, e.i1, ar));
+                ai = fmaf(x.x, e.i1, fmaf(x.y, e.r1, ai));
+            }
+            const double2 x = X[(int64_t)j * d.ld + r];
+            Xn[d.mat_off + (int64_t)j * d.ld + r] =
+                make_double2(x.x + ((double)cs[0][rr][c] + (double)ar), x.y + ((double)cs[1][rr][c] + (double)ai));
+        }
+        return;
+    }
 #pragma unroll 1
     for (int c = cg * XT_CPT; c < cg * XT_CPT + XT_CPT; ++c) {
         const int j = j0 + c;
