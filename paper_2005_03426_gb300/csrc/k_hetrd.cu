@@ -32,7 +32,7 @@ namespace cg = cooperative_groups;
 
 #define HT_THREADS 512
 #define HT_TILE 64
-#define HT_SEG 128   // rows per hemv task (a multiple of 64)
+#define HT_SEG 512   // rows per hemv task (a multiple of 64)
 
 template <class R>
 __device__ __forceinline__ R block_sum(R v, R* red) {
@@ -134,6 +134,17 @@ __device__ __forceinline__ bool ht_task(int h, int nloc, int rank, int CL, int m
 __device__ __forceinline__ void ht_issue(const float2* __restrict__ a22, int ld, const HtTask& t, int r0,
                                          float2* buf, int lane) {
     const float2* colbase = a22 + (int64_t)t.c0 * ld;
+    if (r0 >= t.c0 + 8 && r0 + HT_CH <= t.rend && t.nc == 8) {
+        // the common chunk: below the diagonal block, inside the task, all 8 columns present
+        const float2* p = colbase + r0 + lane;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+#pragma unroll
+            for (int hf = 0; hf < HT_CH / 32; ++hf)
+                cp_async8(buf + jj * HT_CH + lane + 32 * hf, p + (int64_t)jj * ld + 32 * hf, 8);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        return;
+    }
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
 #pragma unroll
