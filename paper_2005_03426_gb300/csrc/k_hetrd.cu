@@ -524,14 +524,38 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                     }
                     __syncthreads();
                     C acc[8];
+                    if constexpr (sizeof(R) == 4) {
+                        // packed FP32 pairs: s1 += (a.x, a.x) c + (b.x, b.x) d, s2 += (a.y, a.y) c + (b.y, b.y) d,
+                        // so that a c + b d = (s1.x - s2.y, s1.y + s2.x)
+                        float2 s1[8], s2[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) acc[q] = czero<C>();
-                    for (int p = 0; p < nb; ++p) {
-                        const C a = tVr[p * HT_TILE + rr], b = tWr[p * HT_TILE + rr];
+                        for (int q = 0; q < 8; ++q) s1[q] = s2[q] = make_float2(0.f, 0.f);
+                        for (int p = 0; p < nb; ++p) {
+                            const float2 a = tVr[p * HT_TILE + rr], b = tWr[p * HT_TILE + rr];
+                            const float2 ax = make_float2(a.x, a.x), ay = make_float2(a.y, a.y);
+                            const float2 bx = make_float2(b.x, b.x), by = make_float2(b.y, b.y);
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int cc = cg + 8 * q;
-                            acc[q] = acc[q] + a * tWc[p * HT_TILE + cc] + b * tVc[p * HT_TILE + cc];
+                            for (int q = 0; q < 8; ++q) {
+                                const int cc = cg + 8 * q;
+                                const float2 c = tWc[p * HT_TILE + cc], dv = tVc[p * HT_TILE + cc];
+                                s1[q] = __ffma2_rn(ax, c, s1[q]);
+                                s1[q] = __ffma2_rn(bx, dv, s1[q]);
+                                s2[q] = __ffma2_rn(ay, c, s2[q]);
+                                s2[q] = __ffma2_rn(by, dv, s2[q]);
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) acc[q] = mk(s1[q].x - s2[q].y, s1[q].y + s2[q].x);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) acc[q] = czero<C>();
+                        for (int p = 0; p < nb; ++p) {
+                            const C a = tVr[p * HT_TILE + rr], b = tWr[p * HT_TILE + rr];
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const int cc = cg + 8 * q;
+                                acc[q] = acc[q] + a * tWc[p * HT_TILE + cc] + b * tVc[p * HT_TILE + cc];
+                            }
                         }
                     }
                     const int r = rbase + rr;
