@@ -118,6 +118,10 @@ __device__ __forceinline__ void atomic_add_c(float2* p, float2 v) {
 // column block (rank + CL (h % nloc)) of 8 columns, rows from segment h / nloc (HT_SEG rows).
 // The arithmetic is branch-free outside the diagonal chunk: the block's 8 entries of v are held
 // in registers per task, the chunk's operands are read from shared memory before the FMAs.
+// Complex products use packed FP32 pair FMAs with split accumulators: for a row r,
+// y_r += sum_jj a v_jj is kept as r1 = sum a (v.x, v.x), r2 = sum a (v.y, v.y), y_r += (r1.x - r2.y,
+// r1.y + r2.x); for a column, sum_r conj(a) v_r as c1 = sum a (v_r.x, v_r.x), c2 = sum a (v_r.y,
+// v_r.y), added as (c1.x + c2.y, c2.x - c1.y).
 struct HtTask {
     int c0, rbeg, rend, nc;
 };
@@ -169,11 +173,13 @@ __device__ int hemv_f32_staged(const float2* __restrict__ a22, int ld, int m, co
     if (h >= nh) return 0;
     int r0 = t.rbeg, buf = 0, nchunks = 0;
     ht_issue(a22, ld, t, r0, stg, lane);
-    float2 v[8], ca[8];
+    float2 v[8], vxx[8], vyy[8], c1[8], c2[8];
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
         v[jj] = (jj < t.nc) ? vS[t.c0 + jj] : czero<float2>();
-        ca[jj] = czero<float2>();
+        vxx[jj] = make_float2(v[jj].x, v[jj].x);
+        vyy[jj] = make_float2(v[jj].y, v[jj].y);
+        c1[jj] = c2[jj] = czero<float2>();
     }
     for (;;) {
         ++nchunks;
@@ -203,19 +209,25 @@ __device__ int hemv_f32_staged(const float2* __restrict__ a22, int ld, int m, co
             for (int jj = 0; jj < 8; ++jj) a[jj] = sb[jj * HT_CH + lane + 32 * hf];  // 0 where not loaded
             const float2 vr = (r < t.rend) ? vS[r] : czero<float2>();
             float2 ra = czero<float2>();
+            const float2 vrx = make_float2(vr.x, vr.x), vry = make_float2(vr.y, vr.y);
             if (!diag) {
+                float2 r1 = make_float2(0.f, 0.f), r2 = r1;
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
-                    ra = ra + a[jj] * v[jj];
-                    ca[jj] = ca[jj] + cmulc(a[jj], vr);
+                    r1 = __ffma2_rn(a[jj], vxx[jj], r1);
+                    r2 = __ffma2_rn(a[jj], vyy[jj], r2);
+                    c1[jj] = __ffma2_rn(a[jj], vrx, c1[jj]);
+                    c2[jj] = __ffma2_rn(a[jj], vry, c2[jj]);
                 }
+                ra = make_float2(r1.x - r2.y, r1.y + r2.x);
             } else {
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
                     const int c = t.c0 + jj;
                     if (r > c) {
                         ra = ra + a[jj] * v[jj];
-                        ca[jj] = ca[jj] + cmulc(a[jj], vr);
+                        c1[jj] = __ffma2_rn(a[jj], vrx, c1[jj]);
+                        c2[jj] = __ffma2_rn(a[jj], vry, c2[jj]);
                     } else if (r == c) {
                         ra = ra + a[jj].x * v[jj];
                     }
@@ -227,13 +239,18 @@ __device__ int hemv_f32_staged(const float2* __restrict__ a22, int ld, int m, co
         if (hn != h || !more) {  // the task is complete: add its column part
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
-                const float sx = warp_sum(ca[jj].x), sy = warp_sum(ca[jj].y);
+                // conj(a) vr summed: (c1.x + c2.y, c2.x - c1.y)
+                const float sx = warp_sum(c1[jj].x + c2[jj].y), sy = warp_sum(c2[jj].x - c1[jj].y);
                 if (lane == 0 && jj < t.nc) atomic_add_c(&yS[t.c0 + jj], mk(sx, sy));
-                ca[jj] = czero<float2>();
+                c1[jj] = c2[jj] = czero<float2>();
             }
             if (!more) break;
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) v[jj] = (jj < tn.nc) ? vS[tn.c0 + jj] : czero<float2>();
+            for (int jj = 0; jj < 8; ++jj) {
+                v[jj] = (jj < tn.nc) ? vS[tn.c0 + jj] : czero<float2>();
+                vxx[jj] = make_float2(v[jj].x, v[jj].x);
+                vyy[jj] = make_float2(v[jj].y, v[jj].y);
+            }
         }
         h = hn;
         t = tn;
