@@ -179,17 +179,18 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma_gemm(const UmmaJob* __re
 
 // ------------------------------------------------------------------ split-TF32, warp-specialized
 // C = A1 B1^T + A1 B2^T + A2 B1^T for pre-tiled operands (layout in mmf_internal.h).  One CTA per
-// 128 x 128 tile of C, six warps: warp 4 (one lane) streams the four 16-KB operand tiles of each
-// K step into a ring of TF_STAGES stages with cp.async.bulk (completion counted on full[stage]);
-// warp 5 (one lane) issues the 12 tcgen05.mma of the step and frees the stage with
-// tcgen05.commit on empty[stage]; warps 0-3 own the tile's rows (their TMEM lanes).
+// 128 x BN tile of C (BN = 128 or 256; the wider tile reads A once per 256 columns of C).  Warps:
+// one producer (one lane) streams the operand tiles of each K step (A1, A2: 16 KB each; B1, B2:
+// BN/128 adjacent 16-KB tiles each) into a ring of stages (3, or 2 for BN = 256) with
+// cp.async.bulk (completion counted on full[stage]); one MMA warp (one lane) issues the 12
+// tcgen05.mma of the step (M = 128, N = BN) and frees the stage with tcgen05.commit on
+// empty[stage]; BN / 32 epilogue warps, two per TMEM lane quadrant for BN = 256, each own 32 rows
+// and 128 columns of the tile.
 // The tensor cores' FP32 accumulation loses accuracy over long K, so the sum is cut into chunks
 // of TF_KC K steps: each chunk is accumulated in one of two TMEM buffers (commit on accfull[b])
 // and added, rounded to nearest, into the epilogue warps' registers, which then free the buffer
 // (accempty[b]) while the next chunk runs.  Every wait is bounded and ends on a shared abort flag.
-#define TF_STAGES 3
 #define TF_TILE_BYTES 16384u
-#define TF_STAGE_BYTES (4u * TF_TILE_BYTES)
 #define TF_KC 4
 
 __device__ __forceinline__ bool tf_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
@@ -222,33 +223,39 @@ __device__ __forceinline__ void tf_ld32(uint32_t ta, uint32_t* v) {
         : "r"(ta));
 }
 
-__global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ jobs, int* __restrict__ err) {
+template <int BN>
+__global__ void __launch_bounds__(32 * (BN / 32 + 2), 1) k_tf3_gemm(const Tf3Job* __restrict__ jobs,
+                                                                   int* __restrict__ err) {
+    constexpr int NE = BN / 32;              // epilogue warps (two per TMEM lane quadrant for BN = 256)
+    constexpr int NST = BN == 128 ? 3 : 2;   // pipeline stages
+    constexpr uint32_t BT = (uint32_t)(BN / 128) * TF_TILE_BYTES;  // one piece of the B tile
+    constexpr uint32_t SB = 2u * TF_TILE_BYTES + 2u * BT;         // stage bytes
     extern __shared__ __align__(1024) unsigned char tf_smem[];
-    __shared__ uint64_t full[TF_STAGES], empty[TF_STAGES], accfull[2], accempty[2];
+    __shared__ uint64_t full[NST], empty[NST], accfull[2], accempty[2];
     __shared__ uint32_t tmem_s;
     __shared__ int abort_s;
     const Tf3Job jb = jobs[blockIdx.z];
     const int I = blockIdx.x, J = blockIdx.y;
-    if (I * 128 >= jb.M || J * 128 >= jb.N) return;
+    if (I * 128 >= jb.M || J * BN >= jb.N) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* base = (unsigned char*)(((uintptr_t)tf_smem + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(base);
     volatile int* abort_flag = &abort_s;
     if (threadIdx.x == 0) {
         abort_s = 0;
-        for (int q = 0; q < TF_STAGES; ++q) {
+        for (int q = 0; q < NST; ++q) {
             mbar_init(&full[q], 1);
             mbar_init(&empty[q], 1);
         }
         for (int q = 0; q < 2; ++q) {
             mbar_init(&accfull[q], 1);
-            mbar_init(&accempty[q], 4);  // one arrival per epilogue warp
+            mbar_init(&accempty[q], NE);  // one arrival per epilogue warp
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
-                     "r"(256u)
+                     "r"(2u * BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -260,40 +267,46 @@ __global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ 
     const int nch = (nt + TF_KC - 1) / TF_KC;
     const int64_t pa = tf3_piece(jb.M, jb.K), pb = tf3_piece(jb.N, jb.K);
 
-    if (warp == 4) {
+    if (warp == NE) {
         if (lane == 0) {
+            // B row tiles of this CTA present in the operand (the last one may hold one of two)
+            const int jt0 = J * (BN / 128), nbv = min(BN / 128, nqb - jt0);
+            const uint32_t bbytes = (uint32_t)nbv * TF_TILE_BYTES;
             for (int t = 0; t < nt; ++t) {
-                const int st = t % TF_STAGES;
-                const uint32_t use = (uint32_t)(t / TF_STAGES);
+                const int st = t % NST;
+                const uint32_t use = (uint32_t)(t / NST);
                 if (use > 0 && !tf_wait(&empty[st], (use - 1) & 1u, abort_flag)) break;
                 const uint32_t fb = smem_u32(&full[st]);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(TF_STAGE_BYTES)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                             "r"(2u * TF_TILE_BYTES + 2u * bbytes)
                              : "memory");
-                const uint32_t dst = sbase + (uint32_t)st * TF_STAGE_BYTES;
+                const uint32_t dst = sbase + (uint32_t)st * SB;
                 const float* src[4] = {jb.A + ((int64_t)t * nqa + I) * 4096, jb.A + pa + ((int64_t)t * nqa + I) * 4096,
-                                       jb.B + ((int64_t)t * nqb + J) * 4096, jb.B + pb + ((int64_t)t * nqb + J) * 4096};
+                                       jb.B + ((int64_t)t * nqb + jt0) * 4096, jb.B + pb + ((int64_t)t * nqb + jt0) * 4096};
+                const uint32_t off[4] = {0u, TF_TILE_BYTES, 2u * TF_TILE_BYTES, 2u * TF_TILE_BYTES + BT};
+                const uint32_t len[4] = {TF_TILE_BYTES, TF_TILE_BYTES, bbytes, bbytes};
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     asm volatile(
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            dst + (uint32_t)q * TF_TILE_BYTES),
-                        "l"(src[q]), "r"(TF_TILE_BYTES), "r"(fb)
+                            dst + off[q]),
+                        "l"(src[q]), "r"(len[q]), "r"(fb)
                         : "memory");
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == NE + 1) {
         if (lane == 0) {
-            const uint32_t idesc = umma_idesc(2);  // TF32, M = N = 128
+            const uint32_t idesc = umma_idesc_mn(2, 128u, (uint32_t)BN);  // TF32, M = 128, N = BN
             for (int t = 0; t < nt; ++t) {
-                const int st = t % TF_STAGES;
+                const int st = t % NST;
                 const int ch = t / TF_KC, kin = t - ch * TF_KC, bsel = ch & 1;
                 if (kin == 0 && ch >= 2 && !tf_wait(&accempty[bsel], (uint32_t)((ch >> 1) - 1) & 1u, abort_flag)) break;
-                if (!tf_wait(&full[st], (uint32_t)(t / TF_STAGES) & 1u, abort_flag)) break;
+                if (!tf_wait(&full[st], (uint32_t)(t / NST) & 1u, abort_flag)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sa = sbase + (uint32_t)st * TF_STAGE_BYTES;
+                const uint32_t sa = sbase + (uint32_t)st * SB;
                 const uint64_t a1 = umma_desc(sa), a2 = umma_desc(sa + TF_TILE_BYTES);
-                const uint64_t b1 = umma_desc(sa + 2 * TF_TILE_BYTES), b2 = umma_desc(sa + 3 * TF_TILE_BYTES);
-                const uint32_t dacc = tmem + (uint32_t)(bsel * 128);
+                const uint64_t b1 = umma_desc(sa + 2 * TF_TILE_BYTES), b2 = umma_desc(sa + 2 * TF_TILE_BYTES + BT);
+                const uint32_t dacc = tmem + (uint32_t)(bsel * BN);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {  // 32 bytes (8 TF32) of K per instruction
                     const uint64_t adv = (uint64_t)((q * 32) >> 4);
@@ -319,8 +332,8 @@ __global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ 
             }
         }
     } else {
-        // epilogue: warp w holds rows 32w .. 32w+31 of the tile (its TMEM lanes); the chunks are
-        // summed in registers
+        // epilogue: warp w holds rows 32 (w % 4) .. +31 of the tile (its TMEM lanes) and columns
+        // 128 (w / 4) .. +127; the chunks are summed in registers
         float acc[128];
 #pragma unroll
         for (int q = 0; q < 128; ++q) acc[q] = 0.f;
@@ -332,7 +345,7 @@ __global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ 
 #pragma unroll
             for (int c0 = 0; c0 < 128; c0 += 32) {
                 uint32_t v[32];
-                tf_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bsel * 128 + c0), v);
+                tf_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(bsel * BN + (warp >> 2) * 128 + c0), v);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int q = 0; q < 32; ++q) acc[c0 + q] += __uint_as_float(v[q]);
@@ -344,10 +357,10 @@ __global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ 
             }
         }
         if (ok) {
-            const int row = I * 128 + warp * 32 + lane;
+            const int row = I * 128 + (warp & 3) * 32 + lane;
 #pragma unroll
             for (int c0 = 0; c0 < 128; c0 += 32) {
-                const int col = J * 128 + c0;
+                const int col = J * BN + (warp >> 2) * 128 + c0;
                 if (col >= jb.N) break;
                 if (jb.mode == TF3_OPERAND) {
                     // the row's 32 values are one 128-byte row of K-tile col / 32 (16-byte chunks
@@ -402,17 +415,25 @@ __global__ void __launch_bounds__(192, 1) k_tf3_gemm(const Tf3Job* __restrict__ 
     __syncthreads();
     if (threadIdx.x == 0 && abort_s) atomicExch(err, 1);
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * BN) : "memory");
 }
 
+template <int BN>
+static cudaError_t launch_tf3(const void* jobs, int count, int Mmax, int Nmax, int* err, cudaStream_t stream) {
+    constexpr int NST = BN == 128 ? 3 : 2;
+    const size_t sm = (size_t)NST * (2 * TF_TILE_BYTES + 2 * (BN / 128) * TF_TILE_BYTES) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_tf3_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((Mmax + 127) / 128, (Nmax + BN - 1) / BN, count);
+    k_tf3_gemm<BN><<<grid, 32 * (BN / 32 + 2), sm, stream>>>((const Tf3Job*)jobs, err);
+    return cudaGetLastError();
+}
+
+// 256-wide tiles (A read once per 256 columns of C) wherever the widest product allows
 cudaError_t mmf_launch_tf3(const void* jobs, int count, int Mmax, int Nmax, int* err, cudaStream_t stream) {
     if (count <= 0) return cudaSuccess;
-    const size_t sm = (size_t)TF_STAGES * TF_STAGE_BYTES + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_tf3_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    dim3 grid((Mmax + 127) / 128, (Nmax + 127) / 128, count);
-    k_tf3_gemm<<<grid, 192, sm, stream>>>((const Tf3Job*)jobs, err);
-    return cudaGetLastError();
+    return Nmax >= 256 ? launch_tf3<256>(jobs, count, Mmax, Nmax, err, stream)
+                       : launch_tf3<128>(jobs, count, Mmax, Nmax, err, stream);
 }
 
 // jobs: device array of `count` UmmaJob; grid covers the largest M and N among them
