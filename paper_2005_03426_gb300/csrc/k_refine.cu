@@ -584,13 +584,14 @@ __global__ void __launch_bounds__(256) k_et_band(const MmfDesc* __restrict__ des
 
 // Xn(:, j) = X(:, j) + C(:, j) + sum_{|i-j|<=W} X(:, i) Et(i, j): C from the tensor cores (Et
 // outside the band), the band in double-FP32 from X1 = fl32(X) (exact in the first step; in a
-// second full step the remainder times Et is below 2^-24 |Et| and dropped) and Et split in two
-// FP32 pieces.  Xn goes to a separate buffer (the band reads neighbouring columns of X).
+// second step the remainder times Et is below 2^-24 |Et| and dropped) and Et split in two FP32
+// pieces, or in plain FP32 where every band entry of the tile is below XT_SMALL (a second step's
+// corrections).  Xn goes to a separate buffer (the band reads neighbouring columns of X).
 // One CTA per XT_R x XT_C tile of Xn: the XT_C + 2W neighbouring columns of X1, the band of Et
 // and the tile of C are staged in shared memory; thread (row, group of XT_CPT columns).
 #define XT_R 32
 #define XT_C 32
-#define XT_SMALL 1e-7f  // band entries below this go through FP32 (see k_xe_apply)
+#define XT_SMALL 1e-7f  // band entries below this go through plain FP32
 #define XT_CPT (XT_C * XT_R / 256)   // output columns per thread
 __global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ descs,
                                                   const int* __restrict__ idx, const double2* __restrict__ Xg,
