@@ -491,3 +491,24 @@ def test_mixed_batch_both_backtransform_paths():
         e1, u1, p1 = solo.get(0)
         assert np.abs(e - e1).max() <= 1e-9 * np.abs(e1).max()
         assert np.abs(u - u1).max() <= 1e-8 and np.abs(pp - p1).max() <= 1e-8
+
+
+def test_mixed_many_levels_time_evolution():
+    """More than 16 levels: the mixed path's U falls back from the tensor-core contraction to the
+    double-FP32 one; against the oracle, alone and in a batch with a tensor-core system."""
+    c = M.Context(0)
+    big = W.random_small(4, D=17, Ns=[2], nharm=[1])
+    small = SOLVE_CASES["random_n125"]()
+    t = W.time_grid(big, 8)
+    s, E, U, P = _solve_gpu(c, big, t, 0.2, precision=M.MMF_MIXED)
+    _compare(big, E, U, P, t, 0.2, e_rel=MIX_E_REL, up_abs=MIX_UP_ABS)
+    nt = 8
+    ps = [small, big]
+    ts = np.stack([W.time_grid(p, nt) for p in ps])
+    b = M.Batch(c, [M.System(c, p) for p in ps], M.MMF_MIXED, nt)
+    b.set_times(0.0, ts)
+    b.run()
+    assert (b.sync() == 0).all()
+    for i, p in enumerate(ps):
+        e, u, pp = b.get(i)
+        _compare(p, e, u, pp, ts[i], 0.0, e_rel=MIX_E_REL, up_abs=MIX_UP_ABS)
