@@ -5,20 +5,21 @@
 // Real form: with a_i = [Re x_i | Im x_i] and a'_j = [Im x_j | -Re x_j] (x_i column i of X1,
 // K = 2n), Re G_ij = a_i . a_j and Im G_ij = a_i . a'_j.
 //
-// Slicing (k_oz_slice): column i is scaled by 2^-e_i (e_i the exponent of its largest entry, so
-// every scaled entry t lies in (-1, 1)) and cut into OZ_S integer slices of OZ_W bits,
-//     t = sum_s 2^-OZ_W(s+1) v_s,   v_0 in [-64, 64], v_s in [-32, 32] (s > 0),
-// each step t <- 64 t - rint(64 t) exact in FP32; the integers are exact in BF16.  The slices
-// cover 42 bits below each column's largest entry.
+// Slicing (k_oz_slice): column i is scaled by 2^-(e_i + 1) (e_i the exponent of its largest
+// entry, so every scaled entry t lies in (-1/2, 1/2)) and cut into OZ_S integer slices of OZ_W
+// bits,
+//     t = sum_s 2^-OZ_W(s+1) v_s,   v_s in [-128, 128],
+// each step t <- 256 t - rint(256 t) exact in FP32; the integers are exact in BF16 (which holds
+// integers up to 256).  The slices cover 40 bits below each column's largest entry.
 //
 // Products (k_oz_gram): for every slice pair (a, b) with a + b <= OZ_L, S_a S_b^T is an integer
 // matrix.  On the tensor cores, BF16 products of these integers are exact and so is their FP32
-// accumulation as long as every partial sum stays below 2^24: K is taken in chunks of OZ_KCH
-// (<= 3968 terms of magnitude <= 2^12), and after each chunk the FP32 accumulator (an exact
-// integer) is added into an int64 accumulator per output, scaled by 2^(6 (OZ_L - a - b) - 6)
-// (the pairs with a + b = OZ_L lose their 6 lowest bits, 2^-42 of the leading term).  At the
-// end G_ij = 2^(e_i + e_j - 6 (OZ_L + 2) + 6) acc_ij, one rounding to FP64.
-// Error: the dropped pairs and slice remainders are below ~2^-40 |x_i| |x_j| per entry.
+// accumulation as long as every partial sum stays within 2^24: K is taken in chunks of OZ_KCH
+// (1024 terms of magnitude <= 2^14), and after each chunk the FP32 accumulator (an exact
+// integer) is added into an int64 accumulator per output, scaled by 2^(OZ_W (OZ_L - a - b)).  At
+// the end G_ij = 2^(e_i + e_j + 2 - OZ_W (OZ_L + 2)) acc_ij, one rounding to FP64.  The int64
+// sums stay below 2^63 for 2n <= 2^17 (n <= OZ_NMAX).
+// Error: the dropped pairs and slice remainders are below ~2^-38 |x_i| |x_j| per entry.
 //
 // Data layout: the slicing kernel writes every slice pre-tiled in the shared-memory layout the
 // tensor cores read (64-row x 64-K tiles of 8 KB, 128-byte swizzle, K-major), so one stage of
@@ -42,13 +43,15 @@
 #include "mmf_internal.h"
 #include "umma_common.h"
 
-#define OZ_W 6
-#define OZ_L 6                 // pairs a + b <= OZ_L
+#define OZ_W 8                 // bits per slice
+#define OZ_L 4                 // pairs a + b <= OZ_L
+#define OZ_SCALE 256.f         // 2^OZ_W
+#define OZ_NMAX 60000          // int64 range of the Gram sums (2n <= 2^17)
 #define OZ_THREADS 128
 #define OZ_TM 128
 #define OZ_TN 64
 #define OZ_KSTEP 64            // BF16 elements of K per stage (one 128-byte row segment)
-#define OZ_KCH (62 * OZ_KSTEP) // K per exact FP32 accumulation: 3968 * 2^12 < 2^24
+#define OZ_KCH (16 * OZ_KSTEP) // K per exact FP32 accumulation: 1024 * 2^14 = 2^24
 #define OZ_STAGE_BYTES (16384 + 8192 + 8192)
 #define OZ_STAGES 6
 #define OZ_TILE_ELEMS 4096      // one 64 x 64 BF16 tile (8 KB)
@@ -83,7 +86,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(const MmfDesc* __restrict__ de
         for (int k = lane; k < n; k += 32) m = fmaxf(m, fmaxf(fabsf(x[k].x), fabsf(x[k].y)));
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     int e = 0;
-    if (m > 0.f) frexpf(m, &e);  // m = f 2^e, f in [0.5, 1): |x| 2^-e < 1
+    if (m > 0.f) frexpf(m, &e);  // m = f 2^e, f in [0.5, 1): |x| 2^-(e+1) < 1/2
     if (live && lane == 0) expg[d.vec_off + i] = e;
     __nv_bfloat16* Sys = S + d.oz_off;
     const int q = i >> 6, r = i & 63;
@@ -103,8 +106,8 @@ __global__ void __launch_bounds__(256) k_oz_slice(const MmfDesc* __restrict__ de
                     vb = -x[k - n].x;  // -Re x_ki
                 }
             }
-            ta[u] = ldexpf(va, -e);
-            tb[u] = ldexpf(vb, -e);
+            ta[u] = ldexpf(va, -(e + 1));
+            tb[u] = ldexpf(vb, -(e + 1));
         }
         const int t = k0 >> 6, j = (k0 & 63) >> 3;
         const int64_t inner = (int64_t)(r >> 3) * 512 + (r & 7) * 64 + ((j ^ (r & 7)) << 3);  // BF16 units
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(const MmfDesc* __restrict__ de
             uint32_t pa[4], pb[4];
 #pragma unroll
             for (int u = 0; u < 8; u += 2) {
-                float a0 = ta[u] * 64.f, a1 = ta[u + 1] * 64.f, b0 = tb[u] * 64.f, b1 = tb[u + 1] * 64.f;
+                float a0 = ta[u] * OZ_SCALE, a1 = ta[u + 1] * OZ_SCALE, b0 = tb[u] * OZ_SCALE, b1 = tb[u + 1] * OZ_SCALE;
                 const float ra0 = rintf(a0), ra1 = rintf(a1), rb0 = rintf(b0), rb1 = rintf(b1);
                 ta[u] = a0 - ra0;
                 ta[u + 1] = a1 - ra1;
@@ -334,7 +337,7 @@ __global__ void __launch_bounds__(OZ_WARPS * 32, 1) k_oz_gram(const MmfDesc* __r
         bool ok = true;
         for (int a = 0; a <= OZ_L && ok; ++a)
             for (int b = 0; a + b <= OZ_L && ok; ++b) {
-                const int sh = 6 * (OZ_L - a - b) - 6;
+                const int sh = OZ_W * (OZ_L - a - b);
                 for (int kc = 0; kc < nkc; ++kc, ++c) {
                     const int buf = c & 1;
                     if (!oz_wait(&accfull[buf], ((uint32_t)c >> 1) & 1u, abort_flag)) { ok = false; break; }
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(OZ_WARPS * 32, 1) k_oz_gram(const MmfDesc* __r
                 for (int q = 0; q < 32; ++q) {
                     const int j = j0 + g + q;
                     if (i < n && j <= i) {  // j <= i < n
-                        const int sc = ei + expg[d.vec_off + j] - 6 * (OZ_L + 2) + 6;
+                        const int sc = ei + expg[d.vec_off + j] + 2 - OZ_W * (OZ_L + 2);
                         const long long ar = (long long)(((unsigned long long)rhi[q] << 32) | rlo[q]);
                         const long long ai = (long long)(((unsigned long long)ihi[q] << 32) | ilo[q]);
                         const double gr = ldexp((double)ar, sc);
@@ -402,8 +405,11 @@ __global__ void __launch_bounds__(OZ_WARPS * 32, 1) k_oz_gram(const MmfDesc* __r
 
 size_t mmf_ozaki_slice_elems(int n) { return (size_t)2 * OZ_S * oz_nt(n) * oz_nq(n) * OZ_TILE_ELEMS; }
 
+int mmf_ozaki_max_n() { return OZ_NMAX; }
+
 cudaError_t mmf_launch_ozaki_gram(const MmfLaunch& L, const float2* X1, void* S, int* exps, double2* G, int* err) {
     if (L.count <= 0) return cudaSuccess;
+    if (L.nmax > OZ_NMAX) return cudaErrorInvalidValue;
     const int rows = oz_nq(L.nmax) * 64;
     k_oz_slice<<<dim3((rows + 7) / 8, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X1, (__nv_bfloat16*)S, exps);
     const int nI = (L.nmax + OZ_TM - 1) / OZ_TM, nJ = (L.nmax + OZ_TN - 1) / OZ_TN;
@@ -422,8 +428,8 @@ cudaError_t mmf_launch_ozaki_gram(const MmfLaunch& L, const float2* X1, void* S,
 // same exact slicing: A rows r = j n + l hold a_r = [Re Z((j, b), l) | Im Z((j, b), l)] over b
 // (K = 2M), B rows t hold [Re F(t, b) | -Im F(t, b)] and B' rows [Im F(t, b) | Re F(t, b)], so
 // that a_r . b_t = Re Phi and a_r . b'_t = Im Phi.  Z (FP64) is sliced from its FP32 pieces
-// Z1 + Zlo in double-FP32 (each step 64 t - rint(64 t) exact, the pair renormalised by TwoSum),
-// F from its pre-split phase table.  Phi goes to FP64 (error below ~2^-40 of each row's largest
+// Z1 + Zlo in double-FP32 (each step 256 t - rint(256 t) exact, the pair renormalised by TwoSum),
+// F from its pre-split phase table.  Phi goes to FP64 (error below ~2^-38 of each row's largest
 // |Z| times sum_b |F|); U(t, t0)[j, i] = sum_l Phi_j(t, l) e^{-i E_l (t - t0)} conj(Z[(i, b0), l])
 // follows in FP64.  The operands and Phi live in the system's operand area.
 struct PhiLayout {
@@ -460,10 +466,10 @@ __device__ __forceinline__ void oz_slices8(float* t1, float* t2, uint4* out) {
             float v[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const float x = t1[u + h] * 64.f;   // exact
+                const float x = t1[u + h] * OZ_SCALE;  // exact
                 const float r = rintf(x);
                 const float a = x - r;               // exact
-                const float b = t2[u + h] * 64.f;    // exact
+                const float b = t2[u + h] * OZ_SCALE;  // exact
                 const float s = a + b;               // TwoSum: (s, err) = a + b exactly
                 const float bb = s - a;
                 t1[u + h] = s;
@@ -500,9 +506,9 @@ __global__ void __launch_bounds__(256) k_phi_slice_a(const MmfDesc* __restrict__
         }
     for (int q = 16; q > 0; q >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, q));
     int e = 0;
-    if (m > 0.f) frexpf(m, &e);  // |z| 2^-e < 1 (also for z1 + zlo, see the comment above)
+    if (m > 0.f) frexpf(m, &e);  // |z| 2^-(e+1) < 1/2 (also for z1 + zlo, see the comment above)
     if (live && lane == 0) reinterpret_cast<int*>(W + o.ea)[r] = e;
-    const float sc = ldexpf(1.f, -e);
+    const float sc = ldexpf(1.f, -(e + 1));
     __nv_bfloat16* SA = reinterpret_cast<__nv_bfloat16*>(W + o.sa);
     const int q = r >> 6, rr = r & 63;
     for (int jc = lane; jc < o.ntk * 8; jc += 32) {
@@ -551,7 +557,7 @@ __global__ void __launch_bounds__(256) k_phi_slice_b(const MmfDesc* __restrict__
     int e = 0;
     if (m > 0.f) frexpf(m, &e);
     if (live && lane == 0) reinterpret_cast<int*>(W + o.eb)[t] = e;
-    const float sc = ldexpf(1.f, -e);
+    const float sc = ldexpf(1.f, -(e + 1));
     __nv_bfloat16* SB = reinterpret_cast<__nv_bfloat16*>(W + o.sb);
     const int q = t >> 6, rr = t & 63;
     for (int jc = lane; jc < o.ntk * 8; jc += 32) {
@@ -724,7 +730,7 @@ __global__ void __launch_bounds__(OZ_WARPS * 32, 1) k_oz_phi(const MmfDesc* __re
         bool ok = true;
         for (int a = 0; a <= OZ_L && ok; ++a)
             for (int b = 0; a + b <= OZ_L && ok; ++b) {
-                const int sh = 6 * (OZ_L - a - b) - 6;
+                const int sh = OZ_W * (OZ_L - a - b);
                 for (int kc = 0; kc < nkc; ++kc, ++c) {
                     const int buf = c & 1;
                     if (!oz_wait(&accfull[buf], ((uint32_t)c >> 1) & 1u, abort_flag)) { ok = false; break; }
@@ -772,7 +778,7 @@ __global__ void __launch_bounds__(OZ_WARPS * 32, 1) k_oz_phi(const MmfDesc* __re
                     for (int q = 0; q < 32; ++q) {
                         const int t = J * OZ_TN + g + q;
                         if (t < nt) {
-                            const int sc = er + eb[t] - 6 * (OZ_L + 2) + 6;
+                            const int sc = er + eb[t] + 2 - OZ_W * (OZ_L + 2);
                             const long long ar = (long long)(((unsigned long long)rhi[q] << 32) | rlo[q]);
                             const long long ai = (long long)(((unsigned long long)ihi[q] << 32) | ilo[q]);
                             Phi[(int64_t)r * nt + t] = make_double2(ldexp((double)ar, sc), ldexp((double)ai, sc));

@@ -734,7 +734,7 @@ static int stage_assemble(mmf_batch* b) {
 // G = X1^H X1 (+ C' + C'^H in a second full step): BF16 tensor cores with exact slicing, or
 // double-FP32 on the FP32 pipes
 static cudaError_t refine_gram(mmf_batch* b, const MmfLaunch& L, int second) {
-    if (b->gram_kernel == 0) {
+    if (b->gram_kernel == 0 && L.nmax <= mmf_ozaki_max_n()) {
         cudaError_t e = mmf_launch_ozaki_gram(L, b->d_X1, b->d_oz, b->d_ozexp, b->d_R, b->d_status);
         if (e != cudaSuccess || !second) return e;
         return mmf_launch_refine_gram_fix(L, b->d_R, b->d_T);

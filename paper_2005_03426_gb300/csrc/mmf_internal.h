@@ -223,9 +223,10 @@ cudaError_t mmf_launch_refine_band_g(const MmfLaunch& L, const double2* X, doubl
 cudaError_t mmf_launch_refine_finish(const MmfLaunch& L, double2* X, double* E, const double* lam, double2* S,
                                      int64_t mat_elems);
 // Gram product on the BF16 tensor cores by exact integer slicing (k_ozaki.cu)
-#define OZ_S 7
+#define OZ_S 5
 size_t mmf_ozaki_slice_elems(int n);
 cudaError_t mmf_launch_ozaki_gram(const MmfLaunch& L, const float2* X1, void* S, int* exps, double2* G, int* err);
+int mmf_ozaki_max_n();  // largest n the exact-slicing Gram product takes (int64 range)
 // time evolution on the tensor cores (mixed path): Phi by exact slicing, then U in FP64; operands
 // and Phi in the system's operand area (mmf_phi_elems BF16 units); Dmax <= mmf_phi_max_levels()
 int64_t mmf_phi_elems(int n, int D, int M, int nt);

@@ -28,9 +28,10 @@ def test_tensor_core_gemm(kind, shape, products):
 @pytest.mark.parametrize("n", [1, 37, 64, 129, 300, 1323, 2049, 4100])
 def test_gram_on_tensor_cores_is_fp64_accurate(n):
     """The mixed path's Gram product by exact integer slicing on the BF16 tensor cores against an
-    FP64 reference: sizes below, at and across the 128 x 64 tiles, the K-chunking (2n > 3968)
-    and entries spread over six orders of magnitude.  Bound: 2^-40 per entry for columns of
-    norm <= sqrt(n)/2 (each slice pair is exact; only the 42-bit truncation remains)."""
+    FP64 reference: sizes below, at and across the 128 x 64 tiles, the K-chunking (2n > 1024)
+    and entries spread over six orders of magnitude.  Bound: 2^-38 per entry for columns of
+    norm <= sqrt(n)/2 (each slice pair is exact; only the truncation to 40 bits below each
+    column's largest entry and the dropped slice pairs remain)."""
     err, ref = ctypes.c_double(0), ctypes.c_double(0)
     rc = M.lib().mmf_selftest_gram(n, ctypes.byref(err), ctypes.byref(ref))
     assert rc == 0, M.lib().mmf_last_error()
