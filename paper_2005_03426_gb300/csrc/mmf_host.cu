@@ -427,7 +427,9 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
             // one area per system, used in turn by the back-transform's operands, the Gram slices
             // (BF16) and split-TF32 operands of the refinement, and the time evolution's slices and Phi
             const int64_t oz = ctx->gram_kernel == 0 ? (int64_t)mmf_ozaki_slice_elems((int)n) : 0;
-            const int64_t ph = (nt > 0 && s->D <= mmf_phi_max_levels()) ? mmf_phi_elems((int)n, s->D, (int)M, nt) : 0;
+            const int64_t ph = (nt > 0 && s->D <= mmf_phi_max_levels() && M <= mmf_ozaki_max_n())
+                                   ? mmf_phi_elems((int)n, s->D, (int)M, nt)
+                                   : 0;
             b->n_oz += std::max<int64_t>(std::max<int64_t>(oz, 2 * mmf_tf3_floats((int)n)),
                                          std::max<int64_t>(tc ? 2 * mmf_bt_floats((int)n) : 0, ph));
         }
@@ -842,7 +844,9 @@ static int stage_outputs(mmf_batch* b) {
     float2* Z1 = b->precision == MMF_MIXED ? b->d_X1 : b->d_Zs;
     float2* Zlo = b->precision == MMF_MIXED ? reinterpret_cast<float2*>(b->d_T) : b->d_Zs + b->n_mat;
     // mixed path: U on the tensor cores (exact slicing) unless a system has too many levels
-    const bool phi = b->precision == MMF_MIXED && b->nt > 0 && b->Dmax <= mmf_phi_max_levels();
+    // (the int64 sums of the exact slicing bound K = 2M as they bound the Gram product's 2n)
+    const bool phi = b->precision == MMF_MIXED && b->nt > 0 && b->Dmax <= mmf_phi_max_levels() &&
+                     b->Mmax <= mmf_ozaki_max_n();
     LAUNCH(mmf_launch_outputs(La, b->Mmax, b->Dmax, b->d_E, b->d_Zf, Z1, Zlo, b->d_t, b->t0, b->nt, b->d_F,
                               b->d_U, b->d_P, 1e-8, phi ? 1 : 0),
            b->nt > 0 ? (phi ? 3 : 4) : 1);
