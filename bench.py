@@ -251,9 +251,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--serve", action="store_true", help="only the serving rate sweep")
-    ap.add_argument("--workload", default="spin1", choices=["spin1", "uneven", "large"],
+    ap.add_argument("--workload", default="spin1", choices=["spin1", "uneven", "large", "lattice"],
                     help="spin1: 64 spin-1 systems n=1323 (default); uneven: 4096 systems n=18..2000; "
-                         "large: one D=8 three-mode system n=17576 with U at 256 times")
+                         "large: one D=8 three-mode system n=17576 with U at 256 times; "
+                         "lattice: 64 frequencies of the D=256 driven lattice, n=1792, spectrum and Pbar")
     ap.add_argument("--serve-requests", type=int, default=240)
     ap.add_argument("--count", type=int, default=COUNT,
                     help="systems per step (64 = the benchmark workload; smaller for profiler captures)")
@@ -302,6 +303,12 @@ def main():
     elif args.workload == "large":
         count, nt = 1, 256
         problems = [W.large_instance(seed=3 + rank)]
+    elif args.workload == "lattice":
+        # spectrum-versus-frequency sweep of the driven lattice: quasienergies, eigenvectors and
+        # Pbar at every frequency (no time grid); each rank takes its own slice of the band
+        nt = 0
+        lo, hi = 0.2 + 0.8 * rank / world, 0.2 + 0.8 * (rank + 1) / world
+        problems = W.lattice_sweep(count, lo=lo, hi=hi)
     else:
         problems = W.spin1_amplitude_set(count, seed=1 + rank)
     ctx = M.Context(local, stream=stream.cuda_stream)
@@ -404,6 +411,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": ("uneven_batch_n18_2000" if args.workload == "uneven" else
                                         "large_D8_three_mode_n17576" if args.workload == "large" else
+                                        f"driven_lattice_D256_N3_n1792_x{count}" if args.workload == "lattice" else
                                         WORKLOAD if count == COUNT else f"{WORKLOAD}[:{count}]"),
                            "systems_per_step": count, "n": n, "nt": nt,
                            "precision": args.precision, "l2": "working set > L2 (no flush)",

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(256) k_phase_table(const MmfDesc* __restrict__
 }
 
 #define U_TPW 8  // times per warp per pass (8 warps -> 64 times per pass)
+#define PB_DSMALL 64  // Pbar in one shared-memory table per system up to this many levels
 
 // Z split once into FP32 pieces, Z = Z1 + Zlo (Z1 = fl32(Z), Zlo = fl32(Z - Z1)), so that the
 // contraction below converts nothing on the FP64 pipe.
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(256) k_transition_avg(const MmfDesc* __restric
     extern __shared__ __align__(16) double psm[];
     const MmfDesc d = descs[idx[blockIdx.y]];
     const int n = d.n, D = d.D;
+    if (D > PB_DSMALL) return;  // many levels: k_pbar_weights / k_pbar_product / k_pbar_clusters
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double* Ps = psm;                     // D*D
     double* Ws = psm + D * D + warp * D;  // per warp D
@@ -166,12 +168,143 @@ __global__ void __launch_bounds__(256) k_transition_avg(const MmfDesc* __restric
         if (Ps[e] != 0.0) atomicAdd(&P[d.p_off + e], Ps[e]);
 }
 
+// ------------------------------------------------------------------ Pbar for many levels
+// Above PB_DSMALL levels the per-system D x D table of k_transition_avg no longer fits shared
+// memory (D = 256 for the driven lattice of Sec. 4.2).  The same sum is then split as
+//   Pbar_{i->j} = sum_l a_il w_jl  +  sum_{C, |C| >= 2} ( sum_b |sum_{l in C} Z[(j,b),l] conj(Z[(i,b0),l])|^2
+//                                                       - sum_{l in C} a_il w_jl )
+//   a_il = |Z[(i,b0),l]|^2,   w_jl = sum_b |Z[(j,b),l]|^2
+// (the singleton clusters give the first sum).  The first sum is a D x n x D product of
+// non-negative terms, tiled in FP64; the cluster terms are added per cluster.  w is kept in a
+// scratch slot of D n doubles per system (the H_F slot, free once the eigenvectors exist).
+#define PB_T 64   // output tile (i, j)
+#define PB_KC 16  // eigenvectors per staged chunk
+
+__device__ __forceinline__ double* pb_w(void* scratch, int esz, const MmfDesc& d) {
+    return reinterpret_cast<double*>(static_cast<unsigned char*>(scratch) + (size_t)esz * d.mat_off);
+}
+
+// w[l * D + j] = sum_b |Z[(j, b), l]|^2; consecutive threads take consecutive j (coalesced in Z)
+__global__ void __launch_bounds__(256) k_pbar_weights(const MmfDesc* __restrict__ descs,
+                                                      const int* __restrict__ idx,
+                                                      const double2* __restrict__ Zg, void* scratch,
+                                                      int esz) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    if (d.D <= PB_DSMALL) return;
+    const int D = d.D, M = d.M;
+    const double2* Z = Zg + d.mat_off;
+    double* w = pb_w(scratch, esz, d);
+    const int64_t tot = (int64_t)d.n * D;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(e / D), j = (int)(e - (int64_t)l * D);
+        const double2* zc = Z + (int64_t)l * d.ld + j;
+        double acc = 0.0;
+        for (int b = 0; b < M; ++b) acc += abs2(zc[(int64_t)b * D]);
+        w[e] = acc;
+    }
+}
+
+// P[i * D + j] = sum_l a_il w_jl over one 64 x 64 (i, j) tile; 256 threads, 4 x 4 outputs each
+__global__ void __launch_bounds__(256) k_pbar_product(const MmfDesc* __restrict__ descs,
+                                                      const int* __restrict__ idx,
+                                                      const double2* __restrict__ Zg,
+                                                      const void* scratch, int esz,
+                                                      double* __restrict__ P) {
+    __shared__ double As[PB_KC][PB_T];
+    __shared__ double Ws[PB_KC][PB_T];
+    const MmfDesc d = descs[idx[blockIdx.z]];
+    const int D = d.D;
+    if (D <= PB_DSMALL) return;
+    const int ti = blockIdx.y * PB_T, tj = blockIdx.x * PB_T;
+    if (ti >= D || tj >= D) return;
+    const double2* Z0 = Zg + d.mat_off + (int64_t)D * d.b0;  // central block rows (i, b0)
+    const double* w = pb_w(const_cast<void*>(scratch), esz, d);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+    for (int l0 = 0; l0 < d.n; l0 += PB_KC) {
+        for (int e = threadIdx.x; e < PB_KC * PB_T; e += 256) {
+            const int k = e / PB_T, r = e - k * PB_T, l = l0 + k;
+            const bool ok = l < d.n;
+            As[k][r] = (ok && ti + r < D) ? abs2(Z0[(int64_t)l * d.ld + ti + r]) : 0.0;
+            Ws[k][r] = (ok && tj + r < D) ? w[(int64_t)l * D + tj + r] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PB_KC; ++k) {
+            double av[4], wv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[k][ty + 16 * a];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) wv[c] = Ws[k][tx + 16 * c];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], wv[c], acc[a][c]);
+        }
+        __syncthreads();
+    }
+    double* Po = P + d.p_off;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = ti + ty + 16 * a;
+        if (i >= D) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = tj + tx + 16 * c;
+            if (j < D) Po[(int64_t)i * D + j] = acc[a][c];
+        }
+    }
+}
+
+// Cluster terms: one block per leading eigenvalue of a cluster of two or more (gaps < delta),
+// its threads over the (i, j) pairs; added after k_pbar_product on the same stream.
+__global__ void __launch_bounds__(256) k_pbar_clusters(const MmfDesc* __restrict__ descs,
+                                                       const int* __restrict__ idx,
+                                                       const double* __restrict__ Eg,
+                                                       const double2* __restrict__ Zg,
+                                                       const void* scratch, int esz, double cluster_rel,
+                                                       double* __restrict__ P) {
+    const MmfDesc d = descs[idx[blockIdx.y]];
+    const int n = d.n, D = d.D, M = d.M;
+    if (D <= PB_DSMALL) return;
+    const double* E = Eg + d.vec_off;
+    const double delta = cluster_rel * fmax(fabs(E[0]), fabs(E[n - 1]));
+    const double* w = pb_w(const_cast<void*>(scratch), esz, d);
+    const double2* Z = Zg + d.mat_off;
+    for (int lam = blockIdx.x; lam < n; lam += gridDim.x) {
+        if (lam > 0 && E[lam] - E[lam - 1] < delta) continue;  // not a cluster's first eigenvalue
+        int c1 = lam + 1;
+        while (c1 < n && E[c1] - E[c1 - 1] < delta) ++c1;
+        if (c1 == lam + 1) continue;
+        for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
+            const int i = e / D, j = e - i * D;
+            double diag = 0.0, tot = 0.0;
+            for (int l = lam; l < c1; ++l)
+                diag += abs2(Z[(int64_t)l * d.ld + i + D * d.b0]) * w[(int64_t)l * D + j];
+            for (int b = 0; b < M; ++b) {
+                double2 amp = make_double2(0.0, 0.0);
+                for (int l = lam; l < c1; ++l) {
+                    const double2* zc = Z + (int64_t)l * d.ld;
+                    amp = amp + cmulc(zc[i + D * d.b0], zc[j + D * b]);
+                }
+                tot += abs2(amp);
+            }
+            atomicAdd(&P[d.p_off + e], tot - diag);
+        }
+    }
+}
+
 // Staged launcher with explicit maxima (the batch knows them).
 // skip_u: the phase table and the FP32 pieces of Z are prepared, but U is left to the
 // tensor-core path (mmf_launch_phi)
 cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const double* E,
                                   const double2* Z, float2* Z1, float2* Zlo, const double* t, double t0, int nt,
-                                  double2* F2, double2* U, double* P, double cluster_rel, int skip_u) {
+                                  double2* F2, double2* U, double* P, double cluster_rel, int skip_u,
+                                  void* scratch, int scratch_esz) {
     static_assert(sizeof(Split) == sizeof(double2), "phase table slots hold one Split each");
     Split* F = reinterpret_cast<Split*>(F2);
     if (L.count <= 0) return cudaSuccess;
@@ -184,7 +317,8 @@ cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const dou
             k_time_evolution<<<dim3((L.nmax + 31) / 32, L.count), 256, 0, L.stream>>>(
                 L.desc, L.idx, E, Z, Z1, Zlo, t, t0, nt, F, U);
     }
-    size_t sm = sizeof(double) * (size_t)(Dmax * Dmax + 8 * Dmax);
+    const int Ds = Dmax < PB_DSMALL ? Dmax : PB_DSMALL;
+    size_t sm = sizeof(double) * (size_t)(Ds * Ds + 8 * Ds);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_transition_avg,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -192,6 +326,19 @@ cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const dou
     }
     k_transition_avg<<<dim3((L.nmax + 7) / 8, L.count), 256, sm, L.stream>>>(L.desc, L.idx, E, Z,
                                                                             cluster_rel, P);
+    if (Dmax > PB_DSMALL) {
+        // scratch holds D n doubles per system at byte offset scratch_esz * mat_off
+        if (!scratch || scratch_esz < (int)sizeof(double)) return cudaErrorInvalidValue;
+        const int64_t wt = (int64_t)L.nmax * Dmax;
+        int gx = (int)((wt + 255) / 256);
+        if (gx > 2048) gx = 2048;
+        k_pbar_weights<<<dim3(gx, L.count), 256, 0, L.stream>>>(L.desc, L.idx, Z, scratch, scratch_esz);
+        const int nt_ = (Dmax + PB_T - 1) / PB_T;
+        k_pbar_product<<<dim3(nt_, nt_, L.count), 256, 0, L.stream>>>(L.desc, L.idx, Z, scratch, scratch_esz, P);
+        int gc = L.nmax < 1024 ? L.nmax : 1024;
+        k_pbar_clusters<<<dim3(gc, L.count), 256, 0, L.stream>>>(L.desc, L.idx, E, Z, scratch, scratch_esz,
+                                                                 cluster_rel, P);
+    }
     return cudaGetLastError();
 }
 

@@ -26,9 +26,14 @@
 // Below that size the second step is hybrid (below): C for all pairs as in the first step, G
 // (FP64-accurate) only on the band |i - j| <= RF_W, where the near pairs need it.
 // A pair is treated as clustered when |lam_i - lam_j| <= 20 |s_ij - lam_j g_ij| (the first-order
-// correction would exceed 0.05) or the gap is below 1e-13 |H_F|; consecutive clustered indices
+// correction would exceed 0.05) or the gap is below RF_GAMMA |H_F|; consecutive clustered indices
 // form a cluster whose eigenvectors are separated by an FP64 Jacobi solve of the small
-// projected matrix X_C^H H_F X_C (clusters of up to RF_CMAX vectors).
+// projected matrix X_C^H H_F X_C (clusters of up to RF_CMAX vectors).  The second rule matters
+// for (near-)degenerate pairs: there the gap of the Rayleigh quotients and s_ij - lam_j g_ij are
+// both second order in the FP32 error, their ratio is meaningless, and a first-order correction
+// taken from it ruins the pair.  RF_GAMMA = 3e-5 keeps every pair that FP32 eigenvectors cannot
+// resolve well (mixing eps32 |H_F| / gap above ~2e-3) in a cluster in both steps, so that the
+// first step leaves second-order errors below ~1e-5 and the second below ~1e-10.
 #include <algorithm>
 
 #include "mmf_internal.h"
@@ -38,6 +43,7 @@
 #define RF_KG 16   // k-chunk of the FP64-accurate Gram kernel
 #define RF_CMAX 32
 #define RF_TAU 20.0
+#define RF_GAMMA 3e-5
 // Band |i - j| <= RF_W of the sorted eigenpairs: every step applies Et there in double-FP32
 // (entries up to ~0.05), and the hybrid second step forms G only inside it.
 #define RF_W 16
@@ -405,7 +411,7 @@ __global__ void __launch_bounds__(256) k_oa_lambda(const MmfDesc* __restrict__ d
         if (i + 1 < n) {
             const double gap = fabs(lam[i + 1] - lam[i]);
             const double2 num = oa_num(C, n, i, i + 1, G[(int64_t)(i + 1) * d.ld + i], lam[i + 1] - lam0[i + 1]);
-            link = (gap <= RF_TAU * sqrt(abs2(num))) || (gap <= 1e-13 * hmax);
+            link = (gap <= RF_TAU * sqrt(abs2(num))) || (gap <= RF_GAMMA * hmax);
         }
         cid[i] = link;
     }
@@ -438,7 +444,7 @@ __global__ void __launch_bounds__(256) k_oa_etilde(const MmfDesc* __restrict__ d
     const double* lam = lamg + d.vec_off;
     const int* cid = cidg + d.vec_off;
     double hmax = fmax(fabs(lam[0]), fabs(lam[n - 1]));
-    const float tiny = (float)(1e-13 * hmax);  // |lam_i| <= hmax (ascending order)
+    const float tiny = (float)(RF_GAMMA * hmax);  // |lam_i| <= hmax (ascending order)
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int j = (int)(e / n), i = (int)(e - (int64_t)j * n);
@@ -452,7 +458,7 @@ __global__ void __launch_bounds__(256) k_oa_etilde(const MmfDesc* __restrict__ d
             const double2 num = oa_num(C, n, i, j, g, lam[j] - lam0[j]);
             const double gap = lam[j] - lam[i];
             const bool clustered = cid[i] == cid[j] || gap * gap <= RF_TAU * RF_TAU * abs2(num) ||
-                                   fabs(gap) <= 1e-13 * fmax(hmax, fabs(lam[i]));
+                                   fabs(gap) <= RF_GAMMA * fmax(hmax, fabs(lam[i]));
             et = clustered ? (-0.5) * g : (1.0 / gap) * num;
         } else {
             // off the band Et goes through the split-TF32 product (FP32 accuracy): FP32 here,
@@ -676,7 +682,8 @@ __global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ de
 }
 
 // ------------------------------------------------------------------ cluster separation
-// One CTA per system; clusters handled one after another.  For cluster C (m vectors):
+// Clusters are independent: each CTA of a system takes every gridDim.x-th candidate first index.
+// For cluster C (m vectors):
 // B = X_C^H H_F X_C in FP64 (H_F X_C from the HX buffer, recomputed for the new X), cyclic
 // Jacobi on B, X_C <- X_C W, lam_C <- eigenvalues of B ascending.
 // CTA-parallel two-sided Jacobi on the m x m Hermitian B (column-major, ld RF_CMAX), with the
@@ -778,7 +785,7 @@ __global__ void __launch_bounds__(256) k_cluster_sep(const MmfDesc* __restrict__
     __shared__ double rot[4 * (RF_CMAX / 2)];
     __shared__ int pq[RF_CMAX + 2];
     __shared__ int flag;
-    const int sid = idx[blockIdx.x];
+    const int sid = idx[blockIdx.y];
     const MmfDesc d = descs[sid];
     const int n = d.n, D = d.D;
     double2* X = Xg + d.mat_off;
@@ -786,9 +793,10 @@ __global__ void __launch_bounds__(256) k_cluster_sep(const MmfDesc* __restrict__
     double* lam = lamg + d.vec_off;
     const int* cid = cidg + d.vec_off;
     const double2* H0 = coef + d.coef_off;
-    int c0 = 0;
-    while (c0 < n) {
-        int c1 = c0 + 1;
+    // clusters are disjoint: the CTAs of a system take them in parallel (c0 = first index)
+    for (int c0 = blockIdx.x; c0 < n; c0 += gridDim.x) {
+        if (cid[c0] != c0 || c0 + 1 >= n || cid[c0 + 1] != c0) continue;
+        int c1 = c0 + 2;
         while (c1 < n && cid[c1] == c0) ++c1;
         const int m = c1 - c0;
         if (m >= 2 && m <= RF_CMAX) {
@@ -866,7 +874,6 @@ __global__ void __launch_bounds__(256) k_cluster_sep(const MmfDesc* __restrict__
         } else if (m > RF_CMAX) {
             if (threadIdx.x == 0) status[sid] = MMF_ST_CLUSTER;
         }
-        c0 = c1;
     }
 }
 
@@ -1036,7 +1043,8 @@ cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, do
         L.desc, L.idx, X, X1, G, Eb, HX);
     e = cudaMemcpyAsync(X, HX, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
     if (e != cudaSuccess) return e;
-    k_cluster_sep<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, coef, X, HX, lam, cid, status);
+    k_cluster_sep<<<dim3(std::min(L.nmax, 1024), L.count), 256, 0, L.stream>>>(L.desc, L.idx, coef, X, HX, lam, cid,
+                                                                                status);
     return cudaGetLastError();
 }
 

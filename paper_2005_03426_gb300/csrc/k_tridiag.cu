@@ -277,47 +277,74 @@ __device__ __forceinline__ R hash_unit(uint64_t x) {
 }
 
 // Solve (T - lam I) y = y in place; u0/u1/u2 are the (strided) U factor arrays.
+#define TRI_PF 8   // steps whose loads are issued ahead of the recurrence (latency hiding)
+
+// (T - lam I) y = b by Gaussian elimination with partial pivoting on the band; the factors go to
+// u0, u1, u2 (row stride s), the loads of each TRI_PF steps are issued before their recurrence.
 template <class R, class In>
 __device__ void tri_solve(const In& in, int n, R lam, R pivtiny, R* y, R* u0, R* u1, R* u2, int64_t s) {
     R p = in.dv(0) - lam, q = (n > 1) ? in.ev(0) : R(0), r = R(0), rb = y[0];
-    for (int i = 0; i < n - 1; ++i) {
-        const R a = in.ev(i);
-        const R bb = in.dv(i + 1) - lam;
-        const R cc = (i + 1 < n - 1) ? in.ev(i + 1) : R(0);
-        const R b1 = y[(int64_t)(i + 1) * s];
-        if (fabs(a) <= fabs(p)) {
-            if (p == R(0)) p = pivtiny;
-            const R l = tdiv(a, p);
-            u0[(int64_t)i * s] = p; u1[(int64_t)i * s] = q; u2[(int64_t)i * s] = r;
-            y[(int64_t)i * s] = rb;
-            p = bb - l * q; q = cc - l * r; r = R(0); rb = b1 - l * rb;
-        } else {
-            const R l = tdiv(p, a);
-            u0[(int64_t)i * s] = a; u1[(int64_t)i * s] = bb; u2[(int64_t)i * s] = cc;
-            y[(int64_t)i * s] = b1;
-            const R np = q - l * bb, nq = r - l * cc, nrb = rb - l * b1;
-            p = np; q = nq; r = R(0); rb = nrb;
+    for (int i0 = 0; i0 < n - 1; i0 += TRI_PF) {
+        R av[TRI_PF], dv[TRI_PF], cv[TRI_PF], b1v[TRI_PF];
+#pragma unroll
+        for (int u = 0; u < TRI_PF; ++u) {
+            const int i = i0 + u;
+            const bool ok = i < n - 1;
+            av[u] = ok ? in.ev(i) : R(0);
+            dv[u] = ok ? in.dv(i + 1) : R(0);
+            cv[u] = (i + 1 < n - 1) ? in.ev(i + 1) : R(0);
+            b1v[u] = ok ? y[(int64_t)(i + 1) * s] : R(0);
+        }
+#pragma unroll
+        for (int u = 0; u < TRI_PF; ++u) {
+            const int i = i0 + u;
+            if (i >= n - 1) break;
+            const R a = av[u], bb = dv[u] - lam, cc = cv[u], b1 = b1v[u];
+            if (fabs(a) <= fabs(p)) {
+                if (p == R(0)) p = pivtiny;
+                const R l = tdiv(a, p);
+                u0[(int64_t)i * s] = p; u1[(int64_t)i * s] = q; u2[(int64_t)i * s] = r;
+                y[(int64_t)i * s] = rb;
+                p = bb - l * q; q = cc - l * r; r = R(0); rb = b1 - l * rb;
+            } else {
+                const R l = tdiv(p, a);
+                u0[(int64_t)i * s] = a; u1[(int64_t)i * s] = bb; u2[(int64_t)i * s] = cc;
+                y[(int64_t)i * s] = b1;
+                const R np = q - l * bb, nq = r - l * cc, nrb = rb - l * b1;
+                p = np; q = nq; r = R(0); rb = nrb;
+            }
         }
     }
     if (fabs(p) < pivtiny) p = (p < R(0)) ? -pivtiny : pivtiny;
     u0[(int64_t)(n - 1) * s] = p;
-    // back substitution
     R y2 = R(0), y1 = tdiv(rb, p);
     y[(int64_t)(n - 1) * s] = y1;
-    for (int i = n - 2; i >= 0; --i) {
-        R up = u0[(int64_t)i * s];
-        if (fabs(up) < pivtiny) up = (up < R(0)) ? -pivtiny : pivtiny;
-        const R yi = tdiv(y[(int64_t)i * s] - u1[(int64_t)i * s] * y1 - u2[(int64_t)i * s] * y2, up);
-        y[(int64_t)i * s] = yi;
-        y2 = y1;
-        y1 = yi;
+    for (int i0 = n - 2; i0 >= 0; i0 -= TRI_PF) {
+        R f0[TRI_PF], f1[TRI_PF], f2[TRI_PF], fy[TRI_PF];
+#pragma unroll
+        for (int u = 0; u < TRI_PF; ++u) {
+            const int i = i0 - u;
+            const bool ok = i >= 0;
+            f0[u] = ok ? u0[(int64_t)i * s] : R(1);
+            f1[u] = ok ? u1[(int64_t)i * s] : R(0);
+            f2[u] = ok ? u2[(int64_t)i * s] : R(0);
+            fy[u] = ok ? y[(int64_t)i * s] : R(0);
+        }
+#pragma unroll
+        for (int u = 0; u < TRI_PF; ++u) {
+            const int i = i0 - u;
+            if (i < 0) break;
+            R up = f0[u];
+            if (fabs(up) < pivtiny) up = (up < R(0)) ? -pivtiny : pivtiny;
+            const R yi = tdiv(fy[u] - f1[u] * y1 - f2[u] * y2, up);
+            y[(int64_t)i * s] = yi;
+            y2 = y1;
+            y1 = yi;
+        }
     }
 }
 
-// FP32 variant: the three U-factor entries of row i and the eliminated right-hand side are kept
-// together, F[i * s] = (u0, u1, u2, rhs), so that each step of either sweep moves one 16-byte
-// word per thread (the sweeps are latency-bound chains).
-#define TRI_PF 8   // steps whose loads are issued ahead of the recurrence (latency hiding)
+
 
 template <class In>
 __device__ void tri_solve_packed(const In& in, int n, float lam, float pivtiny, float* y, float4* F, int64_t s) {
@@ -452,7 +479,9 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
             for (int jp = k; jp < j && sizeof(R) == 8; ++jp) {
                 const R* z = Yw + jp;
                 R dot = R(0);
+#pragma unroll 8
                 for (int i = 0; i < n; ++i) dot += y[(int64_t)i * s] * z[(int64_t)i * s];
+#pragma unroll 8
                 for (int i = 0; i < n; ++i) y[(int64_t)i * s] -= dot * z[(int64_t)i * s];
             }
             R mx = R(0);

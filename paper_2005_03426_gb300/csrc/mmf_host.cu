@@ -848,7 +848,8 @@ static int stage_outputs(mmf_batch* b) {
     const bool phi = b->precision == MMF_MIXED && b->nt > 0 && b->Dmax <= mmf_phi_max_levels() &&
                      b->Mmax <= mmf_ozaki_max_n();
     LAUNCH(mmf_launch_outputs(La, b->Mmax, b->Dmax, b->d_E, b->d_Zf, Z1, Zlo, b->d_t, b->t0, b->nt, b->d_F,
-                              b->d_U, b->d_P, 1e-8, phi ? 1 : 0),
+                              b->d_U, b->d_P, 1e-8, phi ? 1 : 0, b->d_H,
+                              b->precision == MMF_MIXED ? (int)sizeof(float2) : (int)sizeof(double2)),
            b->nt > 0 ? (phi ? 3 : 4) : 1);
     if (phi)
         LAUNCH(mmf_launch_phi(La, b->Dmax, b->nt, Z1, Zlo, b->d_F, b->d_E, b->d_Zf, b->d_t, b->t0, b->d_oz, b->d_U,

@@ -202,7 +202,8 @@ cudaError_t mmf_launch_backtransform(const MmfLaunch& L, const void* H, const vo
 cudaError_t mmf_launch_widen(const MmfLaunch& L, const void* Zp, double2* Z, int fp32);
 cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const double* E,
                                const double2* Z, float2* Z1, float2* Zlo, const double* t, double t0, int nt,
-                               double2* F, double2* U, double* P, double cluster_rel, int skip_u);
+                               double2* F, double2* U, double* P, double cluster_rel, int skip_u,
+                               void* scratch, int scratch_esz);
 int mmf_hetrd_max_n(int fp32);
 cudaError_t mmf_launch_hetrd_large(const MmfDesc& d, void* H, void* Vp, void* Wp, double* dvec, double* evec,
                                    void* tau, void* work, void* sc, int fp32, cudaStream_t st);

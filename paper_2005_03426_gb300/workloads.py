@@ -232,6 +232,39 @@ def large_instance(seed: int = 3, D: int = 8, N: int = 6, sigma: float = 0.05) -
     return Problem(D=D, H0=H0, omegas=omegas, Ns=[N, N, N], couplings=couplings)
 
 
+def driven_lattice(omega: float, D: int = 256, N: int = 3, V0: float = 0.25, t: float = 0.125,
+                   V: float = 0.0625, phi: float = 0.0) -> Problem:
+    """Harmonically driven 1-D lattice (Sec. 4.2, Eq. 9): D sites, D/2 two-site cells.
+
+    Site m = 1..D (1-based, as in Eq. 9) has the offset (-1)^m V0.  The static hopping from
+    site m to m+1 (m = 1..D-1) is t e^{i cos(2 pi m / D)}, with its Hermitian conjugate.  The
+    same bonds carry the uniform modulation V cos(w t + phi).  In this module's convention
+    that modulation is V^{1,1} = (V/2) e^{i phi} A, with A the real nearest-neighbour adjacency
+    (its conjugate term gives the e^{-i w t} part).  One mode, Fourier truncation N, so
+    n = D (2N + 1)."""
+    H0 = np.zeros((D, D), dtype=np.complex128)
+    A = np.zeros((D, D), dtype=np.complex128)
+    for m in range(1, D + 1):
+        H0[m - 1, m - 1] = V0 if m % 2 == 0 else -V0
+    for m in range(1, D):
+        h = t * complex(math.cos(math.cos(2.0 * math.pi * m / D)), math.sin(math.cos(2.0 * math.pi * m / D)))
+        H0[m - 1, m] = h
+        H0[m, m - 1] = h.conjugate()
+        A[m - 1, m] = 1.0
+        A[m, m - 1] = 1.0
+    Vc = 0.5 * V * complex(math.cos(phi), math.sin(phi)) * A
+    return Problem(D=D, H0=H0, omegas=[float(omega)], Ns=[N], couplings=[[Vc]])
+
+
+def lattice_sweep(count: int = 64, lo: float = 0.2, hi: float = 1.0, D: int = 256,
+                  N: int = 3) -> List[Problem]:
+    """Spectrum-versus-frequency sweep of the driven lattice (Fig. 5's parameters: D = 256,
+    V0 = 0.25, t = 0.125, V = 0.0625, phi = 0): omega = linspace(lo, hi, count) inclusive,
+    N = 3 (n = 1792 at D = 256)."""
+    ws = np.linspace(lo, hi, count)
+    return [driven_lattice(float(w), D=D, N=N) for w in ws]
+
+
 def random_small(seed: int, D: int, Ns: List[int], nharm: List[int] | None = None,
                  sigma: float = 0.3, full_h0: bool = True) -> Problem:
     """Small random test system: Hermitian Gaussian H0 (or diagonal), per mode ``nharm[l]``

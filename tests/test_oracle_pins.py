@@ -198,6 +198,48 @@ def test_zero_coupling():
     np.testing.assert_allclose(r["P"], np.eye(D), atol=1e-14)
 
 
+def test_static_lattice_closed_form():
+    """Undriven lattice of Eq. 9 (V = 0): the staggered offsets anticommute with the
+    nearest-neighbour hopping, so H0^2 = V0^2 + T^2, and T (an open chain with |t| on every
+    bond; the bond phases gauge away) has eigenvalues 2 t cos(pi j/(D+1)).  Hence the static
+    levels are +-sqrt(V0^2 + 4 t^2 cos^2(pi j/(D+1))), j = 1..D/2, and the quasienergies are
+    those levels shifted by k w, k = -N..N.  With no drive, Pbar is the static time average
+    sum_a |<j|a>|^2 |<a|i>|^2 over the eigenvectors of H0 (LAPACK's, levels nondegenerate)."""
+    D, N, w, V0, tt = 12, 2, 0.53, 0.25, 0.125
+    p = W.driven_lattice(w, D=D, N=N, V0=V0, t=tt, V=0.0)
+    lev = [s * math.sqrt(V0 ** 2 + 4 * tt ** 2 * math.cos(math.pi * j / (D + 1)) ** 2)
+           for j in range(1, D // 2 + 1) for s in (1.0, -1.0)]
+    ev = sorted(e + k * w for e in lev for k in range(-N, N + 1))
+    r = O.solve(p)
+    np.testing.assert_allclose(r["E"], ev, rtol=0, atol=1e-14)
+    _, Q = np.linalg.eigh(p.H0)
+    w2 = np.abs(Q) ** 2
+    np.testing.assert_allclose(r["P"], w2 @ w2.T, rtol=0, atol=1e-13)
+
+
+def test_driven_lattice_matches_time_domain_integration():
+    """Driven lattice of Eq. 9 with a nonzero drive phase: the Floquet U(t, t0) at a converged
+    truncation equals DOP853 integration of Eq. 1 with H(t) written out from Eq. 9."""
+    D, w, V0, tt, V, phi = 6, 0.7, 0.25, 0.125, 0.3, 0.9
+
+    def ham(time):
+        H = np.zeros((D, D), dtype=complex)
+        for m in range(1, D + 1):
+            H[m - 1, m - 1] = (-1) ** m * V0
+        for m in range(1, D):
+            hop = tt * np.exp(1j * math.cos(2 * math.pi * m / D)) + V * math.cos(w * time + phi)
+            H[m - 1, m] = hop
+            H[m, m - 1] = np.conj(hop)
+        return H
+
+    t0, t1 = 0.2, 3.1
+    sol = solve_ivp(lambda s, y: (-1j * ham(s) @ y.reshape(D, D)).reshape(-1), (t0, t1),
+                    np.eye(D, dtype=complex).reshape(-1), method="DOP853", rtol=1e-12, atol=1e-13)
+    p = W.driven_lattice(w, D=D, N=14, V0=V0, t=tt, V=V, phi=phi)
+    U_f = O.solve(p, t=np.array([t1]), t0=t0)["U"][0]
+    np.testing.assert_allclose(U_f, sol.y[:, -1].reshape(D, D), rtol=0, atol=1e-9)
+
+
 def test_identity_at_t0_and_sum_rule():
     p = W.random_small(7, D=3, Ns=[2, 2], nharm=[2, 1])
     t0 = 0.77

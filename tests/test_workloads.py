@@ -47,3 +47,29 @@ def test_large_instance_shape():
     ev = np.linalg.eigvalsh(p.H0)
     assert ev.min() >= 0.0 and ev.max() <= 2.0
     assert np.allclose(p.H0, p.H0.conj().T)
+
+
+def test_driven_lattice_matches_eq9_in_time_domain():
+    """H(t) = H0 + V e^{iwt} + V^dagger e^{-iwt} from the generator equals Eq. 9 evaluated
+    directly at several times (offsets (-1)^m V0, hopping t e^{i cos(2 pi m/D)}, and the bond
+    modulation V cos(w t + phi)), for a nonzero phase."""
+    D, w, V0, tt, V, phi = 10, 0.55, 0.25, 0.125, 0.0625, 0.4
+    p = W.driven_lattice(w, D=D, N=2, V0=V0, t=tt, V=V, phi=phi)
+    assert p.n == D * 5 and p.K == 1 and p.Ns == [2]
+    for time in (0.0, 0.37, 2.9):
+        H = p.H0 + p.couplings[0][0] * np.exp(1j * w * time) + \
+            p.couplings[0][0].conj().T * np.exp(-1j * w * time)
+        ref = np.zeros((D, D), dtype=complex)
+        for m in range(1, D + 1):
+            ref[m - 1, m - 1] = (-1) ** m * V0
+        for m in range(1, D):
+            hop = tt * np.exp(1j * math.cos(2 * math.pi * m / D)) + V * math.cos(w * time + phi)
+            ref[m - 1, m] += hop
+            ref[m, m - 1] += np.conj(hop)
+        np.testing.assert_allclose(H, ref, rtol=0, atol=1e-15)
+
+
+def test_lattice_sweep_shape():
+    ps = W.lattice_sweep()
+    assert len(ps) == 64 and all(p.n == 1792 and p.D == 256 for p in ps)
+    assert ps[0].omegas[0] == 0.2 and ps[-1].omegas[0] == 1.0
