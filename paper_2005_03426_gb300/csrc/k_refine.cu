@@ -67,6 +67,40 @@ __global__ void __launch_bounds__(256) k_split_coef(const double2* __restrict__ 
     }
 }
 
+// Nonzero pattern of the coefficient rows (layout with coef_matrices in mmf_internal.h): one CTA
+// per system, a thread per (matrix, row).  Exact zeros only, so the sparse and dense sums agree.
+__global__ void __launch_bounds__(256) k_coef_pattern(const MmfDesc* __restrict__ descs,
+                                                      const int* __restrict__ idx,
+                                                      const double2* __restrict__ coef, int* __restrict__ patg) {
+    const MmfDesc d = descs[idx[blockIdx.x]];
+    const int cap = d.pat_cap;
+    if (cap <= 0) return;
+    const int D = d.D, nm = coef_matrices(d);
+    int* pat = patg + d.pat_off;
+    int* cnt = pat + 1;
+    int* jx = pat + 1 + nm * D;
+    __shared__ int ok;
+    if (threadIdx.x == 0) ok = 1;
+    __syncthreads();
+    for (int e = threadIdx.x; e < nm * D; e += blockDim.x) {
+        const int m = e / D, i = e - m * D;
+        const double2* A = coef + d.coef_off + (m == 0 ? 0 : (int64_t)(1 + (m - 1) / 2) * D * D);
+        const bool col = m > 0 && ((m - 1) & 1);  // rows of V^dagger: columns of V
+        int c = 0;
+        for (int j = 0; j < D; ++j) {
+            const double2 v = col ? A[j * D + i] : A[i * D + j];
+            if (v.x != 0.0 || v.y != 0.0) {
+                if (c < cap) jx[(int64_t)e * cap + c] = j;
+                ++c;
+            }
+        }
+        cnt[e] = c < cap ? c : cap;
+        if (c > cap) ok = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) pat[0] = ok;
+}
+
 // X1 = fl32(X) and (Xlo != nullptr) Xlo = fl32(X - X1)
 __global__ void __launch_bounds__(256) k_split_x(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                                                  const double2* __restrict__ Xg, float2* __restrict__ X1g,
@@ -101,6 +135,7 @@ __device__ __forceinline__ void df_cmulc_acc(DF& re, DF& im, const float4 h, flo
 __global__ void __launch_bounds__(256) k_apply_hf_df32(const MmfDesc* __restrict__ descs,
                                                        const int* __restrict__ idx,
                                                        const float4* __restrict__ cs,
+                                                       const int* __restrict__ patg,
                                                        const float2* __restrict__ X1g,
                                                        const float2* __restrict__ Xlog,
                                                        double2* __restrict__ HXg) {
@@ -120,31 +155,68 @@ __global__ void __launch_bounds__(256) k_apply_hf_df32(const MmfDesc* __restrict
     const float2* Xlo = Xlog ? Xlog + d.mat_off : nullptr;
     const float2 z = make_float2(0.f, 0.f);
     double2* HX = HXg + d.mat_off;
+    // sparse coefficient rows (the lattice's are tridiagonal): only the listed nonzeros are read
+    const int* pat = patg + d.pat_off;
+    const bool sp = d.pat_cap > 0 && pat[0] != 0;
+    const int nm = coef_matrices(d), cap = d.pat_cap;
+    const int* cnt = pat + 1;
+    const int* jx = pat + 1 + nm * D;
     for (int c = cbeg; c < cend; ++c) {
         const float2* x1 = X1 + (int64_t)c * d.ld;
         const float2* x2 = Xlo ? Xlo + (int64_t)c * d.ld : nullptr;
         DF re = DF{0.f, 0.f}, im = DF{0.f, 0.f};
-        for (int j = 0; j < D; ++j) {
-            const int q = j + D * b;
-            df_cmul_acc(re, im, H0[i * D + j], x1[q], x2 ? x2[q] : z);
+        // zero coefficients are skipped (exact: they add nothing)
+        if (sp) {
+            for (int k = 0; k < cnt[i]; ++k) {
+                const int j = jx[(int64_t)i * cap + k], q = j + D * b;
+                df_cmul_acc(re, im, H0[i * D + j], x1[q], x2 ? x2[q] : z);
+            }
+        } else {
+            for (int j = 0; j < D; ++j) {
+                const float4 h = H0[i * D + j];
+                if (h.x == 0.f && h.z == 0.f) continue;
+                const int q = j + D * b;
+                df_cmul_acc(re, im, h, x1[q], x2 ? x2[q] : z);
+            }
         }
         df_cmul_acc(re, im, msh, x1[r], x2 ? x2[r] : z);
         int64_t off = d.coef_off + (int64_t)D * D;
+        int m = 1;
         for (int l = 0; l < d.K; ++l) {
-            for (int h = 1; h <= d.nharm[l]; ++h) {
+            for (int h = 1; h <= d.nharm[l]; ++h, m += 2) {
                 const float4* V = cs + off + (int64_t)(h - 1) * D * D;
                 if (nv[l] + h <= d.N[l]) {
                     const int bu = b + h * d.S[l];
-                    for (int j = 0; j < D; ++j) {
-                        const int q = j + D * bu;
-                        df_cmul_acc(re, im, V[i * D + j], x1[q], x2 ? x2[q] : z);
+                    if (sp) {
+                        const int e = m * D + i;
+                        for (int k = 0; k < cnt[e]; ++k) {
+                            const int j = jx[(int64_t)e * cap + k], q = j + D * bu;
+                            df_cmul_acc(re, im, V[i * D + j], x1[q], x2 ? x2[q] : z);
+                        }
+                    } else {
+                        for (int j = 0; j < D; ++j) {
+                            const float4 hv = V[i * D + j];
+                            if (hv.x == 0.f && hv.z == 0.f) continue;
+                            const int q = j + D * bu;
+                            df_cmul_acc(re, im, hv, x1[q], x2 ? x2[q] : z);
+                        }
                     }
                 }
                 if (nv[l] - h >= -d.N[l]) {
                     const int bd = b - h * d.S[l];
-                    for (int j = 0; j < D; ++j) {
-                        const int q = j + D * bd;
-                        df_cmulc_acc(re, im, V[j * D + i], x1[q], x2 ? x2[q] : z);
+                    if (sp) {
+                        const int e = (m + 1) * D + i;
+                        for (int k = 0; k < cnt[e]; ++k) {
+                            const int j = jx[(int64_t)e * cap + k], q = j + D * bd;
+                            df_cmulc_acc(re, im, V[j * D + i], x1[q], x2 ? x2[q] : z);
+                        }
+                    } else {
+                        for (int j = 0; j < D; ++j) {
+                            const float4 hv = V[j * D + i];
+                            if (hv.x == 0.f && hv.z == 0.f) continue;
+                            const int q = j + D * bd;
+                            df_cmulc_acc(re, im, hv, x1[q], x2 ? x2[q] : z);
+                        }
                     }
                 }
             }
@@ -773,6 +845,7 @@ __device__ void cta_jacobi(double2* B, double2* W, int m, double* w, double* rot
 __global__ void __launch_bounds__(256) k_cluster_sep(const MmfDesc* __restrict__ descs,
                                                      const int* __restrict__ idx,
                                                      const double2* __restrict__ coef,
+                                                     const int* __restrict__ patg,
                                                      double2* __restrict__ Xg,
                                                      double2* __restrict__ HXg,
                                                      double* __restrict__ lamg,
@@ -793,6 +866,11 @@ __global__ void __launch_bounds__(256) k_cluster_sep(const MmfDesc* __restrict__
     double* lam = lamg + d.vec_off;
     const int* cid = cidg + d.vec_off;
     const double2* H0 = coef + d.coef_off;
+    const int* pat = patg + d.pat_off;
+    const bool sp = d.pat_cap > 0 && pat[0] != 0;
+    const int nm = coef_matrices(d), cap = d.pat_cap;
+    const int* cnt = pat + 1;
+    const int* jx = pat + 1 + nm * D;
     // clusters are disjoint: the CTAs of a system take them in parallel (c0 = first index)
     for (int c0 = blockIdx.x; c0 < n; c0 += gridDim.x) {
         if (cid[c0] != c0 || c0 + 1 >= n || cid[c0 + 1] != c0) continue;
@@ -809,16 +887,53 @@ __global__ void __launch_bounds__(256) k_cluster_sep(const MmfDesc* __restrict__
                 block_nvec(d, b, nv);
                 const double2* x = X + (int64_t)c * d.ld;
                 double2 acc = make_double2(0.0, 0.0);
-                for (int j = 0; j < D; ++j) acc = acc + H0[i * D + j] * x[j + D * b];
+                if (sp) {
+                    for (int k = 0; k < cnt[i]; ++k) {
+                        const int j = jx[(int64_t)i * cap + k];
+                        acc = acc + H0[i * D + j] * x[j + D * b];
+                    }
+                } else {
+                    for (int j = 0; j < D; ++j) {
+                        const double2 h = H0[i * D + j];
+                        if (h.x != 0.0 || h.y != 0.0) acc = acc + h * x[j + D * b];
+                    }
+                }
                 acc = acc - block_ndotw(d, b) * x[r];
                 int64_t off = d.coef_off + (int64_t)D * D;
+                int mq = 1;
                 for (int l = 0; l < d.K; ++l) {
-                    for (int h = 1; h <= d.nharm[l]; ++h) {
+                    for (int h = 1; h <= d.nharm[l]; ++h, mq += 2) {
                         const double2* V = coef + off + (int64_t)(h - 1) * D * D;
-                        if (nv[l] + h <= d.N[l])
-                            for (int j = 0; j < D; ++j) acc = acc + V[i * D + j] * x[j + D * (b + h * d.S[l])];
-                        if (nv[l] - h >= -d.N[l])
-                            for (int j = 0; j < D; ++j) acc = acc + cmulc(V[j * D + i], x[j + D * (b - h * d.S[l])]);
+                        if (nv[l] + h <= d.N[l]) {
+                            const double2* xu = x + D * (b + h * d.S[l]);
+                            if (sp) {
+                                const int e2 = mq * D + i;
+                                for (int k = 0; k < cnt[e2]; ++k) {
+                                    const int j = jx[(int64_t)e2 * cap + k];
+                                    acc = acc + V[i * D + j] * xu[j];
+                                }
+                            } else {
+                                for (int j = 0; j < D; ++j) {
+                                    const double2 v = V[i * D + j];
+                                    if (v.x != 0.0 || v.y != 0.0) acc = acc + v * xu[j];
+                                }
+                            }
+                        }
+                        if (nv[l] - h >= -d.N[l]) {
+                            const double2* xd = x + D * (b - h * d.S[l]);
+                            if (sp) {
+                                const int e2 = (mq + 1) * D + i;
+                                for (int k = 0; k < cnt[e2]; ++k) {
+                                    const int j = jx[(int64_t)e2 * cap + k];
+                                    acc = acc + cmulc(V[j * D + i], xd[j]);
+                                }
+                            } else {
+                                for (int j = 0; j < D; ++j) {
+                                    const double2 v = V[j * D + i];
+                                    if (v.x != 0.0 || v.y != 0.0) acc = acc + cmulc(v, xd[j]);
+                                }
+                            }
+                        }
                     }
                     off += (int64_t)d.nharm[l] * D * D;
                 }
@@ -985,19 +1100,26 @@ cudaError_t mmf_launch_refine_split_coef(const double2* coef, float4* cs, int64_
 
 // HX = H_F X in double-FP32; X1 = fl32(X) is left in place for the Gram product.  Xlo: FP32
 // remainder buffer (used only when X is not FP32-exact).
-static void apply_hf(const MmfLaunch& L, const float4* cs, const double2* X, float2* X1, float2* Xlo, double2* HX) {
+static void apply_hf(const MmfLaunch& L, const float4* cs, const int* pat, const double2* X, float2* X1, float2* Xlo,
+                     double2* HX) {
     k_split_x<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, X1, Xlo);
     k_apply_hf_df32<<<dim3((L.nmax + 255) / 256, (L.nmax + 15) / 16, L.count), 256, 0, L.stream>>>(
-        L.desc, L.idx, cs, X1, Xlo, HX);
+        L.desc, L.idx, cs, pat, X1, Xlo, HX);
 }
 
-cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const float4* cs, const double2* X, const double* lam0,
-                                  double2* HX, double2* T, float2* X1, void* ops, void* jobs, int* status,
-                                  int second) {
+cudaError_t mmf_launch_coef_pattern(const MmfLaunch& L, const double2* coef, int* pat) {
+    if (L.count <= 0) return cudaSuccess;
+    k_coef_pattern<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, coef, pat);
+    return cudaGetLastError();
+}
+
+cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const float4* cs, const int* pat, const double2* X,
+                                  const double* lam0, double2* HX, double2* T, float2* X1, void* ops, void* jobs,
+                                  int* status, int second) {
     if (L.count <= 0) return cudaSuccess;
     // the first step's X holds FP32 eigenvectors (no remainder); the remainder of a second step's
     // X goes to T, which is free until C is written
-    apply_hf(L, cs, X, X1, second ? reinterpret_cast<float2*>(T) : nullptr, HX);
+    apply_hf(L, cs, pat, X, X1, second ? reinterpret_cast<float2*>(T) : nullptr, HX);
     k_w_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, HX, lam0, ops);
     k_w_prep_A<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X1, ops);
     k_w_jobs<<<(L.count + 127) / 128, 128, 0, L.stream>>>(L.desc, L.idx, L.count, ops, T, 0, (Tf3Job*)jobs);
@@ -1024,7 +1146,8 @@ cudaError_t mmf_launch_refine_gram_fix(const MmfLaunch& L, double2* G, const dou
     return cudaGetLastError();
 }
 
-cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, double2* X, const float2* X1,
+cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, const int* pat, double2* X,
+                                     const float2* X1,
                                      const double* lam0, double2* G, double2* HX, const double2* T, double* lam,
                                      int* status, int* cid, int64_t mat_elems, void* ops, void* jobs,
                                      double2* Eb) {
@@ -1043,8 +1166,8 @@ cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, do
         L.desc, L.idx, X, X1, G, Eb, HX);
     e = cudaMemcpyAsync(X, HX, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
     if (e != cudaSuccess) return e;
-    k_cluster_sep<<<dim3(std::min(L.nmax, 1024), L.count), 256, 0, L.stream>>>(L.desc, L.idx, coef, X, HX, lam, cid,
-                                                                                status);
+    k_cluster_sep<<<dim3(std::min(L.nmax, 1024), L.count), 256, 0, L.stream>>>(L.desc, L.idx, coef, pat, X, HX, lam,
+                                                                                cid, status);
     return cudaGetLastError();
 }
 

@@ -87,6 +87,8 @@ struct mmf_batch {
     int nmax_all = 0, nmax_small = 0, nmax_large = 0, Mmax = 1, Dmax = 1;
     int64_t n_oz = 0;      // BF16 elements of the Gram-product slices (mixed, tensor-core Gram)
     int gram_kernel = 0;   // copied from the context at creation
+    int64_t n_pat = 0;
+    int* d_pat = nullptr;  // mixed path: nonzero pattern of the coefficient rows
     int64_t n_coef = 0, n_mat = 0, n_vec = 0, n_sq = 0, n_pan = 0, n_t = 0, n_f = 0, n_u = 0,
             n_p = 0;
     // device
@@ -415,6 +417,10 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         for (int k = 0; k < d.K; ++k) nc += (int64_t)d.nharm[k] * s->D * s->D;
         d.coef_off = b->n_coef;
         b->n_coef += nc;
+        // sparse coefficient rows pay off in the refinement's H_F products from a few dozen levels
+        d.pat_cap = (precision == MMF_MIXED && s->D >= 32) ? 16 : 0;
+        d.pat_off = b->n_pat;
+        b->n_pat += d.pat_cap ? 1 + (int64_t)coef_matrices(d) * s->D * (1 + d.pat_cap) : 1;
         d.mat_off = b->n_mat;
         b->n_mat += n * d.ld;
         d.vec_off = b->n_vec;
@@ -494,6 +500,7 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     size_t o_F = p.take(sizeof(double2) * std::max<int64_t>(b->n_f, 1));
     size_t o_U = p.take(sizeof(double2) * std::max<int64_t>(b->n_u, 1));
     size_t o_P = p.take(sizeof(double) * b->n_p);
+    size_t o_pat = 0;
     size_t o_R = 0, o_S = 0, o_HX = 0, o_E2 = 0, o_cid = 0, o_jobs = 0, o_Eb = 0, o_T = 0, o_X1 = 0, o_coefs = 0, o_oz = 0,
            o_ozexp = 0;
     const size_t o_Zs = (!fp32 && nt > 0) ? p.take(sizeof(float2) * 2 * b->n_mat) : 0;
@@ -510,6 +517,7 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         o_E2 = p.take(sizeof(double) * b->n_vec);
         o_cid = p.take(sizeof(int) * b->n_vec);
         o_jobs = p.take(std::max(sizeof(UmmaJob), sizeof(Tf3Job)) * count);
+        o_pat = p.take(sizeof(int) * std::max<int64_t>(b->n_pat, 1));
     }
     const size_t o_btjobs = b->btc.empty() ? 0 : p.take(sizeof(Tf3Job) * 4 * b->btc.size());
     b->bytes = p.off;
@@ -573,6 +581,7 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         b->d_coefs = (float4*)(B + o_coefs);
         b->d_oz = B + o_oz;
         b->d_ozexp = (int*)(B + o_ozexp);
+        b->d_pat = (int*)(B + o_pat);
     }
     if (b->pinned) {
         e = cudaMallocHost((void**)&b->h_coef, sizeof(double2) * std::max<int64_t>(b->n_coef, 1));
@@ -792,13 +801,14 @@ static int stage_eig(mmf_batch* b) {
     if (fp32) {
         MmfLaunch La = launch_of(b, b->all, b->d_all, b->nmax_all);
         LAUNCH(mmf_launch_refine_split_coef(b->d_coef, b->d_coefs, b->n_coef, b->stream), 1);
-        LAUNCH(mmf_launch_refine_pre(La, b->d_coefs, b->d_Zf, b->d_E, b->d_HX, b->d_T, b->d_X1, b->d_oz, b->d_jobs,
+        LAUNCH(mmf_launch_coef_pattern(La, b->d_coef, b->d_pat), 1);
+        LAUNCH(mmf_launch_refine_pre(La, b->d_coefs, b->d_pat, b->d_Zf, b->d_E, b->d_HX, b->d_T, b->d_X1, b->d_oz, b->d_jobs,
                                      b->d_status, 0),
                6);
         mark(b, ST_GRAM);
         LAUNCH(refine_gram(b, La, 0), 2);
         mark(b, ST_REFINE2);
-        LAUNCH(mmf_launch_refine_update(La, b->d_coef, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_HX, b->d_T, b->d_E2,
+        LAUNCH(mmf_launch_refine_update(La, b->d_coef, b->d_pat, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_HX, b->d_T, b->d_E2,
                                         b->d_status, b->d_cid, b->n_mat, b->d_oz, b->d_jobs, b->d_Eb),
                9);
         // second step from lam0 = the first step's eigenvalues (E is rewritten at the end)
@@ -806,22 +816,22 @@ static int stage_eig(mmf_batch* b) {
         if (!b->rband.empty()) {
             // hybrid: C = X1^H W for all pairs on the tensor cores, G only on the band
             MmfLaunch Lb = launch_of(b, b->rband, b->d_rband, b->nmax_rband);
-            LAUNCH(mmf_launch_refine_pre(Lb, b->d_coefs, b->d_Zf, b->d_E, b->d_HX, b->d_T, b->d_X1, b->d_oz,
+            LAUNCH(mmf_launch_refine_pre(Lb, b->d_coefs, b->d_pat, b->d_Zf, b->d_E, b->d_HX, b->d_T, b->d_X1, b->d_oz,
                                          b->d_jobs, b->d_status, 2),
                    6);
             LAUNCH(mmf_launch_refine_band_g(Lb, b->d_Zf, b->d_R, b->n_mat), 1);
-            LAUNCH(mmf_launch_refine_update(Lb, b->d_coef, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_HX, b->d_T,
+            LAUNCH(mmf_launch_refine_update(Lb, b->d_coef, b->d_pat, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_HX, b->d_T,
                                             b->d_E2, b->d_status, b->d_cid, b->n_mat, b->d_oz, b->d_jobs, b->d_Eb),
                    9);
         }
         if (!b->rfull.empty()) {
             // full second step: G of the FP64 iterate as G(X1) + C' + C'^H
             MmfLaunch Lf = launch_of(b, b->rfull, b->d_rfull, b->nmax_rfull);
-            LAUNCH(mmf_launch_refine_pre(Lf, b->d_coefs, b->d_Zf, b->d_E, b->d_HX, b->d_T, b->d_X1, b->d_oz,
+            LAUNCH(mmf_launch_refine_pre(Lf, b->d_coefs, b->d_pat, b->d_Zf, b->d_E, b->d_HX, b->d_T, b->d_X1, b->d_oz,
                                          b->d_jobs, b->d_status, 1),
                    9);
             LAUNCH(refine_gram(b, Lf, 1), 3);
-            LAUNCH(mmf_launch_refine_update(Lf, b->d_coef, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_HX, b->d_T,
+            LAUNCH(mmf_launch_refine_update(Lf, b->d_coef, b->d_pat, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_HX, b->d_T,
                                             b->d_E2, b->d_status, b->d_cid, b->n_mat, b->d_oz, b->d_jobs, b->d_Eb),
                    9);
         }

@@ -12,7 +12,8 @@
 
 struct MmfDesc {
     int32_t D, K, M, n;                 // levels, modes, Fourier blocks, n = D * M
-    int32_t ld, b0, small, pad0;        // leading dim, central block index, Jacobi flag
+    int32_t ld, b0, small, pat_cap;     // leading dim, central block index, Jacobi flag,
+                                        // nonzeros kept per coefficient row (0: dense rows)
     int32_t N[MMF_MAX_MODES];           // truncation |n_k| <= N_k
     int32_t nharm[MMF_MAX_MODES];       // harmonics per mode (couplings V^{k,1..nharm})
     int32_t S[MMF_MAX_MODES];           // block strides, S_0 = 1, S_k = prod_{k'<k}(2N_k'+1)
@@ -27,7 +28,20 @@ struct MmfDesc {
     int64_t u_off;      // double2 offset of its nt x D x D time-evolution output
     int64_t p_off;      // offset of its D x D transition-probability output
     int64_t oz_off;     // BF16 offset of its Gram-product slices (mixed path)
+    int64_t pat_off;    // int offset of its coefficient nonzero pattern (mixed path)
 };
+
+// Nonzero pattern of a system's coefficient rows (refinement's H_F products), rebuilt on the
+// device from the current coefficients before every refinement.  Matrices m = 0 (H0 rows),
+// then per coupling q (mode-major, harmonic-minor) m = 1 + 2q (rows of V) and m = 2 + 2q (rows
+// of V^dagger, i.e. columns of V).  Layout at pat + pat_off: [0] = 1 when every row has at most
+// pat_cap nonzeros (else the kernels take the dense rows), then nm D counts, then nm D pat_cap
+// column indices.
+__host__ __device__ __forceinline__ int coef_matrices(const MmfDesc& d) {
+    int nm = 1;
+    for (int l = 0; l < d.K; ++l) nm += 2 * d.nharm[l];
+    return nm;
+}
 
 // ------------------------------------------------------------------ complex helpers
 template <class R> struct Cx;
@@ -210,12 +224,13 @@ cudaError_t mmf_launch_hetrd_large(const MmfDesc& d, void* H, void* Vp, void* Wp
 cudaError_t mmf_launch_micromotion(const MmfLaunch& L, int D, const double2* Z, const double* t,
                                    int nt, int64_t* reps, double2* UF);
 cudaError_t mmf_launch_refine_split_coef(const double2* coef, float4* cs, int64_t count, cudaStream_t st);
-cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const float4* cs, const double2* X, const double* lam0,
+cudaError_t mmf_launch_coef_pattern(const MmfLaunch& L, const double2* coef, int* pat);
+cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const float4* cs, const int* pat, const double2* X, const double* lam0,
                                   double2* HX, double2* T, float2* X1, void* ops, void* jobs, int* status,
                                   int second);
 cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const float2* X1, double2* G, const double2* T, int second);
 cudaError_t mmf_launch_refine_gram_fix(const MmfLaunch& L, double2* G, const double2* T);
-cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, double2* X, const float2* X1,
+cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, const int* pat, double2* X, const float2* X1,
                                      const double* lam0, double2* G, double2* HX, const double2* T, double* lam,
                                      int* status, int* cid, int64_t mat_elems, void* ops, void* jobs,
                                      double2* Eb);
