@@ -260,40 +260,48 @@ __global__ void __launch_bounds__(256) k_pbar_product(const MmfDesc* __restrict_
     }
 }
 
-// Cluster terms: one block per leading eigenvalue of a cluster of two or more (gaps < delta),
-// its threads over the (i, j) pairs; added after k_pbar_product on the same stream.
+// Cluster terms: one block per leading eigenvalue of a cluster of two or more (gaps < delta).
+// With u_il = conj(Z[(i,b0),l]) and S_j(l,l') = sum_b Z[(j,b),l] conj(Z[(j,b),l']), the
+// cluster's sum_b |sum_l u_il Z[(j,b),l]|^2 exceeds its diagonal part sum_l a_il w_jl by
+//   sum_{l < l'} 2 Re( u_il conj(u_il') S_j(l,l') ),
+// which is added pair by pair: S_j in shared memory (D entries), then the D x D pairs of
+// levels.  Added after k_pbar_product on the same stream.
 __global__ void __launch_bounds__(256) k_pbar_clusters(const MmfDesc* __restrict__ descs,
                                                        const int* __restrict__ idx,
                                                        const double* __restrict__ Eg,
-                                                       const double2* __restrict__ Zg,
-                                                       const void* scratch, int esz, double cluster_rel,
+                                                       const double2* __restrict__ Zg, double cluster_rel,
                                                        double* __restrict__ P) {
+    extern __shared__ __align__(16) double2 Sj[];  // D entries
     const MmfDesc d = descs[idx[blockIdx.y]];
     const int n = d.n, D = d.D, M = d.M;
     if (D <= PB_DSMALL) return;
     const double* E = Eg + d.vec_off;
     const double delta = cluster_rel * fmax(fabs(E[0]), fabs(E[n - 1]));
-    const double* w = pb_w(const_cast<void*>(scratch), esz, d);
     const double2* Z = Zg + d.mat_off;
+    const double2* Z0 = Z + (int64_t)D * d.b0;  // central block rows (i, b0)
     for (int lam = blockIdx.x; lam < n; lam += gridDim.x) {
         if (lam > 0 && E[lam] - E[lam - 1] < delta) continue;  // not a cluster's first eigenvalue
         int c1 = lam + 1;
         while (c1 < n && E[c1] - E[c1 - 1] < delta) ++c1;
-        if (c1 == lam + 1) continue;
-        for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
-            const int i = e / D, j = e - i * D;
-            double diag = 0.0, tot = 0.0;
-            for (int l = lam; l < c1; ++l)
-                diag += abs2(Z[(int64_t)l * d.ld + i + D * d.b0]) * w[(int64_t)l * D + j];
-            for (int b = 0; b < M; ++b) {
-                double2 amp = make_double2(0.0, 0.0);
-                for (int l = lam; l < c1; ++l) {
-                    const double2* zc = Z + (int64_t)l * d.ld;
-                    amp = amp + cmulc(zc[i + D * d.b0], zc[j + D * b]);
+        for (int l = lam; l < c1; ++l) {
+            for (int l2 = l + 1; l2 < c1; ++l2) {
+                const double2* za = Z + (int64_t)l * d.ld;
+                const double2* zb = Z + (int64_t)l2 * d.ld;
+                for (int j = threadIdx.x; j < D; j += blockDim.x) {
+                    double2 acc = make_double2(0.0, 0.0);
+                    for (int b = 0; b < M; ++b) acc = acc + cmulc(zb[j + D * b], za[j + D * b]);
+                    Sj[j] = acc;  // sum_b Z[(j,b),l] conj(Z[(j,b),l2])
                 }
-                tot += abs2(amp);
+                __syncthreads();
+                for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
+                    const int i = e / D, j = e - i * D;
+                    // conj(Z[(i,b0),l]) Z[(i,b0),l2] S_j(l,l2)
+                    const double2 uu = cmulc(Z0[(int64_t)l * d.ld + i], Z0[(int64_t)l2 * d.ld + i]);
+                    const double2 sj = Sj[j];
+                    atomicAdd(&P[d.p_off + e], 2.0 * (uu.x * sj.x - uu.y * sj.y));
+                }
+                __syncthreads();
             }
-            atomicAdd(&P[d.p_off + e], tot - diag);
         }
     }
 }
@@ -336,8 +344,12 @@ cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const dou
         const int nt_ = (Dmax + PB_T - 1) / PB_T;
         k_pbar_product<<<dim3(nt_, nt_, L.count), 256, 0, L.stream>>>(L.desc, L.idx, Z, scratch, scratch_esz, P);
         int gc = L.nmax < 1024 ? L.nmax : 1024;
-        k_pbar_clusters<<<dim3(gc, L.count), 256, 0, L.stream>>>(L.desc, L.idx, E, Z, scratch, scratch_esz,
-                                                                 cluster_rel, P);
+        const size_t smc = sizeof(double2) * (size_t)Dmax;
+        if (smc > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_pbar_clusters, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+            if (e != cudaSuccess) return e;
+        }
+        k_pbar_clusters<<<dim3(gc, L.count), 256, smc, L.stream>>>(L.desc, L.idx, E, Z, cluster_rel, P);
     }
     return cudaGetLastError();
 }
