@@ -218,6 +218,39 @@ def run_serving(M, W, ctx, precision, rate_fracs, n_requests, slots=4, max_batch
     return out
 
 
+def rank_workload(W, workload: str, count: int, rank: int, world: int):
+    """The systems rank `rank` of `world` solves, the systems-per-step count and the length of
+    their time grid.  The systems are independent parameter points, so each rank takes its own
+    set (weak scaling) and nothing crosses ranks on the data path: seeded draws per rank for the
+    random workloads, and consecutive slices of one frequency grid for the lattice sweep."""
+    nt = NT
+    if workload == "uneven":
+        count = 4096 if count == COUNT else count
+        problems = W.uneven_batch(count, seed=0 + rank)
+    elif workload == "large":
+        count, nt = 1, 256
+        problems = [W.large_instance(seed=3 + rank)]
+    elif workload == "lattice":
+        # spectrum versus frequency: quasienergies, eigenvectors and Pbar at every frequency of
+        # one grid over all ranks (no time grid)
+        nt = 0
+        problems = W.lattice_sweep(count * world)[rank * count:(rank + 1) * count]
+    else:
+        problems = W.spin1_amplitude_set(count, seed=1 + rank)
+    return problems, count, nt
+
+
+def max_over_ranks(x: float, world: int, dist, device) -> float:
+    """Largest x over the ranks: the job's step time is set by its slowest rank."""
+    if world <= 1:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -295,22 +328,7 @@ def main():
                                   "config": {"workload": "poisson_mix_qubit_spin1_uneven_nt64",
                                              "saturation_solves_per_s": res["saturation_solves_per_s"], **rr}}))
         return
-    count = args.count
-    nt = NT
-    if args.workload == "uneven":
-        count = 4096 if args.count == COUNT else args.count
-        problems = W.uneven_batch(count, seed=0 + rank)
-    elif args.workload == "large":
-        count, nt = 1, 256
-        problems = [W.large_instance(seed=3 + rank)]
-    elif args.workload == "lattice":
-        # spectrum-versus-frequency sweep of the driven lattice: quasienergies, eigenvectors and
-        # Pbar at every frequency (no time grid); each rank takes its own slice of the band
-        nt = 0
-        lo, hi = 0.2 + 0.8 * rank / world, 0.2 + 0.8 * (rank + 1) / world
-        problems = W.lattice_sweep(count, lo=lo, hi=hi)
-    else:
-        problems = W.spin1_amplitude_set(count, seed=1 + rank)
+    problems, count, nt = rank_workload(W, args.workload, args.count, rank, world)
     ctx = M.Context(local, stream=stream.cuda_stream)
     systems = [M.System(ctx, p) for p in problems]
     batch = M.Batch(ctx, systems, prec, nt)
@@ -337,10 +355,7 @@ def main():
     ms = ev0.elapsed_time(ev1) / args.steps
     stage, runs = batch.stage_ms()
     batch.timing(0)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dist, "cuda")
     value = count * world / (ms / 1e3)
 
     # end to end through the public API: H2D of inputs, run, D2H of E, U, Pbar every step
@@ -355,10 +370,7 @@ def main():
         batch.run()
         batch.results(hE, hU, hP)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, dist, "cuda")
     h2d = 16 * sum(p.D * p.D * (1 + sum(len(c) for c in p.couplings)) for p in problems) + 8 * ts.size
     d2h = hE.nbytes + 16 * batch.nU + hP.nbytes
 
