@@ -143,6 +143,19 @@ MMF_API int mmf_micromotion(mmf_sys* sys, int nt, const double* t, double* UF, i
 MMF_API int mmf_time_evolution_operator(mmf_sys* sys, int precision, double t0, int nt,
                                 const double* t, double* U);
 
+/* ---------------------------------------------------------------- spin systems (Sec. 3.4)
+ * Coupling matrices of a spin S = S2/2 (D = S2 + 1 levels, basis m = S, S-1, ..., -S, angular
+ * momentum matrices S_x, S_y, S_z as defined in Sakurai Sec. 3.5), built from the field
+ * parameters of Eq. 7: three amplitudes A[i] and three phases phi[i] (i = x, y, z).
+ *  - is_static = 0: the drive sum_i A_i cos(h w t + phi_i) S_i at one harmonic, written in
+ *    mmf_add_coupling's convention (+ h.c. implied): V = sum_i (A_i / 2) e^{i phi_i} S_i.
+ *    Eq. 7 prints the exponent without its i; it is read as a phase.  The cosine amplitude
+ *    follows Eq. 8 and the example's field settings.
+ *  - is_static = 1: the static part H0 = sum_i A_i S_i (phases ignored).
+ * V: caller-owned, D x D row-major complex (2 D^2 doubles, interleaved re/im).  Host only, no
+ * device or context needed.  Returns MMF_ERR_ARG for S2 < 1 or a NULL pointer. */
+MMF_API int mmf_spin_components(int S2, const double* A, const double* phi, int is_static, double* V);
+
 /* ---------------------------------------------------------------- batches
  * Many systems of any sizes solved together on the device (the data-parallel sweep of the
  * paper's examples, Sec. 4).  A batch is a plan: it allocates all device state once (within

@@ -13,6 +13,8 @@ Functions and the passages they follow (arXiv 2005.03426):
   transition_avg     time/phase-averaged populations (derived; the paper only names it)
   micromotion        Eq. 5 for one Floquet zone
   rk4                brute-force integration of Eq. 1 in the time domain
+  spin_components    Eq. 7 (Sec. 3.4): spin couplings from amplitudes and phases, with the
+                     angular-momentum matrices built from their ladder-operator definition
 """
 
 from __future__ import annotations
@@ -177,3 +179,29 @@ def solve(problem, t=None, t0: float = 0.0, cluster_rel: float = 1e-8):
         out["U"] = time_evolution(problem, E, Z, t, t0)
     out["P"] = transition_avg(problem, E, Z, cluster_rel)
     return out
+
+
+def spin_operators(S2: int):
+    """(S_x, S_y, S_z) for spin S = S2/2 in the basis m = S, S-1, ..., -S: S_z = diag(m) and
+    S_+ = S_x + i S_y with <m+1|S_+|m> = sqrt(S(S+1) - m(m+1))."""
+    S = S2 / 2.0
+    ms = [S - k for k in range(S2 + 1)]
+    Sp = np.zeros((S2 + 1, S2 + 1), dtype=np.complex128)
+    for a, m_row in enumerate(ms):
+        for b, m_col in enumerate(ms):
+            if abs(m_row - (m_col + 1.0)) < 1e-12:
+                Sp[a, b] = np.sqrt(S * (S + 1.0) - m_col * (m_col + 1.0))
+    Sm = Sp.conj().T
+    return (Sp + Sm) / 2.0, (Sp - Sm) / 2.0j, np.diag(np.array(ms, dtype=np.complex128))
+
+
+def spin_components(S2: int, A, phi=(0.0, 0.0, 0.0), static: bool = False) -> np.ndarray:
+    """Eq. 7: the coupling sum_i (A_i/2) e^{i phi_i} S_i of the drive sum_i A_i cos(h w t + phi_i) S_i
+    (the convention H(t) = H0 + V e^{i h w t} + V^dagger e^{-i h w t}), or sum_i A_i S_i for the
+    static part."""
+    ops = spin_operators(S2)
+    V = np.zeros_like(ops[0])
+    for k in range(3):
+        c = A[k] if static else 0.5 * A[k] * np.exp(1j * phi[k])
+        V = V + c * ops[k]
+    return V

@@ -167,6 +167,45 @@ static int64_t sys_dim(const mmf_sys* s) {
     return (int64_t)s->D * m;
 }
 
+// Spin couplings of Eq. 7 (host only).  S_z = diag(m), S_+ |m> = sqrt(S(S+1) - m(m+1)) |m+1>,
+// S_x = (S_+ + S_-)/2, S_y = (S_+ - S_-)/(2i), in the basis m = S, S-1, ..., -S.
+extern "C" int mmf_spin_components(int S2, const double* A, const double* phi, int is_static, double* V) {
+    if (S2 < 1 || !A || !V || (!is_static && !phi)) return fail(MMF_ERR_ARG, "spin components: S2 >= 1, A, phi, V required");
+    const int D = S2 + 1;
+    const double S = 0.5 * S2;
+    // factor of each Cartesian component: A_i (static) or (A_i / 2) e^{i phi_i} (drive)
+    double cr[3], ci[3];
+    for (int k = 0; k < 3; ++k) {
+        if (is_static) {
+            cr[k] = A[k];
+            ci[k] = 0.0;
+        } else {
+            cr[k] = 0.5 * A[k] * std::cos(phi[k]);
+            ci[k] = 0.5 * A[k] * std::sin(phi[k]);
+        }
+    }
+    for (int e = 0; e < 2 * D * D; ++e) V[e] = 0.0;
+    for (int r = 0; r < D; ++r) {
+        const double m = S - r;  // row r holds <m|
+        // S_z
+        V[2 * (r * D + r)] += cr[2] * m;
+        V[2 * (r * D + r) + 1] += ci[2] * m;
+        // <m| S_+ |m-1> = sqrt(S(S+1) - (m-1) m): column r + 1 holds |m - 1>
+        if (r + 1 < D) {
+            const double s = std::sqrt(S * (S + 1.0) - (m - 1.0) * m);
+            // <m|S_x|m-1> = s/2, <m|S_y|m-1> = s/(2i) = -i s/2 ; <m-1|S_x|m> = s/2, <m-1|S_y|m> = i s/2
+            const double hx = 0.5 * s;
+            // upper entry (r, r+1): cx * hx + cy * (-i hx)
+            V[2 * (r * D + r + 1)] += cr[0] * hx + ci[1] * hx;
+            V[2 * (r * D + r + 1) + 1] += ci[0] * hx - cr[1] * hx;
+            // lower entry (r+1, r): cx * hx + cy * (i hx)
+            V[2 * ((r + 1) * D + r)] += cr[0] * hx - ci[1] * hx;
+            V[2 * ((r + 1) * D + r) + 1] += ci[0] * hx + cr[1] * hx;
+        }
+    }
+    return MMF_OK;
+}
+
 extern "C" const char* mmf_strerror(int st) {
     switch (st) {
         case MMF_OK: return "ok";

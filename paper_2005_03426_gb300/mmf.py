@@ -116,6 +116,7 @@ _SIGS = {
     "mmf_selftest_gram": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "mmf_selftest_split_tf32": (_I, [_I, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "mmf_strerror": (ctypes.c_char_p, [_I]),
+    "mmf_spin_components": (_I, [_I, _P, _P, _I, _P]),
     "mmf_last_error": (ctypes.c_char_p, []),
     "mmf_last_launch_count": (_I, []),
 }
@@ -159,6 +160,18 @@ def _ptr(a: np.ndarray):
 
 def _cplx(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def spin_components(S2: int, A, phi=(0.0, 0.0, 0.0), static: bool = False) -> np.ndarray:
+    """Coupling matrix of a spin S = S2/2 from Eq. 7's amplitudes and phases (x, y, z):
+    sum_i (A_i/2) e^{i phi_i} S_i for a drive sum_i A_i cos(h w t + phi_i) S_i, or the static
+    sum_i A_i S_i (static=True).  D x D complex, basis m = S, ..., -S."""
+    D = int(S2) + 1
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(3))
+    phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float64).reshape(3))
+    V = np.zeros((D, D), dtype=np.complex128)
+    _check(lib().mmf_spin_components(int(S2), _ptr(A), _ptr(phi), int(bool(static)), _ptr(V)))
+    return V
 
 
 class Context:
