@@ -15,6 +15,8 @@ Functions and the passages they follow (arXiv 2005.03426):
   rk4                brute-force integration of Eq. 1 in the time domain
   spin_components    Eq. 7 (Sec. 3.4): spin couplings from amplitudes and phases, with the
                      angular-momentum matrices built from their ladder-operator definition
+  dressed_time_evolution
+                     Sec. 3.3 with Eq. 4: U(t2, t1) in the dressed basis of a subset of modes
 """
 
 from __future__ import annotations
@@ -205,3 +207,29 @@ def spin_components(S2: int, A, phi=(0.0, 0.0, 0.0), static: bool = False) -> np
         c = A[k] if static else 0.5 * A[k] * np.exp(1j * phi[k])
         V = V + c * ops[k]
     return V
+
+
+class _Restricted:
+    """A problem restricted to some of its modes (same levels and static part)."""
+
+    def __init__(self, problem, modes):
+        self.D = problem.D
+        self.H0 = problem.H0
+        self.omegas = [problem.omegas[k] for k in modes]
+        self.Ns = [problem.Ns[k] for k in modes]
+        self.couplings = [problem.couplings[k] for k in modes]
+
+
+def dressed_time_evolution(problem, dressing, t1: float, t2: float):
+    """Sec. 3.3: the evolution from t1 to t2 expressed in the time-dependent basis of the
+    dressing modes (indices into the problem's modes).  The problem restricted to those modes
+    gives the micromotion operator U_F(t) of Eq. 5 for one Floquet zone (zone_representatives)
+    and its quasienergies Ebar; the full problem gives U(t2, t1) (Eq. 3-4).  Returns
+    (U_F(t2)^dagger U(t2, t1) U_F(t1), Ebar)."""
+    sub = _Restricted(problem, list(dressing))
+    Ed, Zd, _, _ = eigh(build_hf(sub))
+    reps = zone_representatives(sub, Ed, Zd)
+    UF = micromotion(sub, Zd, reps, np.array([t1, t2], dtype=np.float64))
+    E, Z, _, _ = eigh(build_hf(problem))
+    U = time_evolution(problem, E, Z, np.array([t2], dtype=np.float64), t1)[0]
+    return UF[1].conj().T @ U @ UF[0], Ed[reps]

@@ -382,3 +382,49 @@ def test_pbar_equals_brute_force_time_average():
     P = O.solve(p)["P"]
     # acc[j, i] = avg |U_ji|^2 = Pbar_{i->j}
     np.testing.assert_allclose(acc.T, P, atol=3e-3)
+
+
+# ------------------------------------------------------------ dressed basis (Sec. 3.3)
+def _dressed_qubit(omega_p, amp_pz, N_d=6, N_p=5, amp_x=0.05):
+    """Qubit of Eq. 8: w0 S_z, a resonant dressing drive amp_x cos(t) S_x (mode 1) and a probe
+    amp_pz cos(omega_p t) S_z (mode 2)."""
+    sx = 0.5 * np.array([[0, 1], [1, 0]], dtype=complex)
+    sz = 0.5 * np.array([[1, 0], [0, -1]], dtype=complex)
+    return W.Problem(D=2, H0=1.0 * sz, omegas=[1.0, omega_p], Ns=[N_d, N_p],
+                     couplings=[[0.5 * amp_x * sx], [0.5 * amp_pz * sz]])
+
+
+def test_dressed_frame_without_probe_is_diagonal():
+    """Eq. 4 with only the dressing modes driving: U(t2, t1) = U_F(t2) e^{-i Ebar (t2 - t1)}
+    U_F(t1)^dagger, so the dressed-frame evolution is diag(e^{-i Ebar_a (t2 - t1)}), whereas
+    the bare-frame evolution mixes the levels (Rabi oscillation of the dressing drive)."""
+    p = _dressed_qubit(0.03, 0.0)
+    t1, t2 = 3.0, 41.0
+    Ud, Eb = O.dressed_time_evolution(p, [0], t1, t2)
+    np.testing.assert_allclose(Ud, np.diag(np.exp(-1j * Eb * (t2 - t1))), rtol=0, atol=1e-9)
+    U = O.solve(p, t=np.array([t2]), t0=t1)["U"][0]
+    assert abs(U[1, 0]) > 0.3
+
+
+def test_dressed_frame_probe_resonance():
+    """Sec. 4.1: a weak probe along z drives transitions between the two dressed states when
+    its frequency matches their splitting (about amp_x / 2), and hardly at all when detuned by
+    much more than its own Rabi frequency."""
+    amp_pz = 0.005
+    Eb = O.dressed_time_evolution(_dressed_qubit(0.03, 0.0), [0], 0.0, 1.0)[1]
+    split = abs(Eb[1] - Eb[0]) % 1.0
+    split = min(split, 1.0 - split)
+    assert abs(split - 0.025) < 2e-3
+    times = np.linspace(0.0, 2.5 * np.pi / (0.5 * amp_pz), 9)[1:]
+
+    def transfer(wp):
+        p = _dressed_qubit(wp, amp_pz)
+        return max(abs(O.dressed_time_evolution(p, [0], 0.0, t)[0][1, 0]) ** 2 for t in times)
+
+    on, off = transfer(split), transfer(3.0 * split)
+    assert on > 0.8 and off < 0.1, (on, off)
+
+
+def test_dressed_frame_is_unitary():
+    Ud, _ = O.dressed_time_evolution(_dressed_qubit(0.031, 0.004), [0], 1.5, 60.0)
+    np.testing.assert_allclose(Ud.conj().T @ Ud, np.eye(2), rtol=0, atol=1e-8)
