@@ -73,3 +73,27 @@ def test_lattice_sweep_shape():
     ps = W.lattice_sweep()
     assert len(ps) == 64 and all(p.n == 1792 and p.D == 256 for p in ps)
     assert ps[0].omegas[0] == 0.2 and ps[-1].omegas[0] == 1.0
+
+
+def test_driven_lattice_has_exactly_degenerate_mirror_pairs():
+    """The driven lattice's Floquet spectrum contains exactly degenerate pairs: mirror-image
+    states localised near sites D/4 and 3D/4.  The undriven chain has none.  These pairs are
+    why the mixed path's refinement clusters pairs by absolute gap.  LAPACK on the FP64 H_F;
+    N = 1 keeps it small."""
+    from oracle import oracle as O
+
+    p = W.driven_lattice(0.6, D=256, N=1)
+    E, Z = np.linalg.eigh(O.build_hf(p))
+    gaps = np.diff(E)
+    pairs = np.nonzero(gaps < 1e-12 * np.abs(E).max())[0]
+    assert len(pairs) >= 4
+    D = p.D
+    for k in pairs[:2]:
+        centres = []
+        for col in (k, k + 1):
+            w = np.bincount(np.arange(Z.shape[0]) % D, weights=np.abs(Z[:, col]) ** 2, minlength=D)
+            centres.append((w * np.arange(D)).sum())
+        lo, hi = sorted(c / D for c in centres)
+        assert abs(lo - 0.25) < 0.05 and abs(hi - 0.75) < 0.05, (lo, hi)
+    E0 = np.linalg.eigvalsh(W.driven_lattice(0.6, D=256, N=0).H0)
+    assert (np.diff(E0) > 1e-9).all()
