@@ -3,11 +3,17 @@
 Workload (one step): the spin-1 two-mode system H = w0 Fz + O1 cos(w1 t) Fx + O2 cos(w2 t) Fz,
 w = (1, (sqrt5-1)/2), N = (10, 10) -> n = 1323, for 64 seeded amplitude pairs (O1, O2) ~
 U[0.05, 0.5]^2 (seed 1); per system: H_F assembly, full eigendecomposition, U(t, 0) at 64 times
-over 2 pi / w1 and Pbar.  Synthetic inputs; the per-step working set (~6 GB) exceeds L2, so no
-flush is needed between steps.  With N ranks each rank solves its own 64 systems (seed 1 + rank).
+over 2 pi / w1 and Pbar.  Synthetic inputs; the per-step working set (about 13 GB on the mixed
+path, 7 GB on the FP64 path) exceeds L2, so no flush is needed between steps.  With N ranks each
+rank solves its own 64 systems (seed 1 + rank).
+
+The headline line times the mixed-precision path; the same process then times the plain FP64
+path on the same systems (fp64_value, mixed_over_fp64) and compares both with stored oracle
+results (accuracy_vs_oracle).  The CPU baseline runs complete oracle solves, one system per host
+core.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
-    python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
+    python bench.py --impl reference      # the FP64 CPU oracle, one system per host core
 """
 
 from __future__ import annotations
@@ -17,8 +23,10 @@ import json
 import os
 import subprocess
 import sys
+import multiprocessing as mp
 import threading
 import time
+from concurrent.futures import ProcessPoolExecutor
 
 import numpy as np
 
@@ -113,6 +121,7 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+
 def stage_model(stage: str, n: int, nt: int, mixed: bool):
     """The bounds of a stage's main kernel for one system: a list of (bound, algorithmic work,
     peak per second, unit, peak description, kernel).  The roofline reports the bound whose
@@ -120,9 +129,9 @@ def stage_model(stage: str, n: int, nt: int, mixed: bool):
     - hetrd: (16/3) n^3 real flops (LAPACK count); the hemv of every column streams the trailing
       lower triangle, sum_m m^2/2 = n^3/6 complex entries (8 bytes FP32, 16 bytes FP64).
     - backtransform: 8 n^3 real flops (LAPACK count).
-    - refine_gram: the tensor-core Gram product by integer slicing, 28 slice pairs x (Re, Im) x
-      n x n/2 x 2n multiply-adds (lower-triangle tiles) on the BF16 tensor cores, against the
-      sustained cuBLAS bf16 rate (the kernel runs inside a long step).
+    - refine_gram: the tensor-core Gram product by integer slicing, 15 slice pairs x (Re, Im) x
+      n x n/2 x 2n multiply-adds x 2 flops = 60 n^3 (lower-triangle tiles) on the BF16 tensor
+      cores, against the sustained cuBLAS bf16 rate (the kernel runs inside a long step).
     - outputs: 8 nt n^2 flops (the Phi contraction)."""
     pk = _peaks()
     hbm = pk["hbm_gbs"] * 1e9
@@ -138,57 +147,62 @@ def stage_model(stage: str, n: int, nt: int, mixed: bool):
         return [("alu", 8.0 * n ** 3, alu[0], "TFLOP/s", alu[1],
                  "k_backtransform_f32" if mixed else "k_backtransform")]
     if stage == "refine_gram" and mixed:
-        return [("tensor", 112.0 * n ** 3, bf16, "TFLOP/s",
+        return [("tensor", 60.0 * n ** 3, bf16, "TFLOP/s",
                  f"cuBLAS bf16 sustained {bf16 / 1e12:.1f} TFLOP/s {src}", "k_oz_gram")]
     if stage == "outputs":
         return [("alu", 8.0 * nt * n * n, alu[0], "TFLOP/s", alu[1], "k_time_evolution")]
     return None
 
 
-def cpu_baseline_oracle(problems, budget_s: float = 25.0):
-    """The FP64 oracle on a bounded sample: system 0's H_F build, a bounded number of cyclic
-    Jacobi sweeps, U and Pbar, scaled to a full solve by the sweep count the oracle needs for that
-    system (stored with the golden results when available, else 10)."""
+# ------------------------------------------------------------------ CPU baseline (the oracle)
+def _oracle_solve_c1(i: int):
+    """One complete oracle solve of system i of the benchmark workload (worker process)."""
     from oracle import oracle as O
+    from paper_2005_03426_gb300 import workloads as W
 
-    p = problems[0]
-    t = np.array([k * p.period() / NT for k in range(NT)])
+    p = W.spin1_amplitude_set(COUNT, seed=1)[i]
+    t = W.time_grid(p, NT)
     t0 = time.perf_counter()
-    HF = O.build_hf(p)
-    t_build = time.perf_counter() - t0
-    # time whole sweeps until the budget is spent (at least one)
-    ts = time.perf_counter()
-    _, _, _, sw = O.eigh(HF, max_sweeps=1)
-    t_sweep = time.perf_counter() - ts
-    sweeps_needed = 10
-    gold = os.path.join(ROOT, "tests", "golden", "spin1_c1_sys0.npz")
-    if os.path.exists(gold):
-        sweeps_needed = int(np.load(gold)["sweeps"])
-    n = p.n
-    # U and Pbar with stand-in eigenpairs of the right shape (their cost does not depend on values)
-    E = np.linspace(-1, 1, n)
-    Z = np.eye(n, dtype=np.complex128)
-    tu = time.perf_counter()
-    O.time_evolution(p, E, Z, t[:4], 0.0)
-    t_u = (time.perf_counter() - tu) * NT / 4
-    tp = time.perf_counter()
-    O.transition_avg(p, E, Z)
-    t_p = time.perf_counter() - tp
-    total = t_build + sweeps_needed * t_sweep + t_u + t_p
-    return {"value": 1.0 / total, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"system 0 of the workload: H_F build ({t_build:.2f}s), 1 of {sweeps_needed} "
-                       f"cyclic Jacobi sweeps ({t_sweep:.1f}s, scaled), U at 4 of {NT} times (scaled) "
-                       f"and Pbar; single thread; full solve estimated at {total:.0f}s")}
+    r = O.solve(p, t=t, t0=0.0)
+    return time.perf_counter() - t0, int(r["status"])
 
 
-def run_serving(M, W, ctx, precision, rate_fracs, n_requests, slots=4, max_batch=16, seed=40):
+def _noop(_):
+    return os.getpid()
+
+
+def cpu_baseline_oracle(nsys: int = 0, cores: int = 0):
+    """The FP64 oracle as it stands, timed on complete solves (H_F build, cyclic Jacobi to
+    convergence, U at the 64 times, Pbar) of the benchmark's systems, one system per host core in
+    separate processes (the oracle itself is single-threaded).  nsys systems (default: one per
+    core) are solved in one wave; value = nsys / wall time of the wave."""
+    cores = cores or os.cpu_count() or 1
+    nsys = nsys or cores
+    workers = min(cores, nsys)
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_noop, range(workers)))  # start the workers before the clock
+        t0 = time.perf_counter()
+        res = list(ex.map(_oracle_solve_c1, [i % COUNT for i in range(nsys)]))
+        wall = time.perf_counter() - t0
+    per = [r[0] for r in res]
+    return {"value": nsys / wall, "unit": "solves/s", "cores": workers, "kind": "oracle",
+            "sample": (f"{nsys} complete oracle solves (systems 0..{nsys - 1} of the workload, n = 1323, "
+                       f"U at {NT} times, Pbar) in {workers} processes, one system each; wave {wall:.1f}s, "
+                       f"per solve {min(per):.1f}..{max(per):.1f}s"),
+            "status_max": max(r[1] for r in res)}
+
+
+# ------------------------------------------------------------------ serving
+def run_serving(M, W, ctx, precision, rate_fracs, n_requests, slots=4, max_batch=16, seed=40,
+                max_seconds=None):
     """Poisson request streams through the continuous-batching server.  Saturation throughput is
-    measured first with a burst; each rate is a fraction of it.  Latency = submit -> results on host."""
+    measured first with a burst; each rate is a fraction of it.  Latency = submit -> results on host.
+    max_seconds bounds the arrival span of one rate (fewer requests at low rates)."""
     problems = W.serving_stream(n_requests, seed=seed)
     systems = [M.System(ctx, p) for p in problems]
     times = [W.time_grid(p, NT) for p in problems]
     srv = M.Server(ctx, slots=slots, max_batch=max_batch, precision=precision)
-    # saturation: everything at once
+    # saturation: a burst of everything at once
     burst = min(len(problems), 96)
     t0 = time.perf_counter()
     tk = [srv.submit(systems[i], times[i]) for i in range(burst)]
@@ -200,6 +214,8 @@ def run_serving(M, W, ctx, precision, rate_fracs, n_requests, slots=4, max_batch
         srv.reset_stats()
         rate = frac * sat
         arr = W.poisson_arrivals(len(problems), rate, seed + 1 + r)
+        if max_seconds:
+            arr = arr[arr <= max_seconds] if (arr <= max_seconds).sum() >= 8 else arr[:8]
         tickets = []
         start = time.perf_counter()
         for i, ta in enumerate(arr):
@@ -218,18 +234,40 @@ def run_serving(M, W, ctx, precision, rate_fracs, n_requests, slots=4, max_batch
     return out
 
 
+# ------------------------------------------------------------------ multi-rank workload split
+def balanced_partition(costs, world: int):
+    """Split items with the given costs over `world` ranks: largest cost first, each to the rank
+    with the least total so far (ties to the lower rank).  Returns one sorted index list per rank;
+    together they cover every item exactly once."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
 def rank_workload(W, workload: str, count: int, rank: int, world: int):
     """The systems rank `rank` of `world` solves, the systems-per-step count and the length of
-    their time grid.  The systems are independent parameter points, so each rank takes its own
-    set (weak scaling) and nothing crosses ranks on the data path: seeded draws per rank for the
-    random workloads, and consecutive slices of one frequency grid for the lattice sweep."""
+    their time grid.  The systems are independent parameter points, so nothing crosses ranks on
+    the data path:
+    - spin1: each rank takes its own seeded set of `count` systems (weak scaling);
+    - uneven: the one 4096-system batch (seed 0) is split over the ranks, balanced by the sum of
+      n^3 (the eigensolver's cost), so the ranks share a fixed job (strong scaling);
+    - lattice: consecutive slices of one frequency grid of count x world points;
+    - large: the single large instance runs as a replica on every rank."""
     nt = NT
     if workload == "uneven":
-        count = 4096 if count == COUNT else count
-        problems = W.uneven_batch(count, seed=0 + rank)
+        total = 4096 if count == COUNT else count
+        allp = W.uneven_batch(total, seed=0)
+        part = balanced_partition([float(p.n) ** 3 for p in allp], world)[rank]
+        problems = [allp[i] for i in part]
+        count = len(problems)
     elif workload == "large":
         count, nt = 1, 256
-        problems = [W.large_instance(seed=3 + rank)]
+        problems = [W.large_instance(seed=3)]
     elif workload == "lattice":
         # spectrum versus frequency: quasienergies, eigenvectors and Pbar at every frequency of
         # one grid over all ranks (no time grid)
@@ -238,6 +276,10 @@ def rank_workload(W, workload: str, count: int, rank: int, world: int):
     else:
         problems = W.spin1_amplitude_set(count, seed=1 + rank)
     return problems, count, nt
+
+
+def scaling_kind(workload: str) -> str:
+    return "strong" if workload == "uneven" else "weak"
 
 
 def max_over_ranks(x: float, world: int, dist, device) -> float:
@@ -251,24 +293,99 @@ def max_over_ranks(x: float, world: int, dist, device) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(x: float, world: int, dist, device) -> float:
+    if world <= 1:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ accuracy against the oracle
+def golden_c1():
+    """Stored oracle results of systems of the benchmark workload: {index: (E, U, P)}."""
+    g = {}
+    d = os.path.join(ROOT, "tests", "golden")
+    f0 = os.path.join(d, "spin1_c1_sys0.npz")
+    if os.path.exists(f0):
+        z = np.load(f0)
+        g[0] = (z["E"], z["U"], z["P"])
+    f1 = os.path.join(d, "spin1_c1_sys1_6.npz")
+    if os.path.exists(f1):
+        z = np.load(f1)
+        for i in z["indices"]:
+            g[int(i)] = (z[f"E_{i}"], z[f"U_{i}"], z[f"P_{i}"])
+    return g
+
+
+def accuracy(batch, E, U, P, gold):
+    """Largest errors of the systems with stored oracle results: quasienergies relative to
+    max|E| (= ||H_F||_2), U and Pbar absolute."""
+    if not gold:
+        return None
+    e_rel = u_abs = p_abs = 0.0
+    for i, (ge, gu, gp) in gold.items():
+        if i >= batch.count:
+            continue
+        e, u, pp = batch.unpack(E, U, P, i)
+        e_rel = max(e_rel, float(np.abs(e - ge).max() / np.abs(ge).max()))
+        if u.size:
+            u_abs = max(u_abs, float(np.abs(u - gu).max()))
+        p_abs = max(p_abs, float(np.abs(pp - gp).max()))
+    return {"E_rel_to_normH": e_rel, "U_abs": u_abs, "P_abs": p_abs,
+            "systems": sorted(i for i in gold if i < batch.count)}
+
+
+# ------------------------------------------------------------------ timing
+def time_steps(batch, stream, steps: int, barrier, local: int):
+    """CUDA-event time of `steps` runs of the batch on its stream (after a synchronize and
+    barrier on both sides), per-stage event times, launches and SM clocks sampled meanwhile."""
+    import torch
+
+    batch.timing(steps)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(steps):
+            launches += batch.run()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1) / steps
+    stage, runs = batch.stage_ms()
+    batch.timing(0)
+    per = {k: v / max(runs, 1) for k, v in stage.items()}
+    return ms, per, launches, clk.summary()
+
+
 def run_reference(args):
+    """The oracle as it stands on the host cores, on the benchmark workload: each step is one
+    wave of complete solves, one system per core.  The number of steps is capped so the run ends
+    within a few minutes (a wave takes about as long as one solve, ~40 s)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from paper_2005_03426_gb300 import workloads as W
-
-    problems = W.spin1_amplitude_set(COUNT, seed=1)
-    times = []
-    for _ in range(args.warmup + args.steps):
-        cb = cpu_baseline_oracle(problems)
-        times.append(1.0 / cb["value"])
-    tt = np.mean(times[args.warmup:]) if args.steps else times[-1]
-    value = 1.0 / tt
+    steps = max(1, min(args.steps, args.ref_max_steps))
+    warm = min(args.warmup, max(0, args.ref_max_steps - steps))
+    vals = []
+    for s in range(warm + steps):
+        cb = cpu_baseline_oracle(nsys=args.ref_systems)
+        if s >= warm:
+            vals.append(cb["value"])
+    value = float(np.mean(vals))
+    nsys = args.ref_systems or cb["cores"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": tt * 1e3 * COUNT, "higher_is_better": True, "scaling": "weak",
+            "n_gpus": args.gpus, "steps": steps, "warmup": warm,
+            "steps_requested": args.steps, "warmup_requested": args.warmup,
+            "ms_per_step": nsys / value * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "systems_per_step": COUNT, "n": 1323, "nt": NT},
+            "config": {"workload": WORKLOAD, "systems_per_step": nsys, "n": 1323, "nt": NT,
+                       "note": "a step is one wave of complete oracle solves, one system per host core"},
             "cpu_baseline": {**cb, "value": value},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -283,14 +400,21 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="timed steps of the FP64 comparison arm (0: skip it)")
     ap.add_argument("--serve", action="store_true", help="only the serving rate sweep")
     ap.add_argument("--workload", default="spin1", choices=["spin1", "uneven", "large", "lattice"],
                     help="spin1: 64 spin-1 systems n=1323 (default); uneven: 4096 systems n=18..2000; "
                          "large: one D=8 three-mode system n=17576 with U at 256 times; "
                          "lattice: 64 frequencies of the D=256 driven lattice, n=1792, spectrum and Pbar")
-    ap.add_argument("--serve-requests", type=int, default=240)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-seconds", type=float, default=6.0,
+                    help="arrival span per rate in the default run's serving sweep")
     ap.add_argument("--count", type=int, default=COUNT,
                     help="systems per step (64 = the benchmark workload; smaller for profiler captures)")
+    ap.add_argument("--ref-systems", type=int, default=0,
+                    help="reference arm / CPU baseline: systems per wave (default: one per host core)")
+    ap.add_argument("--ref-max-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -319,16 +443,19 @@ def main():
     prec = M.MMF_MIXED if args.precision == "mixed" else M.MMF_FP64
     if args.serve:
         ctx = M.Context(local, stream=stream.cuda_stream)
-        res = run_serving(M, W, ctx, prec, [0.1, 0.25, 0.5, 0.75, 0.9], args.serve_requests)
-        if rank == 0:
-            for rr in res["rates"]:
-                print(json.dumps({"metric": "serving_latency_p50_ms", "value": rr["p50_ms"], "unit": "ms",
-                                  "higher_is_better": False, "p99_ms": rr["p99_ms"], "n_gpus": world,
-                                  "precision": args.precision, "data": "synthetic",
-                                  "config": {"workload": "poisson_mix_qubit_spin1_uneven_nt64",
-                                             "saturation_solves_per_s": res["saturation_solves_per_s"], **rr}}))
+        for pname, pp in (("mixed", M.MMF_MIXED), ("fp64", M.MMF_FP64)):
+            res = run_serving(M, W, ctx, pp, [0.1, 0.25, 0.5, 0.75, 0.9], args.serve_requests)
+            if rank == 0:
+                for rr in res["rates"]:
+                    print(json.dumps({"metric": "serving_latency_p50_ms", "value": rr["p50_ms"], "unit": "ms",
+                                      "higher_is_better": False, "p99_ms": rr["p99_ms"], "n_gpus": world,
+                                      "precision": pname, "data": "synthetic",
+                                      "config": {"workload": "poisson_mix_qubit_spin1_uneven_nt64",
+                                                 "saturation_solves_per_s": res["saturation_solves_per_s"],
+                                                 **rr}}), flush=True)
         return
     problems, count, nt = rank_workload(W, args.workload, args.count, rank, world)
+    total_count = int(round(sum_over_ranks(float(count), world, dist, "cuda")))
     ctx = M.Context(local, stream=stream.cuda_stream)
     systems = [M.System(ctx, p) for p in problems]
     batch = M.Batch(ctx, systems, prec, nt)
@@ -340,23 +467,9 @@ def main():
     st = batch.sync()
 
     # device-resident timed region
-    batch.timing(args.steps)
-    barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches = 0
-    with Clocks(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            launches += batch.run()
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    stage, runs = batch.stage_ms()
-    batch.timing(0)
+    ms, per, launches, clocks = time_steps(batch, stream, args.steps, barrier, local)
     ms = max_over_ranks(ms, world, dist, "cuda")
-    value = count * world / (ms / 1e3)
+    value = total_count / (ms / 1e3)
 
     # end to end through the public API: H2D of inputs, run, D2H of E, U, Pbar every step
     hE = torch.empty(batch.nE, dtype=torch.float64).pin_memory().numpy()
@@ -374,18 +487,12 @@ def main():
     h2d = 16 * sum(p.D * p.D * (1 + sum(len(c) for c in p.couplings)) for p in problems) + 8 * ts.size
     d2h = hE.nbytes + 16 * batch.nU + hP.nbytes
 
-    # accuracy of system 0 against the stored oracle result
-    acc = None
-    gold = os.path.join(ROOT, "tests", "golden", "spin1_c1_sys0.npz")
-    if rank == 0 and os.path.exists(gold) and args.workload == "spin1":
-        g = np.load(gold)
-        e, u, pp = batch.unpack(hE, hU, hP, 0)
-        nrm = np.abs(g["E"]).max()
-        acc = {"E_rel_to_normH": float(np.abs(e - g["E"]).max() / nrm),
-               "U_abs": float(np.abs(u - g["U"]).max()), "P_abs": float(np.abs(pp - g["P"]).max())}
+    # accuracy of the systems with stored oracle results
+    is_c1 = args.workload == "spin1" and count == COUNT
+    gold = golden_c1() if (rank == 0 and is_c1) else {}
+    acc = accuracy(batch, hE, hU, hP, gold)
 
     # roofline of the dominant kernel (the stage holding it is timed on the library's stream)
-    per = {k: v / max(runs, 1) for k, v in stage.items()}
     n = problems[0].n
     mixed = prec == M.MMF_MIXED
     modelled = {k: v for k, v in per.items() if stage_model(k, n, nt, mixed) is not None}
@@ -399,41 +506,65 @@ def main():
     _, bnd, work, peak, unit, src, kern = max(bounds)
     achieved = work / (per[dom] / 1e3) if per[dom] > 0 else 0.0
     scale = 1e9 if unit == "GB/s" else 1e12
-    wname = WORKLOAD if (args.workload == "spin1" and count == COUNT) else None
+    wname = WORKLOAD if is_c1 else None
     roof = {"kernel": kern, "bound": bnd, "achieved": achieved / scale, "peak": peak / scale,
             "unit": unit, "frac": achieved / peak,
             "traffic": _measured_traffic(kern, wname, args.precision) if wname else None,
             "peak_source": src, "work_per_launch": work}
 
+    # the plain FP64 path on the same systems (the metric's comparison arm)
+    fp64 = None
+    if mixed and args.fp64_steps > 0 and args.workload in ("spin1", "uneven"):
+        b64 = M.Batch(ctx, systems, M.MMF_FP64, nt)
+        b64.set_times(0.0, ts)
+        b64.run()
+        st64 = b64.sync()
+        ms64, per64, _, clk64 = time_steps(b64, stream, args.fp64_steps, barrier, local)
+        ms64 = max_over_ranks(ms64, world, dist, "cuda")
+        E64, U64, P64 = b64.results()
+        v64 = total_count / (ms64 / 1e3)
+        fp64 = {"value": v64, "ms_per_step": ms64, "steps": args.fp64_steps, "warmup": 1,
+                "stage_ms": {k: round(v, 3) for k, v in per64.items()},
+                "accuracy_vs_oracle": accuracy(b64, E64, U64, P64, gold),
+                "status_max": int(st64.max()), "clocks": clk64}
+        b64.close()
+
     serving = None
-    if rank == 0 and world == 1 and args.serve_requests > 0 and count == COUNT and args.workload == "spin1":
-        sv = run_serving(M, W, ctx, prec, [0.75], args.serve_requests)
-        serving = {"saturation_solves_per_s": sv["saturation_solves_per_s"], **sv["rates"][0],
-                   "mix": "1/3 qubit n=82, 1/3 spin-1 n=1323, 1/3 uneven n<=2000; nt=64"}
+    if rank == 0 and world == 1 and args.serve_requests > 0 and is_c1:
+        sv = run_serving(M, W, ctx, prec, [0.1, 0.25, 0.5, 0.75, 0.9], args.serve_requests,
+                         max_seconds=args.serve_seconds)
+        serving = {"saturation_solves_per_s": sv["saturation_solves_per_s"], "rates": sv["rates"],
+                   "mix": "1/3 qubit n=82, 1/3 spin-1 n=1323, 1/3 uneven n<=2000; nt=64",
+                   "arrival_span_s": args.serve_seconds}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "spin1":
-        cpu = cpu_baseline_oracle(problems)
+        cpu = cpu_baseline_oracle()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "higher_is_better": True, "scaling": scaling_kind(args.workload), "vs_baseline": None,
                 "dtype": "f64" if prec == M.MMF_FP64 else "f32+f64",
                 "data": "synthetic",
-                "config": {"workload": ("uneven_batch_n18_2000" if args.workload == "uneven" else
+                "config": {"workload": ("uneven_batch_n18_2000_x4096" if args.workload == "uneven" else
                                         "large_D8_three_mode_n17576" if args.workload == "large" else
                                         f"driven_lattice_D256_N3_n1792_x{count}" if args.workload == "lattice" else
                                         WORKLOAD if count == COUNT else f"{WORKLOAD}[:{count}]"),
-                           "systems_per_step": count, "n": n, "nt": nt,
+                           "systems_per_step": total_count, "n": n, "nt": nt,
                            "precision": args.precision, "l2": "working set > L2 (no flush)",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"replicas x{world}" if args.workload != "uneven"
+                           else f"instances split by sum n^3 over {world} rank(s)"},
                 "stage_ms": {k: round(v, 3) for k, v in per.items()},
-                "roofline": roof, "clocks": clk.summary(), "gpu_launches": launches,
-                "e2e": {"value": count * world / e2e_s, "unit": "solves/s",
+                "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+                "e2e": {"value": total_count / e2e_s, "unit": "solves/s",
                         "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
                 "accuracy_vs_oracle": acc, "status_max": int(st.max()),
                 "status_counts": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
+                "fp64_value": fp64["value"] if fp64 else None,
+                "fp64_ms_per_step": fp64["ms_per_step"] if fp64 else None,
+                "mixed_over_fp64": value / fp64["value"] if fp64 else None,
+                "fp64": fp64,
                 "serving": serving,
                 "cpu_baseline": cpu}
         print(json.dumps(line))

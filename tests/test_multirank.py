@@ -47,6 +47,34 @@ def test_random_workloads_differ_between_ranks():
     assert np.array_equal(a[0].couplings[0][0], a2[0].couplings[0][0])  # seeded: reproducible
 
 
+def test_uneven_batch_split_covers_it_once_and_balances_n_cubed():
+    B = _bench()
+    allp = W.uneven_batch(4096, seed=0)
+    cost = np.array([float(p.n) ** 3 for p in allp])
+    for world in (2, 3, 8):
+        shards = [B.rank_workload(W, "uneven", 64, r, world) for r in range(world)]
+        assert sum(c for _, c, _ in shards) == 4096
+        parts = B.balanced_partition(list(cost), world)
+        idx = np.sort(np.concatenate(parts))
+        np.testing.assert_array_equal(idx, np.arange(4096))  # every system exactly once
+        # the shards are the batch's own systems (same bytes), in batch order
+        for (probs, _, _), part in zip(shards, parts):
+            assert [p.n for p in probs] == [allp[i].n for i in part]
+            assert np.array_equal(probs[0].H0, allp[part[0]].H0)
+        loads = np.array([cost[p].sum() for p in parts])
+        # greedy largest-first: no rank exceeds the mean by more than the largest single system
+        assert loads.max() - loads.mean() <= cost.max()
+        assert loads.max() / loads.mean() < 1.01
+    assert B.scaling_kind("uneven") == "strong" and B.scaling_kind("spin1") == "weak"
+
+
+def test_balanced_partition_small_cases():
+    B = _bench()
+    assert B.balanced_partition([5.0, 1.0, 1.0, 3.0], 2) == [[0], [1, 2, 3]]
+    assert B.balanced_partition([1.0], 3) == [[0], [], []]
+    assert B.balanced_partition([], 2) == [[], []]
+
+
 def _free_port():
     with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
         s.bind(("127.0.0.1", 0))

@@ -1,5 +1,6 @@
-"""bench.py --impl reference on the host cores: the oracle timed on a bounded sample of the
-benchmark workload, printed as one JSON line in the bench's format.  CPU only."""
+"""bench.py --impl reference on the host cores: the oracle timed on complete solves of the
+benchmark workload's systems (one per process), printed as one JSON line in the bench's format.
+CPU only; the test asks for a one-system wave to stay short."""
 
 import json
 import os
@@ -12,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _run(env_extra):
     env = dict(os.environ, **env_extra)
     return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                           "--steps", "1", "--warmup", "0"], cwd=ROOT, env=env,
+                           "--steps", "1", "--warmup", "0", "--ref-systems", "1"], cwd=ROOT, env=env,
                           capture_output=True, text=True, timeout=600)
 
 
@@ -27,6 +28,9 @@ def test_reference_arm_prints_one_line_in_the_bench_format():
     assert d["config"]["workload"] == "spin1_bichromatic_n1323_x64"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert "complete oracle solves" in cb["sample"] and cb["status_max"] == 0
+    assert d["steps"] == 1 and d["config"]["systems_per_step"] == 1
+    assert d["ms_per_step"] == 1e3 / d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
 
