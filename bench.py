@@ -414,7 +414,9 @@ def main():
                     help="systems per step (64 = the benchmark workload; smaller for profiler captures)")
     ap.add_argument("--ref-systems", type=int, default=0,
                     help="reference arm / CPU baseline: systems per wave (default: one per host core)")
-    ap.add_argument("--ref-max-steps", type=int, default=3)
+    ap.add_argument("--ref-max-steps", type=int, default=2)
+    ap.add_argument("--band-max", type=int, default=-1,
+                    help="widest band reduced by the bulge chase (library option; 0: dense reduction only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -457,8 +459,13 @@ def main():
     problems, count, nt = rank_workload(W, args.workload, args.count, rank, world)
     total_count = int(round(sum_over_ranks(float(count), world, dist, "cuda")))
     ctx = M.Context(local, stream=stream.cuda_stream)
+    ctx.set_option(M.MMF_OPT_BAND_MAX, args.band_max)
     systems = [M.System(ctx, p) for p in problems]
     batch = M.Batch(ctx, systems, prec, nt)
+    paths = {}
+    for i in range(batch.count):
+        k = ("jacobi", "dense", "whole_gpu", "band")[batch.path(i)[0]]
+        paths[k] = paths.get(k, 0) + 1
     ts = np.stack([W.time_grid(p, nt) for p in problems])
     batch.set_times(0.0, ts)
 
@@ -556,6 +563,7 @@ def main():
                            "parallelism": f"replicas x{world}" if args.workload != "uneven"
                            else f"instances split by sum n^3 over {world} rank(s)"},
                 "stage_ms": {k: round(v, 3) for k, v in per.items()},
+                "paths": paths,
                 "roofline": roof, "clocks": clocks, "gpu_launches": launches,
                 "e2e": {"value": total_count / e2e_s, "unit": "solves/s",
                         "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

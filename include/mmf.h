@@ -64,7 +64,8 @@ typedef struct mmf_server mmf_server;
 /* ---------------------------------------------------------------- context
  * mmf_ctx_create: bind to CUDA device `device` and stream `cuda_stream` (a cudaStream_t, or
  * NULL for a stream the context creates and owns).  hbm_budget_bytes caps the device memory
- * all batches of this context may hold at once (0 = 90% of the device's free memory).
+ * all batches of this context may hold at once (0 = 90% of the device's free memory, counting
+ * memory that the process's stream-ordered pool holds unused as free).
  * Errors: MMF_ERR_ARG (out == NULL), MMF_ERR_CUDA (no such device).
  */
 MMF_API int mmf_ctx_create(int device, size_t hbm_budget_bytes, void* cuda_stream, mmf_ctx** out);
@@ -87,6 +88,15 @@ MMF_API size_t mmf_ctx_budget(const mmf_ctx* ctx);
  * MMF_OPT_BT_TC_N: in the mixed path, smallest n whose back-transform (Z = Q Y, Sec. 3.2's
  * eigenvectors from the tridiagonal ones) runs on the tensor cores in split TF32 (default 256);
  * smaller systems use the FP32 SIMT kernel.
+ * MMF_OPT_BAND_MAX: largest half-bandwidth b of H_F (the farthest nonzero from the diagonal, set
+ * by the couplings' block offsets of Eq. 6 / Appendix A) for which a system is reduced to
+ * tridiagonal form by Householder bulge chasing on its band (O(n^2 b) work) instead of the dense
+ * reduction (O(n^3)); at most 64; 0 switches the band path off.  Default: 64 on the FP64 path,
+ * 0 on the mixed path (whose dense reduction and tensor-core back-transform are faster at the
+ * benchmark sizes).  Systems with n < 2 b + 2 use the dense reduction.
+ * MMF_OPT_JACOBI_SWEEPS: iteration cap of the shared-memory Jacobi kernel (default 40 sweeps;
+ * values below 1 act as 1).  A system that has not converged at the cap gets MMF_ST_NOCONV from
+ * mmf_batch_sync / mmf_diagonalise.
  * Results do not depend on the path beyond rounding. */
 #define MMF_OPT_JACOBI_N_FP64 1
 #define MMF_OPT_JACOBI_N_MIXED 2
@@ -94,6 +104,8 @@ MMF_API size_t mmf_ctx_budget(const mmf_ctx* ctx);
 #define MMF_OPT_REFINE_FULL_N 4
 #define MMF_OPT_GRAM_KERNEL 5
 #define MMF_OPT_BT_TC_N 6
+#define MMF_OPT_JACOBI_SWEEPS 7
+#define MMF_OPT_BAND_MAX 8
 MMF_API int mmf_ctx_set_option(mmf_ctx* ctx, int option, int64_t value);
 
 /* ---------------------------------------------------------------- system definition
@@ -143,6 +155,54 @@ MMF_API int mmf_micromotion(mmf_sys* sys, int nt, const double* t, double* UF, i
 MMF_API int mmf_time_evolution_operator(mmf_sys* sys, int precision, double t0, int nt,
                                 const double* t, double* U);
 
+/* ---------------------------------------------------------------- device-pointer variants
+ * The same results as mmf_quasienergies, mmf_eigenvectors, mmf_time_evolution and
+ * mmf_transition_avg (Sec. 3.2; Eq. 3-5 for U; the time average for Pbar), written into
+ * caller-owned DEVICE memory (for example torch tensors) on the caller's CUDA stream `stream`
+ * (a cudaStream_t; NULL = the legacy default stream) instead of host arrays.  Layouts as in the
+ * host versions: E n doubles; Z n x n complex column-major (2 n^2 doubles); U nt x D x D complex
+ * with U[k][j][i] = <j|U(t[k], t0)|i>; P D x D doubles, P[i * D + j] = Pbar_{i->j}.  For
+ * mmf_time_evolution_dev the nt times t are device doubles, read in order after the work already
+ * enqueued on `stream`.  The calls are asynchronous: the library's kernels run on the context's
+ * stream, `stream` waits for them before the copy into the caller's buffer, and the context's
+ * stream waits for that copy before any later library work.  The caller owns the buffers and
+ * must keep them alive until `stream` has run the copy.  A change of nt re-plans the system
+ * (its eigenpairs are recomputed, and that step waits on the host).  Errors: MMF_ERR_ARG (NULL
+ * pointer, nt < 1), MMF_ERR_STATE (before mmf_diagonalise), MMF_ERR_CUDA. */
+MMF_API int mmf_quasienergies_dev(mmf_sys* sys, double* E, void* stream);
+MMF_API int mmf_eigenvectors_dev(mmf_sys* sys, double* Z, void* stream);
+MMF_API int mmf_time_evolution_dev(mmf_sys* sys, double t0, int nt, const double* t, double* U, void* stream);
+MMF_API int mmf_transition_avg_dev(mmf_sys* sys, double* P, void* stream);
+
+/* ---------------------------------------------------------------- dressed basis (Sec. 3.3, Eq. 4)
+ * Evolution expressed in the time-dependent basis of a subset of the modes (the "dressing" modes,
+ * Sec. 3.3): with U_F(t) the micromotion operator of Eq. 5 for the system restricted to those
+ * modes (one Floquet zone: its D eigenvectors of largest central-block weight, ties to the lower
+ * index, in ascending order, as mmf_micromotion) and Ebar their quasienergies,
+ *     Ud(t2, t1) = U_F(t2)^dagger U(t2, t1) U_F(t1),
+ * where U(t2, t1) is the evolution of the full system (Eq. 3-4).  Without the other modes Ud is
+ * diag(e^{-i Ebar (t2 - t1)}); with them it shows the transitions they drive between dressed
+ * states (Sec. 4.1's probe spectroscopy).
+ * mmf_sys_restrict: a new system (caller destroys it) with the same levels and H0 and only the
+ *   modes listed in `modes` (indices in call order, each at most once), in that order.
+ * mmf_batch_dressed: `full` is a batch of systems with nt >= 1 times t2 and start t0 = t1 (set by
+ *   mmf_batch_set_times) and `dress` a batch, of the same count and levels, of the same systems
+ *   restricted to their dressing modes (any nt); both have been run.  Writes (host, any may be
+ *   NULL) Ud packed like the full batch's U (mmf_batch_dressed_offset(full, 0, i) in complex
+ *   elements, nt x D x D per system, Ud[k][a][c] = <a|Ud(t2_k, t1)|c>) and Ebar (D doubles per
+ *   system at mmf_batch_dressed_offset(full, 1, i)); mmf_batch_dressed_size(full, 0 or 1) gives
+ *   the totals.  Waits for the result.  Errors: MMF_ERR_ARG (mismatched batches, nt = 0),
+ *   MMF_ERR_STATE (a batch not run).
+ * mmf_dressed_time_evolution: the same for one system: solves the restricted system and the
+ *   full one (precision MMF_FP64 or MMF_MIXED) and writes Ud (nt x D x D complex) for the times
+ *   t2[0..nt-1] from t1, and Ebar (D).  Returns the larger numerical status of the two solves. */
+MMF_API int mmf_sys_restrict(const mmf_sys* sys, int nmodes, const int* modes, mmf_sys** out);
+MMF_API int mmf_batch_dressed(mmf_batch* full, mmf_batch* dress, double* Ud, double* Ebar);
+MMF_API int64_t mmf_batch_dressed_size(const mmf_batch* full, int what);
+MMF_API int64_t mmf_batch_dressed_offset(const mmf_batch* full, int what, int i);
+MMF_API int mmf_dressed_time_evolution(mmf_sys* sys, int ndress, const int* dressing, int precision, double t1,
+                                       int nt, const double* t2, double* Ud, double* Ebar);
+
 /* ---------------------------------------------------------------- spin systems (Sec. 3.4)
  * Coupling matrices of a spin S = S2/2 (D = S2 + 1 levels, basis m = S, S-1, ..., -S, angular
  * momentum matrices S_x, S_y, S_z as defined in Sakurai Sec. 3.5), built from the field
@@ -183,6 +243,10 @@ MMF_API int mmf_batch_eigenvectors(mmf_batch* b, int i, double* Z);
 /* Packed results of all systems (E: sum n, U: sum nt D^2 complex, P: sum D^2) copied to the
  * host with one transfer each; any may be NULL.  Enqueued and waited on the stream. */
 MMF_API int mmf_batch_results(mmf_batch* b, double* E, double* U, double* P);
+/* The packed results of mmf_batch_results copied into caller-owned DEVICE buffers on the
+ * caller's stream (any may be NULL), ordered after the batch's work and before any later work
+ * of the batch's stream; asynchronous (see the device-pointer variants above). */
+MMF_API int mmf_batch_results_dev(mmf_batch* b, double* E, double* U, double* P, void* stream);
 /* Offsets (in doubles for E and P, in complex elements for U) of system i in the packed
  * results: what = 0 (E), 1 (U), 2 (P). */
 MMF_API int64_t mmf_batch_offset(const mmf_batch* b, int what, int i);
@@ -197,17 +261,30 @@ MMF_API int64_t mmf_batch_size(const mmf_batch* b, int what);
 #define MMF_STAGES 9
 MMF_API int mmf_batch_timing(mmf_batch* b, int max_runs);
 MMF_API int mmf_batch_stage_ms(mmf_batch* b, double* ms, int* runs);
+/* Eigensolver path of system i (returns one of MMF_PATH_*; *band, if not NULL, receives the
+ * half-bandwidth used by the band path, else 0): the shared-memory Jacobi kernel, the dense
+ * Householder reduction (one thread-block cluster per system), the whole-GPU dense reduction for
+ * the largest systems, or the band path (bulge chase on the band of H_F, see MMF_OPT_BAND_MAX). */
+#define MMF_PATH_JACOBI 0
+#define MMF_PATH_DENSE 1
+#define MMF_PATH_WHOLE_GPU 2
+#define MMF_PATH_BAND 3
+MMF_API int mmf_batch_path(const mmf_batch* b, int i, int* band);
 /* Device bytes held by the batch. */
 MMF_API size_t mmf_batch_bytes(const mmf_batch* b);
 MMF_API int mmf_batch_destroy(mmf_batch* b);
 
 /* ---------------------------------------------------------------- serving
  * Continuous batching of independent solve requests (the paper's parameter sweeps served as
- * they arrive).  A worker thread groups queued requests (same nt, at most max_batch per plan)
- * into batch plans and runs each plan on one of `slots` CUDA streams; a plan is admitted only
- * while the context's HBM budget has room for it, so requests wait in the queue until slots and
- * memory free up.  Plans on different slots overlap on the device.  Each request's results are
- * those of the same system solved alone (up to summation order).
+ * they arrive).  A worker thread groups queued requests (same nt and the same size class of n as
+ * the oldest waiting request: n <= 128, <= 640, <= 2500, larger; at most max_batch per plan) into
+ * batch plans and runs each plan on one of `slots` CUDA streams; a plan is admitted only while
+ * the context's HBM budget has room for it, so requests wait in the queue until slots and memory
+ * free up.  Plans on different slots overlap on the device.  Finished plans stay resident (up to
+ * max(4, 2 slots) of them, within the budget): a later group whose systems have the same
+ * structure (levels, modes, truncations, harmonics, nt) reuses one, with its own coefficients and
+ * times; resident plans are released, least recently used first, when a new plan needs memory.
+ * Each request's results are those of the same system solved alone (up to summation order).
  *   mmf_serve_submit copies the system definition and the times; the caller may then change or
  *   destroy its system.  *ticket identifies the request.
  *   mmf_serve_wait blocks until the request is done (timeout_ms < 0: no limit; MMF_ERR_STATE on
@@ -226,6 +303,8 @@ MMF_API int mmf_serve_wait(mmf_server* srv, uint64_t ticket, int timeout_ms, dou
 MMF_API int mmf_serve_stats(mmf_server* srv, double* p50_ms, double* p99_ms, double* mean_ms,
                             int64_t* completed);
 MMF_API int mmf_serve_reset_stats(mmf_server* srv);
+/* Plans created, plans reused from the resident set, and plans resident now (any may be NULL). */
+MMF_API int mmf_serve_plan_stats(mmf_server* srv, int64_t* created, int64_t* reused, int64_t* resident);
 MMF_API int mmf_serve_destroy(mmf_server* srv);
 
 /* ---------------------------------------------------------------- no device allocation
@@ -238,14 +317,18 @@ MMF_API int mmf_serve_destroy(mmf_server* srv);
  *   d  device, n doubles (diagonal);  e  device, n-1 doubles (off-diagonal; may be NULL if n == 1)
  *   E  device, n doubles: eigenvalues ascending;  Y  device, n*n doubles, row-major:
  *      Y[i*n + k] = component i of the eigenvector of E[k]
- *   stream: a cudaStream_t (NULL = the legacy default stream); the call only enqueues work.
- * n must be 1..MMF_NOALLOC_TRIDIAG_NMAX, otherwise MMF_ERR_UNSUPPORTED.  The first call on a
- * device looks up the device address of the scratch array (with that device current); make that
- * first call before any stream capture.  All calls share the scratch array: calls whose GPU work
- * overlaps (other streams, other host threads) race on it and must be serialised by the caller. */
+ *   status  device int or NULL: set to MMF_OK, or MMF_ST_NOCONV if a bisection reached its
+ *      iteration cap (the caller reads it after the stream has run the call's work)
+ *   stream: a cudaStream_t (NULL = the legacy default stream).
+ * The call is asynchronous: it enqueues kernels on `stream` (no host copies, no allocation) and
+ * returns.  n must be 1..MMF_NOALLOC_TRIDIAG_NMAX, otherwise MMF_ERR_UNSUPPORTED.  The first call
+ * on a device (and the first after its context was reset) looks up the device address of the
+ * scratch array, with that device current; make that first call before any stream capture.  All
+ * calls share the scratch array: calls whose GPU work overlaps (other streams, other host
+ * threads) race on it and must be serialised by the caller. */
 #define MMF_NOALLOC_TRIDIAG_NMAX 256
 MMF_API int mmf_tridiag_eig_noalloc(const double* d, const double* e, int n, double* E, double* Y,
-                                    void* stream);
+                                    int* status, void* stream);
 
 /* ---------------------------------------------------------------- diagnostics
  * Runs the library's batched tcgen05 GEMM (kind 0: TF32, kind 1: BF16; `products` copies of the

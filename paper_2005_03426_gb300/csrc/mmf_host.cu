@@ -47,6 +47,9 @@ struct mmf_ctx {
     int64_t refine_full_n = -1;      // mixed path: second refinement step in full from this n on
     int64_t gram_kernel = 0;         // mixed path: 0 = BF16 tensor cores (exact slicing), 1 = double-FP32
     int64_t bt_tc_n = -1;            // mixed path: back-transform on the tensor cores from this n on
+    int64_t jacobi_sweeps = -1;      // Jacobi sweep cap; -1 = library default
+    int64_t band_max = -1;           // largest half-bandwidth reduced by the bulge chase; -1 = default
+    cudaEvent_t order_ev = nullptr;  // orders the context stream against callers' streams (*_dev calls)
     std::recursive_mutex mu;
 };
 
@@ -76,7 +79,11 @@ struct mmf_batch {
     int count = 0, precision = 0, nt = 0;
     std::vector<mmf_sys*> sys;
     std::vector<MmfDesc> desc;
-    std::vector<int> all, small, large, medium, huge;  // large = medium + huge
+    std::vector<int> all, small, large, medium, huge;  // large = medium + huge + the banded ones
+    // banded systems reduced by the bulge chase, per window class (8, 16, 32, 64)
+    std::vector<int> sbr[4];
+    int nmax_sbr[4] = {0, 0, 0, 0};
+    int* d_sbr[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<int> rband, rfull;                     // mixed: hybrid / full second refinement step
     std::vector<int> btc, bts;                         // large: back-transform on tensor cores / SIMT
     std::vector<int> btc_n;                            // n of each system in btc
@@ -87,6 +94,7 @@ struct mmf_batch {
     int nmax_all = 0, nmax_small = 0, nmax_large = 0, Mmax = 1, Dmax = 1;
     int64_t n_oz = 0;      // BF16 elements of the Gram-product slices (mixed, tensor-core Gram)
     int gram_kernel = 0;   // copied from the context at creation
+    int jacobi_sweeps = 40;  // copied from the context at creation
     int64_t n_pat = 0;
     int* d_pat = nullptr;  // mixed path: nonzero pattern of the coefficient rows
     int64_t n_coef = 0, n_mat = 0, n_vec = 0, n_sq = 0, n_pan = 0, n_t = 0, n_f = 0, n_u = 0,
@@ -167,6 +175,32 @@ static int64_t sys_dim(const mmf_sys* s) {
     return (int64_t)s->D * m;
 }
 
+// Half-bandwidth of H_F (Eq. 6, Appendix A): the largest |row - col| of a nonzero entry.  H0
+// contributes |i - i'|; harmonic h of mode l (present in H_F only if h <= 2 N_l) puts V^{l,h}
+// at block offset h S_l, so its entry (i, i') lands at column - row = D h S_l + i' - i.
+static int sys_band(const mmf_sys* s) {
+    const int D = s->D;
+    int64_t b = 0;
+    for (int i = 0; i < D; ++i)
+        for (int k = 0; k < D; ++k) {
+            const double2 h = s->H0[(size_t)i * D + k];
+            if (h.x != 0.0 || h.y != 0.0) b = std::max<int64_t>(b, std::abs(i - k));
+        }
+    int64_t S = 1;
+    for (size_t l = 0; l < s->omega.size(); ++l) {
+        for (size_t h = 0; h < s->V[l].size() && (int64_t)(h + 1) <= 2 * (int64_t)s->N[l]; ++h) {
+            const auto& V = s->V[l][h];
+            for (int i = 0; i < D; ++i)
+                for (int k = 0; k < D; ++k) {
+                    const double2 v = V[(size_t)i * D + k];
+                    if (v.x != 0.0 || v.y != 0.0) b = std::max<int64_t>(b, (int64_t)D * (int64_t)(h + 1) * S + k - i);
+                }
+        }
+        S *= 2 * (int64_t)s->N[l] + 1;
+    }
+    return (int)std::min<int64_t>(std::max<int64_t>(b, 1), INT32_MAX / 4);
+}
+
 // Spin couplings of Eq. 7 (host only).  S_z = diag(m), S_+ |m> = sqrt(S(S+1) - m(m+1)) |m+1>,
 // S_x = (S_+ + S_-)/2, S_y = (S_+ - S_-)/(2i), in the basis m = S, S-1, ..., -S.
 extern "C" int mmf_spin_components(int S2, const double* A, const double* phi, int is_static, double* V) {
@@ -245,6 +279,17 @@ extern "C" int mmf_ctx_create(int device, size_t budget, void* stream, mmf_ctx**
         }
         c->own_stream = true;
     }
+    // keep freed batch memory in the stream-ordered pool of this process for reuse
+    cudaMemPool_t pool;
+    uint64_t pool_idle = 0;  // reserved by the pool but not in use: available to new batches
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        uint64_t reserved = 0, used = 0;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+            cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+            pool_idle = reserved - used;
+    }
     if (budget == 0) {
         size_t fr = 0, tot = 0;
         cudaError_t e = cudaMemGetInfo(&fr, &tot);
@@ -253,15 +298,9 @@ extern "C" int mmf_ctx_create(int device, size_t budget, void* stream, mmf_ctx**
             delete c;
             return fail(MMF_ERR_CUDA, cudaGetErrorString(e));
         }
-        budget = fr / 10 * 9;
+        budget = (fr + (size_t)pool_idle) / 10 * 9;
     }
     c->budget = budget;
-    // keep freed batch memory in the stream-ordered pool of this process for reuse
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
-        uint64_t thr = UINT64_MAX;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    }
     *out = c;
     return MMF_OK;
 }
@@ -270,6 +309,7 @@ extern "C" int mmf_ctx_destroy(mmf_ctx* c) {
     if (!c) return MMF_ERR_ARG;
     cudaSetDevice(c->device);
     if (c->own_stream) cudaStreamDestroy(c->stream);
+    if (c->order_ev) cudaEventDestroy(c->order_ev);
     delete c;
     return MMF_OK;
 }
@@ -284,6 +324,8 @@ extern "C" int mmf_ctx_set_option(mmf_ctx* c, int option, int64_t value) {
         case MMF_OPT_LARGE_N: c->large_n = value; return MMF_OK;
         case MMF_OPT_REFINE_FULL_N: c->refine_full_n = value; return MMF_OK;
         case MMF_OPT_BT_TC_N: c->bt_tc_n = value; return MMF_OK;
+        case MMF_OPT_JACOBI_SWEEPS: c->jacobi_sweeps = value; return MMF_OK;
+        case MMF_OPT_BAND_MAX: c->band_max = value; return MMF_OK;
         case MMF_OPT_GRAM_KERNEL:
             if (value > 1) return fail(MMF_ERR_ARG, "MMF_OPT_GRAM_KERNEL: 0 (tensor cores) or 1 (double-FP32)");
             c->gram_kernel = value < 0 ? 0 : value;
@@ -419,6 +461,7 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     b->precision = precision;
     b->nt = nt;
     b->gram_kernel = (int)ctx->gram_kernel;
+    b->jacobi_sweeps = ctx->jacobi_sweeps < 0 ? 40 : (int)std::max<int64_t>(1, std::min<int64_t>(ctx->jacobi_sweeps, 1000));
     b->sys.assign(systems, systems + count);
     b->desc.resize(count);
     const int fp32 = precision == MMF_MIXED;
@@ -466,8 +509,20 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         b->n_vec += n;
         d.sq_off = b->n_sq;
         d.oz_off = b->n_oz;
+        // banded systems: bulge chase instead of the dense reduction and its back-transform
+        const int64_t bmax_opt = ctx->band_max < 0 ? (precision == MMF_FP64 ? 64 : 0)
+                                                   : std::min<int64_t>(ctx->band_max, 64);
+        int cls = 0;
+        if (!d.small && bmax_opt > 0) {
+            const int band = sys_band(s);
+            if (band <= bmax_opt && n >= 2 * (int64_t)band + 2 &&
+                mmf_sbr_store_elems((int)n, band) <= n * (int64_t)d.ld) {
+                d.band = band;
+                cls = mmf_sbr_class(band);
+            }
+        }
         // mixed: back-transform on the tensor cores for large enough systems (SIMT otherwise)
-        const bool tc = precision == MMF_MIXED && !d.small && n >= std::max<int64_t>(bt_tc_n(ctx), 3);
+        const bool tc = precision == MMF_MIXED && !d.small && !cls && n >= std::max<int64_t>(bt_tc_n(ctx), 3);
         if (precision == MMF_MIXED) {
             // one area per system, used in turn by the back-transform's operands, the Gram slices
             // (BF16) and split-TF32 operands of the refinement, and the time evolution's slices and Phi
@@ -478,7 +533,11 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
             b->n_oz += std::max<int64_t>(std::max<int64_t>(oz, 2 * mmf_tf3_floats((int)n)),
                                          std::max<int64_t>(tc ? 2 * mmf_bt_floats((int)n) : 0, ph));
         }
-        if (!d.small) {
+        if (cls) {
+            const int ci = cls == 8 ? 0 : cls == 16 ? 1 : cls == 32 ? 2 : 3;
+            b->sbr[ci].push_back(i);
+            b->nmax_sbr[ci] = std::max(b->nmax_sbr[ci], (int)n);
+        } else if (!d.small) {
             (tc ? b->btc : b->bts).push_back(i);
             if (tc) {
                 b->btc_n.push_back((int)n);
@@ -502,11 +561,11 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         b->n_p += (int64_t)s->D * s->D;
         b->all.push_back(i);
         (d.small ? b->small : b->large).push_back(i);
-        if (!d.small) (n >= lmin ? b->huge : b->medium).push_back(i);
+        if (!d.small && !cls) (n >= lmin ? b->huge : b->medium).push_back(i);
         b->nmax_all = std::max(b->nmax_all, (int)n);
         if (d.small) b->nmax_small = std::max(b->nmax_small, (int)n);
         else b->nmax_large = std::max(b->nmax_large, (int)n);
-        if (!d.small && n < lmin) b->nmax_medium = std::max(b->nmax_medium, (int)n);
+        if (!d.small && !cls && n < lmin) b->nmax_medium = std::max(b->nmax_medium, (int)n);
         b->Mmax = std::max(b->Mmax, (int)M);
         b->Dmax = std::max(b->Dmax, s->D);
         if (n >= refine_full_n(ctx)) {
@@ -524,7 +583,7 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     size_t o_all = p.take(sizeof(int) * count), o_small = p.take(sizeof(int) * count),
            o_large = p.take(sizeof(int) * count), o_medium = p.take(sizeof(int) * count),
            o_status = p.take(sizeof(int) * count), o_rband = p.take(sizeof(int) * count),
-           o_rfull = p.take(sizeof(int) * count), o_btc = p.take(sizeof(int) * count),
+           o_rfull = p.take(sizeof(int) * count), o_sbr = p.take(sizeof(int) * count), o_btc = p.take(sizeof(int) * count),
            o_bts = p.take(sizeof(int) * count);
     size_t o_coef = p.take(sizeof(double2) * b->n_coef);
     size_t o_H = p.take(cs * b->n_mat);
@@ -570,6 +629,16 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
                                         ", largest n " + std::to_string(b_nmax) + ")");
     }
     cudaError_t e = cudaMallocAsync((void**)&b->base, b->bytes, b->stream);
+    if (e == cudaErrorMemoryAllocation) {
+        // memory other contexts of this process freed may sit idle in the pool: release it, retry
+        cudaGetLastError();
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
+            cudaStreamSynchronize(b->stream);
+            cudaMemPoolTrimTo(pool, 0);
+        }
+        e = cudaMallocAsync((void**)&b->base, b->bytes, b->stream);
+    }
     if (e != cudaSuccess) {
         delete b;
         return fail(MMF_ERR_CUDA, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
@@ -586,6 +655,13 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     b->d_rfull = (int*)(B + o_rfull);
     b->d_btc = (int*)(B + o_btc);
     b->d_bts = (int*)(B + o_bts);
+    {  // the four window classes share one index array, one after another
+        int* q = (int*)(B + o_sbr);
+        for (int ci = 0; ci < 4; ++ci) {
+            b->d_sbr[ci] = q;
+            q += b->sbr[ci].size();
+        }
+    }
     if (!b->btc.empty()) b->d_btjobs = B + o_btjobs;
     b->d_coef = (double2*)(B + o_coef);
     b->d_H = B + o_H;
@@ -652,6 +728,10 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         e = cudaMemcpyAsync(b->d_rfull, b->rfull.data(), sizeof(int) * b->rfull.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !b->btc.empty())
         e = cudaMemcpyAsync(b->d_btc, b->btc.data(), sizeof(int) * b->btc.size(), cudaMemcpyHostToDevice, st);
+    for (int ci = 0; ci < 4; ++ci)
+        if (e == cudaSuccess && !b->sbr[ci].empty())
+            e = cudaMemcpyAsync(b->d_sbr[ci], b->sbr[ci].data(), sizeof(int) * b->sbr[ci].size(),
+                                cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !b->bts.empty())
         e = cudaMemcpyAsync(b->d_bts, b->bts.data(), sizeof(int) * b->bts.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
@@ -797,7 +877,7 @@ static int stage_eig(mmf_batch* b) {
     mark(b, ST_JACOBI);
     if (!b->small.empty()) {
         MmfLaunch Ls = launch_of(b, b->small, b->d_small, b->nmax_small);
-        LAUNCH(mmf_launch_jacobi(Ls, b->d_H, nullptr, b->d_E, b->d_Zf, b->d_status, fp32, 40), 1);
+        LAUNCH(mmf_launch_jacobi(Ls, b->d_H, nullptr, b->d_E, b->d_Zf, b->d_status, fp32, b->jacobi_sweeps), 1);
     }
     if (!b->large.empty()) {
         MmfLaunch Ll = launch_of(b, b->large, b->d_large, b->nmax_large);
@@ -805,6 +885,11 @@ static int stage_eig(mmf_batch* b) {
         if (!b->medium.empty()) {
             MmfLaunch Lm = launch_of(b, b->medium, b->d_medium, b->nmax_medium);
             LAUNCH(mmf_launch_hetrd(Lm, b->d_H, b->d_Vp, b->d_Wp, b->d_d, b->d_e, b->d_tau, fp32), 1);
+        }
+        for (int ci = 0; ci < 4; ++ci) {  // banded systems: bulge chase
+            if (b->sbr[ci].empty()) continue;
+            MmfLaunch Lb = launch_of(b, b->sbr[ci], b->d_sbr[ci], b->nmax_sbr[ci]);
+            LAUNCH(mmf_launch_sbr_chase(Lb, 8 << ci, b->d_H, b->d_Zf, b->d_d, b->d_e, b->d_status, fp32), 1);
         }
         for (int i : b->huge) {  // one system at a time over the whole GPU
             const MmfDesc& d = b->desc[i];
@@ -829,6 +914,11 @@ static int stage_eig(mmf_batch* b) {
                                                b->d_btjobs, b->d_status, &nl),
                    0);
             g_launches += nl;
+        }
+        for (int ci = 0; ci < 4; ++ci) {  // banded systems: Z = Q Y from the chase's reflectors
+            if (b->sbr[ci].empty()) continue;
+            MmfLaunch Lb = launch_of(b, b->sbr[ci], b->d_sbr[ci], b->nmax_sbr[ci]);
+            LAUNCH(mmf_launch_sbr_bt(Lb, 8 << ci, b->d_Zf, b->d_Y, b->d_work, b->d_Zp, fp32), 2);
         }
         if (fp32) LAUNCH(mmf_launch_widen(Ll, b->d_Zp, b->d_Zf, fp32), 1);
     } else {
@@ -1034,6 +1124,17 @@ extern "C" int64_t mmf_batch_offset(const mmf_batch* b, int what, int i) {
     return -1;
 }
 
+extern "C" int mmf_batch_path(const mmf_batch* b, int i, int* band) {
+    if (!b || i < 0 || i >= b->count) return fail(MMF_ERR_ARG, "bad batch index");
+    const MmfDesc& d = b->desc[i];
+    if (band) *band = d.band;
+    if (d.small) return MMF_PATH_JACOBI;
+    if (d.band > 0) return MMF_PATH_BAND;
+    for (int h : b->huge)
+        if (h == i) return MMF_PATH_WHOLE_GPU;
+    return MMF_PATH_DENSE;
+}
+
 extern "C" int64_t mmf_batch_size(const mmf_batch* b, int what) {
     if (!b) return -1;
     if (what == 0) return b->n_vec;
@@ -1213,11 +1314,254 @@ extern "C" int mmf_time_evolution_operator(mmf_sys* s, int precision, double t0,
     return rc2 != MMF_OK ? rc2 : rc;
 }
 
+// ------------------------------------------------------------------ device-pointer variants
+// The results go to caller-owned device memory on the caller's stream.  The library's work stays on
+// the context stream; the caller's stream waits for it (event), the copy runs on the caller's
+// stream, and the context stream then waits for the copy, so later library work cannot overwrite
+// the source before it has been read.  Nothing waits on the host.
+static int order_after(mmf_ctx* c, cudaStream_t waiter, cudaStream_t producer) {
+    if (waiter == producer) return MMF_OK;
+    if (!c->order_ev) CU(cudaEventCreateWithFlags(&c->order_ev, cudaEventDisableTiming));
+    CU(cudaEventRecord(c->order_ev, producer));
+    CU(cudaStreamWaitEvent(waiter, c->order_ev, 0));
+    return MMF_OK;
+}
+
+// copy `bytes` (rows x width, pitched source) from the library's state to the caller's buffer
+static int dev_copy_out(mmf_ctx* c, cudaStream_t lib_st, cudaStream_t user, void* dst, size_t dpitch,
+                        const void* src, size_t spitch, size_t width, size_t rows) {
+    int rc = order_after(c, user, lib_st);
+    if (rc != MMF_OK) return rc;
+    if (width && rows) CU(cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, cudaMemcpyDeviceToDevice, user));
+    return order_after(c, lib_st, user);
+}
+
+extern "C" int mmf_quasienergies_dev(mmf_sys* s, double* E, void* stream) {
+    if (!s || !E) return fail(MMF_ERR_ARG, "sys and E required");
+    if (s->state < 2) return fail(MMF_ERR_STATE, "call mmf_diagonalise first");
+    std::lock_guard<std::recursive_mutex> lk(s->ctx->mu);
+    CU(cudaSetDevice(s->ctx->device));
+    mmf_batch* b = s->solo;
+    const MmfDesc& d = b->desc[0];
+    return dev_copy_out(s->ctx, b->stream, (cudaStream_t)stream, E, sizeof(double) * d.n, b->d_E + d.vec_off,
+                        sizeof(double) * d.n, sizeof(double) * d.n, 1);
+}
+
+extern "C" int mmf_eigenvectors_dev(mmf_sys* s, double* Z, void* stream) {
+    if (!s || !Z) return fail(MMF_ERR_ARG, "sys and Z required");
+    if (s->state < 2) return fail(MMF_ERR_STATE, "call mmf_diagonalise first");
+    std::lock_guard<std::recursive_mutex> lk(s->ctx->mu);
+    CU(cudaSetDevice(s->ctx->device));
+    mmf_batch* b = s->solo;
+    const MmfDesc& d = b->desc[0];
+    return dev_copy_out(s->ctx, b->stream, (cudaStream_t)stream, Z, sizeof(double2) * d.n, b->d_Zf + d.mat_off,
+                        sizeof(double2) * d.ld, sizeof(double2) * d.n, d.n);
+}
+
+extern "C" int mmf_time_evolution_dev(mmf_sys* s, double t0, int nt, const double* t, double* U, void* stream) {
+    if (!s || nt < 1 || !t || !U) return fail(MMF_ERR_ARG, "sys, nt >= 1, t and U required");
+    if (!std::isfinite(t0)) return fail(MMF_ST_NONFINITE, "t0 not finite");
+    if (s->state < 2) return fail(MMF_ERR_STATE, "call mmf_diagonalise first");
+    std::lock_guard<std::recursive_mutex> lk(s->ctx->mu);
+    CU(cudaSetDevice(s->ctx->device));
+    cudaStream_t user = (cudaStream_t)stream;
+    mmf_batch* b = s->solo;
+    if (b->nt != nt) {
+        // a plan with room for nt times; the eigenpairs are recomputed on the new plan
+        mmf_batch* nb = nullptr;
+        mmf_sys* arr[1] = {s};
+        int rc = mmf_batch_create(s->ctx, 1, arr, b->precision, nt, &nb);
+        if (rc != MMF_OK) return rc;
+        mmf_batch_destroy(b);
+        s->solo = b = nb;
+        rc = stage_assemble(b);
+        if (rc == MMF_OK) rc = stage_eig(b);
+        if (rc != MMF_OK) return rc;
+    }
+    // the times come from the caller's stream
+    int rc = order_after(s->ctx, b->stream, user);
+    if (rc != MMF_OK) return rc;
+    CU(cudaMemcpyAsync(b->d_t, t, sizeof(double) * nt, cudaMemcpyDeviceToDevice, b->stream));
+    b->t0 = t0;
+    b->times_set = true;
+    rc = stage_outputs(b);
+    if (rc != MMF_OK) return rc;
+    const MmfDesc& d = b->desc[0];
+    const size_t bytes = sizeof(double2) * (size_t)nt * d.D * d.D;
+    return dev_copy_out(s->ctx, b->stream, user, U, bytes, b->d_U + d.u_off, bytes, bytes, 1);
+}
+
+extern "C" int mmf_transition_avg_dev(mmf_sys* s, double* P, void* stream) {
+    if (!s || !P) return fail(MMF_ERR_ARG, "sys and P required");
+    if (s->state < 2) return fail(MMF_ERR_STATE, "call mmf_diagonalise first");
+    std::lock_guard<std::recursive_mutex> lk(s->ctx->mu);
+    CU(cudaSetDevice(s->ctx->device));
+    mmf_batch* b = s->solo;
+    if (b->last_stage < 3) {
+        if (b->nt > 0 && !b->times_set) {
+            std::vector<double> z((size_t)b->nt, 0.0);
+            int rc = mmf_batch_set_times(b, 0.0, z.data());
+            if (rc != MMF_OK) return rc;
+        }
+        int rc = stage_outputs(b);
+        if (rc != MMF_OK) return rc;
+    }
+    const MmfDesc& d = b->desc[0];
+    const size_t bytes = sizeof(double) * d.D * d.D;
+    return dev_copy_out(s->ctx, b->stream, (cudaStream_t)stream, P, bytes, b->d_P + d.p_off, bytes, bytes, 1);
+}
+
+extern "C" int mmf_batch_results_dev(mmf_batch* b, double* E, double* U, double* P, void* stream) {
+    if (!b) return fail(MMF_ERR_ARG, "batch is NULL");
+    if (b->last_stage < 3) return fail(MMF_ERR_STATE, "batch not run");
+    std::lock_guard<std::recursive_mutex> lk(b->ctx->mu);
+    CU(cudaSetDevice(b->ctx->device));
+    cudaStream_t user = (cudaStream_t)stream;
+    int rc = order_after(b->ctx, user, b->stream);
+    if (rc != MMF_OK) return rc;
+    if (E && b->n_vec) CU(cudaMemcpyAsync(E, b->d_E, sizeof(double) * b->n_vec, cudaMemcpyDeviceToDevice, user));
+    if (U && b->n_u) CU(cudaMemcpyAsync(U, b->d_U, sizeof(double2) * b->n_u, cudaMemcpyDeviceToDevice, user));
+    if (P && b->n_p) CU(cudaMemcpyAsync(P, b->d_P, sizeof(double) * b->n_p, cudaMemcpyDeviceToDevice, user));
+    return order_after(b->ctx, b->stream, user);
+}
+
+// ------------------------------------------------------------------ dressed basis (Sec. 3.3, Eq. 4)
+extern "C" int mmf_sys_restrict(const mmf_sys* s, int nmodes, const int* modes, mmf_sys** out) {
+    if (!out) return fail(MMF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!s || nmodes < 1 || !modes) return fail(MMF_ERR_ARG, "sys, nmodes >= 1 and modes required");
+    const int K = (int)s->omega.size();
+    for (int k = 0; k < nmodes; ++k) {
+        if (modes[k] < 0 || modes[k] >= K) return fail(MMF_ERR_ARG, "mode index out of range");
+        for (int q = 0; q < k; ++q)
+            if (modes[q] == modes[k]) return fail(MMF_ERR_ARG, "mode listed twice");
+    }
+    mmf_sys* r = new (std::nothrow) mmf_sys();
+    if (!r) return fail(MMF_ERR_NOMEM, "system allocation");
+    r->ctx = s->ctx;
+    r->D = s->D;
+    r->H0 = s->H0;
+    for (int k = 0; k < nmodes; ++k) {
+        r->omega.push_back(s->omega[modes[k]]);
+        r->N.push_back(s->N[modes[k]]);
+        r->V.push_back(s->V[modes[k]]);
+    }
+    *out = r;
+    return MMF_OK;
+}
+
+extern "C" int64_t mmf_batch_dressed_size(const mmf_batch* b, int what) {
+    if (!b) return -1;
+    int64_t ne = 0;
+    for (const MmfDesc& d : b->desc) ne += d.D;
+    if (what == 0) return b->n_u;
+    if (what == 1) return ne;
+    return -1;
+}
+
+extern "C" int64_t mmf_batch_dressed_offset(const mmf_batch* b, int what, int i) {
+    if (!b || i < 0 || i >= b->count) return -1;
+    if (what == 0) return b->desc[i].u_off;
+    if (what == 1) {
+        int64_t o = 0;
+        for (int q = 0; q < i; ++q) o += b->desc[q].D;
+        return o;
+    }
+    return -1;
+}
+
+extern "C" int mmf_batch_dressed(mmf_batch* full, mmf_batch* dress, double* Ud, double* Ebar) {
+    if (!full || !dress) return fail(MMF_ERR_ARG, "both batches required");
+    if (full->ctx != dress->ctx) return fail(MMF_ERR_ARG, "batches of different contexts");
+    if (full->count != dress->count) return fail(MMF_ERR_ARG, "batches of different sizes");
+    for (int i = 0; i < full->count; ++i)
+        if (full->desc[i].D != dress->desc[i].D) return fail(MMF_ERR_ARG, "system " + std::to_string(i) + ": levels differ");
+    if (full->nt < 1) return fail(MMF_ERR_ARG, "the full batch needs times (nt >= 1)");
+    if (full->last_stage < 3 || dress->last_stage < 2) return fail(MMF_ERR_STATE, "run both batches first");
+    mmf_ctx* c = full->ctx;
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    CU(cudaSetDevice(c->device));
+    cudaStream_t st = full->stream;
+    int rc = order_after(c, st, dress->stream);
+    if (rc != MMF_OK) return rc;
+    const int count = full->count, nt = full->nt;
+    std::vector<int64_t> roff(count), ufoff(count);
+    int64_t ne = 0, nuf = 0;
+    int Dmax = 1, nmax_d = 1;
+    for (int i = 0; i < count; ++i) {
+        const int D = full->desc[i].D;
+        roff[i] = ne;
+        ufoff[i] = nuf;
+        ne += D;
+        nuf += (int64_t)(nt + 1) * D * D;
+        Dmax = std::max(Dmax, D);
+        nmax_d = std::max(nmax_d, dress->desc[i].n);
+    }
+    // temporaries: offsets, representatives, Ebar, U_F, W, Ud
+    Pool p;
+    const size_t o_roff = p.take(sizeof(int64_t) * count), o_uoff = p.take(sizeof(int64_t) * count),
+                 o_reps = p.take(sizeof(int64_t) * ne), o_eb = p.take(sizeof(double) * ne),
+                 o_uf = p.take(sizeof(double2) * nuf), o_w = p.take(sizeof(double2) * full->n_u),
+                 o_ud = p.take(sizeof(double2) * full->n_u);
+    unsigned char* tmp = nullptr;
+    CU(cudaMallocAsync((void**)&tmp, p.off, st));
+    cudaError_t e = cudaMemcpyAsync(tmp + o_roff, roff.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tmp + o_uoff, ufoff.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = mmf_launch_dressed(dress->d_desc, full->d_desc, count, nmax_d, Dmax, dress->d_Zf, dress->d_E, full->d_U,
+                               full->d_t, full->t0, nt, (const int64_t*)(tmp + o_roff), (const int64_t*)(tmp + o_uoff),
+                               (int64_t*)(tmp + o_reps), (double*)(tmp + o_eb), (double2*)(tmp + o_uf),
+                               (double2*)(tmp + o_w), (double2*)(tmp + o_ud), st);
+    if (e == cudaSuccess && Ud)
+        e = cudaMemcpyAsync(Ud, tmp + o_ud, sizeof(double2) * full->n_u, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && Ebar) e = cudaMemcpyAsync(Ebar, tmp + o_eb, sizeof(double) * ne, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(tmp, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(MMF_ERR_CUDA, std::string("dressed basis: ") + cudaGetErrorString(e));
+    if (st != dress->stream) return order_after(c, dress->stream, st);
+    return MMF_OK;
+}
+
+extern "C" int mmf_dressed_time_evolution(mmf_sys* s, int ndress, const int* dressing, int precision, double t1,
+                                          int nt, const double* t2, double* Ud, double* Ebar) {
+    if (!s || nt < 1 || !t2) return fail(MMF_ERR_ARG, "sys, nt >= 1 and t2 required");
+    if (s->omega.empty()) return fail(MMF_ERR_ARG, "system has no drive mode");
+    mmf_sys* r = nullptr;
+    int rc = mmf_sys_restrict(s, ndress, dressing, &r);
+    if (rc != MMF_OK) return rc;
+    std::lock_guard<std::recursive_mutex> lk(s->ctx->mu);
+    mmf_batch *bd = nullptr, *bf = nullptr;
+    mmf_sys* a1[1] = {r};
+    mmf_sys* a2[1] = {s};
+    rc = mmf_batch_create(s->ctx, 1, a1, precision, 0, &bd);
+    if (rc == MMF_OK) rc = mmf_batch_run(bd);
+    if (rc == MMF_OK) rc = mmf_batch_create(s->ctx, 1, a2, precision, nt, &bf);
+    if (rc == MMF_OK) rc = mmf_batch_set_times(bf, t1, t2);
+    if (rc == MMF_OK) rc = mmf_batch_run(bf);
+    int st1 = 0, st2 = 0;
+    if (rc == MMF_OK) st1 = mmf_batch_sync(bd, nullptr);
+    if (rc == MMF_OK) st2 = mmf_batch_sync(bf, nullptr);
+    if (rc == MMF_OK && (st1 < 0 || st2 < 0)) rc = st1 < 0 ? st1 : st2;
+    if (rc == MMF_OK) rc = mmf_batch_dressed(bf, bd, Ud, Ebar);
+    if (bf) mmf_batch_destroy(bf);
+    if (bd) mmf_batch_destroy(bd);
+    mmf_sys_destroy(r);
+    if (rc != MMF_OK) return rc;
+    return std::max(st1, st2);
+}
+
 // ================================================================== serving (continuous batching)
 // A worker thread turns queued requests into batch plans on free slots (each slot = one CUDA
 // stream with at most one plan in flight), admitting a plan only while the context's HBM budget
-// has room for it.  Plans on different slots overlap on the device; a finished plan's results are
-// copied out, its memory goes back to the pool, and the slot takes the next requests at once.
+// has room for it.  A plan groups requests of the same number of times and the same size class
+// (the class of the oldest waiting request first), so a small request never waits for a large
+// system's solve.  Plans on different slots overlap on the device; a finished plan's results are
+// copied out and the slot takes the next requests at once.  Finished plans stay resident (device
+// memory, descriptors, staging) in a small per-server cache keyed by the systems' structure (levels,
+// modes, truncations, harmonics) and nt: a later group of the same structure reuses one by uploading
+// its own coefficients and times.  Cached plans are released, least recently used first, when a
+// new plan needs their memory.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -1238,7 +1582,26 @@ struct ServeReq {
     int status = 0;
     int64_t n = 0;
     int D = 0;
+    int bucket = 0;    // size class of n
+    std::string sig;   // structure of the system (what a plan's layout depends on)
     std::vector<double> E, U, P;
+};
+
+// size classes of the serving admission: Jacobi-size, small, medium, large
+int size_bucket(int64_t n) { return n <= 128 ? 0 : n <= 640 ? 1 : n <= 2500 ? 2 : 3; }
+
+std::string sys_signature(const mmf_sys* s) {
+    // the half-bandwidth decides the eigensolver path, so it is part of the layout
+    std::string k = std::to_string(s->D) + "b" + std::to_string(sys_band(s));
+    for (size_t l = 0; l < s->omega.size(); ++l)
+        k += "/" + std::to_string(s->N[l]) + "h" + std::to_string(s->V[l].size());
+    return k;
+}
+
+struct CachedPlan {
+    mmf_batch* b = nullptr;
+    std::string sig;
+    uint64_t last_use = 0;
 };
 
 struct Slot {
@@ -1280,7 +1643,50 @@ struct mmf_server {
     std::vector<double> lat_ms;
     int64_t completed = 0, solves_started = 0;
     int last_error = 0;
+    // resident plans (worker thread only) and the idle stream they are parked on
+    std::vector<CachedPlan> cache;
+    size_t cache_cap = 8;
+    uint64_t use_clock = 0;
+    cudaStream_t park = nullptr;
+    int64_t plans_created = 0, plans_reused = 0;
 };
+
+static std::string plan_signature(const std::vector<ServeReq*>& g) {
+    std::string k = std::to_string(g[0]->nt);
+    for (const ServeReq* r : g) k += "|" + r->sig;
+    return k;
+}
+
+// Park a finished plan in the cache (evicting the least recently used beyond the cap).
+static void cache_put(mmf_server* sv, mmf_batch* b, const std::string& sig) {
+    b->stream = sv->park;  // nothing of it is in flight; later releases wait on an idle stream
+    sv->cache.push_back({b, sig, ++sv->use_clock});
+    while (sv->cache.size() > sv->cache_cap) {
+        auto it = std::min_element(sv->cache.begin(), sv->cache.end(),
+                                   [](const CachedPlan& a, const CachedPlan& q) { return a.last_use < q.last_use; });
+        mmf_batch_destroy(it->b);
+        sv->cache.erase(it);
+    }
+}
+
+static mmf_batch* cache_take(mmf_server* sv, const std::string& sig) {
+    for (auto it = sv->cache.begin(); it != sv->cache.end(); ++it)
+        if (it->sig == sig) {
+            mmf_batch* b = it->b;
+            sv->cache.erase(it);
+            return b;
+        }
+    return nullptr;
+}
+
+static bool cache_evict_one(mmf_server* sv) {
+    if (sv->cache.empty()) return false;
+    auto it = std::min_element(sv->cache.begin(), sv->cache.end(),
+                               [](const CachedPlan& a, const CachedPlan& q) { return a.last_use < q.last_use; });
+    mmf_batch_destroy(it->b);
+    sv->cache.erase(it);
+    return true;
+}
 
 static mmf_sys* copy_sys(const mmf_sys* s) {
     mmf_sys* c = new (std::nothrow) mmf_sys();
@@ -1314,32 +1720,50 @@ static void serve_finish(mmf_server* sv, Slot& sl) {
             sv->completed++;
         }
     }
-    mmf_batch_destroy(b);
+    cache_put(sv, b, plan_signature(sl.reqs));
     sl.b = nullptr;
     sl.reqs.clear();
     sv->cv.notify_all();
 }
 
-// Start a plan for up to max_batch queued requests (same nt) on a free slot.  Returns true if it
-// started one.
+// Start a plan for up to max_batch queued requests (same nt and size class as the oldest one) on
+// a free slot, reusing a resident plan of the same structure when there is one.  Returns true if
+// it started one.
 static bool serve_admit(mmf_server* sv, Slot& sl) {
     std::vector<ServeReq*> group;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         if (sv->pending.empty()) return false;
-        const int nt = sv->pending.front()->nt;
+        const int nt = sv->pending.front()->nt, bucket = sv->pending.front()->bucket;
         for (auto it = sv->pending.begin(); it != sv->pending.end() && (int)group.size() < sv->max_batch; ++it)
-            if ((*it)->nt == nt) group.push_back(*it);
+            if ((*it)->nt == nt && (*it)->bucket == bucket) group.push_back(*it);
     }
     while (!group.empty()) {
         std::vector<mmf_sys*> sys;
         for (ServeReq* r : group) sys.push_back(r->sys);
-        mmf_batch* b = nullptr;
-        int rc = batch_create(sv->ctx, (int)sys.size(), sys.data(), sv->precision, group[0]->nt, sl.stream,
+        int rc = MMF_OK;
+        mmf_batch* b = cache_take(sv, plan_signature(group));
+        if (b) {  // same layout: new coefficients into the resident plan
+            b->stream = sl.stream;
+            b->sys = sys;
+            fill_coef(b, b->h_coef);
+            for (int i = 0; i < b->count; ++i)  // the frequencies are values, not structure
+                for (int k = 0; k < b->desc[i].K; ++k) b->desc[i].omega[k] = sys[i]->omega[k];
+            cudaError_t e = cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(MmfDesc) * b->count,
+                                            cudaMemcpyHostToDevice, sl.stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(b->d_coef, b->h_coef, sizeof(double2) * b->n_coef, cudaMemcpyHostToDevice,
+                                    sl.stream);
+            if (e != cudaSuccess) rc = fail(MMF_ERR_CUDA, std::string("plan reuse: ") + cudaGetErrorString(e));
+            sv->plans_reused++;
+        } else {
+            rc = batch_create(sv->ctx, (int)sys.size(), sys.data(), sv->precision, group[0]->nt, sl.stream,
                               false, &b);
-        if (rc == MMF_ERR_BUDGET) {  // admit fewer, or wait for memory to come back
-            group.pop_back();
-            continue;
+            if (rc == MMF_ERR_BUDGET) {  // release resident plans, else admit fewer or wait for memory
+                if (!cache_evict_one(sv)) group.pop_back();
+                continue;
+            }
+            if (rc == MMF_OK) sv->plans_created++;
         }
         if (rc != MMF_OK) {
             std::lock_guard<std::mutex> lk(sv->mu);
@@ -1426,6 +1850,11 @@ extern "C" int mmf_serve_create(mmf_ctx* ctx, int slots, int max_batch, int prec
     sv->precision = precision;
     sv->max_batch = max_batch;
     sv->slots.resize(slots);
+    sv->cache_cap = (size_t)std::max(4, 2 * slots);
+    if (cudaStreamCreateWithFlags(&sv->park, cudaStreamNonBlocking) != cudaSuccess) {
+        delete sv;
+        return fail(MMF_ERR_CUDA, "server stream");
+    }
     for (Slot& sl : sv->slots) {
         cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
@@ -1434,6 +1863,7 @@ extern "C" int mmf_serve_create(mmf_ctx* ctx, int slots, int max_batch, int prec
                 if (q.stream) cudaStreamDestroy(q.stream);
                 if (q.done) cudaEventDestroy(q.done);
             }
+            cudaStreamDestroy(sv->park);
             delete sv;
             return fail(MMF_ERR_CUDA, cudaGetErrorString(e));
         }
@@ -1457,6 +1887,8 @@ extern "C" int mmf_serve_submit(mmf_server* sv, const mmf_sys* sys, int nt, cons
     r->t0 = t0;
     r->n = sys_dim(sys);
     r->D = sys->D;
+    r->bucket = size_bucket(r->n);
+    r->sig = sys_signature(sys);
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
@@ -1521,6 +1953,15 @@ extern "C" int mmf_serve_stats(mmf_server* sv, double* p50_ms, double* p99_ms, d
     return MMF_OK;
 }
 
+extern "C" int mmf_serve_plan_stats(mmf_server* sv, int64_t* created, int64_t* reused, int64_t* resident) {
+    if (!sv) return fail(MMF_ERR_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (created) *created = sv->plans_created;
+    if (reused) *reused = sv->plans_reused;
+    if (resident) *resident = (int64_t)sv->cache.size();
+    return MMF_OK;
+}
+
 extern "C" int mmf_serve_reset_stats(mmf_server* sv) {
     if (!sv) return fail(MMF_ERR_ARG, "server is NULL");
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -1546,6 +1987,9 @@ extern "C" int mmf_serve_destroy(mmf_server* sv) {
         mmf_sys_destroy(kv.second->sys);
         delete kv.second;
     }
+    for (CachedPlan& cp : sv->cache) mmf_batch_destroy(cp.b);
+    sv->cache.clear();
+    if (sv->park) cudaStreamDestroy(sv->park);
     for (Slot& sl : sv->slots) {
         cudaStreamDestroy(sl.stream);
         cudaEventDestroy(sl.done);

@@ -14,6 +14,7 @@ struct MmfDesc {
     int32_t D, K, M, n;                 // levels, modes, Fourier blocks, n = D * M
     int32_t ld, b0, small, pat_cap;     // leading dim, central block index, Jacobi flag,
                                         // nonzeros kept per coefficient row (0: dense rows)
+    int32_t band, pad0;                 // half-bandwidth when reduced by the bulge chase (0: dense)
     int32_t N[MMF_MAX_MODES];           // truncation |n_k| <= N_k
     int32_t nharm[MMF_MAX_MODES];       // harmonics per mode (couplings V^{k,1..nharm})
     int32_t S[MMF_MAX_MODES];           // block strides, S_0 = 1, S_k = prod_{k'<k}(2N_k'+1)
@@ -219,6 +220,20 @@ cudaError_t mmf_launch_outputs(const MmfLaunch& L, int Mmax, int Dmax, const dou
                                double2* F, double2* U, double* P, double cluster_rel, int skip_u,
                                void* scratch, int scratch_esz);
 int mmf_hetrd_max_n(int fp32);
+// banded H_F (k_sbr.cu): bulge chase to real tridiagonal form (d, e; reflectors kept in the
+// system's FP64 eigenvector slot), then Z = Q Y into the back-transform's output (Zp)
+int mmf_sbr_class(int band);                 // window class 8/16/32/64, 0 if the band is wider
+int64_t mmf_sbr_store_elems(int n, int band);  // complex elements of the reflector store
+cudaError_t mmf_launch_sbr_chase(const MmfLaunch& L, int bmax, void* H, double2* store, double* dvec, double* evec,
+                                 int* status, int fp32);
+cudaError_t mmf_launch_sbr_bt(const MmfLaunch& L, int bmax, const double2* store, const double* Y, double* work,
+                              void* Zout, int fp32);
+// dressed basis (k_dressed.cu): zone representatives of the dressing batch, U_F at t1 and the
+// full batch's times, and Ud = U_F(t2)^dagger U(t2, t1) U_F(t1) per time
+cudaError_t mmf_launch_dressed(const MmfDesc* ddesc, const MmfDesc* fdesc, int count, int nmax_d, int Dmax,
+                               const double2* Zd, const double* Ed, const double2* U, const double* t, double t1,
+                               int nt, const int64_t* roff, const int64_t* ufoff, int64_t* reps, double* Ebar,
+                               double2* UF, double2* Wt, double2* Ud, cudaStream_t st);
 cudaError_t mmf_launch_hetrd_large(const MmfDesc& d, void* H, void* Vp, void* Wp, double* dvec, double* evec,
                                    void* tau, void* work, void* sc, int fp32, cudaStream_t st);
 cudaError_t mmf_launch_micromotion(const MmfLaunch& L, int D, const double2* Z, const double* t,

@@ -40,6 +40,12 @@ MMF_OPT_LARGE_N = 3
 MMF_OPT_REFINE_FULL_N = 4
 MMF_OPT_GRAM_KERNEL = 5
 MMF_OPT_BT_TC_N = 6
+MMF_OPT_JACOBI_SWEEPS = 7
+MMF_OPT_BAND_MAX = 8
+MMF_PATH_JACOBI = 0
+MMF_PATH_DENSE = 1
+MMF_PATH_WHOLE_GPU = 2
+MMF_PATH_BAND = 3
 
 _lib = None
 _exiting = False
@@ -98,12 +104,23 @@ _SIGS = {
     "mmf_batch_results": (_I, [_P, _P, _P, _P]),
     "mmf_batch_offset": (_I64, [_P, _I, _I]),
     "mmf_batch_size": (_I64, [_P, _I]),
+    "mmf_batch_path": (_I, [_P, _I, ctypes.POINTER(_I)]),
     "mmf_batch_bytes": (_SZ, [_P]),
     "mmf_batch_timing": (_I, [_P, _I]),
     "mmf_batch_graph": (_I, [_P, _I]),
     "mmf_batch_stage_ms": (_I, [_P, _P, _P]),
     "mmf_batch_destroy": (_I, [_P]),
-    "mmf_tridiag_eig_noalloc": (_I, [_P, _P, _I, _P, _P, _P]),
+    "mmf_quasienergies_dev": (_I, [_P, _P, _P]),
+    "mmf_eigenvectors_dev": (_I, [_P, _P, _P]),
+    "mmf_time_evolution_dev": (_I, [_P, _D, _I, _P, _P, _P]),
+    "mmf_transition_avg_dev": (_I, [_P, _P, _P]),
+    "mmf_batch_results_dev": (_I, [_P, _P, _P, _P, _P]),
+    "mmf_sys_restrict": (_I, [_P, _I, _P, _PP]),
+    "mmf_batch_dressed": (_I, [_P, _P, _P, _P]),
+    "mmf_batch_dressed_size": (_I64, [_P, _I]),
+    "mmf_batch_dressed_offset": (_I64, [_P, _I, _I]),
+    "mmf_dressed_time_evolution": (_I, [_P, _I, _P, _I, _D, _I, _P, _P, _P]),
+    "mmf_tridiag_eig_noalloc": (_I, [_P, _P, _I, _P, _P, _P, _P]),
     "mmf_serve_create": (_I, [_P, _I, _I, _I, _PP]),
     "mmf_serve_submit": (_I, [_P, _P, _I, _P, _D, ctypes.POINTER(ctypes.c_uint64)]),
     "mmf_serve_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(_I)]),
@@ -111,6 +128,7 @@ _SIGS = {
     "mmf_serve_stats": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
                              ctypes.POINTER(_I64)]),
     "mmf_serve_reset_stats": (_I, [_P]),
+    "mmf_serve_plan_stats": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "mmf_serve_destroy": (_I, [_P]),
     "mmf_selftest_tensor_cores": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "mmf_selftest_gram": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -175,12 +193,31 @@ def spin_components(S2: int, A, phi=(0.0, 0.0, 0.0), static: bool = False) -> np
 
 
 class Context:
-    """A CUDA device + stream binding with an HBM budget (mmf_ctx_*)."""
+    """A CUDA device + stream binding with an HBM budget (mmf_ctx_*).
+
+    Systems, batches and servers made on a context count as its dependents: the C context is
+    destroyed only once the context is closed and every dependent has been closed, whatever the
+    order in which Python finalises them."""
 
     def __init__(self, device: int = 0, budget: int = 0, stream: Optional[int] = None):
         h = ctypes.c_void_p()
         _check(lib().mmf_ctx_create(device, budget, stream, ctypes.byref(h)))
         self.h = h
+        self._live = 0
+        self._closing = False
+
+    def _acquire(self):
+        self._live += 1
+
+    def _release(self):
+        self._live -= 1
+        if self._closing and self._live <= 0:
+            self._destroy()
+
+    def _destroy(self):
+        if self.h and not _exiting:
+            lib().mmf_ctx_destroy(self.h)
+        self.h = None
 
     def bytes_in_use(self) -> int:
         return int(lib().mmf_ctx_bytes_in_use(self.h))
@@ -192,9 +229,9 @@ class Context:
         return int(lib().mmf_ctx_budget(self.h))
 
     def close(self):
-        if self.h and not _exiting:
-            lib().mmf_ctx_destroy(self.h)
-        self.h = None
+        self._closing = True
+        if self._live <= 0:
+            self._destroy()
 
     def __del__(self):
         try:
@@ -209,11 +246,13 @@ class System:
 
     def __init__(self, ctx: Context, problem):
         self.ctx = ctx
+        self.h = None
         self.D = int(problem.D)
         h = ctypes.c_void_p()
         H0 = _cplx(problem.H0)
         _check(lib().mmf_sys_create(ctx.h, self.D, _ptr(H0), ctypes.byref(h)))
         self.h = h
+        ctx._acquire()
         for l, (w, N) in enumerate(zip(problem.omegas, problem.Ns)):
             mid = ctypes.c_int(-1)
             _check(lib().mmf_add_mode(self.h, float(w), int(N), ctypes.byref(mid)))
@@ -262,6 +301,42 @@ class System:
         _check(lib().mmf_micromotion(self.h, int(t.size), _ptr(t), _ptr(UF), _ptr(reps)))
         return UF, reps
 
+    # device-pointer variants: dst and t are device addresses (e.g. tensor.data_ptr()), stream a
+    # cudaStream_t handle (e.g. torch.cuda.current_stream().cuda_stream)
+    def quasienergies_dev(self, dst: int, stream: int):
+        _check(lib().mmf_quasienergies_dev(self.h, dst, stream))
+
+    def eigenvectors_dev(self, dst: int, stream: int):
+        _check(lib().mmf_eigenvectors_dev(self.h, dst, stream))
+
+    def time_evolution_dev(self, t0: float, nt: int, t: int, dst: int, stream: int):
+        _check(lib().mmf_time_evolution_dev(self.h, float(t0), int(nt), t, dst, stream))
+
+    def transition_avg_dev(self, dst: int, stream: int):
+        _check(lib().mmf_transition_avg_dev(self.h, dst, stream))
+
+    def restrict(self, modes) -> "System":
+        """The same system driven by the listed modes only (Sec. 3.3's dressing modes)."""
+        m = np.ascontiguousarray(np.asarray(modes, dtype=np.int32))
+        h = ctypes.c_void_p()
+        _check(lib().mmf_sys_restrict(self.h, int(m.size), _ptr(m), ctypes.byref(h)))
+        r = System.__new__(System)
+        r.ctx, r.D, r.h = self.ctx, self.D, h
+        self.ctx._acquire()
+        r.n = int(lib().mmf_dim(h))
+        return r
+
+    def dressed_time_evolution(self, dressing, t1: float, t2, precision: int = MMF_FP64):
+        """Ud[k] = U_F(t2_k)^dagger U(t2_k, t1) U_F(t1) in the basis dressed by `dressing` (mode
+        indices), and the dressed quasienergies Ebar."""
+        m = np.ascontiguousarray(np.asarray(dressing, dtype=np.int32))
+        t2 = np.ascontiguousarray(np.atleast_1d(np.asarray(t2, dtype=np.float64)))
+        Ud = np.zeros((t2.size, self.D, self.D), dtype=np.complex128)
+        Eb = np.zeros(self.D)
+        _check(lib().mmf_dressed_time_evolution(self.h, int(m.size), _ptr(m), precision, float(t1), int(t2.size),
+                                                _ptr(t2), _ptr(Ud), _ptr(Eb)), allow_numeric=True)
+        return Ud, Eb
+
     def time_evolution_operator(self, t, t0: float = 0.0, precision: int = MMF_FP64) -> np.ndarray:
         t = np.ascontiguousarray(np.atleast_1d(np.asarray(t, dtype=np.float64)))
         U = np.zeros((t.size, self.D, self.D), dtype=np.complex128)
@@ -270,9 +345,11 @@ class System:
         return U
 
     def close(self):
-        if self.h and not _exiting:
-            lib().mmf_sys_destroy(self.h)
-        self.h = None
+        if self.h:
+            if not _exiting:
+                lib().mmf_sys_destroy(self.h)
+            self.h = None
+            self.ctx._release()
 
     def __del__(self):
         try:
@@ -292,9 +369,11 @@ class Batch:
         self.precision = precision
         arr = (ctypes.c_void_p * self.count)(*[s.h.value for s in self.systems])
         h = ctypes.c_void_p()
+        self.h = None
         _check(lib().mmf_batch_create(ctx.h, self.count, ctypes.cast(arr, ctypes.c_void_p), precision,
                                       self.nt, ctypes.byref(h)))
         self.h = h
+        ctx._acquire()
         self.nE = int(lib().mmf_batch_size(self.h, 0))
         self.nU = int(lib().mmf_batch_size(self.h, 1))
         self.nP = int(lib().mmf_batch_size(self.h, 2))
@@ -340,6 +419,34 @@ class Batch:
         _check(lib().mmf_batch_results(self.h, _ptr(E), _ptr(U), _ptr(P)))
         return E, U, P
 
+    def dressed(self, dress: "Batch"):
+        """Sec. 3.3 for every system: this batch is the full systems (times t2, start t1 = t0 of
+        set_times), `dress` the same systems restricted to their dressing modes; both run.
+        Returns per system (Ud (nt x D x D), Ebar (D))."""
+        nu = int(lib().mmf_batch_dressed_size(self.h, 0))
+        ne = int(lib().mmf_batch_dressed_size(self.h, 1))
+        Ud = np.zeros(max(nu, 1), dtype=np.complex128)
+        Eb = np.zeros(max(ne, 1))
+        _check(lib().mmf_batch_dressed(self.h, dress.h, _ptr(Ud), _ptr(Eb)))
+        out = []
+        for i, s in enumerate(self.systems):
+            ou = int(lib().mmf_batch_dressed_offset(self.h, 0, i))
+            oe = int(lib().mmf_batch_dressed_offset(self.h, 1, i))
+            out.append((Ud[ou:ou + self.nt * s.D * s.D].reshape(self.nt, s.D, s.D), Eb[oe:oe + s.D].copy()))
+        return out
+
+    def path(self, i: int):
+        """(MMF_PATH_* of system i, half-bandwidth used by the band path or 0)."""
+        band = ctypes.c_int(0)
+        rc = lib().mmf_batch_path(self.h, int(i), ctypes.byref(band))
+        if rc < 0:
+            _check(rc)
+        return rc, band.value
+
+    def results_dev(self, E: int, U: int, P: int, stream: int):
+        """Packed results into device buffers (addresses) on the given stream."""
+        _check(lib().mmf_batch_results_dev(self.h, E, U, P, stream))
+
     def unpack(self, E, U, P, i: int):
         s = self.systems[i]
         e = E[self.offE[i]:self.offE[i] + s.n]
@@ -366,9 +473,11 @@ class Batch:
         return int(lib().mmf_batch_bytes(self.h))
 
     def close(self):
-        if self.h and not _exiting:
-            lib().mmf_batch_destroy(self.h)
-        self.h = None
+        if self.h:
+            if not _exiting:
+                lib().mmf_batch_destroy(self.h)
+            self.h = None
+            self.ctx._release()
 
     def __del__(self):
         try:
@@ -383,8 +492,10 @@ class Server:
     def __init__(self, ctx: Context, slots: int = 4, max_batch: int = 16, precision: int = MMF_MIXED):
         self.ctx = ctx
         h = ctypes.c_void_p()
+        self.h = None
         _check(lib().mmf_serve_create(ctx.h, slots, max_batch, precision, ctypes.byref(h)))
         self.h = h
+        ctx._acquire()
         self._shape = {}
 
     def submit(self, system: System, t, t0: float = 0.0) -> int:
@@ -400,13 +511,16 @@ class Server:
         return bool(d.value)
 
     def wait(self, ticket: int, timeout_ms: int = -1):
-        n, D, nt = self._shape.pop(ticket)
+        n, D, nt = self._shape[ticket]
         E = np.zeros(n)
         U = np.zeros((nt, D, D), dtype=np.complex128)
         P = np.zeros((D, D))
         st = ctypes.c_int(0)
-        _check(lib().mmf_serve_wait(self.h, ticket, timeout_ms, _ptr(E), _ptr(U) if nt else None, _ptr(P),
-                                    ctypes.byref(st)))
+        rc = lib().mmf_serve_wait(self.h, ticket, timeout_ms, _ptr(E), _ptr(U) if nt else None, _ptr(P),
+                                  ctypes.byref(st))
+        if rc != MMF_ERR_STATE:  # anything but a time-out releases the request
+            self._shape.pop(ticket, None)
+        _check(rc)
         return E, U, P, int(st.value)
 
     def stats(self):
@@ -419,10 +533,17 @@ class Server:
     def reset_stats(self):
         _check(lib().mmf_serve_reset_stats(self.h))
 
+    def plan_stats(self):
+        c, r, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().mmf_serve_plan_stats(self.h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(k)))
+        return {"created": c.value, "reused": r.value, "resident": k.value}
+
     def close(self):
-        if self.h and not _exiting:
-            lib().mmf_serve_destroy(self.h)
-        self.h = None
+        if self.h:
+            if not _exiting:
+                lib().mmf_serve_destroy(self.h)
+            self.h = None
+            self.ctx._release()
 
     def __del__(self):
         try:

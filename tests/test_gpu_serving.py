@@ -72,9 +72,35 @@ def test_admission_waits_for_budget():
     assert ctx.bytes_in_use() == 0
 
 
-def test_wait_timeout_and_unknown_ticket():
+@pytest.mark.parametrize("precision", [M.MMF_MIXED, M.MMF_FP64])
+def test_resident_plan_reused_with_new_values(precision):
+    """Requests of one structure but different frequencies and couplings, one after another: the
+    second and third reuse the first plan (new coefficients and frequencies uploaded into it), and
+    each result equals the same system solved alone."""
+    ctx = M.Context(0)
+    srv = M.Server(ctx, slots=1, max_batch=1, precision=precision)
+    nt = 8
+    ps = [W.spin1_bichromatic(a, b, N1=5, N2=4) for a, b in ((0.3, 0.2), (0.1, 0.45))]
+    ps[1].omegas = [1.07, 0.55]
+    ps.append(W.two_level(0.9, N=20))
+    ps.append(W.two_level(1.3, N=20))
+    e_rel, up = (1e-9, 1e-8) if precision == M.MMF_MIXED else (1e-12, 1e-10)
+    for p in ps:
+        E, U, P, st = srv.wait(srv.submit(M.System(ctx, p), W.time_grid(p, nt)), timeout_ms=120000)
+        assert st == 0
+        E1, U1, P1 = _alone(ctx, p, precision, nt)
+        assert np.abs(E - E1).max() <= e_rel * np.abs(E1).max()
+        assert np.abs(U - U1).max() <= up and np.abs(P - P1).max() <= up
+    ps_ = srv.plan_stats()
+    assert ps_["created"] == 2 and ps_["reused"] == 2, ps_
+    srv.close()
+    assert ctx.bytes_in_use() == 0
+
+
+def test_unknown_ticket():
     ctx = M.Context(0)
     srv = M.Server(ctx, slots=1, max_batch=1, precision=M.MMF_FP64)
-    with pytest.raises(M.MmfError):
+    with pytest.raises(M.MmfError) as ei:
         srv.poll(12345)
+    assert ei.value.code == M.MMF_ERR_ARG
     srv.close()
