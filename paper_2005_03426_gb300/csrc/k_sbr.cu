@@ -134,11 +134,11 @@ __device__ __forceinline__ void make_reflector(C alpha, R xn2, C& tau, R& beta, 
 // triangle is written to global memory at Hg (column-major, ld) from row/column r.
 template <class R, class C, int BMAX, int G, int P>
 __device__ __forceinline__ void sbr_two_sided(SbrGroup<C, BMAX, P>& S, const C* v, C tau, int l, C* __restrict__ Hg,
-                                              int64_t ld, int r, int tid, int g, double* dout) {
+                                              int ld, int r, int tid, int g, double* dout) {
     const int i = tid % BMAX, p = tid / BMAX;
     C acc = mk(R(0), R(0));
-#pragma unroll 4
-    for (int k = p; k < BMAX; k += P) acc = acc + S.Dm[i][k] * v[k];
+#pragma unroll
+    for (int q = 0; q < BMAX / P; ++q) acc = acc + S.Dm[i][p + q * P] * v[p + q * P];
     S.red[p][i] = acc;
     gbar<G>(g);
     R a_part = R(0);
@@ -156,7 +156,9 @@ __device__ __forceinline__ void sbr_two_sided(SbrGroup<C, BMAX, P>& S, const C* 
     gbar<G>(g);
     // lower triangle, column by column (rows i >= k contiguous in global memory)
     const C vi = v[i], wi = S.w[i];
-    for (int k = p; k < l; k += P) {
+#pragma unroll
+    for (int q = 0; q < BMAX / P; ++q) {
+        const int k = p + q * P;
         if (i >= k && i < l) {
             const C vk = v[k], wk = S.w[k];
             C a0 = S.Dm[i][k];
@@ -165,7 +167,7 @@ __device__ __forceinline__ void sbr_two_sided(SbrGroup<C, BMAX, P>& S, const C* 
                 a0.y = R(0);
                 if (dout && i == 0) *dout = (double)a0.x;
             }
-            Hg[(int64_t)(r + k) * ld + r + i] = a0;
+            Hg[(r + k) * ld + r + i] = a0;
         }
     }
 }
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__
     const int sid = idx[blockIdx.x];
     const MmfDesc d = descs[sid];
     const int n = d.n, b = d.band;
-    const int64_t ld = d.ld;
+    const int ldi = d.ld;  // in-system offsets fit 32 bits (n ld < 2^31, checked by the host)
     C* Hg = Hbase + d.mat_off;
     // the store lives in the system's FP64 complex matrix slot
     C* V = reinterpret_cast<C*>(store_base + (sizeof(R) == 4 ? 2 : 1) * d.mat_off);
@@ -238,15 +240,20 @@ __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__
                 // column j below the diagonal and the diagonal block, lower triangle
                 // all of the step's loads in flight at once (asynchronous copies, zero-filled
                 // outside the l x l block)
-                if (tid < BMAX) cp_elem(&vc[tid], Hg + (int64_t)j * ld + r + (tid < l ? tid : 0), tid < l);
-                for (int k = p; k < BMAX; k += P) {
+                if (tid < BMAX) cp_elem(&vc[tid], Hg + j * ldi + r + (tid < l ? tid : 0), tid < l);
+#pragma unroll
+                for (int q = 0; q < BMAX / P; ++q) {
+                    const int k = p + q * P;
                     const bool ok = i < l && k < l && i >= k;
-                    cp_elem(&S.Dm[i][k], Hg + (ok ? (int64_t)(r + k) * ld + r + i : 0), ok);
+                    cp_elem(&S.Dm[i][k], Hg + (ok ? (r + k) * ldi + r + i : 0), ok);
                 }
                 cp_wait_all();
                 gbar<G>(g);
-                for (int k = p; k < BMAX; k += P)
+#pragma unroll
+                for (int q = 0; q < BMAX / P; ++q) {
+                    const int k = p + q * P;
                     if (i < k) S.Dm[i][k] = conj(S.Dm[k][i]);
+                }
                 const C alpha = vc[0];
                 const R xn2 = group_sum<G, R>((tid >= 1 && tid < l) ? abs2(vc[tid]) : R(0), S.rs, tid, g);
                 R beta;
@@ -255,7 +262,7 @@ __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__
                 if (tid < BMAX) {
                     const C x = vc[tid];
                     vc[tid] = tid == 0 ? mk(R(1), R(0)) : ((tid < l) ? x * scale : mk(R(0), R(0)));
-                    if (tid < l) Hg[(int64_t)j * ld + r + tid] = tid == 0 ? mk(beta, R(0)) : mk(R(0), R(0));
+                    if (tid < l) Hg[j * ldi + r + tid] = tid == 0 ? mk(beta, R(0)) : mk(R(0), R(0));
                 }
                 if (tid == 0) {
                     ee[j] = (double)beta;
@@ -265,79 +272,88 @@ __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__
                 const int rp = r - b;
                 const int lp = min(b, n - rp);
                 const C taup = S.tau[cur ^ 1];
-                for (int k = p; k < BMAX; k += P) {
+#pragma unroll
+                for (int q = 0; q < BMAX / P; ++q) {
+                    const int k = p + q * P;
                     const bool okb = i < l && k < lp, okd = i < l && k < l && i >= k;
-                    cp_elem(&S.B[i][k], Hg + (okb ? (int64_t)(rp + k) * ld + r + i : 0), okb);
-                    cp_elem(&S.Dm[i][k], Hg + (okd ? (int64_t)(r + k) * ld + r + i : 0), okd);
+                    cp_elem(&S.B[i][k], Hg + (okb ? (rp + k) * ldi + r + i : 0), okb);
+                    cp_elem(&S.Dm[i][k], Hg + (okd ? (r + k) * ldi + r + i : 0), okd);
                 }
                 cp_wait_all();
                 gbar<G>(g);
-                for (int k = p; k < BMAX; k += P)
+#pragma unroll
+                for (int q = 0; q < BMAX / P; ++q) {
+                    const int k = p + q * P;
                     if (i < k) S.Dm[i][k] = conj(S.Dm[k][i]);
-                // (a) B <- B H(j, s-1) = B - tau_p (B v_p) v_p^H
+                }
+                // The previous reflector from the right and the new one from the left, as one rank-2
+                // update: with C1 = B H(j,s-1) = B - tau_p y v_p^H (y = B v_p), x = C1(:, 0) gives
+                // H(j,s); then H^H C1 = B - tau_p y v_p^H - conj(tau) v r with
+                // r_k = (v^H B)_k - tau_p (v^H y) conj(v_p,k).
                 C acc = mk(R(0), R(0));
-#pragma unroll 4
-                for (int k = p; k < BMAX; k += P) acc = acc + S.B[i][k] * vp[k];
+#pragma unroll
+                for (int q = 0; q < BMAX / P; ++q) acc = acc + S.B[i][p + q * P] * vp[p + q * P];
                 S.red[p][i] = acc;
                 gbar<G>(g);
                 if (tid < BMAX) {
                     C yy = S.red[0][tid];
 #pragma unroll
                     for (int q = 1; q < P; ++q) yy = yy + S.red[q][tid];
-                    S.y[tid] = taup * yy;
+                    const C ty = taup * yy;
+                    S.y[tid] = ty;                      // tau_p y
+                    S.w[tid] = S.B[tid][0] - ty;        // x = C1(:, 0)   (v_p[0] = 1)
                 }
                 gbar<G>(g);
-                {
-                    const C ty = S.y[i];
-                    for (int k = p; k < BMAX; k += P) S.B[i][k] = S.B[i][k] - ty * conj(vp[k]);
-                }
-                gbar<G>(g);
-                // (b) reflector from B's first column
-                const C alpha = S.B[0][0];
-                const R xn2 = group_sum<G, R>((tid >= 1 && tid < l) ? abs2(S.B[tid][0]) : R(0), S.rs, tid, g);
+                const C alpha = S.w[0];
+                const R xn2 = group_sum<G, R>((tid >= 1 && tid < l) ? abs2(S.w[tid]) : R(0), S.rs, tid, g);
                 R beta;
                 C scale;
                 make_reflector<R, C>(alpha, xn2, tau, beta, scale);
                 if (tid < BMAX) {
-                    const C x = S.B[tid][0];
+                    const C x = S.w[tid];
                     vc[tid] = tid == 0 ? mk(R(1), R(0)) : ((tid < l) ? x * scale : mk(R(0), R(0)));
                 }
                 if (tid == 0) S.tau[cur] = tau;
                 gbar<G>(g);
-                if (tid < BMAX) S.B[tid][0] = tid == 0 ? mk(beta, R(0)) : mk(R(0), R(0));
-                // (c) B(:, 1:) <- H^H B(:, 1:) = B - conj(tau) v (v^H B)
+                // u_k = sum_i conj(v_i) B(i, k) and gamma = v^H (tau_p y)
                 {
                     const int kc = tid % BMAX, pc = tid / BMAX;
                     C z = mk(R(0), R(0));
-                    if (kc >= 1) {
-#pragma unroll 4
-                        for (int q = pc; q < BMAX; q += P) z = z + cmulc(vc[q], S.B[q][kc]);
-                    }
+#pragma unroll
+                    for (int q = 0; q < BMAX / P; ++q) z = z + cmulc(vc[pc + q * P], S.B[pc + q * P][kc]);
                     S.red[pc][kc] = z;
                 }
                 gbar<G>(g);
+                const R gre = group_sum<G, R>(tid < BMAX ? vc[tid].x * S.y[tid].x + vc[tid].y * S.y[tid].y : R(0),
+                                              S.rs, tid, g);
+                const R gim = group_sum<G, R>(tid < BMAX ? vc[tid].x * S.y[tid].y - vc[tid].y * S.y[tid].x : R(0),
+                                              S.rs, tid, g);
                 if (tid < BMAX) {
-                    C zz = S.red[0][tid];
+                    C u = S.red[0][tid];
 #pragma unroll
-                    for (int q = 1; q < P; ++q) zz = zz + S.red[q][tid];
-                    S.w[tid] = conj(tau) * zz;
+                    for (int q = 1; q < P; ++q) u = u + S.red[q][tid];
+                    // r_k = u_k - gamma conj(v_p,k), gamma = v^H (tau_p y); stored conj(tau) r_k
+                    const C rk = u - mk(gre, gim) * conj(vp[tid]);
+                    S.w[tid] = conj(tau) * rk;
                 }
                 gbar<G>(g);
                 {
-                    const C vi = vc[i];
-                    for (int k = p; k < BMAX; k += P)
-                        if (k >= 1) S.B[i][k] = S.B[i][k] - vi * S.w[k];
+                    const C ty = S.y[i], vi = vc[i];
+#pragma unroll
+                    for (int q = 0; q < BMAX / P; ++q) {
+                        const int k = p + q * P;
+                        C bk = S.B[i][k] - ty * conj(vp[k]) - vi * S.w[k];
+                        if (k == 0) bk = i == 0 ? mk(beta, R(0)) : mk(R(0), R(0));
+                        if (i < l && k < lp) Hg[(rp + k) * ldi + r + i] = bk;
+                    }
                 }
-                gbar<G>(g);
-                for (int k = p; k < lp; k += P)
-                    if (i < l) Hg[(int64_t)(rp + k) * ld + r + i] = S.B[i][k];
             }
             // store the reflector for the back-transform
             if (tid < b) V[(sbr_off(n, b, s) + j) * b + tid] = vc[tid];
             if (tid == 0) T[sbr_off(n, b, s) + j] = tau;
             gbar<G>(g);
             // (d) diagonal block A(R_s, R_s) <- H^H A H
-            sbr_two_sided<R, C, BMAX, G, P>(S, vc, tau, l, Hg, ld, r, tid, g, s == 0 ? dd + j + 1 : nullptr);
+            sbr_two_sided<R, C, BMAX, G, P>(S, vc, tau, l, Hg, ldi, r, tid, g, s == 0 ? dd + j + 1 : nullptr);
             cur ^= 1;
             __threadfence_block();
             gbar<G>(g);
