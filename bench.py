@@ -415,6 +415,9 @@ def main():
     ap.add_argument("--ref-systems", type=int, default=0,
                     help="reference arm / CPU baseline: systems per wave (default: one per host core)")
     ap.add_argument("--ref-max-steps", type=int, default=2)
+    ap.add_argument("--tuning", default=os.path.join(ROOT, "paper_2005_03426_gb300", "tuning_gb300.txt"),
+                    help="tuning table of the solver paths (written by paper_2005_03426_gb300/tune.py)")
+    ap.add_argument("--no-tuning", action="store_true")
     ap.add_argument("--band-max", type=int, default=-1,
                     help="widest band reduced by the bulge chase (library option; 0: dense reduction only)")
     args = ap.parse_args()
@@ -460,6 +463,9 @@ def main():
     total_count = int(round(sum_over_ranks(float(count), world, dist, "cuda")))
     ctx = M.Context(local, stream=stream.cuda_stream)
     ctx.set_option(M.MMF_OPT_BAND_MAX, args.band_max)
+    tuning = None
+    if not args.no_tuning and args.tuning and os.path.exists(args.tuning):
+        tuning = {"table": os.path.relpath(args.tuning, ROOT), "rules": ctx.load_tuning(args.tuning)}
     systems = [M.System(ctx, p) for p in problems]
     batch = M.Batch(ctx, systems, prec, nt)
     paths = {}
@@ -522,6 +528,7 @@ def main():
     # the plain FP64 path on the same systems (the metric's comparison arm)
     fp64 = None
     if mixed and args.fp64_steps > 0 and args.workload in ("spin1", "uneven"):
+        batch.close()  # the mixed plan's memory goes back before the FP64 plan is made
         b64 = M.Batch(ctx, systems, M.MMF_FP64, nt)
         b64.set_times(0.0, ts)
         b64.run()
@@ -560,6 +567,7 @@ def main():
                                         WORKLOAD if count == COUNT else f"{WORKLOAD}[:{count}]"),
                            "systems_per_step": total_count, "n": n, "nt": nt,
                            "precision": args.precision, "l2": "working set > L2 (no flush)",
+                           "tuning": tuning,
                            "parallelism": f"replicas x{world}" if args.workload != "uneven"
                            else f"instances split by sum n^3 over {world} rank(s)"},
                 "stage_ms": {k: round(v, 3) for k, v in per.items()},

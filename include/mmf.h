@@ -107,6 +107,22 @@ MMF_API size_t mmf_ctx_budget(const mmf_ctx* ctx);
 #define MMF_OPT_JACOBI_SWEEPS 7
 #define MMF_OPT_BAND_MAX 8
 MMF_API int mmf_ctx_set_option(mmf_ctx* ctx, int option, int64_t value);
+/* Tuning rules (per-system solver choices measured by an autotuner, e.g. the package's tune.py):
+ * for batches created afterwards, a system of the given precision with n_lo <= n <= n_hi and
+ * half-bandwidth band_lo <= b <= band_hi (b as for MMF_OPT_BAND_MAX) takes
+ *   jacobi: 1 the shared-memory Jacobi kernel (if n is within its maximum), 0 the Householder paths;
+ *   band:   1 the band path (if the band allows it), 0 the dense reduction;
+ *   bt_tc:  1 / 0 the mixed path's dense back-transform on the tensor cores / on the FP32 units;
+ * each -1 = no preference (the size thresholds above decide).  The first matching rule wins; a
+ * system's choices depend only on its own n and band, never on the rest of its batch.
+ * mmf_ctx_load_tuning reads rules from a text file, one per line:
+ *   <fp64|mixed> n_lo n_hi band_lo band_hi jacobi band bt_tc      ('#' starts a comment)
+ * and returns the number of rules added (or a negative error with the line in mmf_last_error).
+ * Results do not depend on the choices beyond rounding. */
+MMF_API int mmf_ctx_add_rule(mmf_ctx* ctx, int precision, int64_t n_lo, int64_t n_hi, int band_lo, int band_hi,
+                             int jacobi, int band, int bt_tc);
+MMF_API int mmf_ctx_clear_rules(mmf_ctx* ctx);
+MMF_API int mmf_ctx_load_tuning(mmf_ctx* ctx, const char* path);
 
 /* ---------------------------------------------------------------- system definition
  * The paper's set-up step (Sec. 3.1: the ATOM type, the harmonics array and the MODE
@@ -122,6 +138,10 @@ MMF_API int mmf_add_coupling(mmf_sys* sys, int mode_id, int harmonic, const doub
 MMF_API int mmf_sys_destroy(mmf_sys* sys);
 /* Floquet dimension n = D prod (2 N_l + 1) (Sec. 2, Appendix A); -1 on a NULL handle. */
 MMF_API int64_t mmf_dim(const mmf_sys* sys);
+/* Half-bandwidth of H_F (Eq. 6, Appendix A): the largest |row - col| of a nonzero entry, from the
+ * nonzero entries of H0 (|i - i'|) and of each harmonic h <= 2 N_l of mode l (D h S_l + i' - i,
+ * S_l the block stride of mode l); at least 1; -1 on a NULL handle. */
+MMF_API int mmf_sys_bandwidth(const mmf_sys* sys);
 
 /* ---------------------------------------------------------------- one system (Sec. 3.2)
  * mmf_build: S1, assemble H_F on the device in the given precision (MMF_FP64 / MMF_MIXED);

@@ -37,8 +37,18 @@ int mmf_set_error(int code, const std::string& msg) { return fail(code, msg); }
             return fail(MMF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// A tuning rule: for systems of one precision with n in [n_lo, n_hi] and half-bandwidth in
+// [band_lo, band_hi], the solver choices (-1 = no preference: the context's thresholds decide).
+struct TuneRule {
+    int precision;
+    int64_t n_lo, n_hi;
+    int band_lo, band_hi;
+    int jacobi, band, bt_tc;
+};
+
 struct mmf_ctx {
     int device = 0;
+    std::vector<TuneRule> rules;     // first match wins
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     size_t budget = 0, used = 0;
@@ -335,6 +345,62 @@ extern "C" int mmf_ctx_set_option(mmf_ctx* c, int option, int64_t value) {
 }
 extern "C" size_t mmf_ctx_budget(const mmf_ctx* c) { return c ? c->budget : 0; }
 
+extern "C" int mmf_ctx_add_rule(mmf_ctx* c, int precision, int64_t n_lo, int64_t n_hi, int band_lo, int band_hi,
+                                int jacobi, int band, int bt_tc) {
+    if (!c) return fail(MMF_ERR_ARG, "ctx is NULL");
+    if (precision != MMF_FP64 && precision != MMF_MIXED) return fail(MMF_ERR_ARG, "bad precision");
+    if (n_lo > n_hi || band_lo > band_hi) return fail(MMF_ERR_ARG, "empty rule range");
+    if (jacobi < -1 || jacobi > 1 || band < -1 || band > 1 || bt_tc < -1 || bt_tc > 1)
+        return fail(MMF_ERR_ARG, "rule choices are -1, 0 or 1");
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    c->rules.push_back({precision, n_lo, n_hi, band_lo, band_hi, jacobi, band, bt_tc});
+    return MMF_OK;
+}
+
+extern "C" int mmf_ctx_clear_rules(mmf_ctx* c) {
+    if (!c) return fail(MMF_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    c->rules.clear();
+    return MMF_OK;
+}
+
+extern "C" int mmf_ctx_load_tuning(mmf_ctx* c, const char* path) {
+    if (!c || !path) return fail(MMF_ERR_ARG, "ctx and path required");
+    FILE* f = std::fopen(path, "r");
+    if (!f) return fail(MMF_ERR_ARG, std::string("cannot open tuning table ") + path);
+    char line[512];
+    int ln = 0, added = 0;
+    std::vector<TuneRule> rules;
+    while (std::fgets(line, sizeof(line), f)) {
+        ++ln;
+        char* p = line;
+        while (*p == ' ' || *p == '\t') ++p;
+        if (*p == '#' || *p == '\n' || *p == '\0') continue;
+        char prec[16];
+        long long nlo, nhi;
+        int blo, bhi, jac, bnd, btc;
+        if (std::sscanf(p, "%15s %lld %lld %d %d %d %d %d", prec, &nlo, &nhi, &blo, &bhi, &jac, &bnd, &btc) != 8) {
+            std::fclose(f);
+            return fail(MMF_ERR_ARG, std::string(path) + ":" + std::to_string(ln) + ": expected 8 fields");
+        }
+        const std::string ps(prec);
+        if (ps != "fp64" && ps != "mixed") {
+            std::fclose(f);
+            return fail(MMF_ERR_ARG, std::string(path) + ":" + std::to_string(ln) + ": precision fp64 or mixed");
+        }
+        if (nlo > nhi || blo > bhi || jac < -1 || jac > 1 || bnd < -1 || bnd > 1 || btc < -1 || btc > 1) {
+            std::fclose(f);
+            return fail(MMF_ERR_ARG, std::string(path) + ":" + std::to_string(ln) + ": bad range or choice");
+        }
+        rules.push_back({ps == "fp64" ? MMF_FP64 : MMF_MIXED, (int64_t)nlo, (int64_t)nhi, blo, bhi, jac, bnd, btc});
+        ++added;
+    }
+    std::fclose(f);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    c->rules.insert(c->rules.end(), rules.begin(), rules.end());
+    return added;
+}
+
 // ------------------------------------------------------------------ systems
 extern "C" int mmf_sys_create(mmf_ctx* ctx, int D, const double* H0, mmf_sys** out) {
     if (!out) return fail(MMF_ERR_ARG, "out is NULL");
@@ -403,6 +469,7 @@ extern "C" int mmf_sys_destroy(mmf_sys* s) {
 }
 
 extern "C" int64_t mmf_dim(const mmf_sys* s) { return s ? sys_dim(s) : -1; }
+extern "C" int mmf_sys_bandwidth(const mmf_sys* s) { return s ? sys_band(s) : -1; }
 
 // ------------------------------------------------------------------ batch plan
 static void fill_coef(const mmf_batch* b, double2* dst) {
@@ -494,7 +561,17 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         d.n = (int)n;
         d.b0 = (int)b0;
         d.ld = (int)round_up(std::max<int64_t>(n, MMF_MIN_LD), 4);
+        // solver choices: a matching tuning rule, else the size thresholds
+        const int band_raw = sys_band(s);
+        const TuneRule* rule = nullptr;
+        for (const TuneRule& ru : ctx->rules)
+            if (ru.precision == precision && n >= ru.n_lo && n <= ru.n_hi && band_raw >= ru.band_lo &&
+                band_raw <= ru.band_hi) {
+                rule = &ru;
+                break;
+            }
         d.small = n <= jmax;
+        if (rule && rule->jacobi >= 0) d.small = n <= 4 || (rule->jacobi && n <= jacobi_default(precision));
         int64_t nc = (int64_t)s->D * s->D;
         for (int k = 0; k < d.K; ++k) nc += (int64_t)d.nharm[k] * s->D * s->D;
         d.coef_off = b->n_coef;
@@ -510,19 +587,20 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
         d.sq_off = b->n_sq;
         d.oz_off = b->n_oz;
         // banded systems: bulge chase instead of the dense reduction and its back-transform
-        const int64_t bmax_opt = ctx->band_max < 0 ? (precision == MMF_FP64 ? 64 : 0)
-                                                   : std::min<int64_t>(ctx->band_max, 64);
+        int64_t bmax_opt = ctx->band_max < 0 ? (precision == MMF_FP64 ? 64 : 0) : std::min<int64_t>(ctx->band_max, 64);
+        if (rule && rule->band >= 0) bmax_opt = rule->band ? 64 : 0;
         int cls = 0;
         if (!d.small && bmax_opt > 0) {
-            const int band = sys_band(s);
-            if (band <= bmax_opt && n >= 2 * (int64_t)band + 2 &&
+            const int band = band_raw;
+            if (band <= bmax_opt && n >= 2 * (int64_t)band + 2 && n * (int64_t)d.ld < INT32_MAX &&
                 mmf_sbr_store_elems((int)n, band) <= n * (int64_t)d.ld) {
                 d.band = band;
                 cls = mmf_sbr_class(band);
             }
         }
         // mixed: back-transform on the tensor cores for large enough systems (SIMT otherwise)
-        const bool tc = precision == MMF_MIXED && !d.small && !cls && n >= std::max<int64_t>(bt_tc_n(ctx), 3);
+        bool tc = precision == MMF_MIXED && !d.small && !cls && n >= std::max<int64_t>(bt_tc_n(ctx), 3);
+        if (rule && rule->bt_tc >= 0) tc = precision == MMF_MIXED && !d.small && !cls && n >= 3 && rule->bt_tc;
         if (precision == MMF_MIXED) {
             // one area per system, used in turn by the back-transform's operands, the Gram slices
             // (BF16) and split-TF32 operands of the refinement, and the time evolution's slices and Phi

@@ -80,11 +80,15 @@ _SIGS = {
     "mmf_ctx_bytes_in_use": (_SZ, [_P]),
     "mmf_ctx_budget": (_SZ, [_P]),
     "mmf_ctx_set_option": (_I, [_P, _I, _I64]),
+    "mmf_ctx_add_rule": (_I, [_P, _I, _I64, _I64, _I, _I, _I, _I, _I]),
+    "mmf_ctx_clear_rules": (_I, [_P]),
+    "mmf_ctx_load_tuning": (_I, [_P, ctypes.c_char_p]),
     "mmf_sys_create": (_I, [_P, _I, _P, _PP]),
     "mmf_add_mode": (_I, [_P, _D, _I, ctypes.POINTER(_I)]),
     "mmf_add_coupling": (_I, [_P, _I, _I, _P]),
     "mmf_sys_destroy": (_I, [_P]),
     "mmf_dim": (_I64, [_P]),
+    "mmf_sys_bandwidth": (_I, [_P]),
     "mmf_build": (_I, [_P, _I, ctypes.POINTER(_I64)]),
     "mmf_hamiltonian": (_I, [_P, _P]),
     "mmf_diagonalise": (_I, [_P]),
@@ -228,6 +232,22 @@ class Context:
     def budget(self) -> int:
         return int(lib().mmf_ctx_budget(self.h))
 
+    def add_rule(self, precision: int, n_lo: int, n_hi: int, band_lo: int, band_hi: int,
+                 jacobi: int = -1, band: int = -1, bt_tc: int = -1):
+        """Per-system solver choices for systems in the given size and band range (-1: no preference)."""
+        _check(lib().mmf_ctx_add_rule(self.h, precision, int(n_lo), int(n_hi), int(band_lo), int(band_hi),
+                                      int(jacobi), int(band), int(bt_tc)))
+
+    def clear_rules(self):
+        _check(lib().mmf_ctx_clear_rules(self.h))
+
+    def load_tuning(self, path: str) -> int:
+        """Add the rules of a tuning table file; returns their number."""
+        rc = lib().mmf_ctx_load_tuning(self.h, os.fsencode(path))
+        if rc < 0:
+            _check(rc)
+        return rc
+
     def close(self):
         self._closing = True
         if self._live <= 0:
@@ -259,6 +279,10 @@ class System:
             for hh, V in enumerate(problem.couplings[l], start=1):
                 _check(lib().mmf_add_coupling(self.h, mid.value, hh, _ptr(_cplx(V))))
         self.n = int(lib().mmf_dim(self.h))
+
+    def bandwidth(self) -> int:
+        """Half-bandwidth of this system's H_F."""
+        return int(lib().mmf_sys_bandwidth(self.h))
 
     def build(self, precision: int = MMF_FP64) -> int:
         n = ctypes.c_int64(0)
