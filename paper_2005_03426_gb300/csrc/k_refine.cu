@@ -499,7 +499,10 @@ __global__ void __launch_bounds__(256) k_oa_lambda(const MmfDesc* __restrict__ d
     }
 }
 
-// Et in place of G (diagonal and clustered pairs: r/2; others: OA formula)
+// Et in place of G (diagonal and clustered pairs: r/2; others: OA formula).  One 32 x 32 tile
+// (rows i, columns j) per block iteration: G is column-major (i contiguous) and C row-major
+// (j contiguous), so C's tile is read along j into shared memory first and both are then used
+// with i fastest across the threads.
 __global__ void __launch_bounds__(256) k_oa_etilde(const MmfDesc* __restrict__ descs,
                                                    const int* __restrict__ idx,
                                                    double2* __restrict__ Gg,
@@ -507,9 +510,9 @@ __global__ void __launch_bounds__(256) k_oa_etilde(const MmfDesc* __restrict__ d
                                                    const double* __restrict__ lam0g,
                                                    const double* __restrict__ lamg,
                                                    const int* __restrict__ cidg) {
+    __shared__ float cre[32][33], cim[32][33];
     const MmfDesc d = descs[idx[blockIdx.y]];
     const int n = d.n;
-    const int64_t tot = (int64_t)n * n;
     double2* G = Gg + d.mat_off;
     const float* C = reinterpret_cast<const float*>(Cg + d.mat_off);
     const double* lam0 = lam0g + d.vec_off;
@@ -517,34 +520,51 @@ __global__ void __launch_bounds__(256) k_oa_etilde(const MmfDesc* __restrict__ d
     const int* cid = cidg + d.vec_off;
     double hmax = fmax(fabs(lam[0]), fabs(lam[n - 1]));
     const float tiny = (float)(RF_GAMMA * hmax);  // |lam_i| <= hmax (ascending order)
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e / n), i = (int)(e - (int64_t)j * n);
-        const int64_t o = (int64_t)j * d.ld + i;
-        const double2 g = G[o];
-        double2 et;
-        if (i == j) {
-            et = make_double2(0.5 * (1.0 - g.x), 0.0);
-        } else if (abs(i - j) <= RF_W) {
-            // the band is applied in double-FP32: FP64 here
-            const double2 num = oa_num(C, n, i, j, g, lam[j] - lam0[j]);
-            const double gap = lam[j] - lam[i];
-            const bool clustered = cid[i] == cid[j] || gap * gap <= RF_TAU * RF_TAU * abs2(num) ||
-                                   fabs(gap) <= RF_GAMMA * fmax(hmax, fabs(lam[i]));
-            et = clustered ? (-0.5) * g : (1.0 / gap) * num;
-        } else {
-            // off the band Et goes through the split-TF32 product (FP32 accuracy): FP32 here,
-            // with the gap taken in FP64 before rounding
-            const float gx = (float)g.x, gy = (float)g.y;
-            const float dl = (float)(lam[j] - lam0[j]);
-            const float nr = C[(int64_t)i * 2 * n + j] - dl * gx, ni = C[(int64_t)i * 2 * n + n + j] - dl * gy;
-            const float gap = (float)(lam[j] - lam[i]);
-            const bool clustered = cid[i] == cid[j] || gap * gap <= (float)(RF_TAU * RF_TAU) * (nr * nr + ni * ni) ||
-                                   fabsf(gap) <= tiny;
-            const float r = 1.f / gap;
-            et = clustered ? make_double2(-0.5 * g.x, -0.5 * g.y) : make_double2(nr * r, ni * r);
+    const int nt = (n + 31) / 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int tile = blockIdx.x; tile < nt * nt; tile += gridDim.x) {
+        const int i0 = (tile % nt) * 32, j0 = (tile / nt) * 32;
+        __syncthreads();  // the previous tile's reads of cre / cim are done
+        for (int q = ty; q < 32; q += 8) {  // C(i0 + q, j0 + tx): j contiguous
+            const int i = i0 + q, j = j0 + tx;
+            const bool ok = i < n && j < n;
+            cre[q][tx] = ok ? C[(int64_t)i * 2 * n + j] : 0.f;
+            cim[q][tx] = ok ? C[(int64_t)i * 2 * n + n + j] : 0.f;
         }
-        G[o] = et;
+        __syncthreads();
+        const int i = i0 + tx;
+        if (i >= n) continue;
+        const double lami = lam[i];
+        const int cidi = cid[i];
+        for (int q = ty; q < 32; q += 8) {
+            const int j = j0 + q;
+            if (j >= n) break;
+            const int64_t o = (int64_t)j * d.ld + i;
+            const double2 g = G[o];
+            double2 et;
+            if (i == j) {
+                et = make_double2(0.5 * (1.0 - g.x), 0.0);
+            } else if (abs(i - j) <= RF_W) {
+                // the band is applied in double-FP32: FP64 here
+                const double2 num = oa_num(C, n, i, j, g, lam[j] - lam0[j]);
+                const double gap = lam[j] - lami;
+                const bool clustered = cidi == cid[j] || gap * gap <= RF_TAU * RF_TAU * abs2(num) ||
+                                       fabs(gap) <= RF_GAMMA * fmax(hmax, fabs(lami));
+                et = clustered ? (-0.5) * g : (1.0 / gap) * num;
+            } else {
+                // off the band Et goes through the split-TF32 product (FP32 accuracy): FP32 here,
+                // with the gap taken in FP64 before rounding
+                const float gx = (float)g.x, gy = (float)g.y;
+                const float dl = (float)(lam[j] - lam0[j]);
+                const float nr = cre[tx][q] - dl * gx, ni = cim[tx][q] - dl * gy;
+                const float gap = (float)(lam[j] - lami);
+                const bool clustered = cidi == cid[j] || gap * gap <= (float)(RF_TAU * RF_TAU) * (nr * nr + ni * ni) ||
+                                       fabsf(gap) <= tiny;
+                const float r = 1.f / gap;
+                et = clustered ? make_double2(-0.5 * g.x, -0.5 * g.y) : make_double2(nr * r, ni * r);
+            }
+            G[o] = et;
+        }
     }
 }
 

@@ -136,10 +136,13 @@ template <class R, class C, int BMAX, int G, int P>
 __device__ __forceinline__ void sbr_two_sided(SbrGroup<C, BMAX, P>& S, const C* v, C tau, int l, C* __restrict__ Hg,
                                               int ld, int r, int tid, int g, double* dout) {
     const int i = tid % BMAX, p = tid / BMAX;
-    C acc = mk(R(0), R(0));
+    C acc = mk(R(0), R(0)), acc1 = acc;  // two partial sums: independent FMA chains
 #pragma unroll
-    for (int q = 0; q < BMAX / P; ++q) acc = acc + S.Dm[i][p + q * P] * v[p + q * P];
-    S.red[p][i] = acc;
+    for (int q = 0; q < BMAX / P; q += 2) {
+        acc = acc + S.Dm[i][p + q * P] * v[p + q * P];
+        acc1 = acc1 + S.Dm[i][p + (q + 1) * P] * v[p + (q + 1) * P];
+    }
+    S.red[p][i] = acc + acc1;
     gbar<G>(g);
     R a_part = R(0);
     if (tid < BMAX) {
@@ -290,10 +293,13 @@ __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__
                 // update: with C1 = B H(j,s-1) = B - tau_p y v_p^H (y = B v_p), x = C1(:, 0) gives
                 // H(j,s); then H^H C1 = B - tau_p y v_p^H - conj(tau) v r with
                 // r_k = (v^H B)_k - tau_p (v^H y) conj(v_p,k).
-                C acc = mk(R(0), R(0));
+                C acc = mk(R(0), R(0)), acc1 = acc;
 #pragma unroll
-                for (int q = 0; q < BMAX / P; ++q) acc = acc + S.B[i][p + q * P] * vp[p + q * P];
-                S.red[p][i] = acc;
+                for (int q = 0; q < BMAX / P; q += 2) {
+                    acc = acc + S.B[i][p + q * P] * vp[p + q * P];
+                    acc1 = acc1 + S.B[i][p + (q + 1) * P] * vp[p + (q + 1) * P];
+                }
+                S.red[p][i] = acc + acc1;
                 gbar<G>(g);
                 if (tid < BMAX) {
                     C yy = S.red[0][tid];
@@ -318,10 +324,13 @@ __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__
                 // u_k = sum_i conj(v_i) B(i, k) and gamma = v^H (tau_p y)
                 {
                     const int kc = tid % BMAX, pc = tid / BMAX;
-                    C z = mk(R(0), R(0));
+                    C z = mk(R(0), R(0)), z1 = z;
 #pragma unroll
-                    for (int q = 0; q < BMAX / P; ++q) z = z + cmulc(vc[pc + q * P], S.B[pc + q * P][kc]);
-                    S.red[pc][kc] = z;
+                    for (int q = 0; q < BMAX / P; q += 2) {
+                        z = z + cmulc(vc[pc + q * P], S.B[pc + q * P][kc]);
+                        z1 = z1 + cmulc(vc[pc + (q + 1) * P], S.B[pc + (q + 1) * P][kc]);
+                    }
+                    S.red[pc][kc] = z + z1;
                 }
                 gbar<G>(g);
                 const R gre = group_sum<G, R>(tid < BMAX ? vc[tid].x * S.y[tid].x + vc[tid].y * S.y[tid].y : R(0),
@@ -401,10 +410,11 @@ __global__ void __launch_bounds__(128) k_sbr_bt_f32(const MmfDesc* __restrict__ 
                 if (threadIdx.x < b) vn = V[(off + j - 1) * b + threadIdx.x];
                 if (threadIdx.x == 0) tn = T[off + j - 1];
             }
-            // w = v^H z, z -= tau w v
+            // w = v^H z, z -= tau w v; the dot product runs from the window's bottom up, so that
+            // the row loaded last (zr[0]) is needed last
             float wr0 = 0.f, wi0 = 0.f, wr1 = 0.f, wi1 = 0.f;
 #pragma unroll
-            for (int q = 0; q < BMAX; q += 2) {
+            for (int q = BMAX - 2; q >= 0; q -= 2) {
                 const float4 v2 = *reinterpret_cast<const float4*>(&vs[buf][q]);
                 wr0 = fmaf(v2.x, zr[q].x, wr0);
                 wr0 = fmaf(v2.y, zr[q].y, wr0);

@@ -50,3 +50,24 @@ def test_serving_wait_times_out_then_completes():
     with pytest.raises(M.MmfError):
         srv.poll(tickets[0])  # released by its wait
     srv.close()
+
+
+def test_refinement_reports_a_cluster_too_large_to_separate():
+    """Two modes of the same frequency and no coupling: H_F is diagonal with E - (n1 + n2) w, so
+    the value E appears 2N + 1 = 41 times, a cluster beyond the refinement's 32-vector
+    separation.  The mixed path says so with MMF_ST_CLUSTER (its quasienergies stay exact); the
+    FP64 path, which has no refinement, reports nothing."""
+    D, N, w = 1, 20, 0.7
+    p = W.Problem(D=D, H0=np.array([[0.25]], dtype=complex), omegas=[w, w], Ns=[N, N],
+                  couplings=[[np.zeros((1, 1), dtype=complex)], [np.zeros((1, 1), dtype=complex)]])
+    ctx = M.Context(0)
+    expect = np.sort(np.array([0.25 - (a + c) * w for a in range(-N, N + 1) for c in range(-N, N + 1)]))
+    for precision, status in ((M.MMF_MIXED, M.MMF_ST_CLUSTER), (M.MMF_FP64, M.MMF_OK)):
+        b = M.Batch(ctx, [M.System(ctx, p)], precision, 2)
+        b.set_times(0.0, W.time_grid(p, 2)[None, :])
+        b.run()
+        st = b.sync()
+        assert st[0] == status, (precision, st)
+        E, _, P = b.get(0)
+        assert np.abs(E - expect).max() <= 1e-9 * np.abs(expect).max()
+        np.testing.assert_allclose(P, [[1.0]], atol=1e-8)  # one level: Pbar = 1
