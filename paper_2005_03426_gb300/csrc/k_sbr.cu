@@ -29,7 +29,12 @@
 // of Z keeps a window of BMAX rows in registers, applies the reflector (a length-BMAX dot
 // product and update), and slides the window up one row.  Z is kept row-major so that the
 // threads of a warp (consecutive columns) load and store consecutive addresses.
+#include <cooperative_groups.h>
+#include <cstdlib>
+
 #include "mmf_internal.h"
+
+namespace cg = cooperative_groups;
 
 // ------------------------------------------------------------------ reflector store
 // Pass s holds the reflectors of sweeps j = 0 .. n-2-s b (cnt(s) = n-1-s b of them) starting at
@@ -78,6 +83,19 @@ __device__ __forceinline__ void cp_elem(C* sdst, const C* gsrc, bool ok) {
         asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(ok ? 16 : 0) : "memory");
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gsrc), "r"(ok ? 8 : 0) : "memory");
+}
+// Load of one complex element from L2, bypassing L1: the two CTAs of a cluster run on different
+// SMs, whose L1 caches are not coherent, so band data written by one must not be read by the other
+// from a stale L1 line.
+__device__ __forceinline__ float2 ld_cg(const float2* p) {
+    float2 r;
+    asm volatile("ld.global.cg.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ double2 ld_cg(const double2* p) {
+    double2 r;
+    asm volatile("ld.global.cg.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "l"(p));
+    return r;
 }
 __device__ __forceinline__ void cp_wait_all() {
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -175,7 +193,11 @@ __device__ __forceinline__ void sbr_two_sided(SbrGroup<C, BMAX, P>& S, const C* 
     }
 }
 
-template <class R, int BMAX, int G, int NG>
+// CL = 1: one CTA per system.  CL = 2: a cluster of two CTAs (two SMs) per system, the sweeps
+// dealt round-robin over both CTAs' groups; a group reads its predecessor's progress key from the
+// partner's shared memory (distributed shared memory), the band is read from L2 only (ld.cg), and
+// progress is published after a GPU-scope fence.
+template <class R, int BMAX, int G, int NG, int CL>
 __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                                                     typename Cx<R>::T* __restrict__ Hbase,
                                                     typename Cx<R>::T* __restrict__ store_base,
@@ -184,12 +206,19 @@ __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__
     typedef typename Cx<R>::T C;
     constexpr int P = G / BMAX;
     static_assert(P * BMAX == G && P >= 1, "group size is a multiple of BMAX");
+    constexpr int NGT = CL * NG;                          // groups per system
+    constexpr int LCH = (BMAX / P) < 8 ? (BMAX / P) : 8;  // register-staged loads per batch (CL > 1)
+    static_assert((BMAX / P) % LCH == 0, "load batches divide the block");
     extern __shared__ __align__(16) unsigned char sbr_smem[];
     volatile long long* key = reinterpret_cast<volatile long long*>(sbr_smem);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sbr_smem + 8 * NG);
     SbrGroup<C, BMAX, P>* groups = reinterpret_cast<SbrGroup<C, BMAX, P>*>(sbr_smem + sbr_hdr(NG));
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = CL > 1 ? (int)cluster.block_rank() : 0;
+    volatile int* abort_peer = abort_flag;
+    if (CL > 1) abort_peer = cluster.map_shared_rank(const_cast<int*>(abort_flag), rank ^ 1);
 
-    const int sid = idx[blockIdx.x];
+    const int sid = idx[blockIdx.x / CL];
     const MmfDesc d = descs[sid];
     const int n = d.n, b = d.band;
     const int ldi = d.ld;  // in-system offsets fit 32 bits (n ld < 2^31, checked by the host)
@@ -200,27 +229,32 @@ __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__
     double* dd = dvec + d.vec_off;
     double* ee = evec + d.vec_off;
     const int g = threadIdx.x / G, tid = threadIdx.x % G;
+    const int gg = rank * NG + g;  // the group's number within the system
     SbrGroup<C, BMAX, P>& S = groups[g];
     const long long KK = sbr_passes(n, b) + 3;
+    // the predecessor sweep's group and its progress key (possibly in the partner CTA)
+    const int ggp = (gg + NGT - 1) % NGT;
+    volatile long long* pkey = key + (ggp % NG);
+    if (CL > 1 && ggp / NG != rank)
+        pkey = cluster.map_shared_rank(const_cast<long long*>(key), ggp / NG) + (ggp % NG);
 
     if (threadIdx.x < NG) key[threadIdx.x] = -1;
     if (threadIdx.x == 0) *abort_flag = 0;
-    __syncthreads();
-    if (threadIdx.x == 0) dd[0] = (double)Hg[0].x;
-    if (n < 2) return;
+    if (CL > 1) cluster.sync(); else __syncthreads();
+    if (threadIdx.x == 0 && rank == 0) dd[0] = (double)Hg[0].x;
 
     const int i = tid % BMAX, p = tid / BMAX;
     int cur = 0;  // buffer of the current reflector in S.v
-    for (int j = g; j <= n - 2; j += NG) {
+    bool stopped = false;
+    for (int j = gg; j <= n - 2 && !stopped; j += NGT) {
         const int nsteps = (n - 2 - j) / b + 1;
         for (int s = 0; s < nsteps; ++s) {
             // wait until sweep j-1 has finished step s+1 (or all of its steps)
             if (j > 0) {
                 if (tid == 0) {
                     const long long need = (long long)(j - 1) * KK + (s + 2 < KK - 1 ? s + 2 : KK - 1);
-                    const int pg = (g + NG - 1) % NG;
                     int it = 0;
-                    while (key[pg] < need && !*abort_flag) {
+                    while (*pkey < need && !*abort_flag && !*abort_peer) {
                         if (++it > SBR_WAIT_LIMIT) {
                             *abort_flag = 1;
                             status[sid] = MMF_ST_NOCONV;
@@ -228,11 +262,14 @@ __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__
                         }
                         __nanosleep(64);
                     }
-                    __threadfence_block();
-                    S.stop = *abort_flag;
+                    if (CL > 1) __threadfence(); else __threadfence_block();
+                    S.stop = *abort_flag || *abort_peer;
                 }
                 gbar<G>(g);
-                if (S.stop) return;  // the whole group leaves together
+                if (S.stop) {  // the whole group leaves together
+                    stopped = true;
+                    break;
+                }
             }
             const int r = j + 1 + s * b;
             const int l = min(b, n - r);
@@ -243,14 +280,30 @@ __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__
                 // column j below the diagonal and the diagonal block, lower triangle
                 // all of the step's loads in flight at once (asynchronous copies, zero-filled
                 // outside the l x l block)
-                if (tid < BMAX) cp_elem(&vc[tid], Hg + j * ldi + r + (tid < l ? tid : 0), tid < l);
+                if (CL == 1) {
+                    if (tid < BMAX) cp_elem(&vc[tid], Hg + j * ldi + r + (tid < l ? tid : 0), tid < l);
 #pragma unroll
-                for (int q = 0; q < BMAX / P; ++q) {
-                    const int k = p + q * P;
-                    const bool ok = i < l && k < l && i >= k;
-                    cp_elem(&S.Dm[i][k], Hg + (ok ? (r + k) * ldi + r + i : 0), ok);
+                    for (int q = 0; q < BMAX / P; ++q) {
+                        const int k = p + q * P;
+                        const bool ok = i < l && k < l && i >= k;
+                        cp_elem(&S.Dm[i][k], Hg + (ok ? (r + k) * ldi + r + i : 0), ok);
+                    }
+                    cp_wait_all();
+                } else {
+                    const C z0 = mk(R(0), R(0));
+                    if (tid < BMAX) vc[tid] = tid < l ? ld_cg(Hg + j * ldi + r + tid) : z0;
+#pragma unroll
+                    for (int q0 = 0; q0 < BMAX / P; q0 += LCH) {
+                        C rd[LCH];
+#pragma unroll
+                        for (int u = 0; u < LCH; ++u) {
+                            const int k = p + (q0 + u) * P;
+                            rd[u] = (i < l && k < l && i >= k) ? ld_cg(Hg + (r + k) * ldi + r + i) : z0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < LCH; ++u) S.Dm[i][p + (q0 + u) * P] = rd[u];
+                    }
                 }
-                cp_wait_all();
                 gbar<G>(g);
 #pragma unroll
                 for (int q = 0; q < BMAX / P; ++q) {
@@ -275,14 +328,33 @@ __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__
                 const int rp = r - b;
                 const int lp = min(b, n - rp);
                 const C taup = S.tau[cur ^ 1];
+                if (CL == 1) {
 #pragma unroll
-                for (int q = 0; q < BMAX / P; ++q) {
-                    const int k = p + q * P;
-                    const bool okb = i < l && k < lp, okd = i < l && k < l && i >= k;
-                    cp_elem(&S.B[i][k], Hg + (okb ? (rp + k) * ldi + r + i : 0), okb);
-                    cp_elem(&S.Dm[i][k], Hg + (okd ? (r + k) * ldi + r + i : 0), okd);
+                    for (int q = 0; q < BMAX / P; ++q) {
+                        const int k = p + q * P;
+                        const bool okb = i < l && k < lp, okd = i < l && k < l && i >= k;
+                        cp_elem(&S.B[i][k], Hg + (okb ? (rp + k) * ldi + r + i : 0), okb);
+                        cp_elem(&S.Dm[i][k], Hg + (okd ? (r + k) * ldi + r + i : 0), okd);
+                    }
+                    cp_wait_all();
+                } else {
+                    const C z0 = mk(R(0), R(0));
+#pragma unroll
+                    for (int q0 = 0; q0 < BMAX / P; q0 += LCH) {
+                        C rb[LCH], rd[LCH];
+#pragma unroll
+                        for (int u = 0; u < LCH; ++u) {
+                            const int k = p + (q0 + u) * P;
+                            rb[u] = (i < l && k < lp) ? ld_cg(Hg + (rp + k) * ldi + r + i) : z0;
+                            rd[u] = (i < l && k < l && i >= k) ? ld_cg(Hg + (r + k) * ldi + r + i) : z0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < LCH; ++u) {
+                            S.B[i][p + (q0 + u) * P] = rb[u];
+                            S.Dm[i][p + (q0 + u) * P] = rd[u];
+                        }
+                    }
                 }
-                cp_wait_all();
                 gbar<G>(g);
 #pragma unroll
                 for (int q = 0; q < BMAX / P; ++q) {
@@ -364,11 +436,13 @@ __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__
             // (d) diagonal block A(R_s, R_s) <- H^H A H
             sbr_two_sided<R, C, BMAX, G, P>(S, vc, tau, l, Hg, ldi, r, tid, g, s == 0 ? dd + j + 1 : nullptr);
             cur ^= 1;
-            __threadfence_block();
+            if (CL > 1) __threadfence(); else __threadfence_block();  // the step's writes, then its key
             gbar<G>(g);
             if (tid == 0) key[g] = (long long)j * KK + (s + 1 == nsteps ? KK - 1 : s + 1);
         }
     }
+    // the partner may still read this CTA's keys and abort flag: leave together
+    if (CL > 1) cluster.sync();
 }
 
 // ------------------------------------------------------------------ back-transform
@@ -557,18 +631,29 @@ __global__ void __launch_bounds__(256) k_sbr_out(const MmfDesc* __restrict__ des
 }
 
 // ------------------------------------------------------------------ launchers
-template <class R, int BMAX, int G, int NG>
+template <class R, int BMAX, int G, int NG, int CL>
 static cudaError_t launch_chase(const MmfLaunch& L, void* H, double2* store, double* dvec, double* evec,
                                 int* status) {
     typedef typename Cx<R>::T C;
     static_assert(sizeof(SbrGroup<C, BMAX, G / BMAX>) % 16 == 0, "group blocks keep 16-byte alignment");
     const size_t sm = sbr_hdr(NG) + sizeof(SbrGroup<C, BMAX, G / BMAX>) * NG;
-    cudaError_t e = cudaFuncSetAttribute(k_sbr_chase<R, BMAX, G, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_sbr_chase<R, BMAX, G, NG, CL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_sbr_chase<R, BMAX, G, NG><<<L.count, G * NG, sm, L.stream>>>(L.desc, L.idx, (C*)H, (C*)store, dvec, evec,
-                                                                  status);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(L.count * CL);
+    cfg.blockDim = dim3(G * NG);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_sbr_chase<R, BMAX, G, NG, CL>, L.desc, L.idx, (C*)H, (C*)store, dvec, evec,
+                              status);
 }
 
 template <int BMAX>
@@ -585,24 +670,44 @@ static cudaError_t launch_bt(const MmfLaunch& L, const double2* store, const dou
     return cudaGetLastError();
 }
 
+// The paired (two-SM) chase can be switched off for comparison: MMF_SBR_PAIRS=0 in the
+// environment.
+static bool sbr_pairs_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("MMF_SBR_PAIRS");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 int mmf_sbr_class(int b) { return b <= 8 ? 8 : b <= 16 ? 16 : b <= 32 ? 32 : b <= 64 ? 64 : 0; }
 
 cudaError_t mmf_launch_sbr_chase(const MmfLaunch& L, int bmax, void* H, double2* store, double* dvec, double* evec,
                                  int* status, int fp32) {
     if (L.count <= 0) return cudaSuccess;
+    // two CTAs (SMs) per system for the widest band while the pairs fit the GPU in one wave
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool pair = sbr_pairs_enabled() && 2 * L.count <= sms;
     if (fp32) {
         switch (bmax) {
-            case 8: return launch_chase<float, 8, 32, 15>(L, H, store, dvec, evec, status);
-            case 16: return launch_chase<float, 16, 32, 15>(L, H, store, dvec, evec, status);
-            case 32: return launch_chase<float, 32, 64, 8>(L, H, store, dvec, evec, status);
-            case 64: return launch_chase<float, 64, 128, 3>(L, H, store, dvec, evec, status);
+            case 8: return launch_chase<float, 8, 32, 15, 1>(L, H, store, dvec, evec, status);
+            case 16: return launch_chase<float, 16, 32, 15, 1>(L, H, store, dvec, evec, status);
+            case 32: return launch_chase<float, 32, 64, 8, 1>(L, H, store, dvec, evec, status);
+            case 64:
+                return pair ? launch_chase<float, 64, 128, 3, 2>(L, H, store, dvec, evec, status)
+                            : launch_chase<float, 64, 128, 3, 1>(L, H, store, dvec, evec, status);
         }
     } else {
         switch (bmax) {
-            case 8: return launch_chase<double, 8, 32, 15>(L, H, store, dvec, evec, status);
-            case 16: return launch_chase<double, 16, 32, 12>(L, H, store, dvec, evec, status);
-            case 32: return launch_chase<double, 32, 64, 4>(L, H, store, dvec, evec, status);
-            case 64: return launch_chase<double, 64, 128, 1>(L, H, store, dvec, evec, status);
+            case 8: return launch_chase<double, 8, 32, 15, 1>(L, H, store, dvec, evec, status);
+            case 16: return launch_chase<double, 16, 32, 12, 1>(L, H, store, dvec, evec, status);
+            case 32: return launch_chase<double, 32, 64, 4, 1>(L, H, store, dvec, evec, status);
+            case 64:
+                return pair ? launch_chase<double, 64, 128, 1, 2>(L, H, store, dvec, evec, status)
+                            : launch_chase<double, 64, 128, 1, 1>(L, H, store, dvec, evec, status);
         }
     }
     return cudaErrorInvalidValue;
