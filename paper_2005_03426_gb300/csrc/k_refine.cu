@@ -775,9 +775,13 @@ __global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ de
 
 // ------------------------------------------------------------------ cluster separation
 // Clusters are independent: each CTA of a system takes every gridDim.x-th candidate first index.
-// For cluster C (m vectors):
-// B = X_C^H H_F X_C in FP64 (H_F X_C from the HX buffer, recomputed for the new X), cyclic
-// Jacobi on B, X_C <- X_C W, lam_C <- eigenvalues of B ascending.
+// For cluster C (m vectors), Rayleigh-Ritz on span(X_C) in FP64:
+// B = X_C^H H_F X_C (H_F X_C from the HX buffer, recomputed for the new X) and
+// G_C = X_C^H X_C = L L^H (Cholesky); B' = L^-1 B L^-H, X_C <- X_C L^-H (orthonormal columns);
+// cyclic Jacobi on B', X_C <- X_C W, lam_C <- eigenvalues of B' ascending.  Without the
+// G_C factor the eigenvalues of B would carry an error |lam| |G_C - I|, and after the hybrid
+// second step a cluster's columns are orthonormal only to ~1e-10 (the pair's Et is r/2, first
+// order), which is the size of the separation of the near-degenerate pairs the cluster holds.
 // CTA-parallel two-sided Jacobi on the m x m Hermitian B (column-major, ld RF_CMAX), with the
 // round-robin pivot order: each round rotates m/2 disjoint pairs at once.  W accumulates the
 // rotations; w receives the eigenvalues (unsorted).  All threads of the CTA call it.
@@ -960,16 +964,72 @@ __global__ void __launch_bounds__(256) k_cluster_sep(const MmfDesc* __restrict__
                 HX[(int64_t)c * d.ld + r] = acc;
             }
             __syncthreads();
-            // B = X_C^H HX_C, one warp per entry
+            // B = X_C^H HX_C and G_C = X_C^H X_C (into W), one warp per entry
             for (int e = threadIdx.x >> 5; e < m * m; e += blockDim.x >> 5) {
                 const int p = e % m, q = e / m;
                 const double2* xp = X + (int64_t)(c0 + p) * d.ld;
+                const double2* xq = X + (int64_t)(c0 + q) * d.ld;
                 const double2* hq = HX + (int64_t)(c0 + q) * d.ld;
-                double2 acc = make_double2(0.0, 0.0);
-                for (int r = threadIdx.x & 31; r < n; r += 32) acc = acc + cmulc(xp[r], hq[r]);
+                double2 acc = make_double2(0.0, 0.0), gac = make_double2(0.0, 0.0);
+                for (int r = threadIdx.x & 31; r < n; r += 32) {
+                    acc = acc + cmulc(xp[r], hq[r]);
+                    gac = gac + cmulc(xp[r], xq[r]);
+                }
                 acc.x = warp_sum(acc.x);
                 acc.y = warp_sum(acc.y);
-                if ((threadIdx.x & 31) == 0) B[p + q * RF_CMAX] = acc;
+                gac.x = warp_sum(gac.x);
+                gac.y = warp_sum(gac.y);
+                if ((threadIdx.x & 31) == 0) {
+                    B[p + q * RF_CMAX] = acc;
+                    W[p + q * RF_CMAX] = gac;
+                }
+            }
+            __syncthreads();
+            // L (lower, in W) with G_C = L L^H; a non-positive pivot (columns not independent
+            // to FP64) leaves the cluster without the G_C factor (L = I)
+            if (threadIdx.x == 0) {
+                int ok = 1;
+                for (int j = 0; j < m && ok; ++j) {
+                    double s = W[j + j * RF_CMAX].x;
+                    for (int k = 0; k < j; ++k) s -= abs2(W[j + k * RF_CMAX]);
+                    if (!(s > 0.0)) { ok = 0; break; }
+                    const double ljj = sqrt(s);
+                    W[j + j * RF_CMAX] = make_double2(ljj, 0.0);
+                    for (int i = j + 1; i < m; ++i) {
+                        double2 a = W[i + j * RF_CMAX];
+                        for (int k = 0; k < j; ++k) a = a - W[i + k * RF_CMAX] * conj(W[j + k * RF_CMAX]);
+                        W[i + j * RF_CMAX] = (1.0 / ljj) * a;
+                    }
+                }
+                if (!ok)
+                    for (int j = 0; j < m; ++j)
+                        for (int i = j; i < m; ++i) W[i + j * RF_CMAX] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+            }
+            __syncthreads();
+            // B <- L^-1 B: forward substitution, one column per thread
+            for (int t = threadIdx.x; t < m; t += blockDim.x)
+                for (int i = 0; i < m; ++i) {
+                    double2 a = B[i + t * RF_CMAX];
+                    for (int k = 0; k < i; ++k) a = a - W[i + k * RF_CMAX] * B[k + t * RF_CMAX];
+                    B[i + t * RF_CMAX] = (1.0 / W[i + i * RF_CMAX].x) * a;
+                }
+            __syncthreads();
+            // B <- B L^-H: row t solves y L^H = B[t, :] (y_j = (b_j - sum_k<j y_k conj(L_jk)) / L_jj)
+            for (int t = threadIdx.x; t < m; t += blockDim.x)
+                for (int j = 0; j < m; ++j) {
+                    double2 a = B[t + j * RF_CMAX];
+                    for (int k = 0; k < j; ++k) a = a - B[t + k * RF_CMAX] * conj(W[j + k * RF_CMAX]);
+                    B[t + j * RF_CMAX] = (1.0 / W[j + j * RF_CMAX].x) * a;
+                }
+            // X_C <- X_C L^-H, the same solve on every row of X_C (rows independent)
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {
+                double2 row[RF_CMAX];
+                for (int j = 0; j < m; ++j) {
+                    double2 a = X[(int64_t)(c0 + j) * d.ld + r];
+                    for (int k = 0; k < j; ++k) a = a - row[k] * conj(W[j + k * RF_CMAX]);
+                    row[j] = (1.0 / W[j + j * RF_CMAX].x) * a;
+                    X[(int64_t)(c0 + j) * d.ld + r] = row[j];
+                }
             }
             __syncthreads();
             if (threadIdx.x == 0) {
