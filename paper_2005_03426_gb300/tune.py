@@ -10,7 +10,7 @@ Candidates per bucket (only those the bucket allows):
     units.
 A rule depends only on a system's n and half-bandwidth, so a system takes the same path whatever
 else is in its batch.  Timing: one warm-up run, then the mean of ``reps`` runs of a batch of up to
-``sample`` systems of the bucket (host clock around device-synchronised runs), per system.
+``sample`` systems spread evenly over the bucket (host clock around device-synchronised runs), per system.
 
     python -m paper_2005_03426_gb300.tune --out paper_2005_03426_gb300/tuning_gb300.txt
 """
@@ -31,7 +31,7 @@ from paper_2005_03426_gb300 import mmf as M  # noqa: E402
 from paper_2005_03426_gb300 import workloads as W  # noqa: E402
 
 N_EDGES = [1, 33, 65, 85, 119, 192, 256, 384, 512, 768, 1024, 1400, 2048, 3072, 2 ** 31 - 1]
-BAND_CLASSES = [(0, 8), (9, 16), (17, 32), (33, 64), (65, 2 ** 31 - 1)]
+BAND_CLASSES = [(0, 8), (9, 16), (17, 32), (33, 48), (49, 64), (65, 2 ** 31 - 1)]
 JACOBI_MAX = {M.MMF_FP64: 84, M.MMF_MIXED: 118}
 NAMES = {M.MMF_FP64: "fp64", M.MMF_MIXED: "mixed"}
 
@@ -55,6 +55,14 @@ def default_samples():
     ps += W.qubit_sweep(64)
     ps += W.lattice_sweep(16)
     return ps
+
+
+def spread(items, sample):
+    """Up to ``sample`` items evenly spaced over the list (so that every source workload in a
+    bucket is represented)."""
+    if len(items) <= sample:
+        return list(items)
+    return [items[int(k * len(items) / sample)] for k in range(sample)]
 
 
 def candidates(precision, nb, band_cls, any_band_ok):
@@ -105,7 +113,7 @@ def tune(precisions, problems, sample=64, reps=2, nt=64, log=print):
     lines = []
     for precision in precisions:
         for (nb, bc) in sorted(groups):
-            items = groups[(nb, bc)][:sample]
+            items = spread(groups[(nb, bc)], sample)
             ps = [p for p, _ in items]
             band_ok = any(band <= 64 and p.n >= 2 * band + 2 for p, band in items)
             cands = candidates(precision, nb, bc, band_ok)
