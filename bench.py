@@ -420,6 +420,8 @@ def main():
     ap.add_argument("--no-tuning", action="store_true")
     ap.add_argument("--band-max", type=int, default=-1,
                     help="widest band reduced by the bulge chase (library option; 0: dense reduction only)")
+    ap.add_argument("--hetrd-simt", action="store_true",
+                    help="mixed path: the dense reduction's trailing update on the FP32 units instead of the tensor cores")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -465,6 +467,7 @@ def main():
     total_count = int(round(sum_over_ranks(float(count), world, dist, "cuda")))
     ctx = M.Context(local, stream=stream.cuda_stream)
     ctx.set_option(M.MMF_OPT_BAND_MAX, args.band_max)
+    ctx.set_option(M.MMF_OPT_HETRD_TC, 0 if args.hetrd_simt else 1)
     tuning = None
     if not args.no_tuning and args.tuning and os.path.exists(args.tuning):
         tuning = {"table": os.path.relpath(args.tuning, ROOT), "rules": ctx.load_tuning(args.tuning)}

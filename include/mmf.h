@@ -97,6 +97,9 @@ MMF_API size_t mmf_ctx_budget(const mmf_ctx* ctx);
  * MMF_OPT_JACOBI_SWEEPS: iteration cap of the shared-memory Jacobi kernel (default 40 sweeps;
  * values below 1 act as 1).  A system that has not converged at the cap gets MMF_ST_NOCONV from
  * mmf_batch_sync / mmf_diagonalise.
+ * MMF_OPT_HETRD_TC: in the mixed path, the dense Householder reduction's trailing update
+ * A -= V W^H + W V^H after each panel (Sec. 3.2's diagonalisation) on the tensor cores in split
+ * TF32 (1 or < 0, default) or on the FP32 units (0).
  * Results do not depend on the path beyond rounding. */
 #define MMF_OPT_JACOBI_N_FP64 1
 #define MMF_OPT_JACOBI_N_MIXED 2
@@ -106,6 +109,7 @@ MMF_API size_t mmf_ctx_budget(const mmf_ctx* ctx);
 #define MMF_OPT_BT_TC_N 6
 #define MMF_OPT_JACOBI_SWEEPS 7
 #define MMF_OPT_BAND_MAX 8
+#define MMF_OPT_HETRD_TC 9
 MMF_API int mmf_ctx_set_option(mmf_ctx* ctx, int option, int64_t value);
 /* Tuning rules (per-system solver choices measured by an autotuner, e.g. the package's tune.py):
  * for batches created afterwards, a system of the given precision with n_lo <= n <= n_hi and
@@ -373,6 +377,14 @@ MMF_API int mmf_selftest_gram(int n, double* max_abs_err, double* max_abs_ref);
  * comparison.  M x K, N x K and M x N at most 2^26 each; allocates its own device memory. */
 MMF_API int mmf_selftest_split_tf32(int M, int N, int K, int mode, double* max_rel_err,
                                     double* max_rel_err_fp32);
+/* Runs the mixed path's FP32 Householder reduction to tridiagonal form (Sec. 3.2's
+ * diagonalisation, first step) on `count` seeded Hermitian n x n FP32 matrices in one launch
+ * (2 <= n <= the one-CTA maximum, count <= 512, n^2 count <= 2^27), with the trailing update
+ * A -= V W^H + W V^H on the tensor cores in split TF32 (tensor_cores = 1) or on the FP32 units
+ * (0).  For the first two matrices the host applies the stored reflectors in FP64,
+ * B = Q^H A Q, and returns max |B - tridiag(e, d, e)| over all entries and max |A|.  Allocates its
+ * own device memory; for health checks, not for the solve path. */
+MMF_API int mmf_selftest_hetrd(int n, int count, int tensor_cores, double* max_abs_err, double* max_abs_ref);
 
 /* ---------------------------------------------------------------- misc */
 MMF_API const char* mmf_strerror(int status);

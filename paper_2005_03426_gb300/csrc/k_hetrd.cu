@@ -26,7 +26,12 @@
 // repeats the short O(m) vector steps itself.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "mmf_internal.h"
+#include "umma_common.h"
 
 namespace cg = cooperative_groups;
 
@@ -64,11 +69,15 @@ __host__ __device__ inline size_t ht_big_offset(int nmax) {
     const size_t o = sizeof(typename Cx<R>::T) * 3 * (size_t)nmax + ht_fixed_bytes<R>();
     return (o + 15) & ~(size_t)15;
 }
+// FP32: the hemv's cp.async stages, or (tensor-core trailing update) two operand stages of 64 KB
+// at a 1024-byte boundary
+#define HT_TC_STAGE 65536u
 template <class R>
 __host__ __device__ constexpr size_t ht_big_bytes() {
-    return sizeof(R) == 4 ? (size_t)(HT_THREADS / 32) * 2 * HT_STAGE_ELEMS * sizeof(typename Cx<R>::T)
+    return sizeof(R) == 4 ? (size_t)(HT_THREADS / 32) * 2 * HT_STAGE_ELEMS * sizeof(typename Cx<R>::T) + 1024
                           : (size_t)4 * MMF_NB * HT_TILE * sizeof(typename Cx<R>::T);
 }
+static_assert((HT_THREADS / 32) * 2 * HT_STAGE_ELEMS * 8 >= 2 * HT_TC_STAGE, "tensor-core stages fit");
 
 __device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc, int src_bytes) {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
@@ -260,14 +269,196 @@ __device__ int hemv_f32_staged(const float2* __restrict__ a22, int ld, int m, co
     return nchunks;
 }
 
-template <class R, int CL>
+// ------------------------------------------------------------------ trailing update, tensor cores
+// A(c0:, c0:) -= V W^H + W V^H on the lower triangle (FP32 path), as real split-TF32 products on
+// the tcgen05 engine.  Tiles of 128 rows x 64 complex columns: column block cb = c0 + 64 tj, row
+// blocks rb = cb + 128 ti (the first holds the block's diagonal; entries above it are dropped).
+// With K' = 128 real entries per row in four chunks of 32 (the panel's columns), ordered
+// (Re V, Im V, Re W, Im W),
+//     A'(r)       = [Re V(r,:), Im V(r,:), Re W(r,:), Im W(r,:)]
+//     B'(2j)      = [Re W(c,:), Im W(c,:), Re V(c,:), Im V(c,:)]        (c = cb + j)
+//     B'(2j + 1)  = [-Im W(c,:), Re W(c,:), -Im V(c,:), Re V(c,:)]
+// the product D = A' B'^T holds Re and Im of (V W^H + W V^H)(r, c) in columns 2j and 2j + 1
+// (Re(a conj b) = ar br + ai bi, Im(a conj b) = ai br - ar bi).  Each operand is split into TF32
+// pieces x = x1 + x2 and each chunk's D = A1 B1^T + A1 B2^T + A2 B1^T goes to its own TMEM
+// accumulator (4 x 128 columns), which the epilogue sums in FP32 registers: the tensor cores'
+// accumulation is cut to 96 terms, and the result stays within a few FP32 roundings of the
+// FP32 units' update.  Chunks 0-1 (the V pass) and 2-3 (the W pass) take the same complex
+// values: a thread loads its pass's values once (L2) and builds both chunks from registers into
+// one of two 64 KB stages, in the tensor cores' layout (K-major, 128-byte swizzle); one thread
+// issues each chunk's 12 tcgen05.mma (M = 128, N = 128, K = 8) and commits them to the stage's
+// mbarrier, so that the next chunk is built while they run.  Epilogue: warp w reads TMEM lanes
+// 32 (w % 4) .. +31 (rows) and columns 32 (w / 4) .. +31 (16 complex columns) of each
+// accumulator and subtracts the sum from A, whose old values it loaded when the tile began.
+// Every wait is bounded; a wait that gives up makes the routine return false.
+#define HT_TC_COLS 512u   // TMEM columns: four 128-column accumulators
+struct HtTc {
+    unsigned char* st;   // two stages of HT_TC_STAGE bytes (1024-byte aligned)
+    uint64_t* bar;       // [0], [1]: stage free; [2]: tile's products done
+    uint32_t tmem;
+    uint32_t used[2], waited[2], pacc;
+};
+
+__device__ __forceinline__ void ht_split4(float* hi, float* lo, int off, float x0, float x1, float x2, float x3) {
+    const float4 h = make_float4(tf32_round(x0), tf32_round(x1), tf32_round(x2), tf32_round(x3));
+    *reinterpret_cast<float4*>(hi + off) = h;
+    *reinterpret_cast<float4*>(lo + off) =
+        make_float4(tf32_round(x0 - h.x), tf32_round(x1 - h.y), tf32_round(x2 - h.z), tf32_round(x3 - h.w));
+}
+
+__device__ __forceinline__ void ht_tmem_ld32(uint32_t ta, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(ta));
+}
+
+template <int CL>
+__device__ bool her2k_tc(float2* __restrict__ A, int ld, int n, int c0, const float2* __restrict__ V,
+                         const float2* __restrict__ W, int nb, int rank, HtTc& T) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t idesc = umma_idesc_mn(2, 128u, 128u);  // TF32 x TF32 -> F32, M = N = 128
+    const int ncb = (n - c0 + 63) / 64;
+    int tcount = 0;
+    bool ok = true;
+    for (int tj = 0; tj < ncb && ok; ++tj) {
+        const int cb = c0 + 64 * tj;
+        for (int rb = cb; rb < n && ok; rb += 128) {
+            if ((tcount++ % CL) != rank) continue;
+            // old values of this thread's 16 entries (row r, columns cc .. cc + 15), in flight
+            // while the operands are built
+            const int r = rb + 32 * (warp & 3) + lane, cc = cb + 16 * (warp >> 2);
+            float2 old[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                old[q] = (r < n && cc + q < n && r >= cc + q) ? A[r + (int64_t)(cc + q) * ld] : make_float2(0.f, 0.f);
+            for (int pass = 0; pass < 2 && ok; ++pass) {
+                const float2* P = pass ? W : V;   // A' source
+                const float2* Q = pass ? V : W;   // B' source
+                // items e = tid, tid + 512: operand row rr = e % 128 (lanes over rows: coalesced
+                // column reads), K group kq = e / 128 (4 panel columns)
+                float2 a[2][4], b[2][4];
+#pragma unroll
+                for (int it = 0; it < 2; ++it) {
+                    const int e = tid + it * HT_THREADS, rr = e & 127, kq = e >> 7;
+                    const int ra = rb + rr, cbr = cb + (rr >> 1);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int p = 4 * kq + u;
+                        a[it][u] = (p < nb && ra < n) ? P[ra + (int64_t)p * ld] : make_float2(0.f, 0.f);
+                        b[it][u] = (p < nb && cbr < n) ? Q[cbr + (int64_t)p * ld] : make_float2(0.f, 0.f);
+                    }
+                }
+                for (int half = 0; half < 2 && ok; ++half) {
+                    const int kc = 2 * pass + half, s = half;
+                    if (T.used[s] > T.waited[s]) {  // the products that last read this stage are done
+                        ok = __syncthreads_and(mbar_wait(&T.bar[s], T.waited[s] & 1u) ? 1 : 0) != 0;
+                        ++T.waited[s];
+                        if (!ok) break;
+                    }
+                    float* ahi = reinterpret_cast<float*>(T.st + s * HT_TC_STAGE);
+                    float* alo = ahi + 4096;
+                    float* bhi = alo + 4096;
+                    float* blo = bhi + 4096;
+#pragma unroll
+                    for (int it = 0; it < 2; ++it) {
+                        const int e = tid + it * HT_THREADS, rr = e & 127, kq = e >> 7;
+                        const int off = (rr >> 3) * 256 + (rr & 7) * 32 + ((kq ^ (rr & 7)) << 2);
+                        // A': Re (half 0) or Im (half 1) of the pass's matrix; B' row rr (column
+                        // cb + rr / 2): Re row (rr even) [Re, Im] of the other matrix over the two
+                        // halves, Im row (rr odd) [-Im, Re]
+                        const int h = rr & 1;
+                        float x[4], y[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            x[u] = half ? a[it][u].y : a[it][u].x;
+                            y[u] = h ? (half ? b[it][u].x : -b[it][u].y) : (half ? b[it][u].y : b[it][u].x);
+                        }
+                        ht_split4(ahi, alo, off, x[0], x[1], x[2], x[3]);
+                        ht_split4(bhi, blo, off, y[0], y[1], y[2], y[3]);
+                    }
+                    // the stores above are read by the tensor cores' async proxy
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncthreads();
+                    if (tid == 0) {
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t sa = smem_u32(ahi);
+                        const uint64_t a1 = umma_desc(sa), a2 = umma_desc(sa + 16384u);
+                        const uint64_t b1 = umma_desc(sa + 32768u), b2 = umma_desc(sa + 49152u);
+                        const uint32_t dacc = T.tmem + 128u * (uint32_t)kc;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {  // 32 bytes (8 TF32) of K per instruction
+                            const uint64_t adv = (uint64_t)((q * 32) >> 4);
+                            const uint64_t pa[3] = {a1, a1, a2}, pb[3] = {b1, b2, b1};
+#pragma unroll
+                            for (int pp = 0; pp < 3; ++pp) {
+                                const uint32_t accf = (q > 0 || pp > 0) ? 1u : 0u;
+                                asm volatile(
+                                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
+                                    "l"(pa[pp] + adv), "l"(pb[pp] + adv), "r"(idesc), "r"(accf)
+                                    : "memory");
+                            }
+                        }
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                         smem_u32(&T.bar[s]))
+                                     : "memory");
+                        if (kc == 3)
+                            asm volatile(
+                                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                    smem_u32(&T.bar[2]))
+                                : "memory");
+                    }
+                    ++T.used[s];
+                }
+            }
+            if (!ok) break;
+            ok = __syncthreads_and(mbar_wait(&T.bar[2], T.pacc) ? 1 : 0) != 0;
+            T.pacc ^= 1u;
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ta = T.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
+            float2 acc[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[q] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int kc = 0; kc < 4; ++kc) {
+                uint32_t v[32];
+                ht_tmem_ld32(ta + 128u * (uint32_t)kc, v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    acc[q].x += __uint_as_float(v[2 * q]);
+                    acc[q].y += __uint_as_float(v[2 * q + 1]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (r < n && cc + q < n && r >= cc + q)
+                    A[r + (int64_t)(cc + q) * ld] = make_float2(old[q].x - acc[q].x, old[q].y - acc[q].y);
+            // the next tile's first products overwrite the accumulators after the next barrier
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+    }
+    return ok;
+}
+
+template <class R, int CL, bool TC>
 __global__ void __launch_bounds__(HT_THREADS, 1)
 k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
         typename Cx<R>::T* __restrict__ H, typename Cx<R>::T* __restrict__ Vpool,
         typename Cx<R>::T* __restrict__ Wpool, double* __restrict__ dvec,
-        double* __restrict__ evec, typename Cx<R>::T* __restrict__ taupool, int nmax) {
+        double* __restrict__ evec, typename Cx<R>::T* __restrict__ taupool, int nmax,
+        int* __restrict__ status) {
+    static_assert(!TC || sizeof(R) == 4, "tensor-core trailing update on the FP32 path only");
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint64_t tc_bar[3];
+    __shared__ uint32_t tc_tmem;
     C* vS = reinterpret_cast<C*>(smem_raw);   // nmax
     C* yS = vS + nmax;                          // nmax: this CTA's partial y = A22 v
     C* yF = yS + nmax;                          // nmax: full y (CL = 2)
@@ -296,6 +487,26 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
     C* tau = taupool + d.vec_off;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int NW = HT_THREADS / 32;
+    HtTc T = {};
+    bool tc_ok = true;
+    if constexpr (TC) {
+        if (tid == 0) {
+            for (int q = 0; q < 3; ++q) mbar_init(&tc_bar[q], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tc_tmem)),
+                         "r"(HT_TC_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        T.st = reinterpret_cast<unsigned char*>(((uintptr_t)big + 1023) & ~(uintptr_t)1023);
+        T.bar = tc_bar;
+        T.tmem = tc_tmem;
+    }
 
     for (int j0 = 0; j0 < n; j0 += MMF_NB) {
         const int nb = min(MMF_NB, n - j0);
@@ -523,7 +734,14 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
 
         // trailing her2k on the lower triangle of A(c0:, c0:)
         const int c0 = j0 + nb;
-        if (c0 < n) {
+        if constexpr (TC) {
+            if (c0 < n) {
+                if (tc_ok)
+                    tc_ok = her2k_tc<CL>(reinterpret_cast<float2*>(A), ld, n, c0, reinterpret_cast<const float2*>(V),
+                                         reinterpret_cast<const float2*>(W), nb, rank, T);
+                if (CL > 1) cluster.sync();
+            }
+        } else if (c0 < n) {
             const int nt = (n - c0 + HT_TILE - 1) / HT_TILE;
             const int rr = tid & (HT_TILE - 1), cg = tid / HT_TILE;  // 8 column groups
             int tcount = 0;
@@ -590,6 +808,14 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
             if (CL > 1) cluster.sync();
         }
     }
+    if constexpr (TC) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(T.tmem), "r"(HT_TC_COLS) : "memory");
+        // a wait of the tensor-core update that gave up (the system's reduction is then incomplete)
+        if (!tc_ok && tid == 0) status[idx[blockIdx.x / CL]] = MMF_ST_NOCONV;
+    }
 }
 
 static size_t hetrd_smem(int nmax, int fp32) {
@@ -601,14 +827,16 @@ int mmf_hetrd_max_n(int fp32) {
     const size_t cs = fp32 ? 8 : 16;
     const size_t fixed = fp32 ? ht_fixed_bytes<float>() + ht_big_bytes<float>()
                               : ht_fixed_bytes<double>() + ht_big_bytes<double>();
-    return (int)((227 * 1024 - fixed - 16) / (3 * cs));
+    // 64 bytes for the kernel's static shared variables (tensor-core mbarriers, TMEM address) and
+    // the 16-byte rounding of the operand region
+    return (int)((227 * 1024 - fixed - 64) / (3 * cs));
 }
 
-template <class R, int CL>
+template <class R, int CL, bool TC>
 static cudaError_t launch_hetrd(const MmfLaunch& L, void* H, void* Vp, void* Wp, double* dvec,
-                                double* evec, void* tau, size_t sm) {
+                                double* evec, void* tau, size_t sm, int* status) {
     typedef typename Cx<R>::T C;
-    cudaError_t err = cudaFuncSetAttribute(k_hetrd<R, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t err = cudaFuncSetAttribute(k_hetrd<R, CL, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(L.count * CL);
@@ -622,12 +850,12 @@ static cudaError_t launch_hetrd(const MmfLaunch& L, void* H, void* Vp, void* Wp,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_hetrd<R, CL>, L.desc, L.idx, (C*)H, (C*)Vp, (C*)Wp, dvec, evec,
-                              (C*)tau, L.nmax);
+    return cudaLaunchKernelEx(&cfg, k_hetrd<R, CL, TC>, L.desc, L.idx, (C*)H, (C*)Vp, (C*)Wp, dvec, evec,
+                              (C*)tau, L.nmax, status);
 }
 
 cudaError_t mmf_launch_hetrd(const MmfLaunch& L, void* H, void* Vp, void* Wp, double* dvec,
-                             double* evec, void* tau, int fp32) {
+                             double* evec, void* tau, int fp32, int tc, int* status) {
     if (L.count <= 0) return cudaSuccess;
     if (L.nmax > mmf_hetrd_max_n(fp32)) return cudaErrorInvalidValue;
     const size_t sm = hetrd_smem(L.nmax, fp32);
@@ -636,9 +864,168 @@ cudaError_t mmf_launch_hetrd(const MmfLaunch& L, void* H, void* Vp, void* Wp, do
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // two CTAs per system while that still fits the GPU in one wave
     const bool pair = 2 * L.count <= sms;
+    if (fp32 && tc)
+        return pair ? launch_hetrd<float, 2, true>(L, H, Vp, Wp, dvec, evec, tau, sm, status)
+                    : launch_hetrd<float, 1, true>(L, H, Vp, Wp, dvec, evec, tau, sm, status);
     if (fp32)
-        return pair ? launch_hetrd<float, 2>(L, H, Vp, Wp, dvec, evec, tau, sm)
-                    : launch_hetrd<float, 1>(L, H, Vp, Wp, dvec, evec, tau, sm);
-    return pair ? launch_hetrd<double, 2>(L, H, Vp, Wp, dvec, evec, tau, sm)
-                : launch_hetrd<double, 1>(L, H, Vp, Wp, dvec, evec, tau, sm);
+        return pair ? launch_hetrd<float, 2, false>(L, H, Vp, Wp, dvec, evec, tau, sm, status)
+                    : launch_hetrd<float, 1, false>(L, H, Vp, Wp, dvec, evec, tau, sm, status);
+    return pair ? launch_hetrd<double, 2, false>(L, H, Vp, Wp, dvec, evec, tau, sm, status)
+                : launch_hetrd<double, 1, false>(L, H, Vp, Wp, dvec, evec, tau, sm, status);
+}
+
+// ------------------------------------------------------------------ self-test
+// `count` seeded Hermitian n x n FP32 matrices (entries uniform in the unit square, full
+// mantissas; leading dimension n rounded up to 8) reduced in one launch (two CTAs per system when
+// 2 count fits the SMs, else one), with the trailing update on the tensor cores (tc = 1) or the
+// FP32 units (tc = 0).  For the first two systems the host applies the stored reflectors to the
+// input in FP64, B = P_{n-2}^H ... P_0^H A P_0 ... P_{n-2}, and returns max |B - tridiag(e, d, e)|
+// (every entry) and max |A|.  Returns 0, -1 (bad sizes), -4 (CUDA failure) or 1 (a wait gave up).
+int mmf_hetrd_selftest_impl(int n, int count, int tc, double* max_err, double* max_ref) {
+    if (n < 2 || n > mmf_hetrd_max_n(1) || count < 1 || count > 512 || (int64_t)n * n * count > (1 << 27)) return -1;
+    const int ld = (n + 7) & ~7;
+    const int64_t mat = (int64_t)n * ld, pan = (int64_t)ld * MMF_NB;
+    std::vector<MmfDesc> hd(count);
+    std::vector<int> hidx(count);
+    for (int s = 0; s < count; ++s) {
+        MmfDesc d = {};
+        d.n = n;
+        d.ld = ld;
+        d.D = n;
+        d.M = 1;
+        d.mat_off = s * mat;
+        d.pan_off = s * pan;
+        d.vec_off = (int64_t)s * n;
+        hd[s] = d;
+        hidx[s] = s;
+    }
+    std::vector<float2> hA((size_t)mat * count, make_float2(0.f, 0.f));
+    uint64_t x = 0x9E3779B97F4A7C15ull;
+    auto unif = [&x]() {  // xorshift64*, uniform in [-1, 1)
+        x ^= x >> 12;
+        x ^= x << 25;
+        x ^= x >> 27;
+        return (double)((x * 0x2545F4914F6CDD1Dull) >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    };
+    for (int s = 0; s < count; ++s)
+        for (int c = 0; c < n; ++c)
+            for (int r = c; r < n; ++r) {
+                const float re = (float)unif(), im = r == c ? 0.f : (float)unif();
+                hA[s * mat + r + (int64_t)c * ld] = make_float2(re, im);
+                hA[s * mat + c + (int64_t)r * ld] = make_float2(re, -im);
+            }
+    MmfDesc* dd = nullptr;
+    int *didx = nullptr, *dst = nullptr;
+    float2 *dA = nullptr, *dV = nullptr, *dW = nullptr, *dtau = nullptr;
+    double *dD = nullptr, *dE = nullptr;
+    int rc = 0;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreate(&st) != cudaSuccess) return -4;
+    bool ok = cudaMalloc(&dd, sizeof(MmfDesc) * count) == cudaSuccess &&
+              cudaMalloc(&didx, sizeof(int) * count) == cudaSuccess &&
+              cudaMalloc(&dst, sizeof(int) * count) == cudaSuccess &&
+              cudaMalloc(&dA, sizeof(float2) * mat * count) == cudaSuccess &&
+              cudaMalloc(&dV, sizeof(float2) * pan * count) == cudaSuccess &&
+              cudaMalloc(&dW, sizeof(float2) * pan * count) == cudaSuccess &&
+              cudaMalloc(&dtau, sizeof(float2) * n * count) == cudaSuccess &&
+              cudaMalloc(&dD, sizeof(double) * n * count) == cudaSuccess &&
+              cudaMalloc(&dE, sizeof(double) * n * count) == cudaSuccess;
+    std::vector<double> hD((size_t)n * count), hE((size_t)n * count);
+    std::vector<float2> htau((size_t)n * count);
+    std::vector<int> hst(count);
+    if (ok) {
+        ok = cudaMemcpy(dd, hd.data(), sizeof(MmfDesc) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(didx, hidx.data(), sizeof(int) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemset(dst, 0, sizeof(int) * count) == cudaSuccess &&
+             cudaMemcpy(dA, hA.data(), sizeof(float2) * mat * count, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemset(dV, 0, sizeof(float2) * pan * count) == cudaSuccess &&
+             cudaMemset(dW, 0, sizeof(float2) * pan * count) == cudaSuccess;
+        MmfLaunch L = {dd, didx, count, n, st};
+        ok = ok && mmf_launch_hetrd(L, dA, dV, dW, dD, dE, dtau, 1, tc, dst) == cudaSuccess &&
+             cudaStreamSynchronize(st) == cudaSuccess;
+        std::vector<float2> hR((size_t)mat * count);
+        ok = ok && cudaMemcpy(hR.data(), dA, sizeof(float2) * mat * count, cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(hD.data(), dD, sizeof(double) * n * count, cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(hE.data(), dE, sizeof(double) * n * count, cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(htau.data(), dtau, sizeof(float2) * n * count, cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(hst.data(), dst, sizeof(int) * count, cudaMemcpyDeviceToHost) == cudaSuccess;
+        if (ok) {
+            for (int s = 0; s < count; ++s)
+                if (hst[s] != 0) rc = 1;
+            double err = 0.0, ref = 0.0;
+            std::vector<double2> B((size_t)n * n), v(n), y(n);
+            for (int s = 0; s < std::min(count, 2); ++s) {
+                const float2* A0 = hA.data() + s * mat;
+                const float2* R = hR.data() + s * mat;
+                for (int c = 0; c < n; ++c)
+                    for (int r = 0; r < n; ++r) {
+                        const float2 a = A0[r + (int64_t)c * ld];
+                        B[r + (size_t)c * n] = make_double2(a.x, a.y);
+                        ref = std::max(ref, std::hypot((double)a.x, (double)a.y));
+                    }
+                for (int k = 0; k + 1 < n; ++k) {  // B <- P_k^H B P_k, P_k = I - tau v v^H
+                    const float2 tf = htau[(size_t)s * n + k];
+                    const double tr = tf.x, ti = tf.y;
+                    for (int r = 0; r < n; ++r) {
+                        if (r <= k) v[r] = make_double2(0.0, 0.0);
+                        else if (r == k + 1) v[r] = make_double2(1.0, 0.0);
+                        else v[r] = make_double2(R[r + (int64_t)k * ld].x, R[r + (int64_t)k * ld].y);
+                    }
+                    // B <- B P = B - tau (B v) v^H
+                    for (int r = 0; r < n; ++r) {
+                        double yr = 0.0, yi = 0.0;
+                        for (int c = k + 1; c < n; ++c) {
+                            const double2 b = B[r + (size_t)c * n];
+                            yr += b.x * v[c].x - b.y * v[c].y;
+                            yi += b.x * v[c].y + b.y * v[c].x;
+                        }
+                        const double ur = tr * yr - ti * yi, ui = tr * yi + ti * yr;  // tau (B v)_r
+                        for (int c = k + 1; c < n; ++c) {  // - u conj(v_c)
+                            double2& b = B[r + (size_t)c * n];
+                            b.x -= ur * v[c].x + ui * v[c].y;
+                            b.y -= ui * v[c].x - ur * v[c].y;
+                        }
+                    }
+                    // B <- P^H B = B - conj(tau) v (v^H B)
+                    for (int c = 0; c < n; ++c) {
+                        double yr = 0.0, yi = 0.0;
+                        for (int r = k + 1; r < n; ++r) {
+                            const double2 b = B[r + (size_t)c * n];
+                            yr += v[r].x * b.x + v[r].y * b.y;
+                            yi += v[r].x * b.y - v[r].y * b.x;
+                        }
+                        const double ur = tr * yr + ti * yi, ui = tr * yi - ti * yr;  // conj(tau) (v^H B)_c
+                        for (int r = k + 1; r < n; ++r) {
+                            double2& b = B[r + (size_t)c * n];
+                            b.x -= v[r].x * ur - v[r].y * ui;
+                            b.y -= v[r].x * ui + v[r].y * ur;
+                        }
+                    }
+                }
+                for (int c = 0; c < n; ++c)
+                    for (int r = 0; r < n; ++r) {
+                        double2 t = make_double2(0.0, 0.0);
+                        if (r == c) t.x = hD[(size_t)s * n + r];
+                        else if (r == c + 1) t.x = hE[(size_t)s * n + c];
+                        else if (c == r + 1) t.x = hE[(size_t)s * n + r];
+                        const double2 b = B[r + (size_t)c * n];
+                        err = std::max(err, std::hypot(b.x - t.x, b.y - t.y));
+                    }
+            }
+            *max_err = err;
+            *max_ref = ref;
+        }
+    }
+    if (!ok) rc = -4;
+    cudaFree(dd);
+    cudaFree(didx);
+    cudaFree(dst);
+    cudaFree(dA);
+    cudaFree(dV);
+    cudaFree(dW);
+    cudaFree(dtau);
+    cudaFree(dD);
+    cudaFree(dE);
+    cudaStreamDestroy(st);
+    return rc;
 }

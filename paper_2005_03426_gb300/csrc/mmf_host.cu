@@ -59,6 +59,7 @@ struct mmf_ctx {
     int64_t bt_tc_n = -1;            // mixed path: back-transform on the tensor cores from this n on
     int64_t jacobi_sweeps = -1;      // Jacobi sweep cap; -1 = library default
     int64_t band_max = -1;           // largest half-bandwidth reduced by the bulge chase; -1 = default
+    int64_t hetrd_tc = -1;           // mixed path: dense reduction's trailing update on the tensor cores
     cudaEvent_t order_ev = nullptr;  // orders the context stream against callers' streams (*_dev calls)
     std::recursive_mutex mu;
 };
@@ -105,6 +106,7 @@ struct mmf_batch {
     int64_t n_oz = 0;      // BF16 elements of the Gram-product slices (mixed, tensor-core Gram)
     int gram_kernel = 0;   // copied from the context at creation
     int jacobi_sweeps = 40;  // copied from the context at creation
+    int hetrd_tc = 1;        // copied from the context at creation
     int64_t n_pat = 0;
     int* d_pat = nullptr;  // mixed path: nonzero pattern of the coefficient rows
     int64_t n_coef = 0, n_mat = 0, n_vec = 0, n_sq = 0, n_pan = 0, n_t = 0, n_f = 0, n_u = 0,
@@ -336,6 +338,7 @@ extern "C" int mmf_ctx_set_option(mmf_ctx* c, int option, int64_t value) {
         case MMF_OPT_BT_TC_N: c->bt_tc_n = value; return MMF_OK;
         case MMF_OPT_JACOBI_SWEEPS: c->jacobi_sweeps = value; return MMF_OK;
         case MMF_OPT_BAND_MAX: c->band_max = value; return MMF_OK;
+        case MMF_OPT_HETRD_TC: c->hetrd_tc = value; return MMF_OK;
         case MMF_OPT_GRAM_KERNEL:
             if (value > 1) return fail(MMF_ERR_ARG, "MMF_OPT_GRAM_KERNEL: 0 (tensor cores) or 1 (double-FP32)");
             c->gram_kernel = value < 0 ? 0 : value;
@@ -529,6 +532,7 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     b->nt = nt;
     b->gram_kernel = (int)ctx->gram_kernel;
     b->jacobi_sweeps = ctx->jacobi_sweeps < 0 ? 40 : (int)std::max<int64_t>(1, std::min<int64_t>(ctx->jacobi_sweeps, 1000));
+    b->hetrd_tc = ctx->hetrd_tc != 0;
     b->sys.assign(systems, systems + count);
     b->desc.resize(count);
     const int fp32 = precision == MMF_MIXED;
@@ -962,7 +966,9 @@ static int stage_eig(mmf_batch* b) {
         mark(b, ST_HETRD);
         if (!b->medium.empty()) {
             MmfLaunch Lm = launch_of(b, b->medium, b->d_medium, b->nmax_medium);
-            LAUNCH(mmf_launch_hetrd(Lm, b->d_H, b->d_Vp, b->d_Wp, b->d_d, b->d_e, b->d_tau, fp32), 1);
+            LAUNCH(mmf_launch_hetrd(Lm, b->d_H, b->d_Vp, b->d_Wp, b->d_d, b->d_e, b->d_tau, fp32, b->hetrd_tc,
+                                    b->d_status),
+                   1);
         }
         for (int ci = 0; ci < 4; ++ci) {  // banded systems: bulge chase
             if (b->sbr[ci].empty()) continue;
@@ -2096,6 +2102,15 @@ extern "C" int mmf_selftest_split_tf32(int M, int N, int K, int mode, double* ma
     if (!max_rel_err || !max_rel_err_fp32) return fail(MMF_ERR_ARG, "output pointers required");
     int rc = mmf_tf3_selftest_impl(M, N, K, mode, max_rel_err, max_rel_err_fp32);
     if (rc == -1) return fail(MMF_ERR_ARG, "bad self-test sizes or mode");
+    if (rc == -4) return fail(MMF_ERR_CUDA, "self-test CUDA failure");
+    if (rc == 1) return fail(MMF_ST_NOCONV, "tensor-core pipeline wait timed out");
+    return MMF_OK;
+}
+
+extern "C" int mmf_selftest_hetrd(int n, int count, int tensor_cores, double* max_abs_err, double* max_abs_ref) {
+    if (!max_abs_err || !max_abs_ref) return fail(MMF_ERR_ARG, "output pointers required");
+    int rc = mmf_hetrd_selftest_impl(n, count, tensor_cores, max_abs_err, max_abs_ref);
+    if (rc == -1) return fail(MMF_ERR_ARG, "bad self-test sizes");
     if (rc == -4) return fail(MMF_ERR_CUDA, "self-test CUDA failure");
     if (rc == 1) return fail(MMF_ST_NOCONV, "tensor-core pipeline wait timed out");
     return MMF_OK;

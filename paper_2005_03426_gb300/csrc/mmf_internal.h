@@ -207,8 +207,10 @@ struct MmfLaunch {
 cudaError_t mmf_launch_assemble(const MmfLaunch& L, const double2* coef, void* H, int fp32);
 cudaError_t mmf_launch_jacobi(const MmfLaunch& L, void* H, void* Zw, double* E, void* Z,
                               int* status, int fp32, int max_sweeps);
+// tc (FP32 only): the trailing update of each panel on the tensor cores in split TF32; status:
+// per-system status words (a tensor-core wait that gave up sets MMF_ST_NOCONV)
 cudaError_t mmf_launch_hetrd(const MmfLaunch& L, void* H, void* Vp, void* Wp, double* dvec,
-                             double* evec, void* tau, int fp32);
+                             double* evec, void* tau, int fp32, int tc, int* status);
 cudaError_t mmf_launch_tridiag_eig(const MmfLaunch& L, const double* dvec, const double* evec,
                                    double* aux, double* e2, double* E, double* Y, double* work,
                                    int* status, int fp32, int iters);
@@ -325,6 +327,7 @@ __host__ __device__ __forceinline__ int64_t mmf_tf3_floats(int n) {
 }
 int mmf_umma_selftest_impl(int M, int N, int K, int kind, int P, double* max_abs, double* max_ref);
 int mmf_tf3_selftest_impl(int M, int N, int K, int mode, double* max_rel, double* max_rel_fp32);
+int mmf_hetrd_selftest_impl(int n, int count, int tc, double* max_err, double* max_ref);
 
 // Back-transform of the mixed path on the tensor cores (k_bt_tc.cu): reflectors in super-blocks
 // of MMF_BT_SB, each applied as split-TF32 products.  Systems with n >= MMF_BT_TC_NMIN take it.

@@ -42,6 +42,7 @@ MMF_OPT_GRAM_KERNEL = 5
 MMF_OPT_BT_TC_N = 6
 MMF_OPT_JACOBI_SWEEPS = 7
 MMF_OPT_BAND_MAX = 8
+MMF_OPT_HETRD_TC = 9
 MMF_PATH_JACOBI = 0
 MMF_PATH_DENSE = 1
 MMF_PATH_WHOLE_GPU = 2
@@ -137,6 +138,7 @@ _SIGS = {
     "mmf_selftest_tensor_cores": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "mmf_selftest_gram": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "mmf_selftest_split_tf32": (_I, [_I, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "mmf_selftest_hetrd": (_I, [_I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "mmf_strerror": (ctypes.c_char_p, [_I]),
     "mmf_spin_components": (_I, [_I, _P, _P, _I, _P]),
     "mmf_last_error": (ctypes.c_char_p, []),

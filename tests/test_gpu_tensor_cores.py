@@ -55,3 +55,23 @@ def test_split_tf32_products(mode, shape):
     assert rc == 0, M.lib().mmf_last_error()
     print(f"split TF32 {shape} mode {mode}: {err.value:.3e} (sequential FP32 {err32.value:.3e})")
     assert err.value <= 2.0 ** -24 * (8 + k / 16.0)
+
+
+@pytest.mark.parametrize("n,count", [(2, 1), (33, 3), (64, 2), (129, 2), (300, 2), (457, 1), (200, 90)])
+def test_householder_reduction_trailing_update(n, count):
+    """The FP32 Householder reduction with its trailing update (A -= V W^H + W V^H after each
+    32-column panel) on the tensor cores in split TF32 and on the FP32 units: Q^H A Q rebuilt in
+    FP64 from the stored reflectors equals tridiag(e, d, e) within FP32 backward error of the
+    reduction.  Sizes: below one panel, one 64-column block, a ragged 128-row tile, several
+    panels, and 90 systems (one CTA per system instead of two)."""
+    errs = {}
+    for tc in (0, 1):
+        err, ref = ctypes.c_double(), ctypes.c_double()
+        rc = M.lib().mmf_selftest_hetrd(n, count, tc, ctypes.byref(err), ctypes.byref(ref))
+        assert rc == 0, M.lib().mmf_last_error()
+        errs[tc] = err.value / ref.value
+    print(f"n = {n} x {count}: |Q^H A Q - T| / |A| = {errs[0]:.3e} (FP32 units), {errs[1]:.3e} (tensor cores)")
+    for tc in (0, 1):
+        assert errs[tc] <= 2.0 ** -24 * 4 * n
+    # the split-TF32 products carry a few units of FP32 rounding each, as the FP32 units' do
+    assert errs[1] <= 4 * errs[0] + 2.0 ** -24 * 8
