@@ -122,13 +122,17 @@ class Clocks:
 
 
 
-def stage_model(stage: str, n: int, nt: int, mixed: bool):
-    """The bounds of a stage's main kernel for one system: a list of (bound, algorithmic work,
-    peak per second, unit, peak description, kernel).  The roofline reports the bound whose
-    work / peak is largest (the one that limits the kernel).
-    - hetrd: (16/3) n^3 real flops (LAPACK count); the hemv of every column streams the trailing
-      lower triangle, sum_m m^2/2 = n^3/6 complex entries (8 bytes FP32, 16 bytes FP64).
-    - backtransform: 8 n^3 real flops (LAPACK count).
+def stage_model(stage: str, n: int, nt: int, mixed: bool, band: int = 0):
+    """The bounds of a stage's main kernel for one system on its path (band > 0: the band path
+    with half-bandwidth band): a list of (bound, algorithmic work, peak per second, unit, peak
+    description, kernel).  The roofline reports the bound whose work / peak is largest (the one
+    that limits the kernel).
+    - hetrd, dense path: (16/3) n^3 real flops (LAPACK count); the hemv of every column streams
+      the trailing lower triangle, sum_m m^2/2 = n^3/6 complex entries (8 bytes FP32, 16 FP64).
+    - hetrd, band path (the bulge chase): about 6 b^2 complex multiply-adds per step (the
+      one-sided update of the bulge block, the two-sided update of the diagonal block) over
+      n^2 / (2 b) steps = 24 b n^2 real flops.
+    - backtransform: 8 n^3 real flops (LAPACK count), on either path.
     - refine_gram: the tensor-core Gram product by integer slicing, 15 slice pairs x (Re, Im) x
       n x n/2 x 2n multiply-adds x 2 flops = 60 n^3 (lower-triangle tiles) on the BF16 tensor
       cores, against the sustained cuBLAS bf16 rate (the kernel runs inside a long step).
@@ -140,10 +144,14 @@ def stage_model(stage: str, n: int, nt: int, mixed: bool):
     alu = (FP32_ALU_PEAK, "FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived from unit counts and clock)") \
         if mixed else (FP64_ALU_PEAK, "FP64: nominal 1.25 TFLOP/s")
     if stage == "hetrd":
+        if band:
+            return [("alu", 24.0 * band * n ** 2, alu[0], "TFLOP/s", alu[1], "k_sbr_chase")]
         esz = 8.0 if mixed else 16.0
         return [("alu", 16.0 / 3.0 * n ** 3, alu[0], "TFLOP/s", alu[1], "k_hetrd"),
                 ("hbm", esz * n ** 3 / 6.0, hbm, "GB/s", f"copy bandwidth {pk['hbm_gbs']} GB/s {src}", "k_hetrd")]
     if stage == "backtransform":
+        if band:
+            return [("alu", 8.0 * n ** 3, alu[0], "TFLOP/s", alu[1], "k_sbr_bt_f32" if mixed else "k_sbr_bt_f64")]
         return [("alu", 8.0 * n ** 3, alu[0], "TFLOP/s", alu[1],
                  "k_backtransform_f32" if mixed else "k_backtransform")]
     if stage == "refine_gram" and mixed:
@@ -474,9 +482,13 @@ def main():
     systems = [M.System(ctx, p) for p in problems]
     batch = M.Batch(ctx, systems, prec, nt)
     paths = {}
+    sys_band, sys_path = [], []  # each system's path, and its half-bandwidth on the band path (else 0)
     for i in range(batch.count):
-        k = ("jacobi", "dense", "whole_gpu", "band")[batch.path(i)[0]]
+        pth, bnd_i = batch.path(i)
+        k = ("jacobi", "dense", "whole_gpu", "band")[pth]
         paths[k] = paths.get(k, 0) + 1
+        sys_path.append(k)
+        sys_band.append(bnd_i if k == "band" else 0)
     ts = np.stack([W.time_grid(p, nt) for p in problems])
     batch.set_times(0.0, ts)
 
@@ -515,11 +527,19 @@ def main():
     mixed = prec == M.MMF_MIXED
     modelled = {k: v for k, v in per.items() if stage_model(k, n, nt, mixed) is not None}
     dom = max(modelled, key=modelled.get)
-    jac = 118 if mixed else 84  # systems at or below this size take the shared-memory Jacobi path
+    # the reduction and back-transform stages run the kernels of the systems' own paths; the
+    # roofline follows the path most of the batch takes (all systems at the benchmark sizes)
+    hh = [i for i in range(len(problems)) if sys_path[i] != "jacobi"]
+    if dom in ("hetrd", "backtransform"):
+        nband = sum(1 for i in hh if sys_band[i])
+        use_band = nband * 2 > len(hh)
+        members = [i for i in hh if bool(sys_band[i]) == use_band]
+    else:
+        members = list(range(len(problems)))
+    ref_i = members[0] if members else 0
     bounds = []
-    for j, (bnd, _, peak, unit, src, kern) in enumerate(stage_model(dom, n, nt, mixed)):
-        work = sum(stage_model(dom, p.n, nt, mixed)[j][1] for p in problems
-                   if dom not in ("hetrd", "backtransform") or p.n > jac)
+    for j, (bnd, _, peak, unit, src, kern) in enumerate(stage_model(dom, problems[ref_i].n, nt, mixed, sys_band[ref_i])):
+        work = sum(stage_model(dom, problems[i].n, nt, mixed, sys_band[i])[j][1] for i in members)
         bounds.append((work / peak, bnd, work, peak, unit, src, kern))
     _, bnd, work, peak, unit, src, kern = max(bounds)
     achieved = work / (per[dom] / 1e3) if per[dom] > 0 else 0.0
