@@ -37,24 +37,8 @@
 namespace cg = cooperative_groups;
 
 // ------------------------------------------------------------------ reflector store
-// Pass s holds the reflectors of sweeps j = 0 .. n-2-s b (cnt(s) = n-1-s b of them) starting at
-// off(s) = s (n-1) - b s (s-1) / 2.  Reflector (j, s): v at V[(off(s) + j) b + i], i < b (zero
-// beyond its length), tau at T[off(s) + j] with T = V + nref b.
-__host__ __device__ __forceinline__ int64_t sbr_off(int n, int b, int s) {
-    return (int64_t)s * (n - 1) - (int64_t)b * s * (s - 1) / 2;
-}
-__host__ __device__ __forceinline__ int sbr_passes(int n, int b) { return (n - 2) / b + 1; }
-__host__ __device__ __forceinline__ int64_t sbr_nref(int n, int b) { return sbr_off(n, b, sbr_passes(n, b)); }
-
+// (layout and Z's place: sbr_off / sbr_zbase in mmf_internal.h)
 int64_t mmf_sbr_store_elems(int n, int b) { return sbr_nref(n, b) * (b + 1); }
-
-// Row-major Z of the back-transform in the system's inverse-iteration work slot (3 n^2 doubles,
-// free after the tridiagonal solve): from the slot's first 16-byte boundary (the slot starts
-// 8-byte aligned; Z needs at most 2 n^2 doubles plus 8 bytes).
-__device__ __forceinline__ void* sbr_zbase(double* work, const MmfDesc& d) {
-    const uintptr_t p = (uintptr_t)(work + 3 * d.sq_off);
-    return (void*)((p + 15) & ~(uintptr_t)15);
-}
 
 #define SBR_WAIT_LIMIT (1 << 26)
 // bytes before the groups' blocks in dynamic shared memory (progress keys, abort flag), rounded to
@@ -711,6 +695,13 @@ cudaError_t mmf_launch_sbr_chase(const MmfLaunch& L, int bmax, void* H, double2*
         }
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t mmf_launch_sbr_out(const MmfLaunch& L, double* work, float2* Zout) {
+    if (L.count <= 0) return cudaSuccess;
+    const int t = (L.nmax + 31) / 32;
+    k_sbr_out<float><<<dim3(t, t, L.count), 256, 0, L.stream>>>(L.desc, L.idx, work, Zout);
+    return cudaGetLastError();
 }
 
 cudaError_t mmf_launch_sbr_bt(const MmfLaunch& L, int bmax, const double2* store, const double* Y, double* work,

@@ -95,6 +95,10 @@ struct mmf_batch {
     std::vector<int> sbr[4];
     int nmax_sbr[4] = {0, 0, 0, 0};
     int* d_sbr[4] = {nullptr, nullptr, nullptr, nullptr};
+    // band back-transform: per window class on the FP32 / FP64 units ([0..3]), on the tensor cores ([4])
+    std::vector<int> sbt[5];
+    int nmax_sbt[5] = {0, 0, 0, 0, 0};
+    int* d_sbt[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     std::vector<int> rband, rfull;                     // mixed: hybrid / full second refinement step
     std::vector<int> btc, bts;                         // large: back-transform on tensor cores / SIMT
     std::vector<int> btc_n;                            // n of each system in btc
@@ -602,9 +606,13 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
                 cls = mmf_sbr_class(band);
             }
         }
-        // mixed: back-transform on the tensor cores for large enough systems (SIMT otherwise)
+        // mixed: back-transform on the tensor cores for large enough systems (SIMT otherwise); on
+        // the band path for the widest window class when the blocks' T factors fit the work slot
         bool tc = precision == MMF_MIXED && !d.small && !cls && n >= std::max<int64_t>(bt_tc_n(ctx), 3);
         if (rule && rule->bt_tc >= 0) tc = precision == MMF_MIXED && !d.small && !cls && n >= 3 && rule->bt_tc;
+        const bool band_tc_ok = precision == MMF_MIXED && cls == 64;
+        bool band_tc = band_tc_ok && n >= bt_tc_n(ctx);
+        if (rule && rule->bt_tc >= 0) band_tc = band_tc_ok && rule->bt_tc;
         if (precision == MMF_MIXED) {
             // one area per system, used in turn by the back-transform's operands, the Gram slices
             // (BF16) and split-TF32 operands of the refinement, and the time evolution's slices and Phi
@@ -612,13 +620,16 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
             const int64_t ph = (nt > 0 && s->D <= mmf_phi_max_levels() && M <= mmf_ozaki_max_n())
                                    ? mmf_phi_elems((int)n, s->D, (int)M, nt)
                                    : 0;
-            b->n_oz += std::max<int64_t>(std::max<int64_t>(oz, 2 * mmf_tf3_floats((int)n)),
-                                         std::max<int64_t>(tc ? 2 * mmf_bt_floats((int)n) : 0, ph));
+            const int64_t bt = tc ? 2 * mmf_bt_floats((int)n) : band_tc ? mmf_sbt_ops_elems((int)n, d.band) : 0;
+            b->n_oz += std::max<int64_t>(std::max<int64_t>(oz, 2 * mmf_tf3_floats((int)n)), std::max<int64_t>(bt, ph));
         }
         if (cls) {
             const int ci = cls == 8 ? 0 : cls == 16 ? 1 : cls == 32 ? 2 : 3;
             b->sbr[ci].push_back(i);
             b->nmax_sbr[ci] = std::max(b->nmax_sbr[ci], (int)n);
+            const int bi = band_tc ? 4 : ci;
+            b->sbt[bi].push_back(i);
+            b->nmax_sbt[bi] = std::max(b->nmax_sbt[bi], (int)n);
         } else if (!d.small) {
             (tc ? b->btc : b->bts).push_back(i);
             if (tc) {
@@ -665,7 +676,8 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     size_t o_all = p.take(sizeof(int) * count), o_small = p.take(sizeof(int) * count),
            o_large = p.take(sizeof(int) * count), o_medium = p.take(sizeof(int) * count),
            o_status = p.take(sizeof(int) * count), o_rband = p.take(sizeof(int) * count),
-           o_rfull = p.take(sizeof(int) * count), o_sbr = p.take(sizeof(int) * count), o_btc = p.take(sizeof(int) * count),
+           o_rfull = p.take(sizeof(int) * count), o_sbr = p.take(sizeof(int) * count), o_sbt = p.take(sizeof(int) * count),
+           o_btc = p.take(sizeof(int) * count),
            o_bts = p.take(sizeof(int) * count);
     size_t o_coef = p.take(sizeof(double2) * b->n_coef);
     size_t o_H = p.take(cs * b->n_mat);
@@ -743,6 +755,11 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
             b->d_sbr[ci] = q;
             q += b->sbr[ci].size();
         }
+        int* qt = (int*)(B + o_sbt);
+        for (int ci = 0; ci < 5; ++ci) {
+            b->d_sbt[ci] = qt;
+            qt += b->sbt[ci].size();
+        }
     }
     if (!b->btc.empty()) b->d_btjobs = B + o_btjobs;
     b->d_coef = (double2*)(B + o_coef);
@@ -813,6 +830,10 @@ static int batch_create(mmf_ctx* ctx, int count, mmf_sys* const* systems, int pr
     for (int ci = 0; ci < 4; ++ci)
         if (e == cudaSuccess && !b->sbr[ci].empty())
             e = cudaMemcpyAsync(b->d_sbr[ci], b->sbr[ci].data(), sizeof(int) * b->sbr[ci].size(),
+                                cudaMemcpyHostToDevice, st);
+    for (int ci = 0; ci < 5; ++ci)
+        if (e == cudaSuccess && !b->sbt[ci].empty())
+            e = cudaMemcpyAsync(b->d_sbt[ci], b->sbt[ci].data(), sizeof(int) * b->sbt[ci].size(),
                                 cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !b->bts.empty())
         e = cudaMemcpyAsync(b->d_bts, b->bts.data(), sizeof(int) * b->bts.size(), cudaMemcpyHostToDevice, st);
@@ -1000,9 +1021,13 @@ static int stage_eig(mmf_batch* b) {
             g_launches += nl;
         }
         for (int ci = 0; ci < 4; ++ci) {  // banded systems: Z = Q Y from the chase's reflectors
-            if (b->sbr[ci].empty()) continue;
-            MmfLaunch Lb = launch_of(b, b->sbr[ci], b->d_sbr[ci], b->nmax_sbr[ci]);
+            if (b->sbt[ci].empty()) continue;
+            MmfLaunch Lb = launch_of(b, b->sbt[ci], b->d_sbt[ci], b->nmax_sbt[ci]);
             LAUNCH(mmf_launch_sbr_bt(Lb, 8 << ci, b->d_Zf, b->d_Y, b->d_work, b->d_Zp, fp32), 2);
+        }
+        if (!b->sbt[4].empty()) {  // the same on the tensor cores (T factors, products, transpose)
+            MmfLaunch Lt = launch_of(b, b->sbt[4], b->d_sbt[4], b->nmax_sbt[4]);
+            LAUNCH(mmf_launch_sbr_bt_tc(Lt, b->d_Zf, b->d_Y, b->d_work, b->d_oz, (float2*)b->d_Zp, b->d_status), 3);
         }
         if (fp32) LAUNCH(mmf_launch_widen(Ll, b->d_Zp, b->d_Zf, fp32), 1);
     } else {

@@ -196,6 +196,24 @@ __device__ __forceinline__ double2 df_value(const DF& re, const DF& im) {
 
 // ------------------------------------------------------------------ kernel launchers
 // Every launcher takes the device descriptor array and a device list of system indices.
+// ------------------------------------------------------------------ band path: reflector store
+// Pass s of the bulge chase holds the reflectors of sweeps j = 0 .. n-2-s b (n-1-s b of them)
+// starting at off(s) = s (n-1) - b s (s-1) / 2.  Reflector (j, s): v at V[(off(s) + j) b + i],
+// i < b (zero beyond its length), tau at T[off(s) + j] with T = V + nref b; it acts on rows
+// j + 1 + s b .. j + s b + b.
+__host__ __device__ __forceinline__ int64_t sbr_off(int n, int b, int s) {
+    return (int64_t)s * (n - 1) - (int64_t)b * s * (s - 1) / 2;
+}
+__host__ __device__ __forceinline__ int sbr_passes(int n, int b) { return (n - 2) / b + 1; }
+__host__ __device__ __forceinline__ int64_t sbr_nref(int n, int b) { return sbr_off(n, b, sbr_passes(n, b)); }
+// Row-major Z of the band back-transform in the system's inverse-iteration work slot (3 n^2
+// doubles from work + 3 sq_off, free after the tridiagonal solve): from the slot's first 16-byte
+// boundary (the slot starts 8-byte aligned; Z needs at most 2 n^2 doubles plus 8 bytes).
+__device__ __forceinline__ void* sbr_zbase(double* work, const MmfDesc& d) {
+    const uintptr_t p = (uintptr_t)(work + 3 * d.sq_off);
+    return (void*)((p + 15) & ~(uintptr_t)15);
+}
+
 struct MmfLaunch {
     const MmfDesc* desc;     // device
     const int* idx;          // device: systems in this launch
@@ -230,6 +248,16 @@ cudaError_t mmf_launch_sbr_chase(const MmfLaunch& L, int bmax, void* H, double2*
                                  int* status, int fp32);
 cudaError_t mmf_launch_sbr_bt(const MmfLaunch& L, int bmax, const double2* store, const double* Y, double* work,
                               void* Zout, int fp32);
+// Z (row-major FP32, work slot) -> column-major FP32 output (mixed path)
+cudaError_t mmf_launch_sbr_out(const MmfLaunch& L, double* work, float2* Zout);
+// Band back-transform on the tensor cores (mixed path, half-bandwidth 33..64): per block of 64
+// sweeps its compact-WY factors and both products' B operands into the system's operand area
+// (pool + oz_off BF16 units, mmf_sbt_ops_elems), then one CTA per (system, 128 columns of Z)
+// applying the blocks as split-TF32 products, then the transpose to Zout.  A tensor-core wait that
+// gives up sets the system's status word to MMF_ST_NOCONV.
+cudaError_t mmf_launch_sbr_bt_tc(const MmfLaunch& L, const double2* store, const double* Y, double* work, void* pool,
+                                 float2* Zout, int* status);
+int64_t mmf_sbt_ops_elems(int n, int b);  // operand-area size (BF16 units) of a system's blocks
 // dressed basis (k_dressed.cu): zone representatives of the dressing batch, U_F at t1 and the
 // full batch's times, and Ud = U_F(t2)^dagger U(t2, t1) U_F(t1) per time
 cudaError_t mmf_launch_dressed(const MmfDesc* ddesc, const MmfDesc* fdesc, int count, int nmax_d, int Dmax,

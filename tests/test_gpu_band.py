@@ -108,3 +108,39 @@ def test_band_limit_option():
     assert M.Batch(ctx, [M.System(ctx, p)], M.MMF_FP64, 2).path(0) == (M.MMF_PATH_DENSE, 0)
     ctx.set_option(M.MMF_OPT_BAND_MAX, 64)
     assert M.Batch(ctx, [M.System(ctx, p)], M.MMF_MIXED, 2).path(0) == (M.MMF_PATH_BAND, 33)
+
+
+# the mixed band path's back-transform for half-bandwidths 33..64: on the tensor cores (blocks of
+# 64 sweeps in compact WY form, split-TF32 products) from n = MMF_OPT_BT_TC_N on, FP32 units below
+SIMT_ONLY = 1 << 40
+TC_CASES = {
+    "random_D4_h9_b39_n100": (lambda: W.random_small(5, D=4, Ns=[12], nharm=[9]), 39),
+    "random_D3_h12_b38_n183": (lambda: W.random_small(11, D=3, Ns=[30], nharm=[12]), 38),
+    "spin1_b33": CASES["spin1_b33"],
+    "spin1_b63": CASES["spin1_b63"],
+}
+
+
+@pytest.mark.parametrize("bt_tc_n", [0, SIMT_ONLY])
+@pytest.mark.parametrize("name", sorted(TC_CASES))
+def test_band_backtransform_units_match_oracle(name, bt_tc_n):
+    """Both units forced: one 128-column slab with partial blocks (n = 100), a ragged second slab
+    (n = 183), several slabs and up to 13 passes (n = 429, 567); against the oracle."""
+    p, band = TC_CASES[name][0](), TC_CASES[name][1]
+    nt = 8
+    t = W.time_grid(p, nt)
+    ref = _oracle(name, p, t)
+    ctx = _band_ctx()
+    ctx.set_option(M.MMF_OPT_BT_TC_N, bt_tc_n)
+    ctx.set_option(M.MMF_OPT_JACOBI_N_MIXED, 4)  # n = 100 would take the shared-memory Jacobi kernel
+    b, st, res = _solve(ctx, [p], M.MMF_MIXED, nt)
+    assert b.path(0) == (M.MMF_PATH_BAND, band)
+    assert st[0] == 0
+    e, u, pp = res[0]
+    e_rel, up = TOL[M.MMF_MIXED]
+    assert np.abs(e - ref["E"]).max() <= e_rel * np.abs(ref["E"]).max()
+    assert np.abs(u - ref["U"]).max() <= up
+    assert np.abs(pp - ref["P"]).max() <= up
+    Z = b.eigenvectors(0)
+    HF = O.build_hf(p)
+    assert np.abs(HF @ Z - Z * e[None, :]).max() <= e_rel * np.abs(e).max()
