@@ -71,8 +71,8 @@ __device__ __forceinline__ void sbt_put4(float* hi, float* lo, int off, float x0
 
 // ------------------------------------------------------------------ per-block operands
 // One CTA per block: V's 64 columns (v_c[t], zero past b and past the block's sweeps), the Gram
-// entries G(m, c) = v_m^H v_c of the staircase (nonzero for 0 < c - m < b), the recurrence for T
-// column by column, then both products' B operands (FP32 arithmetic: the products that use them
+// entries G(m, c) = v_m^H v_c of the staircase (nonzero for 0 < c - m < b), T, then both
+// products' B operands (FP32 arithmetic: the products that use them
 // have FP32 accuracy): (1) from V(i, j) = Vs[j][i - j], (2) from Y(i, j) = sum_{k <= j} V(i, k)
 // T(k, j).  Each thread writes float4 groups (four consecutive K' entries of one row) of both
 // pieces at their swizzled places.
@@ -121,18 +121,38 @@ __global__ void __launch_bounds__(256) k_sbr_wy(const MmfDesc* __restrict__ desc
         Gs[m][c] = make_float2(gr, gi);
     }
     __syncthreads();
-    for (int c = 0; c < nbk; ++c) {
-        const float2 tc = tau_s[c];
-        if (tid < c) {
-            float ar = 0.f, ai = 0.f;
-            for (int m = tid; m < c; ++m) {
-                const float2 t = Ts[tid][m], gg = Gs[m][c];
-                ar = fmaf(t.x, gg.x, fmaf(-t.y, gg.y, ar));
-                ai = fmaf(t.x, gg.y, fmaf(t.y, gg.x, ai));
+    // T by merging compact-WY factors of adjacent groups (1, 2, 4, ... 32 columns): for groups A
+    // (columns a .. a+h-1) and B (a+h .. a+2h-1), the product of their reflectors has
+    //     T = [[T_A, -T_A G_AB T_B], [0, T_B]],   G_AB = V_A^H V_B,
+    // which is the column recurrence taken h columns at a time (it holds for any tau, including
+    // the zeros of the block's missing sweeps).  P = G_AB T_B goes to T's free lower triangle
+    // (P(i, j) at Ts[j][i], i < j) between the two steps.
+    if (tid < 64) Ts[tid][tid] = tau_s[tid];
+    __syncthreads();
+    for (int h = 1; h < 64; h *= 2) {
+        for (int e = tid; e < 32 * h; e += 256) {  // (64 / 2h) group pairs x h x h entries
+            const int pr = e / (h * h), rem = e - pr * h * h, ii = rem / h, jj = rem - ii * h;
+            const int a = 2 * h * pr, i = a + ii, j = a + h + jj;
+            float pr_ = 0.f, pi_ = 0.f;
+            for (int m = a + h; m <= j; ++m) {  // T_B upper triangular
+                const float2 gg = Gs[i][m], t = Ts[m][j];
+                pr_ = fmaf(gg.x, t.x, fmaf(-gg.y, t.y, pr_));
+                pi_ = fmaf(gg.x, t.y, fmaf(gg.y, t.x, pi_));
             }
-            Ts[tid][c] = make_float2(-(tc.x * ar - tc.y * ai), -(tc.x * ai + tc.y * ar));
+            Ts[j][i] = make_float2(pr_, pi_);
         }
-        if (tid == 0) Ts[c][c] = tc;
+        __syncthreads();
+        for (int e = tid; e < 32 * h; e += 256) {
+            const int pr = e / (h * h), rem = e - pr * h * h, ii = rem / h, jj = rem - ii * h;
+            const int a = 2 * h * pr, i = a + ii, j = a + h + jj;
+            float tr = 0.f, ti = 0.f;
+            for (int l = i; l < a + h; ++l) {  // T_A upper triangular
+                const float2 t = Ts[i][l], pp = Ts[j][l];
+                tr = fmaf(t.x, pp.x, fmaf(-t.y, pp.y, tr));
+                ti = fmaf(t.x, pp.y, fmaf(t.y, pp.x, ti));
+            }
+            Ts[i][j] = make_float2(-tr, -ti);
+        }
         __syncthreads();
     }
     float* ops = sbt_ops(pool, d) + (pre + g) * (int64_t)SBT_OPS_FLOATS;
