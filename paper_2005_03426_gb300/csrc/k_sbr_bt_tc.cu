@@ -189,17 +189,29 @@ __global__ void __launch_bounds__(256) k_sbr_wy(const MmfDesc* __restrict__ desc
 }
 
 // ------------------------------------------------------------------ back-transform
-// Shared memory: a ring of two A slots (the two pieces of a chunk's A operand, 2 x 16 KB each)
-// and a ring of four B slots of 32 KB.  A product-(1) chunk's B takes one slot (its two 16 KB
-// pieces); a product-(2) chunk's B takes two (one 32 KB piece each).  A producer warp fills B
-// slots ahead with bulk copies (counted on the slot's full barrier) as soon as the products that
-// read them last have committed (the slot's free barrier); the eight builder warps fill the A slot
-// and one of their threads issues the chunk's products.  The builders synchronise among
-// themselves with named barrier 1 (256 threads), so the producer never waits on them.
+// Warps: eight builders (the A operands and the epilogue), one producer (the B operands by bulk
+// copies) and one MMA warp.  Shared memory: a ring of two A slots (a chunk's two A pieces,
+// 2 x 16 KB) and a ring of four B slots of 32 KB; a product-(1) chunk's B takes one slot (its two
+// 16 KB pieces), a product-(2) chunk's B two (one 32 KB piece each).  mbarriers: A slot full
+// (one arrival per builder warp, after each thread's proxy fence) and free (the MMA warp's
+// commit), B slot full (the copies' byte count) and free (commit), and one per product done
+// (commit).  The builders proceed in order (block by block: product (1)'s A, product (2)'s A
+// from TMEM, the epilogue), so an A-full arrival also tells the MMA warp that their earlier TMEM
+// reads are complete: product (1) accumulates in columns 256..511 and product (2) in 0..255, and
+// a block's products overwrite them only after the builders have moved past the reads.  The
+// builders meet at one named barrier per block (the next window shares rows with this one).
 #define SBT_ASLOT 32768u
 #define SBT_BSLOT 32768u
 #define SBT_BSLOTS 4
-#define SBT_CTA (SBT_THREADS + 32)  // builders + the producer warp
+#define SBT_CTA (SBT_THREADS + 64)  // builders + producer warp + MMA warp
+// barrier indices
+#define SB_AFULL 0   // [2]
+#define SB_AFREE 2   // [2]
+#define SB_BFULL 4   // [4]
+#define SB_BFREE 8   // [4]
+#define SB_ACC1 12
+#define SB_ACC2 13
+#define SB_NBAR 14
 
 __device__ __forceinline__ void sbt_ld16(uint32_t ta, uint32_t* v) {
     asm volatile(
@@ -208,105 +220,38 @@ __device__ __forceinline__ void sbt_ld16(uint32_t ta, uint32_t* v) {
           "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
         : "r"(ta));
 }
-// named barrier 1 over the 256 builder threads; returns the AND of pred over them
-__device__ __forceinline__ bool sbt_bar_and(bool pred) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)(pred ? 1 : 0))
-        : "memory");
-    return r != 0;
-}
 __device__ __forceinline__ void sbt_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
-
-struct SbtSched {        // position in the chunk sequence: per block 8 chunks of (1), 4 of (2)
-    uint32_t bslot;       // B slots used so far (ring position)
-};
-// B slot of a chunk's piece: (1) one slot per chunk; (2) two (piece 0 hi, piece 1 lo)
-__device__ __forceinline__ uint32_t sbt_slot(uint32_t pos) { return pos % SBT_BSLOTS; }
-
-struct SbtPipe {
-    unsigned char* a;   // two A slots
-    unsigned char* b;   // four B slots
-    uint64_t* bar;      // [0..1] A slot free, [2..5] B slot free, [6..9] B slot full, [10] product done
-    uint32_t tmem;
-    uint32_t aused[2], await_[2], pacc, chunk, bpos;  // builders' view
-};
-
-// builders: wait (this thread) until A slot s is free
-__device__ __forceinline__ bool sbt_aslot_free(SbtPipe& P, int s) {
-    if (P.aused[s] <= P.await_[s]) return true;
-    const bool ok = mbar_wait(&P.bar[s], P.await_[s] & 1u);
-    ++P.await_[s];
-    return ok;
+__device__ __forceinline__ void sbt_commit(uint64_t* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
+                 : "memory");
 }
 
-// after a chunk's A pieces are in A slot s: make them visible to the tensor cores; one thread
-// waits for the chunk's B slots and issues its 12 products (M = 128, N = 128 or 256) into dacc,
-// then commits them to the A slot's and the B slots' free barriers (and to bar[10] if last).
-__device__ __forceinline__ bool sbt_issue(SbtPipe& P, int s, int nb, uint32_t dacc, uint32_t N, bool first, bool last,
-                                          bool ok, volatile int* fail) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    ok = sbt_bar_and(ok && !*fail);
-    if (ok && threadIdx.x == 0) {
-        const uint32_t s0 = sbt_slot(P.bpos), s1 = sbt_slot(P.bpos + 1);
-        const uint32_t u0 = P.bpos / SBT_BSLOTS, u1 = (P.bpos + 1) / SBT_BSLOTS;  // fills of the slots so far
-        bool got = mbar_wait(&P.bar[6 + s0], u0 & 1u);
-        if (nb == 2) got = got && mbar_wait(&P.bar[6 + s1], u1 & 1u);
-        if (!got) {
-            *fail = 1;
-        } else {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = smem_u32(P.a + s * SBT_ASLOT);
-            const uint32_t sb0 = smem_u32(P.b + s0 * SBT_BSLOT), sb1 = smem_u32(P.b + s1 * SBT_BSLOT);
-            const uint64_t a1 = umma_desc(sa), a2 = umma_desc(sa + 16384u);
-            const uint64_t b1 = umma_desc(sb0), b2 = umma_desc(nb == 2 ? sb1 : sb0 + 16384u);
-            const uint32_t idesc = umma_idesc_mn(2, 128u, N);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint64_t adv = (uint64_t)((q * 32) >> 4);
-                const uint64_t pa[3] = {a1, a1, a2}, pb[3] = {b1, b2, b1};
-#pragma unroll
-                for (int pp = 0; pp < 3; ++pp) {
-                    const uint32_t accf = (!first || q > 0 || pp > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
-                        "l"(pa[pp] + adv), "l"(pb[pp] + adv), "r"(idesc), "r"(accf)
-                        : "memory");
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&P.bar[s]))
-                         : "memory");
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&P.bar[2 + s0]))
-                         : "memory");
-            if (nb == 2)
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_u32(&P.bar[2 + s1]))
-                             : "memory");
-            if (last)
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_u32(&P.bar[10]))
-                             : "memory");
-        }
+// bounded wait that also gives up once the CTA has failed
+__device__ __forceinline__ bool sbt_wait(uint64_t* bar, uint32_t parity, volatile int* fail) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < UM_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 255u) == 255u && *fail) return false;
     }
-    ++P.aused[s];
-    P.bpos += nb;
-    ++P.chunk;
-    return ok;
+    *fail = 1;
+    return false;
 }
 
-// all of a product's chunks done: its accumulators may be read
-__device__ __forceinline__ bool sbt_product_done(SbtPipe& P, volatile int* fail) {
-    bool ok = !*fail && mbar_wait(&P.bar[10], P.pacc);
-    ok = sbt_bar_and(ok);
-    P.pacc ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    return ok;
+// a builder warp has written its part of A slot s: each thread fences its stores for the async
+// proxy (and orders its earlier TMEM reads), then one arrival per warp
+__device__ __forceinline__ void sbt_arrive_a(uint64_t* bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // loads of one product-(1) chunk's A values: column c, window rows 16 q + 8 hh .. + 7
@@ -330,13 +275,13 @@ __device__ __forceinline__ void sbt_load_part(float2* zo, const float2* __restri
 
 // A operand chunk q (K' entries 32 q .. 32 q + 31) from the sum of product (1)'s two TMEM
 // accumulators: warp w holds TMEM lanes (rows) 32 (w % 4) .. +31 and K' half w / 4.
-__device__ __forceinline__ void sbt_a_from_tmem(const SbtPipe& P, float* ahi, float* alo, int q) {
+__device__ __forceinline__ void sbt_a_from_tmem(uint32_t tmem, float* ahi, float* alo, int q) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = 32 * (warp & 3) + lane, h = warp >> 2;
     const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
     uint32_t u[16], v[16];
-    sbt_ld16(P.tmem + lanes + 256u + 32u * q + 16u * h, u);
-    sbt_ld16(P.tmem + lanes + 384u + 32u * q + 16u * h, v);
+    sbt_ld16(tmem + lanes + 256u + 32u * q + 16u * h, u);
+    sbt_ld16(tmem + lanes + 384u + 32u * q + 16u * h, v);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -344,33 +289,25 @@ __device__ __forceinline__ void sbt_a_from_tmem(const SbtPipe& P, float* ahi, fl
                  __uint_as_float(u[4 * k + 1]) + __uint_as_float(v[4 * k + 1]),
                  __uint_as_float(u[4 * k + 2]) + __uint_as_float(v[4 * k + 2]),
                  __uint_as_float(u[4 * k + 3]) + __uint_as_float(v[4 * k + 3]));
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 
-// bounded wait that also gives up once the CTA has failed
-__device__ __forceinline__ bool sbt_wait(uint64_t* bar, uint32_t parity, volatile int* fail) {
-    const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < UM_WAIT_LIMIT; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if ((it & 255u) == 255u && *fail) return false;
-    }
-    *fail = 1;
-    return false;
+// window of pass s, block g
+struct SbtWin {
+    int R0, nrows;
+};
+__device__ __forceinline__ SbtWin sbt_win(int n, int b, int s, int g) {
+    const int jhi = n - 2 - s * b - SBT_NB * g, jlo = max(0, jhi - (SBT_NB - 1));
+    SbtWin w;
+    w.R0 = jlo + 1 + s * b;
+    w.nrows = min(jhi - jlo + b, n - w.R0);  // rows the block changes
+    return w;
 }
 
 __global__ void __launch_bounds__(SBT_CTA, 1) k_sbr_bt_tc(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
                                                         void* __restrict__ pool, const double* __restrict__ Yg,
                                                         double* __restrict__ work, int* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char sbt_smem[];
-    __shared__ uint64_t bar[11];
+    __shared__ uint64_t bar[SB_NBAR];
     __shared__ uint32_t tmem_s;
     __shared__ int fail_s;
     const int sid = idx[blockIdx.y];
@@ -380,9 +317,20 @@ __global__ void __launch_bounds__(SBT_CTA, 1) k_sbr_bt_tc(const MmfDesc* __restr
     if (c0 >= n) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* base = (unsigned char*)(((uintptr_t)sbt_smem + 1023) & ~(uintptr_t)1023);
+    unsigned char* As = base;
+    unsigned char* Bs = base + 2 * SBT_ASLOT;
     volatile int* fail = &fail_s;
     if (tid == 0) {
-        for (int q = 0; q < 11; ++q) mbar_init(&bar[q], 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&bar[SB_AFULL + q], SBT_THREADS / 32);  // one arrival per builder warp
+            mbar_init(&bar[SB_AFREE + q], 1);
+        }
+        for (int q = 0; q < SBT_BSLOTS; ++q) {
+            mbar_init(&bar[SB_BFULL + q], 1);
+            mbar_init(&bar[SB_BFREE + q], 1);
+        }
+        mbar_init(&bar[SB_ACC1], 1);
+        mbar_init(&bar[SB_ACC2], 1);
         fail_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -395,13 +343,14 @@ __global__ void __launch_bounds__(SBT_CTA, 1) k_sbr_bt_tc(const MmfDesc* __restr
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_s;
     const int np = sbr_passes(n, b);
     const float* ops_all = sbt_ops(pool, d);
-    bool ok = true;
 
     if (warp == SBT_THREADS / 32) {
-        // producer: the B pieces of every chunk, in the builders' order, as slots free up
+        // producer: the B pieces of every chunk, in the products' order, as slots free up
         if (lane == 0) {
+            bool ok = true;
             uint32_t pos = 0;
             int64_t blk = 0;
             for (int s = 0; s < np && ok; ++s) {
@@ -411,48 +360,85 @@ __global__ void __launch_bounds__(SBT_CTA, 1) k_sbr_bt_tc(const MmfDesc* __restr
                     for (int q = 0; q < 12 && ok; ++q) {
                         const int nsl = q < 8 ? 1 : 2;
                         for (int k = 0; k < nsl && ok; ++k, ++pos) {
-                            const uint32_t sl = sbt_slot(pos), use = pos / SBT_BSLOTS;
-                            if (use > 0 && !(ok = sbt_wait(&bar[2 + sl], (use - 1) & 1u, fail))) break;
-                            const uint32_t fb = smem_u32(&bar[6 + sl]);
-                            const uint32_t dst = smem_u32(base + 2 * SBT_ASLOT + sl * SBT_BSLOT);
+                            const uint32_t sl = pos % SBT_BSLOTS, use = pos / SBT_BSLOTS;
+                            if (use > 0 && !(ok = sbt_wait(&bar[SB_BFREE + sl], (use - 1) & 1u, fail))) break;
+                            const uint32_t fb = smem_u32(&bar[SB_BFULL + sl]);
+                            const uint32_t dst = smem_u32(Bs + sl * SBT_BSLOT);
                             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(SBT_BSLOT)
                                          : "memory");
                             // (1): the chunk's two 16 KB pieces in one slot; (2): piece k, 32 KB
                             const float* src = q < 8 ? ops + (int64_t)(2 * q) * 4096
                                                      : ops + SBT_B1_FLOATS + (int64_t)(2 * (q - 8) + k) * 8192;
-                            if (q < 8) {
-                                asm volatile(
-                                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                                        dst),
-                                    "l"(src), "r"(16384u), "r"(fb)
-                                    : "memory");
+                            const uint32_t part = q < 8 ? 16384u : 32768u;
+                            asm volatile(
+                                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                    dst),
+                                "l"(src), "r"(part), "r"(fb)
+                                : "memory");
+                            if (q < 8)
                                 asm volatile(
                                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                                         dst + 16384u),
                                     "l"(src + 4096), "r"(16384u), "r"(fb)
                                     : "memory");
-                            } else {
-                                asm volatile(
-                                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                                        dst),
-                                    "l"(src), "r"(32768u), "r"(fb)
-                                    : "memory");
-                            }
                         }
                     }
                 }
             }
         }
+    } else if (warp == SBT_THREADS / 32 + 1) {
+        // MMA warp: each chunk's 12 products once its A and B pieces are in
+        if (lane == 0) {
+            bool ok = true;
+            uint32_t chunk = 0, pos = 0;
+            for (int s = 0; s < np && ok; ++s) {
+                const int nbs = sbt_nblk(n, b, s);
+                for (int g = 0; g < nbs && ok; ++g) {
+                    for (int q = 0; q < 12 && ok; ++q, ++chunk) {
+                        const int nb = q < 8 ? 1 : 2;
+                        const uint32_t sl = chunk & 1u, s0 = pos % SBT_BSLOTS, s1 = (pos + 1) % SBT_BSLOTS;
+                        ok = sbt_wait(&bar[SB_AFULL + sl], (chunk >> 1) & 1u, fail) &&
+                             sbt_wait(&bar[SB_BFULL + s0], (pos / SBT_BSLOTS) & 1u, fail) &&
+                             (nb == 1 || sbt_wait(&bar[SB_BFULL + s1], ((pos + 1) / SBT_BSLOTS) & 1u, fail));
+                        if (!ok) break;
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t sa = smem_u32(As + sl * SBT_ASLOT);
+                        const uint32_t sb0 = smem_u32(Bs + s0 * SBT_BSLOT), sb1 = smem_u32(Bs + s1 * SBT_BSLOT);
+                        const uint64_t a1 = umma_desc(sa), a2 = umma_desc(sa + 16384u);
+                        const uint64_t b1 = umma_desc(sb0), b2 = umma_desc(nb == 2 ? sb1 : sb0 + 16384u);
+                        const uint32_t N = q < 8 ? 128u : 256u;
+                        const uint32_t idesc = umma_idesc_mn(2, 128u, N);
+                        const uint32_t dacc = q < 8 ? tmem + 256u + 128u * (uint32_t)(q >> 2) : tmem;
+                        const bool first = q < 8 ? (q & 3) == 0 : q == 8;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t adv = (uint64_t)((kk * 32) >> 4);
+                            const uint64_t pa[3] = {a1, a1, a2}, pb[3] = {b1, b2, b1};
+#pragma unroll
+                            for (int pp = 0; pp < 3; ++pp) {
+                                const uint32_t accf = (!first || kk > 0 || pp > 0) ? 1u : 0u;
+                                asm volatile(
+                                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
+                                    "l"(pa[pp] + adv), "l"(pb[pp] + adv), "r"(idesc), "r"(accf)
+                                    : "memory");
+                            }
+                        }
+                        sbt_commit(&bar[SB_AFREE + sl]);
+                        sbt_commit(&bar[SB_BFREE + s0]);
+                        if (nb == 2) sbt_commit(&bar[SB_BFREE + s1]);
+                        if (q == 7) sbt_commit(&bar[SB_ACC1]);
+                        if (q == 11) sbt_commit(&bar[SB_ACC2]);
+                        pos += nb;
+                    }
+                }
+            }
+        }
     } else {
-        SbtPipe P = {};
-        P.a = base;
-        P.b = base + 2 * SBT_ASLOT;
-        P.bar = bar;
-        P.tmem = tmem_s;
+        // builders
         const double* Y = Yg + d.sq_off;
         float2* Z = reinterpret_cast<float2*>(sbr_zbase(work, d));
-        // Z = Y on this slab (every row; row 0 is touched by no reflector)
-        {
+        {  // Z = Y on this slab (every row; row 0 is touched by no reflector)
             const int c = c0 + (tid & 127);
             if (c < n)
                 for (int r = tid >> 7; r < n; r += SBT_THREADS / 128)
@@ -460,81 +446,90 @@ __global__ void __launch_bounds__(SBT_CTA, 1) k_sbr_bt_tc(const MmfDesc* __restr
         }
         sbt_bar();
         const int r = tid & 127, hh = tid >> 7;  // product (1): A row r = slab column c0 + r, rows half hh
-        for (int s = 0; s < np && ok; ++s) {
+        const int c = c0 + 32 * (warp & 3) + lane, h = warp >> 2;  // epilogue: column, window rows 64 h ..
+        uint32_t chunk = 0, pacc = 0;
+        float2 z[8];
+        bool zpre = false;
+        bool stop = false;
+        for (int s = 0; s < np && !stop; ++s) {
             const int nbs = sbt_nblk(n, b, s);
-            for (int g = 0; g < nbs && ok; ++g) {
-                const int jhi = n - 2 - s * b - SBT_NB * g, jlo = max(0, jhi - (SBT_NB - 1));
-                const int R0 = jlo + 1 + s * b, nrows = min(jhi - jlo + b, n - R0);  // window rows changed
-
+            for (int g = 0; g < nbs && !stop; ++g) {
+                const SbtWin W = sbt_win(n, b, s, g);
+                if (!zpre) sbt_load_z(z, Z, n, W.R0, W.nrows, c0 + r, 0, hh);
                 // (1) W^T = Z_R^T conj(V): 8 chunks of 16 window rows
-                float2 z[8];
-                sbt_load_z(z, Z, n, R0, nrows, c0 + r, 0, hh);
-                for (int q = 0; q < 8 && ok; ++q) {
-                    const int s_ = (int)(P.chunk & 1u);
-                    const bool w = sbt_aslot_free(P, s_);
-                    float* ahi = reinterpret_cast<float*>(P.a + s_ * SBT_ASLOT);
+                for (int q = 0; q < 8; ++q, ++chunk) {
+                    const uint32_t sl = chunk & 1u, use = chunk >> 1;
+                    if (use > 0) (void)sbt_wait(&bar[SB_AFREE + sl], (use - 1) & 1u, fail);
+                    float* ahi = reinterpret_cast<float*>(As + sl * SBT_ASLOT);
                     float* alo = ahi + 4096;
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         sbt_put4(ahi, alo, sbt_swz(r, 4 * hh + k), z[2 * k].x, z[2 * k].y, z[2 * k + 1].x,
                                  z[2 * k + 1].y);
-                    if (q < 7) sbt_load_z(z, Z, n, R0, nrows, c0 + r, q + 1, hh);  // in flight meanwhile
-                    ok = sbt_issue(P, s_, 1, P.tmem + 256u + 128u * (uint32_t)(q >> 2), 128u, (q & 3) == 0, q == 7, w,
-                                   fail);
+                    if (q < 7) sbt_load_z(z, Z, n, W.R0, W.nrows, c0 + r, q + 1, hh);  // in flight meanwhile
+                    sbt_arrive_a(&bar[SB_AFULL + sl]);
                 }
-                if (!ok || !(ok = sbt_product_done(P, fail))) break;
-
+                (void)sbt_wait(&bar[SB_ACC1], pacc, fail);
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 // (2) Z_R^T -= W^T Y^T (N = 256: 128 window rows, Re and Im): 4 chunks of 16 j
-                for (int q = 0; q < 4 && ok; ++q) {
-                    const int s_ = (int)(P.chunk & 1u);
-                    const bool w = sbt_aslot_free(P, s_);
-                    float* ahi = reinterpret_cast<float*>(P.a + s_ * SBT_ASLOT);
-                    float* alo = ahi + 4096;
-                    sbt_a_from_tmem(P, ahi, alo, q);
-                    ok = sbt_issue(P, s_, 2, P.tmem, 256u, q == 0, q == 3, w, fail);
+                for (int q = 0; q < 4; ++q, ++chunk) {
+                    const uint32_t sl = chunk & 1u, use = chunk >> 1;
+                    if (use > 0) (void)sbt_wait(&bar[SB_AFREE + sl], (use - 1) & 1u, fail);
+                    float* ahi = reinterpret_cast<float*>(As + sl * SBT_ASLOT);
+                    sbt_a_from_tmem(tmem, ahi, ahi + 4096, q);
+                    sbt_arrive_a(&bar[SB_AFULL + sl]);
                 }
-                // epilogue: Z_R -= U; warp w: slab column 32 (w % 4) + lane, window rows 64 (w / 4) ..
-                const int c = c0 + 32 * (warp & 3) + lane, h = warp >> 2;
+                // epilogue: Z_R -= U; the old values of the first part, and (when they do not lie in
+                // this window) the next block's first A rows, load while the products finish
                 float2 zo[16];
-                sbt_load_part(zo, Z, n, R0, nrows, c, 64 * h);
-                if (!ok || !(ok = sbt_product_done(P, fail))) break;
-                {
-                    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
-#pragma unroll 1
-                    for (int part = 0; part < 4; ++part) {
-                        const int ib = 64 * h + 16 * part;  // window rows ib .. ib + 15
-                        uint32_t v[2][16];
-                        sbt_ld16(P.tmem + lanes + (uint32_t)(2 * ib), v[0]);
-                        sbt_ld16(P.tmem + lanes + (uint32_t)(2 * ib + 16), v[1]);
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        float2 zn[16];
-#pragma unroll
-                        for (int u = 0; u < 16; ++u)
-                            zn[u] = make_float2(zo[u].x - __uint_as_float(v[u >> 3][2 * (u & 7)]),
-                                                zo[u].y - __uint_as_float(v[u >> 3][2 * (u & 7) + 1]));
-                        if (part < 3) sbt_load_part(zo, Z, n, R0, nrows, c, ib + 16);
-#pragma unroll
-                        for (int u = 0; u < 16; ++u) {
-                            const int i = ib + u;
-                            if (c < n && i < nrows) Z[(int64_t)(R0 + i) * n + c] = zn[u];
-                        }
+                sbt_load_part(zo, Z, n, W.R0, W.nrows, c, 64 * h);
+                const bool more = g + 1 < nbs || s + 1 < np;
+                zpre = false;
+                if (more) {
+                    const SbtWin Wn = g + 1 < nbs ? sbt_win(n, b, s, g + 1) : sbt_win(n, b, s + 1, 0);
+                    if (Wn.R0 + 16 <= W.R0 || Wn.R0 >= W.R0 + W.nrows) {
+                        sbt_load_z(z, Z, n, Wn.R0, Wn.nrows, c0 + r, 0, hh);
+                        zpre = true;
                     }
-                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 }
-                sbt_bar();  // Z's window and the TMEM reads are done before the next block
+                (void)sbt_wait(&bar[SB_ACC2], pacc, fail);
+                pacc ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+#pragma unroll 1
+                for (int part = 0; part < 4; ++part) {
+                    const int ib = 64 * h + 16 * part;  // window rows ib .. ib + 15
+                    uint32_t v[2][16];
+                    sbt_ld16(tmem + lanes + (uint32_t)(2 * ib), v[0]);
+                    sbt_ld16(tmem + lanes + (uint32_t)(2 * ib + 16), v[1]);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    float2 zn[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u)
+                        zn[u] = make_float2(zo[u].x - __uint_as_float(v[u >> 3][2 * (u & 7)]),
+                                            zo[u].y - __uint_as_float(v[u >> 3][2 * (u & 7) + 1]));
+                    if (part < 3) sbt_load_part(zo, Z, n, W.R0, W.nrows, c, ib + 16);
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int i = ib + u;
+                        if (c < n && i < W.nrows) Z[(int64_t)(W.R0 + i) * n + c] = zn[u];
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                sbt_bar();  // the window's rows are written before the next block reads them
+                stop = *fail != 0;  // read by every builder after the same barrier
             }
         }
-        if (!ok) *fail = 1;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     // on a failure, give the copies and products in flight a bounded time to land before the
     // shared memory and TMEM are released (each wait ends on its own limit)
     if (fail_s && tid == 0)
-        for (int k = 0; k < 11; ++k) (void)mbar_wait(&bar[k], 0u), (void)mbar_wait(&bar[k], 1u);
+        for (int k = 0; k < SB_NBAR; ++k) (void)mbar_wait(&bar[k], 0u), (void)mbar_wait(&bar[k], 1u);
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_s), "r"(SBT_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(SBT_TMEM_COLS) : "memory");
     if (fail_s && tid == 0) status[sid] = MMF_ST_NOCONV;
 }
 
