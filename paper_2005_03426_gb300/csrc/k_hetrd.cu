@@ -317,9 +317,11 @@ __device__ __forceinline__ void ht_tmem_ld32(uint32_t ta, uint32_t* v) {
         : "r"(ta));
 }
 
-template <int CL>
+// Tiles are dealt round-robin over nshare CTAs (this one takes those with index % nshare ==
+// share); full = true would update both triangles (full Hermitian storage: row blocks from c0,
+// no triangle mask).
 __device__ bool her2k_tc(float2* __restrict__ A, int ld, int n, int c0, const float2* __restrict__ V,
-                         const float2* __restrict__ W, int nb, int rank, HtTc& T) {
+                         const float2* __restrict__ W, int nb, int nshare, int share, bool full, HtTc& T) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t idesc = umma_idesc_mn(2, 128u, 128u);  // TF32 x TF32 -> F32, M = N = 128
     const int ncb = (n - c0 + 63) / 64;
@@ -327,15 +329,16 @@ __device__ bool her2k_tc(float2* __restrict__ A, int ld, int n, int c0, const fl
     bool ok = true;
     for (int tj = 0; tj < ncb && ok; ++tj) {
         const int cb = c0 + 64 * tj;
-        for (int rb = cb; rb < n && ok; rb += 128) {
-            if ((tcount++ % CL) != rank) continue;
+        for (int rb = full ? c0 : cb; rb < n && ok; rb += 128) {
+            if ((tcount++ % nshare) != share) continue;
             // old values of this thread's 16 entries (row r, columns cc .. cc + 15), in flight
             // while the operands are built
             const int r = rb + 32 * (warp & 3) + lane, cc = cb + 16 * (warp >> 2);
             float2 old[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q)
-                old[q] = (r < n && cc + q < n && r >= cc + q) ? A[r + (int64_t)(cc + q) * ld] : make_float2(0.f, 0.f);
+                old[q] = (r < n && cc + q < n && (full || r >= cc + q)) ? A[r + (int64_t)(cc + q) * ld]
+                                                                         : make_float2(0.f, 0.f);
             for (int pass = 0; pass < 2 && ok; ++pass) {
                 const float2* P = pass ? W : V;   // A' source
                 const float2* Q = pass ? V : W;   // B' source
@@ -438,7 +441,7 @@ __device__ bool her2k_tc(float2* __restrict__ A, int ld, int n, int c0, const fl
             }
 #pragma unroll
             for (int q = 0; q < 16; ++q)
-                if (r < n && cc + q < n && r >= cc + q)
+                if (r < n && cc + q < n && (full || r >= cc + q))
                     A[r + (int64_t)(cc + q) * ld] = make_float2(old[q].x - acc[q].x, old[q].y - acc[q].y);
             // the next tile's first products overwrite the accumulators after the next barrier
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -737,8 +740,8 @@ k_hetrd(const MmfDesc* __restrict__ descs, const int* __restrict__ idx,
         if constexpr (TC) {
             if (c0 < n) {
                 if (tc_ok)
-                    tc_ok = her2k_tc<CL>(reinterpret_cast<float2*>(A), ld, n, c0, reinterpret_cast<const float2*>(V),
-                                         reinterpret_cast<const float2*>(W), nb, rank, T);
+                    tc_ok = her2k_tc(reinterpret_cast<float2*>(A), ld, n, c0, reinterpret_cast<const float2*>(V),
+                                     reinterpret_cast<const float2*>(W), nb, CL, rank, false, T);
                 if (CL > 1) cluster.sync();
             }
         } else if (c0 < n) {

@@ -1002,7 +1002,7 @@ static int stage_eig(mmf_batch* b) {
             void* sc = (void*)(b->d_aux + 8 * i);
             LAUNCH(mmf_launch_hetrd_large(d, b->d_H, b->d_Vp, b->d_Wp, b->d_d, b->d_e, b->d_tau, work, sc, fp32,
                                           b->stream),
-                   4 * d.n);
+                   6 * d.n + (d.n + MMF_NB - 1) / MMF_NB);
         }
         mark(b, ST_TRIDIAG);
         LAUNCH(mmf_launch_tridiag_eig(Ll, b->d_d, b->d_e, b->d_aux, b->d_e2, b->d_E, b->d_Y, b->d_work,
