@@ -16,13 +16,15 @@
 // one thread handles a whole cluster in ascending order and orthogonalises each iterate against
 // the cluster's earlier vectors (modified Gram-Schmidt), as LAPACK's stein does.  FP32 (followed
 // by the refinement): every vector is iterated on its own thread, and each cluster is then
-// orthonormalised by one warp (two Gram-Schmidt passes), which keeps the serial work per thread
-// at O(n) even where clusters are long.
+// orthonormalised by one CTA (classical Gram-Schmidt twice per column, in contiguous scratch
+// columns), which keeps the serial work per thread at O(n) even where clusters are long.
 // Y is written row-major: Y[i * n + k] = component i of eigenvector k.
 #include "mmf_internal.h"
 
 
 __device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
+
+#define TRI_CMAX 64  // dot products formed per barrier in the cluster orthonormalisation
 
 // FP32 solver work layout inside a system's slot of 3 n^2 doubles (24 n^2 bytes): from the first
 // 16-byte boundary, the packed factors (n^2 float4), the iterate (n^2 floats), then (at an even
@@ -432,7 +434,7 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
     R lam_first = R(E[k] * sc);
     if constexpr (sizeof(R) == 4) {
         // FP32 (mixed path): every vector on its own; clusters are orthonormalised afterwards by
-        // k_cluster_mgs_f32.  Numerically equal eigenvalues (gaps below pert) get staggered shifts
+        // k_cluster_cgs2_f32.  Numerically equal eigenvalues (gaps below pert) get staggered shifts
         // so that their iterates differ: shift = lam of the first of the run + (position) pert.
         int k1 = k;
         while (k1 > 0) {
@@ -501,46 +503,82 @@ __global__ void __launch_bounds__(128) k_inviter(const MmfDesc* __restrict__ des
     }
 }
 
-// FP32 clusters: eigenvalues closer than ortol ||T|| are orthonormalised by one warp each, two
-// passes of modified Gram-Schmidt over the cluster in ascending order (the refinement that
-// follows resolves the eigenvectors inside the cluster).
-__global__ void __launch_bounds__(256) k_cluster_mgs_f32(const MmfDesc* __restrict__ descs,
-                                                         const int* __restrict__ idx,
-                                                         const double* __restrict__ aux,
-                                                         const double* __restrict__ Eg,
-                                                         double* __restrict__ work) {
+// FP32 clusters: eigenvalues closer than ortol ||T|| are orthonormalised by one CTA each
+// (the refinement that follows resolves the eigenvectors inside the cluster).  The cluster's m
+// columns of the row-major iterate are copied to contiguous columns of a scratch area (the
+// inverse iteration's factors, free by now: columns k .. kend-1 of an n x n column-major array,
+// so that clusters never overlap), orthonormalised there by classical Gram-Schmidt applied twice
+// per column ("twice is enough", Giraud, Langou & Rozloznik 2005): all dot products with the
+// earlier columns at once (one warp per column), then one update pass over the rows; and copied
+// back.  Work O(m^2 n) per cluster with O(m) barriers, coalesced in both layouts.
+#define CL_THREADS 256
+__global__ void __launch_bounds__(CL_THREADS) k_cluster_cgs2_f32(const MmfDesc* __restrict__ descs,
+                                                                 const int* __restrict__ idx,
+                                                                 const double* __restrict__ aux,
+                                                                 const double* __restrict__ Eg,
+                                                                 double* __restrict__ work) {
+    __shared__ float dots[TRI_CMAX];
+    __shared__ float red[CL_THREADS / 32];
     const int sid = idx[blockIdx.y];
     const MmfDesc d = descs[sid];
     const int n = d.n;
-    const int lane = threadIdx.x & 31;
-    const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int k = blockIdx.x;
     if (k >= n) return;
     const double* E = Eg + d.vec_off;
     const double ortol = (double)TriP<float>::ortol * aux[8 * sid + 3];
     if (k > 0 && E[k] - E[k - 1] <= ortol) return;  // not the first of its cluster
     int kend = k + 1;
     while (kend < n && E[kend] - E[kend - 1] <= ortol) ++kend;
-    if (kend - k < 2) return;
-    const int64_t s = n, nn = (int64_t)n * n;
-    float* Yw = tri_f32_base((const float*)work, d) + 4 * nn;
-    for (int j = k + 1; j < kend; ++j) {
-        float* y = Yw + j;
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int jp = k; jp < j; ++jp) {
-                const float* z = Yw + jp;
-                float dot = 0.f;
-                for (int i = lane; i < n; i += 32) dot += y[(int64_t)i * s] * z[(int64_t)i * s];
-                dot = warp_sum(dot);
-                for (int i = lane; i < n; i += 32) y[(int64_t)i * s] -= dot * z[(int64_t)i * s];
-                __syncwarp();
+    const int m = kend - k;
+    if (m < 2) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t nn = (int64_t)n * n;
+    float* Yw = tri_f32_base((const float*)work, d) + 4 * nn;  // row-major iterate
+    float* Sc = tri_f32_base((const float*)work, d);           // scratch, column-major
+    // gather: Sc[(k + j) n + i] = Yw[i n + k + j]
+    for (int64_t e = tid; e < (int64_t)m * n; e += CL_THREADS) {
+        const int i = (int)(e / m), j = (int)(e - (int64_t)i * m);
+        Sc[(int64_t)(k + j) * n + i] = Yw[(int64_t)i * n + k + j];
+    }
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+        float* y = Sc + (int64_t)(k + j) * n;
+        for (int pass = 0; pass < 2 && j > 0; ++pass) {
+            // dots with the earlier columns (chunks of TRI_CMAX), then y -= sum dots z
+            for (int j0 = 0; j0 < j; j0 += TRI_CMAX) {
+                const int jn = min(TRI_CMAX, j - j0);
+                for (int jp = warp; jp < jn; jp += CL_THREADS / 32) {
+                    const float* z = Sc + (int64_t)(k + j0 + jp) * n;
+                    float acc = 0.f;
+                    for (int i = lane; i < n; i += 32) acc = fmaf(y[i], z[i], acc);
+                    acc = warp_sum(acc);
+                    if (lane == 0) dots[jp] = acc;
+                }
+                __syncthreads();
+                for (int i = tid; i < n; i += CL_THREADS) {
+                    float v = y[i];
+                    for (int jp = 0; jp < jn; ++jp) v = fmaf(-dots[jp], Sc[(int64_t)(k + j0 + jp) * n + i], v);
+                    y[i] = v;
+                }
+                __syncthreads();
             }
         }
+        float part = 0.f;
+        for (int i = tid; i < n; i += CL_THREADS) part = fmaf(y[i], y[i], part);
+        part = warp_sum(part);
+        if (lane == 0) red[warp] = part;
+        __syncthreads();
         float nrm = 0.f;
-        for (int i = lane; i < n; i += 32) nrm += y[(int64_t)i * s] * y[(int64_t)i * s];
-        nrm = warp_sum(nrm);
+#pragma unroll
+        for (int w = 0; w < CL_THREADS / 32; ++w) nrm += red[w];
         const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
-        for (int i = lane; i < n; i += 32) y[(int64_t)i * s] *= inv;
-        __syncwarp();
+        for (int i = tid; i < n; i += CL_THREADS) y[i] *= inv;
+        __syncthreads();
+    }
+    // scatter back
+    for (int64_t e = tid; e < (int64_t)m * n; e += CL_THREADS) {
+        const int i = (int)(e / m), j = (int)(e - (int64_t)i * m);
+        Yw[(int64_t)i * n + k + j] = Sc[(int64_t)(k + j) * n + i];
     }
 }
 
@@ -564,7 +602,7 @@ cudaError_t mmf_launch_tridiag_eig(const MmfLaunch& L, const double* dvec, const
     if (fp32) {
         k_bisect<float><<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, e2, aux, (const float*)work, E, status);
         k_inviter<float><<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, evec, aux, E, Y, work, iters);
-        k_cluster_mgs_f32<<<dim3((L.nmax + 7) / 8, L.count), 256, 0, L.stream>>>(L.desc, L.idx, aux, E, work);
+        k_cluster_cgs2_f32<<<dim3(L.nmax, L.count), CL_THREADS, 0, L.stream>>>(L.desc, L.idx, aux, E, work);
         k_widen_y_f32<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, work, Y);
     } else {
         k_bisect<double><<<g, 128, 0, L.stream>>>(L.desc, L.idx, dvec, e2, aux, nullptr, E, status);
