@@ -174,8 +174,9 @@ __global__ void __launch_bounds__(LG_B) k_lg_vscale(typename Cx<R>::T* __restric
 // (I, J) with I >= J, numbered along block rows (block b: I = floor((sqrt(8 b + 1) - 1) / 2),
 // J = b - I (I + 1) / 2).  Thread (row r, column half h) reads its 64 entries A(r, c) once and
 // adds a(r, c) v_c to its row's sum and conj(a(r, c)) v_r to column c's sum (strictly below the
-// diagonal; the diagonal entry once, as a real number).  Column sums: warp shuffles over the 32
-// rows of a warp, then shared memory over the block's four warps of that half.
+// diagonal; the diagonal entry once, as a real number).  Column sums: a butterfly reduce-scatter
+// of 8 columns at a time over the 32 rows of a warp (16 shuffles for 16 values), then shared
+// memory over the block's four warps of that half.
 #define LG_HB 128
 template <class R>
 __global__ void __launch_bounds__(256) k_lg_hemv(const typename Cx<R>::T* __restrict__ A, int n, int ld, int k,
@@ -216,17 +217,47 @@ __global__ void __launch_bounds__(256) k_lg_hemv(const typename Cx<R>::T* __rest
             const bool ok = rok && c < m && (I > J || c <= r);
             av[u] = ok ? a[(int64_t)(q0 + u) * ld] : czero<C>();
         }
+        R cv[16];  // column parts of the 8 columns (Re, Im), strictly below the diagonal
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int cl = 64 * h + q0 + u, c = c0 + cl;
             const bool diag = (I == J) && c == r;
             const C aa = diag ? mk(av[u].x, R(0)) : av[u];
             acc = acc + aa * vc_s[cl];
-            // column part: strictly below the diagonal only
-            C cp = diag ? czero<C>() : cmulc(av[u], vr);
-            cp.x = warp_sum(cp.x);
-            cp.y = warp_sum(cp.y);
-            if (lane == 0) colsum[wq][cl] = cp;
+            const C cp = diag ? czero<C>() : cmulc(av[u], vr);
+            cv[2 * u] = cp.x;
+            cv[2 * u + 1] = cp.y;
+        }
+        // the 16 sums over the warp's 32 rows by a butterfly reduce-scatter: after the rounds
+        // with lane offsets 16, 8, 4, 2 lane L holds value (L >> 1) & 15 summed over 16 lanes,
+        // and the last round adds its partner's
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const bool hi = lane & 16;
+            const R keep = hi ? cv[t + 8] : cv[t], send = hi ? cv[t] : cv[t + 8];
+            cv[t] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const bool hi = lane & 8;
+            const R keep = hi ? cv[t + 4] : cv[t], send = hi ? cv[t] : cv[t + 4];
+            cv[t] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const bool hi = lane & 4;
+            const R keep = hi ? cv[t + 2] : cv[t], send = hi ? cv[t] : cv[t + 2];
+            cv[t] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+        {
+            const bool hi = lane & 2;
+            const R keep = hi ? cv[1] : cv[0], send = hi ? cv[0] : cv[1];
+            cv[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+        }
+        cv[0] += __shfl_xor_sync(0xffffffffu, cv[0], 1);
+        if ((lane & 1) == 0) {
+            const int idx = (lane >> 1) & 15;  // column q0 + idx / 2, Re (idx even) or Im
+            reinterpret_cast<R*>(&colsum[wq][64 * h + q0 + (idx >> 1)])[idx & 1] = cv[0];
         }
     }
     if (rok) atomic_add_cx(&ybuf[r], acc);
