@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__
     constexpr int P = G / BMAX;
     static_assert(P * BMAX == G && P >= 1, "group size is a multiple of BMAX");
     constexpr int NGT = CL * NG;                          // groups per system
-    constexpr int LCH = (BMAX / P) < 8 ? (BMAX / P) : 8;  // register-staged loads per batch (CL > 1)
+    constexpr int LCH = (BMAX / P) < 16 ? (BMAX / P) : 16;  // register-staged loads per batch (CL > 1)
     static_assert((BMAX / P) % LCH == 0, "load batches divide the block");
     extern __shared__ __align__(16) unsigned char sbr_smem[];
     volatile long long* key = reinterpret_cast<volatile long long*>(sbr_smem);
