@@ -132,10 +132,12 @@ def stage_model(stage: str, n: int, nt: int, mixed: bool, band: int = 0):
     - hetrd, band path (the bulge chase): about 6 b^2 complex multiply-adds per step (the
       one-sided update of the bulge block, the two-sided update of the diagonal block) over
       n^2 / (2 b) steps = 24 b n^2 real flops.
-    - backtransform: 8 n^3 real flops (LAPACK count), on either path.
-    - refine_gram: the tensor-core Gram product by integer slicing, 15 slice pairs x (Re, Im) x
-      n x n/2 x 2n multiply-adds x 2 flops = 60 n^3 (lower-triangle tiles) on the BF16 tensor
-      cores, against the sustained cuBLAS bf16 rate (the kernel runs inside a long step).
+    - backtransform: 8 n^3 real flops (LAPACK count), on either path; in the mixed path from
+      n = 256 on (band path: half-bandwidths 33..64, the library's default thresholds) on the
+      tensor cores in split TF32, against the TF32 rate (the measured sustained bf16 rate x the
+      nominal TF32 / BF16 ratio 1.1 / 2.25).
+    - refine_gram: the first refinement step's G on the band |i - j| <= 16 in double-FP32,
+      33 n^2 complex multiply-adds = 264 n^2 real flops (FP64-equivalent) against the FP32 rate.
     - outputs: 8 nt n^2 flops (the Phi contraction)."""
     pk = _peaks()
     hbm = pk["hbm_gbs"] * 1e9
@@ -150,13 +152,18 @@ def stage_model(stage: str, n: int, nt: int, mixed: bool, band: int = 0):
         return [("alu", 16.0 / 3.0 * n ** 3, alu[0], "TFLOP/s", alu[1], "k_hetrd"),
                 ("hbm", esz * n ** 3 / 6.0, hbm, "GB/s", f"copy bandwidth {pk['hbm_gbs']} GB/s {src}", "k_hetrd")]
     if stage == "backtransform":
+        tf32 = bf16 * 1.1 / 2.25
+        tc = (f"TF32: cuBLAS bf16 sustained {bf16 / 1e12:.1f} TFLOP/s {src} x 1.1 / 2.25 (nominal ratio)")
         if band:
+            if mixed and n >= 256 and 33 <= band <= 64:
+                return [("tensor", 8.0 * n ** 3, tf32, "TFLOP/s", tc, "k_sbr_bt_tc")]
             return [("alu", 8.0 * n ** 3, alu[0], "TFLOP/s", alu[1], "k_sbr_bt_f32" if mixed else "k_sbr_bt_f64")]
+        if mixed and n >= 256:
+            return [("tensor", 8.0 * n ** 3, tf32, "TFLOP/s", tc, "k_tf3_gemm")]
         return [("alu", 8.0 * n ** 3, alu[0], "TFLOP/s", alu[1],
                  "k_backtransform_f32" if mixed else "k_backtransform")]
     if stage == "refine_gram" and mixed:
-        return [("tensor", 60.0 * n ** 3, bf16, "TFLOP/s",
-                 f"cuBLAS bf16 sustained {bf16 / 1e12:.1f} TFLOP/s {src}", "k_oz_gram")]
+        return [("alu", 264.0 * n ** 2, alu[0], "TFLOP/s", alu[1], "k_gram_band_df32")]
     if stage == "outputs":
         return [("alu", 8.0 * nt * n * n, alu[0], "TFLOP/s", alu[1], "k_time_evolution")]
     return None

@@ -79,11 +79,11 @@ MMF_API size_t mmf_ctx_budget(const mmf_ctx* ctx);
  * (defaults 84 / 118, also the maxima; values below 4 act as 4); MMF_OPT_LARGE_N: smallest n reduced by the whole-GPU
  * Householder reduction, one system at a time (default: sizes one CTA's shared memory cannot
  * hold); MMF_OPT_REFINE_FULL_N: in the mixed path, smallest n whose second refinement step is a
- * full one (default 3000).  Below it the second step is hybrid: the corrections of all pairs from
- * C = X^H W on the tensor cores, with G = X^H X formed FP64-accurately only for pairs within 16
- * places in the sorted order; a full step also forms all of G (costlier, for the dense spectra of
- * large H_F).
- * MMF_OPT_GRAM_KERNEL: the mixed path's Gram product X^H X, 0 (default) on the BF16 tensor
+ * full one (default 3000).  Below it the second step is hybrid, like the first: the corrections
+ * of all pairs from C = X^H W on the tensor cores, with G = X^H X formed FP64-accurately only for
+ * pairs within 16 places in the sorted order; a full step also forms all of G (costlier, for the
+ * dense spectra of large H_F).
+ * MMF_OPT_GRAM_KERNEL: the full second step's Gram product X^H X, 0 (default) on the BF16 tensor
  * cores by exact integer slicing, 1 in double-FP32 on the FP32 units (both FP64-accurate).
  * MMF_OPT_BT_TC_N: in the mixed path, smallest n whose back-transform (Z = Q Y, Sec. 3.2's
  * eigenvectors from the tridiagonal ones) runs on the tensor cores in split TF32 (default 256);

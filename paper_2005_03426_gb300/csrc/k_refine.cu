@@ -19,12 +19,17 @@
 // so lam_i = lam0_i + c_ii / g_ii and s_ij - lam_j g_ij = c_ij - (lam_j - lam0_j) g_ij.  C only
 // needs FP32 relative accuracy (its absolute error is then ~eps32^2 |H_F|) and is taken on the
 // tensor cores in split TF32.  X Et only needs FP32 (Et is small) and is taken there as well.
+// G itself is needed only near the diagonal: off it, g_ij enters the update of a non-clustered
+// pair only through (lam_j - lam0_j) g_ij ~ eps32 |H_F| |g_ij|, negligible, and the pair's
+// orthogonality is restored through C (c_ij - conj(c_ji) = (lam0_i - lam0_j) g_ij, so
+// Et_ij + conj(Et_ji) ~ -g_ij).  Both steps therefore form G in double-FP32 on the band
+// |i - j| <= RF_W only, except a full second step (below), which forms all of it.
 // A second full step (large n, where one step leaves second-order errors ~(eps32 |H_F| / gap)^2
 // between eigenpairs far apart in the sorted order) starts from FP64 X = X1 + Dx with
 // X1 = fl32(X): G = X1^H X1 + C' + C'^H + O(|Dx|^2) with C' = X1^H Dx, the first term by the
 // same double-FP32 kernel (X1 is FP32-exact), C' on the tensor cores (|Dx| ~ 2^-24 |X|).
-// Below that size the second step is hybrid (below): C for all pairs as in the first step, G
-// (FP64-accurate) only on the band |i - j| <= RF_W, where the near pairs need it.
+// Below that size the second step is hybrid (below): C for all pairs and G (FP64-accurate) only
+// on the band |i - j| <= RF_W, as in the first step.
 // A pair is treated as clustered when |lam_i - lam_j| <= 20 |s_ij - lam_j g_ij| (the first-order
 // correction would exceed 0.05) or the gap is below RF_GAMMA |H_F|; consecutive clustered indices
 // form a cluster whose eigenvectors are separated by an FP64 Jacobi solve of the small
@@ -44,8 +49,9 @@
 #define RF_CMAX 32
 #define RF_TAU 20.0
 #define RF_GAMMA 3e-5
-// Band |i - j| <= RF_W of the sorted eigenpairs: every step applies Et there in double-FP32
-// (entries up to ~0.05), and the hybrid second step forms G only inside it.
+// Band |i - j| <= RF_W of the sorted eigenpairs: the last step applies Et there in double-FP32
+// (entries up to ~0.05; the first step, which another follows, in FP32), and the hybrid second
+// step forms G only inside it.
 #define RF_W 16
 #define RF_BW (2 * RF_W + 1)
 static_assert(RF_BW == MMF_REFINE_BW, "band buffer width");
@@ -684,7 +690,11 @@ __global__ void __launch_bounds__(256) k_et_band(const MmfDesc* __restrict__ des
 // outside the band), the band in double-FP32 from X1 = fl32(X) (exact in the first step; in a
 // second step the remainder times Et is below 2^-24 |Et| and dropped) and Et split in two FP32
 // pieces, or in plain FP32 where every band entry of the tile is below XT_SMALL (a second step's
-// corrections).  Xn goes to a separate buffer (the band reads neighbouring columns of X).
+// corrections) or where a further full step follows (band_fp32): the FP32 band then adds an
+// error of at most ~RF_BW x 2^-24 x 0.05 ~ 1e-7 (typically ~1e-8) to the columns of Xn, below
+// the second-order error ~1e-5 the step leaves between close pairs, and the next step, which
+// forms G and C from Xn itself, removes both.  Xn overwrites X in place: the band reads the
+// neighbouring columns from X1, and each thread reads only the element of X it writes.
 // One CTA per XT_R x XT_C tile of Xn: the XT_C + 2W neighbouring columns of X1, the band of Et
 // and the tile of C are staged in shared memory; thread (row, group of XT_CPT columns).
 #define XT_R 32
@@ -692,9 +702,9 @@ __global__ void __launch_bounds__(256) k_et_band(const MmfDesc* __restrict__ des
 #define XT_SMALL 1e-7f  // band entries below this go through plain FP32
 #define XT_CPT (XT_C * XT_R / 256)   // output columns per thread
 __global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ descs,
-                                                  const int* __restrict__ idx, const double2* __restrict__ Xg,
+                                                  const int* __restrict__ idx, double2* Xg,
                                                   const float2* __restrict__ X1g, const double2* __restrict__ R,
-                                                  const double2* __restrict__ Ebg, double2* __restrict__ Xn) {
+                                                  const double2* __restrict__ Ebg, int band_fp32) {
     __shared__ float2 xs[XT_C + 2 * RF_W][XT_R];
     __shared__ Split es[RF_BW][XT_C];
     __shared__ float cs[2][XT_R][XT_C + 1];
@@ -730,10 +740,11 @@ __global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ de
     const int rr = threadIdx.x & (XT_R - 1), cg = threadIdx.x / XT_R;
     const int r = r0 + rr;
     if (r >= n) return;
-    const double2* X = Xg + d.mat_off;
-    if (!big) {
+    double2* X = Xg + d.mat_off;
+    if (!big || band_fp32) {
         // every band entry of the tile is below XT_SMALL (a second step's corrections): plain
-        // FP32, whose error (about 33 x 2^-24 x XT_SMALL for |X| <= 1) stays near 2e-13 at most
+        // FP32, whose error (about 33 x 2^-24 x XT_SMALL for |X| <= 1) stays near 2e-13 at most;
+        // or a full step follows, which removes the FP32 error of this one
 #pragma unroll 1
         for (int c = cg * XT_CPT; c < cg * XT_CPT + XT_CPT; ++c) {
             const int j = j0 + c;
@@ -747,7 +758,7 @@ __global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ de
                 ai = fmaf(x.x, e.i1, fmaf(x.y, e.r1, ai));
             }
             const double2 x = X[(int64_t)j * d.ld + r];
-            Xn[d.mat_off + (int64_t)j * d.ld + r] =
+            X[(int64_t)j * d.ld + r] =
                 make_double2(x.x + ((double)cs[0][rr][c] + (double)ar), x.y + ((double)cs[1][rr][c] + (double)ai));
         }
         return;
@@ -768,7 +779,7 @@ __global__ void __launch_bounds__(256) k_xe_apply(const MmfDesc* __restrict__ de
         }
         const double2 band = df_value(ar, ai);
         const double2 x = X[(int64_t)j * d.ld + r];
-        Xn[d.mat_off + (int64_t)j * d.ld + r] =
+        X[(int64_t)j * d.ld + r] =
             make_double2(x.x + ((double)cs[0][rr][c] + band.x), x.y + ((double)cs[1][rr][c] + band.y));
     }
 }
@@ -1101,13 +1112,13 @@ __global__ void __launch_bounds__(256) k_sort_pairs(const MmfDesc* __restrict__ 
     for (int r = threadIdx.x; r < n; r += blockDim.x) dst[r] = src[r];
 }
 
-// ================================================================== hybrid second step
-// After one full step X is accurate to second order in the FP32 iterate's error.  The second step
-// (below the size of a full one) takes C = X^H W for all pairs on the tensor cores, as the first
-// step does, but G = X^H X only on the band |i - j| <= RF_W: off the band G - I is of the size of
-// the first step's second-order error, and (lam0_j - lam_j) G_ij, the only place it enters the
-// update of a non-clustered pair, is negligible; a cluster wider than the band meets G_ij ~ 0
-// outside it, the same up to that error.  Only near pairs need G to FP64 accuracy.
+// ================================================================== band G (first and hybrid second step)
+// Both the first step and the second step below the size of a full one take C = X^H W for all
+// pairs on the tensor cores but G = X^H X only on the band |i - j| <= RF_W: (lam0_j - lam_j) G_ij,
+// the only place an entry off the band enters the update of a non-clustered pair, is negligible
+// (|G_ij| ~ eps32 before the first step, of the size of its second-order error after it), and a
+// cluster wider than the band meets G_ij ~ 0 outside it in the update; the cluster separation
+// then forms the cluster's own Gram matrix from X.  Only near pairs need G to FP64 accuracy.
 #define RF_BC 32            // columns per CTA
 #define RF_BR 16            // rows per staged chunk
 
@@ -1169,9 +1180,9 @@ __global__ void __launch_bounds__(256) k_gram_band_df32(const MmfDesc* __restric
 // The refinement is launched in parts so that the host can time the FP64-accurate Gram product
 // on its own and choose the second step per system:
 //   pre:    HX = H_F X, C = X^H W (and C' = X1^H Dx for a second full step) on the tensor cores
-//   gram:   G = X1^H X1 in double-FP32 (+ C' + C'^H)
-//   update: lam, Et, X <- X + X Et, cluster separation
-//   band_g: G on the band for the hybrid second step;   finish: final ordering.
+//   band_g: G on the band (first step, hybrid second step)
+//   gram:   all of G = X1^H X1 in double-FP32 (+ C' + C'^H) for a full second step
+//   update: lam, Et, X <- X + X Et, cluster separation;   finish: final ordering.
 cudaError_t mmf_launch_refine_split_coef(const double2* coef, float4* cs, int64_t count, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     k_split_coef<<<(int)std::min<int64_t>((count + 255) / 256, 1024), 256, 0, st>>>(coef, cs, count);
@@ -1229,12 +1240,13 @@ cudaError_t mmf_launch_refine_gram_fix(const MmfLaunch& L, double2* G, const dou
 cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, const int* pat, double2* X,
                                      const float2* X1,
                                      const double* lam0, double2* G, double2* HX, const double2* T, double* lam,
-                                     int* status, int* cid, int64_t mat_elems, void* ops, void* jobs,
-                                     double2* Eb) {
+                                     int* status, int* cid, void* ops, void* jobs, double2* Eb,
+                                     int band_fp32) {
     if (L.count <= 0) return cudaSuccess;
     k_oa_lambda<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, T, lam0, lam, cid);
     k_oa_etilde<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, T, lam0, lam, cid);
-    // X <- X + X Et: band in double-FP32, the rest on the tensor cores (split TF32)
+    // X <- X + X Et: band in double-FP32 (FP32 when another step follows), the rest on the tensor
+    // cores (split TF32)
     k_et_band<<<dim3(64, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, Eb);
     k_xe_prep_B<<<dim3(512, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, ops);
     k_xe_prep_A<<<dim3(tf3_nq(L.nmax) * 4, (L.nmax + 31) / 32, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X1,
@@ -1243,9 +1255,7 @@ cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, co
     cudaError_t e = mmf_launch_tf3(jobs, L.count, L.nmax, 2 * L.nmax, status, L.stream);
     if (e != cudaSuccess) return e;
     k_xe_apply<<<dim3((L.nmax + XT_R - 1) / XT_R, (L.nmax + XT_C - 1) / XT_C, L.count), 256, 0, L.stream>>>(
-        L.desc, L.idx, X, X1, G, Eb, HX);
-    e = cudaMemcpyAsync(X, HX, sizeof(double2) * mat_elems, cudaMemcpyDeviceToDevice, L.stream);
-    if (e != cudaSuccess) return e;
+        L.desc, L.idx, X, X1, G, Eb, band_fp32);
     k_cluster_sep<<<dim3(std::min(L.nmax, 1024), L.count), 256, 0, L.stream>>>(L.desc, L.idx, coef, pat, X, HX, lam,
                                                                                 cid, status);
     return cudaGetLastError();

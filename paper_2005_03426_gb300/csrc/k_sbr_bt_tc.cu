@@ -170,17 +170,19 @@ __global__ void __launch_bounds__(256) k_sbr_wy(const MmfDesc* __restrict__ desc
     // (2): Y(i, j) for the pair j, j + 1; rows 2i (Re) and 2i + 1 (Im) of window row i
     for (int e = tid; e < 128 * 32; e += 256) {
         const int kq = e & 7, i = (e >> 3) & 127, q = e >> 10, j = 16 * q + 2 * kq;
-        float2 y[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            float yr = 0.f, yi = 0.f;
-            for (int k = max(0, i - 63); k <= min(j + u, i); ++k) {  // V(i, k) = 0 unless 0 <= i - k < 64
-                const float2 v = Vs[k][i - k], t = Ts[k][j + u];
-                yr = fmaf(v.x, t.x, fmaf(-v.y, t.y, yr));
-                yi = fmaf(v.x, t.y, fmaf(v.y, t.x, yi));
-            }
-            y[u] = make_float2(yr, yi);
+        // Y(i, j) and Y(i, j + 1) in one pass over k (V(i, k) = 0 unless 0 <= i - k < 64; T upper
+        // triangular, so T(k, j) is used for k <= j only: its lower part holds scratch)
+        float yr0 = 0.f, yi0 = 0.f, yr1 = 0.f, yi1 = 0.f;
+        const int khi = min(j + 1, i);
+        for (int k = max(0, i - 63); k <= khi; ++k) {
+            const float2 v = Vs[k][i - k], t1 = Ts[k][j + 1];
+            const float2 t0 = k <= j ? Ts[k][j] : make_float2(0.f, 0.f);
+            yr0 = fmaf(v.x, t0.x, fmaf(-v.y, t0.y, yr0));
+            yi0 = fmaf(v.x, t0.y, fmaf(v.y, t0.x, yi0));
+            yr1 = fmaf(v.x, t1.x, fmaf(-v.y, t1.y, yr1));
+            yi1 = fmaf(v.x, t1.y, fmaf(v.y, t1.x, yi1));
         }
+        const float2 y[2] = {make_float2(yr0, yi0), make_float2(yr1, yi1)};
         float* hi = ops + SBT_B1_FLOATS + (int64_t)(2 * q) * 8192;
         float* lo = hi + 8192;
         sbt_put4(hi, lo, sbt_swz(2 * i, kq), y[0].x, -y[0].y, y[1].x, -y[1].y);
