@@ -508,14 +508,15 @@ __global__ void __launch_bounds__(256) k_oa_lambda(const MmfDesc* __restrict__ d
 // Et in place of G (diagonal and clustered pairs: r/2; others: OA formula).  One 32 x 32 tile
 // (rows i, columns j) per block iteration: G is column-major (i contiguous) and C row-major
 // (j contiguous), so C's tile is read along j into shared memory first and both are then used
-// with i fastest across the threads.
+// with i fastest across the threads.  g_band: G was formed only on the band |i - j| <= RF_W and
+// is taken as 0 off it (its entries there are not read and need not be set).
 __global__ void __launch_bounds__(256) k_oa_etilde(const MmfDesc* __restrict__ descs,
                                                    const int* __restrict__ idx,
                                                    double2* __restrict__ Gg,
                                                    const double2* __restrict__ Cg,
                                                    const double* __restrict__ lam0g,
                                                    const double* __restrict__ lamg,
-                                                   const int* __restrict__ cidg) {
+                                                   const int* __restrict__ cidg, int g_band) {
     __shared__ float cre[32][33], cim[32][33];
     const MmfDesc d = descs[idx[blockIdx.y]];
     const int n = d.n;
@@ -546,7 +547,7 @@ __global__ void __launch_bounds__(256) k_oa_etilde(const MmfDesc* __restrict__ d
             const int j = j0 + q;
             if (j >= n) break;
             const int64_t o = (int64_t)j * d.ld + i;
-            const double2 g = G[o];
+            const double2 g = (g_band && abs(i - j) > RF_W) ? make_double2(0.0, 0.0) : G[o];
             double2 et;
             if (i == j) {
                 et = make_double2(0.5 * (1.0 - g.x), 0.0);
@@ -1123,7 +1124,7 @@ __global__ void __launch_bounds__(256) k_sort_pairs(const MmfDesc* __restrict__ 
 #define RF_BR 16            // rows per staged chunk
 
 // G = X^H X on the band |i - j| <= RF_W in double-FP32, written into the full n x n G (column-major,
-// ld), whose other entries the caller has zeroed.
+// ld); its other entries are left as they are (the update reads G only on the band then).
 __global__ void __launch_bounds__(256) k_gram_band_df32(const MmfDesc* __restrict__ descs,
                                                         const int* __restrict__ idx,
                                                         const double2* __restrict__ Xg,
@@ -1241,10 +1242,10 @@ cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, co
                                      const float2* X1,
                                      const double* lam0, double2* G, double2* HX, const double2* T, double* lam,
                                      int* status, int* cid, void* ops, void* jobs, double2* Eb,
-                                     int band_fp32) {
+                                     int band_fp32, int g_band) {
     if (L.count <= 0) return cudaSuccess;
     k_oa_lambda<<<L.count, 256, 0, L.stream>>>(L.desc, L.idx, G, T, lam0, lam, cid);
-    k_oa_etilde<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, T, lam0, lam, cid);
+    k_oa_etilde<<<dim3(256, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, T, lam0, lam, cid, g_band);
     // X <- X + X Et: band in double-FP32 (FP32 when another step follows), the rest on the tensor
     // cores (split TF32)
     k_et_band<<<dim3(64, L.count), 256, 0, L.stream>>>(L.desc, L.idx, G, Eb);
@@ -1261,10 +1262,8 @@ cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, co
     return cudaGetLastError();
 }
 
-cudaError_t mmf_launch_refine_band_g(const MmfLaunch& L, const double2* X, double2* G, int64_t mat_elems) {
+cudaError_t mmf_launch_refine_band_g(const MmfLaunch& L, const double2* X, double2* G) {
     if (L.count <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double2) * mat_elems, L.stream);
-    if (e != cudaSuccess) return e;
     k_gram_band_df32<<<dim3((L.nmax + RF_BC - 1) / RF_BC, L.count), 256, 0, L.stream>>>(L.desc, L.idx, X, G);
     return cudaGetLastError();
 }

@@ -413,9 +413,10 @@ __global__ void __launch_bounds__(G* NG) k_sbr_chase(const MmfDesc* __restrict__
                     }
                 }
             }
-            // store the reflector for the back-transform
-            if (tid < b) V[(sbr_off(n, b, s) + j) * b + tid] = vc[tid];
-            if (tid == 0) T[sbr_off(n, b, s) + j] = tau;
+            // store the reflector for the back-transform, marked evict-first: the store is written
+            // once and read only after the chase, and L2 should keep the band's lines instead
+            if (tid < b) __stcs(&V[(sbr_off(n, b, s) + j) * b + tid], vc[tid]);
+            if (tid == 0) __stcs(&T[sbr_off(n, b, s) + j], tau);
             gbar<G>(g);
             // (d) diagonal block A(R_s, R_s) <- H^H A H
             sbr_two_sided<R, C, BMAX, G, P>(S, vc, tau, l, Hg, ldi, r, tid, g, s == 0 ? dd + j + 1 : nullptr);

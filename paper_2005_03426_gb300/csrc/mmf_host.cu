@@ -1046,12 +1046,12 @@ static int stage_eig(mmf_batch* b) {
         mark(b, ST_GRAM);
         // the first step needs G = X^H X only on the band |i - j| <= 16 (far pairs enter its update
         // through C), as the hybrid second step does
-        LAUNCH(mmf_launch_refine_band_g(La, b->d_Zf, b->d_R, b->n_mat), 1);
+        LAUNCH(mmf_launch_refine_band_g(La, b->d_Zf, b->d_R), 1);
         mark(b, ST_REFINE2);
         // every system takes a second step (hybrid or full) below, so the first one applies the
         // near band of Et in FP32
         LAUNCH(mmf_launch_refine_update(La, b->d_coef, b->d_pat, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_HX, b->d_T, b->d_E2,
-                                        b->d_status, b->d_cid, b->d_oz, b->d_jobs, b->d_Eb, 1),
+                                        b->d_status, b->d_cid, b->d_oz, b->d_jobs, b->d_Eb, 1, 1),
                9);
         // second step from lam0 = the first step's eigenvalues (E is rewritten at the end)
         CU(cudaMemcpyAsync(b->d_E, b->d_E2, sizeof(double) * b->n_vec, cudaMemcpyDeviceToDevice, b->stream));
@@ -1061,9 +1061,9 @@ static int stage_eig(mmf_batch* b) {
             LAUNCH(mmf_launch_refine_pre(Lb, b->d_coefs, b->d_pat, b->d_Zf, b->d_E, b->d_HX, b->d_T, b->d_X1, b->d_oz,
                                          b->d_jobs, b->d_status, 2),
                    6);
-            LAUNCH(mmf_launch_refine_band_g(Lb, b->d_Zf, b->d_R, b->n_mat), 1);
+            LAUNCH(mmf_launch_refine_band_g(Lb, b->d_Zf, b->d_R), 1);
             LAUNCH(mmf_launch_refine_update(Lb, b->d_coef, b->d_pat, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_HX, b->d_T,
-                                            b->d_E2, b->d_status, b->d_cid, b->d_oz, b->d_jobs, b->d_Eb, 0),
+                                            b->d_E2, b->d_status, b->d_cid, b->d_oz, b->d_jobs, b->d_Eb, 0, 1),
                    9);
         }
         if (!b->rfull.empty()) {
@@ -1074,7 +1074,7 @@ static int stage_eig(mmf_batch* b) {
                    9);
             LAUNCH(refine_gram(b, Lf, 1), 3);
             LAUNCH(mmf_launch_refine_update(Lf, b->d_coef, b->d_pat, b->d_Zf, b->d_X1, b->d_E, b->d_R, b->d_HX, b->d_T,
-                                            b->d_E2, b->d_status, b->d_cid, b->d_oz, b->d_jobs, b->d_Eb, 0),
+                                            b->d_E2, b->d_status, b->d_cid, b->d_oz, b->d_jobs, b->d_Eb, 0, 0),
                    9);
         }
         LAUNCH(mmf_launch_refine_finish(La, b->d_Zf, b->d_E, b->d_E2, b->d_S, b->n_mat), 1);

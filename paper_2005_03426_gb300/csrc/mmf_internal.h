@@ -278,9 +278,10 @@ cudaError_t mmf_launch_refine_gram_fix(const MmfLaunch& L, double2* G, const dou
 cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, const int* pat, double2* X, const float2* X1,
                                      const double* lam0, double2* G, double2* HX, const double2* T, double* lam,
                                      int* status, int* cid, void* ops, void* jobs, double2* Eb,
-                                     int band_fp32);
-// hybrid second step: G = X^H X on the band |i - j| <= 16 (double-FP32) into the zeroed full G
-cudaError_t mmf_launch_refine_band_g(const MmfLaunch& L, const double2* X, double2* G, int64_t mat_elems);
+                                     int band_fp32, int g_band);
+// first step and hybrid second step: G = X^H X on the band |i - j| <= 16 (double-FP32), the rest
+// of G left unset (the update then runs with g_band = 1)
+cudaError_t mmf_launch_refine_band_g(const MmfLaunch& L, const double2* X, double2* G);
 cudaError_t mmf_launch_refine_finish(const MmfLaunch& L, double2* X, double* E, const double* lam, double2* S,
                                      int64_t mat_elems);
 // Gram product on the BF16 tensor cores by exact integer slicing (k_ozaki.cu)
