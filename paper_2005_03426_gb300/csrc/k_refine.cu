@@ -20,10 +20,13 @@
 // needs FP32 relative accuracy (its absolute error is then ~eps32^2 |H_F|) and is taken on the
 // tensor cores in split TF32.  X Et only needs FP32 (Et is small) and is taken there as well.
 // G itself is needed only near the diagonal: off it, g_ij enters the update of a non-clustered
-// pair only through (lam_j - lam0_j) g_ij ~ eps32 |H_F| |g_ij|, negligible, and the pair's
-// orthogonality is restored through C (c_ij - conj(c_ji) = (lam0_i - lam0_j) g_ij, so
-// Et_ij + conj(Et_ji) ~ -g_ij).  Both steps therefore form G in double-FP32 on the band
-// |i - j| <= RF_W only, except a full second step (below), which forms all of it.
+// pair only through (lam_j - lam0_j) g_ij ~ eps32 |H_F| |g_ij|, negligible against c_ij there,
+// and the pair's orthogonality is restored through C (c_ij - conj(c_ji) = (lam0_i - lam0_j) g_ij,
+// so Et_ij + conj(Et_ji) ~ -g_ij).  Near pairs do need it: for a (near-)degenerate pair c_ij and
+// (lam_j - lam0_j) g_ij are both second order in the FP32 error, and G decides whether the pair
+// is clustered and gives a clustered pair's correction (keeping only the diagonal of G put a
+// quasienergy of the driven lattice 3e-5 off).  Both steps therefore form G in double-FP32 on the
+// band |i - j| <= RF_W only, except a full second step (below), which forms all of it.
 // A second full step (large n, where one step leaves second-order errors ~(eps32 |H_F| / gap)^2
 // between eigenpairs far apart in the sorted order) starts from FP64 X = X1 + Dx with
 // X1 = fl32(X): G = X1^H X1 + C' + C'^H + O(|Dx|^2) with C' = X1^H Dx, the first term by the
