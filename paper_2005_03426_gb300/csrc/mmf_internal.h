@@ -275,6 +275,9 @@ cudaError_t mmf_launch_refine_pre(const MmfLaunch& L, const float4* cs, const in
                                   int second);
 cudaError_t mmf_launch_refine_gram(const MmfLaunch& L, const float2* X1, double2* G, const double2* T, int second);
 cudaError_t mmf_launch_refine_gram_fix(const MmfLaunch& L, double2* G, const double2* T);
+// one Ogita-Aishima update (lam, Et, X <- X + X Et in place, cluster separation).  band_fp32: apply
+// the near band of Et in FP32 (only when another full-accuracy step follows); g_band: G was formed
+// only on the band |i - j| <= 16 and is taken as 0 off it.
 cudaError_t mmf_launch_refine_update(const MmfLaunch& L, const double2* coef, const int* pat, double2* X, const float2* X1,
                                      const double* lam0, double2* G, double2* HX, const double2* T, double* lam,
                                      int* status, int* cid, void* ops, void* jobs, double2* Eb,
